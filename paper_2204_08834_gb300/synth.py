@@ -1,0 +1,203 @@
+"""Seeded synthetic inputs for the projection step (shared by tests, smoke and bench).
+
+This module holds no arithmetic of the projection method itself: it only draws the
+fields that the method consumes (velocity predictor, density, two pressure levels)
+and the z grid, with the shapes and structure of the paper's workloads:
+
+  * sphere      - one sphere of density 10 in density 1, 32^3 periodic (a small case);
+  * emulsion    - a dispersed-droplet field in a triply periodic box, the shape of the
+                  emulsion-in-HIT run (Sec. 7.1: 512^3, dispersed droplets);
+  * two_layer   - a heavy layer under a light one between walls with a perturbed flat
+                  interface and tanh-stretched z, the shape of the two-layer
+                  Rayleigh-Benard run (Sec. 7.2: 1024x1024x512, aspect ratio 2, walls in z).
+
+Density follows the one-fluid rule rho = rho_1 phi + rho_2 (1 - phi) (Eq. material_prop)
+with a tanh volume-fraction profile of width 1.5 cells:
+phi = (1 - tanh(s / eps)) / 2, s the signed distance to the interface (positive outside
+the dense phase), eps = 0.75 * cell width, evaluated at cell centres.
+
+Every array is float64, C-contiguous, shape (nz, ny, nx); every random stream is a
+numpy PCG64 generator keyed by a fixed seed per field.
+"""
+
+import numpy as np
+
+__all__ = ["Case", "stretched_dzf", "sphere", "emulsion", "two_layer", "ensemble_member"]
+
+
+class Case(dict):
+    """A dict of inputs with attribute access: u, v, w, rho, pn, pnm1, dt, dx, dy, dzf, lz, bc."""
+
+    __getattr__ = dict.__getitem__
+
+    @property
+    def shape(self):
+        return self["rho"].shape
+
+    @property
+    def npts(self):
+        return int(np.prod(self["rho"].shape))
+
+
+def _rng(seed):
+    return np.random.Generator(np.random.PCG64(seed))
+
+
+def stretched_dzf(nz, lz, beta):
+    """Cell widths of the wall-clustered grid z_f(k) = lz (1 + tanh(beta (2k/nz - 1)) / tanh beta) / 2."""
+    k = np.arange(nz + 1, dtype=np.float64)
+    zf = lz * 0.5 * (1.0 + np.tanh(beta * (2.0 * k / nz - 1.0)) / np.tanh(beta))
+    zf[0], zf[-1] = 0.0, lz
+    return np.diff(zf)
+
+
+def _phi(s, eps):
+    return 0.5 * (1.0 - np.tanh(s / eps))
+
+
+def _droplet_phi(n, h, centres, radii, cutoff_cells=6.0):
+    """phi = max over droplets, each evaluated on a periodic box of radius r + cutoff cells."""
+    phi = np.zeros((n, n, n))
+    eps = 0.75 * h
+    for (cx, cy, cz), r in zip(centres, radii):
+        ext = min(int(np.ceil(r / h + cutoff_cells)), (n - 2) // 2)
+        idx = []
+        for c in (cz, cy, cx):
+            i0 = int(np.floor(c / h - 0.5))
+            idx.append(np.arange(i0 - ext, i0 + ext + 2))
+        kz, jy, ix = idx
+        zc = (kz + 0.5) * h - cz
+        yc = (jy + 0.5) * h - cy
+        xc = (ix + 0.5) * h - cx
+        dist = np.sqrt(zc[:, None, None] ** 2 + yc[None, :, None] ** 2 + xc[None, None, :] ** 2)
+        s = dist - r
+        local = np.where(s <= cutoff_cells * h, _phi(s, eps), 0.0)
+        sub = np.ix_(kz % n, jy % n, ix % n)
+        phi[sub] = np.maximum(phi[sub], local)
+    return phi
+
+
+def _place_droplets(rng, count, rmin, rmax, gap, max_tries=1_000_000):
+    """Random non-overlapping droplets in the unit periodic box (minimum-image gap test)."""
+    centres, radii = [], []
+    tries = 0
+    while len(centres) < count:
+        tries += 1
+        if tries > max_tries:
+            raise RuntimeError("droplet placement did not converge")
+        c = rng.random(3)
+        r = rng.uniform(rmin, rmax)
+        ok = True
+        for c2, r2 in zip(centres, radii):
+            d = np.abs(c - c2)
+            d = np.minimum(d, 1.0 - d)
+            if np.sqrt(np.sum(d * d)) < r + r2 + gap:
+                ok = False
+                break
+        if ok:
+            centres.append(c)
+            radii.append(r)
+    return np.array(centres), np.array(radii)
+
+
+def sphere(n=32, rho_in=10.0, rho_out=1.0, radius=0.25, dt=1e-3):
+    """One sphere in a triply periodic unit box; u** ~ U[-1, 1]; p^n, p^{n-1} ~ U[-1, 1]."""
+    h = 1.0 / n
+    centre = _rng(1).random(3)  # (x, y, z)
+    x = (np.arange(n) + 0.5) * h
+    d2 = 0.0
+    for axis, c in zip((2, 1, 0), centre):
+        dd = np.abs(x - c)
+        dd = np.minimum(dd, 1.0 - dd)
+        shape = [1, 1, 1]
+        shape[axis] = n
+        d2 = d2 + (dd ** 2).reshape(shape)
+    phi = _phi(np.sqrt(d2) - radius, 0.75 * h)
+    rho = rho_in * phi + rho_out * (1.0 - phi)
+    r2 = _rng(2)
+    u, v, w = (r2.uniform(-1.0, 1.0, (n, n, n)) for _ in range(3))
+    pn = _rng(3).uniform(-1.0, 1.0, (n, n, n))
+    pnm1 = _rng(4).uniform(-1.0, 1.0, (n, n, n))
+    return Case(u=u, v=v, w=w, rho=np.ascontiguousarray(rho), pn=pn, pnm1=pnm1, dt=dt,
+                dx=h, dy=h, dzf=np.full(n, h), lz=1.0, bc="periodic", name=f"sphere{n}")
+
+
+def emulsion(n=512, ratio=10.0, ndrops=200, rmin_cells=4.0, rmax_cells=12.0, dt=1e-3,
+             seed=10):
+    """Dispersed droplets (density `ratio`) in a carrier of density 1, triply periodic unit box.
+
+    Droplet radii U[rmin, rmax] cells, centres U[0,1)^3, rejected until every pair has a
+    minimum-image surface gap of at least 2 cells.  u** ~ N(0, 1);
+    p^n, p^{n-1} ~ N(0, 1) * 0.1 * rho0 h / dt.
+    """
+    h = 1.0 / n
+    centres, radii = _place_droplets(_rng(seed), ndrops, rmin_cells * h, rmax_cells * h, 2.0 * h)
+    phi = _droplet_phi(n, h, centres, radii)
+    rho = ratio * phi + 1.0 * (1.0 - phi)
+    del phi
+    r = _rng(seed + 1)
+    u = r.standard_normal((n, n, n))
+    v = r.standard_normal((n, n, n))
+    w = r.standard_normal((n, n, n))
+    scale = 0.1 * min(1.0, ratio) * h / dt
+    pn = _rng(seed + 2).standard_normal((n, n, n))
+    pn *= scale
+    pnm1 = _rng(seed + 3).standard_normal((n, n, n))
+    pnm1 *= scale
+    return Case(u=u, v=v, w=w, rho=rho, pn=pn, pnm1=pnm1, dt=dt, dx=h, dy=h,
+                dzf=np.full(n, h), lz=1.0, bc="periodic", name=f"emulsion{n}_r{ratio:g}")
+
+
+def two_layer(nx=512, ny=512, nz=256, lx=2.0, ly=2.0, lz=1.0, beta=1.5, rho_low=1.5,
+              rho_high=1.0, amp=0.02, dt=1e-3, seed=20, stretched=True):
+    """Heavy layer (rho_low) under a light one between z walls; interface at z = lz/2 + eta(x, y).
+
+    eta is a sum of three seeded sinusoidal modes scaled so that max |eta| = amp.
+    z is tanh-stretched with parameter beta (uniform if stretched=False).
+    u** ~ N(0, 1) with w = 0 on the top wall face; p^n, p^{n-1} as in `emulsion`.
+    """
+    dx, dy = lx / nx, ly / ny
+    dzf = stretched_dzf(nz, lz, beta) if stretched else np.full(nz, lz / nz)
+    zc = np.concatenate(([0.0], np.cumsum(dzf)[:-1])) + 0.5 * dzf
+    r = _rng(seed)
+    a = r.integers(1, 5, 3)
+    b = r.integers(1, 5, 3)
+    ph = r.uniform(0.0, 2.0 * np.pi, 3)
+    am = r.uniform(0.5, 1.0, 3)
+    x = (np.arange(nx) + 0.5) * dx
+    y = (np.arange(ny) + 0.5) * dy
+    eta = np.zeros((ny, nx))
+    for m in range(3):
+        eta += am[m] * np.sin(2.0 * np.pi * (a[m] * x[None, :] / lx + b[m] * y[:, None] / ly) + ph[m])
+    eta *= amp / np.max(np.abs(eta))
+    rho = np.empty((nz, ny, nx))
+    for k in range(nz):
+        phi = _phi(zc[k] - (0.5 * lz + eta), 0.75 * dzf[k])
+        rho[k] = rho_low * phi + rho_high * (1.0 - phi)
+    rr = _rng(seed + 1)
+    u = rr.standard_normal((nz, ny, nx))
+    v = rr.standard_normal((nz, ny, nx))
+    w = rr.standard_normal((nz, ny, nx))
+    w[-1] = 0.0
+    scale = 0.1 * min(rho_low, rho_high) * dx / dt
+    pn = _rng(seed + 2).standard_normal((nz, ny, nx))
+    pn *= scale
+    pnm1 = _rng(seed + 3).standard_normal((nz, ny, nx))
+    pnm1 *= scale
+    return Case(u=u, v=v, w=w, rho=rho, pn=pn, pnm1=pnm1, dt=dt, dx=dx, dy=dy, dzf=dzf,
+                lz=lz, bc="walls", name=f"two_layer{nx}x{ny}x{nz}")
+
+
+def ensemble_member(m, sizes=(32, 48, 64, 96, 128)):
+    """Member m of the mixed-size ensemble: size sizes[m % 5]; periodic z for even m, uniform
+    z walls for odd m; 8 droplets of density ratio U[1, 20]; seed 50 + m."""
+    n = sizes[m % len(sizes)]
+    r = _rng(50 + m)
+    ratio = float(r.uniform(1.0, 20.0))
+    rmin, rmax = max(2.0, n / 32.0), max(3.0, 3.0 * n / 32.0)
+    c = emulsion(n, ratio=ratio, ndrops=8, rmin_cells=rmin, rmax_cells=rmax, seed=1000 + 10 * m)
+    if m % 2 == 1:
+        c["bc"] = "walls"
+        c["w"][-1] = 0.0
+    c["name"] = f"member{m}_n{n}_{c['bc']}"
+    return c
