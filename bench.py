@@ -1,0 +1,381 @@
+#!/usr/bin/env python3
+"""Throughput of the GB300 projection step (set_density, rhs, solve to 1e-10, correct).
+
+Metric: Mpts/s per Poisson solve at 512^3, FP32+refine vs FP64, both at relative residual
+<= 1e-10.  One step is one pass of the whole hot path over the 512^3 emulsion workload
+(200 droplets of density 10 in density 1, triply periodic) with inputs resident in HBM:
+set_density (rho0 = min rho, face coefficients), rhs, solve (FP32 transforms + FP64
+residual refinement to 1e-10) and correct.  The FP64 direct path is timed the same way
+and reported beside it.
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl ours|reference] [--workload NAME]
+
+Prints ONE JSON line on rank 0.  Under torchrun (N > 1) every rank runs an independent
+replica of the workload (the single solve has no data-parallel split without an
+all-to-all), timing is the max over ranks, value = all ranks' points / that time.
+"""
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "Mpts/s per Poisson solve at 512³: FP32+refine vs FP64 at 1e-10 residual"
+
+WORKLOADS = {
+    "emulsion512": dict(kind="emulsion", n=512, ratio=10.0,
+                        desc="emulsion 512^3 triply periodic, 200 droplets r in [4,12] cells, density ratio 10, "
+                             "u** ~ N(0,1), dt = 1e-3"),
+    "emulsion512_r1": dict(kind="emulsion", n=512, ratio=1.0,
+                           desc="emulsion 512^3 triply periodic, 200 droplets, density ratio 1"),
+    "emulsion256": dict(kind="emulsion", n=256, ratio=10.0,
+                        desc="emulsion 256^3 triply periodic, 200 droplets, density ratio 10"),
+    "two_layer512": dict(kind="two_layer", nx=512, ny=512, nz=256,
+                         desc="two-layer 512x512x256, z walls, tanh-stretched dz (beta 1.5), density 1.5 under 1"),
+    "sphere32": dict(kind="sphere", n=32, desc="sphere 32^3 periodic, density 10 in 1"),
+}
+
+# Algorithmic FP64 flops per cell of k_rhs (each face flux once, FMA = 2 flops):
+# p~ = fma(-s2, p^{n-1}, s1 p^n) 3; three face fluxes q = fma(b, dp~, u) 3 x 3 = 9;
+# divergence: three differences 3, one scale 1, two FMAs 4 -> 8.  Total 20.
+RHS_FLOPS_PER_CELL = 20.0
+# Compulsory HBM bytes per cell of k_rhs: read u, v, w, bx, by, bz, p^n, p^{n-1}; write f.
+RHS_BYTES_PER_CELL = 9 * 8.0
+
+
+def make_case(name):
+    from paper_2204_08834_gb300 import synth
+    w = WORKLOADS[name]
+    if w["kind"] == "emulsion":
+        return synth.emulsion(w["n"], ratio=w["ratio"])
+    if w["kind"] == "two_layer":
+        return synth.two_layer(w["nx"], w["ny"], w["nz"])
+    return synth.sphere(w["n"])
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return d, "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+# FP64 pipe peak: 499.3 G DFMA lane-ops/s measured on this machine's GB300 by the committed
+# micro-benchmark (paper_2204_08834_gb300/microbench/peaks.cu) = 0.999 TFLOP/s with FMA = 2.
+FP64_TFLOPS_MEASURED = 0.9986
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clock and throttle reasons while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, f[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def run_ours(args, rank, world, dev):
+    import torch
+
+    from paper_2204_08834_gb300 import flups
+
+    torch.cuda.set_device(dev)
+    c = make_case(args.workload)
+    nz, ny, nx = c.shape
+    npts = c.npts
+    stream = torch.cuda.current_stream().cuda_stream
+    keys = ("u", "v", "w", "rho", "pn", "pnm1")
+    d0 = {k: torch.from_numpy(c[k]).cuda() for k in keys}
+    work = {k: torch.empty_like(d0["u"]) for k in ("u", "v", "w")}
+    f = torch.empty_like(d0["u"])
+    p = torch.empty_like(d0["u"])
+    torch.cuda.synchronize()
+
+    def timed_steps(plan, steps, warmup, rtol):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+        tot = {"set_density": 0.0, "rhs": 0.0, "solve": 0.0, "correct": 0.0, "step": 0.0}
+        iters, rel = [], []
+        l0 = None
+        for s in range(warmup + steps):
+            for k in ("u", "v", "w"):
+                work[k].copy_(d0[k])           # restore u** (outside the timed events)
+            if s == warmup:
+                torch.cuda.synchronize()
+                if world > 1:
+                    torch.distributed.barrier()
+                l0 = plan.launches
+            ev[0].record()
+            plan.set_density(d0["rho"])
+            ev[1].record()
+            plan.rhs(work["u"], work["v"], work["w"], d0["pn"], d0["pnm1"], 2.0, 1.0, c.dt, f)
+            ev[2].record()
+            info = plan.solve(f, p, rtol=rtol, max_iter=12)
+            ev[3].record()
+            plan.correct(p, d0["pn"], d0["pnm1"], 2.0, 1.0, c.dt, work["u"], work["v"], work["w"])
+            ev[4].record()
+            torch.cuda.synchronize()
+            if s >= warmup:
+                for q, k in enumerate(("set_density", "rhs", "solve", "correct")):
+                    tot[k] += ev[q].elapsed_time(ev[q + 1])
+                tot["step"] += ev[0].elapsed_time(ev[4])
+                iters.append(info.iters)
+                rel.append(info.rel_res)
+        launches = plan.launches - l0
+        return tot, iters, rel, launches
+
+    res = {}
+    with ClockSampler(dev) as clk:
+        for prec, steps in (("fp32_refine", args.steps), ("fp64", max(2, args.steps // 2))):
+            with flups.Plan(nx, ny, nz, c.dx, c.dy, c.dzf, c.bc, prec, stream) as plan:
+                res[prec] = timed_steps(plan, steps, args.warmup, args.rtol) + (steps,)
+    # max over ranks of the timed sum
+    t32 = res["fp32_refine"][0]["step"]
+    t64 = res["fp64"][0]["step"]
+    if world > 1:
+        tt = torch.tensor([t32, t64], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t32, t64 = float(tt[0]), float(tt[1])
+
+    out = {"c": c, "npts": npts, "res": res, "t32": t32, "t64": t64, "clocks": clk.summary()}
+
+    # end to end: the same projection through flups_project_host on pinned host buffers
+    if not args.no_e2e:
+        hb = {k: torch.empty(c.shape, dtype=torch.float64, pin_memory=True).numpy() for k in keys}
+        for k in keys:
+            np.copyto(hb[k], c[k])
+        pout = torch.empty(c.shape, dtype=torch.float64, pin_memory=True).numpy()
+        e2e_steps = max(1, min(args.steps, 3))
+        t_e2e = 0.0
+        with flups.Plan(nx, ny, nz, c.dx, c.dy, c.dzf, c.bc, "fp32_refine", stream) as plan:
+            for s in range(1 + e2e_steps):
+                for k in ("u", "v", "w"):
+                    np.copyto(hb[k], c[k])
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                plan.project_host(hb["u"], hb["v"], hb["w"], hb["rho"], hb["pn"], hb["pnm1"], 2.0, 1.0, c.dt, pout,
+                                  rtol=args.rtol, max_iter=12)
+                t1 = time.perf_counter()
+                if s >= 1:
+                    t_e2e += t1 - t0
+        if world > 1:
+            tt = torch.tensor([t_e2e], dtype=torch.float64, device="cuda")
+            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+            t_e2e = float(tt[0])
+        out["e2e"] = (t_e2e, e2e_steps)
+    return out
+
+
+def cpu_baseline():
+    """The FP64 oracle (numpy, as it stands) on a bounded sample: three 256^3 emulsion
+    projections (the 256^3 size of the same emulsion configuration)."""
+    import oracle
+    from paper_2204_08834_gb300 import synth
+
+    c = synth.emulsion(256, ratio=10.0)
+    g = oracle.make_grid(256, 256, 256, c.dx, c.dy, c.dzf, c.bc)
+    reps = 3
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        oracle.project(c.u, c.v, c.w, c.rho, c.pn, c.pnm1, 2.0, 1.0, c.dt, g)
+    t = time.perf_counter() - t0
+    return {"value": round(reps * c.npts / t / 1e6, 3), "unit": "Mpts/s", "cores": 1, "kind": "oracle",
+            "sample": "3 full projections (rhs, direct FP64 solve, correct) of the 256^3 emulsion case, "
+                      "numpy single-threaded"}
+
+
+def run_reference(args, rank, world):
+    """Reference arm: the FP64 oracle timed on the host cores (no reference program exists)."""
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_2204_08834_gb300 import synth
+
+    c = synth.emulsion(256, ratio=10.0)
+    g = oracle.make_grid(256, 256, 256, c.dx, c.dy, c.dzf, c.bc)
+    tot = 0.0
+    for s in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        oracle.project(c.u, c.v, c.w, c.rho, c.pn, c.pnm1, 2.0, 1.0, c.dt, g)
+        t1 = time.perf_counter()
+        if s >= args.warmup:
+            tot += t1 - t0
+    val = args.steps * c.npts / tot / 1e6
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(val, 3), "unit": "Mpts/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * tot / args.steps, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "emulsion 256^3 triply periodic, 200 droplets, density ratio 10 (bounded sample "
+                               "of the 512^3 emulsion workload)",
+                   "step": "oracle.project: rhs + FP64 direct solve + correct", "threads": 1},
+        "cpu_baseline": {"value": round(val, 3), "unit": "Mpts/s", "cores": 1, "kind": "oracle",
+                         "sample": "one 256^3 emulsion projection per step"},
+        "e2e": {"value": round(val, 3), "unit": "Mpts/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="emulsion512", choices=list(WORKLOADS))
+    ap.add_argument("--rtol", type=float, default=1e-10)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    if world > 1:
+        torch.cuda.set_device(local)
+        torch.distributed.init_process_group("nccl")
+    if not torch.cuda.is_available():
+        print(json.dumps({"metric": METRIC, "error": "no CUDA device"}))
+        return 1
+
+    out = run_ours(args, rank, world, local)
+    if world > 1:
+        torch.distributed.barrier()
+    if rank != 0:
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return 0
+
+    c, npts, res = out["c"], out["npts"], out["res"]
+    tot32, it32, rel32, l32, k32 = res["fp32_refine"]
+    tot64, it64, rel64, l64, k64 = res["fp64"]
+    ms32 = out["t32"] / k32
+    ms64 = out["t64"] / k64
+    value = world * npts / (ms32 * 1e-3) / 1e6
+    pk, pk_kind = peaks()
+    # roofline of k_rhs (one kernel per flups_rhs call, timed by its own events)
+    rhs_ms = tot32["rhs"] / k32
+    flops = RHS_FLOPS_PER_CELL * npts
+    achieved = flops / (rhs_ms * 1e-3) / 1e12
+    line = {
+        "metric": METRIC,
+        "value": round(value, 2),
+        "unit": "Mpts/s",
+        "n_gpus": world,
+        "steps": k32,
+        "warmup": args.warmup,
+        "ms_per_step": round(ms32, 4),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64+f32",
+        "data": "synthetic",
+        "config": {
+            "workload": WORKLOADS[args.workload]["desc"] + "; FP32 transforms + FP64 residual refinement to "
+                        f"rel. residual {args.rtol:g}",
+            "grid": list(c.shape[::-1]),
+            "step": "set_density + rhs + solve + correct (one projection)",
+            "l2": "inputs larger than L2 (each field 1 GiB at 512^3)",
+            "timing": "sum of per-step CUDA-event intervals on the launch stream; the copy that restores u** "
+                      "between steps is outside the events",
+            "parallelism": f"replicas x{world}",
+        },
+        "solve_mpts": round(world * npts / (tot32["solve"] / k32 * 1e-3) / 1e6, 2),
+        "breakdown_ms": {k: round(v / k32, 4) for k, v in tot32.items()},
+        "iters": statistics.median(it32),
+        "rel_res": max(rel32),
+        "fp64": {
+            "value": round(world * npts / (ms64 * 1e-3) / 1e6, 2),
+            "ms_per_step": round(ms64, 4),
+            "solve_mpts": round(world * npts / (tot64["solve"] / k64 * 1e-3) / 1e6, 2),
+            "breakdown_ms": {k: round(v / k64, 4) for k, v in tot64.items()},
+            "steps": k64,
+        },
+        "roofline": {
+            "kernel": "k_rhs",
+            "bound": "alu",
+            "achieved": round(achieved, 4),
+            "peak": FP64_TFLOPS_MEASURED,
+            "unit": "TFLOP/s",
+            "frac": round(achieved / FP64_TFLOPS_MEASURED, 4),
+            "traffic": None,
+            "peak_source": "FP64 DFMA rate measured by microbench/peaks.cu on this pool (not in MEASURED_PEAKS.json)",
+            "hbm_frac": round(RHS_BYTES_PER_CELL * npts / (rhs_ms * 1e-3) / 1e9 / pk["hbm_gbs"], 4),
+            "hbm_peak_source": pk_kind,
+        },
+        "gpu_launches": int(l32),
+        "clocks": out["clocks"],
+    }
+    if "e2e" in out:
+        t_e2e, ne = out["e2e"]
+        line["e2e"] = {"value": round(world * npts * ne / t_e2e / 1e6, 2), "unit": "Mpts/s",
+                       "h2d_bytes_per_step": 6 * 8 * npts, "d2h_bytes_per_step": 4 * 8 * npts,
+                       "steps": ne, "call": "flups_project_host (pinned host buffers)"}
+    if world == 1 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline()
+    print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,163 @@
+/*
+ * flups.h - C ABI of the GB300 (sm_103a) FFT pressure-projection library.
+ *
+ * The library computes the pressure-projection step of FluTAS (arXiv 2204.08834,
+ * Sec. 3.3 "Pressure correction algorithm", Eqs. us_predic, poisson, corr, p_upt) with
+ * the FFT/tridiagonal direct Poisson solver of Sec. 3.3.1:
+ *
+ *   f       = (rho0/dt) D u** + D[(1 - rho0/rho_f) G p_hat],   p_hat = c1 p^n - c2 p^{n-1}
+ *   L p     = f - <f>_V,   <p>_V = 0                            (L = D G, 7-point MAC operator)
+ *   u^{n+1} = u** - (dt/rho0) [G p - (1 - rho0/rho_f) G p_hat]
+ *
+ * with rho0 the minimum density (Sec. 3.3), rho_f the arithmetic mean of the two cell
+ * densities beside a face, and <.>_V the volume-weighted mean.  x and y are periodic;
+ * z is periodic (uniform spacing, third Fourier transform) or bounded by walls
+ * (homogeneous Neumann for p, w = 0 on the wall faces, possibly stretched spacing,
+ * Gauss elimination along z per (kx, ky) wavenumber).
+ *
+ * Layout of every field: float64, C-contiguous [nz][ny][nx] (x fastest), DEVICE memory
+ * owned by the caller unless a function says HOST.  u[k][j][i] is the x-face i+1/2,
+ * v[k][j][i] the y-face j+1/2, w[k][j][i] the z-face k+1/2 (top face of cell k; with
+ * walls w[nz-1] is the top wall face).  Field pointers must be 16-byte aligned.
+ *
+ * Streams: every call is stream-ordered on the plan's CUDA stream and returns without
+ * waiting for the GPU, except where a function says it synchronises.
+ *
+ * Errors: no call throws.  Argument errors are returned at once; CUDA errors are
+ * returned as FLUPS_ECUDA by the call that observes them.  A call that fails leaves
+ * the output buffers in an unspecified state.
+ */
+#ifndef FLUPS_H
+#define FLUPS_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct flups_plan_s* flups_plan;
+
+typedef enum {
+    FLUPS_OK = 0,
+    FLUPS_EINVAL = 1,        /* bad argument: null pointer, size, spacing, alignment       */
+    FLUPS_EUNSUPPORTED = 2,  /* size outside what the kernels support (see plan_create)     */
+    FLUPS_ENOMEM = 3,        /* device allocation failed                                   */
+    FLUPS_ECUDA = 4,         /* a CUDA runtime call or kernel launch failed                */
+    FLUPS_ENONFINITE = 5,    /* a non-finite or non-positive density, or a NaN residual    */
+    FLUPS_ENOCONV = 6,       /* refinement did not reach rtol within max_iter              */
+    FLUPS_ESTATE = 7         /* call order violated (rhs/correct before set_density)       */
+} flups_status;
+
+typedef enum { FLUPS_BC_PERIODIC = 0, FLUPS_BC_WALLS = 1 } flups_bc;
+
+typedef enum {
+    FLUPS_FP64 = 0,          /* FFTs and z solve in FP64, one direct pass                  */
+    FLUPS_FP32_REFINE = 1    /* FFTs and z solve in FP32; FP64 residual f - L p, FP64
+                                defect-correction update p += delta, repeated to rtol      */
+} flups_prec;
+
+#define FLUPS_HIST 16
+
+typedef struct {
+    int iters;                          /* FP32 solves performed (FP64: 1)                   */
+    double rel_res;                     /* ||f - <f> - L p||_2 / ||f - <f>||_2 last computed;
+                                           -1 when not computed (FP64 with rtol <= 0)        */
+    double rel_res_hist[FLUPS_HIST];    /* rel_res after each FP32 solve                     */
+} flups_info;
+
+/*
+ * flups_plan_create - plan a projection on an nx x ny x nz grid (Sec. 3, MAC grid).
+ *   nx, ny : even powers of two in [8, 4096] (x, y periodic).
+ *   nz     : power of two in [8, 4096] when bc = FLUPS_BC_PERIODIC; any value in
+ *            [2, 8192] with bc = FLUPS_BC_WALLS.
+ *            With prec = FLUPS_FP64, ny and a periodic nz are at most 2048.
+ *   dx, dy : uniform spacings (> 0).
+ *   dzf    : HOST array of nz cell widths along z (> 0), copied; must be uniform when
+ *            bc = FLUPS_BC_PERIODIC.  Cell centres lie midway between faces.
+ *   prec   : flups_prec.
+ *   stream : cudaStream_t (NULL = legacy default stream).
+ * The plan allocates its own device workspace (spectrum, face coefficients, tables);
+ * flups_workspace_bytes reports its size.  The current CUDA device is recorded and
+ * made current by every later call on the plan.
+ */
+flups_status flups_plan_create(flups_plan* out, int nx, int ny, int nz, double dx, double dy,
+                               const double* dzf, int bc, int prec, void* stream);
+flups_status flups_plan_destroy(flups_plan plan);
+flups_status flups_set_stream(flups_plan plan, void* stream);
+size_t       flups_workspace_bytes(flups_plan plan);
+/* flups_launch_count - number of CUDA kernels this plan has launched so far (host counter). */
+unsigned long long flups_launch_count(flups_plan plan);
+
+/*
+ * flups_set_density - register the density field for the next rhs/correct calls (Sec. 3.3).
+ *   rho  : DEVICE [nz][ny][nx], read once here; not retained.
+ *   rho0 : > 0 uses this value as rho0; <= 0 computes rho0 = min(rho) on the device
+ *          (Sec. 3.3: "the minimum value of the density field").
+ * Stores the face coefficients (1 - rho0/rho_f)/h per face in the plan workspace.
+ * Non-finite or non-positive densities are reported as FLUPS_ENONFINITE by the next
+ * synchronising call (flups_get_rho0 or flups_solve with info != NULL).
+ */
+flups_status flups_set_density(flups_plan plan, const double* rho, double rho0);
+
+/* flups_get_rho0 - copy rho0 to *rho0_host (HOST); synchronises the plan's stream. */
+flups_status flups_get_rho0(flups_plan plan, double* rho0_host);
+
+/*
+ * flups_rhs - right-hand side of the split Poisson equation (Eqs. us_predic + poisson):
+ *   f = (rho0/dt) D u** + D[(1 - rho0/rho_f) G p_hat],  p_hat = c1 p_n - c2 p_nm1.
+ *   u, v, w   : DEVICE, the predicted velocity u** (read only).
+ *   p_n, p_nm1: DEVICE pressures at t^n and t^{n-1}; p_nm1 may be NULL (then p_hat = c1 p_n).
+ *   c1, c2    : extrapolation weights (1 + r, r with r = dt^{n+1}/dt^n; 2 and 1 at constant dt).
+ *   dt        : > 0.
+ *   f         : DEVICE output [nz][ny][nx]; must not alias an input.
+ */
+flups_status flups_rhs(flups_plan plan, const double* u, const double* v, const double* w,
+                       const double* p_n, const double* p_nm1, double c1, double c2, double dt,
+                       double* f);
+
+/*
+ * flups_solve - p with L p = f - <f>_V and <p>_V = 0 (Sec. 3.3.1: forward FFT along x and
+ * y, Gauss elimination along z or a z FFT, inverse y and x).
+ *   f        : DEVICE input (read only); p : DEVICE output, may not alias f.
+ *   rtol     : FLUPS_FP32_REFINE: stop when the FP64 relative residual <= rtol (1e-10 for
+ *              the throughput metric); FLUPS_FP64: if > 0 and info != NULL the residual is
+ *              evaluated after the direct solve and reported (not needed otherwise).
+ *   max_iter : maximum number of FP32 solves (refine mode), 1..64.
+ *   info     : HOST, may be NULL.  Refine mode synchronises once per FP32 solve to read
+ *              the residual norm; FP64 mode synchronises only when info != NULL.
+ * Returns FLUPS_ENOCONV if rtol was not reached (p holds the last iterate),
+ * FLUPS_ENONFINITE if a residual norm is not finite.
+ */
+flups_status flups_solve(flups_plan plan, const double* f, double* p, double rtol, int max_iter,
+                         flups_info* info);
+
+/*
+ * flups_correct - velocity correction (Eqs. us_predic + corr):
+ *   u^{n+1} = u** - (dt/rho0) [G p - (1 - rho0/rho_f) G p_hat], in place on u, v, w.
+ *   p        : DEVICE solution of flups_solve; p_n, p_nm1, c1, c2 as in flups_rhs.
+ * With walls the top wall face w[nz-1] is set to 0.
+ */
+flups_status flups_correct(flups_plan plan, const double* p, const double* p_n,
+                           const double* p_nm1, double c1, double c2, double dt,
+                           double* u, double* v, double* w);
+
+/*
+ * flups_project_host - one whole projection with HOST buffers (end-to-end form):
+ * copies u, v, w, rho, p_n, p_nm1 to plan-owned device buffers, runs set_density(rho,
+ * rho0 = min), rhs, solve and correct, and copies u, v, w (in place) and p back.
+ * Host buffers should be page-locked for full copy bandwidth.  Synchronises.
+ */
+flups_status flups_project_host(flups_plan plan, double* u, double* v, double* w,
+                                const double* rho, const double* p_n, const double* p_nm1,
+                                double c1, double c2, double dt, double rtol, int max_iter,
+                                double* p_out, flups_info* info);
+
+/* flups_status_string - static, human-readable name of a status code. */
+const char* flups_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FLUPS_H */

@@ -1,0 +1,660 @@
+// fft_kernels.cu - transforms and z solves of the eigen-expansion Poisson solver
+// (FluTAS Sec. 3.3.1: forward transforms along x and y, Gauss elimination along z per
+// (kx, ky) or a third transform along z when z is periodic, inverse y and x).
+//
+// One batched, shared-memory Stockham engine (radix 8/4/2, register-resident butterflies)
+// serves every direction.  A CTA stages a tile of B independent lines in shared memory as
+// [n][c] (line index c fastest, pitch B+1), so that
+//   * x lines (rows of the field, contiguous in HBM) are read coalesced along x and
+//     transposed into the tile on the way in,
+//   * y and z lines (columns of the spectrum) are read as B consecutive kx values
+//     (128-256 contiguous bytes) per row at stride ldS or ny*ldS.
+// The real transform along x uses the half-length complex FFT with the standard
+// even/odd split (z_n = x_{2n} + i x_{2n+1}) and a post/pre-processing twiddle pass.
+// Transforms are unnormalised; the whole 1/(M ny nz) (or 1/(M ny) with walls) factor is
+// folded into the eigenvalue / tridiagonal tables, M = nx/2.
+#include "flups_impl.cuh"
+
+namespace {
+
+// ------------------------------------------------------------------ complex helpers
+template <typename C> __device__ __forceinline__ C cadd(C a, C b) { C r; r.x = a.x + b.x; r.y = a.y + b.y; return r; }
+template <typename C> __device__ __forceinline__ C csub(C a, C b) { C r; r.x = a.x - b.x; r.y = a.y - b.y; return r; }
+// a * w (forward) or a * conj(w) (inverse)
+template <bool INV, typename C> __device__ __forceinline__ C ctw(C a, C w) {
+    C r;
+    if (INV) { r.x = a.x * w.x + a.y * w.y; r.y = a.y * w.x - a.x * w.y; }
+    else     { r.x = a.x * w.x - a.y * w.y; r.y = a.x * w.y + a.y * w.x; }
+    return r;
+}
+// a * (-i) forward, a * (+i) inverse
+template <bool INV, typename C> __device__ __forceinline__ C cmi(C a) {
+    C r;
+    if (INV) { r.x = -a.y; r.y = a.x; } else { r.x = a.y; r.y = -a.x; }
+    return r;
+}
+
+template <bool INV, typename C> __device__ __forceinline__ void dft2(C* v) {
+    C t = v[0];
+    v[0] = cadd(t, v[1]);
+    v[1] = csub(t, v[1]);
+}
+
+template <bool INV, typename C> __device__ __forceinline__ void dft4(C& a0, C& a1, C& a2, C& a3) {
+    C s02 = cadd(a0, a2), d02 = csub(a0, a2), s13 = cadd(a1, a3), d13 = cmi<INV>(csub(a1, a3));
+    a0 = cadd(s02, s13);
+    a2 = csub(s02, s13);
+    a1 = cadd(d02, d13);
+    a3 = csub(d02, d13);
+}
+
+// 8-point DFT as two 4-point DFTs (even/odd inputs) and the W_8^k combination.
+template <bool INV, typename C> __device__ __forceinline__ void dft8(C* v) {
+    typedef decltype(v[0].x) T;
+    const T r = (T)0.70710678118654752440;
+    C e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6];
+    C o0 = v[1], o1 = v[3], o2 = v[5], o3 = v[7];
+    dft4<INV>(e0, e1, e2, e3);
+    dft4<INV>(o0, o1, o2, o3);
+    C t1, t2, t3;
+    if (INV) {  // W^-1 = (r, r), W^-2 = i, W^-3 = (-r, r)
+        t1.x = r * (o1.x - o1.y); t1.y = r * (o1.x + o1.y);
+        t2.x = -o2.y; t2.y = o2.x;
+        t3.x = -r * (o3.x + o3.y); t3.y = r * (o3.x - o3.y);
+    } else {    // W^1 = (r, -r), W^2 = -i, W^3 = (-r, -r)
+        t1.x = r * (o1.x + o1.y); t1.y = r * (o1.y - o1.x);
+        t2.x = o2.y; t2.y = -o2.x;
+        t3.x = r * (o3.y - o3.x); t3.y = -r * (o3.x + o3.y);
+    }
+    v[0] = cadd(e0, o0); v[4] = csub(e0, o0);
+    v[1] = cadd(e1, t1); v[5] = csub(e1, t1);
+    v[2] = cadd(e2, t2); v[6] = csub(e2, t2);
+    v[3] = cadd(e3, t3); v[7] = csub(e3, t3);
+}
+
+template <int R, bool INV, typename C> __device__ __forceinline__ void dftR(C* v) {
+    if (R == 2) dft2<INV>(v);
+    else if (R == 4) dft4<INV>(v[0], v[1], v[2], v[3]);
+    else dft8<INV>(v);
+}
+
+// One Stockham radix-R pass over B lines of length N held in shared memory as
+// s[n * pitch + c].  Butterfly j (0 <= j < N/R) of line c reads n = j + r N/R and writes
+// n = (j - k) R + k + r Ns with k = j mod Ns, after the twiddles W_{Ns R}^{k r}.
+// Every thread owns E/R butterflies (nthr * E == B * N).
+template <typename C, int E, int R, bool INV>
+__device__ __forceinline__ void stockham_pass(C* s, int pitch, int lgB, int N, int Ns,
+                                              const C* __restrict__ tw) {
+    constexpr int S = E / R;
+    const int nthr = blockDim.x, tid = threadIdx.x;
+    const int NR = N / R, twstep = N / (Ns * R), Bm = (1 << lgB) - 1;
+    C v[S][R];
+    int jj[S], cc[S];
+#pragma unroll
+    for (int t = 0; t < S; ++t) {
+        const int slot = tid + t * nthr;
+        cc[t] = slot & Bm;
+        jj[t] = slot >> lgB;
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[t][r] = s[(jj[t] + r * NR) * pitch + cc[t]];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int t = 0; t < S; ++t) {
+        const int k = jj[t] & (Ns - 1);
+        if (Ns > 1) {
+#pragma unroll
+            for (int r = 1; r < R; ++r) v[t][r] = ctw<INV>(v[t][r], __ldg(&tw[k * r * twstep]));
+        }
+        dftR<R, INV>(v[t]);
+        const int base = (jj[t] - k) * R + k;
+#pragma unroll
+        for (int r = 0; r < R; ++r) s[(base + r * Ns) * pitch + cc[t]] = v[t][r];
+    }
+    __syncthreads();
+}
+
+// Full transform of length L.n on the tile (all threads of the CTA take part).
+template <typename C, int E, bool INV>
+__device__ __forceinline__ void fft_tile(C* s, int pitch, int lgB, const FftLen& L, const C* __restrict__ tw) {
+    int Ns = 1;
+    for (int st = 0; st < L.nst; ++st) {
+        const int R = L.rad[st];
+        if (R == 8) stockham_pass<C, E, 8, INV>(s, pitch, lgB, L.n, Ns, tw);
+        else if (R == 4) stockham_pass<C, E, 4, INV>(s, pitch, lgB, L.n, Ns, tw);
+        else stockham_pass<C, E, 2, INV>(s, pitch, lgB, L.n, Ns, tw);
+        Ns *= R;
+    }
+}
+
+template <typename T> __device__ __forceinline__ typename cplx<T>::t mk(T a, T b) {
+    typename cplx<T>::t r; r.x = a; r.y = b; return r;
+}
+
+// Block-wide sum of up to three per-thread values into part[blockIdx.x * 3 + q].
+__device__ void block_sum3(double a, double b, double c, double* __restrict__ part) {
+    __shared__ double red[3][32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_down_sync(0xffffffffu, a, o);
+        b += __shfl_down_sync(0xffffffffu, b, o);
+        c += __shfl_down_sync(0xffffffffu, c, o);
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    if (lane == 0) { red[0][wid] = a; red[1][wid] = b; red[2][wid] = c; }
+    __syncthreads();
+    if (wid == 0) {
+        a = lane < nw ? red[0][lane] : 0.0;
+        b = lane < nw ? red[1][lane] : 0.0;
+        c = lane < nw ? red[2][lane] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            a += __shfl_down_sync(0xffffffffu, a, o);
+            b += __shfl_down_sync(0xffffffffu, b, o);
+            c += __shfl_down_sync(0xffffffffu, c, o);
+        }
+        if (lane == 0) {
+            part[blockIdx.x * 3 + 0] = a;
+            part[blockIdx.x * 3 + 1] = b;
+            part[blockIdx.x * 3 + 2] = c;
+        }
+    }
+}
+
+// ------------------------------------------------------------- forward along x (R2C)
+// MODE 0: input f (FP64).  With STATS, also the partial sums
+//         sum_k dzf_k sum_ij f (FP64), sum f^2 and sum f (FP32 per thread, FP64 across).
+// MODE 1: input r = f - (L p + <f>_V) evaluated in FP64 on the fly (the defect of the
+//         refinement), with the partial sum of r^2.
+template <typename T, int E, int MODE, bool STATS>
+__global__ void __launch_bounds__(1024) k_xfwd(const double* __restrict__ f, const double* __restrict__ p,
+                                               typename cplx<T>::t* __restrict__ S, Geo g, FftLen L,
+                                               const typename cplx<T>::t* __restrict__ tw,
+                                               const typename cplx<T>::t* __restrict__ twr,
+                                               const double* __restrict__ dd, int lgB, int nrows,
+                                               const DevScalars* __restrict__ sc, double* __restrict__ part) {
+    typedef typename cplx<T>::t C;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    C* s = reinterpret_cast<C*>(smraw);
+    const int B = 1 << lgB, pitch = B + 1, M = g.M, Mm = M - 1;
+    int lgM = 0;
+    while ((1 << lgM) < M) ++lgM;
+    const int row0 = blockIdx.x * B, tid = threadIdx.x, nthr = blockDim.x;
+    const int nx = g.nx;
+    double accw = 0.0;
+    float acc2 = 0.f, acc1 = 0.f;
+    double mf = 0.0;
+    if (MODE == 1) mf = sc->mean_f;
+    for (int idx = tid; idx < (B << lgM); idx += nthr) {
+        const int c = idx >> lgM, n = idx & Mm;
+        const int row = row0 + c;
+        C z = mk<T>((T)0, (T)0);
+        if (row < nrows) {
+            const double2 fv = __ldg(reinterpret_cast<const double2*>(f + (size_t)row * nx) + n);
+            if (MODE == 0) {
+                z = mk<T>((T)fv.x, (T)fv.y);
+                if (STATS) {
+                    const int k = row / g.ny;
+                    accw = fma(fv.x + fv.y, __ldg(g.dzf + k), accw);
+                    acc2 = fmaf((float)z.x, (float)z.x, fmaf((float)z.y, (float)z.y, acc2));
+                    acc1 += (float)z.x + (float)z.y;
+                }
+            } else {
+                const int k = row / g.ny, j = row - k * g.ny;
+                const int x0 = 2 * n;
+                const double* pr = p + (size_t)row * nx;
+                const double2 pc = __ldg(reinterpret_cast<const double2*>(pr) + n);
+                const double pw = __ldg(pr + ((x0 - 1) & (nx - 1)));
+                const double pe = __ldg(pr + ((x0 + 2) & (nx - 1)));
+                const int jm = (j - 1) & (g.ny - 1), jp = (j + 1) & (g.ny - 1);
+                int km, kp;
+                if (g.walls) { km = k > 0 ? k - 1 : 0; kp = k < g.nz - 1 ? k + 1 : g.nz - 1; }
+                else { km = (k - 1 + g.nz) % g.nz; kp = (k + 1) % g.nz; }
+                const double2 ps = __ldg(reinterpret_cast<const double2*>(p + ((size_t)k * g.ny + jm) * nx) + n);
+                const double2 pn = __ldg(reinterpret_cast<const double2*>(p + ((size_t)k * g.ny + jp) * nx) + n);
+                const double2 pb = __ldg(reinterpret_cast<const double2*>(p + ((size_t)km * g.ny + j) * nx) + n);
+                const double2 pt = __ldg(reinterpret_cast<const double2*>(p + ((size_t)kp * g.ny + j) * nx) + n);
+                const double azk = __ldg(g.az + k), czk = __ldg(g.cz + k), dk = __ldg(dd + k);
+                double a0 = fma(g.sx, pw + pc.y, mf);
+                a0 = fma(g.sy, ps.x + pn.x, a0);
+                a0 = fma(azk, pb.x, a0);
+                a0 = fma(czk, pt.x, a0);
+                a0 = fma(-dk, pc.x, a0);
+                double a1 = fma(g.sx, pc.x + pe, mf);
+                a1 = fma(g.sy, ps.y + pn.y, a1);
+                a1 = fma(azk, pb.y, a1);
+                a1 = fma(czk, pt.y, a1);
+                a1 = fma(-dk, pc.y, a1);
+                z = mk<T>((T)(fv.x - a0), (T)(fv.y - a1));
+                acc2 = fmaf((float)z.x, (float)z.x, fmaf((float)z.y, (float)z.y, acc2));
+            }
+        }
+        s[n * pitch + c] = z;
+    }
+    if (STATS || MODE == 1) block_sum3(accw, (double)acc2, (double)acc1, part);
+    __syncthreads();
+    fft_tile<C, E, false>(s, pitch, lgB, L, tw);
+    // X_k = A_k + W_nx^k B_k and X_{M-k} = conj(A_k - W_nx^k B_k), k = 0..M/2, with
+    // A_k = (Z_k + conj Z_{M-k})/2 and B_k = (Z_k - conj Z_{M-k})/(2i).
+    const int H = M / 2 + 1;
+    for (int idx = tid; idx < B * H; idx += nthr) {
+        const int c = idx / H, k = idx - c * H;
+        const int row = row0 + c;
+        if (row >= nrows) continue;
+        const C zk = s[k * pitch + c];
+        const C zm = s[((M - k) & Mm) * pitch + c];
+        const T ax = (zk.x + zm.x) * (T)0.5, ay = (zk.y - zm.y) * (T)0.5;
+        const T bxx = (zk.y + zm.y) * (T)0.5, byy = (zm.x - zk.x) * (T)0.5;
+        const C w = __ldg(&twr[k]);
+        const T tx = w.x * bxx - w.y * byy, ty = w.x * byy + w.y * bxx;
+        C* out = S + (size_t)row * g.ldS;
+        out[k] = mk<T>(ax + tx, ay + ty);
+        if (k != M - k) out[M - k] = mk<T>(ax - tx, ty - ay);
+    }
+}
+
+// ------------------------------------------------------------- inverse along x (C2R)
+// ACC = 0: p = x (FP64 store);  ACC = 1: p += x (FP64 defect-correction update).
+// MEAN (with ACC = 0): also the partial sums of dzf * p for the volume-weighted mean of the
+// first FP32 iterate, whose rounding leaves a constant of order eps32 |p| that the
+// residual cannot see; SUBM (with ACC = 1) removes that constant in the first update.
+template <typename T, int E, int ACC, bool MEAN, bool SUBM>
+__global__ void __launch_bounds__(1024) k_xinv(const typename cplx<T>::t* __restrict__ S, double* __restrict__ p,
+                                               Geo g, FftLen L, const typename cplx<T>::t* __restrict__ tw,
+                                               const typename cplx<T>::t* __restrict__ twr, int lgB, int nrows,
+                                               const DevScalars* __restrict__ sc, double* __restrict__ part) {
+    typedef typename cplx<T>::t C;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    C* s = reinterpret_cast<C*>(smraw);
+    const int B = 1 << lgB, pitch = B + 1, M = g.M, Mm = M - 1;
+    int lgM = 0;
+    while ((1 << lgM) < M) ++lgM;
+    const int row0 = blockIdx.x * B, tid = threadIdx.x, nthr = blockDim.x;
+    const int H = M / 2 + 1;
+    // Z_k = A_k + i B_k, Z_{M-k} = conj(A_k) + i conj(B_k) with A_k = (X_k + conj X_{M-k})/2,
+    // B_k = (X_k - conj X_{M-k}) conj(W_nx^k)/2; X_0 and X_M are taken real.
+    for (int idx = tid; idx < B * H; idx += nthr) {
+        const int c = idx / H, k = idx - c * H;
+        const int row = row0 + c;
+        C xk = mk<T>((T)0, (T)0), xm = xk;
+        if (row < nrows) {
+            const C* in = S + (size_t)row * g.ldS;
+            xk = in[k];
+            xm = in[M - k];
+            if (k == 0) { xk.y = (T)0; xm.y = (T)0; }
+        }
+        const T ax = (xk.x + xm.x) * (T)0.5, ay = (xk.y - xm.y) * (T)0.5;
+        const T dx = (xk.x - xm.x) * (T)0.5, dy = (xk.y + xm.y) * (T)0.5;
+        const C w = __ldg(&twr[k]);
+        const T bxx = dx * w.x + dy * w.y, byy = dy * w.x - dx * w.y;
+        s[k * pitch + c] = mk<T>(ax - byy, ay + bxx);
+        if (k != 0 && k != M - k) s[(M - k) * pitch + c] = mk<T>(ax + byy, bxx - ay);
+    }
+    __syncthreads();
+    fft_tile<C, E, true>(s, pitch, lgB, L, tw);
+    const int nx = g.nx;
+    double accw = 0.0;
+    T msub = (T)0;
+    if (SUBM) msub = (T)sc->mean_p;
+    for (int idx = tid; idx < (B << lgM); idx += nthr) {
+        const int c = idx >> lgM, n = idx & Mm;
+        const int row = row0 + c;
+        if (row >= nrows) continue;
+        C z = s[n * pitch + c];
+        if (SUBM) { z.x -= msub; z.y -= msub; }
+        double2* dst = reinterpret_cast<double2*>(p + (size_t)row * nx) + n;
+        double2 o;
+        if (ACC) {
+            o = *dst;
+            o.x += (double)z.x;
+            o.y += (double)z.y;
+        } else {
+            o.x = (double)z.x;
+            o.y = (double)z.y;
+            if (MEAN) accw = fma(o.x + o.y, __ldg(g.dzf + row / g.ny), accw);
+        }
+        *dst = o;
+    }
+    if (MEAN) block_sum3(accw, 0.0, 0.0, part);
+}
+
+// ------------------------------------------------------- column transform along y
+template <typename T, int E, bool INV>
+__global__ void __launch_bounds__(1024) k_ycol(typename cplx<T>::t* __restrict__ S, Geo g, FftLen L,
+                                               const typename cplx<T>::t* __restrict__ tw, int lgB, int kx0) {
+    typedef typename cplx<T>::t C;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    C* s = reinterpret_cast<C*>(smraw);
+    const int B = 1 << lgB, pitch = B + 1;
+    const int kxa = kx0 + blockIdx.x * B;
+    const int ncol = min(B, g.nxh - kxa);
+    C* base = S + (size_t)blockIdx.y * g.ny * g.ldS + kxa;
+    const int tid = threadIdx.x, nthr = blockDim.x, N = g.ny;
+    for (int idx = tid; idx < B * N; idx += nthr) {
+        const int c = idx & (B - 1), j = idx >> lgB;
+        s[j * pitch + c] = c < ncol ? base[(size_t)j * g.ldS + c] : mk<T>((T)0, (T)0);
+    }
+    __syncthreads();
+    fft_tile<C, E, INV>(s, pitch, lgB, L, tw);
+    for (int idx = tid; idx < B * N; idx += nthr) {
+        const int c = idx & (B - 1), j = idx >> lgB;
+        if (c < ncol) base[(size_t)j * g.ldS + c] = s[j * pitch + c];
+    }
+}
+
+// -------------------------------------- periodic z: forward z FFT, divide, inverse z FFT
+// lam tables hold eigenvalue / norm; the (0,0,0) mode is set to zero (zero-mean p).
+template <typename T, int E>
+__global__ void __launch_bounds__(1024) k_zper(typename cplx<T>::t* __restrict__ S, Geo g, FftLen L,
+                                               const typename cplx<T>::t* __restrict__ tw,
+                                               const T* __restrict__ lamx, const T* __restrict__ lamy,
+                                               const T* __restrict__ lamz, int lgB, int kx0) {
+    typedef typename cplx<T>::t C;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    C* s = reinterpret_cast<C*>(smraw);
+    const int B = 1 << lgB, pitch = B + 1;
+    const int kxa = kx0 + blockIdx.x * B, ky = blockIdx.y;
+    const int ncol = min(B, g.nxh - kxa);
+    const size_t zs = (size_t)g.ny * g.ldS;
+    C* base = S + (size_t)ky * g.ldS + kxa;
+    const int tid = threadIdx.x, nthr = blockDim.x, N = g.nz;
+    for (int idx = tid; idx < B * N; idx += nthr) {
+        const int c = idx & (B - 1), k = idx >> lgB;
+        s[k * pitch + c] = c < ncol ? base[k * zs + c] : mk<T>((T)0, (T)0);
+    }
+    __syncthreads();
+    fft_tile<C, E, false>(s, pitch, lgB, L, tw);
+    const T lxy0 = __ldg(&lamy[ky]);
+    for (int idx = tid; idx < B * N; idx += nthr) {
+        const int c = idx & (B - 1), k = idx >> lgB;
+        const int kx = min(kxa + c, g.nxh - 1);
+        const T lam = __ldg(&lamx[kx]) + lxy0 + __ldg(&lamz[k]);
+        const T inv = lam != (T)0 ? (T)1 / lam : (T)0;
+        C v = s[k * pitch + c];
+        v.x *= inv;
+        v.y *= inv;
+        s[k * pitch + c] = v;
+    }
+    __syncthreads();
+    fft_tile<C, E, true>(s, pitch, lgB, L, tw);
+    for (int idx = tid; idx < B * N; idx += nthr) {
+        const int c = idx & (B - 1), k = idx >> lgB;
+        if (c < ncol) base[k * zs + c] = s[k * pitch + c];
+    }
+}
+
+// ------------------------------------------ z walls: Gauss elimination (Thomas) along z
+// One thread per (kx, ky) column; neighbouring threads take neighbouring kx, so every row
+// access of a warp is a contiguous run.  tri = [a_k, b_k, c_k] / norm.  The forward
+// multipliers c'_k go to a scratch array, the eliminated right-hand side d'_k overwrites
+// the spectrum in place, then the back substitution overwrites it with the solution.
+// Column (0, 0) is singular: its row 0 is dropped, P_0 = 0, and the column is shifted
+// to zero dzf-weighted mean.
+template <typename T>
+__global__ void __launch_bounds__(128) k_ztri(typename cplx<T>::t* __restrict__ S, T* __restrict__ cps, Geo g,
+                                              const T* __restrict__ lamx, const T* __restrict__ lamy,
+                                              const T* __restrict__ tri) {
+    typedef typename cplx<T>::t C;
+    const int ncols = g.nxh * g.ny;
+    const int col = blockIdx.x * blockDim.x + threadIdx.x;
+    if (col >= ncols) return;
+    const int ky = col / g.nxh, kx = col - ky * g.nxh;
+    const int nz = g.nz;
+    const T* ta = tri;
+    const T* tb = tri + nz;
+    const T* tc = tri + 2 * nz;
+    const size_t zs = (size_t)g.ny * g.ldS;
+    C* x = S + (size_t)ky * g.ldS + kx;
+    T* cp = cps + col;
+    const size_t cs = (size_t)ncols;
+    const bool sing = (col == 0);
+    const T lam = sing ? (T)0 : __ldg(&lamx[kx]) + __ldg(&lamy[ky]);
+    const int k0 = sing ? 1 : 0;
+    T cprev = (T)0;
+    C dprev = mk<T>((T)0, (T)0);
+    for (int k = k0; k < nz; ++k) {
+        const T a = k > k0 ? __ldg(&ta[k]) : (T)0;
+        const T m = (__ldg(&tb[k]) + lam) - a * cprev;
+        const T inv = (T)1 / m;
+        const C F = x[k * zs];
+        cprev = __ldg(&tc[k]) * inv;
+        dprev = mk<T>((F.x - a * dprev.x) * inv, (F.y - a * dprev.y) * inv);
+        cp[k * cs] = cprev;
+        x[k * zs] = dprev;
+    }
+    C xv = dprev;
+    T sx = (T)0, sy = (T)0;
+    if (sing) { const T w = (T)g.dzf[nz - 1]; sx = w * xv.x; sy = w * xv.y; }
+    for (int k = nz - 2; k >= k0; --k) {
+        const T c = cp[k * cs];
+        const C d = x[k * zs];
+        xv = mk<T>(d.x - c * xv.x, d.y - c * xv.y);
+        x[k * zs] = xv;
+        if (sing) { const T w = (T)g.dzf[k]; sx += w * xv.x; sy += w * xv.y; }
+    }
+    if (sing) {
+        x[0] = mk<T>((T)0, (T)0);
+        T sw = (T)0;
+        for (int k = 0; k < nz; ++k) sw += (T)g.dzf[k];
+        const T mx = sx / sw, my = sy / sw;
+        for (int k = 0; k < nz; ++k) {
+            C v = x[k * zs];
+            v.x -= mx;
+            v.y -= my;
+            x[k * zs] = v;
+        }
+    }
+}
+
+// Deterministic final reduction of the per-block partial sums (one block).
+__global__ void k_finalize(const double* __restrict__ part, int nblk, DevScalars* sc, int what, double nrm_w,
+                           double npts) {
+    __shared__ double red[3][32];
+    double a = 0.0, b = 0.0, c = 0.0;
+    for (int i = threadIdx.x; i < nblk; i += blockDim.x) {
+        a += part[3 * i + 0];
+        b += part[3 * i + 1];
+        c += part[3 * i + 2];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_down_sync(0xffffffffu, a, o);
+        b += __shfl_down_sync(0xffffffffu, b, o);
+        c += __shfl_down_sync(0xffffffffu, c, o);
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (lane == 0) { red[0][wid] = a; red[1][wid] = b; red[2][wid] = c; }
+    __syncthreads();
+    if (wid == 0) {
+        a = lane < nw ? red[0][lane] : 0.0;
+        b = lane < nw ? red[1][lane] : 0.0;
+        c = lane < nw ? red[2][lane] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            a += __shfl_down_sync(0xffffffffu, a, o);
+            b += __shfl_down_sync(0xffffffffu, b, o);
+            c += __shfl_down_sync(0xffffffffu, c, o);
+        }
+        if (lane == 0) {
+            if (what == 0) {          // a = sum dzf f, b = sum f^2, c = sum f
+                const double m = a * nrm_w;
+                sc->mean_f = m;
+                sc->f2 = b - 2.0 * m * c + npts * m * m;
+            } else if (what == 1) {   // b = sum r^2
+                sc->r2 = b;
+            } else {                  // a = sum dzf p
+                sc->mean_p = a * nrm_w;
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------------- host helpers
+int ilog2i(int x) { int l = 0; while ((1 << l) < x) ++l; return l; }
+
+// Tile width B (lines per CTA): as wide as possible up to bmax while the CTA has at most
+// 1024 threads and 74 KB of tile (three CTAs per SM).
+int pick_lgB(int N, int csize, int E, int bmax, int ncols) {
+    int B = bmax;
+    while (B > 1 && ((long)B * N / E > 1024 || (long)N * (B + 1) * csize > 74 * 1024)) B >>= 1;
+    while (B > 1 && B > ncols) B >>= 1;
+    while ((long)B * N < E) B <<= 1;
+    return ilog2i(B);
+}
+
+template <typename K> void allow_smem(K kern) {
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 74 * 1024);
+}
+
+template <typename T> struct Eof { static const int E = sizeof(T) == 4 ? 16 : 8; };
+
+template <typename T, bool INV>
+void run_ycol(flups_plan P, typename cplx<T>::t* S, const Geo& g) {
+    typedef typename cplx<T>::t C;
+    const int E = Eof<T>::E, N = g.ny;
+    const int lgB = pick_lgB(N, sizeof(C), E, sizeof(T) == 4 ? 32 : 16, g.M);
+    const int B = 1 << lgB;
+    auto kern = k_ycol<T, Eof<T>::E, INV>;
+    allow_smem(kern);
+    const size_t sm = (size_t)N * (B + 1) * sizeof(C);
+    kern<<<dim3(g.M / B, g.nz), B * N / E, sm, P->stream>>>(S, g, P->ly, (const C*)P->twy, lgB, 0);
+    const int lgT = ilog2i(N >= E ? 1 : E / N);   // the Nyquist column kx = M
+    const int BT = 1 << lgT;
+    kern<<<dim3(1, g.nz), BT * N / E, (size_t)N * (BT + 1) * sizeof(C), P->stream>>>(S, g, P->ly, (const C*)P->twy, lgT, g.M);
+    FLUPS_COUNT(P, 2);
+}
+
+template <typename T>
+void run_zsolve(flups_plan P, typename cplx<T>::t* S, const Geo& g) {
+    typedef typename cplx<T>::t C;
+    const int E = Eof<T>::E;
+    if (!g.walls) {
+        const int N = g.nz;
+        const int lgB = pick_lgB(N, sizeof(C), E, sizeof(T) == 4 ? 32 : 16, g.M);
+        const int B = 1 << lgB;
+        auto kern = k_zper<T, Eof<T>::E>;
+        allow_smem(kern);
+        kern<<<dim3(g.M / B, g.ny), B * N / E, (size_t)N * (B + 1) * sizeof(C), P->stream>>>(
+            S, g, P->lz, (const C*)P->twz, (const T*)P->lamx, (const T*)P->lamy, (const T*)P->lamz, lgB, 0);
+        const int lgT = ilog2i(N >= E ? 1 : E / N);
+        const int BT = 1 << lgT;
+        kern<<<dim3(1, g.ny), BT * N / E, (size_t)N * (BT + 1) * sizeof(C), P->stream>>>(
+            S, g, P->lz, (const C*)P->twz, (const T*)P->lamx, (const T*)P->lamy, (const T*)P->lamz, lgT, g.M);
+        FLUPS_COUNT(P, 2);
+    } else {
+        const int ncols = g.nxh * g.ny;
+        k_ztri<T><<<(ncols + 127) / 128, 128, 0, P->stream>>>(S, (T*)P->zscr, g, (const T*)P->lamx,
+                                                                (const T*)P->lamy, (const T*)P->tri);
+        FLUPS_COUNT(P, 1);
+    }
+}
+
+template <typename T, int MODE, bool STATS>
+void run_xfwd(flups_plan P, const double* f, const double* p, const Geo& g) {
+    typedef typename cplx<T>::t C;
+    const int E = Eof<T>::E, N = g.M, nrows = g.ny * g.nz;
+    const int lgB = pick_lgB(N, sizeof(C), E, sizeof(T) == 4 ? 32 : 16, nrows);
+    const int B = 1 << lgB;
+    auto kern = k_xfwd<T, Eof<T>::E, MODE, STATS>;
+    allow_smem(kern);
+    const int nblk = (nrows + B - 1) / B;
+    kern<<<nblk, B * N / E, (size_t)N * (B + 1) * sizeof(C), P->stream>>>(
+        f, p, (C*)P->spec, g, P->lx, (const C*)P->twx, (const C*)P->twxr, P->tabs64 + 5 * g.nz, lgB, nrows,
+        P->sc, P->part);
+    FLUPS_COUNT(P, 1);
+}
+
+template <typename T, int ACC, bool MEAN, bool SUBM>
+void run_xinv(flups_plan P, double* p, const Geo& g) {
+    typedef typename cplx<T>::t C;
+    const int E = Eof<T>::E, N = g.M, nrows = g.ny * g.nz;
+    const int lgB = pick_lgB(N, sizeof(C), E, sizeof(T) == 4 ? 32 : 16, nrows);
+    const int B = 1 << lgB;
+    auto kern = k_xinv<T, Eof<T>::E, ACC, MEAN, SUBM>;
+    allow_smem(kern);
+    const int nblk = (nrows + B - 1) / B;
+    kern<<<nblk, B * N / E, (size_t)N * (B + 1) * sizeof(C), P->stream>>>(
+        (const C*)P->spec, p, g, P->lx, (const C*)P->twx, (const C*)P->twxr, lgB, nrows, P->sc, P->part);
+    FLUPS_COUNT(P, 1);
+}
+
+int xfwd_blocks(flups_plan P, int csize, int E) {
+    const int nrows = P->ny * P->nz;
+    const int lgB = pick_lgB(P->M, csize, E, csize == 8 ? 32 : 16, nrows);
+    return (nrows + (1 << lgB) - 1) >> lgB;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ launchers
+cudaError_t launch_solve64(flups_plan P, const double* f, double* p) {
+    const Geo g = plan_geo(P);
+    run_xfwd<double, 0, false>(P, f, nullptr, g);
+    run_ycol<double, false>(P, (double2*)P->spec, g);
+    run_zsolve<double>(P, (double2*)P->spec, g);
+    run_ycol<double, true>(P, (double2*)P->spec, g);
+    run_xinv<double, 0, false, false>(P, p, g);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_xfwd32_from_f(flups_plan P, const double* f) {
+    const Geo g = plan_geo(P);
+    run_xfwd<float, 0, true>(P, f, nullptr, g);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finalize_f(flups_plan P) {
+    const int nblk = xfwd_blocks(P, 8, 16);
+    k_finalize<<<1, 1024, 0, P->stream>>>(P->part, nblk, P->sc, 0, 1.0 / ((double)P->nx * P->ny * P->sum_dzf),
+                                          (double)P->npts);
+    FLUPS_COUNT(P, 1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_xfwd32_residual(flups_plan P, const double* f, const double* p) {
+    const Geo g = plan_geo(P);
+    run_xfwd<float, 1, false>(P, f, p, g);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finalize_r(flups_plan P) {
+    const int nblk = xfwd_blocks(P, 8, 16);
+    k_finalize<<<1, 1024, 0, P->stream>>>(P->part, nblk, P->sc, 1, 0.0, 0.0);
+    FLUPS_COUNT(P, 1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_yz_solve32(flups_plan P) {
+    const Geo g = plan_geo(P);
+    run_ycol<float, false>(P, (float2*)P->spec, g);
+    run_zsolve<float>(P, (float2*)P->spec, g);
+    run_ycol<float, true>(P, (float2*)P->spec, g);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_xinv32(flups_plan P, double* p, int mode) {
+    const Geo g = plan_geo(P);
+    if (mode == 0) {                       // p = delta, and the volume-weighted mean of p
+        run_xinv<float, 0, true, false>(P, p, g);
+        const int nblk = xfwd_blocks(P, 8, 16);
+        k_finalize<<<1, 1024, 0, P->stream>>>(P->part, nblk, P->sc, 2, 1.0 / ((double)P->nx * P->ny * P->sum_dzf), 0.0);
+        FLUPS_COUNT(P, 1);
+    } else if (mode == 1) {                // p += delta - <p_0>
+        run_xinv<float, 1, false, true>(P, p, g);
+    } else {                               // p += delta
+        run_xinv<float, 1, false, false>(P, p, g);
+    }
+    return cudaGetLastError();
+}
+
+size_t flups_part_blocks_needed(int nx, int ny, int nz) {
+    const int M = nx / 2, nrows = ny * nz;
+    size_t worst = 0;
+    const int cs[2] = {8, 16}, es[2] = {16, 8};
+    for (int q = 0; q < 2; ++q) {
+        const int lgB = pick_lgB(M, cs[q], es[q], cs[q] == 8 ? 32 : 16, nrows);
+        const size_t nb = (size_t)((nrows + (1 << lgB) - 1) >> lgB);
+        if (nb > worst) worst = nb;
+    }
+    return worst;
+}

@@ -1,0 +1,427 @@
+// flups_api.cu - the C ABI declared in include/flups.h: plans, workspace, tables, and the
+// sequencing of the kernels (FluTAS Sec. 3.3 projection; Sec. 3.3.1 solver step order).
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "flups_impl.cuh"
+
+size_t flups_part_blocks_needed(int nx, int ny, int nz);
+
+namespace {
+
+bool pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
+
+// Radix sequence for n = 2^m: as many radix-8 passes as possible, then a 4 (or 4, 4 / 2).
+bool make_len(int n, FftLen* L) {
+    if (!pow2(n)) return false;
+    int m = 0;
+    while ((1 << m) < n) ++m;
+    L->n = n;
+    L->nst = 0;
+    int q = m / 3, r = m % 3;
+    if (r == 1 && q >= 1) { q -= 1; r = 4; }
+    for (int i = 0; i < q; ++i) L->rad[L->nst++] = 8;
+    if (r == 2) L->rad[L->nst++] = 4;
+    else if (r == 4) { L->rad[L->nst++] = 4; L->rad[L->nst++] = 4; }
+    else if (r == 1) L->rad[L->nst++] = 2;
+    return L->nst <= FLUPS_MAX_STAGES;
+}
+
+// -4 sin^2(pi k / n) / h^2: the eigenvalues (2 cos(2 pi k/n) - 2)/h^2 without cancellation.
+double eig(int k, int n, double h) {
+    const double s = std::sin(M_PI * (double)k / (double)n);
+    return -4.0 * s * s / (h * h);
+}
+
+struct DevAlloc {
+    std::vector<void*> ptrs;
+    bool ok = true;
+    void* get(size_t bytes) {
+        void* p = nullptr;
+        if (cudaMalloc(&p, bytes ? bytes : 16) != cudaSuccess) { ok = false; return nullptr; }
+        ptrs.push_back(p);
+        return p;
+    }
+};
+
+template <typename T>
+void twiddles(std::vector<T>& out, int n, int count) {
+    out.resize(2 * (size_t)count);
+    for (int m = 0; m < count; ++m) {
+        const double a = 2.0 * M_PI * (double)m / (double)n;
+        out[2 * m] = (T)std::cos(a);
+        out[2 * m + 1] = (T)(-std::sin(a));
+    }
+}
+
+template <typename T>
+bool upload(void** dst, const std::vector<T>& v, DevAlloc& A) {
+    *dst = A.get(v.size() * sizeof(T));
+    if (!*dst) return false;
+    return cudaMemcpy(*dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice) == cudaSuccess;
+}
+
+template <typename T>
+bool build_tables(flups_plan P, const std::vector<double>& dzf, DevAlloc& A) {
+    std::vector<T> tw;
+    twiddles(tw, P->M, P->M);
+    if (!upload(&P->twx, tw, A)) return false;
+    twiddles(tw, P->nx, P->M / 2 + 1);
+    if (!upload(&P->twxr, tw, A)) return false;
+    twiddles(tw, P->ny, P->ny);
+    if (!upload(&P->twy, tw, A)) return false;
+    const bool walls = P->bc == FLUPS_BC_WALLS;
+    // inverse of the overall normalisation of the unnormalised transforms
+    const double scale = (double)P->M * P->ny * (walls ? 1.0 : (double)P->nz);
+    std::vector<T> lx(P->nxh), ly(P->ny);
+    for (int k = 0; k < P->nxh; ++k) lx[k] = (T)(eig(k, P->nx, P->dx) * scale);
+    for (int k = 0; k < P->ny; ++k) ly[k] = (T)(eig(k, P->ny, P->dy) * scale);
+    if (!upload(&P->lamx, lx, A) || !upload(&P->lamy, ly, A)) return false;
+    if (!walls) {
+        twiddles(tw, P->nz, P->nz);
+        if (!upload(&P->twz, tw, A)) return false;
+        std::vector<T> lz(P->nz);
+        for (int k = 0; k < P->nz; ++k) lz[k] = (T)(eig(k, P->nz, dzf[0]) * scale);
+        if (!upload(&P->lamz, lz, A)) return false;
+    } else {
+        const int nz = P->nz;
+        std::vector<T> tri(3 * (size_t)nz);
+        for (int k = 0; k < nz; ++k) {
+            const double a = k > 0 ? 1.0 / (dzf[k] * 0.5 * (dzf[k - 1] + dzf[k])) : 0.0;
+            const double c = k < nz - 1 ? 1.0 / (dzf[k] * 0.5 * (dzf[k] + dzf[k + 1])) : 0.0;
+            tri[k] = (T)(a * scale);
+            tri[nz + k] = (T)(-(a + c) * scale);
+            tri[2 * nz + k] = (T)(c * scale);
+        }
+        if (!upload(&P->tri, tri, A)) return false;
+        P->zscr = A.get((size_t)P->nxh * P->ny * nz * sizeof(T));
+        if (!P->zscr) return false;
+    }
+    return true;
+}
+
+flups_status cuda_status(cudaError_t e) {
+    if (e == cudaSuccess) return FLUPS_OK;
+    if (e == cudaErrorMemoryAllocation) return FLUPS_ENOMEM;
+    return FLUPS_ECUDA;
+}
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+        else prev = -1;
+    }
+    ~DeviceGuard() { if (prev >= 0) cudaSetDevice(prev); }
+};
+
+bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+flups_status sync_scalars(flups_plan P) {
+    cudaError_t e = cudaMemcpyAsync(P->sc_host, P->sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, P->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(P->stream);
+    return cuda_status(e);
+}
+
+}  // namespace
+
+Geo plan_geo(flups_plan P) {
+    Geo g;
+    g.nx = P->nx; g.ny = P->ny; g.nz = P->nz; g.M = P->M; g.nxh = P->nxh; g.ldS = P->ldS;
+    g.walls = P->bc == FLUPS_BC_WALLS;
+    g.uniform_z = 0;
+    g.dx = P->dx; g.dy = P->dy;
+    g.sx = 1.0 / (P->dx * P->dx); g.sy = 1.0 / (P->dy * P->dy);
+    const int nz = P->nz;
+    g.idzf = P->tabs64;
+    g.az = P->tabs64 + nz;
+    g.cz = P->tabs64 + 2 * nz;
+    g.idzc = P->tabs64 + 3 * nz;
+    g.dzf = P->tabs64 + 4 * nz;
+    return g;
+}
+
+extern "C" {
+
+const char* flups_status_string(int s) {
+    switch (s) {
+        case FLUPS_OK: return "FLUPS_OK";
+        case FLUPS_EINVAL: return "FLUPS_EINVAL: invalid argument";
+        case FLUPS_EUNSUPPORTED: return "FLUPS_EUNSUPPORTED: size not supported";
+        case FLUPS_ENOMEM: return "FLUPS_ENOMEM: device allocation failed";
+        case FLUPS_ECUDA: return "FLUPS_ECUDA: CUDA error";
+        case FLUPS_ENONFINITE: return "FLUPS_ENONFINITE: non-finite or invalid value";
+        case FLUPS_ENOCONV: return "FLUPS_ENOCONV: refinement did not converge";
+        case FLUPS_ESTATE: return "FLUPS_ESTATE: call order violated";
+        default: return "unknown flups status";
+    }
+}
+
+flups_status flups_plan_create(flups_plan* out, int nx, int ny, int nz, double dx, double dy,
+                               const double* dzf, int bc, int prec, void* stream) {
+    if (!out) return FLUPS_EINVAL;
+    *out = nullptr;
+    if (!dzf || !(dx > 0.0) || !(dy > 0.0) || !std::isfinite(dx) || !std::isfinite(dy)) return FLUPS_EINVAL;
+    if (bc != FLUPS_BC_PERIODIC && bc != FLUPS_BC_WALLS) return FLUPS_EINVAL;
+    if (prec != FLUPS_FP64 && prec != FLUPS_FP32_REFINE) return FLUPS_EINVAL;
+    if (nx <= 0 || ny <= 0 || nz <= 0) return FLUPS_EINVAL;
+    if (!pow2(nx) || !pow2(ny) || nx < 8 || ny < 8 || nx > 4096 || ny > 4096) return FLUPS_EUNSUPPORTED;
+    if (bc == FLUPS_BC_PERIODIC && (!pow2(nz) || nz < 8 || nz > 4096)) return FLUPS_EUNSUPPORTED;
+    if (bc == FLUPS_BC_WALLS && (nz < 2 || nz > 8192)) return FLUPS_EUNSUPPORTED;
+    std::vector<double> dz(dzf, dzf + nz);
+    double sum = 0.0;
+    for (int k = 0; k < nz; ++k) {
+        if (!(dz[k] > 0.0) || !std::isfinite(dz[k])) return FLUPS_EINVAL;
+        sum += dz[k];
+    }
+    if (bc == FLUPS_BC_PERIODIC)
+        for (int k = 1; k < nz; ++k)
+            if (dz[k] != dz[0]) return FLUPS_EINVAL;
+    if ((size_t)nx * ny * nz >= (size_t)1 << 31) return FLUPS_EUNSUPPORTED;
+    // an FP64 line of n complex values needs n * 2 * 16 bytes of shared memory at the
+    // narrowest tile, so FP64 transforms are limited to 2048 points
+    if (prec == FLUPS_FP64 && (ny > 2048 || (bc == FLUPS_BC_PERIODIC && nz > 2048))) return FLUPS_EUNSUPPORTED;
+
+    flups_plan P = new (std::nothrow) flups_plan_s();
+    if (!P) return FLUPS_ENOMEM;
+    P->nx = nx; P->ny = ny; P->nz = nz; P->bc = bc; P->prec = prec;
+    P->dx = dx; P->dy = dy;
+    P->stream = (cudaStream_t)stream;
+    cudaGetDevice(&P->dev);
+    P->M = nx / 2;
+    P->nxh = nx / 2 + 1;
+    const int csize = prec == FLUPS_FP64 ? 16 : 8;
+    const int align = 128 / csize;
+    P->ldS = (P->nxh + align - 1) / align * align;
+    P->npts = (size_t)nx * ny * nz;
+    P->nspec = (size_t)P->ldS * ny * nz;
+    P->sum_dzf = sum;
+    if (!make_len(P->M, &P->lx) || !make_len(ny, &P->ly) || (bc == FLUPS_BC_PERIODIC && !make_len(nz, &P->lz))) {
+        delete P;
+        return FLUPS_EUNSUPPORTED;
+    }
+    DevAlloc A;
+    P->spec = A.get(P->nspec * csize);
+    P->bx = (double*)A.get(P->npts * sizeof(double));
+    P->by = (double*)A.get(P->npts * sizeof(double));
+    P->bz = (double*)A.get(P->npts * sizeof(double));
+    P->sc = (DevScalars*)A.get(sizeof(DevScalars));
+    P->npart = 3 * std::max<size_t>(flups_part_blocks_needed(nx, ny, nz), 2048);
+    P->part = (double*)A.get(P->npart * sizeof(double));
+    P->tabs64 = (double*)A.get(6 * (size_t)nz * sizeof(double));
+    bool ok = A.ok;
+    if (ok) {
+        std::vector<double> t(6 * (size_t)nz);
+        const double sx = 1.0 / (dx * dx), sy = 1.0 / (dy * dy);
+        for (int k = 0; k < nz; ++k) {
+            double dzc_lo, dzc_hi;
+            if (bc == FLUPS_BC_PERIODIC) {
+                dzc_lo = dzc_hi = dz[0];
+            } else {
+                dzc_lo = k > 0 ? 0.5 * (dz[k - 1] + dz[k]) : 0.0;
+                dzc_hi = k < nz - 1 ? 0.5 * (dz[k] + dz[k + 1]) : 0.0;
+            }
+            const double a = dzc_lo > 0.0 ? 1.0 / (dz[k] * dzc_lo) : 0.0;
+            const double c = dzc_hi > 0.0 ? 1.0 / (dz[k] * dzc_hi) : 0.0;
+            t[k] = 1.0 / dz[k];
+            t[nz + k] = a;
+            t[2 * nz + k] = c;
+            t[3 * nz + k] = dzc_hi > 0.0 ? 1.0 / dzc_hi : 0.0;
+            t[4 * nz + k] = dz[k];
+            t[5 * nz + k] = 2.0 * sx + 2.0 * sy + a + c;
+        }
+        ok = cudaMemcpy(P->tabs64, t.data(), t.size() * sizeof(double), cudaMemcpyHostToDevice) == cudaSuccess;
+        ok = ok && cudaMemset(P->spec, 0, P->nspec * csize) == cudaSuccess;
+        ok = ok && cudaMemset(P->sc, 0, sizeof(DevScalars)) == cudaSuccess;
+    }
+    if (ok) ok = prec == FLUPS_FP64 ? build_tables<double>(P, dz, A) : build_tables<float>(P, dz, A);
+    if (ok) ok = cudaMallocHost(&P->sc_host, sizeof(DevScalars)) == cudaSuccess;
+    if (!ok) {
+        for (void* p : A.ptrs) cudaFree(p);
+        if (P->sc_host) cudaFreeHost(P->sc_host);
+        delete P;
+        cudaGetLastError();
+        return FLUPS_ENOMEM;
+    }
+    P->nallocs = (int)A.ptrs.size();
+    P->allocs = (void**)std::malloc(A.ptrs.size() * sizeof(void*));
+    if (!P->allocs) {
+        for (void* p : A.ptrs) cudaFree(p);
+        cudaFreeHost(P->sc_host);
+        delete P;
+        return FLUPS_ENOMEM;
+    }
+    for (size_t q = 0; q < A.ptrs.size(); ++q) P->allocs[q] = A.ptrs[q];
+    P->total_bytes = P->nspec * csize + 3 * P->npts * sizeof(double) +
+                     (bc == FLUPS_BC_WALLS ? (size_t)P->nxh * ny * nz * (csize / 2) : 0);
+    P->density_set = 0;
+    P->launches = 0;
+    P->hbuf = nullptr;
+    *out = P;
+    return FLUPS_OK;
+}
+
+flups_status flups_plan_destroy(flups_plan P) {
+    if (!P) return FLUPS_EINVAL;
+    DeviceGuard dg(P->dev);
+    cudaError_t e = cudaStreamSynchronize(P->stream);
+    for (int q = 0; q < P->nallocs; ++q) cudaFree(P->allocs[q]);
+    std::free(P->allocs);
+    if (P->hbuf) cudaFree(P->hbuf);
+    if (P->sc_host) cudaFreeHost(P->sc_host);
+    delete P;
+    return cuda_status(e);
+}
+
+flups_status flups_set_stream(flups_plan P, void* stream) {
+    if (!P) return FLUPS_EINVAL;
+    P->stream = (cudaStream_t)stream;
+    return FLUPS_OK;
+}
+
+size_t flups_workspace_bytes(flups_plan P) { return P ? P->total_bytes : 0; }
+
+unsigned long long flups_launch_count(flups_plan P) { return P ? P->launches : 0ull; }
+
+flups_status flups_set_density(flups_plan P, const double* rho, double rho0) {
+    if (!P || !rho || !aligned16(rho) || std::isnan(rho0)) return FLUPS_EINVAL;
+    DeviceGuard dg(P->dev);
+    const flups_status st = cuda_status(launch_set_density(P, rho, rho0));
+    if (st == FLUPS_OK) P->density_set = 1;
+    return st;
+}
+
+flups_status flups_get_rho0(flups_plan P, double* rho0_host) {
+    if (!P || !rho0_host) return FLUPS_EINVAL;
+    if (!P->density_set) return FLUPS_ESTATE;
+    DeviceGuard dg(P->dev);
+    const flups_status st = sync_scalars(P);
+    if (st != FLUPS_OK) return st;
+    *rho0_host = P->sc_host->rho0;
+    return P->sc_host->bad_rho ? FLUPS_ENONFINITE : FLUPS_OK;
+}
+
+flups_status flups_rhs(flups_plan P, const double* u, const double* v, const double* w, const double* p_n,
+                       const double* p_nm1, double c1, double c2, double dt, double* f) {
+    if (!P || !u || !v || !w || !p_n || !f) return FLUPS_EINVAL;
+    if (!aligned16(u) || !aligned16(v) || !aligned16(w) || !aligned16(p_n) || !aligned16(f) ||
+        (p_nm1 && !aligned16(p_nm1)))
+        return FLUPS_EINVAL;
+    if (!(dt > 0.0) || !std::isfinite(dt) || !std::isfinite(c1) || !std::isfinite(c2)) return FLUPS_EINVAL;
+    if (f == u || f == v || f == w || f == p_n || f == p_nm1) return FLUPS_EINVAL;
+    if (!P->density_set) return FLUPS_ESTATE;
+    DeviceGuard dg(P->dev);
+    return cuda_status(launch_rhs(P, u, v, w, p_n, p_nm1, c1, c2, dt, f));
+}
+
+flups_status flups_correct(flups_plan P, const double* p, const double* p_n, const double* p_nm1, double c1,
+                           double c2, double dt, double* u, double* v, double* w) {
+    if (!P || !p || !p_n || !u || !v || !w) return FLUPS_EINVAL;
+    if (!aligned16(p) || !aligned16(p_n) || !aligned16(u) || !aligned16(v) || !aligned16(w) ||
+        (p_nm1 && !aligned16(p_nm1)))
+        return FLUPS_EINVAL;
+    if (!(dt > 0.0) || !std::isfinite(dt) || !std::isfinite(c1) || !std::isfinite(c2)) return FLUPS_EINVAL;
+    if (!P->density_set) return FLUPS_ESTATE;
+    DeviceGuard dg(P->dev);
+    return cuda_status(launch_correct(P, p, p_n, p_nm1, c1, c2, dt, u, v, w));
+}
+
+flups_status flups_solve(flups_plan P, const double* f, double* p, double rtol, int max_iter, flups_info* info) {
+    if (!P || !f || !p || f == p || !aligned16(f) || !aligned16(p)) return FLUPS_EINVAL;
+    if (std::isnan(rtol)) return FLUPS_EINVAL;
+    DeviceGuard dg(P->dev);
+    if (info) {
+        info->iters = 0;
+        info->rel_res = -1.0;
+        for (int q = 0; q < FLUPS_HIST; ++q) info->rel_res_hist[q] = -1.0;
+    }
+    if (P->prec == FLUPS_FP64) {
+        flups_status st = cuda_status(launch_solve64(P, f, p));
+        if (st != FLUPS_OK || !info) return st;
+        info->iters = 1;
+        if (rtol > 0.0) {
+            st = cuda_status(launch_residual64_norm(P, f, p));
+            if (st == FLUPS_OK) st = sync_scalars(P);
+            if (st != FLUPS_OK) return st;
+            const double rr = P->sc_host->f2 > 0.0 ? std::sqrt(P->sc_host->r2 / P->sc_host->f2) : 0.0;
+            info->rel_res = rr;
+            info->rel_res_hist[0] = rr;
+            if (!std::isfinite(rr)) return FLUPS_ENONFINITE;
+            if (rr > rtol) return FLUPS_ENOCONV;
+        }
+        return FLUPS_OK;
+    }
+    if (max_iter < 1 || max_iter > 64 || !(rtol >= 0.0)) return FLUPS_EINVAL;
+    // First FP32 solve on f itself (the initial iterate is p = 0, so the defect is f).
+    flups_status st = cuda_status(launch_xfwd32_from_f(P, f));
+    if (st == FLUPS_OK) st = cuda_status(launch_finalize_f(P));
+    if (st == FLUPS_OK) st = cuda_status(launch_yz_solve32(P));
+    if (st == FLUPS_OK) st = cuda_status(launch_xinv32(P, p, 0));
+    if (st != FLUPS_OK) return st;
+    double rr = -1.0;
+    int it = 1;
+    for (;; ++it) {
+        // FP64 defect r = f - <f> - L p, fused with the forward x transform of r.
+        st = cuda_status(launch_xfwd32_residual(P, f, p));
+        if (st == FLUPS_OK) st = cuda_status(launch_finalize_r(P));
+        if (st == FLUPS_OK) st = sync_scalars(P);
+        if (st != FLUPS_OK) return st;
+        const double f2 = P->sc_host->f2;
+        rr = f2 > 0.0 ? std::sqrt(P->sc_host->r2 / f2) : (P->sc_host->r2 > 0.0 ? INFINITY : 0.0);
+        if (info) {
+            info->iters = it;
+            info->rel_res = rr;
+            if (it - 1 < FLUPS_HIST) info->rel_res_hist[it - 1] = rr;
+        }
+        if (!std::isfinite(rr)) return FLUPS_ENONFINITE;
+        if (rr <= rtol) return FLUPS_OK;
+        if (it >= max_iter) return FLUPS_ENOCONV;
+        // delta = L^-1 r in FP32, p += delta in FP64.
+        st = cuda_status(launch_yz_solve32(P));
+        if (st == FLUPS_OK) st = cuda_status(launch_xinv32(P, p, it == 1 ? 1 : 2));
+        if (st != FLUPS_OK) return st;
+    }
+}
+
+flups_status flups_project_host(flups_plan P, double* u, double* v, double* w, const double* rho,
+                                const double* p_n, const double* p_nm1, double c1, double c2, double dt,
+                                double rtol, int max_iter, double* p_out, flups_info* info) {
+    if (!P || !u || !v || !w || !rho || !p_n || !p_out) return FLUPS_EINVAL;
+    DeviceGuard dg(P->dev);
+    const size_t n = P->npts, b = n * sizeof(double);
+    if (!P->hbuf) {
+        if (cudaMalloc(&P->hbuf, 8 * b) != cudaSuccess) { cudaGetLastError(); P->hbuf = nullptr; return FLUPS_ENOMEM; }
+    }
+    double* du = P->hbuf;
+    double* dv = du + n;
+    double* dw = dv + n;
+    double* dr = dw + n;
+    double* dpn = dr + n;
+    double* dpm = dpn + n;
+    double* df = dpm + n;
+    double* dp = df + n;
+    cudaStream_t s = P->stream;
+    cudaError_t e = cudaMemcpyAsync(du, u, b, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dv, v, b, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dw, w, b, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dr, rho, b, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dpn, p_n, b, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && p_nm1) e = cudaMemcpyAsync(dpm, p_nm1, b, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return cuda_status(e);
+    flups_status st = flups_set_density(P, dr, 0.0);
+    if (st == FLUPS_OK) st = flups_rhs(P, du, dv, dw, dpn, p_nm1 ? dpm : nullptr, c1, c2, dt, df);
+    if (st == FLUPS_OK) st = flups_solve(P, df, dp, rtol, max_iter, info);
+    if (st == FLUPS_OK) st = flups_correct(P, dp, dpn, p_nm1 ? dpm : nullptr, c1, c2, dt, du, dv, dw);
+    if (st != FLUPS_OK) return st;
+    e = cudaMemcpyAsync(u, du, b, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(v, dv, b, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(w, dw, b, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(p_out, dp, b, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    return cuda_status(e);
+}
+
+}  // extern "C"

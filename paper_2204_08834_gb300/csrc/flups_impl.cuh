@@ -1,0 +1,108 @@
+// flups_impl.cuh - internal declarations shared by the CUDA translation units of libflups.
+//
+// Data layout in HBM (per plan):
+//   fields          float64 [nz][ny][nx], caller-owned
+//   spectrum S      complex (float2 in FP32-refine mode, double2 in FP64 mode)
+//                   [nz][ny][ldS], ldS = nx/2+1 rounded up so every row starts on a
+//                   128-byte boundary; entries nx/2+1 .. ldS-1 are never read
+//   face coeffs     float64 bx, by, bz [nz][ny][nx]: (1 - rho0/rho_f)/h for the face above
+//                   each cell in x, y, z (h = dx, dy, dzc_k); bz = 0 on the top wall face
+//   z scratch       T [nz][ny][nx/2+1]: forward-sweep multipliers of the z Thomas solve
+//   tables          FP64/FP32 twiddles, eigenvalues, z coefficients
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stddef.h>
+
+#include "../../include/flups.h"
+
+#define FLUPS_MAX_STAGES 14
+
+template <typename T> struct cplx;
+template <> struct cplx<float> { typedef float2 t; };
+template <> struct cplx<double> { typedef double2 t; };
+
+// One 1-D transform length and its radix sequence (each radix 2, 4 or 8).
+struct FftLen {
+    int n;
+    int nst;
+    int rad[FLUPS_MAX_STAGES];
+};
+
+// Device-side scalars written by the reduction kernels.
+struct DevScalars {
+    double rho0;        // minimum density
+    double inv_rho0;    // 1/rho0
+    double mean_f;      // volume-weighted mean of f
+    double f2;          // ||f - <f>||^2
+    double r2;          // ||r||^2 of the last residual pass
+    double mean_p;      // volume-weighted mean of the first FP32 iterate p_0
+    int    bad_rho;     // nonzero: non-finite, non-positive or out-of-range density seen
+    int    pad;
+};
+
+// Geometry and tables handed to kernels by value.
+struct Geo {
+    int nx, ny, nz, M, nxh, ldS, walls, uniform_z;
+    double dx, dy;
+    double sx, sy;               // 1/dx^2, 1/dy^2
+    const double* idzf;          // [nz] 1/dzf_k
+    const double* az;            // [nz] Laplacian z sub-diagonal   1/(dzf_k dzc_{k-1}) (0 at k=0 with walls)
+    const double* cz;            // [nz] Laplacian z super-diagonal 1/(dzf_k dzc_k) (0 at k=nz-1 with walls)
+    const double* idzc;          // [nz] 1/dzc_k (0 on the top wall face)
+    const double* dzf;           // [nz]
+};
+
+struct flups_plan_s {
+    int nx, ny, nz, bc, prec, dev;
+    double dx, dy;
+    cudaStream_t stream;
+    int M, nxh, ldS;
+    size_t npts, nspec;
+    FftLen lx, ly, lz;           // lengths M (complex along x), ny, nz
+    // workspace
+    void* spec;                  // spectrum, float2 or double2
+    void* zscr;                  // z Thomas multipliers (walls)
+    double* bx; double* by; double* bz;
+    DevScalars* sc;              // device scalars
+    DevScalars* sc_host;         // pinned host mirror
+    double* part;                // reduction partials
+    size_t npart;
+    // tables (device)
+    void* twx; void* twxr; void* twy; void* twz;   // W_M, W_nx (k<=M), W_ny, W_nz in compute type
+    double* tabs64;              // [6][nz]: idzf, az, cz, idzc, dzf, dd = 2sx + 2sy + az + cz
+    void* lamx; void* lamy; void* lamz;             // eigenvalues / norm, compute type
+    void* tri;                   // walls: a_k/norm, b_k/norm, c_k/norm, compute type (3*nz)
+    double sum_dzf;
+    int density_set;
+    // host-buffer (end-to-end) path, allocated on first use
+    double* hbuf;                // 8 fields: u v w rho pn pnm1 f p
+    size_t total_bytes;
+    void** allocs;               // every workspace allocation, freed by destroy
+    int nallocs;
+    unsigned long long launches; // kernels launched on this plan so far
+};
+
+// Every launcher adds the number of kernels it launched to P->launches.
+#define FLUPS_COUNT(P, n) ((P)->launches += (unsigned long long)(n))
+
+// Launchers (return cudaGetLastError()).
+cudaError_t launch_set_density(flups_plan P, const double* rho, double rho0);
+cudaError_t launch_rhs(flups_plan P, const double* u, const double* v, const double* w,
+                       const double* pn, const double* pnm1, double c1, double c2, double dt, double* f);
+cudaError_t launch_correct(flups_plan P, const double* p, const double* pn, const double* pnm1,
+                           double c1, double c2, double dt, double* u, double* v, double* w);
+// FP64 direct solve
+cudaError_t launch_solve64(flups_plan P, const double* f, double* p);
+// FP32 pipeline pieces
+cudaError_t launch_xfwd32_from_f(flups_plan P, const double* f);            // S = FFTx(f), partial sums of f
+cudaError_t launch_finalize_f(flups_plan P);                                 // mean_f, ||f - mean||^2
+cudaError_t launch_xfwd32_residual(flups_plan P, const double* f, const double* p);  // S = FFTx(r), ||r||^2 partials
+cudaError_t launch_finalize_r(flups_plan P);
+cudaError_t launch_yz_solve32(flups_plan P);                                 // y fwd, z solve, y inv on S
+cudaError_t launch_xinv32(flups_plan P, double* p, int mode);  // 0: p = FFTx^-1(S) (+ mean); 1: p += . - mean; 2: p += .
+// FP64 residual (report only)
+cudaError_t launch_residual64_norm(flups_plan P, const double* f, const double* p);
+
+Geo plan_geo(flups_plan P);

@@ -1,0 +1,187 @@
+"""ctypes binding of libflups (include/flups.h): argument marshalling only.
+
+Every step of the projection runs in the library's CUDA kernels; this module only turns
+torch CUDA tensors (or raw integer device addresses) into pointers, passes the current
+CUDA stream, and raises on a non-OK status.  There is no CPU fallback: if libflups.so is
+missing or cannot be loaded, every call raises.
+"""
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libflups.so")
+
+OK, EINVAL, EUNSUPPORTED, ENOMEM, ECUDA, ENONFINITE, ENOCONV, ESTATE = range(8)
+BC = {"periodic": 0, "walls": 1}
+PREC = {"fp64": 0, "fp32_refine": 1}
+HIST = 16
+
+# every entry point declared in include/flups.h
+SYMBOLS = [
+    "flups_plan_create", "flups_plan_destroy", "flups_set_stream", "flups_workspace_bytes", "flups_launch_count",
+    "flups_set_density", "flups_get_rho0", "flups_rhs", "flups_solve", "flups_correct",
+    "flups_project_host", "flups_status_string",
+]
+
+
+class FlupsError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        super().__init__(f"{where}: {status_string(status)}")
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("rel_res", ctypes.c_double), ("rel_res_hist", ctypes.c_double * HIST)]
+
+    def history(self):
+        return [h for h in self.rel_res_hist[: max(self.iters, 0)]]
+
+
+_lib = None
+
+
+def lib():
+    """Load libflups.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_2204_08834_gb300.build.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        P, D, I, V = ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.c_void_p
+        L.flups_plan_create.argtypes = [ctypes.POINTER(P), I, I, I, D, D, ctypes.POINTER(D), I, I, V]
+        L.flups_plan_destroy.argtypes = [P]
+        L.flups_set_stream.argtypes = [P, V]
+        L.flups_workspace_bytes.argtypes = [P]
+        L.flups_workspace_bytes.restype = ctypes.c_size_t
+        L.flups_launch_count.argtypes = [P]
+        L.flups_launch_count.restype = ctypes.c_ulonglong
+        L.flups_set_density.argtypes = [P, V, D]
+        L.flups_get_rho0.argtypes = [P, ctypes.POINTER(D)]
+        L.flups_rhs.argtypes = [P, V, V, V, V, V, D, D, D, V]
+        L.flups_solve.argtypes = [P, V, V, D, I, ctypes.POINTER(Info)]
+        L.flups_correct.argtypes = [P, V, V, V, D, D, D, V, V, V]
+        L.flups_project_host.argtypes = [P, V, V, V, V, V, V, D, D, D, D, I, V, ctypes.POINTER(Info)]
+        L.flups_status_string.argtypes = [I]
+        L.flups_status_string.restype = ctypes.c_char_p
+        for name in SYMBOLS:
+            if name not in ("flups_status_string", "flups_workspace_bytes", "flups_launch_count"):
+                getattr(L, name).restype = I
+        _lib = L
+    return _lib
+
+
+def status_string(s):
+    return lib().flups_status_string(int(s)).decode()
+
+
+def _check(status, where):
+    if status != OK:
+        raise FlupsError(status, where)
+
+
+def ptr(x):
+    """Device address of a contiguous float64 CUDA tensor, or an int address, or None."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        if not x.is_cuda or x.dtype.__repr__() != "torch.float64" or not x.is_contiguous():
+            raise ValueError("expected a contiguous float64 CUDA tensor")
+        return x.data_ptr()
+    raise TypeError(f"cannot pass {type(x)} as a device pointer")
+
+
+def hptr(a):
+    """Host address of a C-contiguous float64 numpy array."""
+    if not (isinstance(a, np.ndarray) and a.dtype == np.float64 and a.flags.c_contiguous):
+        raise ValueError("expected a C-contiguous float64 numpy array")
+    return a.ctypes.data
+
+
+def current_stream():
+    import torch
+    return torch.cuda.current_stream().cuda_stream
+
+
+class Plan:
+    """One projection plan (flups_plan_create).  Fields are [nz][ny][nx] float64."""
+
+    def __init__(self, nx, ny, nz, dx, dy, dzf, bc="periodic", prec="fp32_refine", stream=None):
+        self.shape = (nz, ny, nx)
+        self.bc, self.prec = bc, prec
+        dz = np.ascontiguousarray(np.broadcast_to(np.asarray(dzf, dtype=np.float64), (nz,)))
+        self._dz = dz
+        h = ctypes.c_void_p()
+        st = lib().flups_plan_create(ctypes.byref(h), int(nx), int(ny), int(nz), float(dx), float(dy),
+                                     dz.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), BC[bc], PREC[prec],
+                                     stream)
+        _check(st, "flups_plan_create")
+        self._h = h
+
+    @classmethod
+    def for_case(cls, case, prec="fp32_refine", stream=None):
+        nz, ny, nx = case.shape
+        if stream is None:
+            stream = current_stream()
+        return cls(nx, ny, nz, case.dx, case.dy, case.dzf, case.bc, prec, stream)
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            lib().flups_plan_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    __del__ = close
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    @property
+    def launches(self):
+        return lib().flups_launch_count(self._h)
+
+    @property
+    def workspace_bytes(self):
+        return lib().flups_workspace_bytes(self._h)
+
+    def set_stream(self, stream):
+        _check(lib().flups_set_stream(self._h, stream), "flups_set_stream")
+
+    def set_density(self, rho, rho0=0.0):
+        _check(lib().flups_set_density(self._h, ptr(rho), float(rho0)), "flups_set_density")
+
+    def rho0(self):
+        r = ctypes.c_double()
+        _check(lib().flups_get_rho0(self._h, ctypes.byref(r)), "flups_get_rho0")
+        return r.value
+
+    def rhs(self, u, v, w, pn, pnm1, c1, c2, dt, f):
+        _check(lib().flups_rhs(self._h, ptr(u), ptr(v), ptr(w), ptr(pn), ptr(pnm1), float(c1), float(c2),
+                               float(dt), ptr(f)), "flups_rhs")
+
+    def solve(self, f, p, rtol=1e-10, max_iter=16, info=True, check=True):
+        inf = Info() if info else None
+        st = lib().flups_solve(self._h, ptr(f), ptr(p), float(rtol), int(max_iter),
+                               ctypes.byref(inf) if inf is not None else None)
+        if check:
+            _check(st, "flups_solve")
+        return inf if check else (st, inf)
+
+    def correct(self, p, pn, pnm1, c1, c2, dt, u, v, w):
+        _check(lib().flups_correct(self._h, ptr(p), ptr(pn), ptr(pnm1), float(c1), float(c2), float(dt),
+                                   ptr(u), ptr(v), ptr(w)), "flups_correct")
+
+    def project_host(self, u, v, w, rho, pn, pnm1, c1, c2, dt, p_out, rtol=1e-10, max_iter=16):
+        """Whole projection on HOST numpy arrays (u, v, w updated in place; p_out written)."""
+        inf = Info()
+        st = lib().flups_project_host(self._h, hptr(u), hptr(v), hptr(w), hptr(rho), hptr(pn),
+                                      hptr(pnm1) if pnm1 is not None else None, float(c1), float(c2),
+                                      float(dt), float(rtol), int(max_iter), hptr(p_out), ctypes.byref(inf))
+        _check(st, "flups_project_host")
+        return inf

@@ -22,7 +22,7 @@ numpy PCG64 generator keyed by a fixed seed per field.
 
 import numpy as np
 
-__all__ = ["Case", "stretched_dzf", "sphere", "emulsion", "two_layer", "ensemble_member"]
+__all__ = ["Case", "stretched_dzf", "sphere", "emulsion", "two_layer", "ensemble_member", "random_fields"]
 
 
 class Case(dict):
@@ -201,3 +201,32 @@ def ensemble_member(m, sizes=(32, 48, 64, 96, 128)):
         c["w"][-1] = 0.0
     c["name"] = f"member{m}_n{n}_{c['bc']}"
     return c
+
+
+def random_fields(nx, ny, nz, bc="periodic", stretched=False, lx=1.0, ly=1.3, lz=0.7, ratio=10.0,
+                  seed=90, dt=1e-3):
+    """Anisotropic grids for edge cases: a blob density (ratio `ratio`, tanh profile of a
+    random ellipsoid), u** ~ U[-1, 1], p^n, p^{n-1} ~ U[-1, 1]; walls optional, z stretched
+    with beta = 1.5 if asked."""
+    r = _rng(seed)
+    dx, dy = lx / nx, ly / ny
+    dzf = stretched_dzf(nz, lz, 1.5) if stretched else np.full(nz, lz / nz)
+    zc = np.concatenate(([0.0], np.cumsum(dzf)[:-1])) + 0.5 * dzf
+    x = (np.arange(nx) + 0.5) * dx
+    y = (np.arange(ny) + 0.5) * dy
+    c = r.random(3) * np.array([lx, ly, lz])
+    ax = 0.2 + 0.1 * r.random(3)
+    d = np.sqrt(((zc[:, None, None] - c[2]) / (ax[2] * lz)) ** 2 + ((y[None, :, None] - c[1]) / (ax[1] * ly)) ** 2
+                + ((x[None, None, :] - c[0]) / (ax[0] * lx)) ** 2)
+    h = min(dx, dy, float(dzf.min()))
+    phi = _phi((d - 1.0) * min(ax[0] * lx, ax[1] * ly, ax[2] * lz), 0.75 * h)
+    rho = ratio * phi + 1.0 * (1.0 - phi)
+    u = r.uniform(-1.0, 1.0, (nz, ny, nx))
+    v = r.uniform(-1.0, 1.0, (nz, ny, nx))
+    w = r.uniform(-1.0, 1.0, (nz, ny, nx))
+    if bc == "walls":
+        w[-1] = 0.0
+    pn = r.uniform(-1.0, 1.0, (nz, ny, nx))
+    pnm1 = r.uniform(-1.0, 1.0, (nz, ny, nx))
+    return Case(u=u, v=v, w=w, rho=np.ascontiguousarray(rho), pn=pn, pnm1=pnm1, dt=dt, dx=dx, dy=dy,
+                dzf=dzf, lz=lz, bc=bc, name=f"random{nx}x{ny}x{nz}_{bc}{'_str' if stretched else ''}")

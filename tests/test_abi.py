@@ -1,0 +1,88 @@
+"""The C ABI library (CPU-only checks): it builds, loads, exports every entry point that
+include/flups.h declares, and rejects bad arguments before touching the GPU."""
+
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2204_08834_gb300 import build, flups
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return flups.lib()
+
+
+def declared_symbols():
+    text = open(os.path.join(ROOT, "include", "flups.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(flups_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_header_and_binding_agree():
+    assert declared_symbols() == sorted(flups.SYMBOLS)
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in declared_symbols():
+        assert hasattr(lib, name), name
+
+
+def test_status_strings(lib):
+    for s in range(8):
+        assert flups.status_string(s).startswith("FLUPS_")
+    assert "unknown" in flups.status_string(99)
+
+
+def _create(lib, nx, ny, nz, dzf, bc=0, prec=1, dx=0.1, dy=0.1):
+    h = ctypes.c_void_p()
+    dz = np.ascontiguousarray(np.broadcast_to(np.asarray(dzf, float), (max(nz, 1),)))
+    st = lib.flups_plan_create(ctypes.byref(h), nx, ny, nz, dx, dy,
+                               dz.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), bc, prec, None)
+    return st, h
+
+
+@pytest.mark.parametrize("nx,ny,nz,bc,want", [
+    (12, 16, 16, 0, flups.EUNSUPPORTED),   # nx not a power of two
+    (16, 4, 16, 0, flups.EUNSUPPORTED),    # ny below 8
+    (16, 16, 24, 0, flups.EUNSUPPORTED),   # periodic nz must be a power of two
+    (16, 16, 1, 1, flups.EUNSUPPORTED),    # walls need nz >= 2
+    (8192, 16, 16, 0, flups.EUNSUPPORTED),
+    (16, 16, 16, 7, flups.EINVAL),         # unknown bc
+])
+def test_plan_rejects_bad_sizes(lib, nx, ny, nz, bc, want):
+    st, h = _create(lib, nx, ny, nz, 1.0 / max(nz, 1), bc=bc)
+    assert st == want and not h.value
+
+
+def test_plan_rejects_bad_spacing(lib):
+    assert _create(lib, 16, 16, 16, 0.1, dx=0.0)[0] == flups.EINVAL
+    assert _create(lib, 16, 16, 16, 0.1, dy=float("nan"))[0] == flups.EINVAL
+    assert _create(lib, 16, 16, 16, [0.1] * 15 + [-0.1], bc=1)[0] == flups.EINVAL
+    assert _create(lib, 16, 16, 16, np.linspace(0.05, 0.1, 16), bc=0)[0] == flups.EINVAL  # periodic, stretched
+    assert _create(lib, 16, 16, 16, 0.1, prec=5)[0] == flups.EINVAL
+    h = ctypes.c_void_p()
+    assert lib.flups_plan_create(ctypes.byref(h), 16, 16, 16, 0.1, 0.1, None, 0, 0, None) == flups.EINVAL
+    assert lib.flups_plan_create(None, 16, 16, 16, 0.1, 0.1, None, 0, 0, None) == flups.EINVAL
+
+
+def test_null_plan_calls_are_rejected(lib):
+    assert lib.flups_plan_destroy(None) == flups.EINVAL
+    assert lib.flups_set_density(None, None, 0.0) == flups.EINVAL
+    assert lib.flups_solve(None, None, None, 1e-10, 4, None) == flups.EINVAL
+    assert lib.flups_rhs(None, None, None, None, None, None, 2.0, 1.0, 1e-3, None) == flups.EINVAL
+    assert lib.flups_correct(None, None, None, None, 2.0, 1.0, 1e-3, None, None, None) == flups.EINVAL
+    assert lib.flups_workspace_bytes(None) == 0
+
+
+def test_no_cpu_fallback_when_library_missing(monkeypatch, tmp_path):
+    monkeypatch.setattr(flups, "_lib", None)
+    monkeypatch.setattr(flups, "LIB_PATH", str(tmp_path / "missing.so"))
+    with pytest.raises(RuntimeError):
+        flups.lib()
