@@ -153,6 +153,29 @@ flups_status flups_project_host(flups_plan plan, double* u, double* v, double* w
                                 double c1, double c2, double dt, double rtol, int max_iter,
                                 double* p_out, flups_info* info);
 
+/*
+ * flups_solve_fp64_noalloc - the FP64 direct solve of flups_solve (FLUPS_FP64 mode) for
+ * callers that cannot allocate device memory, for example a solver plug-in inside a host
+ * application that owns and pre-reserves the whole device memory budget, or code running
+ * under a memory manager that forbids allocations once a run has started.  The paper has
+ * no counterpart to this entry point.
+ *   nx, ny, nz, dx, dy, dzf (HOST), bc : as in flups_plan_create; ny and a periodic nz are
+ *              at most 2048.
+ *   f, p     : DEVICE input and output, as in flups_solve (p may not alias f).
+ *   stream   : cudaStream_t (NULL = legacy default stream).
+ * No plan is needed and nothing is allocated: the workspace (spectrum, z multipliers,
+ * tables) lives in one static device array of FLUPS_NOALLOC_MAX_BYTES that every GPU
+ * loading the library holds until exit.  A grid whose workspace does not fit (about
+ * 16 MiB: e.g. 64^3 or 128x128x32 periodic fit, 128^3 does not) returns
+ * FLUPS_EUNSUPPORTED before any GPU work.  The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  Every call reuses the same array, so calls that overlap on
+ * the GPU race: serialise them.  Stream-ordered; does not synchronise.
+ */
+#define FLUPS_NOALLOC_MAX_BYTES (16u << 20)
+flups_status flups_solve_fp64_noalloc(int nx, int ny, int nz, double dx, double dy, const double* dzf,
+                                      int bc, const double* f, double* p, void* stream);
+
 /* flups_status_string - static, human-readable name of a status code. */
 const char* flups_status_string(int status);
 

@@ -23,7 +23,7 @@ HIST = 16
 SYMBOLS = [
     "flups_plan_create", "flups_plan_destroy", "flups_set_stream", "flups_workspace_bytes", "flups_launch_count",
     "flups_set_density", "flups_get_rho0", "flups_rhs", "flups_solve", "flups_correct",
-    "flups_project_host", "flups_status_string",
+    "flups_project_host", "flups_status_string", "flups_solve_fp64_noalloc",
 ]
 
 
@@ -64,6 +64,7 @@ def lib():
         L.flups_solve.argtypes = [P, V, V, D, I, ctypes.POINTER(Info)]
         L.flups_correct.argtypes = [P, V, V, V, D, D, D, V, V, V]
         L.flups_project_host.argtypes = [P, V, V, V, V, V, V, D, D, D, D, I, V, ctypes.POINTER(Info)]
+        L.flups_solve_fp64_noalloc.argtypes = [I, I, I, D, D, ctypes.POINTER(D), I, V, V, V]
         L.flups_status_string.argtypes = [I]
         L.flups_status_string.restype = ctypes.c_char_p
         for name in SYMBOLS:
@@ -185,3 +186,20 @@ class Plan:
                                       float(dt), float(rtol), int(max_iter), hptr(p_out), ctypes.byref(inf))
         _check(st, "flups_project_host")
         return inf
+
+
+def solve_fp64_noalloc(nx, ny, nz, dx, dy, dzf, bc, f, p, stream=None, check=True):
+    """FP64 direct solve without any device allocation (flups_solve_fp64_noalloc).
+
+    For callers that may not call cudaMalloc (the library then uses one fixed 16 MiB
+    device array per GPU as workspace); calls that overlap on the GPU race on that array.
+    """
+    dz = np.ascontiguousarray(np.broadcast_to(np.asarray(dzf, dtype=np.float64), (nz,)))
+    if stream is None:
+        stream = current_stream()
+    st = lib().flups_solve_fp64_noalloc(int(nx), int(ny), int(nz), float(dx), float(dy),
+                                        dz.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), BC[bc], ptr(f),
+                                        ptr(p), stream)
+    if check:
+        _check(st, "flups_solve_fp64_noalloc")
+    return st
