@@ -43,12 +43,21 @@ WORKLOADS = {
     "sphere32": dict(kind="sphere", n=32, desc="sphere 32^3 periodic, density 10 in 1"),
 }
 
-# Algorithmic FP64 flops per cell of k_rhs (each face flux once, FMA = 2 flops):
-# p~ = fma(-s2, p^{n-1}, s1 p^n) 3; three face fluxes q = fma(b, dp~, u) 3 x 3 = 9;
-# divergence: three differences 3, one scale 1, two FMAs 4 -> 8.  Total 20.
-RHS_FLOPS_PER_CELL = 20.0
-# Compulsory HBM bytes per cell of k_rhs: read u, v, w, bx, by, bz, p^n, p^{n-1}; write f.
-RHS_BYTES_PER_CELL = 9 * 8.0
+# Per-kernel algorithmic work per grid point (N = nx ny nz; the half spectrum holds N/2
+# complex values, 4 B/point in FP32).  "bound" names the roofline each kernel is held to:
+#   hbm: compulsory bytes (each array touched once) / time vs the measured copy bandwidth;
+#   alu: FP64 flops (FMA = 2) / time vs the measured FP64 rate.
+KERNEL_WORK = {
+    # r = f - <f> - L p: 2 adds + 5 FMAs + 1 subtract = 13 FP64 flops; reads f, p, writes S.
+    "k_xfwd_residual32": {"bound": "alu", "flops": 13.0, "bytes": 8 + 8 + 4},
+    "k_xfwd_f32": {"bound": "hbm", "bytes": 8 + 4},
+    "k_ycol32": {"bound": "hbm", "bytes": 4 + 4},
+    "k_zper32": {"bound": "hbm", "bytes": 4 + 4},
+    "k_ztri32": {"bound": "hbm", "bytes": 4 + 4},
+    "k_xinv32": {"bound": "hbm", "bytes": 4 + 12},   # mean of p = (first) and p += (later)
+    "k_face_coeffs": {"bound": "hbm", "bytes": 8 + 24},
+    "k_rho_minmax": {"bound": "hbm", "bytes": 8},
+}
 
 
 def make_case(name):
@@ -163,7 +172,11 @@ def run_ours(args, rank, world, dev):
             ev[1].record()
             plan.rhs(work["u"], work["v"], work["w"], d0["pn"], d0["pnm1"], 2.0, 1.0, c.dt, f)
             ev[2].record()
-            info = plan.solve(f, p, rtol=rtol, max_iter=12)
+            # the direct FP64 solve needs no residual evaluation; it is checked after the loop
+            if plan.prec == "fp32_refine":
+                info = plan.solve(f, p, rtol=rtol, max_iter=12)
+            else:
+                info = plan.solve(f, p, rtol=0.0, info=False)   # returns None
             ev[3].record()
             plan.correct(p, d0["pn"], d0["pnm1"], 2.0, 1.0, c.dt, work["u"], work["v"], work["w"])
             ev[4].record()
@@ -172,16 +185,28 @@ def run_ours(args, rank, world, dev):
                 for q, k in enumerate(("set_density", "rhs", "solve", "correct")):
                     tot[k] += ev[q].elapsed_time(ev[q + 1])
                 tot["step"] += ev[0].elapsed_time(ev[4])
-                iters.append(info.iters)
-                rel.append(info.rel_res)
+                if info is not None:
+                    iters.append(info.iters)
+                    rel.append(info.rel_res)
         launches = plan.launches - l0
+        if not iters:   # FP64: one residual evaluation outside the timed steps
+            info = plan.solve(f, p, rtol=rtol, max_iter=12)
+            iters.append(info.iters)
+            rel.append(info.rel_res)
         return tot, iters, rel, launches
 
     res = {}
+    prof = {}
     with ClockSampler(dev) as clk:
         for prec, steps in (("fp32_refine", args.steps), ("fp64", max(2, args.steps // 2))):
             with flups.Plan(nx, ny, nz, c.dx, c.dy, c.dzf, c.bc, prec, stream) as plan:
                 res[prec] = timed_steps(plan, steps, args.warmup, args.rtol) + (steps,)
+                if prec == "fp32_refine":
+                    # two more steps with per-kernel CUDA events inside the library
+                    plan.set_profiling(True)
+                    timed_steps(plan, 2, 0, args.rtol)
+                    prof = {k: (ms / 2.0, n / 2.0) for k, (ms, n) in plan.profile().items()}
+                    plan.set_profiling(False)
     # max over ranks of the timed sum
     t32 = res["fp32_refine"][0]["step"]
     t64 = res["fp64"][0]["step"]
@@ -190,7 +215,7 @@ def run_ours(args, rank, world, dev):
         torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
         t32, t64 = float(tt[0]), float(tt[1])
 
-    out = {"c": c, "npts": npts, "res": res, "t32": t32, "t64": t64, "clocks": clk.summary()}
+    out = {"c": c, "npts": npts, "res": res, "t32": t32, "t64": t64, "clocks": clk.summary(), "prof": prof}
 
     # end to end: the same projection through flups_project_host on pinned host buffers
     if not args.no_e2e:
@@ -311,10 +336,20 @@ def main():
     ms64 = out["t64"] / k64
     value = world * npts / (ms32 * 1e-3) / 1e6
     pk, pk_kind = peaks()
-    # roofline of k_rhs (one kernel per flups_rhs call, timed by its own events)
-    rhs_ms = tot32["rhs"] / k32
-    flops = RHS_FLOPS_PER_CELL * npts
-    achieved = flops / (rhs_ms * 1e-3) / 1e12
+    prof = out["prof"]
+    tot_prof = sum(ms for ms, n in prof.values()) or 1.0
+    kernels = {k: {"ms_per_step": round(ms, 4), "launch_regions_per_step": n, "share": round(ms / tot_prof, 4)}
+               for k, (ms, n) in sorted(prof.items(), key=lambda kv: -kv[1][0])}
+    dom = max(prof, key=lambda k: prof[k][0])
+    work = KERNEL_WORK.get(dom, {"bound": "hbm", "bytes": None})
+    dom_ms_per_region = prof[dom][0] / max(prof[dom][1], 1e-9)
+    if work["bound"] == "alu":
+        achieved = work["flops"] * npts / (dom_ms_per_region * 1e-3) / 1e12
+        peak, unit, psrc = FP64_TFLOPS_MEASURED, "TFLOP/s", ("FP64 DFMA rate measured by "
+                                                              "microbench/peaks.cu on this pool")
+    else:
+        achieved = (work["bytes"] or 0) * npts / (dom_ms_per_region * 1e-3) / 1e9
+        peak, unit, psrc = pk["hbm_gbs"], "GB/s", f"MEASURED_PEAKS.json hbm_gbs ({pk_kind})"
     line = {
         "metric": METRIC,
         "value": round(value, 2),
@@ -348,19 +383,23 @@ def main():
             "solve_mpts": round(world * npts / (tot64["solve"] / k64 * 1e-3) / 1e6, 2),
             "breakdown_ms": {k: round(v / k64, 4) for k, v in tot64.items()},
             "steps": k64,
+            "rel_res": max(rel64),
         },
         "roofline": {
-            "kernel": "k_rhs",
-            "bound": "alu",
+            "kernel": dom,
+            "bound": work["bound"],
             "achieved": round(achieved, 4),
-            "peak": FP64_TFLOPS_MEASURED,
-            "unit": "TFLOP/s",
-            "frac": round(achieved / FP64_TFLOPS_MEASURED, 4),
+            "peak": peak,
+            "unit": unit,
+            "frac": round(achieved / peak, 4),
             "traffic": None,
-            "peak_source": "FP64 DFMA rate measured by microbench/peaks.cu on this pool (not in MEASURED_PEAKS.json)",
-            "hbm_frac": round(RHS_BYTES_PER_CELL * npts / (rhs_ms * 1e-3) / 1e9 / pk["hbm_gbs"], 4),
-            "hbm_peak_source": pk_kind,
+            "per_launch_ms": round(dom_ms_per_region, 4),
+            "peak_source": psrc,
+            "algorithmic": {k: v for k, v in work.items() if k != "bound"},
+            "hbm_frac": (round(work["bytes"] * npts / (dom_ms_per_region * 1e-3) / 1e9 / pk["hbm_gbs"], 4)
+                         if work.get("bytes") else None),
         },
+        "kernels": kernels,
         "gpu_launches": int(l32),
         "clocks": out["clocks"],
     }

@@ -90,6 +90,20 @@ size_t       flups_workspace_bytes(flups_plan plan);
 unsigned long long flups_launch_count(flups_plan plan);
 
 /*
+ * Per-kernel timing (tracing aid; no counterpart in the paper, which reports only a
+ * breakdown of the whole time step, Sec. 6.2).  flups_set_profiling(plan, 1) makes every
+ * later launch bracket its kernel(s) with CUDA events on the plan's stream (up to 1024
+ * regions between reads; later ones are not recorded); 0 stops it.  flups_profile_read
+ * synchronises the stream and writes, for every kernel id 0 <= k < FLUPS_NKERNELS, the
+ * total milliseconds ms[k] and the number of timed regions n[k] (HOST arrays) recorded
+ * since the previous read.  flups_kernel_name(k) names kernel id k (static string).
+ */
+#define FLUPS_NKERNELS 17
+flups_status flups_set_profiling(flups_plan plan, int on);
+flups_status flups_profile_read(flups_plan plan, double* ms, long long* n);
+const char*  flups_kernel_name(int id);
+
+/*
  * flups_set_density - register the density field for the next rhs/correct calls (Sec. 3.3).
  *   rho  : DEVICE [nz][ny][nx], read once here; not retained.
  *   rho0 : > 0 uses this value as rho0; <= 0 computes rho0 = min(rho) on the device

@@ -127,6 +127,38 @@ __device__ __forceinline__ void fft_tile(C* s, int pitch, int lgB, const FftLen&
     }
 }
 
+// FP64 -> FP32 with round-to-nearest-even, built from the IEEE-754 binary64/binary32
+// layouts with integer operations (on GB300 the F2F conversion instruction runs on the
+// narrow FP64 pipe).  Values outside the normal binary32 range use the hardware conversion.
+__device__ __forceinline__ float d2f_bits(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned int hi = (unsigned int)(b >> 32);
+    const int e = (int)((hi >> 20) & 0x7FFu);
+    if (e < 897 || e > 1150) return __double2float_rn(x);
+    unsigned int r = ((unsigned int)(e - 896) << 23) | ((unsigned int)(b >> 29) & 0x7FFFFFu);
+    const unsigned int rem = (unsigned int)b & 0x1FFFFFFFu;
+    r += (rem > 0x10000000u) | ((rem == 0x10000000u) & (r & 1u));
+    return __uint_as_float(r | (hi & 0x80000000u));
+}
+
+// FP32 -> FP64 (exact) from the bit layouts; zero, subnormal, inf and NaN use the hardware.
+__device__ __forceinline__ double f2d_bits(float x) {
+    const unsigned int b = __float_as_uint(x);
+    const unsigned int e = (b >> 23) & 0xFFu;
+    if (e == 0u || e == 255u) return (double)x;
+    const unsigned int hi = (b & 0x80000000u) | ((e + 896u) << 20) | ((b & 0x7FFFFFu) >> 3);
+    return __hiloint2double((int)hi, (int)((b & 7u) << 29));
+}
+
+template <typename T> __device__ __forceinline__ T from_double(double x) {
+    if constexpr (sizeof(T) == 4) return d2f_bits(x);
+    else return x;
+}
+template <typename T> __device__ __forceinline__ double to_double(T x) {
+    if constexpr (sizeof(T) == 4) return f2d_bits(x);
+    else return x;
+}
+
 template <typename T> __device__ __forceinline__ typename cplx<T>::t mk(T a, T b) {
     typename cplx<T>::t r; r.x = a; r.y = b; return r;
 }
@@ -192,7 +224,7 @@ __global__ void __launch_bounds__(1024) k_xfwd(const double* __restrict__ f, con
         if (row < nrows) {
             const double2 fv = __ldg(reinterpret_cast<const double2*>(f + (size_t)row * nx) + n);
             if (MODE == 0) {
-                z = mk<T>((T)fv.x, (T)fv.y);
+                z = mk<T>(from_double<T>(fv.x), from_double<T>(fv.y));
                 if (STATS) {
                     const int k = row / g.ny;
                     accw = fma(fv.x + fv.y, __ldg(g.dzf + k), accw);
@@ -225,7 +257,7 @@ __global__ void __launch_bounds__(1024) k_xfwd(const double* __restrict__ f, con
                 a1 = fma(azk, pb.y, a1);
                 a1 = fma(czk, pt.y, a1);
                 a1 = fma(-dk, pc.y, a1);
-                z = mk<T>((T)(fv.x - a0), (T)(fv.y - a1));
+                z = mk<T>(from_double<T>(fv.x - a0), from_double<T>(fv.y - a1));
                 acc2 = fmaf((float)z.x, (float)z.x, fmaf((float)z.y, (float)z.y, acc2));
             }
         }
@@ -306,11 +338,11 @@ __global__ void __launch_bounds__(1024) k_xinv(const typename cplx<T>::t* __rest
         double2 o;
         if (ACC) {
             o = *dst;
-            o.x += (double)z.x;
-            o.y += (double)z.y;
+            o.x += to_double<T>(z.x);
+            o.y += to_double<T>(z.y);
         } else {
-            o.x = (double)z.x;
-            o.y = (double)z.y;
+            o.x = to_double<T>(z.x);
+            o.y = to_double<T>(z.y);
             if (MEAN) accw = fma(o.x + o.y, __ldg(g.dzf + row / g.ny), accw);
         }
         *dst = o;
@@ -330,9 +362,18 @@ __global__ void __launch_bounds__(1024) k_ycol(typename cplx<T>::t* __restrict__
     const int ncol = min(B, g.nxh - kxa);
     C* base = S + (size_t)blockIdx.y * g.ny * g.ldS + kxa;
     const int tid = threadIdx.x, nthr = blockDim.x, N = g.ny;
-    for (int idx = tid; idx < B * N; idx += nthr) {
-        const int c = idx & (B - 1), j = idx >> lgB;
-        s[j * pitch + c] = c < ncol ? base[(size_t)j * g.ldS + c] : mk<T>((T)0, (T)0);
+    {   // every thread issues its E loads before touching shared memory (nthr * E == B * N)
+        C r[E];
+#pragma unroll
+        for (int t = 0; t < E; ++t) {
+            const int idx = tid + t * nthr, c = idx & (B - 1), j = idx >> lgB;
+            r[t] = c < ncol ? base[(size_t)j * g.ldS + c] : mk<T>((T)0, (T)0);
+        }
+#pragma unroll
+        for (int t = 0; t < E; ++t) {
+            const int idx = tid + t * nthr, c = idx & (B - 1), j = idx >> lgB;
+            s[j * pitch + c] = r[t];
+        }
     }
     __syncthreads();
     fft_tile<C, E, INV>(s, pitch, lgB, L, tw);
@@ -358,9 +399,18 @@ __global__ void __launch_bounds__(1024) k_zper(typename cplx<T>::t* __restrict__
     const size_t zs = (size_t)g.ny * g.ldS;
     C* base = S + (size_t)ky * g.ldS + kxa;
     const int tid = threadIdx.x, nthr = blockDim.x, N = g.nz;
-    for (int idx = tid; idx < B * N; idx += nthr) {
-        const int c = idx & (B - 1), k = idx >> lgB;
-        s[k * pitch + c] = c < ncol ? base[k * zs + c] : mk<T>((T)0, (T)0);
+    {   // every thread issues its E loads before touching shared memory (nthr * E == B * N)
+        C r[E];
+#pragma unroll
+        for (int t = 0; t < E; ++t) {
+            const int idx = tid + t * nthr, c = idx & (B - 1), k = idx >> lgB;
+            r[t] = c < ncol ? base[k * zs + c] : mk<T>((T)0, (T)0);
+        }
+#pragma unroll
+        for (int t = 0; t < E; ++t) {
+            const int idx = tid + t * nthr, c = idx & (B - 1), k = idx >> lgB;
+            s[k * pitch + c] = r[t];
+        }
     }
     __syncthreads();
     fft_tile<C, E, false>(s, pitch, lgB, L, tw);
@@ -516,11 +566,13 @@ void run_ycol(flups_plan P, typename cplx<T>::t* S, const Geo& g) {
     const int B = 1 << lgB;
     auto kern = k_ycol<T, Eof<T>::E, INV>;
     allow_smem(kern);
+    flups_prof_begin(P, sizeof(T) == 4 ? FK_YCOL32 : FK_YCOL64);
     const size_t sm = (size_t)N * (B + 1) * sizeof(C);
     kern<<<dim3(g.M / B, g.nz), B * N / E, sm, P->stream>>>(S, g, P->ly, (const C*)P->twy, lgB, 0);
     const int lgT = ilog2i(N >= E ? 1 : E / N);   // the Nyquist column kx = M
     const int BT = 1 << lgT;
     kern<<<dim3(1, g.nz), BT * N / E, (size_t)N * (BT + 1) * sizeof(C), P->stream>>>(S, g, P->ly, (const C*)P->twy, lgT, g.M);
+    flups_prof_end(P);
     FLUPS_COUNT(P, 2);
 }
 
@@ -534,17 +586,21 @@ void run_zsolve(flups_plan P, typename cplx<T>::t* S, const Geo& g) {
         const int B = 1 << lgB;
         auto kern = k_zper<T, Eof<T>::E>;
         allow_smem(kern);
+        flups_prof_begin(P, sizeof(T) == 4 ? FK_ZPER32 : FK_ZPER64);
         kern<<<dim3(g.M / B, g.ny), B * N / E, (size_t)N * (B + 1) * sizeof(C), P->stream>>>(
             S, g, P->lz, (const C*)P->twz, (const T*)P->lamx, (const T*)P->lamy, (const T*)P->lamz, lgB, 0);
         const int lgT = ilog2i(N >= E ? 1 : E / N);
         const int BT = 1 << lgT;
         kern<<<dim3(1, g.ny), BT * N / E, (size_t)N * (BT + 1) * sizeof(C), P->stream>>>(
             S, g, P->lz, (const C*)P->twz, (const T*)P->lamx, (const T*)P->lamy, (const T*)P->lamz, lgT, g.M);
+        flups_prof_end(P);
         FLUPS_COUNT(P, 2);
     } else {
         const int ncols = g.nxh * g.ny;
+        flups_prof_begin(P, sizeof(T) == 4 ? FK_ZTRI32 : FK_ZTRI64);
         k_ztri<T><<<(ncols + 127) / 128, 128, 0, P->stream>>>(S, (T*)P->zscr, g, (const T*)P->lamx,
                                                                 (const T*)P->lamy, (const T*)P->tri);
+        flups_prof_end(P);
         FLUPS_COUNT(P, 1);
     }
 }
@@ -557,10 +613,12 @@ void run_xfwd(flups_plan P, const double* f, const double* p, const Geo& g) {
     const int B = 1 << lgB;
     auto kern = k_xfwd<T, Eof<T>::E, MODE, STATS>;
     allow_smem(kern);
+    flups_prof_begin(P, sizeof(T) == 8 ? FK_XFWD64 : (MODE == 1 ? FK_XFWD_RES32 : FK_XFWD_F32));
     const int nblk = (nrows + B - 1) / B;
     kern<<<nblk, B * N / E, (size_t)N * (B + 1) * sizeof(C), P->stream>>>(
         f, p, (C*)P->spec, g, P->lx, (const C*)P->twx, (const C*)P->twxr, P->tabs64 + 5 * g.nz, lgB, nrows,
         P->sc, P->part);
+    flups_prof_end(P);
     FLUPS_COUNT(P, 1);
 }
 
@@ -572,9 +630,11 @@ void run_xinv(flups_plan P, double* p, const Geo& g) {
     const int B = 1 << lgB;
     auto kern = k_xinv<T, Eof<T>::E, ACC, MEAN, SUBM>;
     allow_smem(kern);
+    flups_prof_begin(P, sizeof(T) == 4 ? FK_XINV32 : FK_XINV64);
     const int nblk = (nrows + B - 1) / B;
     kern<<<nblk, B * N / E, (size_t)N * (B + 1) * sizeof(C), P->stream>>>(
         (const C*)P->spec, p, g, P->lx, (const C*)P->twx, (const C*)P->twxr, lgB, nrows, P->sc, P->part);
+    flups_prof_end(P);
     FLUPS_COUNT(P, 1);
 }
 
@@ -605,8 +665,10 @@ cudaError_t launch_xfwd32_from_f(flups_plan P, const double* f) {
 
 cudaError_t launch_finalize_f(flups_plan P) {
     const int nblk = xfwd_blocks(P, 8, 16);
+    flups_prof_begin(P, FK_FINALIZE);
     k_finalize<<<1, 1024, 0, P->stream>>>(P->part, nblk, P->sc, 0, 1.0 / ((double)P->nx * P->ny * P->sum_dzf),
                                           (double)P->npts);
+    flups_prof_end(P);
     FLUPS_COUNT(P, 1);
     return cudaGetLastError();
 }
@@ -619,7 +681,9 @@ cudaError_t launch_xfwd32_residual(flups_plan P, const double* f, const double* 
 
 cudaError_t launch_finalize_r(flups_plan P) {
     const int nblk = xfwd_blocks(P, 8, 16);
+    flups_prof_begin(P, FK_FINALIZE);
     k_finalize<<<1, 1024, 0, P->stream>>>(P->part, nblk, P->sc, 1, 0.0, 0.0);
+    flups_prof_end(P);
     FLUPS_COUNT(P, 1);
     return cudaGetLastError();
 }
@@ -637,7 +701,9 @@ cudaError_t launch_xinv32(flups_plan P, double* p, int mode) {
     if (mode == 0) {                       // p = delta, and the volume-weighted mean of p
         run_xinv<float, 0, true, false>(P, p, g);
         const int nblk = xfwd_blocks(P, 8, 16);
+        flups_prof_begin(P, FK_FINALIZE);
         k_finalize<<<1, 1024, 0, P->stream>>>(P->part, nblk, P->sc, 2, 1.0 / ((double)P->nx * P->ny * P->sum_dzf), 0.0);
+        flups_prof_end(P);
         FLUPS_COUNT(P, 1);
     } else if (mode == 1) {                // p += delta - <p_0>
         run_xinv<float, 1, false, true>(P, p, g);

@@ -128,6 +128,25 @@ flups_status sync_scalars(flups_plan P) {
 
 }  // namespace
 
+static const char* kKernelNames[FK_COUNT] = {
+    "k_rho_minmax", "k_face_coeffs", "k_rhs", "k_correct", "k_xfwd_f32", "k_xfwd_residual32", "k_ycol32",
+    "k_zper32", "k_ztri32", "k_xinv32", "k_finalize", "k_xfwd64", "k_ycol64", "k_zper64", "k_ztri64", "k_xinv64",
+    "k_res64"};
+
+void flups_prof_begin(flups_plan P, int kid) {
+    P->prof_open = 0;
+    if (!P->prof_on || P->prof_n >= P->prof_cap) return;
+    if (cudaEventRecord(P->prof_ev[2 * P->prof_n], P->stream) != cudaSuccess) return;
+    P->prof_kid[P->prof_n] = kid;
+    P->prof_open = 1;
+}
+
+void flups_prof_end(flups_plan P) {
+    if (!P->prof_open) return;
+    P->prof_open = 0;
+    if (cudaEventRecord(P->prof_ev[2 * P->prof_n + 1], P->stream) == cudaSuccess) P->prof_n++;
+}
+
 Geo plan_geo(flups_plan P) {
     Geo g;
     g.nx = P->nx; g.ny = P->ny; g.nz = P->nz; g.M = P->M; g.nxh = P->nxh; g.ldS = P->ldS;
@@ -135,6 +154,12 @@ Geo plan_geo(flups_plan P) {
     g.uniform_z = 0;
     g.dx = P->dx; g.dy = P->dy;
     g.sx = 1.0 / (P->dx * P->dx); g.sy = 1.0 / (P->dy * P->dy);
+    g.idx = 1.0 / P->dx; g.idy = 1.0 / P->dy;
+    g.rx = P->nx < 32 ? P->nx : 32;
+    g.tnx = P->nx / g.rx;
+    g.tny = P->ny / FLUPS_TY;
+    g.tnz = (P->nz + FLUPS_KC - 1) / FLUPS_KC;
+    g.tflags = P->tflags;
     const int nz = P->nz;
     g.idzf = P->tabs64;
     g.az = P->tabs64 + nz;
@@ -208,6 +233,11 @@ flups_status flups_plan_create(flups_plan* out, int nx, int ny, int nz, double d
     P->bx = (double*)A.get(P->npts * sizeof(double));
     P->by = (double*)A.get(P->npts * sizeof(double));
     P->bz = (double*)A.get(P->npts * sizeof(double));
+    {
+        const int rx = nx < 32 ? nx : 32;
+        P->tflags = (unsigned int*)A.get((size_t)(nx / rx) * (ny / FLUPS_TY) * ((nz + FLUPS_KC - 1) / FLUPS_KC) *
+                                         sizeof(unsigned int));
+    }
     P->sc = (DevScalars*)A.get(sizeof(DevScalars));
     P->npart = 3 * std::max<size_t>(flups_part_blocks_needed(nx, ny, nz), 2048);
     P->part = (double*)A.get(P->npart * sizeof(double));
@@ -269,6 +299,11 @@ flups_status flups_plan_destroy(flups_plan P) {
     DeviceGuard dg(P->dev);
     cudaError_t e = cudaStreamSynchronize(P->stream);
     for (int q = 0; q < P->nallocs; ++q) cudaFree(P->allocs[q]);
+    if (P->prof_ev) {
+        for (int q = 0; q < 2 * P->prof_cap; ++q) cudaEventDestroy(P->prof_ev[q]);
+        std::free(P->prof_ev);
+        std::free(P->prof_kid);
+    }
     std::free(P->allocs);
     if (P->hbuf) cudaFree(P->hbuf);
     if (P->sc_host) cudaFreeHost(P->sc_host);
@@ -285,6 +320,48 @@ flups_status flups_set_stream(flups_plan P, void* stream) {
 size_t flups_workspace_bytes(flups_plan P) { return P ? P->total_bytes : 0; }
 
 unsigned long long flups_launch_count(flups_plan P) { return P ? P->launches : 0ull; }
+
+const char* flups_kernel_name(int id) { return (id >= 0 && id < FK_COUNT) ? kKernelNames[id] : "unknown"; }
+
+flups_status flups_set_profiling(flups_plan P, int on) {
+    if (!P) return FLUPS_EINVAL;
+    DeviceGuard dg(P->dev);
+    if (on && !P->prof_ev) {
+        const int cap = 1024;
+        P->prof_ev = (cudaEvent_t*)std::calloc(2 * cap, sizeof(cudaEvent_t));
+        P->prof_kid = (int*)std::calloc(cap, sizeof(int));
+        if (!P->prof_ev || !P->prof_kid) return FLUPS_ENOMEM;
+        for (int q = 0; q < 2 * cap; ++q)
+            if (cudaEventCreate(&P->prof_ev[q]) != cudaSuccess) return FLUPS_ECUDA;
+        P->prof_cap = cap;
+    }
+    P->prof_on = on ? 1 : 0;
+    P->prof_n = 0;
+    for (int q = 0; q < FK_COUNT; ++q) { P->prof_ms[q] = 0.0; P->prof_cnt[q] = 0; }
+    return FLUPS_OK;
+}
+
+flups_status flups_profile_read(flups_plan P, double* ms, long long* n) {
+    if (!P || !ms || !n) return FLUPS_EINVAL;
+    DeviceGuard dg(P->dev);
+    cudaError_t e = cudaStreamSynchronize(P->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    for (int q = 0; q < P->prof_n; ++q) {
+        float t = 0.f;
+        if (cudaEventElapsedTime(&t, P->prof_ev[2 * q], P->prof_ev[2 * q + 1]) == cudaSuccess) {
+            P->prof_ms[P->prof_kid[q]] += t;
+            P->prof_cnt[P->prof_kid[q]] += 1;
+        }
+    }
+    P->prof_n = 0;
+    for (int q = 0; q < FK_COUNT; ++q) {
+        ms[q] = P->prof_ms[q];
+        n[q] = P->prof_cnt[q];
+        P->prof_ms[q] = 0.0;
+        P->prof_cnt[q] = 0;
+    }
+    return FLUPS_OK;
+}
 
 flups_status flups_set_density(flups_plan P, const double* rho, double rho0) {
     if (!P || !rho || !aligned16(rho) || std::isnan(rho0)) return FLUPS_EINVAL;

@@ -34,6 +34,9 @@ struct FftLen {
 struct DevScalars {
     double rho0;        // minimum density
     double inv_rho0;    // 1/rho0
+    double m2r0;        // -2 rho0
+    double m2r0_dx;     // -2 rho0 / dx
+    double m2r0_dy;     // -2 rho0 / dy
     double mean_f;      // volume-weighted mean of f
     double f2;          // ||f - <f>||^2
     double r2;          // ||r||^2 of the last residual pass
@@ -43,15 +46,31 @@ struct DevScalars {
 };
 
 // Geometry and tables handed to kernels by value.
+// Stencil tiles: a CTA of the rhs/correct kernels covers RX x FLUPS_TY cells of a plane,
+// RX = min(32, nx), and marches up FLUPS_KC planes.  set_density flags every tile in which
+// some face coefficient (1 - rho0/rho_f) that the tile's CTA reads is nonzero.
+#define FLUPS_TY 8
+#define FLUPS_KC 16
+
 struct Geo {
     int nx, ny, nz, M, nxh, ldS, walls, uniform_z;
     double dx, dy;
+    double idx, idy;             // 1/dx, 1/dy
     double sx, sy;               // 1/dx^2, 1/dy^2
+    int rx, tnx, tny, tnz;       // stencil tile width and tile counts
+    unsigned int* tflags;        // [tnz][tny][tnx] nonzero: the tile needs the p_hat terms
     const double* idzf;          // [nz] 1/dzf_k
     const double* az;            // [nz] Laplacian z sub-diagonal   1/(dzf_k dzc_{k-1}) (0 at k=0 with walls)
     const double* cz;            // [nz] Laplacian z super-diagonal 1/(dzf_k dzc_k) (0 at k=nz-1 with walls)
     const double* idzc;          // [nz] 1/dzc_k (0 on the top wall face)
     const double* dzf;           // [nz]
+};
+
+// Optional per-kernel timing (flups_set_profiling): each launcher brackets its kernel(s)
+// with CUDA events on the plan's stream.  Kernel ids name the timed regions.
+enum FlupsKernelId {
+    FK_RHO_MINMAX = 0, FK_FACE_COEFFS, FK_RHS, FK_CORRECT, FK_XFWD_F32, FK_XFWD_RES32, FK_YCOL32, FK_ZPER32,
+    FK_ZTRI32, FK_XINV32, FK_FINALIZE, FK_XFWD64, FK_YCOL64, FK_ZPER64, FK_ZTRI64, FK_XINV64, FK_RES64, FK_COUNT
 };
 
 struct flups_plan_s {
@@ -65,6 +84,7 @@ struct flups_plan_s {
     void* spec;                  // spectrum, float2 or double2
     void* zscr;                  // z Thomas multipliers (walls)
     double* bx; double* by; double* bz;
+    unsigned int* tflags;        // stencil tile flags (see FLUPS_TY)
     DevScalars* sc;              // device scalars
     DevScalars* sc_host;         // pinned host mirror
     double* part;                // reduction partials
@@ -82,10 +102,19 @@ struct flups_plan_s {
     void** allocs;               // every workspace allocation, freed by destroy
     int nallocs;
     unsigned long long launches; // kernels launched on this plan so far
+    // per-kernel timing
+    int prof_on, prof_n, prof_cap, prof_open;
+    cudaEvent_t* prof_ev;        // 2 * prof_cap events
+    int* prof_kid;               // kernel id of each recorded pair
+    double prof_ms[FK_COUNT];
+    long long prof_cnt[FK_COUNT];
 };
 
 // Every launcher adds the number of kernels it launched to P->launches.
 #define FLUPS_COUNT(P, n) ((P)->launches += (unsigned long long)(n))
+
+void flups_prof_begin(flups_plan P, int kid);
+void flups_prof_end(flups_plan P);
 
 // Launchers (return cudaGetLastError()).
 cudaError_t launch_set_density(flups_plan P, const double* rho, double rho0);

@@ -68,7 +68,8 @@ __global__ void k_rho_minmax(const double* __restrict__ rho, size_t n, long long
     }
 }
 
-__global__ void k_rho_finalize(const long long* __restrict__ part, int nblk, DevScalars* sc, double rho0_user) {
+__global__ void k_rho_finalize(const long long* __restrict__ part, int nblk, DevScalars* sc, double rho0_user,
+                               double idx, double idy) {
     if (threadIdx.x != 0) return;
     long long mn = 0x7FFFFFFFFFFFFFFFLL;
     int bad = 0;
@@ -79,54 +80,140 @@ __global__ void k_rho_finalize(const long long* __restrict__ part, int nblk, Dev
     const double r0 = rho0_user > 0.0 ? rho0_user : __longlong_as_double(mn);
     sc->rho0 = r0;
     sc->inv_rho0 = 1.0 / r0;
+    sc->m2r0 = -2.0 * r0;
+    sc->m2r0_dx = -2.0 * r0 * idx;
+    sc->m2r0_dy = -2.0 * r0 * idy;
     sc->bad_rho = bad;
 }
 
 // b = (1 - rho0/rho_f) / h = 1/h - (2 rho0 / h) / (rho_a + rho_b) for the face above each
-// cell in x, y and z.  With walls the top face gets b = 0 (1/dzc = 0 there).
+// cell in x, y and z.  With walls the top face gets b = 0 (1/dzc = 0 there).  A face whose
+// two cells both hold exactly rho0 has b = 0 exactly; that is decided on the bit patterns,
+// without FP64 instructions, and skips the reciprocal.  The kernel also flags every stencil
+// tile whose CTA reads a nonzero b: the tile that owns the cell, and the tile above it in
+// x, y or z when the cell's face is that tile's lower boundary face.
+// The three coefficients of one cell when some face has a density other than rho0.  Kept
+// out of line so that the compiler does not evaluate the reciprocals speculatively in the
+// (common) warps where every face is at rho0.
+__device__ __noinline__ double3 face_coeffs_slow(double rc, double re, double rn, double rt, double iz, bool nx_,
+                                                 bool ny_, bool nz_, const DevScalars* __restrict__ sc, double idx,
+                                                 double idy) {
+    double3 v = make_double3(0.0, 0.0, 0.0);
+    if (nx_) v.x = fma(sc->m2r0_dx, recip64(rc + re), idx);
+    if (ny_) v.y = fma(sc->m2r0_dy, recip64(rc + rn), idy);
+    if (nz_) v.z = iz * fma(sc->m2r0, recip64(rc + rt), 1.0);
+    return v;
+}
+
 __global__ void __launch_bounds__(256) k_face_coeffs(const double* __restrict__ rho, double* __restrict__ bx,
                                                      double* __restrict__ by, double* __restrict__ bz, Geo g,
                                                      const DevScalars* __restrict__ sc) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y, k = blockIdx.z;
-    if (i >= g.nx) return;
-    const double r0 = sc->rho0;
-    const size_t idx = ((size_t)k * g.ny + j) * g.nx + i;
-    const double rc = __ldg(rho + idx);
-    const double re = __ldg(rho + ((size_t)k * g.ny + j) * g.nx + ((i + 1) & (g.nx - 1)));
-    const double rn = __ldg(rho + ((size_t)k * g.ny + ((j + 1) & (g.ny - 1))) * g.nx + i);
-    const int kp = g.walls ? (k + 1 < g.nz ? k + 1 : k) : (k + 1 == g.nz ? 0 : k + 1);
-    const double rt = __ldg(rho + ((size_t)kp * g.ny + j) * g.nx + i);
-    const double ix = 1.0 / g.dx, iy = 1.0 / g.dy, iz = __ldg(g.idzc + k);
-    bx[idx] = fma(-2.0 * r0 * ix, recip64(rc + re), ix);
-    by[idx] = fma(-2.0 * r0 * iy, recip64(rc + rn), iy);
-    bz[idx] = fma(-2.0 * r0 * iz, recip64(rc + rt), iz);
+    const bool act = i < g.nx;
+    const long long b0 = __double_as_longlong(sc->rho0);
+    double vx = 0.0, vy = 0.0, vz = 0.0;
+    size_t idx = 0;
+    long long bc_ = b0, be = b0, bn = b0, bt = b0;
+    double iz = 0.0;
+    if (act) {
+        idx = ((size_t)k * g.ny + j) * g.nx + i;
+        bc_ = __double_as_longlong(__ldg(rho + idx));
+        be = __double_as_longlong(__ldg(rho + ((size_t)k * g.ny + j) * g.nx + ((i + 1) & (g.nx - 1))));
+        bn = __double_as_longlong(__ldg(rho + ((size_t)k * g.ny + ((j + 1) & (g.ny - 1))) * g.nx + i));
+        const int kp = g.walls ? (k + 1 < g.nz ? k + 1 : k) : (k + 1 == g.nz ? 0 : k + 1);
+        bt = __double_as_longlong(__ldg(rho + ((size_t)kp * g.ny + j) * g.nx + i));
+        iz = __ldg(g.idzc + k);
+    }
+    const bool cz0 = bc_ == b0;
+    const bool need_x = !(cz0 && be == b0), need_y = !(cz0 && bn == b0);
+    const bool need_z = !(cz0 && bt == b0) && __double_as_longlong(iz) != 0;
+    if (__any_sync(0xffffffffu, need_x || need_y || need_z)) {
+        const double3 v = face_coeffs_slow(__longlong_as_double(bc_), __longlong_as_double(be),
+                                           __longlong_as_double(bn), __longlong_as_double(bt), iz, need_x, need_y,
+                                           need_z, sc, g.idx, g.idy);
+        vx = v.x;
+        vy = v.y;
+        vz = v.z;
+    }
+    if (act) {
+        bx[idx] = vx;
+        by[idx] = vy;
+        bz[idx] = vz;
+    }
+    // tile flags
+    const int tx = i / g.rx, ty = j / FLUPS_TY, tz = k / FLUPS_KC;
+    const int txp = (tx + 1 == g.tnx) ? 0 : tx + 1;
+    const int typ = (ty + 1 == g.tny) ? 0 : ty + 1;
+    const int tzp = (tz + 1 == g.tnz) ? 0 : tz + 1;
+    // nonzero tests on the bit patterns (+0 and -0 both count as zero)
+    const bool nzx = (__double_as_longlong(vx) << 1) != 0, nzy = (__double_as_longlong(vy) << 1) != 0;
+    const bool nzz = (__double_as_longlong(vz) << 1) != 0;
+    const bool last_x = act && (i % g.rx == g.rx - 1), last_y = (j % FLUPS_TY) == FLUPS_TY - 1;
+    const bool last_z = (k % FLUPS_KC) == FLUPS_KC - 1 || k == g.nz - 1;
+    auto tile = [&](int a, int b, int c) { return (size_t)(c * g.tny + b) * g.tnx + a; };
+    if (g.rx == 32) {
+        // the 32 lanes of a warp are the 32 columns of one tile row
+        const unsigned any = __ballot_sync(0xffffffffu, nzx || nzy || nzz);
+        const unsigned anyy = __ballot_sync(0xffffffffu, nzy);
+        const unsigned anyz = __ballot_sync(0xffffffffu, nzz);
+        if ((threadIdx.x & 31) == 0 && act) {
+            if (any) atomicOr(g.tflags + tile(tx, ty, tz), 1u);
+            if (anyy && last_y) atomicOr(g.tflags + tile(tx, typ, tz), 1u);
+            if (anyz && last_z && !(g.walls && k == g.nz - 1)) atomicOr(g.tflags + tile(tx, ty, tzp), 1u);
+        }
+        if (nzx && last_x) atomicOr(g.tflags + tile(txp, ty, tz), 1u);
+    } else if (act) {
+        if (nzx || nzy || nzz) atomicOr(g.tflags + tile(tx, ty, tz), 1u);
+        if (nzx && last_x) atomicOr(g.tflags + tile(txp, ty, tz), 1u);
+        if (nzy && last_y) atomicOr(g.tflags + tile(tx, typ, tz), 1u);
+        if (nzz && last_z && !(g.walls && k == g.nz - 1)) atomicOr(g.tflags + tile(tx, ty, tzp), 1u);
+    }
 }
 
 // ------------------------------------------------------------------------- rhs
 // CTA = RX x TY cells of one plane, marching up KC planes.  Shared memory holds p~ on an
 // extended plane (cells j0-1 .. j0+TY, i0-1 .. i0+RX) for the current and the next level,
-// and the x- and y-face fluxes of the current level.
+// and the x- and y-face fluxes of the current level.  A tile with every face coefficient
+// zero has q = u on all its faces and reduces to f = (rho0/dt) D u (same bits).
 template <int RX, int TY>
 __global__ void __launch_bounds__(RX * TY) k_rhs(const double* __restrict__ u, const double* __restrict__ v,
                                                  const double* __restrict__ w, const double* __restrict__ pn,
                                                  const double* __restrict__ pnm1, const double* __restrict__ bx,
                                                  const double* __restrict__ by, const double* __restrict__ bz,
                                                  double* __restrict__ f, Geo g, double c1, double c2, double dt,
-                                                 double inv_dt, int kc, const DevScalars* __restrict__ sc) {
+                                                 double inv_dt, const DevScalars* __restrict__ sc) {
     __shared__ double Pt[2][TY + 2][RX + 2];
     __shared__ double QX[TY][RX + 1];
     __shared__ double QY[TY + 1][RX];
+    constexpr int KC = FLUPS_KC;
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * RX + tx, nthr = RX * TY;
     const int i0 = blockIdx.x * RX, j0 = blockIdx.y * TY;
-    const int kb = blockIdx.z * kc, ke = min(kb + kc, g.nz);
+    const int kb = blockIdx.z * KC, ke = min(kb + KC, g.nz);
     const int nx = g.nx, ny = g.ny, nz = g.nz;
+    const double rdt = sc->rho0 * inv_dt;          // rho0 / dt
+    const double kx = rdt * g.idx, ky = rdt * g.idy;
+    const int i = i0 + tx, j = j0 + ty;
+    const int im = (i - 1) & (nx - 1), jm = (j - 1) & (ny - 1);
+
+    if (g.tflags[(blockIdx.z * g.tny + blockIdx.y) * g.tnx + blockIdx.x] == 0) {
+        double wlo = 0.0;
+        if (!(g.walls && kb == 0)) wlo = __ldg(w + ((size_t)(kb == 0 ? nz - 1 : kb - 1) * ny + j) * nx + i);
+        for (int k = kb; k < ke; ++k) {
+            const size_t row = (size_t)k * ny;
+            const size_t qc = (row + j) * nx + i;
+            const double whi = (g.walls && k == nz - 1) ? 0.0 : __ldg(w + qc);
+            const double du = __ldg(u + qc) - __ldg(u + (row + j) * nx + im);
+            const double dv = __ldg(v + qc) - __ldg(v + (row + jm) * nx + i);
+            f[qc] = fma(du, kx, fma(dv, ky, (whi - wlo) * (rdt * __ldg(g.idzf + k))));
+            wlo = whi;
+        }
+        return;
+    }
+
     const double s = dt * sc->inv_rho0;            // dt / rho0
     const double s1 = s * c1, s2 = s * c2;         // p~ = s1 p^n - s2 p^{n-1}
-    const double rdt = sc->rho0 * inv_dt;          // rho0 / dt
-    const double kx = rdt / g.dx, ky = rdt / g.dy;
     const bool two = pnm1 != nullptr;
-
     auto pt_at = [&](size_t q) -> double {
         const double a = s1 * __ldg(pn + q);
         return two ? fma(-s2, __ldg(pnm1 + q), a) : a;
@@ -134,12 +221,10 @@ __global__ void __launch_bounds__(RX * TY) k_rhs(const double* __restrict__ u, c
     auto fill = [&](int k, int buf) {
         for (int e = tid; e < (TY + 2) * (RX + 2); e += nthr) {
             const int bb = e / (RX + 2), aa = e - bb * (RX + 2);
-            const int j = (j0 - 1 + bb) & (ny - 1), i = (i0 - 1 + aa) & (nx - 1);
-            Pt[buf][bb][aa] = pt_at(((size_t)k * ny + j) * nx + i);
+            const int jj = (j0 - 1 + bb) & (ny - 1), ii = (i0 - 1 + aa) & (nx - 1);
+            Pt[buf][bb][aa] = pt_at(((size_t)k * ny + jj) * nx + ii);
         }
     };
-
-    const int i = i0 + tx, j = j0 + ty;
     // z flux through the bottom face of cell kb
     double qz_lo = 0.0;
     if (!(g.walls && kb == 0)) {
@@ -176,21 +261,46 @@ __global__ void __launch_bounds__(RX * TY) k_rhs(const double* __restrict__ u, c
 
 // --------------------------------------------------------------------- correct
 // Each cell owns the faces above it: u_new = u - a (p_+ - p) + b (p~_+ - p~), a = dt/(rho0 h).
+// A tile with every face coefficient zero skips p~ (same bits: the b term is +0).
 template <int RX, int TY>
 __global__ void __launch_bounds__(RX * TY) k_correct(const double* __restrict__ p, const double* __restrict__ pn,
                                                      const double* __restrict__ pnm1, const double* __restrict__ bx,
                                                      const double* __restrict__ by, const double* __restrict__ bz,
                                                      double* __restrict__ u, double* __restrict__ v,
                                                      double* __restrict__ w, Geo g, double c1, double c2,
-                                                     double dt, int kc, const DevScalars* __restrict__ sc) {
+                                                     double dt, const DevScalars* __restrict__ sc) {
     __shared__ double Pt[2][TY + 1][RX + 1];
+    constexpr int KC = FLUPS_KC;
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * RX + tx, nthr = RX * TY;
     const int i0 = blockIdx.x * RX, j0 = blockIdx.y * TY;
-    const int kb = blockIdx.z * kc, ke = min(kb + kc, g.nz);
+    const int kb = blockIdx.z * KC, ke = min(kb + KC, g.nz);
     const int nx = g.nx, ny = g.ny, nz = g.nz;
     const double s = dt * sc->inv_rho0;
+    const double ax = s * g.idx, ay = s * g.idy;
+    const int i = i0 + tx, j = j0 + ty;
+    const int ie = (i + 1) & (nx - 1), jn = (j + 1) & (ny - 1);
+
+    if (g.tflags[(blockIdx.z * g.tny + blockIdx.y) * g.tnx + blockIdx.x] == 0) {
+        for (int k = kb; k < ke; ++k) {
+            const bool top = g.walls && (k == nz - 1);
+            const int kp = k + 1 == nz ? 0 : k + 1;
+            const size_t qc = ((size_t)k * ny + j) * nx + i;
+            const double pc = __ldg(p + qc);
+            const double pe = __ldg(p + ((size_t)k * ny + j) * nx + ie);
+            const double pnb = __ldg(p + ((size_t)k * ny + jn) * nx + i);
+            u[qc] = fma(-ax, pe - pc, u[qc]);
+            v[qc] = fma(-ay, pnb - pc, v[qc]);
+            if (top) {
+                w[qc] = 0.0;
+            } else {
+                const double pt = __ldg(p + ((size_t)kp * ny + j) * nx + i);
+                w[qc] = fma(-(s * __ldg(g.idzc + k)), pt - pc, w[qc]);
+            }
+        }
+        return;
+    }
+
     const double s1 = s * c1, s2 = s * c2;
-    const double ax = s / g.dx, ay = s / g.dy;
     const bool two = pnm1 != nullptr;
     auto pt_at = [&](size_t q) -> double {
         const double a = s1 * __ldg(pn + q);
@@ -203,8 +313,6 @@ __global__ void __launch_bounds__(RX * TY) k_correct(const double* __restrict__ 
             Pt[buf][bb][aa] = pt_at(((size_t)k * ny + jj) * nx + ii);
         }
     };
-    const int i = i0 + tx, j = j0 + ty;
-    const int ie = (i + 1) & (nx - 1), jn = (j + 1) & (ny - 1);
     fill(kb, kb & 1);
     for (int k = kb; k < ke; ++k) {
         const int cur = k & 1, nxt = cur ^ 1;
@@ -305,22 +413,24 @@ __global__ void k_res64_finalize(const double* __restrict__ part, int nblk, DevS
 template <int RX>
 void run_rhs(flups_plan P, const double* u, const double* v, const double* w, const double* pn,
              const double* pnm1, double c1, double c2, double dt, double* f, const Geo& g) {
-    constexpr int TY = 8;
-    const int kc = 16;
-    dim3 grid(g.nx / RX, g.ny / TY, (g.nz + kc - 1) / kc);
+    constexpr int TY = FLUPS_TY;
+    dim3 grid(g.tnx, g.tny, g.tnz);
+    flups_prof_begin(P, FK_RHS);
     k_rhs<RX, TY><<<grid, dim3(RX, TY), 0, P->stream>>>(u, v, w, pn, pnm1, P->bx, P->by, P->bz, f, g, c1, c2, dt,
-                                                         1.0 / dt, kc, P->sc);
+                                                         1.0 / dt, P->sc);
+    flups_prof_end(P);
     FLUPS_COUNT(P, 1);
 }
 
 template <int RX>
 void run_correct(flups_plan P, const double* p, const double* pn, const double* pnm1, double c1, double c2,
                  double dt, double* u, double* v, double* w, const Geo& g) {
-    constexpr int TY = 8;
-    const int kc = 16;
-    dim3 grid(g.nx / RX, g.ny / TY, (g.nz + kc - 1) / kc);
+    constexpr int TY = FLUPS_TY;
+    dim3 grid(g.tnx, g.tny, g.tnz);
+    flups_prof_begin(P, FK_CORRECT);
     k_correct<RX, TY><<<grid, dim3(RX, TY), 0, P->stream>>>(p, pn, pnm1, P->bx, P->by, P->bz, u, v, w, g, c1, c2,
-                                                             dt, kc, P->sc);
+                                                             dt, P->sc);
+    flups_prof_end(P);
     FLUPS_COUNT(P, 1);
 }
 
@@ -329,10 +439,16 @@ void run_correct(flups_plan P, const double* p, const double* pn, const double* 
 cudaError_t launch_set_density(flups_plan P, const double* rho, double rho0) {
     const Geo g = plan_geo(P);
     const int nblk = 1024;
+    flups_prof_begin(P, FK_RHO_MINMAX);
     k_rho_minmax<<<nblk, 256, 0, P->stream>>>(rho, P->npts, reinterpret_cast<long long*>(P->part));
-    k_rho_finalize<<<1, 32, 0, P->stream>>>(reinterpret_cast<const long long*>(P->part), nblk, P->sc, rho0);
+    k_rho_finalize<<<1, 32, 0, P->stream>>>(reinterpret_cast<const long long*>(P->part), nblk, P->sc, rho0, g.idx,
+                                            g.idy);
+    flups_prof_end(P);
+    cudaMemsetAsync(P->tflags, 0, (size_t)g.tnx * g.tny * g.tnz * sizeof(unsigned int), P->stream);
     dim3 grid((g.nx + 255) / 256, g.ny, g.nz);
+    flups_prof_begin(P, FK_FACE_COEFFS);
     k_face_coeffs<<<grid, 256, 0, P->stream>>>(rho, P->bx, P->by, P->bz, g, P->sc);
+    flups_prof_end(P);
     FLUPS_COUNT(P, 3);
     return cudaGetLastError();
 }
@@ -358,11 +474,13 @@ cudaError_t launch_correct(flups_plan P, const double* p, const double* pn, cons
 cudaError_t launch_residual64_norm(flups_plan P, const double* f, const double* p) {
     const Geo g = plan_geo(P);
     const int nblk = 1024;
+    flups_prof_begin(P, FK_RES64);
     k_res64<<<nblk, 256, 0, P->stream>>>(f, p, g, P->sc, 0, P->part);
     k_res64_finalize<<<1, 32, 0, P->stream>>>(P->part, nblk, P->sc, 0, 1.0 / ((double)P->nx * P->ny * P->sum_dzf),
                                               (double)P->npts);
     k_res64<<<nblk, 256, 0, P->stream>>>(f, p, g, P->sc, 1, P->part);
     k_res64_finalize<<<1, 32, 0, P->stream>>>(P->part, nblk, P->sc, 1, 0.0, 0.0);
+    flups_prof_end(P);
     FLUPS_COUNT(P, 4);
     return cudaGetLastError();
 }

@@ -24,7 +24,9 @@ SYMBOLS = [
     "flups_plan_create", "flups_plan_destroy", "flups_set_stream", "flups_workspace_bytes", "flups_launch_count",
     "flups_set_density", "flups_get_rho0", "flups_rhs", "flups_solve", "flups_correct",
     "flups_project_host", "flups_status_string", "flups_solve_fp64_noalloc",
+    "flups_set_profiling", "flups_profile_read", "flups_kernel_name",
 ]
+NKERNELS = 17
 
 
 class FlupsError(RuntimeError):
@@ -65,10 +67,15 @@ def lib():
         L.flups_correct.argtypes = [P, V, V, V, D, D, D, V, V, V]
         L.flups_project_host.argtypes = [P, V, V, V, V, V, V, D, D, D, D, I, V, ctypes.POINTER(Info)]
         L.flups_solve_fp64_noalloc.argtypes = [I, I, I, D, D, ctypes.POINTER(D), I, V, V, V]
+        L.flups_set_profiling.argtypes = [P, I]
+        L.flups_profile_read.argtypes = [P, ctypes.POINTER(D), ctypes.POINTER(ctypes.c_longlong)]
+        L.flups_kernel_name.argtypes = [I]
+        L.flups_kernel_name.restype = ctypes.c_char_p
         L.flups_status_string.argtypes = [I]
         L.flups_status_string.restype = ctypes.c_char_p
         for name in SYMBOLS:
-            if name not in ("flups_status_string", "flups_workspace_bytes", "flups_launch_count"):
+            if name not in ("flups_status_string", "flups_workspace_bytes", "flups_launch_count",
+                            "flups_kernel_name"):
                 getattr(L, name).restype = I
         _lib = L
     return _lib
@@ -150,6 +157,16 @@ class Plan:
     @property
     def workspace_bytes(self):
         return lib().flups_workspace_bytes(self._h)
+
+    def set_profiling(self, on=True):
+        _check(lib().flups_set_profiling(self._h, int(bool(on))), "flups_set_profiling")
+
+    def profile(self):
+        """{kernel name: (total ms, timed regions)} recorded since the last call (synchronises)."""
+        ms = (ctypes.c_double * NKERNELS)()
+        n = (ctypes.c_longlong * NKERNELS)()
+        _check(lib().flups_profile_read(self._h, ms, n), "flups_profile_read")
+        return {lib().flups_kernel_name(k).decode(): (ms[k], n[k]) for k in range(NKERNELS) if n[k]}
 
     def set_stream(self, stream):
         _check(lib().flups_set_stream(self._h, stream), "flups_set_stream")

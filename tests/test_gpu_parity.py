@@ -209,3 +209,22 @@ def test_solve_zero_rhs_gives_zero():
     with flups.Plan.for_case(c, "fp64") as plan:
         plan.solve(f, p, rtol=0.0, info=False)
         assert np.all(host(p) == 0.0)
+
+
+def test_profiling_reports_every_launched_kernel():
+    c, g, (fo, _, _, _, _) = case("sphere32")
+    d = {k: dev(c[k]) for k in ("u", "v", "w", "rho", "pn", "pnm1")}
+    f = torch.empty_like(d["u"])
+    p = torch.empty_like(d["u"])
+    with flups.Plan.for_case(c, "fp32_refine") as plan:
+        plan.set_profiling(True)
+        plan.set_density(d["rho"])
+        plan.rhs(d["u"], d["v"], d["w"], d["pn"], d["pnm1"], 2.0, 1.0, c.dt, f)
+        info = plan.solve(f, p, rtol=1e-10)
+        plan.correct(p, d["pn"], d["pnm1"], 2.0, 1.0, c.dt, d["u"], d["v"], d["w"])
+        prof = plan.profile()
+    for k in ("k_rho_minmax", "k_face_coeffs", "k_rhs", "k_correct", "k_xfwd_f32", "k_xfwd_residual32",
+              "k_ycol32", "k_zper32", "k_xinv32"):
+        assert k in prof and prof[k][0] > 0.0, k
+    assert prof["k_xfwd_residual32"][1] == info.iters
+    assert prof["k_xinv32"][1] == info.iters
