@@ -150,6 +150,19 @@ __device__ __forceinline__ double f2d_bits(float x) {
     return __hiloint2double((int)hi, (int)((b & 7u) << 29));
 }
 
+// x * 2^(58 - E) as a 64-bit integer, truncated toward zero, for |x| < 2^E; sh = 1017 + E.
+// Built from the binary64 layout with integer operations only.  The 7-point sums of such
+// values are exact in 64-bit integers (|sum| < 12 * 2^58 < 2^62).
+__device__ __forceinline__ long long fixq(double x, int sh) {
+    const long long b = __double_as_longlong(x);
+    const int e = (int)((b >> 52) & 0x7FF);
+    const int sft = e - sh;
+    const long long m = (b & 0xFFFFFFFFFFFFFLL) | 0x10000000000000LL;
+    long long v = sft >= 0 ? (m << sft) : (sft > -54 ? (m >> -sft) : 0LL);
+    v = e == 0 ? 0LL : v;
+    return b < 0 ? -v : v;
+}
+
 template <typename T> __device__ __forceinline__ T from_double(double x) {
     if constexpr (sizeof(T) == 4) return d2f_bits(x);
     else return x;
@@ -198,6 +211,10 @@ __device__ void block_sum3(double a, double b, double c, double* __restrict__ pa
 //         sum_k dzf_k sum_ij f (FP64), sum f^2 and sum f (FP32 per thread, FP64 across).
 // MODE 1: input r = f - (L p + <f>_V) evaluated in FP64 on the fly (the defect of the
 //         refinement), with the partial sum of r^2.
+// MODE 2: the same defect on a grid with one spacing h in x, y and z: h^2 L p is an integer
+//         combination of the seven p values, summed exactly in 64-bit fixed point (scale
+//         2^(58-E), E from the largest exponent of p recorded when p was written), then
+//         r = (f - <f>) - (2^(E-58)/h^2) S with one conversion and one FMA in FP64.
 template <typename T, int E, int MODE, bool STATS>
 __global__ void __launch_bounds__(1024) k_xfwd(const double* __restrict__ f, const double* __restrict__ p,
                                                typename cplx<T>::t* __restrict__ S, Geo g, FftLen L,
@@ -216,7 +233,15 @@ __global__ void __launch_bounds__(1024) k_xfwd(const double* __restrict__ f, con
     double accw = 0.0;
     float acc2 = 0.f, acc1 = 0.f;
     double mf = 0.0;
-    if (MODE == 1) mf = sc->mean_f;
+    if (MODE >= 1) mf = sc->mean_f;
+    int sh = 0;
+    double cfix = 0.0;
+    if (MODE == 2) {
+        const int pe_ = sc->pexp;
+        sh = pe_ - 5;
+        if (pe_ >= 2047) cfix = __longlong_as_double(0x7FF8000000000000LL);           // NaN: p not finite
+        else if (pe_ - 57 >= 1) cfix = __hiloint2double((pe_ - 57) << 20, 0) * g.sx;   // 2^(pexp-1080) / h^2
+    }
     for (int idx = tid; idx < (B << lgM); idx += nthr) {
         const int c = idx >> lgM, n = idx & Mm;
         const int row = row0 + c;
@@ -231,6 +256,32 @@ __global__ void __launch_bounds__(1024) k_xfwd(const double* __restrict__ f, con
                     acc2 = fmaf((float)z.x, (float)z.x, fmaf((float)z.y, (float)z.y, acc2));
                     acc1 += (float)z.x + (float)z.y;
                 }
+            } else if (MODE == 2) {
+                const int k = row / g.ny, j = row - k * g.ny;
+                const int x0 = 2 * n;
+                const double* pr = p + (size_t)row * nx;
+                const double2 pc = __ldg(reinterpret_cast<const double2*>(pr) + n);
+                const double pw = __ldg(pr + ((x0 - 1) & (nx - 1)));
+                const double pe = __ldg(pr + ((x0 + 2) & (nx - 1)));
+                const int jm = (j - 1) & (g.ny - 1), jp = (j + 1) & (g.ny - 1);
+                int km, kp;
+                if (g.walls) { km = k > 0 ? k - 1 : 0; kp = k < g.nz - 1 ? k + 1 : g.nz - 1; }
+                else { km = (k - 1 + g.nz) % g.nz; kp = (k + 1) % g.nz; }
+                const double2 ps = __ldg(reinterpret_cast<const double2*>(p + ((size_t)k * g.ny + jm) * nx) + n);
+                const double2 pn = __ldg(reinterpret_cast<const double2*>(p + ((size_t)k * g.ny + jp) * nx) + n);
+                const double2 pb = __ldg(reinterpret_cast<const double2*>(p + ((size_t)km * g.ny + j) * nx) + n);
+                const double2 pt = __ldg(reinterpret_cast<const double2*>(p + ((size_t)kp * g.ny + j) * nx) + n);
+                const long long q0 = fixq(pc.x, sh), q1 = fixq(pc.y, sh);
+                long long s0 = fixq(pw, sh) + q1 + fixq(ps.x, sh) + fixq(pn.x, sh);
+                long long s1 = q0 + fixq(pe, sh) + fixq(ps.y, sh) + fixq(pn.y, sh);
+                int nd = 4;
+                if (!g.walls || k > 0) { s0 += fixq(pb.x, sh); s1 += fixq(pb.y, sh); ++nd; }
+                if (!g.walls || k < g.nz - 1) { s0 += fixq(pt.x, sh); s1 += fixq(pt.y, sh); ++nd; }
+                s0 -= (long long)nd * q0;
+                s1 -= (long long)nd * q1;
+                z = mk<T>(from_double<T>(fma(-cfix, __ll2double_rn(s0), fv.x - mf)),
+                          from_double<T>(fma(-cfix, __ll2double_rn(s1), fv.y - mf)));
+                acc2 = fmaf((float)z.x, (float)z.x, fmaf((float)z.y, (float)z.y, acc2));
             } else {
                 const int k = row / g.ny, j = row - k * g.ny;
                 const int x0 = 2 * n;
@@ -263,7 +314,7 @@ __global__ void __launch_bounds__(1024) k_xfwd(const double* __restrict__ f, con
         }
         s[n * pitch + c] = z;
     }
-    if (STATS || MODE == 1) block_sum3(accw, (double)acc2, (double)acc1, part);
+    if (STATS || MODE >= 1) block_sum3(accw, (double)acc2, (double)acc1, part);
     __syncthreads();
     fft_tile<C, E, false>(s, pitch, lgB, L, tw);
     // X_k = A_k + W_nx^k B_k and X_{M-k} = conj(A_k - W_nx^k B_k), k = 0..M/2, with
@@ -294,7 +345,7 @@ template <typename T, int E, int ACC, bool MEAN, bool SUBM>
 __global__ void __launch_bounds__(1024) k_xinv(const typename cplx<T>::t* __restrict__ S, double* __restrict__ p,
                                                Geo g, FftLen L, const typename cplx<T>::t* __restrict__ tw,
                                                const typename cplx<T>::t* __restrict__ twr, int lgB, int nrows,
-                                               const DevScalars* __restrict__ sc, double* __restrict__ part) {
+                                               DevScalars* __restrict__ sc, double* __restrict__ part) {
     typedef typename cplx<T>::t C;
     extern __shared__ __align__(16) unsigned char smraw[];
     C* s = reinterpret_cast<C*>(smraw);
@@ -326,6 +377,7 @@ __global__ void __launch_bounds__(1024) k_xinv(const typename cplx<T>::t* __rest
     fft_tile<C, E, true>(s, pitch, lgB, L, tw);
     const int nx = g.nx;
     double accw = 0.0;
+    int emax = 0;       // largest binary64 exponent field written (FP32 mode: scale of the next defect)
     T msub = (T)0;
     if (SUBM) msub = (T)sc->mean_p;
     for (int idx = tid; idx < (B << lgM); idx += nthr) {
@@ -346,6 +398,15 @@ __global__ void __launch_bounds__(1024) k_xinv(const typename cplx<T>::t* __rest
             if (MEAN) accw = fma(o.x + o.y, __ldg(g.dzf + row / g.ny), accw);
         }
         *dst = o;
+        if (sizeof(T) == 4) {
+            const int ex = (int)((__double_as_longlong(o.x) >> 52) & 0x7FF);
+            const int ey = (int)((__double_as_longlong(o.y) >> 52) & 0x7FF);
+            emax = max(emax, max(ex, ey));
+        }
+    }
+    if (sizeof(T) == 4) {
+        emax = __reduce_max_sync(0xffffffffu, emax);
+        if ((tid & 31) == 0) atomicMax(&sc->pexp, emax);
     }
     if (MEAN) block_sum3(accw, 0.0, 0.0, part);
 }
@@ -613,7 +674,7 @@ void run_xfwd(flups_plan P, const double* f, const double* p, const Geo& g) {
     const int B = 1 << lgB;
     auto kern = k_xfwd<T, Eof<T>::E, MODE, STATS>;
     allow_smem(kern);
-    flups_prof_begin(P, sizeof(T) == 8 ? FK_XFWD64 : (MODE == 1 ? FK_XFWD_RES32 : FK_XFWD_F32));
+    flups_prof_begin(P, sizeof(T) == 8 ? FK_XFWD64 : (MODE >= 1 ? FK_XFWD_RES32 : FK_XFWD_F32));
     const int nblk = (nrows + B - 1) / B;
     kern<<<nblk, B * N / E, (size_t)N * (B + 1) * sizeof(C), P->stream>>>(
         f, p, (C*)P->spec, g, P->lx, (const C*)P->twx, (const C*)P->twxr, P->tabs64 + 5 * g.nz, lgB, nrows,
@@ -675,7 +736,8 @@ cudaError_t launch_finalize_f(flups_plan P) {
 
 cudaError_t launch_xfwd32_residual(flups_plan P, const double* f, const double* p) {
     const Geo g = plan_geo(P);
-    run_xfwd<float, 1, false>(P, f, p, g);
+    if (P->uniform_h) run_xfwd<float, 2, false>(P, f, p, g);
+    else run_xfwd<float, 1, false>(P, f, p, g);
     return cudaGetLastError();
 }
 
@@ -698,6 +760,7 @@ cudaError_t launch_yz_solve32(flups_plan P) {
 
 cudaError_t launch_xinv32(flups_plan P, double* p, int mode) {
     const Geo g = plan_geo(P);
+    cudaMemsetAsync(&P->sc->pexp, 0, sizeof(int), P->stream);
     if (mode == 0) {                       // p = delta, and the volume-weighted mean of p
         run_xinv<float, 0, true, false>(P, p, g);
         const int nblk = xfwd_blocks(P, 8, 16);

@@ -42,7 +42,7 @@ struct DevScalars {
     double r2;          // ||r||^2 of the last residual pass
     double mean_p;      // volume-weighted mean of the first FP32 iterate p_0
     int    bad_rho;     // nonzero: non-finite, non-positive or out-of-range density seen
-    int    pad;
+    int    pexp;        // largest binary64 exponent field of p written by the last FP32 inverse-x pass
 };
 
 // Geometry and tables handed to kernels by value.
@@ -70,7 +70,8 @@ struct Geo {
 // with CUDA events on the plan's stream.  Kernel ids name the timed regions.
 enum FlupsKernelId {
     FK_RHO_MINMAX = 0, FK_FACE_COEFFS, FK_RHS, FK_CORRECT, FK_XFWD_F32, FK_XFWD_RES32, FK_YCOL32, FK_ZPER32,
-    FK_ZTRI32, FK_XINV32, FK_FINALIZE, FK_XFWD64, FK_YCOL64, FK_ZPER64, FK_ZTRI64, FK_XINV64, FK_RES64, FK_COUNT
+    FK_ZTRI32, FK_XINV32, FK_FINALIZE, FK_XFWD64, FK_YCOL64, FK_ZPER64, FK_ZTRI64, FK_XINV64, FK_RES64,
+    FK_TILE_FLAGS, FK_COUNT
 };
 
 struct flups_plan_s {
@@ -95,6 +96,7 @@ struct flups_plan_s {
     void* lamx; void* lamy; void* lamz;             // eigenvalues / norm, compute type
     void* tri;                   // walls: a_k/norm, b_k/norm, c_k/norm, compute type (3*nz)
     double sum_dzf;
+    int uniform_h;               // dx == dy == every dzf: the exact fixed-point defect applies
     int density_set;
     // host-buffer (end-to-end) path, allocated on first use
     double* hbuf;                // 8 fields: u v w rho pn pnm1 f p

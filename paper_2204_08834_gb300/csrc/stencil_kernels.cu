@@ -86,12 +86,55 @@ __global__ void k_rho_finalize(const long long* __restrict__ part, int nblk, Dev
     sc->bad_rho = bad;
 }
 
-// b = (1 - rho0/rho_f) / h = 1/h - (2 rho0 / h) / (rho_a + rho_b) for the face above each
-// cell in x, y and z.  With walls the top face gets b = 0 (1/dzc = 0 there).  A face whose
-// two cells both hold exactly rho0 has b = 0 exactly; that is decided on the bit patterns,
-// without FP64 instructions, and skips the reciprocal.  The kernel also flags every stencil
-// tile whose CTA reads a nonzero b: the tile that owns the cell, and the tile above it in
-// x, y or z when the cell's face is that tile's lower boundary face.
+// Tile flags: a face whose two cells both hold exactly rho0 has (1 - rho0/rho_f) = 0; the
+// test runs on the bit patterns, without FP64 instructions.  Every stencil tile whose CTA
+// reads a nonzero coefficient is flagged: the tile that owns the cell, and the tile above
+// it in x, y or z when the cell's face is that tile's lower boundary face.
+__global__ void __launch_bounds__(256) k_tile_flags(const double* __restrict__ rho, Geo g,
+                                                    const DevScalars* __restrict__ sc) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y, k = blockIdx.z;
+    const bool act = i < g.nx;
+    const long long b0 = __double_as_longlong(sc->rho0);
+    long long bc_ = b0, be = b0, bn = b0, bt = b0;
+    bool top_wall = g.walls && k == g.nz - 1;
+    if (act) {
+        const size_t idx = ((size_t)k * g.ny + j) * g.nx + i;
+        bc_ = __double_as_longlong(__ldg(rho + idx));
+        be = __double_as_longlong(__ldg(rho + ((size_t)k * g.ny + j) * g.nx + ((i + 1) & (g.nx - 1))));
+        bn = __double_as_longlong(__ldg(rho + ((size_t)k * g.ny + ((j + 1) & (g.ny - 1))) * g.nx + i));
+        const int kp = g.walls ? (k + 1 < g.nz ? k + 1 : k) : (k + 1 == g.nz ? 0 : k + 1);
+        bt = __double_as_longlong(__ldg(rho + ((size_t)kp * g.ny + j) * g.nx + i));
+    }
+    const bool cz0 = bc_ == b0;
+    const bool nzx = act && !(cz0 && be == b0), nzy = act && !(cz0 && bn == b0);
+    const bool nzz = act && !(cz0 && bt == b0) && !top_wall;
+    const int tx = i / g.rx, ty = j / FLUPS_TY, tz = k / FLUPS_KC;
+    const int txp = (tx + 1 == g.tnx) ? 0 : tx + 1;
+    const int typ = (ty + 1 == g.tny) ? 0 : ty + 1;
+    const int tzp = (tz + 1 == g.tnz) ? 0 : tz + 1;
+    const bool last_x = act && (i % g.rx == g.rx - 1), last_y = (j % FLUPS_TY) == FLUPS_TY - 1;
+    const bool last_z = (k % FLUPS_KC) == FLUPS_KC - 1 || k == g.nz - 1;
+    auto tile = [&](int a, int b, int c) { return (size_t)(c * g.tny + b) * g.tnx + a; };
+    if (g.rx == 32) {
+        // the 32 lanes of a warp are the 32 columns of one tile row
+        const unsigned any = __ballot_sync(0xffffffffu, nzx || nzy || nzz);
+        const unsigned anyy = __ballot_sync(0xffffffffu, nzy);
+        const unsigned anyz = __ballot_sync(0xffffffffu, nzz);
+        if ((threadIdx.x & 31) == 0 && act) {
+            if (any) atomicOr(g.tflags + tile(tx, ty, tz), 1u);
+            if (anyy && last_y) atomicOr(g.tflags + tile(tx, typ, tz), 1u);
+            if (anyz && last_z) atomicOr(g.tflags + tile(tx, ty, tzp), 1u);
+        }
+        if (nzx && last_x) atomicOr(g.tflags + tile(txp, ty, tz), 1u);
+    } else if (act) {
+        if (nzx || nzy || nzz) atomicOr(g.tflags + tile(tx, ty, tz), 1u);
+        if (nzx && last_x) atomicOr(g.tflags + tile(txp, ty, tz), 1u);
+        if (nzy && last_y) atomicOr(g.tflags + tile(tx, typ, tz), 1u);
+        if (nzz && last_z) atomicOr(g.tflags + tile(tx, ty, tzp), 1u);
+    }
+}
+
 // The three coefficients of one cell when some face has a density other than rho0.  Kept
 // out of line so that the compiler does not evaluate the reciprocals speculatively in the
 // (common) warps where every face is at rho0.
@@ -105,69 +148,45 @@ __device__ __noinline__ double3 face_coeffs_slow(double rc, double re, double rn
     return v;
 }
 
-__global__ void __launch_bounds__(256) k_face_coeffs(const double* __restrict__ rho, double* __restrict__ bx,
-                                                     double* __restrict__ by, double* __restrict__ bz, Geo g,
-                                                     const DevScalars* __restrict__ sc) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int j = blockIdx.y, k = blockIdx.z;
-    const bool act = i < g.nx;
+// b = (1 - rho0/rho_f) / h = 1/h - (2 rho0 / h) / (rho_a + rho_b) for the face above each
+// cell in x, y and z (b = 0 on the top wall face), written only inside flagged tiles and on
+// their one-cell lower halo in x, y and z: exactly the coefficients the rhs and correct
+// kernels read.  One CTA per tile, RX x TY threads marching up the tile's planes.
+template <int RX>
+__global__ void __launch_bounds__(RX * FLUPS_TY) k_face_coeffs(const double* __restrict__ rho,
+                                                               double* __restrict__ bx, double* __restrict__ by,
+                                                               double* __restrict__ bz, Geo g,
+                                                               const DevScalars* __restrict__ sc) {
+    if (g.tflags[(blockIdx.z * g.tny + blockIdx.y) * g.tnx + blockIdx.x] == 0) return;
+    const int i0 = blockIdx.x * RX, j0 = blockIdx.y * FLUPS_TY;
+    const int kb = blockIdx.z * FLUPS_KC, ke = min(kb + FLUPS_KC, g.nz);
+    const int k_lo = (g.walls && kb == 0) ? 0 : kb - 1;
     const long long b0 = __double_as_longlong(sc->rho0);
-    double vx = 0.0, vy = 0.0, vz = 0.0;
-    size_t idx = 0;
-    long long bc_ = b0, be = b0, bn = b0, bt = b0;
-    double iz = 0.0;
-    if (act) {
-        idx = ((size_t)k * g.ny + j) * g.nx + i;
-        bc_ = __double_as_longlong(__ldg(rho + idx));
-        be = __double_as_longlong(__ldg(rho + ((size_t)k * g.ny + j) * g.nx + ((i + 1) & (g.nx - 1))));
-        bn = __double_as_longlong(__ldg(rho + ((size_t)k * g.ny + ((j + 1) & (g.ny - 1))) * g.nx + i));
+    const int tid = threadIdx.y * RX + threadIdx.x, nthr = RX * FLUPS_TY;
+    constexpr int W = RX + 1, Hh = FLUPS_TY + 1;
+    for (int kk = k_lo; kk < ke; ++kk) {
+        const int k = kk < 0 ? g.nz - 1 : kk;
         const int kp = g.walls ? (k + 1 < g.nz ? k + 1 : k) : (k + 1 == g.nz ? 0 : k + 1);
-        bt = __double_as_longlong(__ldg(rho + ((size_t)kp * g.ny + j) * g.nx + i));
-        iz = __ldg(g.idzc + k);
-    }
-    const bool cz0 = bc_ == b0;
-    const bool need_x = !(cz0 && be == b0), need_y = !(cz0 && bn == b0);
-    const bool need_z = !(cz0 && bt == b0) && __double_as_longlong(iz) != 0;
-    if (__any_sync(0xffffffffu, need_x || need_y || need_z)) {
-        const double3 v = face_coeffs_slow(__longlong_as_double(bc_), __longlong_as_double(be),
-                                           __longlong_as_double(bn), __longlong_as_double(bt), iz, need_x, need_y,
-                                           need_z, sc, g.idx, g.idy);
-        vx = v.x;
-        vy = v.y;
-        vz = v.z;
-    }
-    if (act) {
-        bx[idx] = vx;
-        by[idx] = vy;
-        bz[idx] = vz;
-    }
-    // tile flags
-    const int tx = i / g.rx, ty = j / FLUPS_TY, tz = k / FLUPS_KC;
-    const int txp = (tx + 1 == g.tnx) ? 0 : tx + 1;
-    const int typ = (ty + 1 == g.tny) ? 0 : ty + 1;
-    const int tzp = (tz + 1 == g.tnz) ? 0 : tz + 1;
-    // nonzero tests on the bit patterns (+0 and -0 both count as zero)
-    const bool nzx = (__double_as_longlong(vx) << 1) != 0, nzy = (__double_as_longlong(vy) << 1) != 0;
-    const bool nzz = (__double_as_longlong(vz) << 1) != 0;
-    const bool last_x = act && (i % g.rx == g.rx - 1), last_y = (j % FLUPS_TY) == FLUPS_TY - 1;
-    const bool last_z = (k % FLUPS_KC) == FLUPS_KC - 1 || k == g.nz - 1;
-    auto tile = [&](int a, int b, int c) { return (size_t)(c * g.tny + b) * g.tnx + a; };
-    if (g.rx == 32) {
-        // the 32 lanes of a warp are the 32 columns of one tile row
-        const unsigned any = __ballot_sync(0xffffffffu, nzx || nzy || nzz);
-        const unsigned anyy = __ballot_sync(0xffffffffu, nzy);
-        const unsigned anyz = __ballot_sync(0xffffffffu, nzz);
-        if ((threadIdx.x & 31) == 0 && act) {
-            if (any) atomicOr(g.tflags + tile(tx, ty, tz), 1u);
-            if (anyy && last_y) atomicOr(g.tflags + tile(tx, typ, tz), 1u);
-            if (anyz && last_z && !(g.walls && k == g.nz - 1)) atomicOr(g.tflags + tile(tx, ty, tzp), 1u);
+        const double iz = __ldg(g.idzc + k);
+        for (int e = tid; e < W * Hh; e += nthr) {
+            const int bb = e / W, aa = e - bb * W;
+            const int i = (i0 - 1 + aa) & (g.nx - 1), j = (j0 - 1 + bb) & (g.ny - 1);
+            const size_t idx = ((size_t)k * g.ny + j) * g.nx + i;
+            const long long bc_ = __double_as_longlong(__ldg(rho + idx));
+            const long long be = __double_as_longlong(__ldg(rho + ((size_t)k * g.ny + j) * g.nx + ((i + 1) & (g.nx - 1))));
+            const long long bn = __double_as_longlong(__ldg(rho + ((size_t)k * g.ny + ((j + 1) & (g.ny - 1))) * g.nx + i));
+            const long long bt = __double_as_longlong(__ldg(rho + ((size_t)kp * g.ny + j) * g.nx + i));
+            const bool cz0 = bc_ == b0;
+            const bool need_x = !(cz0 && be == b0), need_y = !(cz0 && bn == b0);
+            const bool need_z = !(cz0 && bt == b0) && __double_as_longlong(iz) != 0;
+            double3 v = make_double3(0.0, 0.0, 0.0);
+            if (__any_sync(__activemask(), need_x || need_y || need_z))
+                v = face_coeffs_slow(__longlong_as_double(bc_), __longlong_as_double(be), __longlong_as_double(bn),
+                                     __longlong_as_double(bt), iz, need_x, need_y, need_z, sc, g.idx, g.idy);
+            bx[idx] = v.x;
+            by[idx] = v.y;
+            bz[idx] = v.z;
         }
-        if (nzx && last_x) atomicOr(g.tflags + tile(txp, ty, tz), 1u);
-    } else if (act) {
-        if (nzx || nzy || nzz) atomicOr(g.tflags + tile(tx, ty, tz), 1u);
-        if (nzx && last_x) atomicOr(g.tflags + tile(txp, ty, tz), 1u);
-        if (nzy && last_y) atomicOr(g.tflags + tile(tx, typ, tz), 1u);
-        if (nzz && last_z && !(g.walls && k == g.nz - 1)) atomicOr(g.tflags + tile(tx, ty, tzp), 1u);
     }
 }
 
@@ -446,10 +465,16 @@ cudaError_t launch_set_density(flups_plan P, const double* rho, double rho0) {
     flups_prof_end(P);
     cudaMemsetAsync(P->tflags, 0, (size_t)g.tnx * g.tny * g.tnz * sizeof(unsigned int), P->stream);
     dim3 grid((g.nx + 255) / 256, g.ny, g.nz);
-    flups_prof_begin(P, FK_FACE_COEFFS);
-    k_face_coeffs<<<grid, 256, 0, P->stream>>>(rho, P->bx, P->by, P->bz, g, P->sc);
+    flups_prof_begin(P, FK_TILE_FLAGS);
+    k_tile_flags<<<grid, 256, 0, P->stream>>>(rho, g, P->sc);
     flups_prof_end(P);
-    FLUPS_COUNT(P, 3);
+    flups_prof_begin(P, FK_FACE_COEFFS);
+    dim3 tgrid(g.tnx, g.tny, g.tnz);
+    if (g.rx == 32) k_face_coeffs<32><<<tgrid, dim3(32, FLUPS_TY), 0, P->stream>>>(rho, P->bx, P->by, P->bz, g, P->sc);
+    else if (g.rx == 16) k_face_coeffs<16><<<tgrid, dim3(16, FLUPS_TY), 0, P->stream>>>(rho, P->bx, P->by, P->bz, g, P->sc);
+    else k_face_coeffs<8><<<tgrid, dim3(8, FLUPS_TY), 0, P->stream>>>(rho, P->bx, P->by, P->bz, g, P->sc);
+    flups_prof_end(P);
+    FLUPS_COUNT(P, 4);
     return cudaGetLastError();
 }
 

@@ -26,7 +26,7 @@ SYMBOLS = [
     "flups_project_host", "flups_status_string", "flups_solve_fp64_noalloc",
     "flups_set_profiling", "flups_profile_read", "flups_kernel_name",
 ]
-NKERNELS = 17
+NKERNELS = 18
 
 
 class FlupsError(RuntimeError):

@@ -49,6 +49,9 @@ CASES = {
     "walls_str_64x16x2": lambda: synth.random_fields(64, 16, 2, "walls", True, seed=94),
     "two_layer_64x64x40": lambda: synth.two_layer(64, 64, 40),
     "emulsion64": lambda: synth.emulsion(64, ndrops=20),
+    # one spacing in x, y and z with walls: the exact fixed-point defect applies
+    "walls_cubic_32x16x24": lambda: synth.random_fields(32, 16, 24, "walls", False, lx=1.0, ly=0.5, lz=0.75,
+                                                        seed=96),
 }
 _cache = {}
 
