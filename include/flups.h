@@ -46,7 +46,8 @@ typedef enum {
     FLUPS_ECUDA = 4,         /* a CUDA runtime call or kernel launch failed                */
     FLUPS_ENONFINITE = 5,    /* a non-finite or non-positive density, or a NaN residual    */
     FLUPS_ENOCONV = 6,       /* refinement did not reach rtol within max_iter              */
-    FLUPS_ESTATE = 7         /* call order violated (rhs/correct before set_density)       */
+    FLUPS_ESTATE = 7,        /* call order violated (rhs/correct before set_density)       */
+    FLUPS_ETIMEOUT = 8       /* a bounded device-side wait gave up; outputs are invalid    */
 } flups_status;
 
 typedef enum { FLUPS_BC_PERIODIC = 0, FLUPS_BC_WALLS = 1 } flups_bc;

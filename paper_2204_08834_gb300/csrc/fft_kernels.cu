@@ -13,6 +13,8 @@
 // even/odd split (z_n = x_{2n} + i x_{2n+1}) and a post/pre-processing twiddle pass.
 // Transforms are unnormalised; the whole 1/(M ny nz) (or 1/(M ny) with walls) factor is
 // folded into the eigenvalue / tridiagonal tables, M = nx/2.
+#include <cstdlib>
+
 #include "flups_impl.cuh"
 
 namespace {
@@ -81,35 +83,48 @@ template <int R, bool INV, typename C> __device__ __forceinline__ void dftR(C* v
 // One Stockham radix-R pass over B lines of length N held in shared memory as
 // s[n * pitch + c].  Butterfly j (0 <= j < N/R) of line c reads n = j + r N/R and writes
 // n = (j - k) R + k + r Ns with k = j mod Ns, after the twiddles W_{Ns R}^{k r}.
-// Every thread owns E/R butterflies (nthr * E == B * N).
+// The CTA has nthr = B N / E threads (N >= E): thread tid always works on line
+// c = tid mod B and on butterflies j = tid / B + t N/E, t < E/R, so every index is a
+// per-thread base plus a compile-time multiple of a stride.
 template <typename C, int E, int R, bool INV>
 __device__ __forceinline__ void stockham_pass(C* s, int pitch, int lgB, int N, int Ns,
                                               const C* __restrict__ tw) {
     constexpr int S = E / R;
-    const int nthr = blockDim.x, tid = threadIdx.x;
-    const int NR = N / R, twstep = N / (Ns * R), Bm = (1 << lgB) - 1;
+    const int tid = threadIdx.x;
+    const int cc = tid & ((1 << lgB) - 1), j0 = tid >> lgB;
+    const int NE = N / E, NR = N / R, twstep = N / (Ns * R);
     C v[S][R];
-    int jj[S], cc[S];
 #pragma unroll
     for (int t = 0; t < S; ++t) {
-        const int slot = tid + t * nthr;
-        cc[t] = slot & Bm;
-        jj[t] = slot >> lgB;
+        const C* src = s + (j0 + t * NE) * pitch + cc;
 #pragma unroll
-        for (int r = 0; r < R; ++r) v[t][r] = s[(jj[t] + r * NR) * pitch + cc[t]];
+        for (int r = 0; r < R; ++r) v[t][r] = src[r * NR * pitch];
     }
     __syncthreads();
 #pragma unroll
     for (int t = 0; t < S; ++t) {
-        const int k = jj[t] & (Ns - 1);
+        const int jj = j0 + t * NE;
+        const int k = jj & (Ns - 1);
         if (Ns > 1) {
+            // W^{k r} for r = 1..R-1 from one table entry W^k by repeated multiplication
+            // (a few ulp in FP32, exact enough for the refined solve; table lookups in FP64)
+            if (sizeof(v[0][0].x) == 4) {
+                const C w1 = __ldg(&tw[k * twstep]);
+                C wr = w1;
 #pragma unroll
-            for (int r = 1; r < R; ++r) v[t][r] = ctw<INV>(v[t][r], __ldg(&tw[k * r * twstep]));
+                for (int r = 1; r < R; ++r) {
+                    v[t][r] = ctw<INV>(v[t][r], wr);
+                    if (r + 1 < R) wr = ctw<false>(wr, w1);
+                }
+            } else {
+#pragma unroll
+                for (int r = 1; r < R; ++r) v[t][r] = ctw<INV>(v[t][r], __ldg(&tw[k * r * twstep]));
+            }
         }
         dftR<R, INV>(v[t]);
-        const int base = (jj[t] - k) * R + k;
+        C* dst = s + ((jj - k) * R + k) * pitch + cc;
 #pragma unroll
-        for (int r = 0; r < R; ++r) s[(base + r * Ns) * pitch + cc[t]] = v[t][r];
+        for (int r = 0; r < R; ++r) dst[r * Ns * pitch] = v[t][r];
     }
     __syncthreads();
 }
@@ -119,9 +134,11 @@ template <typename C, int E, bool INV>
 __device__ __forceinline__ void fft_tile(C* s, int pitch, int lgB, const FftLen& L, const C* __restrict__ tw) {
     int Ns = 1;
     for (int st = 0; st < L.nst; ++st) {
-        const int R = L.rad[st];
-        if (R == 8) stockham_pass<C, E, 8, INV>(s, pitch, lgB, L.n, Ns, tw);
-        else if (R == 4) stockham_pass<C, E, 4, INV>(s, pitch, lgB, L.n, Ns, tw);
+        const int R = (int)((L.code >> (4 * st)) & 15u);
+        if constexpr (E >= 8) {
+            if (R == 8) { stockham_pass<C, E, 8, INV>(s, pitch, lgB, L.n, Ns, tw); Ns *= R; continue; }
+        }
+        if (R == 4) stockham_pass<C, E, 4, INV>(s, pitch, lgB, L.n, Ns, tw);
         else stockham_pass<C, E, 2, INV>(s, pitch, lgB, L.n, Ns, tw);
         Ns *= R;
     }
@@ -412,41 +429,56 @@ __global__ void __launch_bounds__(1024) k_xinv(const typename cplx<T>::t* __rest
 }
 
 // ------------------------------------------------------- column transform along y
-template <typename T, int E, bool INV>
+// TAIL = false: a tile of B consecutive kx columns of plane blockIdx.y.
+// TAIL = true : the Nyquist column kx = M of B consecutive planes (blockIdx.x * B + c), so
+//               that this ragged column is transformed by full tiles too.
+template <typename T, int E, bool INV, bool TAIL>
 __global__ void __launch_bounds__(1024) k_ycol(typename cplx<T>::t* __restrict__ S, Geo g, FftLen L,
                                                const typename cplx<T>::t* __restrict__ tw, int lgB, int kx0) {
     typedef typename cplx<T>::t C;
     extern __shared__ __align__(16) unsigned char smraw[];
     C* s = reinterpret_cast<C*>(smraw);
     const int B = 1 << lgB, pitch = B + 1;
-    const int kxa = kx0 + blockIdx.x * B;
-    const int ncol = min(B, g.nxh - kxa);
-    C* base = S + (size_t)blockIdx.y * g.ny * g.ldS + kxa;
-    const int tid = threadIdx.x, nthr = blockDim.x, N = g.ny;
-    {   // every thread issues its E loads before touching shared memory (nthr * E == B * N)
+    const size_t plane = (size_t)g.ny * g.ldS;
+    C* base;
+    size_t cs;
+    int ncol;
+    if (TAIL) {
+        base = S + (size_t)blockIdx.x * B * plane + g.M;
+        cs = plane;
+        ncol = min(B, g.nz - (int)blockIdx.x * B);
+    } else {
+        const int kxa = kx0 + blockIdx.x * B;
+        base = S + (size_t)blockIdx.y * plane + kxa;
+        cs = 1;
+        ncol = min(B, g.nxh - kxa);
+    }
+    const int tid = threadIdx.x, N = g.ny;
+    // thread tid owns line c = tid mod B and rows j0 + t N/E, t < E (nthr * E == B * N)
+    const int c = tid & (B - 1), j0 = tid >> lgB, NE = N / E;
+    const bool live = c < ncol;
+    {   // every thread issues its E loads before touching shared memory
         C r[E];
+        const C* src = base + (size_t)j0 * g.ldS + c * cs;
 #pragma unroll
-        for (int t = 0; t < E; ++t) {
-            const int idx = tid + t * nthr, c = idx & (B - 1), j = idx >> lgB;
-            r[t] = c < ncol ? base[(size_t)j * g.ldS + c] : mk<T>((T)0, (T)0);
-        }
+        for (int t = 0; t < E; ++t) r[t] = live ? src[(size_t)t * NE * g.ldS] : mk<T>((T)0, (T)0);
 #pragma unroll
-        for (int t = 0; t < E; ++t) {
-            const int idx = tid + t * nthr, c = idx & (B - 1), j = idx >> lgB;
-            s[j * pitch + c] = r[t];
-        }
+        for (int t = 0; t < E; ++t) s[(j0 + t * NE) * pitch + c] = r[t];
     }
     __syncthreads();
     fft_tile<C, E, INV>(s, pitch, lgB, L, tw);
-    for (int idx = tid; idx < B * N; idx += nthr) {
-        const int c = idx & (B - 1), j = idx >> lgB;
-        if (c < ncol) base[(size_t)j * g.ldS + c] = s[j * pitch + c];
+    if (live) {
+        C* dst = base + (size_t)j0 * g.ldS + c * cs;
+#pragma unroll
+        for (int t = 0; t < E; ++t) dst[(size_t)t * NE * g.ldS] = s[(j0 + t * NE) * pitch + c];
     }
 }
 
 // -------------------------------------- periodic z: forward z FFT, divide, inverse z FFT
 // lam tables hold eigenvalue / norm; the (0,0,0) mode is set to zero (zero-mean p).
-template <typename T, int E>
+// TAIL = false: B consecutive kx columns at ky = blockIdx.y; TAIL = true: the Nyquist column
+// kx = M at B consecutive ky (blockIdx.x * B + c).
+template <typename T, int E, bool TAIL>
 __global__ void __launch_bounds__(1024) k_zper(typename cplx<T>::t* __restrict__ S, Geo g, FftLen L,
                                                const typename cplx<T>::t* __restrict__ tw,
                                                const T* __restrict__ lamx, const T* __restrict__ lamy,
@@ -455,42 +487,187 @@ __global__ void __launch_bounds__(1024) k_zper(typename cplx<T>::t* __restrict__
     extern __shared__ __align__(16) unsigned char smraw[];
     C* s = reinterpret_cast<C*>(smraw);
     const int B = 1 << lgB, pitch = B + 1;
-    const int kxa = kx0 + blockIdx.x * B, ky = blockIdx.y;
-    const int ncol = min(B, g.nxh - kxa);
     const size_t zs = (size_t)g.ny * g.ldS;
-    C* base = S + (size_t)ky * g.ldS + kxa;
-    const int tid = threadIdx.x, nthr = blockDim.x, N = g.nz;
-    {   // every thread issues its E loads before touching shared memory (nthr * E == B * N)
+    C* base;
+    size_t cs;
+    int ncol, kxa, ky0;
+    if (TAIL) {
+        ky0 = blockIdx.x * B;
+        kxa = g.M;
+        base = S + (size_t)ky0 * g.ldS + g.M;
+        cs = g.ldS;
+        ncol = min(B, g.ny - ky0);
+    } else {
+        ky0 = blockIdx.y;
+        kxa = kx0 + blockIdx.x * B;
+        base = S + (size_t)ky0 * g.ldS + kxa;
+        cs = 1;
+        ncol = min(B, g.nxh - kxa);
+    }
+    const int tid = threadIdx.x, N = g.nz;
+    const int c = tid & (B - 1), j0 = tid >> lgB, NE = N / E;
+    const bool live = c < ncol;
+    {
         C r[E];
+        const C* src = base + (size_t)j0 * zs + c * cs;
 #pragma unroll
-        for (int t = 0; t < E; ++t) {
-            const int idx = tid + t * nthr, c = idx & (B - 1), k = idx >> lgB;
-            r[t] = c < ncol ? base[k * zs + c] : mk<T>((T)0, (T)0);
-        }
+        for (int t = 0; t < E; ++t) r[t] = live ? src[(size_t)t * NE * zs] : mk<T>((T)0, (T)0);
 #pragma unroll
-        for (int t = 0; t < E; ++t) {
-            const int idx = tid + t * nthr, c = idx & (B - 1), k = idx >> lgB;
-            s[k * pitch + c] = r[t];
-        }
+        for (int t = 0; t < E; ++t) s[(j0 + t * NE) * pitch + c] = r[t];
     }
     __syncthreads();
     fft_tile<C, E, false>(s, pitch, lgB, L, tw);
-    const T lxy0 = __ldg(&lamy[ky]);
-    for (int idx = tid; idx < B * N; idx += nthr) {
-        const int c = idx & (B - 1), k = idx >> lgB;
-        const int kx = min(kxa + c, g.nxh - 1);
-        const T lam = __ldg(&lamx[kx]) + lxy0 + __ldg(&lamz[k]);
-        const T inv = lam != (T)0 ? (T)1 / lam : (T)0;
-        C v = s[k * pitch + c];
-        v.x *= inv;
-        v.y *= inv;
-        s[k * pitch + c] = v;
+    {
+        const int cc = min(c, ncol - 1);
+        const T lxy = TAIL ? __ldg(&lamx[kxa]) + __ldg(&lamy[ky0 + cc]) : __ldg(&lamx[kxa + cc]) + __ldg(&lamy[ky0]);
+#pragma unroll
+        for (int t = 0; t < E; ++t) {
+            const int k = j0 + t * NE;
+            const T lam = lxy + __ldg(&lamz[k]);
+            const T inv = lam != (T)0 ? (T)1 / lam : (T)0;
+            C v = s[k * pitch + c];
+            v.x *= inv;
+            v.y *= inv;
+            s[k * pitch + c] = v;
+        }
     }
     __syncthreads();
     fft_tile<C, E, true>(s, pitch, lgB, L, tw);
-    for (int idx = tid; idx < B * N; idx += nthr) {
-        const int c = idx & (B - 1), k = idx >> lgB;
-        if (c < ncol) base[k * zs + c] = s[k * pitch + c];
+    if (live) {
+        C* dst = base + (size_t)j0 * zs + c * cs;
+#pragma unroll
+        for (int t = 0; t < E; ++t) dst[(size_t)t * NE * zs] = s[(j0 + t * NE) * pitch + c];
+    }
+}
+
+// ------------------------------------- persistent, double-buffered column transforms
+// FP32 column passes (y transform, or periodic z: transform, divide, inverse transform)
+// with a persistent grid: each CTA owns a sequence of tiles (B consecutive kx columns by N
+// rows) and keeps two tile buffers in shared memory.  While the threads transform tile i in
+// place, the next tile streams into the other buffer by cp.async.bulk row copies (B
+// complex = 128 bytes per row, 16-byte aligned) that complete on an mbarrier.  Tile rows are
+// stored with coalesced 128-byte writes.  Every mbarrier wait is bounded: on time-out the
+// CTA records an error and leaves (after a bounded wait for its own copies in flight).
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(unsigned long long* m, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(m)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* m, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(m)), "r"(bytes) : "memory");
+}
+// 3-D tiled TMA load of one box of the spectrum (coordinates x = kx, y = ky, z = k).
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* tm, int x, int y, int z,
+                                            unsigned long long* m) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+        ::"r"(smem_u32(dst)), "l"(reinterpret_cast<unsigned long long>(tm)), "r"(x), "r"(y), "r"(z),
+          "r"(smem_u32(m)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* m, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok) : "r"(smem_u32(m)), "r"(parity) : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* m, unsigned parity) {
+    for (int i = 0; i < (1 << 22); ++i)
+        if (mbar_try_wait(m, parity)) return true;
+    return false;
+}
+
+// KIND 0: y transform (INV picks the direction); KIND 1: periodic z solve.
+template <int KIND, bool INV>
+__global__ void __launch_bounds__(1024, 1) k_cols_pipe(float2* __restrict__ S, const __grid_constant__ CUtensorMap tm,
+                                                       Geo g, FftLen L, const float2* __restrict__ tw,
+                                                       const float* __restrict__ lamx, const float* __restrict__ lamy,
+                                                       const float* __restrict__ lamz, int lgB, int box_rows,
+                                                       int* __restrict__ err) {
+    constexpr int E = 8;
+    typedef float2 C;
+    extern __shared__ __align__(1024) unsigned char smraw[];   // [tile 0][tile 1][2 mbarriers]
+    const int B = 1 << lgB;
+    const int N = KIND == 0 ? g.ny : g.nz;
+    const size_t rs = KIND == 0 ? (size_t)g.ldS : (size_t)g.ny * g.ldS;    // row stride (elements)
+    const int tiles_x = g.M >> lgB;
+    const int ntiles = tiles_x * (KIND == 0 ? g.nz : g.ny);
+    const unsigned tile_bytes = (unsigned)(N * B * sizeof(C));
+    C* buf0 = reinterpret_cast<C*>(smraw);
+    C* buf1 = reinterpret_cast<C*>(smraw + tile_bytes);
+    unsigned long long* mbar = reinterpret_cast<unsigned long long*>(smraw + 2 * (size_t)tile_bytes);
+    const int tid = threadIdx.x;
+    const int c = tid & (B - 1), j0 = tid >> lgB, NE = N / E;
+
+    auto tile_base = [&](int t) -> C* {
+        const int tx = t % tiles_x, ty = t / tiles_x;
+        return KIND == 0 ? S + (size_t)ty * g.ny * g.ldS + (size_t)tx * B : S + (size_t)ty * g.ldS + (size_t)tx * B;
+    };
+    auto issue = [&](int t, int b) {      // one thread: expect the tile's bytes, then TMA its boxes
+        if (tid == 0) {
+            C* dst = b ? buf1 : buf0;
+            const int tx = t % tiles_x, ty = t / tiles_x;
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            mbar_expect_tx(&mbar[b], tile_bytes);
+            for (int r0 = 0; r0 < N; r0 += box_rows) {
+                if (KIND == 0) tma_load_3d(dst + r0 * B, &tm, tx * B, r0, ty, &mbar[b]);
+                else tma_load_3d(dst + r0 * B, &tm, tx * B, ty, r0, &mbar[b]);
+            }
+        }
+    };
+
+    if (smem_u32(smraw) & 127u) {   // TMA box destinations must be 128-byte aligned
+        if (tid == 0) atomicExch(err, 2);
+        return;
+    }
+    if (tid == 0) {
+        mbar_init(&mbar[0], 1);
+        mbar_init(&mbar[1], 1);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    __syncthreads();
+    unsigned parity[2] = {0u, 0u};
+    int t = blockIdx.x;
+    if (t < ntiles) issue(t, 0);
+    bool pending_other = false;
+    for (int it = 0; t < ntiles; ++it, t += gridDim.x) {
+        const int b = it & 1;
+        const int tn = t + gridDim.x;
+        if (tn < ntiles) issue(tn, b ^ 1);
+        pending_other = tn < ntiles;
+        const bool ok = __syncthreads_and(mbar_wait_bounded(&mbar[b], parity[b]));
+        parity[b] ^= 1u;
+        if (!ok) {   // leave only after (bounded) waits for both buffers' copies
+            if (tid == 0) atomicExch(err, 1);
+            mbar_wait_bounded(&mbar[b], parity[b] ^ 1u);
+            if (pending_other) mbar_wait_bounded(&mbar[b ^ 1], parity[b ^ 1]);
+            return;
+        }
+        C* s = b ? buf1 : buf0;
+        if (KIND == 0) {
+            fft_tile<C, E, INV>(s, B, lgB, L, tw);
+        } else {
+            fft_tile<C, E, false>(s, B, lgB, L, tw);
+            const int tx = t % tiles_x, ky = t / tiles_x;
+            const float lxy = __ldg(&lamx[tx * B + c]) + __ldg(&lamy[ky]);
+#pragma unroll
+            for (int q = 0; q < E; ++q) {
+                const int k = j0 + q * NE;
+                const float lam = lxy + __ldg(&lamz[k]);
+                const float inv = lam != 0.f ? 1.f / lam : 0.f;
+                C v = s[k * B + c];
+                v.x *= inv;
+                v.y *= inv;
+                s[k * B + c] = v;
+            }
+            __syncthreads();
+            fft_tile<C, E, true>(s, B, lgB, L, tw);
+        }
+        C* dst = tile_base(t) + (size_t)j0 * rs + c;
+#pragma unroll
+        for (int q = 0; q < E; ++q) dst[(size_t)q * NE * rs] = s[(j0 + q * NE) * B + c];
+        __syncthreads();
     }
 }
 
@@ -603,11 +780,25 @@ __global__ void k_finalize(const double* __restrict__ part, int nblk, DevScalars
 // ------------------------------------------------------------------- host helpers
 int ilog2i(int x) { int l = 0; while ((1 << l) < x) ++l; return l; }
 
+// Largest CTA of the non-pipelined transform kernels: 256 threads by default (measured best
+// on GB300 for the x passes at 512^3); the FLUPS_CTA_THREADS environment variable (256, 512
+// or 1024) overrides it.
+int cta_threads() {
+    static int v = 0;
+    if (!v) {
+        const char* e = getenv("FLUPS_CTA_THREADS");
+        const int q = e ? atoi(e) : 256;
+        v = (q == 512 || q == 1024) ? q : 256;
+    }
+    return v;
+}
+
 // Tile width B (lines per CTA): as wide as possible up to bmax while the CTA has at most
-// 1024 threads and 74 KB of tile (three CTAs per SM).
+// cta_threads() threads and 74 KB of tile (three CTAs per SM by shared memory).
 int pick_lgB(int N, int csize, int E, int bmax, int ncols) {
     int B = bmax;
-    while (B > 1 && ((long)B * N / E > 1024 || (long)N * (B + 1) * csize > 74 * 1024)) B >>= 1;
+    const long tmax = cta_threads();
+    while (B > 1 && ((long)B * N / E > tmax || (long)N * (B + 1) * csize > 74 * 1024)) B >>= 1;
     while (B > 1 && B > ncols) B >>= 1;
     while ((long)B * N < E) B <<= 1;
     return ilog2i(B);
@@ -617,45 +808,91 @@ template <typename K> void allow_smem(K kern) {
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 74 * 1024);
 }
 
-template <typename T> struct Eof { static const int E = sizeof(T) == 4 ? 16 : 8; };
+// Elements per thread: 16 (FP32) or 8 (FP64) complex values; 4 for transforms shorter than that.
+// (The radix sequences use radix 8 only for lengths >= 8, so E >= the largest radix.)
+template <typename T> int e_for(int N) { return N >= 8 ? 8 : 4; }
+template <typename T> struct Ebig { static const int E = 8; };
 
-template <typename T, bool INV>
-void run_ycol(flups_plan P, typename cplx<T>::t* S, const Geo& g) {
+FftLen packed(FftLen L) {
+    L.code = 0ull;
+    for (int st = 0; st < L.nst; ++st) L.code |= (unsigned long long)L.rad[st] << (4 * st);
+    return L;
+}
+
+// Tile of the pipelined kernel: B columns with B * N * 8 bytes <= 64 KB, B <= 16, B <= M.
+int pipe_lgB(int N, int M) {
+    int B = 16;
+    while (B > 1 && ((long)B * N * 8 > 64 * 1024 || B > M)) B >>= 1;
+    return ilog2i(B);
+}
+// The pipelined path needs its tensor map (built with the plan), rows of at least 16 bytes
+// (B >= 2) and at most 1024 threads (B N / 8).
+bool pipe_ok(flups_plan P, int N) {
+    if (!P->tma_ok) return false;
+    const int B = 1 << pipe_lgB(N, P->M);
+    return B >= 2 && (long)B * N / 8 <= 1024 && N >= 8;
+}
+
+template <int KIND, bool INV>
+void run_cols_pipe(flups_plan P, float2* S, const Geo& g, const FftLen& L, const float2* tw) {
+    const int N = KIND == 0 ? g.ny : g.nz;
+    const int lgB = pipe_lgB(N, g.M), B = 1 << lgB;
+    const size_t sm = 2 * (size_t)N * B * sizeof(float2) + 2 * sizeof(unsigned long long);
+    auto kern = k_cols_pipe<KIND, INV>;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    int nsm = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const int ntiles = (g.M / B) * (KIND == 0 ? g.nz : g.ny);
+    const int grid = ntiles < nsm ? ntiles : nsm;
+    kern<<<grid, B * N / 8, sm, P->stream>>>(S, KIND == 0 ? P->tm_y : P->tm_z, g, L, tw, (const float*)P->lamx,
+                                             (const float*)P->lamy, (const float*)P->lamz, lgB, N < 256 ? N : 256,
+                                             &P->sc->err);
+}
+
+template <typename T, int E, bool INV>
+void run_ycol_e(flups_plan P, typename cplx<T>::t* S, const Geo& g) {
     typedef typename cplx<T>::t C;
-    const int E = Eof<T>::E, N = g.ny;
+    const int N = g.ny;
     const int lgB = pick_lgB(N, sizeof(C), E, sizeof(T) == 4 ? 32 : 16, g.M);
     const int B = 1 << lgB;
-    auto kern = k_ycol<T, Eof<T>::E, INV>;
+    const FftLen L = packed(P->ly);
+    auto kern = k_ycol<T, E, INV, false>;
+    auto tail = k_ycol<T, E, INV, true>;
     allow_smem(kern);
+    allow_smem(tail);
     flups_prof_begin(P, sizeof(T) == 4 ? FK_YCOL32 : FK_YCOL64);
     const size_t sm = (size_t)N * (B + 1) * sizeof(C);
-    kern<<<dim3(g.M / B, g.nz), B * N / E, sm, P->stream>>>(S, g, P->ly, (const C*)P->twy, lgB, 0);
-    const int lgT = ilog2i(N >= E ? 1 : E / N);   // the Nyquist column kx = M
+    if (sizeof(T) == 4 && E == 8 && pipe_ok(P, N)) run_cols_pipe<0, INV>(P, (float2*)S, g, L, (const float2*)P->twy);
+    else kern<<<dim3(g.M / B, g.nz), B * N / E, sm, P->stream>>>(S, g, L, (const C*)P->twy, lgB, 0);
+    // the Nyquist column kx = M of every plane, B planes per tile
+    const int lgT = pick_lgB(N, sizeof(C), E, sizeof(T) == 4 ? 32 : 16, g.nz);
     const int BT = 1 << lgT;
-    kern<<<dim3(1, g.nz), BT * N / E, (size_t)N * (BT + 1) * sizeof(C), P->stream>>>(S, g, P->ly, (const C*)P->twy, lgT, g.M);
+    tail<<<dim3((g.nz + BT - 1) / BT, 1), BT * N / E, (size_t)N * (BT + 1) * sizeof(C), P->stream>>>(
+        S, g, L, (const C*)P->twy, lgT, g.M);
     flups_prof_end(P);
     FLUPS_COUNT(P, 2);
 }
 
+template <typename T, bool INV>
+void run_ycol(flups_plan P, typename cplx<T>::t* S, const Geo& g) {
+    const int e = e_for<T>(g.ny);
+    if (e == 4) run_ycol_e<T, 4, INV>(P, S, g);
+    else if (e == 8) run_ycol_e<T, 8, INV>(P, S, g);
+    else run_ycol_e<T, Ebig<T>::E, INV>(P, S, g);
+}
+
+template <typename T, int E>
+void run_zper_e(flups_plan P, typename cplx<T>::t* S, const Geo& g);
+
 template <typename T>
 void run_zsolve(flups_plan P, typename cplx<T>::t* S, const Geo& g) {
     typedef typename cplx<T>::t C;
-    const int E = Eof<T>::E;
     if (!g.walls) {
-        const int N = g.nz;
-        const int lgB = pick_lgB(N, sizeof(C), E, sizeof(T) == 4 ? 32 : 16, g.M);
-        const int B = 1 << lgB;
-        auto kern = k_zper<T, Eof<T>::E>;
-        allow_smem(kern);
-        flups_prof_begin(P, sizeof(T) == 4 ? FK_ZPER32 : FK_ZPER64);
-        kern<<<dim3(g.M / B, g.ny), B * N / E, (size_t)N * (B + 1) * sizeof(C), P->stream>>>(
-            S, g, P->lz, (const C*)P->twz, (const T*)P->lamx, (const T*)P->lamy, (const T*)P->lamz, lgB, 0);
-        const int lgT = ilog2i(N >= E ? 1 : E / N);
-        const int BT = 1 << lgT;
-        kern<<<dim3(1, g.ny), BT * N / E, (size_t)N * (BT + 1) * sizeof(C), P->stream>>>(
-            S, g, P->lz, (const C*)P->twz, (const T*)P->lamx, (const T*)P->lamy, (const T*)P->lamz, lgT, g.M);
-        flups_prof_end(P);
-        FLUPS_COUNT(P, 2);
+        const int e = e_for<T>(g.nz);
+        if (e == 4) run_zper_e<T, 4>(P, S, g);
+        else if (e == 8) run_zper_e<T, 8>(P, S, g);
+        else run_zper_e<T, Ebig<T>::E>(P, S, g);
     } else {
         const int ncols = g.nxh * g.ny;
         flups_prof_begin(P, sizeof(T) == 4 ? FK_ZTRI32 : FK_ZTRI64);
@@ -666,41 +903,86 @@ void run_zsolve(flups_plan P, typename cplx<T>::t* S, const Geo& g) {
     }
 }
 
-template <typename T, int MODE, bool STATS>
-void run_xfwd(flups_plan P, const double* f, const double* p, const Geo& g) {
+template <typename T, int E>
+void run_zper_e(flups_plan P, typename cplx<T>::t* S, const Geo& g) {
     typedef typename cplx<T>::t C;
-    const int E = Eof<T>::E, N = g.M, nrows = g.ny * g.nz;
+    if (!g.walls) {
+        const int N = g.nz;
+        const int lgB = pick_lgB(N, sizeof(C), E, sizeof(T) == 4 ? 32 : 16, g.M);
+        const int B = 1 << lgB;
+        const FftLen L = packed(P->lz);
+        auto kern = k_zper<T, E, false>;
+        auto tail = k_zper<T, E, true>;
+        allow_smem(kern);
+        allow_smem(tail);
+        flups_prof_begin(P, sizeof(T) == 4 ? FK_ZPER32 : FK_ZPER64);
+        if (sizeof(T) == 4 && E == 8 && pipe_ok(P, N))
+            run_cols_pipe<1, false>(P, (float2*)S, g, L, (const float2*)P->twz);
+        else
+            kern<<<dim3(g.M / B, g.ny), B * N / E, (size_t)N * (B + 1) * sizeof(C), P->stream>>>(
+                S, g, L, (const C*)P->twz, (const T*)P->lamx, (const T*)P->lamy, (const T*)P->lamz, lgB, 0);
+        const int lgT = pick_lgB(N, sizeof(C), E, sizeof(T) == 4 ? 32 : 16, g.ny);
+        const int BT = 1 << lgT;
+        tail<<<dim3((g.ny + BT - 1) / BT, 1), BT * N / E, (size_t)N * (BT + 1) * sizeof(C), P->stream>>>(
+            S, g, L, (const C*)P->twz, (const T*)P->lamx, (const T*)P->lamy, (const T*)P->lamz, lgT, g.M);
+        flups_prof_end(P);
+        FLUPS_COUNT(P, 2);
+    }
+}
+
+template <typename T, int E, int MODE, bool STATS>
+void run_xfwd_e(flups_plan P, const double* f, const double* p, const Geo& g) {
+    typedef typename cplx<T>::t C;
+    const int N = g.M, nrows = g.ny * g.nz;
     const int lgB = pick_lgB(N, sizeof(C), E, sizeof(T) == 4 ? 32 : 16, nrows);
     const int B = 1 << lgB;
-    auto kern = k_xfwd<T, Eof<T>::E, MODE, STATS>;
+    auto kern = k_xfwd<T, E, MODE, STATS>;
     allow_smem(kern);
     flups_prof_begin(P, sizeof(T) == 8 ? FK_XFWD64 : (MODE >= 1 ? FK_XFWD_RES32 : FK_XFWD_F32));
     const int nblk = (nrows + B - 1) / B;
     kern<<<nblk, B * N / E, (size_t)N * (B + 1) * sizeof(C), P->stream>>>(
-        f, p, (C*)P->spec, g, P->lx, (const C*)P->twx, (const C*)P->twxr, P->tabs64 + 5 * g.nz, lgB, nrows,
+        f, p, (C*)P->spec, g, packed(P->lx), (const C*)P->twx, (const C*)P->twxr, P->tabs64 + 5 * g.nz, lgB, nrows,
         P->sc, P->part);
+    flups_prof_end(P);
+    FLUPS_COUNT(P, 1);
+}
+
+template <typename T, int MODE, bool STATS>
+void run_xfwd(flups_plan P, const double* f, const double* p, const Geo& g) {
+    const int e = e_for<T>(g.M);
+    if (e == 4) run_xfwd_e<T, 4, MODE, STATS>(P, f, p, g);
+    else if (e == 8) run_xfwd_e<T, 8, MODE, STATS>(P, f, p, g);
+    else run_xfwd_e<T, Ebig<T>::E, MODE, STATS>(P, f, p, g);
+}
+
+template <typename T, int E, int ACC, bool MEAN, bool SUBM>
+void run_xinv_e(flups_plan P, double* p, const Geo& g) {
+    typedef typename cplx<T>::t C;
+    const int N = g.M, nrows = g.ny * g.nz;
+    const int lgB = pick_lgB(N, sizeof(C), E, sizeof(T) == 4 ? 32 : 16, nrows);
+    const int B = 1 << lgB;
+    auto kern = k_xinv<T, E, ACC, MEAN, SUBM>;
+    allow_smem(kern);
+    flups_prof_begin(P, sizeof(T) == 4 ? FK_XINV32 : FK_XINV64);
+    const int nblk = (nrows + B - 1) / B;
+    kern<<<nblk, B * N / E, (size_t)N * (B + 1) * sizeof(C), P->stream>>>(
+        (const C*)P->spec, p, g, packed(P->lx), (const C*)P->twx, (const C*)P->twxr, lgB, nrows, P->sc, P->part);
     flups_prof_end(P);
     FLUPS_COUNT(P, 1);
 }
 
 template <typename T, int ACC, bool MEAN, bool SUBM>
 void run_xinv(flups_plan P, double* p, const Geo& g) {
-    typedef typename cplx<T>::t C;
-    const int E = Eof<T>::E, N = g.M, nrows = g.ny * g.nz;
-    const int lgB = pick_lgB(N, sizeof(C), E, sizeof(T) == 4 ? 32 : 16, nrows);
-    const int B = 1 << lgB;
-    auto kern = k_xinv<T, Eof<T>::E, ACC, MEAN, SUBM>;
-    allow_smem(kern);
-    flups_prof_begin(P, sizeof(T) == 4 ? FK_XINV32 : FK_XINV64);
-    const int nblk = (nrows + B - 1) / B;
-    kern<<<nblk, B * N / E, (size_t)N * (B + 1) * sizeof(C), P->stream>>>(
-        (const C*)P->spec, p, g, P->lx, (const C*)P->twx, (const C*)P->twxr, lgB, nrows, P->sc, P->part);
-    flups_prof_end(P);
-    FLUPS_COUNT(P, 1);
+    const int e = e_for<T>(g.M);
+    if (e == 4) run_xinv_e<T, 4, ACC, MEAN, SUBM>(P, p, g);
+    else if (e == 8) run_xinv_e<T, 8, ACC, MEAN, SUBM>(P, p, g);
+    else run_xinv_e<T, Ebig<T>::E, ACC, MEAN, SUBM>(P, p, g);
 }
 
-int xfwd_blocks(flups_plan P, int csize, int E) {
+// CTAs of the x passes (one partial sum each) for a complex element of csize bytes.
+int xfwd_blocks(flups_plan P, int csize, int /*unused*/) {
     const int nrows = P->ny * P->nz;
+    const int E = P->M >= 8 ? 8 : 4;
     const int lgB = pick_lgB(P->M, csize, E, csize == 8 ? 32 : 16, nrows);
     return (nrows + (1 << lgB) - 1) >> lgB;
 }
@@ -776,10 +1058,13 @@ cudaError_t launch_xinv32(flups_plan P, double* p, int mode) {
     return cudaGetLastError();
 }
 
+int flups_pipe_lgB(int N, int M) { return pipe_lgB(N, M); }
+
 size_t flups_part_blocks_needed(int nx, int ny, int nz) {
     const int M = nx / 2, nrows = ny * nz;
     size_t worst = 0;
-    const int cs[2] = {8, 16}, es[2] = {16, 8};
+    const int cs[2] = {8, 16};
+    const int es[2] = {M >= 8 ? 8 : 4, M >= 8 ? 8 : 4};
     for (int q = 0; q < 2; ++q) {
         const int lgB = pick_lgB(M, cs[q], es[q], cs[q] == 8 ? 32 : 16, nrows);
         const size_t nb = (size_t)((nrows + (1 << lgB) - 1) >> lgB);

@@ -103,6 +103,39 @@ bool build_tables(flups_plan P, const std::vector<double>& dzf, DevAlloc& A) {
     return true;
 }
 
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link to libcuda).
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn encode_tiled() {
+    static EncodeTiledFn fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            fn = (EncodeTiledFn)p;
+        cudaGetLastError();
+    }
+    return fn;
+}
+
+// 3-D tiled map over the FP32 spectrum [nz][ny][ldS] (8-byte complex elements) with box
+// (bx, by, bz); rows of the box land densely in shared memory.
+bool make_spec_map(CUtensorMap* m, void* spec, int ldS, int ny, int nz, int bx, int by, int bz) {
+    EncodeTiledFn fn = encode_tiled();
+    if (!fn) return false;
+    const cuuint64_t dims[3] = {(cuuint64_t)ldS, (cuuint64_t)ny, (cuuint64_t)nz};
+    const cuuint64_t strides[2] = {(cuuint64_t)ldS * 8, (cuuint64_t)ldS * ny * 8};
+    const cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)by, (cuuint32_t)bz};
+    const cuuint32_t es[3] = {1, 1, 1};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_UINT64, 3, spec, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+              CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 flups_status cuda_status(cudaError_t e) {
     if (e == cudaSuccess) return FLUPS_OK;
     if (e == cudaErrorMemoryAllocation) return FLUPS_ENOMEM;
@@ -120,10 +153,16 @@ struct DeviceGuard {
 
 bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 
+// Copies the device scalars to the host; reports (and clears) a device-side wait time-out.
 flups_status sync_scalars(flups_plan P) {
     cudaError_t e = cudaMemcpyAsync(P->sc_host, P->sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, P->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(P->stream);
-    return cuda_status(e);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (P->sc_host->err) {
+        cudaMemsetAsync(&P->sc->err, 0, sizeof(int), P->stream);
+        return FLUPS_ETIMEOUT;
+    }
+    return FLUPS_OK;
 }
 
 }  // namespace
@@ -156,6 +195,7 @@ Geo plan_geo(flups_plan P) {
     g.sx = 1.0 / (P->dx * P->dx); g.sy = 1.0 / (P->dy * P->dy);
     g.idx = 1.0 / P->dx; g.idy = 1.0 / P->dy;
     g.rx = P->nx < 32 ? P->nx : 32;
+    g.lgrx = g.rx == 32 ? 5 : (g.rx == 16 ? 4 : 3);
     g.tnx = P->nx / g.rx;
     g.tny = P->ny / FLUPS_TY;
     g.tnz = (P->nz + FLUPS_KC - 1) / FLUPS_KC;
@@ -181,6 +221,7 @@ const char* flups_status_string(int s) {
         case FLUPS_ENONFINITE: return "FLUPS_ENONFINITE: non-finite or invalid value";
         case FLUPS_ENOCONV: return "FLUPS_ENOCONV: refinement did not converge";
         case FLUPS_ESTATE: return "FLUPS_ESTATE: call order violated";
+        case FLUPS_ETIMEOUT: return "FLUPS_ETIMEOUT: a bounded device-side wait timed out";
         default: return "unknown flups status";
     }
 }
@@ -291,6 +332,12 @@ flups_status flups_plan_create(flups_plan* out, int nx, int ny, int nz, double d
                      (bc == FLUPS_BC_WALLS ? (size_t)P->nxh * ny * nz * (csize / 2) : 0);
     P->density_set = 0;
     P->launches = 0;
+    P->tma_ok = 0;
+    if (prec == FLUPS_FP32_REFINE) {
+        const int By = 1 << flups_pipe_lgB(ny, P->M), Bz = 1 << flups_pipe_lgB(nz, P->M);
+        P->tma_ok = make_spec_map(&P->tm_y, P->spec, P->ldS, ny, nz, By, ny < 256 ? ny : 256, 1) &&
+                    (bc == FLUPS_BC_WALLS || make_spec_map(&P->tm_z, P->spec, P->ldS, ny, nz, Bz, 1, nz < 256 ? nz : 256));
+    }
     P->hbuf = nullptr;
     *out = P;
     return FLUPS_OK;

@@ -11,6 +11,7 @@
 //   tables          FP64/FP32 twiddles, eigenvalues, z coefficients
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <stddef.h>
@@ -28,6 +29,7 @@ struct FftLen {
     int n;
     int nst;
     int rad[FLUPS_MAX_STAGES];
+    unsigned long long code;     // rad[] packed 4 bits per stage (filled by the launchers)
 };
 
 // Device-side scalars written by the reduction kernels.
@@ -43,6 +45,8 @@ struct DevScalars {
     double mean_p;      // volume-weighted mean of the first FP32 iterate p_0
     int    bad_rho;     // nonzero: non-finite, non-positive or out-of-range density seen
     int    pexp;        // largest binary64 exponent field of p written by the last FP32 inverse-x pass
+    int    err;         // nonzero: a bounded device-side wait timed out (the result is invalid)
+    int    pad;
 };
 
 // Geometry and tables handed to kernels by value.
@@ -57,7 +61,7 @@ struct Geo {
     double dx, dy;
     double idx, idy;             // 1/dx, 1/dy
     double sx, sy;               // 1/dx^2, 1/dy^2
-    int rx, tnx, tny, tnz;       // stencil tile width and tile counts
+    int rx, lgrx, tnx, tny, tnz; // stencil tile width (a power of two), its log2, tile counts
     unsigned int* tflags;        // [tnz][tny][tnx] nonzero: the tile needs the p_hat terms
     const double* idzf;          // [nz] 1/dzf_k
     const double* az;            // [nz] Laplacian z sub-diagonal   1/(dzf_k dzc_{k-1}) (0 at k=0 with walls)
@@ -104,6 +108,11 @@ struct flups_plan_s {
     void** allocs;               // every workspace allocation, freed by destroy
     int nallocs;
     unsigned long long launches; // kernels launched on this plan so far
+    // TMA descriptors of the FP32 spectrum [nz][ny][ldS] for the pipelined column passes:
+    // boxes of (B kx, up to 256 ky, 1 k) and (B kx, 1 ky, up to 256 k)
+    alignas(64) CUtensorMap tm_y;
+    alignas(64) CUtensorMap tm_z;
+    int tma_ok;
     // per-kernel timing
     int prof_on, prof_n, prof_cap, prof_open;
     cudaEvent_t* prof_ev;        // 2 * prof_cap events
@@ -137,3 +146,5 @@ cudaError_t launch_xinv32(flups_plan P, double* p, int mode);  // 0: p = FFTx^-1
 cudaError_t launch_residual64_norm(flups_plan P, const double* f, const double* p);
 
 Geo plan_geo(flups_plan P);
+// Tile width (log2) of the pipelined column passes for length N and M = nx/2 columns.
+int flups_pipe_lgB(int N, int M);

@@ -38,11 +38,28 @@ __device__ __forceinline__ bool rho_bad(double r) {
 __global__ void k_rho_minmax(const double* __restrict__ rho, size_t n, long long* __restrict__ part) {
     long long mn = 0x7FFFFFFFFFFFFFFFLL;
     int bad = 0;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-        const double r = __ldg(rho + i);
-        const long long b = __double_as_longlong(r);
+    // four 16-byte loads in flight per thread (n is even: nx is a power of two >= 8)
+    const double2* r2 = reinterpret_cast<const double2*>(rho);
+    const size_t n2 = n / 2, stride = (size_t)gridDim.x * blockDim.x;
+    size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    for (; i + 3 * stride < n2; i += 4 * stride) {
+        double2 v[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) v[q] = __ldg(r2 + i + q * stride);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const long long a = __double_as_longlong(v[q].x), b = __double_as_longlong(v[q].y);
+            mn = a < mn ? a : mn;
+            mn = b < mn ? b : mn;
+            bad |= rho_bad(v[q].x) | rho_bad(v[q].y);
+        }
+    }
+    for (; i < n2; i += stride) {
+        const double2 v = __ldg(r2 + i);
+        const long long a = __double_as_longlong(v.x), b = __double_as_longlong(v.y);
+        mn = a < mn ? a : mn;
         mn = b < mn ? b : mn;
-        bad |= rho_bad(r);
+        bad |= rho_bad(v.x) | rho_bad(v.y);
     }
     __shared__ long long smn[32];
     __shared__ int sbad[32];
@@ -109,11 +126,11 @@ __global__ void __launch_bounds__(256) k_tile_flags(const double* __restrict__ r
     const bool cz0 = bc_ == b0;
     const bool nzx = act && !(cz0 && be == b0), nzy = act && !(cz0 && bn == b0);
     const bool nzz = act && !(cz0 && bt == b0) && !top_wall;
-    const int tx = i / g.rx, ty = j / FLUPS_TY, tz = k / FLUPS_KC;
+    const int tx = i >> g.lgrx, ty = j / FLUPS_TY, tz = k / FLUPS_KC;
     const int txp = (tx + 1 == g.tnx) ? 0 : tx + 1;
     const int typ = (ty + 1 == g.tny) ? 0 : ty + 1;
     const int tzp = (tz + 1 == g.tnz) ? 0 : tz + 1;
-    const bool last_x = act && (i % g.rx == g.rx - 1), last_y = (j % FLUPS_TY) == FLUPS_TY - 1;
+    const bool last_x = act && ((i & (g.rx - 1)) == g.rx - 1), last_y = (j % FLUPS_TY) == FLUPS_TY - 1;
     const bool last_z = (k % FLUPS_KC) == FLUPS_KC - 1 || k == g.nz - 1;
     auto tile = [&](int a, int b, int c) { return (size_t)(c * g.tny + b) * g.tnx + a; };
     if (g.rx == 32) {

@@ -14,7 +14,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libflups.so")
 
-OK, EINVAL, EUNSUPPORTED, ENOMEM, ECUDA, ENONFINITE, ENOCONV, ESTATE = range(8)
+OK, EINVAL, EUNSUPPORTED, ENOMEM, ECUDA, ENONFINITE, ENOCONV, ESTATE, ETIMEOUT = range(9)
 BC = {"periodic": 0, "walls": 1}
 PREC = {"fp64": 0, "fp32_refine": 1}
 HIST = 16

@@ -35,7 +35,7 @@ def test_library_exports_every_declared_symbol(lib):
 
 
 def test_status_strings(lib):
-    for s in range(8):
+    for s in range(9):
         assert flups.status_string(s).startswith("FLUPS_")
     assert "unknown" in flups.status_string(99)
 

@@ -165,8 +165,9 @@ def test_project_host_matches_device_path():
     u, v, w = c.u.copy(), c.v.copy(), c.w.copy()
     p = np.empty_like(u)
     with flups.Plan.for_case(c, "fp32_refine") as plan:
-        info = plan.project_host(u, v, w, c.rho, c.pn, c.pnm1, 2.0, 1.0, c.dt, p, rtol=1e-12)
-    assert info.rel_res <= 1e-12
+        # refinement past the divergence gate, as in test_projection_divergence_free
+        info = plan.project_host(u, v, w, c.rho, c.pn, c.pnm1, 2.0, 1.0, c.dt, p, rtol=1e-13)
+    assert info.rel_res <= 1e-13
     assert np.linalg.norm(p - po) / np.linalg.norm(po) <= 1e-10
     assert np.max(np.abs(u - uo)) <= 1e-10 * np.max(np.abs(uo))
     assert oracle.div_rel(u, v, w, c.u, c.v, c.w, g) <= 1e-12
