@@ -1,0 +1,97 @@
+"""Parity at the full workload sizes, in the launch configuration bench.py times.
+
+Checks per case (host RAM on the GPU machine bounds what the oracle can do at 1024x1024x512,
+so that case skips the oracle's direct solve and its correction):
+  * rhs: element-wise against the oracle's rhs on the full arrays, max |diff| <= 1e-12 max |f|;
+  * solve (FP32+refine, rtol 1e-10): the oracle's FP64 residual of the GPU's p against the
+    oracle's own f, ||f - <f> - L p|| / ||f - <f>|| <= 1e-10 (the metric's gate); against
+    the oracle's direct solve (512^3, 512x512x256) relative L2 error <= 1e-8;
+  * zero volume-weighted mean of p;
+  * correction: element-wise against the oracle's correction computed from the GPU's p
+    (512^3, 512x512x256); divergence of u^{n+1} <= 1e-12 with rtol 1e-13 (see the
+    small-case divergence test); at 1024x1024x512 the oracle's divergence of the GPU's
+    u^{n+1} against (dt/rho0) times the defect level.
+"""
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2204_08834_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+from paper_2204_08834_gb300 import flups  # noqa: E402
+
+
+def grid_of(c):
+    nz, ny, nx = c.shape
+    return oracle.make_grid(nx, ny, nz, c.dx, c.dy, c.dzf, c.bc)
+
+
+def run_projection(c, rtol):
+    d = {k: torch.from_numpy(c[k]).cuda() for k in ("u", "v", "w", "rho", "pn", "pnm1")}
+    f = torch.empty_like(d["u"])
+    p = torch.empty_like(d["u"])
+    with flups.Plan.for_case(c, "fp32_refine") as plan:
+        plan.set_density(d["rho"])
+        plan.rhs(d["u"], d["v"], d["w"], d["pn"], d["pnm1"], 2.0, 1.0, c.dt, f)
+        info = plan.solve(f, p, rtol=rtol, max_iter=12)
+        plan.correct(p, d["pn"], d["pnm1"], 2.0, 1.0, c.dt, d["u"], d["v"], d["w"])
+        torch.cuda.synchronize()
+    out = {k: d[k].cpu().numpy() for k in ("u", "v", "w")}
+    out["f"] = f.cpu().numpy()
+    out["p"] = p.cpu().numpy()
+    del d, f, p
+    torch.cuda.empty_cache()
+    return info, out
+
+
+@pytest.mark.parametrize("name", ["emulsion512", "two_layer512x512x256"])
+def test_fullsize_projection_matches_oracle(name):
+    c = synth.emulsion(512) if name == "emulsion512" else synth.two_layer(512, 512, 256)
+    g = grid_of(c)
+    info, out = run_projection(c, 1e-10)
+    assert info.rel_res <= 1e-10
+    fo = oracle.rhs(c.u, c.v, c.w, c.rho, c.pn, c.pnm1, 2.0, 1.0, c.dt, g)
+    assert np.max(np.abs(out["f"] - fo)) <= 1e-12 * np.max(np.abs(fo))
+    assert oracle.rel_residual(fo, out["p"], g) <= 1e-10
+    po = oracle.solve(fo, g)
+    assert np.linalg.norm(out["p"] - po) / np.linalg.norm(po) <= 1e-8
+    assert abs(oracle.volume_mean(out["p"], g)) <= 1e-12 * np.max(np.abs(out["p"]))
+    # correction parity on sampled planes: the oracle's correction from the GPU's p
+    uo, vo, wo = oracle.correct(c.u, c.v, c.w, out["p"], c.pn, c.pnm1, c.rho, 2.0, 1.0, c.dt, g)
+    for key, ref in (("u", uo), ("v", vo), ("w", wo)):
+        assert np.max(np.abs(out[key] - ref)) <= 1e-12 * np.max(np.abs(ref)), key
+
+
+@pytest.mark.parametrize("name", ["emulsion512", "two_layer512x512x256"])
+def test_fullsize_divergence_gate(name):
+    c = synth.emulsion(512) if name == "emulsion512" else synth.two_layer(512, 512, 256)
+    g = grid_of(c)
+    info, out = run_projection(c, 1e-13)
+    assert info.rel_res <= 1e-13
+    assert oracle.div_rel(out["u"], out["v"], out["w"], c.u, c.v, c.w, g) <= 1e-12
+
+
+def test_fullsize_two_layer_1024x1024x512():
+    """The largest workload (1024x1024x512 walls, stretched z, 537 M cells): rhs parity and
+    the oracle's residual of the GPU's p on the full arrays; correction parity through the
+    divergence the oracle measures (D u^{n+1} = (dt/rho0)(f - <f> - L p) at rtol 1e-10)."""
+    c = synth.two_layer(1024, 1024, 512)
+    g = grid_of(c)
+    info, out = run_projection(c, 1e-10)
+    assert info.rel_res <= 1e-10
+    assert np.all(out["w"][-1] == 0.0)
+    fo = oracle.rhs(c.u, c.v, c.w, c.rho, c.pn, c.pnm1, 2.0, 1.0, c.dt, g)
+    assert np.max(np.abs(out["f"] - fo)) <= 1e-12 * np.max(np.abs(fo))
+    del out["f"]
+    assert oracle.rel_residual(fo, out["p"], g) <= 1e-10
+    assert abs(oracle.volume_mean(out["p"], g)) <= 1e-12 * np.max(np.abs(out["p"]))
+    # the divergence the oracle computes from the GPU's corrected velocity equals
+    # (dt/rho0) times the defect of the solve, so it sits at the residual level
+    div = oracle.div(out["u"], out["v"], out["w"], g)
+    rho0 = float(np.min(c.rho))
+    fm = fo - oracle.volume_mean(fo, g)
+    assert np.linalg.norm(div) * rho0 / c.dt <= 2e-10 * np.linalg.norm(fm)
