@@ -74,8 +74,25 @@ template <bool INV, typename C> __device__ __forceinline__ void dft8(C* v) {
     v[3] = cadd(e3, t3); v[7] = csub(e3, t3);
 }
 
+// 3-point DFT: y0 = a+b+c, y1,2 = a - (b+c)/2 -/+ i (sqrt3/2)(b-c) (forward; signs flip inverse).
+template <bool INV, typename C> __device__ __forceinline__ void dft3(C* v) {
+    typedef decltype(v[0].x) T;
+    const T h = (T)0.86602540378443864676;
+    const C a = v[0], b = v[1], c = v[2];
+    const C sbc = cadd(b, c), dbc = csub(b, c);
+    C m;
+    m.x = a.x - (T)0.5 * sbc.x;
+    m.y = a.y - (T)0.5 * sbc.y;
+    C r;                     // forward: -i h (b - c); inverse: +i h (b - c)
+    if (INV) { r.x = -h * dbc.y; r.y = h * dbc.x; } else { r.x = h * dbc.y; r.y = -h * dbc.x; }
+    v[0] = cadd(a, sbc);
+    v[1] = cadd(m, r);
+    v[2] = csub(m, r);
+}
+
 template <int R, bool INV, typename C> __device__ __forceinline__ void dftR(C* v) {
     if (R == 2) dft2<INV>(v);
+    else if (R == 3) dft3<INV>(v);
     else if (R == 4) dft4<INV>(v[0], v[1], v[2], v[3]);
     else dft8<INV>(v);
 }
@@ -104,7 +121,7 @@ __device__ __forceinline__ void stockham_pass(C* s, int pitch, int lgB, int N, i
 #pragma unroll
     for (int t = 0; t < S; ++t) {
         const int jj = j0 + t * NE;
-        const int k = jj & (Ns - 1);
+        const int k = (Ns & (Ns - 1)) == 0 ? (jj & (Ns - 1)) : jj % Ns;
         if (Ns > 1) {
             // W^{k r} for r = 1..R-1 from one table entry W^k by repeated multiplication
             // (a few ulp in FP32, exact enough for the refined solve; table lookups in FP64)
@@ -135,8 +152,11 @@ __device__ __forceinline__ void fft_tile(C* s, int pitch, int lgB, const FftLen&
     int Ns = 1;
     for (int st = 0; st < L.nst; ++st) {
         const int R = (int)((L.code >> (4 * st)) & 15u);
-        if constexpr (E >= 8) {
+        if constexpr (E % 8 == 0) {
             if (R == 8) { stockham_pass<C, E, 8, INV>(s, pitch, lgB, L.n, Ns, tw); Ns *= R; continue; }
+        }
+        if constexpr (E % 3 == 0) {
+            if (R == 3) { stockham_pass<C, E, 3, INV>(s, pitch, lgB, L.n, Ns, tw); Ns *= R; continue; }
         }
         if (R == 4) stockham_pass<C, E, 4, INV>(s, pitch, lgB, L.n, Ns, tw);
         else stockham_pass<C, E, 2, INV>(s, pitch, lgB, L.n, Ns, tw);
@@ -242,9 +262,7 @@ __global__ void __launch_bounds__(1024) k_xfwd(const double* __restrict__ f, con
     typedef typename cplx<T>::t C;
     extern __shared__ __align__(16) unsigned char smraw[];
     C* s = reinterpret_cast<C*>(smraw);
-    const int B = 1 << lgB, pitch = B + 1, M = g.M, Mm = M - 1;
-    int lgM = 0;
-    while ((1 << lgM) < M) ++lgM;
+    const int B = 1 << lgB, pitch = B + 1, M = g.M;
     const int row0 = blockIdx.x * B, tid = threadIdx.x, nthr = blockDim.x;
     const int nx = g.nx;
     double accw = 0.0;
@@ -259,8 +277,8 @@ __global__ void __launch_bounds__(1024) k_xfwd(const double* __restrict__ f, con
         if (pe_ >= 2047) cfix = __longlong_as_double(0x7FF8000000000000LL);           // NaN: p not finite
         else if (pe_ - 57 >= 1) cfix = __hiloint2double((pe_ - 57) << 20, 0) * g.sx;   // 2^(pexp-1080) / h^2
     }
-    for (int idx = tid; idx < (B << lgM); idx += nthr) {
-        const int c = idx >> lgM, n = idx & Mm;
+    for (int idx = tid; idx < B * M; idx += nthr) {
+        const int c = idx / M, n = idx - c * M;
         const int row = row0 + c;
         C z = mk<T>((T)0, (T)0);
         if (row < nrows) {
@@ -278,9 +296,9 @@ __global__ void __launch_bounds__(1024) k_xfwd(const double* __restrict__ f, con
                 const int x0 = 2 * n;
                 const double* pr = p + (size_t)row * nx;
                 const double2 pc = __ldg(reinterpret_cast<const double2*>(pr) + n);
-                const double pw = __ldg(pr + ((x0 - 1) & (nx - 1)));
-                const double pe = __ldg(pr + ((x0 + 2) & (nx - 1)));
-                const int jm = (j - 1) & (g.ny - 1), jp = (j + 1) & (g.ny - 1);
+                const double pw = __ldg(pr + (wrapm(x0 - 1, nx)));
+                const double pe = __ldg(pr + (wrapm(x0 + 2, nx)));
+                const int jm = wrapm(j - 1, g.ny), jp = wrapm(j + 1, g.ny);
                 int km, kp;
                 if (g.walls) { km = k > 0 ? k - 1 : 0; kp = k < g.nz - 1 ? k + 1 : g.nz - 1; }
                 else { km = (k - 1 + g.nz) % g.nz; kp = (k + 1) % g.nz; }
@@ -304,9 +322,9 @@ __global__ void __launch_bounds__(1024) k_xfwd(const double* __restrict__ f, con
                 const int x0 = 2 * n;
                 const double* pr = p + (size_t)row * nx;
                 const double2 pc = __ldg(reinterpret_cast<const double2*>(pr) + n);
-                const double pw = __ldg(pr + ((x0 - 1) & (nx - 1)));
-                const double pe = __ldg(pr + ((x0 + 2) & (nx - 1)));
-                const int jm = (j - 1) & (g.ny - 1), jp = (j + 1) & (g.ny - 1);
+                const double pw = __ldg(pr + (wrapm(x0 - 1, nx)));
+                const double pe = __ldg(pr + (wrapm(x0 + 2, nx)));
+                const int jm = wrapm(j - 1, g.ny), jp = wrapm(j + 1, g.ny);
                 int km, kp;
                 if (g.walls) { km = k > 0 ? k - 1 : 0; kp = k < g.nz - 1 ? k + 1 : g.nz - 1; }
                 else { km = (k - 1 + g.nz) % g.nz; kp = (k + 1) % g.nz; }
@@ -342,7 +360,7 @@ __global__ void __launch_bounds__(1024) k_xfwd(const double* __restrict__ f, con
         const int row = row0 + c;
         if (row >= nrows) continue;
         const C zk = s[k * pitch + c];
-        const C zm = s[((M - k) & Mm) * pitch + c];
+        const C zm = s[(k == 0 ? 0 : M - k) * pitch + c];
         const T ax = (zk.x + zm.x) * (T)0.5, ay = (zk.y - zm.y) * (T)0.5;
         const T bxx = (zk.y + zm.y) * (T)0.5, byy = (zm.x - zk.x) * (T)0.5;
         const C w = __ldg(&twr[k]);
@@ -366,9 +384,7 @@ __global__ void __launch_bounds__(1024) k_xinv(const typename cplx<T>::t* __rest
     typedef typename cplx<T>::t C;
     extern __shared__ __align__(16) unsigned char smraw[];
     C* s = reinterpret_cast<C*>(smraw);
-    const int B = 1 << lgB, pitch = B + 1, M = g.M, Mm = M - 1;
-    int lgM = 0;
-    while ((1 << lgM) < M) ++lgM;
+    const int B = 1 << lgB, pitch = B + 1, M = g.M;
     const int row0 = blockIdx.x * B, tid = threadIdx.x, nthr = blockDim.x;
     const int H = M / 2 + 1;
     // Z_k = A_k + i B_k, Z_{M-k} = conj(A_k) + i conj(B_k) with A_k = (X_k + conj X_{M-k})/2,
@@ -397,8 +413,8 @@ __global__ void __launch_bounds__(1024) k_xinv(const typename cplx<T>::t* __rest
     int emax = 0;       // largest binary64 exponent field written (FP32 mode: scale of the next defect)
     T msub = (T)0;
     if (SUBM) msub = (T)sc->mean_p;
-    for (int idx = tid; idx < (B << lgM); idx += nthr) {
-        const int c = idx >> lgM, n = idx & Mm;
+    for (int idx = tid; idx < B * M; idx += nthr) {
+        const int c = idx / M, n = idx - c * M;
         const int row = row0 + c;
         if (row >= nrows) continue;
         C z = s[n * pitch + c];
@@ -451,7 +467,7 @@ __global__ void __launch_bounds__(1024) k_ycol(typename cplx<T>::t* __restrict__
         const int kxa = kx0 + blockIdx.x * B;
         base = S + (size_t)blockIdx.y * plane + kxa;
         cs = 1;
-        ncol = min(B, g.nxh - kxa);
+        ncol = min(B, g.M - kxa);   // kx = M is the TAIL launch's
     }
     const int tid = threadIdx.x, N = g.ny;
     // thread tid owns line c = tid mod B and rows j0 + t N/E, t < E (nthr * E == B * N)
@@ -502,7 +518,7 @@ __global__ void __launch_bounds__(1024) k_zper(typename cplx<T>::t* __restrict__
         kxa = kx0 + blockIdx.x * B;
         base = S + (size_t)ky0 * g.ldS + kxa;
         cs = 1;
-        ncol = min(B, g.nxh - kxa);
+        ncol = min(B, g.M - kxa);   // kx = M is the TAIL launch's
     }
     const int tid = threadIdx.x, N = g.nz;
     const int c = tid & (B - 1), j0 = tid >> lgB, NE = N / E;
@@ -810,7 +826,7 @@ template <typename K> void allow_smem(K kern) {
 
 // Elements per thread: 16 (FP32) or 8 (FP64) complex values; 4 for transforms shorter than that.
 // (The radix sequences use radix 8 only for lengths >= 8, so E >= the largest radix.)
-template <typename T> int e_for(int N) { return N >= 8 ? 8 : 4; }
+template <typename T> int e_for(int N) { return N % 3 == 0 ? 12 : (N >= 8 ? 8 : 4); }
 template <typename T> struct Ebig { static const int E = 8; };
 
 FftLen packed(FftLen L) {
@@ -828,9 +844,9 @@ int pipe_lgB(int N, int M) {
 // The pipelined path needs its tensor map (built with the plan), rows of at least 16 bytes
 // (B >= 2) and at most 1024 threads (B N / 8).
 bool pipe_ok(flups_plan P, int N) {
-    if (!P->tma_ok) return false;
+    if (!P->tma_ok || (N & (N - 1)) != 0) return false;
     const int B = 1 << pipe_lgB(N, P->M);
-    return B >= 2 && (long)B * N / 8 <= 1024 && N >= 8;
+    return B >= 2 && P->M % B == 0 && (long)B * N / 8 <= 1024 && N >= 8;
 }
 
 template <int KIND, bool INV>
@@ -864,7 +880,7 @@ void run_ycol_e(flups_plan P, typename cplx<T>::t* S, const Geo& g) {
     flups_prof_begin(P, sizeof(T) == 4 ? FK_YCOL32 : FK_YCOL64);
     const size_t sm = (size_t)N * (B + 1) * sizeof(C);
     if (sizeof(T) == 4 && E == 8 && pipe_ok(P, N)) run_cols_pipe<0, INV>(P, (float2*)S, g, L, (const float2*)P->twy);
-    else kern<<<dim3(g.M / B, g.nz), B * N / E, sm, P->stream>>>(S, g, L, (const C*)P->twy, lgB, 0);
+    else kern<<<dim3((g.M + B - 1) / B, g.nz), B * N / E, sm, P->stream>>>(S, g, L, (const C*)P->twy, lgB, 0);
     // the Nyquist column kx = M of every plane, B planes per tile
     const int lgT = pick_lgB(N, sizeof(C), E, sizeof(T) == 4 ? 32 : 16, g.nz);
     const int BT = 1 << lgT;
@@ -879,6 +895,7 @@ void run_ycol(flups_plan P, typename cplx<T>::t* S, const Geo& g) {
     const int e = e_for<T>(g.ny);
     if (e == 4) run_ycol_e<T, 4, INV>(P, S, g);
     else if (e == 8) run_ycol_e<T, 8, INV>(P, S, g);
+    else if (e == 12) run_ycol_e<T, 12, INV>(P, S, g);
     else run_ycol_e<T, Ebig<T>::E, INV>(P, S, g);
 }
 
@@ -892,6 +909,7 @@ void run_zsolve(flups_plan P, typename cplx<T>::t* S, const Geo& g) {
         const int e = e_for<T>(g.nz);
         if (e == 4) run_zper_e<T, 4>(P, S, g);
         else if (e == 8) run_zper_e<T, 8>(P, S, g);
+        else if (e == 12) run_zper_e<T, 12>(P, S, g);
         else run_zper_e<T, Ebig<T>::E>(P, S, g);
     } else {
         const int ncols = g.nxh * g.ny;
@@ -919,7 +937,7 @@ void run_zper_e(flups_plan P, typename cplx<T>::t* S, const Geo& g) {
         if (sizeof(T) == 4 && E == 8 && pipe_ok(P, N))
             run_cols_pipe<1, false>(P, (float2*)S, g, L, (const float2*)P->twz);
         else
-            kern<<<dim3(g.M / B, g.ny), B * N / E, (size_t)N * (B + 1) * sizeof(C), P->stream>>>(
+            kern<<<dim3((g.M + B - 1) / B, g.ny), B * N / E, (size_t)N * (B + 1) * sizeof(C), P->stream>>>(
                 S, g, L, (const C*)P->twz, (const T*)P->lamx, (const T*)P->lamy, (const T*)P->lamz, lgB, 0);
         const int lgT = pick_lgB(N, sizeof(C), E, sizeof(T) == 4 ? 32 : 16, g.ny);
         const int BT = 1 << lgT;
@@ -952,6 +970,7 @@ void run_xfwd(flups_plan P, const double* f, const double* p, const Geo& g) {
     const int e = e_for<T>(g.M);
     if (e == 4) run_xfwd_e<T, 4, MODE, STATS>(P, f, p, g);
     else if (e == 8) run_xfwd_e<T, 8, MODE, STATS>(P, f, p, g);
+    else if (e == 12) run_xfwd_e<T, 12, MODE, STATS>(P, f, p, g);
     else run_xfwd_e<T, Ebig<T>::E, MODE, STATS>(P, f, p, g);
 }
 
@@ -976,13 +995,14 @@ void run_xinv(flups_plan P, double* p, const Geo& g) {
     const int e = e_for<T>(g.M);
     if (e == 4) run_xinv_e<T, 4, ACC, MEAN, SUBM>(P, p, g);
     else if (e == 8) run_xinv_e<T, 8, ACC, MEAN, SUBM>(P, p, g);
+    else if (e == 12) run_xinv_e<T, 12, ACC, MEAN, SUBM>(P, p, g);
     else run_xinv_e<T, Ebig<T>::E, ACC, MEAN, SUBM>(P, p, g);
 }
 
 // CTAs of the x passes (one partial sum each) for a complex element of csize bytes.
 int xfwd_blocks(flups_plan P, int csize, int /*unused*/) {
     const int nrows = P->ny * P->nz;
-    const int E = P->M >= 8 ? 8 : 4;
+    const int E = P->M % 3 == 0 ? 12 : (P->M >= 8 ? 8 : 4);
     const int lgB = pick_lgB(P->M, csize, E, csize == 8 ? 32 : 16, nrows);
     return (nrows + (1 << lgB) - 1) >> lgB;
 }
@@ -1064,7 +1084,8 @@ size_t flups_part_blocks_needed(int nx, int ny, int nz) {
     const int M = nx / 2, nrows = ny * nz;
     size_t worst = 0;
     const int cs[2] = {8, 16};
-    const int es[2] = {M >= 8 ? 8 : 4, M >= 8 ? 8 : 4};
+    const int e1 = M % 3 == 0 ? 12 : (M >= 8 ? 8 : 4);
+    const int es[2] = {e1, e1};
     for (int q = 0; q < 2; ++q) {
         const int lgB = pick_lgB(M, cs[q], es[q], cs[q] == 8 ? 32 : 16, nrows);
         const size_t nb = (size_t)((nrows + (1 << lgB) - 1) >> lgB);

@@ -13,14 +13,26 @@ size_t flups_part_blocks_needed(int nx, int ny, int nz);
 namespace {
 
 bool pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
+// 2^a or 3 * 2^a
+bool smooth23(int n) { return pow2(n) || (n % 3 == 0 && pow2(n / 3)); }
 
-// Radix sequence for n = 2^m: as many radix-8 passes as possible, then a 4 (or 4, 4 / 2).
+// Radix sequence.  n = 2^m: as many radix-8 passes as possible, then a 4 (or 4, 4 / 2).
+// n = 3 * 2^m: radix-4 passes, a 2 if m is odd, then the 3 (every radix divides the 12
+// elements per thread that such lengths use).
 bool make_len(int n, FftLen* L) {
-    if (!pow2(n)) return false;
-    int m = 0;
-    while ((1 << m) < n) ++m;
+    if (!smooth23(n)) return false;
     L->n = n;
     L->nst = 0;
+    if (n % 3 == 0) {
+        int m = 0;
+        while ((3 << m) < n) ++m;
+        for (int i = 0; i < m / 2; ++i) L->rad[L->nst++] = 4;
+        if (m % 2) L->rad[L->nst++] = 2;
+        L->rad[L->nst++] = 3;
+        return L->nst <= FLUPS_MAX_STAGES;
+    }
+    int m = 0;
+    while ((1 << m) < n) ++m;
     int q = m / 3, r = m % 3;
     if (r == 1 && q >= 1) { q -= 1; r = 4; }
     for (int i = 0; i < q; ++i) L->rad[L->nst++] = 8;
@@ -28,6 +40,12 @@ bool make_len(int n, FftLen* L) {
     else if (r == 4) { L->rad[L->nst++] = 4; L->rad[L->nst++] = 4; }
     else if (r == 1) L->rad[L->nst++] = 2;
     return L->nst <= FLUPS_MAX_STAGES;
+}
+
+// Sizes the kernels support: 2^a >= 8, or 3 * 2^a >= 24 and a multiple of 8 (x and y).
+bool size_ok(int n, int lo) {
+    if (pow2(n)) return n >= lo;
+    return n % 3 == 0 && pow2(n / 3) && n >= 24 && n % 8 == 0;
 }
 
 // -4 sin^2(pi k / n) / h^2: the eigenvalues (2 cos(2 pi k/n) - 2)/h^2 without cancellation.
@@ -194,7 +212,8 @@ Geo plan_geo(flups_plan P) {
     g.dx = P->dx; g.dy = P->dy;
     g.sx = 1.0 / (P->dx * P->dx); g.sy = 1.0 / (P->dy * P->dy);
     g.idx = 1.0 / P->dx; g.idy = 1.0 / P->dy;
-    g.rx = P->nx < 32 ? P->nx : 32;
+    g.rx = 32;                                   // largest power of two <= 32 dividing nx
+    while (P->nx % g.rx) g.rx >>= 1;
     g.lgrx = g.rx == 32 ? 5 : (g.rx == 16 ? 4 : 3);
     g.tnx = P->nx / g.rx;
     g.tny = P->ny / FLUPS_TY;
@@ -234,8 +253,8 @@ flups_status flups_plan_create(flups_plan* out, int nx, int ny, int nz, double d
     if (bc != FLUPS_BC_PERIODIC && bc != FLUPS_BC_WALLS) return FLUPS_EINVAL;
     if (prec != FLUPS_FP64 && prec != FLUPS_FP32_REFINE) return FLUPS_EINVAL;
     if (nx <= 0 || ny <= 0 || nz <= 0) return FLUPS_EINVAL;
-    if (!pow2(nx) || !pow2(ny) || nx < 8 || ny < 8 || nx > 4096 || ny > 4096) return FLUPS_EUNSUPPORTED;
-    if (bc == FLUPS_BC_PERIODIC && (!pow2(nz) || nz < 8 || nz > 4096)) return FLUPS_EUNSUPPORTED;
+    if (!size_ok(nx, 8) || !size_ok(ny, 8) || nx > 4096 || ny > 4096) return FLUPS_EUNSUPPORTED;
+    if (bc == FLUPS_BC_PERIODIC && (!size_ok(nz, 8) || nz > 4096)) return FLUPS_EUNSUPPORTED;
     if (bc == FLUPS_BC_WALLS && (nz < 2 || nz > 8192)) return FLUPS_EUNSUPPORTED;
     std::vector<double> dz(dzf, dzf + nz);
     double sum = 0.0;
@@ -277,7 +296,8 @@ flups_status flups_plan_create(flups_plan* out, int nx, int ny, int nz, double d
     P->by = (double*)A.get(P->npts * sizeof(double));
     P->bz = (double*)A.get(P->npts * sizeof(double));
     {
-        const int rx = nx < 32 ? nx : 32;
+        int rx = 32;
+        while (nx % rx) rx >>= 1;
         P->tflags = (unsigned int*)A.get((size_t)(nx / rx) * (ny / FLUPS_TY) * ((nz + FLUPS_KC - 1) / FLUPS_KC) *
                                          sizeof(unsigned int));
     }

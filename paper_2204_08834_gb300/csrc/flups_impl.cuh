@@ -20,11 +20,14 @@
 
 #define FLUPS_MAX_STAGES 14
 
+// v mod n for v in [-n, 2n): the periodic wrap of a neighbour index (any n, not only 2^k).
+__device__ __forceinline__ int wrapm(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
+
 template <typename T> struct cplx;
 template <> struct cplx<float> { typedef float2 t; };
 template <> struct cplx<double> { typedef double2 t; };
 
-// One 1-D transform length and its radix sequence (each radix 2, 4 or 8).
+// One 1-D transform length and its radix sequence (each radix 2, 3, 4 or 8).
 struct FftLen {
     int n;
     int nst;

@@ -118,8 +118,8 @@ __global__ void __launch_bounds__(256) k_tile_flags(const double* __restrict__ r
     if (act) {
         const size_t idx = ((size_t)k * g.ny + j) * g.nx + i;
         bc_ = __double_as_longlong(__ldg(rho + idx));
-        be = __double_as_longlong(__ldg(rho + ((size_t)k * g.ny + j) * g.nx + ((i + 1) & (g.nx - 1))));
-        bn = __double_as_longlong(__ldg(rho + ((size_t)k * g.ny + ((j + 1) & (g.ny - 1))) * g.nx + i));
+        be = __double_as_longlong(__ldg(rho + ((size_t)k * g.ny + j) * g.nx + (wrapm(i + 1, g.nx))));
+        bn = __double_as_longlong(__ldg(rho + ((size_t)k * g.ny + (wrapm(j + 1, g.ny))) * g.nx + i));
         const int kp = g.walls ? (k + 1 < g.nz ? k + 1 : k) : (k + 1 == g.nz ? 0 : k + 1);
         bt = __double_as_longlong(__ldg(rho + ((size_t)kp * g.ny + j) * g.nx + i));
     }
@@ -187,11 +187,11 @@ __global__ void __launch_bounds__(RX * FLUPS_TY) k_face_coeffs(const double* __r
         const double iz = __ldg(g.idzc + k);
         for (int e = tid; e < W * Hh; e += nthr) {
             const int bb = e / W, aa = e - bb * W;
-            const int i = (i0 - 1 + aa) & (g.nx - 1), j = (j0 - 1 + bb) & (g.ny - 1);
+            const int i = wrapm(i0 - 1 + aa, g.nx), j = wrapm(j0 - 1 + bb, g.ny);
             const size_t idx = ((size_t)k * g.ny + j) * g.nx + i;
             const long long bc_ = __double_as_longlong(__ldg(rho + idx));
-            const long long be = __double_as_longlong(__ldg(rho + ((size_t)k * g.ny + j) * g.nx + ((i + 1) & (g.nx - 1))));
-            const long long bn = __double_as_longlong(__ldg(rho + ((size_t)k * g.ny + ((j + 1) & (g.ny - 1))) * g.nx + i));
+            const long long be = __double_as_longlong(__ldg(rho + ((size_t)k * g.ny + j) * g.nx + (wrapm(i + 1, g.nx))));
+            const long long bn = __double_as_longlong(__ldg(rho + ((size_t)k * g.ny + (wrapm(j + 1, g.ny))) * g.nx + i));
             const long long bt = __double_as_longlong(__ldg(rho + ((size_t)kp * g.ny + j) * g.nx + i));
             const bool cz0 = bc_ == b0;
             const bool need_x = !(cz0 && be == b0), need_y = !(cz0 && bn == b0);
@@ -230,7 +230,7 @@ __global__ void __launch_bounds__(RX * TY) k_rhs(const double* __restrict__ u, c
     const double rdt = sc->rho0 * inv_dt;          // rho0 / dt
     const double kx = rdt * g.idx, ky = rdt * g.idy;
     const int i = i0 + tx, j = j0 + ty;
-    const int im = (i - 1) & (nx - 1), jm = (j - 1) & (ny - 1);
+    const int im = wrapm(i - 1, nx), jm = wrapm(j - 1, ny);
 
     if (g.tflags[(blockIdx.z * g.tny + blockIdx.y) * g.tnx + blockIdx.x] == 0) {
         double wlo = 0.0;
@@ -257,7 +257,7 @@ __global__ void __launch_bounds__(RX * TY) k_rhs(const double* __restrict__ u, c
     auto fill = [&](int k, int buf) {
         for (int e = tid; e < (TY + 2) * (RX + 2); e += nthr) {
             const int bb = e / (RX + 2), aa = e - bb * (RX + 2);
-            const int jj = (j0 - 1 + bb) & (ny - 1), ii = (i0 - 1 + aa) & (nx - 1);
+            const int jj = wrapm(j0 - 1 + bb, ny), ii = wrapm(i0 - 1 + aa, nx);
             Pt[buf][bb][aa] = pt_at(((size_t)k * ny + jj) * nx + ii);
         }
     };
@@ -277,12 +277,12 @@ __global__ void __launch_bounds__(RX * TY) k_rhs(const double* __restrict__ u, c
         __syncthreads();
         for (int e = tid; e < TY * (RX + 1); e += nthr) {       // x faces i0-1/2 .. i0+RX-1/2
             const int b = e / (RX + 1), a = e - b * (RX + 1);
-            const size_t q = ((size_t)k * ny + (j0 + b)) * nx + ((i0 - 1 + a) & (nx - 1));
+            const size_t q = ((size_t)k * ny + (j0 + b)) * nx + (wrapm(i0 - 1 + a, nx));
             QX[b][a] = fma(__ldg(bx + q), Pt[cur][b + 1][a + 1] - Pt[cur][b + 1][a], __ldg(u + q));
         }
         for (int e = tid; e < (TY + 1) * RX; e += nthr) {       // y faces j0-1/2 .. j0+TY-1/2
             const int b = e / RX, a = e - b * RX;
-            const size_t q = ((size_t)k * ny + ((j0 - 1 + b) & (ny - 1))) * nx + (i0 + a);
+            const size_t q = ((size_t)k * ny + (wrapm(j0 - 1 + b, ny))) * nx + (i0 + a);
             QY[b][a] = fma(__ldg(by + q), Pt[cur][b + 1][a + 1] - Pt[cur][b][a + 1], __ldg(v + q));
         }
         const size_t qc = ((size_t)k * ny + j) * nx + i;
@@ -314,7 +314,7 @@ __global__ void __launch_bounds__(RX * TY) k_correct(const double* __restrict__ 
     const double s = dt * sc->inv_rho0;
     const double ax = s * g.idx, ay = s * g.idy;
     const int i = i0 + tx, j = j0 + ty;
-    const int ie = (i + 1) & (nx - 1), jn = (j + 1) & (ny - 1);
+    const int ie = wrapm(i + 1, nx), jn = wrapm(j + 1, ny);
 
     if (g.tflags[(blockIdx.z * g.tny + blockIdx.y) * g.tnx + blockIdx.x] == 0) {
         for (int k = kb; k < ke; ++k) {
@@ -345,7 +345,7 @@ __global__ void __launch_bounds__(RX * TY) k_correct(const double* __restrict__ 
     auto fill = [&](int k, int buf) {
         for (int e = tid; e < (TY + 1) * (RX + 1); e += nthr) {
             const int bb = e / (RX + 1), aa = e - bb * (RX + 1);
-            const int jj = (j0 + bb) & (ny - 1), ii = (i0 + aa) & (nx - 1);
+            const int jj = wrapm(j0 + bb, ny), ii = wrapm(i0 + aa, nx);
             Pt[buf][bb][aa] = pt_at(((size_t)k * ny + jj) * nx + ii);
         }
     };
@@ -395,9 +395,9 @@ __global__ void __launch_bounds__(256) k_res64(const double* __restrict__ f, con
         } else {
             const size_t row = rr * g.nx;
             const double pc = p[q];
-            const double pw = p[row + ((i - 1) & (g.nx - 1))], pe = p[row + ((i + 1) & (g.nx - 1))];
-            const double ps = p[((size_t)k * g.ny + ((j - 1) & (g.ny - 1))) * g.nx + i];
-            const double pnn = p[((size_t)k * g.ny + ((j + 1) & (g.ny - 1))) * g.nx + i];
+            const double pw = p[row + (wrapm(i - 1, g.nx))], pe = p[row + (wrapm(i + 1, g.nx))];
+            const double ps = p[((size_t)k * g.ny + (wrapm(j - 1, g.ny))) * g.nx + i];
+            const double pnn = p[((size_t)k * g.ny + (wrapm(j + 1, g.ny))) * g.nx + i];
             int km, kp;
             if (g.walls) { km = k > 0 ? k - 1 : 0; kp = k < g.nz - 1 ? k + 1 : g.nz - 1; }
             else { km = (k - 1 + g.nz) % g.nz; kp = (k + 1) % g.nz; }
@@ -498,8 +498,8 @@ cudaError_t launch_set_density(flups_plan P, const double* rho, double rho0) {
 cudaError_t launch_rhs(flups_plan P, const double* u, const double* v, const double* w, const double* pn,
                        const double* pnm1, double c1, double c2, double dt, double* f) {
     const Geo g = plan_geo(P);
-    if (g.nx >= 32) run_rhs<32>(P, u, v, w, pn, pnm1, c1, c2, dt, f, g);
-    else if (g.nx == 16) run_rhs<16>(P, u, v, w, pn, pnm1, c1, c2, dt, f, g);
+    if (g.rx == 32) run_rhs<32>(P, u, v, w, pn, pnm1, c1, c2, dt, f, g);
+    else if (g.rx == 16) run_rhs<16>(P, u, v, w, pn, pnm1, c1, c2, dt, f, g);
     else run_rhs<8>(P, u, v, w, pn, pnm1, c1, c2, dt, f, g);
     return cudaGetLastError();
 }
@@ -507,8 +507,8 @@ cudaError_t launch_rhs(flups_plan P, const double* u, const double* v, const dou
 cudaError_t launch_correct(flups_plan P, const double* p, const double* pn, const double* pnm1, double c1,
                            double c2, double dt, double* u, double* v, double* w) {
     const Geo g = plan_geo(P);
-    if (g.nx >= 32) run_correct<32>(P, p, pn, pnm1, c1, c2, dt, u, v, w, g);
-    else if (g.nx == 16) run_correct<16>(P, p, pn, pnm1, c1, c2, dt, u, v, w, g);
+    if (g.rx == 32) run_correct<32>(P, p, pn, pnm1, c1, c2, dt, u, v, w, g);
+    else if (g.rx == 16) run_correct<16>(P, p, pn, pnm1, c1, c2, dt, u, v, w, g);
     else run_correct<8>(P, p, pn, pnm1, c1, c2, dt, u, v, w, g);
     return cudaGetLastError();
 }

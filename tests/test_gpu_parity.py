@@ -52,6 +52,10 @@ CASES = {
     # one spacing in x, y and z with walls: the exact fixed-point defect applies
     "walls_cubic_32x16x24": lambda: synth.random_fields(32, 16, 24, "walls", False, lx=1.0, ly=0.5, lz=0.75,
                                                         seed=96),
+    # lengths 3 * 2^a (radix-3 passes): the 48 and 96 members of the ensemble
+    "per_48x24x96": lambda: synth.random_fields(48, 24, 96, "periodic", seed=97),
+    "walls_str_96x48x30": lambda: synth.random_fields(96, 48, 30, "walls", True, seed=98),
+    "emulsion48": lambda: synth.emulsion(48, ndrops=6, rmin_cells=2.0, rmax_cells=5.0),
 }
 _cache = {}
 
