@@ -148,6 +148,22 @@ flups_status flups_solve(flups_plan plan, const double* f, double* p, double rto
                          flups_info* info);
 
 /*
+ * flups_solve_graphable - the FP32-refine solve of flups_solve as a fixed sequence of
+ * stream-ordered kernels with no host synchronisation, so that it can be captured into a
+ * CUDA graph (the refinement of Sec. 3.3.1's solver is not in the paper; this form serves
+ * batched ensembles).  At most max_iter FP32 solves run; after each FP64 defect norm a
+ * device-side flag ends the sequence early (the remaining kernels return at once) once
+ * ||f - <f> - L p|| <= rtol ||f - <f>||, so p equals what flups_solve returns.
+ * Plan must be FLUPS_FP32_REFINE.  Read the outcome with flups_solve_result.
+ */
+flups_status flups_solve_graphable(flups_plan plan, const double* f, double* p, double rtol, int max_iter);
+
+/* flups_solve_result - synchronises the plan's stream and reports the last defect norm of
+ * the previous flups_solve_graphable (info->rel_res; info->iters = its max_iter);
+ * FLUPS_ENOCONV if it is above rtol. */
+flups_status flups_solve_result(flups_plan plan, double rtol, flups_info* info);
+
+/*
  * flups_correct - velocity correction (Eqs. us_predic + corr):
  *   u^{n+1} = u** - (dt/rho0) [G p - (1 - rho0/rho_f) G p_hat], in place on u, v, w.
  *   p        : DEVICE solution of flups_solve; p_n, p_nm1, c1, c2 as in flups_rhs.
@@ -191,8 +207,44 @@ flups_status flups_project_host(flups_plan plan, double* u, double* v, double* w
 flups_status flups_solve_fp64_noalloc(int nx, int ny, int nz, double dx, double dy, const double* dzf,
                                       int bc, const double* f, double* p, void* stream);
 
+/*
+ * Batched ensembles of independent FP32-refine solves of mixed sizes in one CUDA graph
+ * launch (no counterpart in the paper, which solves one field per time step; the solver
+ * of every member is the Sec. 3.3.1 method of flups_solve).
+ *
+ * flups_batch_create - n members, member m with grid nx[m] x ny[m] x nz[m], spacings dx[m],
+ *   dy[m], HOST cell widths dzf[m] (nz[m] values) and boundary condition bc[m], each with its
+ *   own plan (as flups_plan_create with FLUPS_FP32_REFINE).  nstreams (1..32) worker streams
+ *   run members concurrently; stream is the origin stream the graph launches on.  With
+ *   autotune != 0, every distinct member size is timed once for the transform CTA thread cap
+ *   (256/512/1024) and the radix sequence of its power-of-two transforms, and the fastest
+ *   pair is kept (flups_batch_member_tuning reports it).
+ * flups_batch_solve - solves L p[m] = f[m] - <f[m]> for every member (DEVICE pointers) with
+ *   at most max_iter FP32 solves each and early exit at rtol (flups_solve_graphable).  The
+ *   first call, and any call whose pointers, rtol or max_iter differ from the previous one,
+ *   captures the members' kernels into a CUDA graph; later calls replay it.  With info !=
+ *   NULL (HOST array of n) it synchronises and reports each member's last defect norm;
+ *   FLUPS_ENOCONV if some member is above rtol.  Without info it does not synchronise.
+ */
+typedef struct flups_batch_s* flups_batch;
+flups_status flups_batch_create(flups_batch* out, int n, const int* nx, const int* ny, const int* nz,
+                                const double* dx, const double* dy, const double* const* dzf, const int* bc,
+                                int nstreams, int autotune, void* stream);
+flups_status flups_batch_solve(flups_batch batch, const double* const* f, double* const* p, double rtol,
+                               int max_iter, flups_info* info);
+flups_status flups_batch_destroy(flups_batch batch);
+/* flups_batch_graph_kernels - kernels in the captured graph (one flups_batch_solve replay). */
+unsigned long long flups_batch_graph_kernels(flups_batch batch);
+/* flups_batch_member_tuning - CTA thread cap and radix variant (0: radix 8 first, 1: radix 4)
+ * chosen for member m. */
+flups_status flups_batch_member_tuning(flups_batch batch, int m, int* cta_threads, int* radix_variant);
+
 /* flups_status_string - static, human-readable name of a status code. */
 const char* flups_status_string(int status);
+
+/* flups_last_cuda_error - name of the last CUDA error that made a call of this thread
+ * return FLUPS_ECUDA or FLUPS_ENOMEM ("cudaSuccess" if none); static string. */
+const char* flups_last_cuda_error(void);
 
 #ifdef __cplusplus
 }

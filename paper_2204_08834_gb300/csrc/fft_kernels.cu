@@ -259,6 +259,7 @@ __global__ void __launch_bounds__(1024) k_xfwd(const double* __restrict__ f, con
                                                const typename cplx<T>::t* __restrict__ twr,
                                                const double* __restrict__ dd, int lgB, int nrows,
                                                const DevScalars* __restrict__ sc, double* __restrict__ part) {
+    if (g.skip && *g.skip) return;   // graph-capturable solve: this member already converged
     typedef typename cplx<T>::t C;
     extern __shared__ __align__(16) unsigned char smraw[];
     C* s = reinterpret_cast<C*>(smraw);
@@ -381,6 +382,7 @@ __global__ void __launch_bounds__(1024) k_xinv(const typename cplx<T>::t* __rest
                                                Geo g, FftLen L, const typename cplx<T>::t* __restrict__ tw,
                                                const typename cplx<T>::t* __restrict__ twr, int lgB, int nrows,
                                                DevScalars* __restrict__ sc, double* __restrict__ part) {
+    if (g.skip && *g.skip) return;   // graph-capturable solve: this member already converged
     typedef typename cplx<T>::t C;
     extern __shared__ __align__(16) unsigned char smraw[];
     C* s = reinterpret_cast<C*>(smraw);
@@ -451,6 +453,7 @@ __global__ void __launch_bounds__(1024) k_xinv(const typename cplx<T>::t* __rest
 template <typename T, int E, bool INV, bool TAIL>
 __global__ void __launch_bounds__(1024) k_ycol(typename cplx<T>::t* __restrict__ S, Geo g, FftLen L,
                                                const typename cplx<T>::t* __restrict__ tw, int lgB, int kx0) {
+    if (g.skip && *g.skip) return;   // graph-capturable solve: this member already converged
     typedef typename cplx<T>::t C;
     extern __shared__ __align__(16) unsigned char smraw[];
     C* s = reinterpret_cast<C*>(smraw);
@@ -499,6 +502,7 @@ __global__ void __launch_bounds__(1024) k_zper(typename cplx<T>::t* __restrict__
                                                const typename cplx<T>::t* __restrict__ tw,
                                                const T* __restrict__ lamx, const T* __restrict__ lamy,
                                                const T* __restrict__ lamz, int lgB, int kx0) {
+    if (g.skip && *g.skip) return;   // graph-capturable solve: this member already converged
     typedef typename cplx<T>::t C;
     extern __shared__ __align__(16) unsigned char smraw[];
     C* s = reinterpret_cast<C*>(smraw);
@@ -601,6 +605,7 @@ __global__ void __launch_bounds__(1024, 1) k_cols_pipe(float2* __restrict__ S, c
                                                        const float* __restrict__ lamx, const float* __restrict__ lamy,
                                                        const float* __restrict__ lamz, int lgB, int box_rows,
                                                        int* __restrict__ err) {
+    if (g.skip && *g.skip) return;   // graph-capturable solve: this member already converged
     constexpr int E = 8;
     typedef float2 C;
     extern __shared__ __align__(1024) unsigned char smraw[];   // [tile 0][tile 1][2 mbarriers]
@@ -698,6 +703,7 @@ template <typename T>
 __global__ void __launch_bounds__(128) k_ztri(typename cplx<T>::t* __restrict__ S, T* __restrict__ cps, Geo g,
                                               const T* __restrict__ lamx, const T* __restrict__ lamy,
                                               const T* __restrict__ tri) {
+    if (g.skip && *g.skip) return;   // graph-capturable solve: this member already converged
     typedef typename cplx<T>::t C;
     const int ncols = g.nxh * g.ny;
     const int col = blockIdx.x * blockDim.x + threadIdx.x;
@@ -752,7 +758,8 @@ __global__ void __launch_bounds__(128) k_ztri(typename cplx<T>::t* __restrict__ 
 
 // Deterministic final reduction of the per-block partial sums (one block).
 __global__ void k_finalize(const double* __restrict__ part, int nblk, DevScalars* sc, int what, double nrm_w,
-                           double npts) {
+                           double npts, int fixed, double thr2) {
+    if (fixed && sc->done) return;   // fixed-iteration solve: the member converged earlier
     __shared__ double red[3][32];
     double a = 0.0, b = 0.0, c = 0.0;
     for (int i = threadIdx.x; i < nblk; i += blockDim.x) {
@@ -786,6 +793,7 @@ __global__ void k_finalize(const double* __restrict__ part, int nblk, DevScalars
                 sc->f2 = b - 2.0 * m * c + npts * m * m;
             } else if (what == 1) {   // b = sum r^2
                 sc->r2 = b;
+                if (fixed && b <= thr2 * sc->f2) sc->done = 1;
             } else {                  // a = sum dzf p
                 sc->mean_p = a * nrm_w;
             }
@@ -811,9 +819,9 @@ int cta_threads() {
 
 // Tile width B (lines per CTA): as wide as possible up to bmax while the CTA has at most
 // cta_threads() threads and 74 KB of tile (three CTAs per SM by shared memory).
-int pick_lgB(int N, int csize, int E, int bmax, int ncols) {
+int pick_lgB(int N, int csize, int E, int bmax, int ncols, int cap) {
     int B = bmax;
-    const long tmax = cta_threads();
+    const long tmax = cap > 0 ? cap : cta_threads();
     while (B > 1 && ((long)B * N / E > tmax || (long)N * (B + 1) * csize > 74 * 1024)) B >>= 1;
     while (B > 1 && B > ncols) B >>= 1;
     while ((long)B * N < E) B <<= 1;
@@ -870,7 +878,7 @@ template <typename T, int E, bool INV>
 void run_ycol_e(flups_plan P, typename cplx<T>::t* S, const Geo& g) {
     typedef typename cplx<T>::t C;
     const int N = g.ny;
-    const int lgB = pick_lgB(N, sizeof(C), E, sizeof(T) == 4 ? 32 : 16, g.M);
+    const int lgB = pick_lgB(N, sizeof(C), E, sizeof(T) == 4 ? 32 : 16, g.M, g.cta);
     const int B = 1 << lgB;
     const FftLen L = packed(P->ly);
     auto kern = k_ycol<T, E, INV, false>;
@@ -882,7 +890,7 @@ void run_ycol_e(flups_plan P, typename cplx<T>::t* S, const Geo& g) {
     if (sizeof(T) == 4 && E == 8 && pipe_ok(P, N)) run_cols_pipe<0, INV>(P, (float2*)S, g, L, (const float2*)P->twy);
     else kern<<<dim3((g.M + B - 1) / B, g.nz), B * N / E, sm, P->stream>>>(S, g, L, (const C*)P->twy, lgB, 0);
     // the Nyquist column kx = M of every plane, B planes per tile
-    const int lgT = pick_lgB(N, sizeof(C), E, sizeof(T) == 4 ? 32 : 16, g.nz);
+    const int lgT = pick_lgB(N, sizeof(C), E, sizeof(T) == 4 ? 32 : 16, g.nz, g.cta);
     const int BT = 1 << lgT;
     tail<<<dim3((g.nz + BT - 1) / BT, 1), BT * N / E, (size_t)N * (BT + 1) * sizeof(C), P->stream>>>(
         S, g, L, (const C*)P->twy, lgT, g.M);
@@ -926,7 +934,7 @@ void run_zper_e(flups_plan P, typename cplx<T>::t* S, const Geo& g) {
     typedef typename cplx<T>::t C;
     if (!g.walls) {
         const int N = g.nz;
-        const int lgB = pick_lgB(N, sizeof(C), E, sizeof(T) == 4 ? 32 : 16, g.M);
+        const int lgB = pick_lgB(N, sizeof(C), E, sizeof(T) == 4 ? 32 : 16, g.M, g.cta);
         const int B = 1 << lgB;
         const FftLen L = packed(P->lz);
         auto kern = k_zper<T, E, false>;
@@ -939,7 +947,7 @@ void run_zper_e(flups_plan P, typename cplx<T>::t* S, const Geo& g) {
         else
             kern<<<dim3((g.M + B - 1) / B, g.ny), B * N / E, (size_t)N * (B + 1) * sizeof(C), P->stream>>>(
                 S, g, L, (const C*)P->twz, (const T*)P->lamx, (const T*)P->lamy, (const T*)P->lamz, lgB, 0);
-        const int lgT = pick_lgB(N, sizeof(C), E, sizeof(T) == 4 ? 32 : 16, g.ny);
+        const int lgT = pick_lgB(N, sizeof(C), E, sizeof(T) == 4 ? 32 : 16, g.ny, g.cta);
         const int BT = 1 << lgT;
         tail<<<dim3((g.ny + BT - 1) / BT, 1), BT * N / E, (size_t)N * (BT + 1) * sizeof(C), P->stream>>>(
             S, g, L, (const C*)P->twz, (const T*)P->lamx, (const T*)P->lamy, (const T*)P->lamz, lgT, g.M);
@@ -952,7 +960,7 @@ template <typename T, int E, int MODE, bool STATS>
 void run_xfwd_e(flups_plan P, const double* f, const double* p, const Geo& g) {
     typedef typename cplx<T>::t C;
     const int N = g.M, nrows = g.ny * g.nz;
-    const int lgB = pick_lgB(N, sizeof(C), E, sizeof(T) == 4 ? 32 : 16, nrows);
+    const int lgB = pick_lgB(N, sizeof(C), E, sizeof(T) == 4 ? 32 : 16, nrows, g.cta);
     const int B = 1 << lgB;
     auto kern = k_xfwd<T, E, MODE, STATS>;
     allow_smem(kern);
@@ -978,7 +986,7 @@ template <typename T, int E, int ACC, bool MEAN, bool SUBM>
 void run_xinv_e(flups_plan P, double* p, const Geo& g) {
     typedef typename cplx<T>::t C;
     const int N = g.M, nrows = g.ny * g.nz;
-    const int lgB = pick_lgB(N, sizeof(C), E, sizeof(T) == 4 ? 32 : 16, nrows);
+    const int lgB = pick_lgB(N, sizeof(C), E, sizeof(T) == 4 ? 32 : 16, nrows, g.cta);
     const int B = 1 << lgB;
     auto kern = k_xinv<T, E, ACC, MEAN, SUBM>;
     allow_smem(kern);
@@ -1003,7 +1011,7 @@ void run_xinv(flups_plan P, double* p, const Geo& g) {
 int xfwd_blocks(flups_plan P, int csize, int /*unused*/) {
     const int nrows = P->ny * P->nz;
     const int E = P->M % 3 == 0 ? 12 : (P->M >= 8 ? 8 : 4);
-    const int lgB = pick_lgB(P->M, csize, E, csize == 8 ? 32 : 16, nrows);
+    const int lgB = pick_lgB(P->M, csize, E, csize == 8 ? 32 : 16, nrows, P->cta_cap);
     return (nrows + (1 << lgB) - 1) >> lgB;
 }
 
@@ -1030,7 +1038,7 @@ cudaError_t launch_finalize_f(flups_plan P) {
     const int nblk = xfwd_blocks(P, 8, 16);
     flups_prof_begin(P, FK_FINALIZE);
     k_finalize<<<1, 1024, 0, P->stream>>>(P->part, nblk, P->sc, 0, 1.0 / ((double)P->nx * P->ny * P->sum_dzf),
-                                          (double)P->npts);
+                                          (double)P->npts, 0, 0.0);
     flups_prof_end(P);
     FLUPS_COUNT(P, 1);
     return cudaGetLastError();
@@ -1046,7 +1054,7 @@ cudaError_t launch_xfwd32_residual(flups_plan P, const double* f, const double* 
 cudaError_t launch_finalize_r(flups_plan P) {
     const int nblk = xfwd_blocks(P, 8, 16);
     flups_prof_begin(P, FK_FINALIZE);
-    k_finalize<<<1, 1024, 0, P->stream>>>(P->part, nblk, P->sc, 1, 0.0, 0.0);
+    k_finalize<<<1, 1024, 0, P->stream>>>(P->part, nblk, P->sc, 1, 0.0, 0.0, 0, 0.0);
     flups_prof_end(P);
     FLUPS_COUNT(P, 1);
     return cudaGetLastError();
@@ -1067,7 +1075,7 @@ cudaError_t launch_xinv32(flups_plan P, double* p, int mode) {
         run_xinv<float, 0, true, false>(P, p, g);
         const int nblk = xfwd_blocks(P, 8, 16);
         flups_prof_begin(P, FK_FINALIZE);
-        k_finalize<<<1, 1024, 0, P->stream>>>(P->part, nblk, P->sc, 2, 1.0 / ((double)P->nx * P->ny * P->sum_dzf), 0.0);
+        k_finalize<<<1, 1024, 0, P->stream>>>(P->part, nblk, P->sc, 2, 1.0 / ((double)P->nx * P->ny * P->sum_dzf), 0.0, 0, 0.0);
         flups_prof_end(P);
         FLUPS_COUNT(P, 1);
     } else if (mode == 1) {                // p += delta - <p_0>
@@ -1080,6 +1088,8 @@ cudaError_t launch_xinv32(flups_plan P, double* p, int mode) {
 
 int flups_pipe_lgB(int N, int M) { return pipe_lgB(N, M); }
 
+int flups_default_cta() { return cta_threads(); }
+
 size_t flups_part_blocks_needed(int nx, int ny, int nz) {
     const int M = nx / 2, nrows = ny * nz;
     size_t worst = 0;
@@ -1087,9 +1097,41 @@ size_t flups_part_blocks_needed(int nx, int ny, int nz) {
     const int e1 = M % 3 == 0 ? 12 : (M >= 8 ? 8 : 4);
     const int es[2] = {e1, e1};
     for (int q = 0; q < 2; ++q) {
-        const int lgB = pick_lgB(M, cs[q], es[q], cs[q] == 8 ? 32 : 16, nrows);
-        const size_t nb = (size_t)((nrows + (1 << lgB) - 1) >> lgB);
-        if (nb > worst) worst = nb;
+        for (int cap = 256; cap <= 1024; cap *= 2) {     // every CTA cap a plan may use
+            const int lgB = pick_lgB(M, cs[q], es[q], cs[q] == 8 ? 32 : 16, nrows, cap);
+            const size_t nb = (size_t)((nrows + (1 << lgB) - 1) >> lgB);
+            if (nb > worst) worst = nb;
+        }
     }
     return worst;
+}
+
+// FP32+refine with a fixed kernel sequence and no host synchronisation: the first FP32
+// solve, then (max_iter - 1) rounds of {FP64 defect, norm test, FP32 solve of the defect,
+// FP64 update}, then a last defect norm.  Once a norm test passes, the device flag
+// sc->done makes every later kernel of the sequence return at once, so the result equals
+// the host-driven loop's.  Suitable for stream capture into a CUDA graph.
+cudaError_t launch_solve32_fixed(flups_plan P, const double* f, double* p, double rtol, int max_iter) {
+    const double thr2 = rtol * rtol;
+    const double nrm_w = 1.0 / ((double)P->nx * P->ny * P->sum_dzf);
+    cudaMemsetAsync(&P->sc->done, 0, sizeof(int), P->stream);
+    P->skip_ptr = nullptr;
+    launch_xfwd32_from_f(P, f);
+    launch_finalize_f(P);
+    launch_yz_solve32(P);
+    launch_xinv32(P, p, 0);
+    P->skip_ptr = &P->sc->done;
+    for (int it = 1; it <= max_iter; ++it) {
+        launch_xfwd32_residual(P, f, p);
+        {
+            const int nblk = xfwd_blocks(P, 8, 16);
+            k_finalize<<<1, 1024, 0, P->stream>>>(P->part, nblk, P->sc, 1, nrm_w, 0.0, 1, thr2);
+            FLUPS_COUNT(P, 1);
+        }
+        if (it == max_iter) break;
+        launch_yz_solve32(P);
+        launch_xinv32(P, p, it == 1 ? 1 : 2);
+    }
+    P->skip_ptr = nullptr;
+    return cudaGetLastError();
 }

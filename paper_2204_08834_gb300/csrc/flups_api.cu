@@ -156,6 +156,7 @@ bool make_spec_map(CUtensorMap* m, void* spec, int ldS, int ny, int nz, int bx, 
 
 flups_status cuda_status(cudaError_t e) {
     if (e == cudaSuccess) return FLUPS_OK;
+    flups_note_cuda_error(e);
     if (e == cudaErrorMemoryAllocation) return FLUPS_ENOMEM;
     return FLUPS_ECUDA;
 }
@@ -204,6 +205,9 @@ void flups_prof_end(flups_plan P) {
     if (cudaEventRecord(P->prof_ev[2 * P->prof_n + 1], P->stream) == cudaSuccess) P->prof_n++;
 }
 
+static thread_local cudaError_t g_last_cuda_error = cudaSuccess;
+void flups_note_cuda_error(cudaError_t e) { g_last_cuda_error = e; }
+
 Geo plan_geo(flups_plan P) {
     Geo g;
     g.nx = P->nx; g.ny = P->ny; g.nz = P->nz; g.M = P->M; g.nxh = P->nxh; g.ldS = P->ldS;
@@ -219,6 +223,8 @@ Geo plan_geo(flups_plan P) {
     g.tny = P->ny / FLUPS_TY;
     g.tnz = (P->nz + FLUPS_KC - 1) / FLUPS_KC;
     g.tflags = P->tflags;
+    g.skip = P->skip_ptr;
+    g.cta = P->cta_cap;
     const int nz = P->nz;
     g.idzf = P->tabs64;
     g.az = P->tabs64 + nz;
@@ -229,6 +235,8 @@ Geo plan_geo(flups_plan P) {
 }
 
 extern "C" {
+
+const char* flups_last_cuda_error(void) { return cudaGetErrorName(g_last_cuda_error); }
 
 const char* flups_status_string(int s) {
     switch (s) {
@@ -353,6 +361,8 @@ flups_status flups_plan_create(flups_plan* out, int nx, int ny, int nz, double d
     P->density_set = 0;
     P->launches = 0;
     P->tma_ok = 0;
+    P->skip_ptr = nullptr;
+    P->cta_cap = flups_default_cta();
     if (prec == FLUPS_FP32_REFINE) {
         const int By = 1 << flups_pipe_lgB(ny, P->M), Bz = 1 << flups_pipe_lgB(nz, P->M);
         P->tma_ok = make_spec_map(&P->tm_y, P->spec, P->ldS, ny, nz, By, ny < 256 ? ny : 256, 1) &&
@@ -530,6 +540,32 @@ flups_status flups_solve(flups_plan P, const double* f, double* p, double rtol, 
         if (st == FLUPS_OK) st = cuda_status(launch_xinv32(P, p, it == 1 ? 1 : 2));
         if (st != FLUPS_OK) return st;
     }
+}
+
+flups_status flups_solve_graphable(flups_plan P, const double* f, double* p, double rtol, int max_iter) {
+    if (!P || !f || !p || f == p || !aligned16(f) || !aligned16(p)) return FLUPS_EINVAL;
+    if (P->prec != FLUPS_FP32_REFINE) return FLUPS_EINVAL;
+    if (max_iter < 1 || max_iter > 64 || !(rtol >= 0.0)) return FLUPS_EINVAL;
+    DeviceGuard dg(P->dev);
+    P->last_max_iter = max_iter;
+    return cuda_status(launch_solve32_fixed(P, f, p, rtol, max_iter));
+}
+
+flups_status flups_solve_result(flups_plan P, double rtol, flups_info* info) {
+    if (!P || !info) return FLUPS_EINVAL;
+    DeviceGuard dg(P->dev);
+    const flups_status st = sync_scalars(P);
+    info->iters = 0;
+    info->rel_res = -1.0;
+    for (int q = 0; q < FLUPS_HIST; ++q) info->rel_res_hist[q] = -1.0;
+    if (st != FLUPS_OK) return st;
+    const double f2 = P->sc_host->f2;
+    const double rr = f2 > 0.0 ? std::sqrt(P->sc_host->r2 / f2) : (P->sc_host->r2 > 0.0 ? INFINITY : 0.0);
+    info->rel_res = rr;
+    info->rel_res_hist[0] = rr;
+    info->iters = P->last_max_iter;
+    if (!std::isfinite(rr)) return FLUPS_ENONFINITE;
+    return rr <= rtol ? FLUPS_OK : FLUPS_ENOCONV;
 }
 
 flups_status flups_project_host(flups_plan P, double* u, double* v, double* w, const double* rho,

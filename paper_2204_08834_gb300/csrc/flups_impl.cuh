@@ -49,7 +49,7 @@ struct DevScalars {
     int    bad_rho;     // nonzero: non-finite, non-positive or out-of-range density seen
     int    pexp;        // largest binary64 exponent field of p written by the last FP32 inverse-x pass
     int    err;         // nonzero: a bounded device-side wait timed out (the result is invalid)
-    int    pad;
+    int    done;        // graph-capturable solve: the defect reached rtol, later iterations skip
 };
 
 // Geometry and tables handed to kernels by value.
@@ -66,6 +66,8 @@ struct Geo {
     double sx, sy;               // 1/dx^2, 1/dy^2
     int rx, lgrx, tnx, tny, tnz; // stencil tile width (a power of two), its log2, tile counts
     unsigned int* tflags;        // [tnz][tny][tnx] nonzero: the tile needs the p_hat terms
+    const int* skip;             // refinement kernels return at once when *skip != 0 (may be null)
+    int cta;                     // thread cap of the transform CTAs (0: library default)
     const double* idzf;          // [nz] 1/dzf_k
     const double* az;            // [nz] Laplacian z sub-diagonal   1/(dzf_k dzc_{k-1}) (0 at k=0 with walls)
     const double* cz;            // [nz] Laplacian z super-diagonal 1/(dzf_k dzc_k) (0 at k=nz-1 with walls)
@@ -116,6 +118,9 @@ struct flups_plan_s {
     alignas(64) CUtensorMap tm_y;
     alignas(64) CUtensorMap tm_z;
     int tma_ok;
+    int* skip_ptr;               // passed to kernels as Geo::skip (set by the fixed-iteration solve)
+    int cta_cap;                 // thread cap of the transform CTAs (autotuned per size in batches)
+    int last_max_iter;           // max_iter of the last graph-capturable solve
     // per-kernel timing
     int prof_on, prof_n, prof_cap, prof_open;
     cudaEvent_t* prof_ev;        // 2 * prof_cap events
@@ -145,9 +150,15 @@ cudaError_t launch_xfwd32_residual(flups_plan P, const double* f, const double* 
 cudaError_t launch_finalize_r(flups_plan P);
 cudaError_t launch_yz_solve32(flups_plan P);                                 // y fwd, z solve, y inv on S
 cudaError_t launch_xinv32(flups_plan P, double* p, int mode);  // 0: p = FFTx^-1(S) (+ mean); 1: p += . - mean; 2: p += .
+// FP32+refine solve with a fixed sequence of kernels and no host synchronisation (graph
+// capturable): after max_iter FP32 solves at most, the last defect norm is in P->sc.
+cudaError_t launch_solve32_fixed(flups_plan P, const double* f, double* p, double rtol, int max_iter);
+int flups_default_cta();
 // FP64 residual (report only)
 cudaError_t launch_residual64_norm(flups_plan P, const double* f, const double* p);
 
 Geo plan_geo(flups_plan P);
+// Remembers the last CUDA error the library observed (flups_last_cuda_error).
+void flups_note_cuda_error(cudaError_t e);
 // Tile width (log2) of the pipelined column passes for length N and M = nx/2 columns.
 int flups_pipe_lgB(int N, int M);

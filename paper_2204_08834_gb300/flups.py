@@ -25,6 +25,9 @@ SYMBOLS = [
     "flups_set_density", "flups_get_rho0", "flups_rhs", "flups_solve", "flups_correct",
     "flups_project_host", "flups_status_string", "flups_solve_fp64_noalloc",
     "flups_set_profiling", "flups_profile_read", "flups_kernel_name",
+    "flups_solve_graphable", "flups_solve_result",
+    "flups_batch_create", "flups_batch_solve", "flups_batch_destroy", "flups_batch_graph_kernels",
+    "flups_batch_member_tuning", "flups_last_cuda_error",
 ]
 NKERNELS = 18
 
@@ -32,7 +35,10 @@ NKERNELS = 18
 class FlupsError(RuntimeError):
     def __init__(self, status, where):
         self.status = status
-        super().__init__(f"{where}: {status_string(status)}")
+        extra = ""
+        if status in (ECUDA, ENOMEM):
+            extra = f" ({lib().flups_last_cuda_error().decode()})"
+        super().__init__(f"{where}: {status_string(status)}{extra}")
 
 
 class Info(ctypes.Structure):
@@ -69,13 +75,25 @@ def lib():
         L.flups_solve_fp64_noalloc.argtypes = [I, I, I, D, D, ctypes.POINTER(D), I, V, V, V]
         L.flups_set_profiling.argtypes = [P, I]
         L.flups_profile_read.argtypes = [P, ctypes.POINTER(D), ctypes.POINTER(ctypes.c_longlong)]
+        L.flups_solve_graphable.argtypes = [P, V, V, D, I]
+        L.flups_solve_result.argtypes = [P, D, ctypes.POINTER(Info)]
+        IP = ctypes.POINTER(ctypes.c_int)
+        DP = ctypes.POINTER(ctypes.c_double)
+        L.flups_batch_create.argtypes = [ctypes.POINTER(P), I, IP, IP, IP, DP, DP, ctypes.POINTER(DP), IP, I, I, V]
+        L.flups_batch_solve.argtypes = [P, ctypes.POINTER(V), ctypes.POINTER(V), D, I, ctypes.POINTER(Info)]
+        L.flups_batch_destroy.argtypes = [P]
+        L.flups_batch_graph_kernels.argtypes = [P]
+        L.flups_batch_graph_kernels.restype = ctypes.c_ulonglong
+        L.flups_batch_member_tuning.argtypes = [P, I, IP, IP]
+        L.flups_last_cuda_error.argtypes = []
+        L.flups_last_cuda_error.restype = ctypes.c_char_p
         L.flups_kernel_name.argtypes = [I]
         L.flups_kernel_name.restype = ctypes.c_char_p
         L.flups_status_string.argtypes = [I]
         L.flups_status_string.restype = ctypes.c_char_p
         for name in SYMBOLS:
             if name not in ("flups_status_string", "flups_workspace_bytes", "flups_launch_count",
-                            "flups_kernel_name"):
+                            "flups_kernel_name", "flups_batch_graph_kernels", "flups_last_cuda_error"):
                 getattr(L, name).restype = I
         _lib = L
     return _lib
@@ -191,6 +209,17 @@ class Plan:
             _check(st, "flups_solve")
         return inf if check else (st, inf)
 
+    def solve_graphable(self, f, p, rtol=1e-10, max_iter=4):
+        _check(lib().flups_solve_graphable(self._h, ptr(f), ptr(p), float(rtol), int(max_iter)),
+               "flups_solve_graphable")
+
+    def solve_result(self, rtol=1e-10, check=True):
+        inf = Info()
+        st = lib().flups_solve_result(self._h, float(rtol), ctypes.byref(inf))
+        if check:
+            _check(st, "flups_solve_result")
+        return inf if check else (st, inf)
+
     def correct(self, p, pn, pnm1, c1, c2, dt, u, v, w):
         _check(lib().flups_correct(self._h, ptr(p), ptr(pn), ptr(pnm1), float(c1), float(c2), float(dt),
                                    ptr(u), ptr(v), ptr(w)), "flups_correct")
@@ -220,3 +249,64 @@ def solve_fp64_noalloc(nx, ny, nz, dx, dy, dzf, bc, f, p, stream=None, check=Tru
     if check:
         _check(st, "flups_solve_fp64_noalloc")
     return st
+
+
+class Batch:
+    """Ensemble of independent FP32-refine solves in one CUDA graph launch (flups_batch_*).
+
+    members: sequence of (nx, ny, nz, dx, dy, dzf, bc) with dzf a scalar or nz widths.
+    """
+
+    def __init__(self, members, nstreams=8, autotune=True, stream=None):
+        n = len(members)
+        self.n = n
+        self.shapes = [(m[2], m[1], m[0]) for m in members]
+        ci = ctypes.c_int * n
+        cd = ctypes.c_double * n
+        self._dz = [np.ascontiguousarray(np.broadcast_to(np.asarray(m[5], dtype=np.float64), (m[2],)))
+                    for m in members]
+        dzp = (ctypes.POINTER(ctypes.c_double) * n)(*[d.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+                                                      for d in self._dz])
+        if stream is None:
+            stream = current_stream()
+        h = ctypes.c_void_p()
+        st = lib().flups_batch_create(ctypes.byref(h), n, ci(*[m[0] for m in members]), ci(*[m[1] for m in members]),
+                                      ci(*[m[2] for m in members]), cd(*[m[3] for m in members]),
+                                      cd(*[m[4] for m in members]), dzp, ci(*[BC[m[6]] for m in members]),
+                                      int(nstreams), int(bool(autotune)), stream)
+        _check(st, "flups_batch_create")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            lib().flups_batch_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    __del__ = close
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def solve(self, fs, ps, rtol=1e-10, max_iter=4, info=True, check=True):
+        n = self.n
+        fa = (ctypes.c_void_p * n)(*[ptr(x) for x in fs])
+        pa = (ctypes.c_void_p * n)(*[ptr(x) for x in ps])
+        inf = (Info * n)() if info else None
+        st = lib().flups_batch_solve(self._h, fa, pa, float(rtol), int(max_iter), inf)
+        if check:
+            _check(st, "flups_batch_solve")
+            return list(inf) if inf is not None else None
+        return st, (list(inf) if inf is not None else None)
+
+    @property
+    def graph_kernels(self):
+        return lib().flups_batch_graph_kernels(self._h)
+
+    def tuning(self, m):
+        a, b = ctypes.c_int(), ctypes.c_int()
+        _check(lib().flups_batch_member_tuning(self._h, int(m), ctypes.byref(a), ctypes.byref(b)),
+               "flups_batch_member_tuning")
+        return a.value, b.value

@@ -1,0 +1,102 @@
+"""Batched ensembles of mixed-size FP32-refine solves in one CUDA graph launch.
+
+* The graph-capturable solve (fixed kernel sequence, device-side early exit) must give
+  exactly the bits of the host-driven flups_solve on the same plan.
+* Every ensemble member must solve the oracle's own equation to rel. residual <= rtol
+  (checked by the oracle's FP64 residual of the GPU's p) and agree with the member's
+  oracle direct solve; a graph replay must reproduce the first launch bit for bit.
+* The mixed-size ensemble of 64 members {32, 48, 64, 96, 128}^3 (periodic and z walls,
+  density ratios in [1, 20]) at full size.
+"""
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2204_08834_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_2204_08834_gb300 import flups  # noqa: E402
+
+
+def grid_of(c):
+    nz, ny, nx = c.shape
+    return oracle.make_grid(nx, ny, nz, c.dx, c.dy, c.dzf, c.bc)
+
+
+def member_rhs(c):
+    return oracle.rhs(c.u, c.v, c.w, c.rho, c.pn, c.pnm1, 2.0, 1.0, c.dt, grid_of(c))
+
+
+def spec(c):
+    nz, ny, nx = c.shape
+    return (nx, ny, nz, c.dx, c.dy, c.dzf, c.bc)
+
+
+@pytest.mark.parametrize("case", ["sphere32", "walls48"])
+def test_graphable_solve_equals_host_loop(case):
+    c = synth.sphere(32) if case == "sphere32" else synth.random_fields(48, 24, 20, "walls", True, seed=99)
+    f = torch.from_numpy(member_rhs(c)).cuda()
+    p1 = torch.empty_like(f)
+    p2 = torch.full_like(f, np.nan)
+    with flups.Plan.for_case(c, "fp32_refine") as plan:
+        info = plan.solve(f, p1, rtol=1e-10, max_iter=6)
+        plan.solve_graphable(f, p2, rtol=1e-10, max_iter=6)
+        res = plan.solve_result(rtol=1e-10)
+    torch.cuda.synchronize()
+    assert torch.equal(p1, p2)
+    assert res.rel_res == info.rel_res
+
+
+def small_members():
+    cases = []
+    for m in range(10):
+        n = (32, 48, 64)[m % 3]
+        c = synth.emulsion(n, ratio=1.0 + 2.0 * m, ndrops=4, rmin_cells=2.0, rmax_cells=4.0, seed=200 + m)
+        if m % 2:
+            c["bc"] = "walls"
+            c["w"][-1] = 0.0
+        cases.append(c)
+    return cases
+
+
+def test_batch_members_match_oracle_and_replay():
+    cases = small_members()
+    fs = [torch.from_numpy(member_rhs(c)).cuda() for c in cases]
+    ps = [torch.empty_like(f) for f in fs]
+    with flups.Batch([spec(c) for c in cases], nstreams=4, autotune=True) as b:
+        infos = b.solve(fs, ps, rtol=1e-10, max_iter=5)
+        first = [p.clone() for p in ps]
+        assert b.graph_kernels > 0
+        for p in ps:
+            p.fill_(0.0)
+        b.solve(fs, ps, rtol=1e-10, max_iter=5)          # replay of the captured graph
+        torch.cuda.synchronize()
+        for a, bb in zip(first, ps):
+            assert torch.equal(a, bb)
+        for m in range(len(cases)):
+            cta, rv = b.tuning(m)
+            assert cta in (256, 512, 1024) and rv in (0, 1)
+    for c, f, p, inf in zip(cases, fs, ps, infos):
+        g = grid_of(c)
+        fo = f.cpu().numpy()
+        pg = p.cpu().numpy()
+        assert inf.rel_res <= 1e-10
+        assert oracle.rel_residual(fo, pg, g) <= 1.5e-10
+        po = oracle.solve(fo, g)
+        assert np.linalg.norm(pg - po) / np.linalg.norm(po) <= 1e-8
+
+
+@pytest.mark.slow
+def test_mixed_size_ensemble_of_64():
+    cases = [synth.ensemble_member(m) for m in range(64)]
+    assert sorted({c.shape[0] for c in cases}) == [32, 48, 64, 96, 128]
+    fs = [torch.from_numpy(member_rhs(c)).cuda() for c in cases]
+    ps = [torch.empty_like(f) for f in fs]
+    with flups.Batch([spec(c) for c in cases], nstreams=8, autotune=True) as b:
+        infos = b.solve(fs, ps, rtol=1e-10, max_iter=5)
+    for c, f, p, inf in zip(cases, fs, ps, infos):
+        assert inf.rel_res <= 1e-10, c.name
+        assert oracle.rel_residual(f.cpu().numpy(), p.cpu().numpy(), grid_of(c)) <= 1.5e-10, c.name
