@@ -239,6 +239,75 @@ unsigned long long flups_batch_graph_kernels(flups_batch batch);
  * chosen for member m. */
 flups_status flups_batch_member_tuning(flups_batch batch, int m, int* cta_threads, int* radix_variant);
 
+/*
+ * flups_varcoef_solve - the exact variable-coefficient pressure that the split of Sec. 3.3
+ * approximates (the split replaces 1/rho by the constant 1/rho0 in the Poisson operator and
+ * carries the difference through p_hat, Eqs. us_predic and poisson):
+ *     D((rho0/rho_f) G p) = f - <f>_V,   <p>_V = 0,
+ * rho_f the arithmetic mean of the two cell densities beside a face, rho0 the plan's minimum
+ * density from flups_set_density.  Solved by conjugate gradients in the volume-weighted inner
+ * product, preconditioned with the plan's own constant-coefficient solve (FP64 plans: one
+ * direct pass; FP32-refine plans: three FP32 passes with FP64 defect correction).  Not in the
+ * paper: these pressures are the training targets of the learned p_hat (flups_pnet_*) and the
+ * reference its splitting error is measured against.  With p_hat = p, flups_rhs/solve/correct
+ * return p again and the velocity u** - (dt/rho_f) G p.
+ *   rho  : DEVICE density, the field given to flups_set_density
+ *   f    : DEVICE right-hand side, e.g. flups_rhs with c1 = c2 = 0, i.e. (rho0/dt) D u**
+ *   p    : DEVICE output (may not alias f or rho)
+ *   rtol : stop when ||r||_V <= rtol ||f - <f>_V||_V (volume-weighted 2-norms)
+ *   info : HOST, may be NULL: iterations, final relative residual, first 16 residuals
+ * Returns FLUPS_ESTATE before set_density, FLUPS_ENOCONV after max_iter iterations (p holds
+ * the last iterate).  Allocates 7 fields of plan-owned workspace on the first call.
+ * Synchronises once per iteration.
+ */
+flups_status flups_varcoef_solve(flups_plan plan, const double* rho, const double* f, double* p, double rtol,
+                                 int max_iter, flups_info* info);
+
+/*
+ * Learned splitting pressure (not in the paper, which extrapolates p_hat = 2 p^n - p^{n-1} for
+ * a constant time step, Sec. 3.3).  A periodic 3-D convolutional net predicts a correction to
+ * the extrapolation:
+ *     p_hat = 2 p^n - p^{n-1} + s y(1 - rho0/rho, p^n/s, p^{n-1}/s),   s = rms(p^n),
+ * y = four 3x3x3 convolutions 3 -> 16 -> 16 -> 16 -> 1 with ReLU between layers.  Convolutions
+ * run on the tensor cores with bfloat16 weights and FP32 accumulation; activations and
+ * gradients are stored as bfloat16, master weights and Adam moments as FP32.
+ *
+ * Parameters (FLUPS_PNET_NPARAMS floats, HOST arrays): for each layer l = 1..4 its weights
+ * W_l[out][in][27] followed by its biases b_l[out]; tap t = 9 (dz+1) + 3 (dy+1) + (dx+1)
+ * multiplies the input at cell (k+dz, j+dy, i+dx), indices periodic.
+ *
+ * flups_pnet_create  - a net for one grid nx x ny x nz (all periodic) with nx a multiple of
+ *                      32, ny of 8, nz of 4, at most 2^28 cells (FLUPS_EUNSUPPORTED
+ *                      otherwise); params must be finite.  Allocates 224 bytes a cell plus
+ *                      the weight-gradient partials.  Synchronises.
+ * flups_pnet_predict - p_hat (DEVICE, may not alias the inputs) from DEVICE rho, p_n, p_nm1
+ *                      and rho0 > 0 (HOST, normally the plan's flups_get_rho0).
+ * flups_pnet_train_step - one Adam step (beta1 0.9, beta2 0.999, eps 1e-8, learning rate lr)
+ *                      on loss = mean over cells of (y - (p_next - 2 p_n + p_nm1)/s)^2;
+ *                      loss (HOST, may be NULL) receives the loss before the step, and then
+ *                      the call synchronises; without it the call is stream-ordered only.
+ * flups_pnet_eval_loss - the same loss without a step (synchronises).
+ * flups_pnet_set_params / get_params - HOST copies of the FP32 master parameters; set resets
+ *                      the Adam state; both synchronise.
+ * flups_pnet_get_grads - the parameter gradient of the last train step (HOST); synchronises.
+ * flups_pnet_launch_count - kernels this net has launched so far.
+ * Every call runs on the stream given at create.
+ */
+#define FLUPS_PNET_NPARAMS 15601
+typedef struct flups_pnet_s* flups_pnet;
+flups_status flups_pnet_create(flups_pnet* out, int nx, int ny, int nz, const float* params, void* stream);
+flups_status flups_pnet_destroy(flups_pnet net);
+flups_status flups_pnet_set_params(flups_pnet net, const float* params);
+flups_status flups_pnet_get_params(flups_pnet net, float* params);
+flups_status flups_pnet_get_grads(flups_pnet net, float* grads);
+flups_status flups_pnet_predict(flups_pnet net, const double* rho, double rho0, const double* p_n,
+                                const double* p_nm1, double* p_hat);
+flups_status flups_pnet_train_step(flups_pnet net, const double* rho, double rho0, const double* p_n,
+                                   const double* p_nm1, const double* p_next, float lr, double* loss);
+flups_status flups_pnet_eval_loss(flups_pnet net, const double* rho, double rho0, const double* p_n,
+                                  const double* p_nm1, const double* p_next, double* loss);
+unsigned long long flups_pnet_launch_count(flups_pnet net);
+
 /* flups_status_string - static, human-readable name of a status code. */
 const char* flups_status_string(int status);
 

@@ -369,6 +369,8 @@ flups_status flups_plan_create(flups_plan* out, int nx, int ny, int nz, double d
                     (bc == FLUPS_BC_WALLS || make_spec_map(&P->tm_z, P->spec, P->ldS, ny, nz, Bz, 1, nz < 256 ? nz : 256));
     }
     P->hbuf = nullptr;
+    P->vcbuf = nullptr;
+    P->vcs_host = nullptr;
     *out = P;
     return FLUPS_OK;
 }
@@ -385,6 +387,8 @@ flups_status flups_plan_destroy(flups_plan P) {
     }
     std::free(P->allocs);
     if (P->hbuf) cudaFree(P->hbuf);
+    if (P->vcbuf) cudaFree(P->vcbuf);
+    if (P->vcs_host) cudaFreeHost(P->vcs_host);
     if (P->sc_host) cudaFreeHost(P->sc_host);
     delete P;
     return cuda_status(e);

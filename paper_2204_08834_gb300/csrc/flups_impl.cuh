@@ -121,6 +121,9 @@ struct flups_plan_s {
     int* skip_ptr;               // passed to kernels as Geo::skip (set by the fixed-iteration solve)
     int cta_cap;                 // thread cap of the transform CTAs (autotuned per size in batches)
     int last_max_iter;           // max_iter of the last graph-capturable solve
+    // exact variable-coefficient solve (flups_varcoef_solve), allocated on first use
+    void* vcbuf;                 // face coefficients cx, cy, cz and PCG vectors r, z, d, q + scalars
+    void* vcs_host;              // pinned host mirror of the PCG scalars
     // per-kernel timing
     int prof_on, prof_n, prof_cap, prof_open;
     cudaEvent_t* prof_ev;        // 2 * prof_cap events

@@ -1,0 +1,712 @@
+// pnet.cu - learned splitting pressure: a periodic 3-D convolutional net that predicts the
+// correction to the linear extrapolation p_hat = 2 p^n - p^{n-1} of Sec. 3.3, trained on the
+// exact variable-coefficient pressures of flups_varcoef_solve.
+//
+//   features  x = (1 - rho0/rho, p^n/s, p^{n-1}/s), s = rms(p^n)
+//   net       four 3x3x3 convolutions 3 -> 16 -> 16 -> 16 -> 1, ReLU between layers
+//   output    p_hat = 2 p^n - p^{n-1} + s y
+//   training  loss = mean (y - (p^{n+1} - 2 p^n + p^{n-1})/s)^2, Adam (beta 0.9/0.999, eps 1e-8)
+//
+// Arithmetic: every convolution is an implicit GEMM on the tensor cores (mma.sync m16n8k16,
+// bfloat16 operands, FP32 accumulation).  Activations and gradients are stored as bfloat16
+// [point][16 channels] (32 bytes a point, channels fastest); master weights, Adam moments and
+// gradients are FP32; biases are added in FP32.
+//
+// A CTA computes a tile of 4 (z) x 8 (y) x 32 (x) output points from a shared-memory halo tile
+// of 6 x 10 x 34 input points.  The 16-byte halves of a point are stored swapped when bit 2 of
+// the point's tile index is set, so the eight 16-byte rows an ldmatrix reads for eight
+// consecutive points fall in eight different bank groups.
+//
+// Packed weights (per layer, bfloat16 [27 taps][16 rows][24]): the forward form has rows = output
+// channel and columns = input channel; the backward-data form of layer l has rows = input
+// channel, columns = output channel and the taps reversed (tap t -> 26 - t), so the gradient
+// with respect to a layer's input is the same convolution kernel run on the output gradient.
+// Padding columns/rows are zero.
+
+#include "flups_impl.cuh"
+
+#include <cuda_bf16.h>
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#define PN_NP 15601
+#define PN_WPK (27 * 16 * 24)          // packed weights of one layer (bf16 elements)
+#define PN_PART 6928                   // one CTA's weight-gradient partial: 27*16*16 + 16 biases
+
+namespace {
+
+constexpr int TZ = 4, TY = 8, TX = 32;
+constexpr int HZ = TZ + 2, HY = TY + 2, HX = TX + 2;
+constexpr int NHALO = HZ * HY * HX;                       // 2040 points
+constexpr int TILE_PTS = TZ * TY * TX;                    // 1024 points
+constexpr int SMEM_IN = NHALO * 32;                       // 65280 bytes
+constexpr int SMEM_W = PN_WPK * 2;                        // 20736 bytes
+constexpr int SMEM_DZ = TILE_PTS * 32;                    // 32768 bytes
+constexpr int CONV_SMEM = SMEM_IN + SMEM_W;
+constexpr int WGRAD_SMEM = SMEM_IN + SMEM_DZ;
+constexpr int THREADS = 256;
+
+// layer geometry: inputs, outputs, offsets of W and b in the parameter vector
+__host__ __device__ constexpr int lay_in(int l) { return l == 0 ? 3 : 16; }
+__host__ __device__ constexpr int lay_out(int l) { return l == 3 ? 1 : 16; }
+__host__ __device__ constexpr int lay_w(int l) { return l == 0 ? 0 : (l == 1 ? 1312 : (l == 2 ? 8240 : 15168)); }
+__host__ __device__ constexpr int lay_b(int l) { return lay_w(l) + lay_out(l) * lay_in(l) * 27; }
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void ldsm_x4(uint32_t addr, uint32_t (&r)[4]) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]) : "r"(addr));
+}
+__device__ __forceinline__ void ldsm_x4_t(uint32_t addr, uint32_t (&r)[4]) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]) : "r"(addr));
+}
+__device__ __forceinline__ void ldsm_x2(uint32_t addr, uint32_t& r0, uint32_t& r1) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];\n" : "=r"(r0), "=r"(r1) : "r"(addr));
+}
+__device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+    asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+                 "{%0,%1,%2,%3};\n"
+                 : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+                 : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// byte offset of 16-byte half h of tile point sp (swizzled)
+__device__ __forceinline__ uint32_t swz(int sp, int h) { return (uint32_t)((sp * 2 + (h ^ ((sp >> 2) & 1))) * 16); }
+
+__device__ __forceinline__ int wrapc(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
+
+struct TileOrigin { int x0, y0, z0; };
+
+__device__ __forceinline__ TileOrigin tile_origin(int nx, int ny) {
+    const int tnx = nx / TX, tny = ny / TY;
+    const int b = blockIdx.x;
+    TileOrigin o;
+    o.x0 = (b % tnx) * TX;
+    o.y0 = ((b / tnx) % tny) * TY;
+    o.z0 = (b / (tnx * tny)) * TZ;
+    return o;
+}
+
+// Loads the periodic halo tile of a [n][16] bfloat16 field into shared memory (swizzled).
+__device__ __forceinline__ void load_halo(const __nv_bfloat16* __restrict__ in, unsigned char* sm, TileOrigin o,
+                                          int nx, int ny, int nz) {
+    const uint4* src = reinterpret_cast<const uint4*>(in);
+    for (int c = threadIdx.x; c < NHALO * 2; c += THREADS) {
+        const int sp = c >> 1, h = c & 1;
+        const int xx = sp % HX, t = sp / HX;
+        const int yy = t % HY, zz = t / HY;
+        const int gx = wrapc(o.x0 + xx - 1, nx), gy = wrapc(o.y0 + yy - 1, ny), gz = wrapc(o.z0 + zz - 1, nz);
+        const long long pt = ((long long)gz * ny + gy) * nx + gx;
+        *reinterpret_cast<uint4*>(sm + swz(sp, h)) = __ldg(src + pt * 2 + h);
+    }
+}
+
+struct ConvArgs {
+    const __nv_bfloat16* in;     // [n][16]
+    const __nv_bfloat16* w;      // packed weights [27][16][24]
+    const float* bias;           // FP32 biases (EPI 0, 1, 2)
+    __nv_bfloat16* out;          // EPI 0: activation; EPI 2: output gradient (channel 0); EPI 3: masked gradient
+    const __nv_bfloat16* mask;   // EPI 3: activation whose positive entries pass the gradient
+    const double* pn;            // EPI 1, 2
+    const double* pnm1;
+    const double* pnext;         // EPI 2
+    double* phat;                // EPI 1
+    const double* sc;            // [0] s, [1] 1/s
+    double* red;                 // EPI 2: per-CTA sum of squared errors
+    double gscale;               // EPI 2: d loss / d y = gscale * error
+    int nx, ny, nz;
+};
+
+// EPI 0: out = bf16(relu(acc + b))           (hidden layer, NT = 2)
+// EPI 1: p_hat = 2 p^n - p^{n-1} + s (acc + b) (last layer inference, NT = 1)
+// EPI 2: e = acc + b - t, out[.][0] = bf16(gscale e), red += e^2 (last layer training, NT = 1)
+// EPI 3: out = bf16(acc * (mask > 0))          (gradient w.r.t. a hidden layer's output, NT = 2)
+template <int NT, int EPI>
+__global__ void __launch_bounds__(THREADS, 2) k_pnet_conv(ConvArgs a) {
+    extern __shared__ __align__(128) unsigned char sm[];
+    unsigned char* sin = sm;
+    unsigned char* sw = sm + SMEM_IN;
+    const TileOrigin o = tile_origin(a.nx, a.ny);
+    load_halo(a.in, sin, o, a.nx, a.ny, a.nz);
+    {
+        const uint4* src = reinterpret_cast<const uint4*>(a.w);
+        const int nchunk = (NT == 2 ? 16 : 8) * 24 * 2 / 16;     // 16-byte chunks per tap (rows used)
+        for (int c = threadIdx.x; c < 27 * nchunk; c += THREADS) {
+            const int tap = c / nchunk, r = c % nchunk;
+            reinterpret_cast<uint4*>(sw)[tap * 48 + r] = __ldg(src + tap * 48 + r);
+        }
+    }
+    __syncthreads();
+
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int zl = warp >> 1, ybase = (warp & 1) * 4;
+    const uint32_t sin_u = smem_u32(sin), sw_u = smem_u32(sw);
+    // ldmatrix row of this lane: A operand (points x channels), B operand (weights)
+    const int a_row = (lane & 7) + ((lane >> 3) & 1) * 8, a_half = lane >> 4;
+    const uint32_t b_off = (uint32_t)((((lane >> 4) * 8 + (lane & 7)) * 24 + ((lane >> 3) & 1) * 8) * 2);
+    const int g = lane >> 2, t4 = lane & 3;
+
+    double sq = 0.0;
+    for (int grp = 0; grp < 2; ++grp) {
+        float acc[4][NT][4];
+#pragma unroll
+        for (int mi = 0; mi < 4; ++mi)
+#pragma unroll
+            for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) acc[mi][nt][q] = 0.0f;
+        const int y0l = ybase + 2 * grp;
+#pragma unroll 1
+        for (int tap = 0; tap < 27; ++tap) {
+            const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
+            uint32_t b[4];
+            if (NT == 2) {
+                ldsm_x4(sw_u + tap * (16 * 24 * 2) + b_off, b);
+            } else {
+                ldsm_x2(sw_u + tap * (16 * 24 * 2) + b_off, b[0], b[1]);
+            }
+#pragma unroll
+            for (int mi = 0; mi < 4; ++mi) {
+                const int yl = y0l + (mi >> 1), xh = mi & 1;
+                const int sp = ((zl + dz + 1) * HY + (yl + dy + 1)) * HX + xh * 16 + dx + 1 + a_row;
+                uint32_t av[4];
+                ldsm_x4(sin_u + swz(sp, a_half), av);
+                mma_bf16(acc[mi][0], av, b[0], b[1]);
+                if (NT == 2) mma_bf16(acc[mi][NT - 1], av, b[2], b[3]);
+            }
+        }
+        // epilogue
+#pragma unroll
+        for (int mi = 0; mi < 4; ++mi) {
+            const int yl = y0l + (mi >> 1), xh = mi & 1;
+            const long long rowbase = ((long long)(o.z0 + zl) * a.ny + (o.y0 + yl)) * a.nx + o.x0 + xh * 16;
+#pragma unroll
+            for (int hr = 0; hr < 2; ++hr) {
+                const long long pt = rowbase + g + 8 * hr;
+                if (EPI == 0 || EPI == 3) {
+#pragma unroll
+                    for (int nt = 0; nt < NT; ++nt) {
+                        const int n = nt * 8 + 2 * t4;
+                        float v0 = acc[mi][nt][2 * hr], v1 = acc[mi][nt][2 * hr + 1];
+                        if (EPI == 0) {
+                            v0 = fmaxf(v0 + __ldg(a.bias + n), 0.0f);
+                            v1 = fmaxf(v1 + __ldg(a.bias + n + 1), 0.0f);
+                        } else {
+                            const uint32_t mk = __ldg(reinterpret_cast<const unsigned int*>(a.mask + pt * 16 + n));
+                            if (!(mk & 0x7fffu)) v0 = 0.0f;
+                            if (!(mk & 0x7fff0000u)) v1 = 0.0f;
+                        }
+                        *reinterpret_cast<__nv_bfloat162*>(a.out + pt * 16 + n) = __floats2bfloat162_rn(v0, v1);
+                    }
+                } else if (t4 == 0) {
+                    const double y = (double)(acc[mi][0][2 * hr] + __ldg(a.bias));
+                    const double pn = a.pn[pt], pm = a.pnm1[pt];
+                    if (EPI == 1) {
+                        a.phat[pt] = 2.0 * pn - pm + a.sc[0] * y;
+                    } else {
+                        const double e = y - (a.pnext[pt] - (2.0 * pn - pm)) * a.sc[1];
+                        sq += e * e;
+                        a.out[pt * 16] = __double2bfloat16(a.gscale * e);
+                    }
+                }
+            }
+        }
+    }
+    if (EPI == 2) {
+        __shared__ double ws[THREADS / 32];
+        for (int s = 16; s > 0; s >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, s);
+        if (lane == 0) ws[warp] = sq;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int w = 0; w < THREADS / 32; ++w) t += ws[w];
+            a.red[blockIdx.x] = t;
+        }
+    }
+}
+
+// Weight gradient of one layer over the CTA's tile:
+//   part[cta][tap][o][i] = sum_v dz(v)[o] act(v + tap)[i],  part[cta][6912 + o] = sum_v dz(v)[o]
+__global__ void __launch_bounds__(THREADS, 2) k_pnet_wgrad(const __nv_bfloat16* __restrict__ dz,
+                                                           const __nv_bfloat16* __restrict__ act,
+                                                           float* __restrict__ part, int nx, int ny, int nz) {
+    extern __shared__ __align__(128) unsigned char sm[];
+    unsigned char* sin = sm;
+    unsigned char* sdz = sm + SMEM_IN;
+    const TileOrigin o = tile_origin(nx, ny);
+    load_halo(act, sin, o, nx, ny, nz);
+    {
+        const uint4* src = reinterpret_cast<const uint4*>(dz);
+        for (int c = threadIdx.x; c < TILE_PTS * 2; c += THREADS) {
+            const int q = c >> 1, h = c & 1;
+            const int xl = q % TX, yl = (q / TX) % TY, zl = q / (TX * TY);
+            const long long pt = ((long long)(o.z0 + zl) * ny + (o.y0 + yl)) * nx + o.x0 + xl;
+            *reinterpret_cast<uint4*>(sdz + swz(q, h)) = __ldg(src + pt * 2 + h);
+        }
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int ntap = warp < 3 ? 4 : 3;                 // taps warp, warp + 8, warp + 16 (, warp + 24)
+    const uint32_t sin_u = smem_u32(sin), sdz_u = smem_u32(sdz);
+    const int r = lane & 7, j = lane >> 3;
+    float acc[4][2][4];
+#pragma unroll
+    for (int s = 0; s < 4; ++s)
+#pragma unroll
+        for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[s][nt][q] = 0.0f;
+#pragma unroll 1
+    for (int chunk = 0; chunk < TILE_PTS / 16; ++chunk) {
+        const int zl = chunk >> 4, yl = (chunk >> 1) & 7, xh = chunk & 1;
+        uint32_t av[4];
+        {
+            const int q = (zl * TY + yl) * TX + xh * 16 + r + 8 * (j >> 1);
+            ldsm_x4_t(sdz_u + swz(q, j & 1), av);
+        }
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+            if (s < ntap) {
+                const int tap = warp + 8 * s;
+                const int dzz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
+                const int sp = ((zl + dzz + 1) * HY + (yl + dy + 1)) * HX + xh * 16 + dx + 1 + r + 8 * (j & 1);
+                uint32_t bv[4];
+                ldsm_x4_t(sin_u + swz(sp, j >> 1), bv);
+                mma_bf16(acc[s][0], av, bv[0], bv[1]);
+                mma_bf16(acc[s][1], av, bv[2], bv[3]);
+            }
+        }
+    }
+    float* dst = part + (size_t)blockIdx.x * PN_PART;
+    const int g = lane >> 2, t4 = lane & 3;
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+        if (s < ntap) {
+            const int tap = warp + 8 * s;
+#pragma unroll
+            for (int nt = 0; nt < 2; ++nt) {
+                const int i = nt * 8 + 2 * t4;
+                *reinterpret_cast<float2*>(dst + tap * 256 + g * 16 + i) = make_float2(acc[s][nt][0], acc[s][nt][1]);
+                *reinterpret_cast<float2*>(dst + tap * 256 + (g + 8) * 16 + i) = make_float2(acc[s][nt][2], acc[s][nt][3]);
+            }
+        }
+    }
+    // bias gradient: channel oc = tid & 15 summed over points q = tid >> 4 (mod 16)
+    __shared__ float bs[THREADS];
+    {
+        const int oc = threadIdx.x & 15, q0 = threadIdx.x >> 4;
+        const __nv_bfloat16* e = reinterpret_cast<const __nv_bfloat16*>(sdz);
+        float s = 0.0f;
+        for (int q = q0; q < TILE_PTS; q += 16) s += __bfloat162float(e[swz(q, oc >> 3) / 2 + (oc & 7)]);
+        bs[threadIdx.x] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x < 16) {
+        float s = 0.0f;
+        for (int q = 0; q < 16; ++q) s += bs[q * 16 + threadIdx.x];
+        dst[6912 + threadIdx.x] = s;
+    }
+}
+
+// grad[param] = sum over CTAs of the partials (fixed order, FP64 accumulation).
+__global__ void k_pnet_reduce(const float* __restrict__ part, int ncta, float* __restrict__ grad) {
+    const int l = blockIdx.y;
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= PN_PART) return;
+    int pidx;
+    if (e < 6912) {
+        const int tap = e >> 8, oc = (e >> 4) & 15, ic = e & 15;
+        if (oc >= lay_out(l) || ic >= lay_in(l)) return;
+        pidx = lay_w(l) + (oc * lay_in(l) + ic) * 27 + tap;
+    } else {
+        const int oc = e - 6912;
+        if (oc >= lay_out(l)) return;
+        pidx = lay_b(l) + oc;
+    }
+    const float* p = part + (size_t)l * ncta * PN_PART + e;
+    double s = 0.0;
+    for (int c = 0; c < ncta; ++c) s += p[(size_t)c * PN_PART];
+    grad[pidx] = (float)s;
+}
+
+// Adam step (optional) and packing of the bfloat16 weights.
+__global__ void k_pnet_adam_pack(float* __restrict__ w, float* __restrict__ m, float* __restrict__ v,
+                                 const float* __restrict__ grad, int adam, float lr, float bc1, float bc2,
+                                 __nv_bfloat16* __restrict__ wf, __nv_bfloat16* __restrict__ wb) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= PN_NP) return;
+    float x = w[p];
+    if (adam) {
+        const float gr = grad[p];
+        const float mm = 0.9f * m[p] + 0.1f * gr;
+        const float vv = 0.999f * v[p] + 0.001f * gr * gr;
+        m[p] = mm;
+        v[p] = vv;
+        x -= lr * (mm * bc1) / (sqrtf(vv * bc2) + 1e-8f);
+        w[p] = x;
+    }
+    int l = 0;
+    while (l < 3 && p >= lay_w(l + 1)) ++l;
+    if (p >= lay_b(l)) return;                   // a bias: used in FP32
+    const int q = p - lay_w(l);
+    const int tap = q % 27, ic = (q / 27) % lay_in(l), oc = q / (27 * lay_in(l));
+    const __nv_bfloat16 h = __float2bfloat16_rn(x);
+    wf[(size_t)l * PN_WPK + (tap * 16 + oc) * 24 + ic] = h;
+    if (l > 0) wb[(size_t)l * PN_WPK + ((26 - tap) * 16 + ic) * 24 + oc] = h;
+}
+
+__global__ void k_pnet_sumsq(const double* __restrict__ x, long long n, double* __restrict__ red) {
+    double s = 0.0;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x)
+        s += x[c] * x[c];
+    __shared__ double ws[THREADS / 32];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < THREADS / 32; ++w) t += ws[w];
+        red[blockIdx.x] = t;
+    }
+}
+
+// what 0: sc[0] = s = sqrt(S / n) (1 if 0), sc[1] = 1/s;  what 1: sc[2] = S / n (loss)
+__global__ void k_pnet_fin(const double* __restrict__ red, int nblk, double* __restrict__ sc, int what, double inv_n) {
+    __shared__ double ws[32];
+    double s = 0.0;
+    for (int b = threadIdx.x; b < nblk; b += blockDim.x) s += red[b];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += ws[w];
+        if (what == 0) {
+            double sv = sqrt(t * inv_n);
+            if (!(sv > 0.0)) sv = 1.0;
+            sc[0] = sv;
+            sc[1] = 1.0 / sv;
+        } else {
+            sc[2] = t * inv_n;
+        }
+    }
+}
+
+__global__ void k_pnet_features(const double* __restrict__ rho, double rho0, const double* __restrict__ pn,
+                                 const double* __restrict__ pnm1, const double* __restrict__ sc, long long n,
+                                 __nv_bfloat16* __restrict__ feat) {
+    const double is = sc[1];
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
+        __nv_bfloat162 lo, hi;
+        lo.x = __double2bfloat16(1.0 - rho0 / rho[c]);
+        lo.y = __double2bfloat16(pn[c] * is);
+        hi.x = __double2bfloat16(pnm1[c] * is);
+        hi.y = __float2bfloat16_rn(0.0f);
+        uint2 u;
+        u.x = *reinterpret_cast<unsigned int*>(&lo);
+        u.y = *reinterpret_cast<unsigned int*>(&hi);
+        *reinterpret_cast<uint2*>(feat + c * 16) = u;
+    }
+}
+
+}  // namespace
+
+struct flups_pnet_s {
+    int nx, ny, nz, dev, ncta, nred;
+    long long n;
+    cudaStream_t stream;
+    float* w; float* m; float* v; float* grad;    // FP32 master weights, Adam moments, gradient
+    __nv_bfloat16* wf; __nv_bfloat16* wb;         // packed bfloat16 weights (4 layers each)
+    __nv_bfloat16* feat; __nv_bfloat16* act[3]; __nv_bfloat16* dy; __nv_bfloat16* g[2];
+    float* part;                                  // weight-gradient partials [4][ncta][PN_PART]
+    double* red;                                  // per-CTA scalar partials
+    double* sc;                                   // s, 1/s, loss
+    double* sc_host;
+    void* base;
+    int step;
+    unsigned long long launches;
+};
+
+namespace {
+
+struct PnGuard {
+    int prev = -1;
+    explicit PnGuard(int dev) {
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+        else prev = -1;
+    }
+    ~PnGuard() { if (prev >= 0) cudaSetDevice(prev); }
+};
+
+flups_status pn_status(cudaError_t e) {
+    if (e == cudaSuccess) return FLUPS_OK;
+    flups_note_cuda_error(e);
+    return e == cudaErrorMemoryAllocation ? FLUPS_ENOMEM : FLUPS_ECUDA;
+}
+
+bool al16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+cudaError_t set_smem_attrs() {
+    static int done = -1;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (done == dev) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(k_pnet_conv<2, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, CONV_SMEM);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_pnet_conv<2, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, CONV_SMEM);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_pnet_conv<1, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, CONV_SMEM);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_pnet_conv<1, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, CONV_SMEM);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_pnet_wgrad, cudaFuncAttributeMaxDynamicSharedMemorySize, WGRAD_SMEM);
+    if (e == cudaSuccess) done = dev;
+    return e;
+}
+
+ConvArgs conv_args(flups_pnet N) {
+    ConvArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.sc = N->sc;
+    a.red = N->red;
+    a.nx = N->nx; a.ny = N->ny; a.nz = N->nz;
+    return a;
+}
+
+template <int NT, int EPI>
+void conv(flups_pnet N, const ConvArgs& a) {
+    k_pnet_conv<NT, EPI><<<N->ncta, THREADS, CONV_SMEM, N->stream>>>(a);
+    N->launches++;
+}
+
+void pack(flups_pnet N, int adam, float lr) {
+    float bc1 = 1.0f, bc2 = 1.0f;
+    if (adam) {
+        N->step++;
+        bc1 = (float)(1.0 / (1.0 - std::pow(0.9, N->step)));
+        bc2 = (float)(1.0 / (1.0 - std::pow(0.999, N->step)));
+    }
+    k_pnet_adam_pack<<<(PN_NP + 255) / 256, 256, 0, N->stream>>>(N->w, N->m, N->v, N->grad, adam, lr, bc1, bc2, N->wf,
+                                                                 N->wb);
+    N->launches++;
+}
+
+// features + layers 1..3 (hidden activations)
+void forward_hidden(flups_pnet N, const double* rho, double rho0, const double* pn, const double* pnm1) {
+    cudaStream_t s = N->stream;
+    k_pnet_sumsq<<<N->nred, THREADS, 0, s>>>(pn, N->n, N->red);
+    k_pnet_fin<<<1, 1024, 0, s>>>(N->red, N->nred, N->sc, 0, 1.0 / (double)N->n);
+    k_pnet_features<<<N->nred, THREADS, 0, s>>>(rho, rho0, pn, pnm1, N->sc, N->n, N->feat);
+    N->launches += 3;
+    const __nv_bfloat16* in = N->feat;
+    for (int l = 0; l < 3; ++l) {
+        ConvArgs a = conv_args(N);
+        a.in = in;
+        a.w = N->wf + (size_t)l * PN_WPK;
+        a.bias = N->w + lay_b(l);
+        a.out = N->act[l];
+        conv<2, 0>(N, a);
+        in = N->act[l];
+    }
+}
+
+void wgrad(flups_pnet N, int l, const __nv_bfloat16* dz, const __nv_bfloat16* act) {
+    k_pnet_wgrad<<<N->ncta, THREADS, WGRAD_SMEM, N->stream>>>(dz, act, N->part + (size_t)l * N->ncta * PN_PART, N->nx,
+                                                              N->ny, N->nz);
+    N->launches++;
+}
+
+flups_status check_fields(flups_pnet N, const double* rho, double rho0, const double* pn, const double* pnm1) {
+    if (!N || !rho || !pn || !pnm1) return FLUPS_EINVAL;
+    if (!al16(rho) || !al16(pn) || !al16(pnm1)) return FLUPS_EINVAL;
+    if (!(rho0 > 0.0) || !std::isfinite(rho0)) return FLUPS_EINVAL;
+    return FLUPS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+flups_status flups_pnet_create(flups_pnet* out, int nx, int ny, int nz, const float* params, void* stream) {
+    if (!out) return FLUPS_EINVAL;
+    *out = nullptr;
+    if (!params) return FLUPS_EINVAL;
+    if (nx < TX || ny < TY || nz < TZ) return FLUPS_EUNSUPPORTED;
+    if (nx % TX || ny % TY || nz % TZ) return FLUPS_EUNSUPPORTED;
+    if ((long long)nx * ny * nz > (1LL << 28)) return FLUPS_EUNSUPPORTED;
+    for (int p = 0; p < PN_NP; ++p)
+        if (!std::isfinite(params[p])) return FLUPS_EINVAL;
+    flups_pnet N = new (std::nothrow) flups_pnet_s();
+    if (!N) return FLUPS_ENOMEM;
+    N->nx = nx; N->ny = ny; N->nz = nz;
+    N->n = (long long)nx * ny * nz;
+    N->ncta = (int)(N->n / TILE_PTS);
+    N->nred = (int)std::min<long long>((N->n + 4 * THREADS - 1) / (4 * THREADS), 1216);
+    N->stream = (cudaStream_t)stream;
+    cudaGetDevice(&N->dev);
+    cudaError_t e = set_smem_attrs();
+    if (e != cudaSuccess) { delete N; return pn_status(e); }
+    const size_t fbytes = (size_t)N->n * 16 * sizeof(__nv_bfloat16);
+    const size_t off_w = 0, off_wf = 4 * (size_t)16384 * 4;
+    const size_t off_wb = off_wf + 4 * (size_t)PN_WPK * 2;
+    const size_t off_feat = (off_wb + 4 * (size_t)PN_WPK * 2 + 255) / 256 * 256;
+    const size_t off_part = off_feat + 7 * fbytes;
+    const size_t off_red = off_part + 4 * (size_t)N->ncta * PN_PART * sizeof(float);
+    const size_t off_sc = off_red + (size_t)std::max(N->nred, N->ncta) * sizeof(double);
+    const size_t total = off_sc + 8 * sizeof(double);
+    e = cudaMalloc(&N->base, total);
+    if (e != cudaSuccess) { delete N; return pn_status(e); }
+    unsigned char* b = (unsigned char*)N->base;
+    N->w = (float*)(b + off_w);
+    N->m = N->w + 16384;
+    N->v = N->m + 16384;
+    N->grad = N->v + 16384;
+    N->wf = (__nv_bfloat16*)(b + off_wf);
+    N->wb = (__nv_bfloat16*)(b + off_wb);
+    __nv_bfloat16* f = (__nv_bfloat16*)(b + off_feat);
+    const size_t fe = (size_t)N->n * 16;
+    N->feat = f;
+    N->act[0] = f + fe; N->act[1] = f + 2 * fe; N->act[2] = f + 3 * fe;
+    N->dy = f + 4 * fe; N->g[0] = f + 5 * fe; N->g[1] = f + 6 * fe;
+    N->part = (float*)(b + off_part);
+    N->red = (double*)(b + off_red);
+    N->sc = (double*)(b + off_sc);
+    e = cudaMallocHost(&N->sc_host, 8 * sizeof(double));
+    if (e != cudaSuccess) { cudaFree(N->base); delete N; return pn_status(e); }
+    // zero: moments, packed weights (padding), feature and output-gradient channels never written
+    e = cudaMemsetAsync(b, 0, off_feat, N->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(N->feat, 0, fbytes, N->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(N->dy, 0, fbytes, N->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(N->w, params, PN_NP * sizeof(float), cudaMemcpyHostToDevice, N->stream);
+    if (e == cudaSuccess) { pack(N, 0, 0.0f); e = cudaGetLastError(); }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(N->stream);
+    if (e != cudaSuccess) {
+        cudaFreeHost(N->sc_host);
+        cudaFree(N->base);
+        delete N;
+        return pn_status(e);
+    }
+    *out = N;
+    return FLUPS_OK;
+}
+
+flups_status flups_pnet_destroy(flups_pnet N) {
+    if (!N) return FLUPS_EINVAL;
+    PnGuard dg(N->dev);
+    cudaError_t e = cudaStreamSynchronize(N->stream);
+    cudaFree(N->base);
+    cudaFreeHost(N->sc_host);
+    delete N;
+    return pn_status(e);
+}
+
+flups_status flups_pnet_set_params(flups_pnet N, const float* params) {
+    if (!N || !params) return FLUPS_EINVAL;
+    for (int p = 0; p < PN_NP; ++p)
+        if (!std::isfinite(params[p])) return FLUPS_EINVAL;
+    PnGuard dg(N->dev);
+    cudaError_t e = cudaMemcpyAsync(N->w, params, PN_NP * sizeof(float), cudaMemcpyHostToDevice, N->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(N->m, 0, 2 * 16384 * sizeof(float), N->stream);
+    if (e == cudaSuccess) { pack(N, 0, 0.0f); e = cudaGetLastError(); }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(N->stream);   // params may be freed on return
+    N->step = 0;
+    return pn_status(e);
+}
+
+flups_status flups_pnet_get_params(flups_pnet N, float* params) {
+    if (!N || !params) return FLUPS_EINVAL;
+    PnGuard dg(N->dev);
+    cudaError_t e = cudaMemcpyAsync(params, N->w, PN_NP * sizeof(float), cudaMemcpyDeviceToHost, N->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(N->stream);
+    return pn_status(e);
+}
+
+flups_status flups_pnet_get_grads(flups_pnet N, float* grads) {
+    if (!N || !grads) return FLUPS_EINVAL;
+    PnGuard dg(N->dev);
+    cudaError_t e = cudaMemcpyAsync(grads, N->grad, PN_NP * sizeof(float), cudaMemcpyDeviceToHost, N->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(N->stream);
+    return pn_status(e);
+}
+
+flups_status flups_pnet_predict(flups_pnet N, const double* rho, double rho0, const double* p_n, const double* p_nm1,
+                                double* p_hat) {
+    flups_status st = check_fields(N, rho, rho0, p_n, p_nm1);
+    if (st != FLUPS_OK) return st;
+    if (!p_hat || !al16(p_hat) || p_hat == p_n || p_hat == p_nm1 || p_hat == rho) return FLUPS_EINVAL;
+    PnGuard dg(N->dev);
+    forward_hidden(N, rho, rho0, p_n, p_nm1);
+    ConvArgs a = conv_args(N);
+    a.in = N->act[2];
+    a.w = N->wf + 3 * (size_t)PN_WPK;
+    a.bias = N->w + lay_b(3);
+    a.pn = p_n; a.pnm1 = p_nm1; a.phat = p_hat;
+    conv<1, 1>(N, a);
+    return pn_status(cudaGetLastError());
+}
+
+// Forward through the loss; with train != 0 also the backward pass and one Adam step.
+static flups_status pnet_loss(flups_pnet N, const double* rho, double rho0, const double* p_n, const double* p_nm1,
+                              const double* p_next, int train, float lr, double* loss) {
+    flups_status st = check_fields(N, rho, rho0, p_n, p_nm1);
+    if (st != FLUPS_OK) return st;
+    if (!p_next || !al16(p_next)) return FLUPS_EINVAL;
+    if (train && (!(lr >= 0.0f) || !std::isfinite(lr))) return FLUPS_EINVAL;
+    PnGuard dg(N->dev);
+    forward_hidden(N, rho, rho0, p_n, p_nm1);
+    ConvArgs a = conv_args(N);
+    a.in = N->act[2];
+    a.w = N->wf + 3 * (size_t)PN_WPK;
+    a.bias = N->w + lay_b(3);
+    a.pn = p_n; a.pnm1 = p_nm1; a.pnext = p_next;
+    a.out = N->dy;
+    a.gscale = 2.0 / (double)N->n;
+    conv<1, 2>(N, a);
+    k_pnet_fin<<<1, 1024, 0, N->stream>>>(N->red, N->ncta, N->sc, 1, 1.0 / (double)N->n);
+    N->launches++;
+    if (train) {
+        // dZ of layer l+1's input side: g = conv(dZ_{l+1}, W_{l+1} reversed) masked by act_l > 0
+        const __nv_bfloat16* dzl = N->dy;
+        for (int l = 3; l >= 1; --l) {
+            __nv_bfloat16* gout = N->g[l & 1];
+            ConvArgs b = conv_args(N);
+            b.in = dzl;
+            b.w = N->wb + (size_t)l * PN_WPK;
+            b.mask = N->act[l - 1];
+            b.out = gout;
+            conv<2, 3>(N, b);
+            wgrad(N, l, dzl, N->act[l - 1]);
+            dzl = gout;
+        }
+        wgrad(N, 0, dzl, N->feat);
+        dim3 rg((PN_PART + 255) / 256, 4);
+        k_pnet_reduce<<<rg, 256, 0, N->stream>>>(N->part, N->ncta, N->grad);
+        N->launches++;
+        pack(N, 1, lr);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return pn_status(e);
+    if (loss) {
+        e = cudaMemcpyAsync(N->sc_host, N->sc, 3 * sizeof(double), cudaMemcpyDeviceToHost, N->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(N->stream);
+        if (e != cudaSuccess) return pn_status(e);
+        *loss = N->sc_host[2];
+        if (!std::isfinite(*loss)) return FLUPS_ENONFINITE;
+    }
+    return FLUPS_OK;
+}
+
+flups_status flups_pnet_train_step(flups_pnet N, const double* rho, double rho0, const double* p_n,
+                                   const double* p_nm1, const double* p_next, float lr, double* loss) {
+    return pnet_loss(N, rho, rho0, p_n, p_nm1, p_next, 1, lr, loss);
+}
+
+flups_status flups_pnet_eval_loss(flups_pnet N, const double* rho, double rho0, const double* p_n,
+                                  const double* p_nm1, const double* p_next, double* loss) {
+    if (!loss) return FLUPS_EINVAL;
+    return pnet_loss(N, rho, rho0, p_n, p_nm1, p_next, 0, 0.0f, loss);
+}
+
+unsigned long long flups_pnet_launch_count(flups_pnet N) { return N ? N->launches : 0; }
+
+}  // extern "C"

@@ -27,8 +27,12 @@ SYMBOLS = [
     "flups_set_profiling", "flups_profile_read", "flups_kernel_name",
     "flups_solve_graphable", "flups_solve_result",
     "flups_batch_create", "flups_batch_solve", "flups_batch_destroy", "flups_batch_graph_kernels",
-    "flups_batch_member_tuning", "flups_last_cuda_error",
+    "flups_batch_member_tuning", "flups_last_cuda_error", "flups_varcoef_solve",
+    "flups_pnet_create", "flups_pnet_destroy", "flups_pnet_set_params", "flups_pnet_get_params",
+    "flups_pnet_get_grads", "flups_pnet_predict", "flups_pnet_train_step", "flups_pnet_eval_loss",
+    "flups_pnet_launch_count",
 ]
+PNET_NPARAMS = 15601
 NKERNELS = 18
 
 
@@ -85,6 +89,18 @@ def lib():
         L.flups_batch_graph_kernels.argtypes = [P]
         L.flups_batch_graph_kernels.restype = ctypes.c_ulonglong
         L.flups_batch_member_tuning.argtypes = [P, I, IP, IP]
+        L.flups_varcoef_solve.argtypes = [P, V, V, V, D, I, ctypes.POINTER(Info)]
+        FP = ctypes.POINTER(ctypes.c_float)
+        L.flups_pnet_create.argtypes = [ctypes.POINTER(P), I, I, I, FP, V]
+        L.flups_pnet_destroy.argtypes = [P]
+        L.flups_pnet_set_params.argtypes = [P, FP]
+        L.flups_pnet_get_params.argtypes = [P, FP]
+        L.flups_pnet_get_grads.argtypes = [P, FP]
+        L.flups_pnet_predict.argtypes = [P, V, D, V, V, V]
+        L.flups_pnet_train_step.argtypes = [P, V, D, V, V, V, ctypes.c_float, DP]
+        L.flups_pnet_eval_loss.argtypes = [P, V, D, V, V, V, DP]
+        L.flups_pnet_launch_count.argtypes = [P]
+        L.flups_pnet_launch_count.restype = ctypes.c_ulonglong
         L.flups_last_cuda_error.argtypes = []
         L.flups_last_cuda_error.restype = ctypes.c_char_p
         L.flups_kernel_name.argtypes = [I]
@@ -93,7 +109,8 @@ def lib():
         L.flups_status_string.restype = ctypes.c_char_p
         for name in SYMBOLS:
             if name not in ("flups_status_string", "flups_workspace_bytes", "flups_launch_count",
-                            "flups_kernel_name", "flups_batch_graph_kernels", "flups_last_cuda_error"):
+                            "flups_kernel_name", "flups_batch_graph_kernels", "flups_last_cuda_error",
+                            "flups_pnet_launch_count"):
                 getattr(L, name).restype = I
         _lib = L
     return _lib
@@ -224,6 +241,15 @@ class Plan:
         _check(lib().flups_correct(self._h, ptr(p), ptr(pn), ptr(pnm1), float(c1), float(c2), float(dt),
                                    ptr(u), ptr(v), ptr(w)), "flups_correct")
 
+    def varcoef_solve(self, rho, f, p, rtol=1e-12, max_iter=500, check=True):
+        """Exact variable-coefficient pressure D((rho0/rho_f) G p) = f - <f> (PCG)."""
+        inf = Info()
+        st = lib().flups_varcoef_solve(self._h, ptr(rho), ptr(f), ptr(p), float(rtol), int(max_iter),
+                                       ctypes.byref(inf))
+        if check:
+            _check(st, "flups_varcoef_solve")
+        return inf if check else (st, inf)
+
     def project_host(self, u, v, w, rho, pn, pnm1, c1, c2, dt, p_out, rtol=1e-10, max_iter=16):
         """Whole projection on HOST numpy arrays (u, v, w updated in place; p_out written)."""
         inf = Info()
@@ -310,3 +336,78 @@ class Batch:
         _check(lib().flups_batch_member_tuning(self._h, int(m), ctypes.byref(a), ctypes.byref(b)),
                "flups_batch_member_tuning")
         return a.value, b.value
+
+
+def _fparams(params):
+    a = np.ascontiguousarray(np.asarray(params, dtype=np.float32).ravel())
+    if a.size != PNET_NPARAMS:
+        raise ValueError(f"expected {PNET_NPARAMS} parameters, got {a.size}")
+    return a
+
+
+class PNet:
+    """Learned splitting-pressure net on one periodic grid (flups_pnet_*).
+
+    params: FLUPS_PNET_NPARAMS floats, per layer W[out][in][27] then b[out]."""
+
+    def __init__(self, nx, ny, nz, params, stream=None):
+        self.shape = (nz, ny, nx)
+        if stream is None:
+            stream = current_stream()
+        a = _fparams(params)
+        h = ctypes.c_void_p()
+        st = lib().flups_pnet_create(ctypes.byref(h), int(nx), int(ny), int(nz),
+                                     a.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), stream)
+        _check(st, "flups_pnet_create")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            lib().flups_pnet_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    __del__ = close
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    @property
+    def launches(self):
+        return lib().flups_pnet_launch_count(self._h)
+
+    def set_params(self, params):
+        a = _fparams(params)
+        _check(lib().flups_pnet_set_params(self._h, a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))),
+               "flups_pnet_set_params")
+
+    def params(self):
+        a = np.empty(PNET_NPARAMS, np.float32)
+        _check(lib().flups_pnet_get_params(self._h, a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))),
+               "flups_pnet_get_params")
+        return a
+
+    def grads(self):
+        a = np.empty(PNET_NPARAMS, np.float32)
+        _check(lib().flups_pnet_get_grads(self._h, a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))),
+               "flups_pnet_get_grads")
+        return a
+
+    def predict(self, rho, rho0, pn, pnm1, p_hat):
+        _check(lib().flups_pnet_predict(self._h, ptr(rho), float(rho0), ptr(pn), ptr(pnm1), ptr(p_hat)),
+               "flups_pnet_predict")
+
+    def train_step(self, rho, rho0, pn, pnm1, pnext, lr, want_loss=True):
+        loss = ctypes.c_double()
+        _check(lib().flups_pnet_train_step(self._h, ptr(rho), float(rho0), ptr(pn), ptr(pnm1), ptr(pnext),
+                                           float(lr), ctypes.byref(loss) if want_loss else None),
+               "flups_pnet_train_step")
+        return loss.value if want_loss else None
+
+    def eval_loss(self, rho, rho0, pn, pnm1, pnext):
+        loss = ctypes.c_double()
+        _check(lib().flups_pnet_eval_loss(self._h, ptr(rho), float(rho0), ptr(pn), ptr(pnm1), ptr(pnext),
+                                          ctypes.byref(loss)), "flups_pnet_eval_loss")
+        return loss.value

@@ -10,6 +10,11 @@ and the z grid, with the shapes and structure of the paper's workloads:
   * two_layer   - a heavy layer under a light one between walls with a perturbed flat
                   interface and tanh-stretched z, the shape of the two-layer
                   Rayleigh-Benard run (Sec. 7.2: 1024x1024x512, aspect ratio 2, walls in z).
+  * droplet_density + velocity_series - windows of a time series for the learned p_hat:
+                  a fixed droplet field (density ratio 20) and a velocity predictor that
+                  evolves as an AR(1) sequence u^{m+1} = a u^m + sqrt(1 - a^2) xi with smooth
+                  (Gaussian-filtered) noise xi; the pressures of the series are computed by
+                  the library's exact variable-coefficient solve, not here.
 
 Density follows the one-fluid rule rho = rho_1 phi + rho_2 (1 - phi) (Eq. material_prop)
 with a tanh volume-fraction profile of width 1.5 cells:
@@ -22,7 +27,8 @@ numpy PCG64 generator keyed by a fixed seed per field.
 
 import numpy as np
 
-__all__ = ["Case", "stretched_dzf", "sphere", "emulsion", "two_layer", "ensemble_member", "random_fields"]
+__all__ = ["Case", "stretched_dzf", "sphere", "emulsion", "two_layer", "ensemble_member", "random_fields",
+           "droplet_density", "smooth_noise", "velocity_series"]
 
 
 class Case(dict):
@@ -230,3 +236,61 @@ def random_fields(nx, ny, nz, bc="periodic", stretched=False, lx=1.0, ly=1.3, lz
     pnm1 = r.uniform(-1.0, 1.0, (nz, ny, nx))
     return Case(u=u, v=v, w=w, rho=np.ascontiguousarray(rho), pn=pn, pnm1=pnm1, dt=dt, dx=dx, dy=dy,
                 dzf=dzf, lz=lz, bc=bc, name=f"random{nx}x{ny}x{nz}_{bc}{'_str' if stretched else ''}")
+
+
+def droplet_density(n, ndrops, rmin_cells, rmax_cells, ratio, seed):
+    """Density of `ndrops` droplets (density `ratio`) in a carrier of density 1, n^3 periodic."""
+    h = 1.0 / n
+    centres, radii = _place_droplets(_rng(seed), ndrops, rmin_cells * h, rmax_cells * h, 2.0 * h)
+    phi = _droplet_phi(n, h, centres, radii)
+    return np.ascontiguousarray(ratio * phi + (1.0 - phi))
+
+
+_FILTERS = {}
+
+
+def _gauss_filter(n, sigma_cells):
+    key = (n, sigma_cells)
+    if key not in _FILTERS:
+        k = 2.0 * np.pi * np.fft.fftfreq(n)
+        kr = 2.0 * np.pi * np.fft.rfftfreq(n)
+        k2 = k[:, None, None] ** 2 + k[None, :, None] ** 2 + kr[None, None, :] ** 2
+        _FILTERS[key] = np.exp(-0.5 * sigma_cells ** 2 * k2)
+    return _FILTERS[key]
+
+
+def smooth_noise(rng, n, sigma_cells):
+    """Periodic N(0,1) white noise filtered by a Gaussian of standard deviation `sigma_cells`
+    cells (applied as exp(-sigma^2 |k|^2 / 2) in Fourier space), rescaled to unit rms."""
+    import scipy.fft as sfft
+    x = rng.standard_normal((n, n, n))
+    y = sfft.irfftn(sfft.rfftn(x, workers=-1) * _gauss_filter(n, sigma_cells), s=x.shape, axes=(0, 1, 2),
+                    workers=-1)
+    return np.ascontiguousarray(y / np.sqrt(np.mean(y * y)))
+
+
+def velocity_series(n, steps, seed, a=0.95, sigma_cells=2.0):
+    """Yields `steps` velocity predictors (u, v, w) of an AR(1) sequence started in its
+    stationary state: u^0 = xi_0, u^{m+1} = a u^m + sqrt(1 - a^2) xi_{m+1}, per component."""
+    rng = _rng(seed)
+    b = np.sqrt(1.0 - a * a)
+    cur = [smooth_noise(rng, n, sigma_cells) for _ in range(3)]
+    for m in range(steps):
+        if m:
+            cur = [a * c + b * smooth_noise(rng, n, sigma_cells) for c in cur]
+        yield tuple(cur)
+
+
+def learned_window(kind, w, n=None):
+    """Window w of the learned-p_hat workload: (rho, velocity-series seed, n, dt).
+
+    kind "train": 64^3, 50 droplets of radius U[2, 6] cells (seeds (30, w) and (31, w));
+    kind "infer": 128^3, 50 droplets of radius U[4, 12] cells (seeds (32, w) and (33, w)).
+    Density ratio 20 in both."""
+    if kind == "train":
+        n = n or 64
+        rho = droplet_density(n, 50, 2.0, 6.0, 20.0, [30, w])
+        return rho, [31, w], n, 1e-3
+    n = n or 128
+    rho = droplet_density(n, 50, 4.0, 12.0, 20.0, [32, w])
+    return rho, [33, w], n, 1e-3
