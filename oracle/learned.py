@@ -19,7 +19,8 @@ Two plain FP64 pieces:
   stores values: each layer's input (features, hidden activations) on the way forward and
   each layer's output gradient on the way back; with rnd=None everything stays FP64.
 * The splitting error of a p_hat (the measure the linear extrapolation is judged by):
-  e_p = ||p_split - p_ex|| / ||p_ex|| and e_u = ||u_split - u_ex|| / ||u_ex - u**|| with
+  e_p = ||p_split - p_ex|| / ||p_ex||, e_u = ||u_split - u_ex|| / ||u_ex|| and, relative to
+  the size of the pressure correction, e_du = ||u_split - u_ex|| / ||u_ex - u**||, with
   u_ex = u** - (dt/rho_f) G p_ex the exactly projected velocity.
 
 Parity of the learned predictor with the paper is unpinned: the paper has no learned p_hat.
@@ -192,7 +193,7 @@ def adam_update(param, grad_, m, v, step, lr, b1=0.9, b2=0.999, eps=1e-8):
 # ------------------------------------------------------------------ splitting error
 
 def split_error(u, v, w, rho, p_hat, dt, g, p_ex=None):
-    """(e_p, e_u, p_split, p_ex) for the split projection with predictor p_hat."""
+    """(e_p, e_u, e_du, p_split, p_ex) for the split projection with predictor p_hat."""
     rho0 = min_density(rho)
     z = np.zeros_like(p_hat)
     if p_ex is None:
@@ -204,5 +205,6 @@ def split_error(u, v, w, rho, p_hat, dt, g, p_ex=None):
     ue = correct(u, v, w, p_ex, p_ex, z, rho, 1.0, 0.0, dt, g)
     e_p = np.linalg.norm(ps - p_ex) / np.linalg.norm(p_ex)
     num = sum(np.linalg.norm(a - b) ** 2 for a, b in zip(us, ue))
-    den = sum(np.linalg.norm(a - b) ** 2 for a, b in zip(ue, (u, v, w)))
-    return float(e_p), float(np.sqrt(num / den)), ps, p_ex
+    den_u = sum(np.linalg.norm(a) ** 2 for a in ue)
+    den_du = sum(np.linalg.norm(a - b) ** 2 for a, b in zip(ue, (u, v, w)))
+    return float(e_p), float(np.sqrt(num / den_u)), float(np.sqrt(num / den_du)), ps, p_ex

@@ -120,17 +120,17 @@ def test_bf16_rounding_against_float32_bits():
 def test_splitting_error_vanishes_for_exact_pressure_and_constant_density():
     c = synth.sphere(12)
     g = grid_of(c)
-    e_p, e_u, ps, p_ex = L.split_error(c.u, c.v, c.w, c.rho, c.pn, c.dt, g)
-    assert e_p > 1e-3                                         # a random p_hat is far off
-    e_p0, e_u0, _, _ = L.split_error(c.u, c.v, c.w, c.rho, p_ex, c.dt, g, p_ex)
-    assert e_p0 <= 1e-10 and e_u0 <= 1e-10
+    e_p, e_u, e_du, ps, p_ex = L.split_error(c.u, c.v, c.w, c.rho, c.pn, c.dt, g)
+    assert e_p > 1e-3 and e_du > e_u > 0.0                    # a random p_hat is far off
+    e_p0, e_u0, e_du0, _, _ = L.split_error(c.u, c.v, c.w, c.rho, p_ex, c.dt, g, p_ex)
+    assert e_p0 <= 1e-10 and e_u0 <= 1e-10 and e_du0 <= 1e-10
     # u_ex is divergence free
     z = np.zeros_like(p_ex)
     ue = oracle.correct(c.u, c.v, c.w, p_ex, p_ex, z, c.rho, 1.0, 0.0, c.dt, g)
     assert np.max(np.abs(oracle.div(*ue, g))) <= 1e-9 * np.max(np.abs(oracle.div(c.u, c.v, c.w, g)))
     # constant density: the split is exact whatever p_hat is
     rho1 = np.full(c.shape, 3.0)
-    e_p1, e_u1, _, _ = L.split_error(c.u, c.v, c.w, rho1, c.pn, c.dt, g)
+    e_p1, e_u1, e_du1, _, _ = L.split_error(c.u, c.v, c.w, rho1, c.pn, c.dt, g)
     assert e_p1 <= 1e-12 and e_u1 <= 1e-12
 
 
