@@ -220,6 +220,8 @@ def run_ours(args, rank, world, dev):
     out = {"c": c, "npts": npts, "res": res, "t32": t32, "t64": t64, "clocks": clk.summary(), "prof": prof}
     if not args.no_ensemble:
         out["ensemble"] = run_ensemble(args)
+    if not args.no_learned:
+        out["learned"] = run_learned(args)
 
     # end to end: the same projection through flups_project_host on pinned host buffers
     if not args.no_e2e:
@@ -253,15 +255,21 @@ def run_ensemble(args):
     and z walls, density ratios in [1, 20]) as one CUDA graph launch, timed over K replays."""
     import torch
 
-    import oracle
     from paper_2204_08834_gb300 import flups, synth
 
     cases = [synth.ensemble_member(m) for m in range(64)]
     fs = []
+    stream = torch.cuda.current_stream().cuda_stream
     for cm in cases:
+        # each member's right-hand side from its own fields by the library's rhs kernel
+        d = {k: torch.from_numpy(cm[k]).cuda() for k in ("u", "v", "w", "rho", "pn", "pnm1")}
+        f = torch.empty_like(d["u"])
         nz_, ny_, nx_ = cm.shape
-        g = oracle.make_grid(nx_, ny_, nz_, cm.dx, cm.dy, cm.dzf, cm.bc)
-        fs.append(torch.from_numpy(oracle.rhs(cm.u, cm.v, cm.w, cm.rho, cm.pn, cm.pnm1, 2.0, 1.0, cm.dt, g)).cuda())
+        with flups.Plan(nx_, ny_, nz_, cm.dx, cm.dy, cm.dzf, cm.bc, "fp32_refine", stream) as plan:
+            plan.set_density(d["rho"])
+            plan.rhs(d["u"], d["v"], d["w"], d["pn"], d["pnm1"], 2.0, 1.0, cm.dt, f)
+            torch.cuda.synchronize()
+        fs.append(f)
     ps = [torch.empty_like(f) for f in fs]
     pts = sum(cm.npts for cm in cases)
     specs = [(cm.shape[2], cm.shape[1], cm.shape[0], cm.dx, cm.dy, cm.dzf, cm.bc) for cm in cases]
@@ -284,6 +292,96 @@ def run_ensemble(args):
             "mpts_per_s": round(pts / (ms * 1e-3) / 1e6, 2), "graph_kernels": int(kernels),
             "max_rel_res": max(i.rel_res for i in infos), "autotune_s": round(t_tune, 2),
             "sizes": "{32,48,64,96,128}^3, periodic (even m) / z walls (odd m), density ratio U[1,20]"}
+
+
+# Algorithmic flops per grid point of the learned p_hat's convolutions (FMA = 2): 27 taps x
+# inputs x outputs x 2 per layer; layer 1 has 3 inputs (the kernel pads them to 16).
+PNET_FLOPS = {"hidden": 2 * 27 * (3 * 16 + 16 * 16 + 16 * 16), "out": 2 * 27 * 16}
+
+
+def run_learned(args):
+    """The learned p_hat workload: exact variable-coefficient pressures of 64^3 windows (20
+    samples each, 90 % train / 10 % validation), Adam training, then 128^3 inference with the
+    splitting error of the learned and the linear predictors."""
+    import torch
+
+    from paper_2204_08834_gb300 import flups, learned
+
+    nwin = args.learned_windows
+    nval = max(1, nwin // 10)
+    t0 = time.perf_counter()
+    wins = [learned.make_window("train", w, 22)[0] for w in range(nwin)]
+    torch.cuda.synchronize()
+    t_data = time.perf_counter() - t0
+    train_w, val_w = wins[:nwin - nval], wins[nwin - nval:]
+    nsamp = sum(len(w.p) - 2 for w in train_w)
+    steps = args.learned_epochs * nsamp
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with flups.PNet(64, 64, 64, learned.init_params()) as net:
+        learned.train(net, train_w[:1], 3, lr=0.0)                 # warm-up, no change to the weights
+        net.set_params(learned.init_params())
+        e0.record()
+        learned.train(net, train_w, steps, lr=1e-3)
+        e1.record()
+        torch.cuda.synchronize()
+        train_ms = e0.elapsed_time(e1)
+        l_net, l_lin = learned.eval_losses(net, val_w)
+        params = net.params()
+    del wins, train_w, val_w
+    win, dt = learned.make_window("infer", 0, 6, keep_velocity=True)
+    n = win.rho.shape[0]
+    npts = win.rho.numel()
+    ph = torch.empty_like(win.rho)
+    with flups.PNet(n, n, n, params) as net, \
+            flups.Plan(n, n, n, 1.0 / n, 1.0 / n, np.full(n, 1.0 / n), "periodic", "fp64",
+                       torch.cuda.current_stream().cuda_stream) as plan:
+        plan.set_density(win.rho)
+        errs = learned.compare_predictors(net, win, dt, plan)
+        reps = max(args.steps, 10)
+        for _ in range(3):
+            net.predict(win.rho, win.rho0, win.p[1], win.p[0], ph)
+        l0 = net.launches
+        e0.record()
+        for _ in range(reps):
+            net.predict(win.rho, win.rho0, win.p[1], win.p[0], ph)
+        e1.record()
+        torch.cuda.synchronize()
+        pred_ms = e0.elapsed_time(e1) / reps
+        launches = (net.launches - l0) / reps
+        net.set_profiling(True)
+        for _ in range(reps):
+            net.predict(win.rho, win.rho0, win.p[1], win.p[0], ph)
+        prof = {k: (ms / reps, c / reps) for k, (ms, c) in net.profile().items()}
+        net.set_profiling(False)
+    pk, pk_kind = peaks()
+    hid_ms = prof["k_pnet_conv_hidden"][0]
+    achieved = PNET_FLOPS["hidden"] * npts / (hid_ms * 1e-3) / 1e12
+    mean = lambda k, i: float(np.mean([e[i] for e in errs[k]]))
+    return {
+        "workload": "learned p_hat: 64^3 training windows (50 droplets r U[2,6] cells, density ratio 20, "
+                    "AR(1) velocity a = 0.95, smooth noise sigma 2 cells), 128^3 inference window (50 droplets "
+                    "r U[4,12] cells); pressures from the exact variable-coefficient PCG solve to 1e-12",
+        "samples": {"train": nsamp, "validation": nval * 20, "windows": nwin},
+        "data_gen_s": round(t_data, 2),
+        "train": {"steps": steps, "epochs": args.learned_epochs, "ms_per_step": round(train_ms / steps, 4),
+                  "samples_per_s": round(steps / (train_ms * 1e-3), 1),
+                  "mpts_per_s": round(steps * 64 ** 3 / (train_ms * 1e-3) / 1e6, 1)},
+        "val_loss": {"net": round(l_net, 5), "linear": round(l_lin, 5)},
+        "splitting_error_128": {"p_net": round(mean("net", 0), 5), "p_linear": round(mean("lin", 0), 5),
+                                "u_net": round(mean("net", 1), 7), "u_linear": round(mean("lin", 1), 7),
+                                "du_net": round(mean("net", 2), 5), "du_linear": round(mean("lin", 2), 5),
+                                "steps": len(errs["net"]),
+                                "definition": "e_p = |p_split - p_ex| / |p_ex|, e_u = |u_split - u_ex| / |u_ex|, "
+                                              "e_du = |u_split - u_ex| / |u_ex - u**| (2-norms, mean over steps)"},
+        "inference": {"grid": [n, n, n], "ms": round(pred_ms, 4), "mpts_per_s": round(npts / (pred_ms * 1e-3) / 1e6, 1),
+                      "gpu_launches": launches,
+                      "kernels_ms": {k: round(v[0], 4) for k, v in prof.items()}},
+        "roofline": {"kernel": "k_pnet_conv_hidden (3 launches per inference)", "bound": "tensor",
+                     "achieved": round(achieved, 2), "peak": pk["bf16_tflops"], "unit": "TFLOP/s",
+                     "frac": round(achieved / pk["bf16_tflops"], 4), "traffic": None,
+                     "algorithmic": f"{PNET_FLOPS['hidden']} flops/pt (layers 3->16, 16->16, 16->16)",
+                     "peak_source": f"MEASURED_PEAKS.json bf16_tflops ({pk_kind}); mma.sync bf16 path"},
+    }
 
 
 def cpu_baseline():
@@ -347,6 +445,10 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-ensemble", action="store_true")
+    ap.add_argument("--no-learned", action="store_true")
+    ap.add_argument("--learned-windows", type=int, default=100,
+                    help="64^3 training windows of 20 samples (default 100: 2000 samples)")
+    ap.add_argument("--learned-epochs", type=int, default=3)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -453,6 +555,8 @@ def main():
                        "steps": ne, "call": "flups_project_host (pinned host buffers)"}
     if "ensemble" in out:
         line["ensemble"] = out["ensemble"]
+    if "learned" in out:
+        line["learned"] = out["learned"]
     if world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line))

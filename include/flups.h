@@ -291,6 +291,10 @@ flups_status flups_varcoef_solve(flups_plan plan, const double* rho, const doubl
  *                      the Adam state; both synchronise.
  * flups_pnet_get_grads - the parameter gradient of the last train step (HOST); synchronises.
  * flups_pnet_launch_count - kernels this net has launched so far.
+ * flups_pnet_set_profiling / profile_read / kernel_name - optional CUDA-event timing of the
+ *                      net's kernel groups (FLUPS_PNET_NKERNELS entries: features, hidden
+ *                      convolutions, output convolution, backward-data convolutions, weight
+ *                      gradients, update), as flups_set_profiling for plans.
  * Every call runs on the stream given at create.
  */
 #define FLUPS_PNET_NPARAMS 15601
@@ -307,6 +311,18 @@ flups_status flups_pnet_train_step(flups_pnet net, const double* rho, double rho
 flups_status flups_pnet_eval_loss(flups_pnet net, const double* rho, double rho0, const double* p_n,
                                   const double* p_nm1, const double* p_next, double* loss);
 unsigned long long flups_pnet_launch_count(flups_pnet net);
+#define FLUPS_PNET_NKERNELS 6
+flups_status flups_pnet_set_profiling(flups_pnet net, int on);
+flups_status flups_pnet_profile_read(flups_pnet net, double* ms, long long* n);
+const char* flups_pnet_kernel_name(int id);
+
+/* flups_selftest_wait_timeout - diagnostic of the library's failure detection (no paper
+ * counterpart): launches one kernel whose thread waits, through the same bounded wait the
+ * pipelined transform passes use, on an mbarrier that nothing ever arrives at, with `limit`
+ * polls (1 .. 2^20).  The wait gives up, the kernel records the time-out in a device error
+ * word and returns, and the call returns FLUPS_ETIMEOUT with the context still usable
+ * (FLUPS_OK would mean the wait did not time out).  Synchronises `stream`. */
+flups_status flups_selftest_wait_timeout(void* stream, int limit);
 
 /* flups_status_string - static, human-readable name of a status code. */
 const char* flups_status_string(int status);

@@ -592,10 +592,22 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long* m, unsigned pa
         : "=r"(ok) : "r"(smem_u32(m)), "r"(parity) : "memory");
     return ok != 0;
 }
-__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* m, unsigned parity) {
-    for (int i = 0; i < (1 << 22); ++i)
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* m, unsigned parity, int limit = 1 << 22) {
+    for (int i = 0; i < limit; ++i)
         if (mbar_try_wait(m, parity)) return true;
     return false;
+}
+
+// Self-test of the bounded wait above: one thread waits on an mbarrier that nothing ever
+// arrives at, gives up after `limit` polls, records err = 3 and returns (no trap, no hang).
+__global__ void k_selftest_wait(int limit, int* __restrict__ err) {
+    __shared__ __align__(8) unsigned long long m;
+    if (threadIdx.x == 0) mbar_init(&m, 1);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (!mbar_wait_bounded(&m, 0, limit)) atomicExch(err, 3);
+        asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(&m)) : "memory");
+    }
 }
 
 // KIND 0: y transform (INV picks the direction); KIND 1: periodic z solve.
@@ -1134,4 +1146,23 @@ cudaError_t launch_solve32_fixed(flups_plan P, const double* f, double* p, doubl
     }
     P->skip_ptr = nullptr;
     return cudaGetLastError();
+}
+
+extern "C" flups_status flups_selftest_wait_timeout(void* stream, int limit) {
+    if (limit < 1 || limit > (1 << 20)) return FLUPS_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    int* err = nullptr;
+    cudaError_t e = cudaMalloc(&err, sizeof(int));
+    if (e != cudaSuccess) { flups_note_cuda_error(e); return FLUPS_ENOMEM; }
+    int h = 0;
+    e = cudaMemsetAsync(err, 0, sizeof(int), s);
+    if (e == cudaSuccess) {
+        k_selftest_wait<<<1, 32, 0, s>>>(limit, err);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(err);
+    if (e != cudaSuccess) { flups_note_cuda_error(e); return FLUPS_ECUDA; }
+    return h ? FLUPS_ETIMEOUT : FLUPS_OK;
 }

@@ -28,6 +28,7 @@
 #include <cuda_bf16.h>
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 
@@ -429,9 +430,34 @@ struct flups_pnet_s {
     void* base;
     int step;
     unsigned long long launches;
+    // optional per-kernel timing (flups_pnet_set_profiling)
+    int prof_on, prof_n, prof_cap, prof_open;
+    cudaEvent_t* prof_ev;
+    int* prof_kid;
+    double prof_ms[FLUPS_PNET_NKERNELS];
+    long long prof_cnt[FLUPS_PNET_NKERNELS];
 };
 
+static const char* kPnetKernelNames[FLUPS_PNET_NKERNELS] = {
+    "k_pnet_features", "k_pnet_conv_hidden", "k_pnet_conv_out", "k_pnet_conv_bwd", "k_pnet_wgrad", "k_pnet_update"};
+
 namespace {
+
+enum { PK_FEATURES = 0, PK_CONV_HIDDEN, PK_CONV_OUT, PK_CONV_BWD, PK_WGRAD, PK_UPDATE };
+
+void pk_begin(flups_pnet N, int kid) {
+    N->prof_open = 0;
+    if (!N->prof_on || N->prof_n >= N->prof_cap) return;
+    if (cudaEventRecord(N->prof_ev[2 * N->prof_n], N->stream) != cudaSuccess) return;
+    N->prof_kid[N->prof_n] = kid;
+    N->prof_open = 1;
+}
+
+void pk_end(flups_pnet N) {
+    if (!N->prof_open) return;
+    N->prof_open = 0;
+    if (cudaEventRecord(N->prof_ev[2 * N->prof_n + 1], N->stream) == cudaSuccess) N->prof_n++;
+}
 
 struct PnGuard {
     int prev = -1;
@@ -475,7 +501,9 @@ ConvArgs conv_args(flups_pnet N) {
 
 template <int NT, int EPI>
 void conv(flups_pnet N, const ConvArgs& a) {
+    pk_begin(N, EPI == 0 ? PK_CONV_HIDDEN : (EPI == 3 ? PK_CONV_BWD : PK_CONV_OUT));
     k_pnet_conv<NT, EPI><<<N->ncta, THREADS, CONV_SMEM, N->stream>>>(a);
+    pk_end(N);
     N->launches++;
 }
 
@@ -486,17 +514,21 @@ void pack(flups_pnet N, int adam, float lr) {
         bc1 = (float)(1.0 / (1.0 - std::pow(0.9, N->step)));
         bc2 = (float)(1.0 / (1.0 - std::pow(0.999, N->step)));
     }
+    pk_begin(N, PK_UPDATE);
     k_pnet_adam_pack<<<(PN_NP + 255) / 256, 256, 0, N->stream>>>(N->w, N->m, N->v, N->grad, adam, lr, bc1, bc2, N->wf,
                                                                  N->wb);
+    pk_end(N);
     N->launches++;
 }
 
 // features + layers 1..3 (hidden activations)
 void forward_hidden(flups_pnet N, const double* rho, double rho0, const double* pn, const double* pnm1) {
     cudaStream_t s = N->stream;
+    pk_begin(N, PK_FEATURES);
     k_pnet_sumsq<<<N->nred, THREADS, 0, s>>>(pn, N->n, N->red);
     k_pnet_fin<<<1, 1024, 0, s>>>(N->red, N->nred, N->sc, 0, 1.0 / (double)N->n);
     k_pnet_features<<<N->nred, THREADS, 0, s>>>(rho, rho0, pn, pnm1, N->sc, N->n, N->feat);
+    pk_end(N);
     N->launches += 3;
     const __nv_bfloat16* in = N->feat;
     for (int l = 0; l < 3; ++l) {
@@ -511,8 +543,10 @@ void forward_hidden(flups_pnet N, const double* rho, double rho0, const double* 
 }
 
 void wgrad(flups_pnet N, int l, const __nv_bfloat16* dz, const __nv_bfloat16* act) {
+    pk_begin(N, PK_WGRAD);
     k_pnet_wgrad<<<N->ncta, THREADS, WGRAD_SMEM, N->stream>>>(dz, act, N->part + (size_t)l * N->ncta * PN_PART, N->nx,
                                                               N->ny, N->nz);
+    pk_end(N);
     N->launches++;
 }
 
@@ -596,8 +630,57 @@ flups_status flups_pnet_destroy(flups_pnet N) {
     cudaError_t e = cudaStreamSynchronize(N->stream);
     cudaFree(N->base);
     cudaFreeHost(N->sc_host);
+    if (N->prof_ev) {
+        for (int q = 0; q < 2 * N->prof_cap; ++q) cudaEventDestroy(N->prof_ev[q]);
+        std::free(N->prof_ev);
+        std::free(N->prof_kid);
+    }
     delete N;
     return pn_status(e);
+}
+
+flups_status flups_pnet_set_profiling(flups_pnet N, int on) {
+    if (!N) return FLUPS_EINVAL;
+    PnGuard dg(N->dev);
+    if (on && !N->prof_ev) {
+        const int cap = 1024;
+        N->prof_ev = (cudaEvent_t*)std::calloc(2 * cap, sizeof(cudaEvent_t));
+        N->prof_kid = (int*)std::calloc(cap, sizeof(int));
+        if (!N->prof_ev || !N->prof_kid) return FLUPS_ENOMEM;
+        for (int q = 0; q < 2 * cap; ++q)
+            if (cudaEventCreate(&N->prof_ev[q]) != cudaSuccess) return FLUPS_ECUDA;
+        N->prof_cap = cap;
+    }
+    N->prof_on = on ? 1 : 0;
+    N->prof_n = 0;
+    for (int q = 0; q < FLUPS_PNET_NKERNELS; ++q) { N->prof_ms[q] = 0.0; N->prof_cnt[q] = 0; }
+    return FLUPS_OK;
+}
+
+flups_status flups_pnet_profile_read(flups_pnet N, double* ms, long long* n) {
+    if (!N || !ms || !n) return FLUPS_EINVAL;
+    PnGuard dg(N->dev);
+    cudaError_t e = cudaStreamSynchronize(N->stream);
+    if (e != cudaSuccess) return pn_status(e);
+    for (int q = 0; q < N->prof_n; ++q) {
+        float t = 0.f;
+        if (cudaEventElapsedTime(&t, N->prof_ev[2 * q], N->prof_ev[2 * q + 1]) == cudaSuccess) {
+            N->prof_ms[N->prof_kid[q]] += t;
+            N->prof_cnt[N->prof_kid[q]] += 1;
+        }
+    }
+    N->prof_n = 0;
+    for (int q = 0; q < FLUPS_PNET_NKERNELS; ++q) {
+        ms[q] = N->prof_ms[q];
+        n[q] = N->prof_cnt[q];
+        N->prof_ms[q] = 0.0;
+        N->prof_cnt[q] = 0;
+    }
+    return FLUPS_OK;
+}
+
+const char* flups_pnet_kernel_name(int id) {
+    return (id >= 0 && id < FLUPS_PNET_NKERNELS) ? kPnetKernelNames[id] : "unknown";
 }
 
 flups_status flups_pnet_set_params(flups_pnet N, const float* params) {
@@ -662,7 +745,9 @@ static flups_status pnet_loss(flups_pnet N, const double* rho, double rho0, cons
     a.out = N->dy;
     a.gscale = 2.0 / (double)N->n;
     conv<1, 2>(N, a);
+    pk_begin(N, PK_UPDATE);
     k_pnet_fin<<<1, 1024, 0, N->stream>>>(N->red, N->ncta, N->sc, 1, 1.0 / (double)N->n);
+    pk_end(N);
     N->launches++;
     if (train) {
         // dZ of layer l+1's input side: g = conv(dZ_{l+1}, W_{l+1} reversed) masked by act_l > 0
@@ -680,7 +765,9 @@ static flups_status pnet_loss(flups_pnet N, const double* rho, double rho0, cons
         }
         wgrad(N, 0, dzl, N->feat);
         dim3 rg((PN_PART + 255) / 256, 4);
+        pk_begin(N, PK_UPDATE);
         k_pnet_reduce<<<rg, 256, 0, N->stream>>>(N->part, N->ncta, N->grad);
+        pk_end(N);
         N->launches++;
         pack(N, 1, lr);
     }

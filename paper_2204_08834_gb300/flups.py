@@ -30,8 +30,10 @@ SYMBOLS = [
     "flups_batch_member_tuning", "flups_last_cuda_error", "flups_varcoef_solve",
     "flups_pnet_create", "flups_pnet_destroy", "flups_pnet_set_params", "flups_pnet_get_params",
     "flups_pnet_get_grads", "flups_pnet_predict", "flups_pnet_train_step", "flups_pnet_eval_loss",
-    "flups_pnet_launch_count",
+    "flups_pnet_launch_count", "flups_pnet_set_profiling", "flups_pnet_profile_read", "flups_pnet_kernel_name",
+    "flups_selftest_wait_timeout",
 ]
+PNET_NKERNELS = 6
 PNET_NPARAMS = 15601
 NKERNELS = 18
 
@@ -101,6 +103,11 @@ def lib():
         L.flups_pnet_eval_loss.argtypes = [P, V, D, V, V, V, DP]
         L.flups_pnet_launch_count.argtypes = [P]
         L.flups_pnet_launch_count.restype = ctypes.c_ulonglong
+        L.flups_pnet_set_profiling.argtypes = [P, I]
+        L.flups_pnet_profile_read.argtypes = [P, DP, ctypes.POINTER(ctypes.c_longlong)]
+        L.flups_pnet_kernel_name.argtypes = [I]
+        L.flups_pnet_kernel_name.restype = ctypes.c_char_p
+        L.flups_selftest_wait_timeout.argtypes = [V, I]
         L.flups_last_cuda_error.argtypes = []
         L.flups_last_cuda_error.restype = ctypes.c_char_p
         L.flups_kernel_name.argtypes = [I]
@@ -110,7 +117,7 @@ def lib():
         for name in SYMBOLS:
             if name not in ("flups_status_string", "flups_workspace_bytes", "flups_launch_count",
                             "flups_kernel_name", "flups_batch_graph_kernels", "flups_last_cuda_error",
-                            "flups_pnet_launch_count"):
+                            "flups_pnet_launch_count", "flups_pnet_kernel_name"):
                 getattr(L, name).restype = I
         _lib = L
     return _lib
@@ -260,6 +267,13 @@ class Plan:
         return inf
 
 
+def selftest_wait_timeout(limit=4096, stream=None):
+    """Status of flups_selftest_wait_timeout (ETIMEOUT when the bounded wait works)."""
+    if stream is None:
+        stream = current_stream()
+    return lib().flups_selftest_wait_timeout(stream, int(limit))
+
+
 def solve_fp64_noalloc(nx, ny, nz, dx, dy, dzf, bc, f, p, stream=None, check=True):
     """FP64 direct solve without any device allocation (flups_solve_fp64_noalloc).
 
@@ -377,6 +391,16 @@ class PNet:
     @property
     def launches(self):
         return lib().flups_pnet_launch_count(self._h)
+
+    def set_profiling(self, on=True):
+        _check(lib().flups_pnet_set_profiling(self._h, int(bool(on))), "flups_pnet_set_profiling")
+
+    def profile(self):
+        """{kernel group: (total ms, timed regions)} since the last call (synchronises)."""
+        ms = (ctypes.c_double * PNET_NKERNELS)()
+        n = (ctypes.c_longlong * PNET_NKERNELS)()
+        _check(lib().flups_pnet_profile_read(self._h, ms, n), "flups_pnet_profile_read")
+        return {lib().flups_pnet_kernel_name(k).decode(): (ms[k], n[k]) for k in range(PNET_NKERNELS) if n[k]}
 
     def set_params(self, params):
         a = _fparams(params)

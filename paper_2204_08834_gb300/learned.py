@@ -11,7 +11,8 @@ AR(1) series; the pressures p^m of the series are exact variable-coefficient sol
 The splitting error of a predictor p_hat at step n+1 (u** = u^{n+1} of the series):
 p_split = split solve with p_hat, u_split its corrected velocity; against p_ex = p^{n+1} and
 u_ex = u** - (dt/rho_f) G p_ex:  e_p = ||p_split - p_ex|| / ||p_ex||,
-e_u = ||u_split - u_ex|| / ||u_ex - u**||.
+e_u = ||u_split - u_ex|| / ||u_ex||, and relative to the pressure correction itself
+e_du = ||u_split - u_ex|| / ||u_ex - u**||.
 """
 
 import numpy as np
@@ -112,7 +113,7 @@ def eval_losses(net, windows):
 
 
 def splitting_errors(win, m, dt, pn, pnm1, c1, c2, plan):
-    """(e_p, e_u) of the split projection of step m with p_hat = c1 pn - c2 pnm1."""
+    """(e_p, e_u, e_du) of the split projection of step m with p_hat = c1 pn - c2 pnm1."""
     import torch
     u, v, w = win.vel[m]
     f = torch.empty_like(u)
@@ -128,8 +129,9 @@ def splitting_errors(win, m, dt, pn, pnm1, c1, c2, plan):
     pe_h = h(pe)
     e_p = np.linalg.norm(h(p) - pe_h) / np.linalg.norm(pe_h)
     num = sum(np.linalg.norm(h(a) - h(b)) ** 2 for a, b in ((us, ue), (vs, ve), (ws, we)))
-    den = sum(np.linalg.norm(h(a) - h(b)) ** 2 for a, b in ((ue, u), (ve, v), (we, w)))
-    return float(e_p), float(np.sqrt(num / den))
+    den_u = sum(np.linalg.norm(h(a)) ** 2 for a in (ue, ve, we))
+    den_du = sum(np.linalg.norm(h(a) - h(b)) ** 2 for a, b in ((ue, u), (ve, v), (we, w)))
+    return float(e_p), float(np.sqrt(num / den_u)), float(np.sqrt(num / den_du))
 
 
 def compare_predictors(net, win, dt, plan):

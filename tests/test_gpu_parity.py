@@ -236,3 +236,18 @@ def test_profiling_reports_every_launched_kernel():
         assert k in prof and prof[k][0] > 0.0, k
     assert prof["k_xfwd_residual32"][1] == info.iters
     assert prof["k_xinv32"][1] == info.iters
+
+
+def test_bounded_device_wait_reports_timeout():
+    """A device-side wait on a barrier nothing arrives at gives up and returns ETIMEOUT; the
+    context stays usable (a solve right after still matches the oracle)."""
+    assert flups.selftest_wait_timeout(4096) == flups.ETIMEOUT
+    assert flups.selftest_wait_timeout(1) == flups.ETIMEOUT
+    c = synth.sphere(16)
+    f = oracle.rhs(c.u, c.v, c.w, c.rho, c.pn, c.pnm1, 2.0, 1.0, c.dt, grid_of(c))
+    fd = torch.from_numpy(f).cuda()
+    p = torch.empty_like(fd)
+    with flups.Plan.for_case(c, "fp64") as plan:
+        plan.solve(fd, p, rtol=1e-12)
+    po = oracle.solve(f, grid_of(c))
+    assert np.max(np.abs(p.cpu().numpy() - po)) <= 1e-10 * np.max(np.abs(po))
