@@ -62,6 +62,14 @@ KERNEL_WORK = {
 }
 
 
+# DRAM bytes per point of one launch from an ncu capture (dram__bytes_read.sum +
+# dram__bytes_write.sum) of the 256^3 emulsion, scaled to any size by the point count.
+# Only valid for the kernel code that was captured; remove the entry when the kernel changes.
+MEASURED_TRAFFIC_PER_POINT = {
+    "k_xfwd_residual32": (271.137 + 53.565) * 1e6 / 256 ** 3,
+}
+
+
 def make_case(name):
     from paper_2204_08834_gb300 import synth
     w = WORKLOADS[name]
@@ -537,7 +545,10 @@ def main():
             "peak": peak,
             "unit": unit,
             "frac": round(achieved / peak, 4),
-            "traffic": None,
+            "traffic": (round(MEASURED_TRAFFIC_PER_POINT[dom] * npts) if dom in MEASURED_TRAFFIC_PER_POINT
+                        else None),
+            "traffic_note": ("bytes per launch: ncu DRAM read + write of the 256^3 capture scaled by points"
+                             if dom in MEASURED_TRAFFIC_PER_POINT else None),
             "per_launch_ms": round(dom_ms_per_region, 4),
             "peak_source": psrc,
             "algorithmic": {k: v for k, v in work.items() if k != "bound"},
