@@ -165,26 +165,38 @@ __device__ __forceinline__ void fft_tile(C* s, int pitch, int lgB, const FftLen&
 }
 
 // FP64 -> FP32 with round-to-nearest-even, built from the IEEE-754 binary64/binary32
-// layouts with integer operations (on GB300 the F2F conversion instruction runs on the
-// narrow FP64 pipe).  Values outside the normal binary32 range use the hardware conversion.
+// layouts with integer operations only (on GB300 the F2F conversion instruction runs on the
+// narrow FP64 pipe).  Outside the normal binary32 range the result is chosen with integer
+// selects, so no conversion instruction is issued for any lane: |x| < 2^-126 gives a signed
+// zero (binary32 subnormal results are flushed), |x| >= 2^128 and infinities give a signed
+// infinity, NaN gives a quiet NaN.  Rounding up at the top of the range carries into the
+// exponent and gives infinity, as IEEE rounding does.
 __device__ __forceinline__ float d2f_bits(double x) {
     const unsigned long long b = (unsigned long long)__double_as_longlong(x);
     const unsigned int hi = (unsigned int)(b >> 32);
     const int e = (int)((hi >> 20) & 0x7FFu);
-    if (e < 897 || e > 1150) return __double2float_rn(x);
     unsigned int r = ((unsigned int)(e - 896) << 23) | ((unsigned int)(b >> 29) & 0x7FFFFFu);
     const unsigned int rem = (unsigned int)b & 0x1FFFFFFFu;
     r += (rem > 0x10000000u) | ((rem == 0x10000000u) & (r & 1u));
+    const bool nan = e == 2047 && (b & 0xFFFFFFFFFFFFFull) != 0ull;
+    r = e < 897 ? 0u : r;
+    r = e > 1150 ? (nan ? 0x7FC00000u : 0x7F800000u) : r;
     return __uint_as_float(r | (hi & 0x80000000u));
 }
 
-// FP32 -> FP64 (exact) from the bit layouts; zero, subnormal, inf and NaN use the hardware.
+// FP32 -> FP64 (exact for normal numbers) from the bit layouts with integer operations only:
+// zero and binary32 subnormals give a signed zero (flushed), infinities and NaNs keep their
+// class (the low mantissa bits of a NaN stay in the low word).
 __device__ __forceinline__ double f2d_bits(float x) {
     const unsigned int b = __float_as_uint(x);
     const unsigned int e = (b >> 23) & 0xFFu;
-    if (e == 0u || e == 255u) return (double)x;
-    const unsigned int hi = (b & 0x80000000u) | ((e + 896u) << 20) | ((b & 0x7FFFFFu) >> 3);
-    return __hiloint2double((int)hi, (int)((b & 7u) << 29));
+    const unsigned int sg = b & 0x80000000u;
+    unsigned int hi = sg | ((e + 896u) << 20) | ((b & 0x7FFFFFu) >> 3);
+    unsigned int lo = (b & 7u) << 29;
+    hi = e == 0u ? sg : hi;
+    lo = e == 0u ? 0u : lo;
+    hi = e == 255u ? (sg | 0x7FF00000u | ((b & 0x7FFFFFu) >> 3)) : hi;
+    return __hiloint2double((int)hi, (int)lo);
 }
 
 // x * 2^(58 - E) as a 64-bit integer, truncated toward zero, for |x| < 2^E; sh = 1017 + E.
@@ -253,7 +265,7 @@ __device__ void block_sum3(double a, double b, double c, double* __restrict__ pa
 //         2^(58-E), E from the largest exponent of p recorded when p was written), then
 //         r = (f - <f>) - (2^(E-58)/h^2) S with one conversion and one FMA in FP64.
 template <typename T, int E, int MODE, bool STATS>
-__global__ void __launch_bounds__(1024) k_xfwd(const double* __restrict__ f, const double* __restrict__ p,
+__global__ void __launch_bounds__(512) k_xfwd(const double* __restrict__ f, const double* __restrict__ p,
                                                typename cplx<T>::t* __restrict__ S, Geo g, FftLen L,
                                                const typename cplx<T>::t* __restrict__ tw,
                                                const typename cplx<T>::t* __restrict__ twr,
@@ -278,7 +290,37 @@ __global__ void __launch_bounds__(1024) k_xfwd(const double* __restrict__ f, con
         if (pe_ >= 2047) cfix = __longlong_as_double(0x7FF8000000000000LL);           // NaN: p not finite
         else if (pe_ - 57 >= 1) cfix = __hiloint2double((pe_ - 57) << 20, 0) * g.sx;   // 2^(pexp-1080) / h^2
     }
-    for (int idx = tid; idx < B * M; idx += nthr) {
+    // Every thread handles exactly E elements (nthr = B M / E): compile-time trip counts let
+    // the loads of a thread be issued before they are used.
+    if (MODE == 0) {
+        double2 fvs[E];
+#pragma unroll
+        for (int q = 0; q < E; ++q) {
+            const int idx = tid + q * nthr;
+            const int c = idx / M, n = idx - c * M;
+            const int row = row0 + c;
+            fvs[q] = row < nrows ? __ldg(reinterpret_cast<const double2*>(f + (size_t)row * nx) + n)
+                                 : make_double2(0.0, 0.0);
+        }
+#pragma unroll
+        for (int q = 0; q < E; ++q) {
+            const int idx = tid + q * nthr;
+            const int c = idx / M, n = idx - c * M;
+            const int row = row0 + c;
+            const double2 fv = fvs[q];
+            const C z = mk<T>(from_double<T>(fv.x), from_double<T>(fv.y));
+            if (STATS && row < nrows) {
+                const int k = row / g.ny;
+                accw = fma(fv.x + fv.y, __ldg(g.dzf + k), accw);
+                acc2 = fmaf((float)z.x, (float)z.x, fmaf((float)z.y, (float)z.y, acc2));
+                acc1 += (float)z.x + (float)z.y;
+            }
+            s[n * pitch + c] = z;
+        }
+    } else {
+#pragma unroll 2
+    for (int q = 0; q < E; ++q) {
+        const int idx = tid + q * nthr;
         const int c = idx / M, n = idx - c * M;
         const int row = row0 + c;
         C z = mk<T>((T)0, (T)0);
@@ -350,6 +392,7 @@ __global__ void __launch_bounds__(1024) k_xfwd(const double* __restrict__ f, con
         }
         s[n * pitch + c] = z;
     }
+    }
     if (STATS || MODE >= 1) block_sum3(accw, (double)acc2, (double)acc1, part);
     __syncthreads();
     fft_tile<C, E, false>(s, pitch, lgB, L, tw);
@@ -378,7 +421,7 @@ __global__ void __launch_bounds__(1024) k_xfwd(const double* __restrict__ f, con
 // first FP32 iterate, whose rounding leaves a constant of order eps32 |p| that the
 // residual cannot see; SUBM (with ACC = 1) removes that constant in the first update.
 template <typename T, int E, int ACC, bool MEAN, bool SUBM>
-__global__ void __launch_bounds__(1024) k_xinv(const typename cplx<T>::t* __restrict__ S, double* __restrict__ p,
+__global__ void __launch_bounds__(512) k_xinv(const typename cplx<T>::t* __restrict__ S, double* __restrict__ p,
                                                Geo g, FftLen L, const typename cplx<T>::t* __restrict__ tw,
                                                const typename cplx<T>::t* __restrict__ twr, int lgB, int nrows,
                                                DevScalars* __restrict__ sc, double* __restrict__ part) {
@@ -391,16 +434,29 @@ __global__ void __launch_bounds__(1024) k_xinv(const typename cplx<T>::t* __rest
     const int H = M / 2 + 1;
     // Z_k = A_k + i B_k, Z_{M-k} = conj(A_k) + i conj(B_k) with A_k = (X_k + conj X_{M-k})/2,
     // B_k = (X_k - conj X_{M-k}) conj(W_nx^k)/2; X_0 and X_M are taken real.
-    for (int idx = tid; idx < B * H; idx += nthr) {
+    // B H = nthr (E/2) + B elements: at most E/2 + 1 per thread, loaded before use.
+    constexpr int QH = E / 2 + 1;
+    C xks[QH], xms[QH];
+#pragma unroll
+    for (int q = 0; q < QH; ++q) {
+        const int idx = tid + q * nthr;
         const int c = idx / H, k = idx - c * H;
         const int row = row0 + c;
-        C xk = mk<T>((T)0, (T)0), xm = xk;
-        if (row < nrows) {
+        xks[q] = mk<T>((T)0, (T)0);
+        xms[q] = xks[q];
+        if (idx < B * H && row < nrows) {
             const C* in = S + (size_t)row * g.ldS;
-            xk = in[k];
-            xm = in[M - k];
-            if (k == 0) { xk.y = (T)0; xm.y = (T)0; }
+            xks[q] = in[k];
+            xms[q] = in[M - k];
         }
+    }
+#pragma unroll
+    for (int q = 0; q < QH; ++q) {
+        const int idx = tid + q * nthr;
+        if (idx >= B * H) break;
+        const int c = idx / H, k = idx - c * H;
+        C xk = xks[q], xm = xms[q];
+        if (k == 0) { xk.y = (T)0; xm.y = (T)0; }
         const T ax = (xk.x + xm.x) * (T)0.5, ay = (xk.y - xm.y) * (T)0.5;
         const T dx = (xk.x - xm.x) * (T)0.5, dy = (xk.y + xm.y) * (T)0.5;
         const C w = __ldg(&twr[k]);
@@ -415,7 +471,20 @@ __global__ void __launch_bounds__(1024) k_xinv(const typename cplx<T>::t* __rest
     int emax = 0;       // largest binary64 exponent field written (FP32 mode: scale of the next defect)
     T msub = (T)0;
     if (SUBM) msub = (T)sc->mean_p;
-    for (int idx = tid; idx < B * M; idx += nthr) {
+    double2 pold[ACC ? E : 1];
+    if (ACC) {
+#pragma unroll
+        for (int q = 0; q < E; ++q) {
+            const int idx = tid + q * nthr;
+            const int c = idx / M, n = idx - c * M;
+            const int row = row0 + c;
+            pold[q] = row < nrows ? *(reinterpret_cast<const double2*>(p + (size_t)row * nx) + n)
+                                  : make_double2(0.0, 0.0);
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < E; ++q) {
+        const int idx = tid + q * nthr;
         const int c = idx / M, n = idx - c * M;
         const int row = row0 + c;
         if (row >= nrows) continue;
@@ -424,7 +493,7 @@ __global__ void __launch_bounds__(1024) k_xinv(const typename cplx<T>::t* __rest
         double2* dst = reinterpret_cast<double2*>(p + (size_t)row * nx) + n;
         double2 o;
         if (ACC) {
-            o = *dst;
+            o = pold[ACC ? q : 0];
             o.x += to_double<T>(z.x);
             o.y += to_double<T>(z.y);
         } else {
@@ -840,6 +909,10 @@ int pick_lgB(int N, int csize, int E, int bmax, int ncols, int cap) {
     return ilog2i(B);
 }
 
+// Thread cap of the x passes: at most 512 threads, so that their per-thread prefetch
+// registers (E complex values) fit without spills (launch bound 512: up to 128 registers).
+int x_cap(int cta) { return std::min(cta > 0 ? cta : cta_threads(), 512); }
+
 template <typename K> void allow_smem(K kern) {
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 74 * 1024);
 }
@@ -972,7 +1045,7 @@ template <typename T, int E, int MODE, bool STATS>
 void run_xfwd_e(flups_plan P, const double* f, const double* p, const Geo& g) {
     typedef typename cplx<T>::t C;
     const int N = g.M, nrows = g.ny * g.nz;
-    const int lgB = pick_lgB(N, sizeof(C), E, sizeof(T) == 4 ? 32 : 16, nrows, g.cta);
+    const int lgB = pick_lgB(N, sizeof(C), E, sizeof(T) == 4 ? 32 : 16, nrows, x_cap(g.cta));
     const int B = 1 << lgB;
     auto kern = k_xfwd<T, E, MODE, STATS>;
     allow_smem(kern);
@@ -998,7 +1071,7 @@ template <typename T, int E, int ACC, bool MEAN, bool SUBM>
 void run_xinv_e(flups_plan P, double* p, const Geo& g) {
     typedef typename cplx<T>::t C;
     const int N = g.M, nrows = g.ny * g.nz;
-    const int lgB = pick_lgB(N, sizeof(C), E, sizeof(T) == 4 ? 32 : 16, nrows, g.cta);
+    const int lgB = pick_lgB(N, sizeof(C), E, sizeof(T) == 4 ? 32 : 16, nrows, x_cap(g.cta));
     const int B = 1 << lgB;
     auto kern = k_xinv<T, E, ACC, MEAN, SUBM>;
     allow_smem(kern);
@@ -1023,7 +1096,7 @@ void run_xinv(flups_plan P, double* p, const Geo& g) {
 int xfwd_blocks(flups_plan P, int csize, int /*unused*/) {
     const int nrows = P->ny * P->nz;
     const int E = P->M % 3 == 0 ? 12 : (P->M >= 8 ? 8 : 4);
-    const int lgB = pick_lgB(P->M, csize, E, csize == 8 ? 32 : 16, nrows, P->cta_cap);
+    const int lgB = pick_lgB(P->M, csize, E, csize == 8 ? 32 : 16, nrows, x_cap(P->cta_cap));
     return (nrows + (1 << lgB) - 1) >> lgB;
 }
 
