@@ -58,7 +58,7 @@ KERNEL_WORK = {
     "k_ztri32": {"bound": "hbm", "bytes": 4 + 4},
     "k_xinv32": {"bound": "hbm", "bytes": 4 + 12},   # mean of p = (first) and p += (later)
     "k_face_coeffs": {"bound": "hbm", "bytes": 8 + 24},
-    "k_rho_minmax": {"bound": "hbm", "bytes": 8},
+    "k_rho_tiles": {"bound": "hbm", "bytes": 8},
 }
 
 

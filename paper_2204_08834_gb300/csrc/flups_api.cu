@@ -187,9 +187,9 @@ flups_status sync_scalars(flups_plan P) {
 }  // namespace
 
 static const char* kKernelNames[FK_COUNT] = {
-    "k_rho_minmax", "k_face_coeffs", "k_rhs", "k_correct", "k_xfwd_f32", "k_xfwd_residual32", "k_ycol32",
+    "k_rho_tiles", "k_face_coeffs", "k_rhs", "k_correct", "k_xfwd_f32", "k_xfwd_residual32", "k_ycol32",
     "k_zper32", "k_ztri32", "k_xinv32", "k_finalize", "k_xfwd64", "k_ycol64", "k_zper64", "k_ztri64", "k_xinv64",
-    "k_res64", "k_tile_flags"};
+    "k_res64", "k_rho_finalize"};
 
 void flups_prof_begin(flups_plan P, int kid) {
     P->prof_open = 0;
@@ -222,7 +222,7 @@ Geo plan_geo(flups_plan P) {
     g.tnx = P->nx / g.rx;
     g.tny = P->ny / FLUPS_TY;
     g.tnz = (P->nz + FLUPS_KC - 1) / FLUPS_KC;
-    g.tflags = P->tflags;
+    g.trange = P->trange;
     g.skip = P->skip_ptr;
     g.cta = P->cta_cap;
     const int nz = P->nz;
@@ -306,11 +306,17 @@ flups_status flups_plan_create(flups_plan* out, int nx, int ny, int nz, double d
     {
         int rx = 32;
         while (nx % rx) rx >>= 1;
-        P->tflags = (unsigned int*)A.get((size_t)(nx / rx) * (ny / FLUPS_TY) * ((nz + FLUPS_KC - 1) / FLUPS_KC) *
-                                         sizeof(unsigned int));
+        P->trange = (long long*)A.get((size_t)(nx / rx) * (ny / FLUPS_TY) * ((nz + FLUPS_KC - 1) / FLUPS_KC) * 2 *
+                                      sizeof(long long));
     }
     P->sc = (DevScalars*)A.get(sizeof(DevScalars));
-    P->npart = 3 * std::max<size_t>(flups_part_blocks_needed(nx, ny, nz), 2048);
+    {
+        // partials: 3 per x-pass CTA, 2 per stencil tile (density pass), at least 2048 blocks
+        int rx = 32;
+        while (nx % rx) rx >>= 1;
+        const size_t ntiles = (size_t)(nx / rx) * (ny / FLUPS_TY) * ((nz + FLUPS_KC - 1) / FLUPS_KC);
+        P->npart = std::max<size_t>(3 * std::max<size_t>(flups_part_blocks_needed(nx, ny, nz), 2048), 2 * ntiles);
+    }
     P->part = (double*)A.get(P->npart * sizeof(double));
     P->tabs64 = (double*)A.get(6 * (size_t)nz * sizeof(double));
     bool ok = A.ok;

@@ -54,8 +54,9 @@ struct DevScalars {
 
 // Geometry and tables handed to kernels by value.
 // Stencil tiles: a CTA of the rhs/correct kernels covers RX x FLUPS_TY cells of a plane,
-// RX = min(32, nx), and marches up FLUPS_KC planes.  set_density flags every tile in which
-// some face coefficient (1 - rho0/rho_f) that the tile's CTA reads is nonzero.
+// RX = min(32, nx), and marches up FLUPS_KC planes.  set_density records each tile's density
+// range over its cells and one-cell halo; a tile whose range is [rho0, rho0] reads only zero
+// face coefficients (1 - rho0/rho_f) and takes the constant-density path.
 #define FLUPS_TY 8
 #define FLUPS_KC 16
 
@@ -65,7 +66,7 @@ struct Geo {
     double idx, idy;             // 1/dx, 1/dy
     double sx, sy;               // 1/dx^2, 1/dy^2
     int rx, lgrx, tnx, tny, tnz; // stencil tile width (a power of two), its log2, tile counts
-    unsigned int* tflags;        // [tnz][tny][tnx] nonzero: the tile needs the p_hat terms
+    const long long* trange;     // [tnz][tny][tnx][2] density range (bit patterns) of each tile and its halo
     const int* skip;             // refinement kernels return at once when *skip != 0 (may be null)
     int cta;                     // thread cap of the transform CTAs (0: library default)
     const double* idzf;          // [nz] 1/dzf_k
@@ -94,7 +95,7 @@ struct flups_plan_s {
     void* spec;                  // spectrum, float2 or double2
     void* zscr;                  // z Thomas multipliers (walls)
     double* bx; double* by; double* bz;
-    unsigned int* tflags;        // stencil tile flags (see FLUPS_TY)
+    long long* trange;           // stencil tile density ranges (see FLUPS_TY)
     DevScalars* sc;              // device scalars
     DevScalars* sc_host;         // pinned host mirror
     double* part;                // reduction partials

@@ -35,64 +35,116 @@ __device__ __forceinline__ bool rho_bad(double r) {
     return b < 0x39B4484BFEEBC2A0LL || b > 0x46293E5939A08CEALL;   // 1e-30, 1e30
 }
 
-__global__ void k_rho_minmax(const double* __restrict__ rho, size_t n, long long* __restrict__ part) {
-    long long mn = 0x7FFFFFFFFFFFFFFFLL;
+// One CTA per stencil tile (RX x TY cells of a plane, KC planes): the tile's density range
+// over the cells whose values its rhs and correct CTAs read (the tile and its one-cell halo
+// in -x, +x, -y, +y, -z, +z, no edges or corners), as binary64 bit patterns (positive
+// doubles order like their bit patterns, so min and max are integer compares); and, over
+// the tile's own cells only, the partial minimum and the invalid-density flag for rho0.
+// A tile whose range is [rho0, rho0] has every face coefficient (1 - rho0/rho_f) equal to
+// zero.  trange[2t] = min, trange[2t+1] = max; part[2t] = min over own cells, part[2t+1] = bad.
+template <int RX>
+__global__ void __launch_bounds__(RX * FLUPS_TY) k_rho_tiles(const double* __restrict__ rho, Geo g,
+                                                             long long* __restrict__ trange,
+                                                             long long* __restrict__ part) {
+    constexpr int TY = FLUPS_TY, KC = FLUPS_KC;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int i0 = blockIdx.x * RX, j0 = blockIdx.y * TY;
+    const int kb = blockIdx.z * KC, ke = min(kb + KC, g.nz);
+    const int nx = g.nx, ny = g.ny;
+    const int i = i0 + tx, j = j0 + ty;
+    const long long BIG = 0x7FFFFFFFFFFFFFFFLL;
+    long long mn_own = BIG, mn = BIG, mx = -BIG;
     int bad = 0;
-    // four 16-byte loads in flight per thread (n is even: nx is a power of two >= 8)
-    const double2* r2 = reinterpret_cast<const double2*>(rho);
-    const size_t n2 = n / 2, stride = (size_t)gridDim.x * blockDim.x;
-    size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-    for (; i + 3 * stride < n2; i += 4 * stride) {
-        double2 v[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) v[q] = __ldg(r2 + i + q * stride);
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const long long a = __double_as_longlong(v[q].x), b = __double_as_longlong(v[q].y);
-            mn = a < mn ? a : mn;
-            mn = b < mn ? b : mn;
-            bad |= rho_bad(v[q].x) | rho_bad(v[q].y);
+    // x and y halo cells of this thread (lanes at the tile's x edges, rows at its y edges)
+    const int ih = tx == 0 ? wrapm(i0 - 1, nx) : (tx == RX - 1 ? wrapm(i0 + RX, nx) : -1);
+    const int jh = ty == 0 ? wrapm(j0 - 1, ny) : (ty == TY - 1 ? wrapm(j0 + TY, ny) : -1);
+    for (int k = kb; k < ke; ++k) {
+        const size_t pl = (size_t)k * ny;
+        const double r = __ldg(rho + (pl + j) * nx + i);
+        const long long b = __double_as_longlong(r);
+        mn_own = b < mn_own ? b : mn_own;
+        bad |= rho_bad(r);
+        mx = b > mx ? b : mx;
+        if (ih >= 0) {
+            const long long h = __double_as_longlong(__ldg(rho + (pl + j) * nx + ih));
+            mn = h < mn ? h : mn;
+            mx = h > mx ? h : mx;
+        }
+        if (jh >= 0) {
+            const long long h = __double_as_longlong(__ldg(rho + (pl + jh) * nx + i));
+            mn = h < mn ? h : mn;
+            mx = h > mx ? h : mx;
         }
     }
-    for (; i < n2; i += stride) {
-        const double2 v = __ldg(r2 + i);
-        const long long a = __double_as_longlong(v.x), b = __double_as_longlong(v.y);
-        mn = a < mn ? a : mn;
-        mn = b < mn ? b : mn;
-        bad |= rho_bad(v.x) | rho_bad(v.y);
+    mn = mn_own < mn ? mn_own : mn;
+    // z halo planes (a wall has no plane beyond it)
+    const bool lo = !(g.walls && kb == 0), hi = !(g.walls && ke == g.nz);
+    if (lo) {
+        const int k = kb == 0 ? g.nz - 1 : kb - 1;
+        const long long h = __double_as_longlong(__ldg(rho + ((size_t)k * ny + j) * nx + i));
+        mn = h < mn ? h : mn;
+        mx = h > mx ? h : mx;
     }
-    __shared__ long long smn[32];
-    __shared__ int sbad[32];
+    if (hi) {
+        const int k = ke == g.nz ? 0 : ke;
+        const long long h = __double_as_longlong(__ldg(rho + ((size_t)k * ny + j) * nx + i));
+        mn = h < mn ? h : mn;
+        mx = h > mx ? h : mx;
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-        const long long t = __shfl_down_sync(0xffffffffu, mn, o);
+        long long t = __shfl_xor_sync(0xffffffffu, mn_own, o);
+        mn_own = t < mn_own ? t : mn_own;
+        t = __shfl_xor_sync(0xffffffffu, mn, o);
         mn = t < mn ? t : mn;
-        bad |= __shfl_down_sync(0xffffffffu, bad, o);
+        t = __shfl_xor_sync(0xffffffffu, mx, o);
+        mx = t > mx ? t : mx;
+        bad |= __shfl_xor_sync(0xffffffffu, bad, o);
     }
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    if (lane == 0) { smn[wid] = mn; sbad[wid] = bad; }
+    constexpr int NW = RX * TY / 32;
+    __shared__ long long s_own[NW], s_mn[NW], s_mx[NW];
+    __shared__ int s_bad[NW];
+    const int tid = ty * RX + tx, lane = tid & 31, wid = tid >> 5;
+    if (lane == 0) { s_own[wid] = mn_own; s_mn[wid] = mn; s_mx[wid] = mx; s_bad[wid] = bad; }
     __syncthreads();
-    if (wid == 0) {
-        mn = lane < nw ? smn[lane] : 0x7FFFFFFFFFFFFFFFLL;
-        bad = lane < nw ? sbad[lane] : 0;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            const long long t = __shfl_down_sync(0xffffffffu, mn, o);
-            mn = t < mn ? t : mn;
-            bad |= __shfl_down_sync(0xffffffffu, bad, o);
+    if (tid == 0) {
+        for (int w = 1; w < NW; ++w) {
+            mn_own = s_own[w] < mn_own ? s_own[w] : mn_own;
+            mn = s_mn[w] < mn ? s_mn[w] : mn;
+            mx = s_mx[w] > mx ? s_mx[w] : mx;
+            bad |= s_bad[w];
         }
-        if (lane == 0) { part[2 * blockIdx.x] = mn; part[2 * blockIdx.x + 1] = bad; }
+        const int t = (blockIdx.z * g.tny + blockIdx.y) * g.tnx + blockIdx.x;
+        trange[2 * t] = mn;
+        trange[2 * t + 1] = mx;
+        part[2 * t] = mn_own;
+        part[2 * t + 1] = bad;
     }
 }
 
-__global__ void k_rho_finalize(const long long* __restrict__ part, int nblk, DevScalars* sc, double rho0_user,
-                               double idx, double idy) {
-    if (threadIdx.x != 0) return;
+__global__ void __launch_bounds__(1024) k_rho_finalize(const long long* __restrict__ part, int nblk, DevScalars* sc,
+                                                       double rho0_user, double idx, double idy) {
     long long mn = 0x7FFFFFFFFFFFFFFFLL;
     int bad = 0;
-    for (int i = 0; i < nblk; ++i) {
+    for (int i = threadIdx.x; i < nblk; i += blockDim.x) {
         mn = part[2 * i] < mn ? part[2 * i] : mn;
         bad |= (int)part[2 * i + 1];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const long long t = __shfl_xor_sync(0xffffffffu, mn, o);
+        mn = t < mn ? t : mn;
+        bad |= __shfl_xor_sync(0xffffffffu, bad, o);
+    }
+    __shared__ long long smn[32];
+    __shared__ int sbad[32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) { smn[wid] = mn; sbad[wid] = bad; }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+        mn = smn[w] < mn ? smn[w] : mn;
+        bad |= sbad[w];
     }
     const double r0 = rho0_user > 0.0 ? rho0_user : __longlong_as_double(mn);
     sc->rho0 = r0;
@@ -103,53 +155,12 @@ __global__ void k_rho_finalize(const long long* __restrict__ part, int nblk, Dev
     sc->bad_rho = bad;
 }
 
-// Tile flags: a face whose two cells both hold exactly rho0 has (1 - rho0/rho_f) = 0; the
-// test runs on the bit patterns, without FP64 instructions.  Every stencil tile whose CTA
-// reads a nonzero coefficient is flagged: the tile that owns the cell, and the tile above
-// it in x, y or z when the cell's face is that tile's lower boundary face.
-__global__ void __launch_bounds__(256) k_tile_flags(const double* __restrict__ rho, Geo g,
-                                                    const DevScalars* __restrict__ sc) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int j = blockIdx.y, k = blockIdx.z;
-    const bool act = i < g.nx;
+// True when every face coefficient a tile's CTA reads is zero: the tile's density range
+// (cells and one-cell halo) is exactly [rho0, rho0].
+__device__ __forceinline__ bool tile_uniform(const Geo& g, const DevScalars* __restrict__ sc) {
+    const int t = (blockIdx.z * g.tny + blockIdx.y) * g.tnx + blockIdx.x;
     const long long b0 = __double_as_longlong(sc->rho0);
-    long long bc_ = b0, be = b0, bn = b0, bt = b0;
-    bool top_wall = g.walls && k == g.nz - 1;
-    if (act) {
-        const size_t idx = ((size_t)k * g.ny + j) * g.nx + i;
-        bc_ = __double_as_longlong(__ldg(rho + idx));
-        be = __double_as_longlong(__ldg(rho + ((size_t)k * g.ny + j) * g.nx + (wrapm(i + 1, g.nx))));
-        bn = __double_as_longlong(__ldg(rho + ((size_t)k * g.ny + (wrapm(j + 1, g.ny))) * g.nx + i));
-        const int kp = g.walls ? (k + 1 < g.nz ? k + 1 : k) : (k + 1 == g.nz ? 0 : k + 1);
-        bt = __double_as_longlong(__ldg(rho + ((size_t)kp * g.ny + j) * g.nx + i));
-    }
-    const bool cz0 = bc_ == b0;
-    const bool nzx = act && !(cz0 && be == b0), nzy = act && !(cz0 && bn == b0);
-    const bool nzz = act && !(cz0 && bt == b0) && !top_wall;
-    const int tx = i >> g.lgrx, ty = j / FLUPS_TY, tz = k / FLUPS_KC;
-    const int txp = (tx + 1 == g.tnx) ? 0 : tx + 1;
-    const int typ = (ty + 1 == g.tny) ? 0 : ty + 1;
-    const int tzp = (tz + 1 == g.tnz) ? 0 : tz + 1;
-    const bool last_x = act && ((i & (g.rx - 1)) == g.rx - 1), last_y = (j % FLUPS_TY) == FLUPS_TY - 1;
-    const bool last_z = (k % FLUPS_KC) == FLUPS_KC - 1 || k == g.nz - 1;
-    auto tile = [&](int a, int b, int c) { return (size_t)(c * g.tny + b) * g.tnx + a; };
-    if (g.rx == 32) {
-        // the 32 lanes of a warp are the 32 columns of one tile row
-        const unsigned any = __ballot_sync(0xffffffffu, nzx || nzy || nzz);
-        const unsigned anyy = __ballot_sync(0xffffffffu, nzy);
-        const unsigned anyz = __ballot_sync(0xffffffffu, nzz);
-        if ((threadIdx.x & 31) == 0 && act) {
-            if (any) atomicOr(g.tflags + tile(tx, ty, tz), 1u);
-            if (anyy && last_y) atomicOr(g.tflags + tile(tx, typ, tz), 1u);
-            if (anyz && last_z) atomicOr(g.tflags + tile(tx, ty, tzp), 1u);
-        }
-        if (nzx && last_x) atomicOr(g.tflags + tile(txp, ty, tz), 1u);
-    } else if (act) {
-        if (nzx || nzy || nzz) atomicOr(g.tflags + tile(tx, ty, tz), 1u);
-        if (nzx && last_x) atomicOr(g.tflags + tile(txp, ty, tz), 1u);
-        if (nzy && last_y) atomicOr(g.tflags + tile(tx, typ, tz), 1u);
-        if (nzz && last_z) atomicOr(g.tflags + tile(tx, ty, tzp), 1u);
-    }
+    return g.trange[2 * t] == b0 && g.trange[2 * t + 1] == b0;
 }
 
 // The three coefficients of one cell when some face has a density other than rho0.  Kept
@@ -174,7 +185,7 @@ __global__ void __launch_bounds__(RX * FLUPS_TY) k_face_coeffs(const double* __r
                                                                double* __restrict__ bx, double* __restrict__ by,
                                                                double* __restrict__ bz, Geo g,
                                                                const DevScalars* __restrict__ sc) {
-    if (g.tflags[(blockIdx.z * g.tny + blockIdx.y) * g.tnx + blockIdx.x] == 0) return;
+    if (tile_uniform(g, sc)) return;
     const int i0 = blockIdx.x * RX, j0 = blockIdx.y * FLUPS_TY;
     const int kb = blockIdx.z * FLUPS_KC, ke = min(kb + FLUPS_KC, g.nz);
     const int k_lo = (g.walls && kb == 0) ? 0 : kb - 1;
@@ -232,7 +243,7 @@ __global__ void __launch_bounds__(RX * TY) k_rhs(const double* __restrict__ u, c
     const int i = i0 + tx, j = j0 + ty;
     const int im = wrapm(i - 1, nx), jm = wrapm(j - 1, ny);
 
-    if (g.tflags[(blockIdx.z * g.tny + blockIdx.y) * g.tnx + blockIdx.x] == 0) {
+    if (tile_uniform(g, sc)) {
         double wlo = 0.0;
         if (!(g.walls && kb == 0)) wlo = __ldg(w + ((size_t)(kb == 0 ? nz - 1 : kb - 1) * ny + j) * nx + i);
         for (int k = kb; k < ke; ++k) {
@@ -316,7 +327,7 @@ __global__ void __launch_bounds__(RX * TY) k_correct(const double* __restrict__ 
     const int i = i0 + tx, j = j0 + ty;
     const int ie = wrapm(i + 1, nx), jn = wrapm(j + 1, ny);
 
-    if (g.tflags[(blockIdx.z * g.tny + blockIdx.y) * g.tnx + blockIdx.x] == 0) {
+    if (tile_uniform(g, sc)) {
         for (int k = kb; k < ke; ++k) {
             const bool top = g.walls && (k == nz - 1);
             const int kp = k + 1 == nz ? 0 : k + 1;
@@ -474,24 +485,23 @@ void run_correct(flups_plan P, const double* p, const double* pn, const double* 
 
 cudaError_t launch_set_density(flups_plan P, const double* rho, double rho0) {
     const Geo g = plan_geo(P);
-    const int nblk = 1024;
+    const int ntiles = g.tnx * g.tny * g.tnz;
+    dim3 tgrid(g.tnx, g.tny, g.tnz);
+    long long* part = reinterpret_cast<long long*>(P->part);
     flups_prof_begin(P, FK_RHO_MINMAX);
-    k_rho_minmax<<<nblk, 256, 0, P->stream>>>(rho, P->npts, reinterpret_cast<long long*>(P->part));
-    k_rho_finalize<<<1, 32, 0, P->stream>>>(reinterpret_cast<const long long*>(P->part), nblk, P->sc, rho0, g.idx,
-                                            g.idy);
+    if (g.rx == 32) k_rho_tiles<32><<<tgrid, dim3(32, FLUPS_TY), 0, P->stream>>>(rho, g, P->trange, part);
+    else if (g.rx == 16) k_rho_tiles<16><<<tgrid, dim3(16, FLUPS_TY), 0, P->stream>>>(rho, g, P->trange, part);
+    else k_rho_tiles<8><<<tgrid, dim3(8, FLUPS_TY), 0, P->stream>>>(rho, g, P->trange, part);
     flups_prof_end(P);
-    cudaMemsetAsync(P->tflags, 0, (size_t)g.tnx * g.tny * g.tnz * sizeof(unsigned int), P->stream);
-    dim3 grid((g.nx + 255) / 256, g.ny, g.nz);
     flups_prof_begin(P, FK_TILE_FLAGS);
-    k_tile_flags<<<grid, 256, 0, P->stream>>>(rho, g, P->sc);
+    k_rho_finalize<<<1, 1024, 0, P->stream>>>(part, ntiles, P->sc, rho0, g.idx, g.idy);
     flups_prof_end(P);
     flups_prof_begin(P, FK_FACE_COEFFS);
-    dim3 tgrid(g.tnx, g.tny, g.tnz);
     if (g.rx == 32) k_face_coeffs<32><<<tgrid, dim3(32, FLUPS_TY), 0, P->stream>>>(rho, P->bx, P->by, P->bz, g, P->sc);
     else if (g.rx == 16) k_face_coeffs<16><<<tgrid, dim3(16, FLUPS_TY), 0, P->stream>>>(rho, P->bx, P->by, P->bz, g, P->sc);
     else k_face_coeffs<8><<<tgrid, dim3(8, FLUPS_TY), 0, P->stream>>>(rho, P->bx, P->by, P->bz, g, P->sc);
     flups_prof_end(P);
-    FLUPS_COUNT(P, 4);
+    FLUPS_COUNT(P, 3);
     return cudaGetLastError();
 }
 

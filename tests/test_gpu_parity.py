@@ -231,7 +231,7 @@ def test_profiling_reports_every_launched_kernel():
         info = plan.solve(f, p, rtol=1e-10)
         plan.correct(p, d["pn"], d["pnm1"], 2.0, 1.0, c.dt, d["u"], d["v"], d["w"])
         prof = plan.profile()
-    for k in ("k_rho_minmax", "k_face_coeffs", "k_rhs", "k_correct", "k_xfwd_f32", "k_xfwd_residual32",
+    for k in ("k_rho_tiles", "k_rho_finalize", "k_face_coeffs", "k_rhs", "k_correct", "k_xfwd_f32", "k_xfwd_residual32",
               "k_ycol32", "k_zper32", "k_xinv32"):
         assert k in prof and prof[k][0] > 0.0, k
     assert prof["k_xfwd_residual32"][1] == info.iters
