@@ -225,32 +225,41 @@ template <typename T> __device__ __forceinline__ typename cplx<T>::t mk(T a, T b
     typename cplx<T>::t r; r.x = a; r.y = b; return r;
 }
 
-// Block-wide sum of up to three per-thread values into part[blockIdx.x * 3 + q].
-__device__ void block_sum3(double a, double b, double c, double* __restrict__ part) {
+
+// Block sums into part[blockIdx.x * 3 + q] of the partials a (FP64, reduced only when
+// HAS_A), b and c (FP32, reduced in FP32 within each warp, only when HAS_B / HAS_C); absent
+// partials are written as 0.  Warp values are added in FP64 by warp 0.  Per thread this costs
+// 5 FP64 adds for a and none for b, c (FP64 instructions run on GB300's narrow FP64 pipe).
+template <bool HAS_A, bool HAS_B, bool HAS_C>
+__device__ void block_sum_abc(double a, float b, float c, double* __restrict__ part) {
     __shared__ double red[3][32];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-        a += __shfl_down_sync(0xffffffffu, a, o);
-        b += __shfl_down_sync(0xffffffffu, b, o);
-        c += __shfl_down_sync(0xffffffffu, c, o);
+        if (HAS_A) a += __shfl_xor_sync(0xffffffffu, a, o);
+        if (HAS_B) b += __shfl_xor_sync(0xffffffffu, b, o);
+        if (HAS_C) c += __shfl_xor_sync(0xffffffffu, c, o);
     }
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
-    if (lane == 0) { red[0][wid] = a; red[1][wid] = b; red[2][wid] = c; }
+    if (lane == 0) {
+        red[0][wid] = HAS_A ? a : 0.0;
+        red[1][wid] = HAS_B ? (double)b : 0.0;
+        red[2][wid] = HAS_C ? (double)c : 0.0;
+    }
     __syncthreads();
     if (wid == 0) {
-        a = lane < nw ? red[0][lane] : 0.0;
-        b = lane < nw ? red[1][lane] : 0.0;
-        c = lane < nw ? red[2][lane] : 0.0;
+        double x = lane < nw ? red[0][lane] : 0.0;
+        double y = lane < nw ? red[1][lane] : 0.0;
+        double z = lane < nw ? red[2][lane] : 0.0;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
-            a += __shfl_down_sync(0xffffffffu, a, o);
-            b += __shfl_down_sync(0xffffffffu, b, o);
-            c += __shfl_down_sync(0xffffffffu, c, o);
+            x += __shfl_down_sync(0xffffffffu, x, o);
+            y += __shfl_down_sync(0xffffffffu, y, o);
+            z += __shfl_down_sync(0xffffffffu, z, o);
         }
         if (lane == 0) {
-            part[blockIdx.x * 3 + 0] = a;
-            part[blockIdx.x * 3 + 1] = b;
-            part[blockIdx.x * 3 + 2] = c;
+            part[blockIdx.x * 3 + 0] = x;
+            part[blockIdx.x * 3 + 1] = y;
+            part[blockIdx.x * 3 + 2] = z;
         }
     }
 }
@@ -393,7 +402,8 @@ __global__ void __launch_bounds__(512) k_xfwd(const double* __restrict__ f, cons
         s[n * pitch + c] = z;
     }
     }
-    if (STATS || MODE >= 1) block_sum3(accw, (double)acc2, (double)acc1, part);
+    if (STATS) block_sum_abc<true, true, true>(accw, acc2, acc1, part);
+    else if (MODE >= 1) block_sum_abc<false, true, false>(0.0, acc2, 0.f, part);
     __syncthreads();
     fft_tile<C, E, false>(s, pitch, lgB, L, tw);
     // X_k = A_k + W_nx^k B_k and X_{M-k} = conj(A_k - W_nx^k B_k), k = 0..M/2, with
@@ -512,7 +522,7 @@ __global__ void __launch_bounds__(512) k_xinv(const typename cplx<T>::t* __restr
         emax = __reduce_max_sync(0xffffffffu, emax);
         if ((tid & 31) == 0) atomicMax(&sc->pexp, emax);
     }
-    if (MEAN) block_sum3(accw, 0.0, 0.0, part);
+    if (MEAN) block_sum_abc<true, false, false>(accw, 0.f, 0.f, part);
 }
 
 // ------------------------------------------------------- column transform along y
