@@ -200,16 +200,20 @@ __device__ __forceinline__ double f2d_bits(float x) {
 }
 
 // x * 2^(58 - E) as a 64-bit integer, truncated toward zero, for |x| < 2^E; sh = 1017 + E.
-// Built from the binary64 layout with integer operations only.  The 7-point sums of such
-// values are exact in 64-bit integers (|sum| < 12 * 2^58 < 2^62).
+// Built from the binary64 layout with integer operations only: the 53-bit significand is
+// placed 5 bits up and shifted right by 5 - (e - sh) >= 0 (a shift of 64 or more gives 0,
+// which covers zero and subnormals).  The 7-point sums of such values are exact in 64-bit
+// integers (|sum| < 12 * 2^58 < 2^62).
 __device__ __forceinline__ long long fixq(double x, int sh) {
     const long long b = __double_as_longlong(x);
     const int e = (int)((b >> 52) & 0x7FF);
-    const int sft = e - sh;
-    const long long m = (b & 0xFFFFFFFFFFFFFLL) | 0x10000000000000LL;
-    long long v = sft >= 0 ? (m << sft) : (sft > -54 ? (m >> -sft) : 0LL);
-    v = e == 0 ? 0LL : v;
-    return b < 0 ? -v : v;
+    const unsigned long long m = ((unsigned long long)(b & 0xFFFFFFFFFFFFFLL) | 0x10000000000000ULL) << 5;
+    int r = 5 - (e - sh);
+    r = r < 0 ? 0 : (r > 64 ? 64 : r);
+    unsigned long long v;
+    asm("shr.b64 %0, %1, %2;" : "=l"(v) : "l"(m), "r"(r));
+    const long long sg = b >> 63;           // 0 or -1
+    return ((long long)v ^ sg) - sg;
 }
 
 template <typename T> __device__ __forceinline__ T from_double(double x) {
@@ -264,6 +268,14 @@ __device__ void block_sum_abc(double a, float b, float c, double* __restrict__ p
     }
 }
 
+// The residual pass (MODE 2) uses shared-memory fixed-point rows when one thread per pair
+// position covers B = E rows of one plane: E = 8, M a multiple of 32 up to 512, ny % 8 == 0.
+__host__ __device__ __forceinline__ bool xres_tiled(int E, int B, int M, int ny) {
+    return E == 8 && B == 8 && M % 32 == 0 && M <= 512 && ny % 8 == 0;
+}
+// Shared memory of that path: B + 2 rows of M fixed-point pairs (16 bytes each).
+__host__ __device__ __forceinline__ size_t xres_smem(int M) { return (size_t)10 * M * 16; }
+
 // ------------------------------------------------------------- forward along x (R2C)
 // MODE 0: input f (FP64).  With STATS, also the partial sums
 //         sum_k dzf_k sum_ij f (FP64), sum f^2 and sum f (FP32 per thread, FP64 across).
@@ -301,7 +313,49 @@ __global__ void __launch_bounds__(512) k_xfwd(const double* __restrict__ f, cons
     }
     // Every thread handles exactly E elements (nthr = B M / E): compile-time trip counts let
     // the loads of a thread be issued before they are used.
-    if (MODE == 0) {
+    if (MODE == 2 && xres_tiled(E, B, M, g.ny)) {
+        // B = E rows row0 .. row0+B-1 (consecutive y of one plane), one pair position n = tid
+        // per thread.  The rows and their two y-halo rows are converted to fixed point once into
+        // shared memory (rows 0 .. B+1 = j0-1 .. j0+B): each value then serves as the centre and
+        // as the x and y neighbour of the cells beside it; the z neighbours are converted per
+        // row.  The FFT tile reuses the same shared memory after the stencil.
+        longlong2* Q = reinterpret_cast<longlong2*>(smraw);
+        const int n = tid;
+        const int k = row0 / g.ny, j0 = row0 - k * g.ny;
+        const double2* P2 = reinterpret_cast<const double2*>(p);
+#pragma unroll
+        for (int r = 0; r < E + 2; ++r) {
+            const double2 v = __ldg(P2 + ((size_t)k * g.ny + wrapm(j0 - 1 + r, g.ny)) * M + n);
+            Q[r * M + n] = make_longlong2(fixq(v.x, sh), fixq(v.y, sh));
+        }
+        int km, kp;
+        if (g.walls) { km = k > 0 ? k - 1 : 0; kp = k < g.nz - 1 ? k + 1 : g.nz - 1; }
+        else { km = k == 0 ? g.nz - 1 : k - 1; kp = k + 1 == g.nz ? 0 : k + 1; }
+        const bool hb = !g.walls || k > 0, ht = !g.walls || k < g.nz - 1;
+        const long long nd = 4 + (hb ? 1 : 0) + (ht ? 1 : 0);
+        const int nw_ = n == 0 ? M - 1 : n - 1, ne_ = n + 1 == M ? 0 : n + 1;
+        __syncthreads();
+        C zr[E];
+#pragma unroll
+        for (int c = 0; c < E; ++c) {
+            const size_t jrow = (size_t)j0 + c;
+            const double2 fv = __ldg(reinterpret_cast<const double2*>(f + (size_t)(row0 + c) * nx) + n);
+            const double2 vb = __ldg(P2 + ((size_t)km * g.ny + jrow) * M + n);
+            const double2 vt = __ldg(P2 + ((size_t)kp * g.ny + jrow) * M + n);
+            const longlong2 qc = Q[(c + 1) * M + n], qs = Q[c * M + n], qn = Q[(c + 2) * M + n];
+            const long long qw = Q[(c + 1) * M + nw_].y, qe = Q[(c + 1) * M + ne_].x;
+            long long s0 = qw + qc.y + qs.x + qn.x - nd * qc.x;
+            long long s1 = qc.x + qe + qs.y + qn.y - nd * qc.y;
+            if (hb) { s0 += fixq(vb.x, sh); s1 += fixq(vb.y, sh); }
+            if (ht) { s0 += fixq(vt.x, sh); s1 += fixq(vt.y, sh); }
+            zr[c] = mk<T>(from_double<T>(fma(-cfix, __ll2double_rn(s0), fv.x - mf)),
+                          from_double<T>(fma(-cfix, __ll2double_rn(s1), fv.y - mf)));
+            acc2 = fmaf((float)zr[c].x, (float)zr[c].x, fmaf((float)zr[c].y, (float)zr[c].y, acc2));
+        }
+        __syncthreads();                  // every Q read is done: the tile may overwrite it
+#pragma unroll
+        for (int c = 0; c < E; ++c) s[n * pitch + c] = zr[c];
+    } else if (MODE == 0) {
         double2 fvs[E];
 #pragma unroll
         for (int q = 0; q < E; ++q) {
@@ -924,7 +978,7 @@ int pick_lgB(int N, int csize, int E, int bmax, int ncols, int cap) {
 int x_cap(int cta) { return std::min(cta > 0 ? cta : cta_threads(), 512); }
 
 template <typename K> void allow_smem(K kern) {
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 74 * 1024);
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
 }
 
 // Elements per thread: 16 (FP32) or 8 (FP64) complex values; 4 for transforms shorter than that.
@@ -1055,13 +1109,16 @@ template <typename T, int E, int MODE, bool STATS>
 void run_xfwd_e(flups_plan P, const double* f, const double* p, const Geo& g) {
     typedef typename cplx<T>::t C;
     const int N = g.M, nrows = g.ny * g.nz;
-    const int lgB = pick_lgB(N, sizeof(C), E, sizeof(T) == 4 ? 32 : 16, nrows, x_cap(g.cta));
+    const bool tiled = MODE == 2 && xres_tiled(E, E, N, g.ny);
+    const int lgB = tiled ? 3 : pick_lgB(N, sizeof(C), E, sizeof(T) == 4 ? 32 : 16, nrows, x_cap(g.cta));
     const int B = 1 << lgB;
     auto kern = k_xfwd<T, E, MODE, STATS>;
     allow_smem(kern);
     flups_prof_begin(P, sizeof(T) == 8 ? FK_XFWD64 : (MODE >= 1 ? FK_XFWD_RES32 : FK_XFWD_F32));
     const int nblk = (nrows + B - 1) / B;
-    kern<<<nblk, B * N / E, (size_t)N * (B + 1) * sizeof(C), P->stream>>>(
+    size_t smem = (size_t)N * (B + 1) * sizeof(C);
+    if (tiled && xres_smem(N) > smem) smem = xres_smem(N);
+    kern<<<nblk, B * N / E, smem, P->stream>>>(
         f, p, (C*)P->spec, g, packed(P->lx), (const C*)P->twx, (const C*)P->twxr, P->tabs64 + 5 * g.nz, lgB, nrows,
         P->sc, P->part);
     flups_prof_end(P);
@@ -1102,10 +1159,12 @@ void run_xinv(flups_plan P, double* p, const Geo& g) {
     else run_xinv_e<T, Ebig<T>::E, ACC, MEAN, SUBM>(P, p, g);
 }
 
-// CTAs of the x passes (one partial sum each) for a complex element of csize bytes.
-int xfwd_blocks(flups_plan P, int csize, int /*unused*/) {
+// CTAs of the x passes (one partial sum each) for a complex element of csize bytes; with
+// residual != 0, of the FP32 residual pass (which may use the tiled fixed-point layout).
+int xfwd_blocks(flups_plan P, int csize, int residual) {
     const int nrows = P->ny * P->nz;
     const int E = P->M % 3 == 0 ? 12 : (P->M >= 8 ? 8 : 4);
+    if (residual && csize == 8 && P->uniform_h && xres_tiled(E, E, P->M, P->ny)) return (nrows + 7) >> 3;
     const int lgB = pick_lgB(P->M, csize, E, csize == 8 ? 32 : 16, nrows, x_cap(P->cta_cap));
     return (nrows + (1 << lgB) - 1) >> lgB;
 }
@@ -1130,7 +1189,7 @@ cudaError_t launch_xfwd32_from_f(flups_plan P, const double* f) {
 }
 
 cudaError_t launch_finalize_f(flups_plan P) {
-    const int nblk = xfwd_blocks(P, 8, 16);
+    const int nblk = xfwd_blocks(P, 8, 0);
     flups_prof_begin(P, FK_FINALIZE);
     k_finalize<<<1, 1024, 0, P->stream>>>(P->part, nblk, P->sc, 0, 1.0 / ((double)P->nx * P->ny * P->sum_dzf),
                                           (double)P->npts, 0, 0.0);
@@ -1147,7 +1206,7 @@ cudaError_t launch_xfwd32_residual(flups_plan P, const double* f, const double* 
 }
 
 cudaError_t launch_finalize_r(flups_plan P) {
-    const int nblk = xfwd_blocks(P, 8, 16);
+    const int nblk = xfwd_blocks(P, 8, 1);
     flups_prof_begin(P, FK_FINALIZE);
     k_finalize<<<1, 1024, 0, P->stream>>>(P->part, nblk, P->sc, 1, 0.0, 0.0, 0, 0.0);
     flups_prof_end(P);
@@ -1168,7 +1227,7 @@ cudaError_t launch_xinv32(flups_plan P, double* p, int mode) {
     cudaMemsetAsync(&P->sc->pexp, 0, sizeof(int), P->stream);
     if (mode == 0) {                       // p = delta, and the volume-weighted mean of p
         run_xinv<float, 0, true, false>(P, p, g);
-        const int nblk = xfwd_blocks(P, 8, 16);
+        const int nblk = xfwd_blocks(P, 8, 0);
         flups_prof_begin(P, FK_FINALIZE);
         k_finalize<<<1, 1024, 0, P->stream>>>(P->part, nblk, P->sc, 2, 1.0 / ((double)P->nx * P->ny * P->sum_dzf), 0.0, 0, 0.0);
         flups_prof_end(P);
@@ -1187,7 +1246,7 @@ int flups_default_cta() { return cta_threads(); }
 
 size_t flups_part_blocks_needed(int nx, int ny, int nz) {
     const int M = nx / 2, nrows = ny * nz;
-    size_t worst = 0;
+    size_t worst = (size_t)(nrows + 7) / 8;      // the tiled residual pass: 8 rows per CTA
     const int cs[2] = {8, 16};
     const int e1 = M % 3 == 0 ? 12 : (M >= 8 ? 8 : 4);
     const int es[2] = {e1, e1};
@@ -1219,7 +1278,7 @@ cudaError_t launch_solve32_fixed(flups_plan P, const double* f, double* p, doubl
     for (int it = 1; it <= max_iter; ++it) {
         launch_xfwd32_residual(P, f, p);
         {
-            const int nblk = xfwd_blocks(P, 8, 16);
+            const int nblk = xfwd_blocks(P, 8, 1);
             k_finalize<<<1, 1024, 0, P->stream>>>(P->part, nblk, P->sc, 1, nrm_w, 0.0, 1, thr2);
             FLUPS_COUNT(P, 1);
         }
