@@ -244,15 +244,19 @@ __global__ void __launch_bounds__(RX * TY) k_rhs(const double* __restrict__ u, c
     const int im = wrapm(i - 1, nx), jm = wrapm(j - 1, ny);
 
     if (tile_uniform(g, sc)) {
+        // (rho0/dt)/dzf_k once per plane for the CTA (six FP64 instructions per cell remain)
+        __shared__ double kzf[KC];
+        if (tid < ke - kb) kzf[tid] = rdt * __ldg(g.idzf + kb + tid);
         double wlo = 0.0;
         if (!(g.walls && kb == 0)) wlo = __ldg(w + ((size_t)(kb == 0 ? nz - 1 : kb - 1) * ny + j) * nx + i);
+        __syncthreads();
         for (int k = kb; k < ke; ++k) {
             const size_t row = (size_t)k * ny;
             const size_t qc = (row + j) * nx + i;
             const double whi = (g.walls && k == nz - 1) ? 0.0 : __ldg(w + qc);
             const double du = __ldg(u + qc) - __ldg(u + (row + j) * nx + im);
             const double dv = __ldg(v + qc) - __ldg(v + (row + jm) * nx + i);
-            f[qc] = fma(du, kx, fma(dv, ky, (whi - wlo) * (rdt * __ldg(g.idzf + k))));
+            f[qc] = fma(du, kx, fma(dv, ky, (whi - wlo) * kzf[k - kb]));
             wlo = whi;
         }
         return;
@@ -328,6 +332,10 @@ __global__ void __launch_bounds__(RX * TY) k_correct(const double* __restrict__ 
     const int ie = wrapm(i + 1, nx), jn = wrapm(j + 1, ny);
 
     if (tile_uniform(g, sc)) {
+        // -(dt/rho0)/dzc_k once per plane for the CTA (six FP64 instructions per cell remain)
+        __shared__ double azc[KC];
+        if (tid < ke - kb) azc[tid] = -(s * __ldg(g.idzc + kb + tid));
+        __syncthreads();
         for (int k = kb; k < ke; ++k) {
             const bool top = g.walls && (k == nz - 1);
             const int kp = k + 1 == nz ? 0 : k + 1;
@@ -341,7 +349,7 @@ __global__ void __launch_bounds__(RX * TY) k_correct(const double* __restrict__ 
                 w[qc] = 0.0;
             } else {
                 const double pt = __ldg(p + ((size_t)kp * ny + j) * nx + i);
-                w[qc] = fma(-(s * __ldg(g.idzc + k)), pt - pc, w[qc]);
+                w[qc] = fma(azc[k - kb], pt - pc, w[qc]);
             }
         }
         return;
