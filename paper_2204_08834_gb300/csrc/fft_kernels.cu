@@ -201,13 +201,14 @@ __device__ __forceinline__ double f2d_bits(float x) {
 
 // x * 2^(58 - E) as a 64-bit integer, truncated toward zero, for |x| < 2^E; sh = 1017 + E.
 // Built from the binary64 layout with integer operations only: the 53-bit significand is
-// placed 5 bits up and shifted right by 5 - (e - sh) >= 0 (a shift of 64 or more gives 0,
-// which covers zero and subnormals).  The 7-point sums of such values are exact in 64-bit
+// placed 5 bits up and shifted right by 5 - (e - sh) >= 0 (a shift of 64 or more gives 0);
+// zero and subnormal inputs give 0.  The 7-point sums of such values are exact in 64-bit
 // integers (|sum| < 12 * 2^58 < 2^62).
 __device__ __forceinline__ long long fixq(double x, int sh) {
     const long long b = __double_as_longlong(x);
     const int e = (int)((b >> 52) & 0x7FF);
-    const unsigned long long m = ((unsigned long long)(b & 0xFFFFFFFFFFFFFLL) | 0x10000000000000ULL) << 5;
+    unsigned long long m = ((unsigned long long)(b & 0xFFFFFFFFFFFFFLL) | 0x10000000000000ULL) << 5;
+    m = e == 0 ? 0ull : m;                  // zero and subnormals give 0 at any scale
     int r = 5 - (e - sh);
     r = r < 0 ? 0 : (r > 64 ? 64 : r);
     unsigned long long v;
@@ -907,10 +908,11 @@ __global__ void k_finalize(const double* __restrict__ part, int nblk, DevScalars
     if (fixed && sc->done) return;   // fixed-iteration solve: the member converged earlier
     __shared__ double red[3][32];
     double a = 0.0, b = 0.0, c = 0.0;
+#pragma unroll 8
     for (int i = threadIdx.x; i < nblk; i += blockDim.x) {
-        a += part[3 * i + 0];
-        b += part[3 * i + 1];
-        c += part[3 * i + 2];
+        a += __ldg(part + 3 * i + 0);
+        b += __ldg(part + 3 * i + 1);
+        c += __ldg(part + 3 * i + 2);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
