@@ -22,6 +22,15 @@
 // channel, columns = output channel and the taps reversed (tap t -> 26 - t), so the gradient
 // with respect to a layer's input is the same convolution kernel run on the output gradient.
 // Padding columns/rows are zero.
+//
+// On grids with nx a multiple of 128 the convolutions run on the 5th-generation tensor cores
+// instead (k_pnet_conv_tc): each MMA computes 128 consecutive x-points x 16 output channels
+// with K = 16 input channels of one tap (tcgen05.mma kind::f16, bf16 operands from shared
+// memory, FP32 accumulator in tensor memory); the 27 taps accumulate into the same tensor-memory
+// columns.  The A operand is read straight out of the halo tile with one descriptor per tap:
+// the tile stores each point's two 8-channel halves in two planes (point stride 16 bytes), so
+// an x-shifted window of 128 points is again a K-major operand (core matrices of 8 points x 16
+// bytes 128 bytes apart, the two K halves one plane apart).
 
 #include "flups_impl.cuh"
 
@@ -35,6 +44,7 @@
 #define PN_NP 15601
 #define PN_WPK (27 * 16 * 24)          // packed weights of one layer (bf16 elements)
 #define PN_PART 6928                   // one CTA's weight-gradient partial: 27*16*16 + 16 biases
+#define PN_TCW (27 * 256)              // tcgen05-layout weights of one layer (bf16 elements)
 
 namespace {
 
@@ -93,22 +103,38 @@ __device__ __forceinline__ TileOrigin tile_origin(int nx, int ny) {
 }
 
 // Loads the periodic halo tile of a [n][16] bfloat16 field into shared memory (swizzled).
+// Loads are issued in batches of 8 per thread before the shared-memory stores.
 __device__ __forceinline__ void load_halo(const __nv_bfloat16* __restrict__ in, unsigned char* sm, TileOrigin o,
                                           int nx, int ny, int nz) {
     const uint4* src = reinterpret_cast<const uint4*>(in);
-    for (int c = threadIdx.x; c < NHALO * 2; c += THREADS) {
-        const int sp = c >> 1, h = c & 1;
-        const int xx = sp % HX, t = sp / HX;
-        const int yy = t % HY, zz = t / HY;
-        const int gx = wrapc(o.x0 + xx - 1, nx), gy = wrapc(o.y0 + yy - 1, ny), gz = wrapc(o.z0 + zz - 1, nz);
-        const long long pt = ((long long)gz * ny + gy) * nx + gx;
-        *reinterpret_cast<uint4*>(sm + swz(sp, h)) = __ldg(src + pt * 2 + h);
+    constexpr int NC = NHALO * 2, BT = 8;
+    for (int c0 = threadIdx.x; c0 < NC; c0 += THREADS * BT) {
+        uint4 v[BT];
+        uint32_t dst[BT];
+#pragma unroll
+        for (int q = 0; q < BT; ++q) {
+            const int c = c0 + q * THREADS;
+            if (c < NC) {
+                const int sp = c >> 1, h = c & 1;
+                const int xx = sp % HX, t = sp / HX;
+                const int yy = t % HY, zz = t / HY;
+                const int gx = wrapc(o.x0 + xx - 1, nx), gy = wrapc(o.y0 + yy - 1, ny), gz = wrapc(o.z0 + zz - 1, nz);
+                const long long pt = ((long long)gz * ny + gy) * nx + gx;
+                v[q] = __ldg(src + pt * 2 + h);
+                dst[q] = swz(sp, h);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < BT; ++q)
+            if (c0 + q * THREADS < NC) *reinterpret_cast<uint4*>(sm + dst[q]) = v[q];
     }
 }
 
 struct ConvArgs {
     const __nv_bfloat16* in;     // [n][16]
-    const __nv_bfloat16* w;      // packed weights [27][16][24]
+    const __nv_bfloat16* w;      // packed weights [27][16][24] (mma.sync kernel)
+    const __nv_bfloat16* wtc;    // packed weights [27][2 halves][16][8] (tcgen05 kernel)
+    int* err;                    // nonzero: a bounded wait of the tcgen05 kernel timed out
     const float* bias;           // FP32 biases (EPI 0, 1, 2)
     __nv_bfloat16* out;          // EPI 0: activation; EPI 2: output gradient (channel 0); EPI 3: masked gradient
     const __nv_bfloat16* mask;   // EPI 3: activation whose positive entries pass the gradient
@@ -230,6 +256,381 @@ __global__ void __launch_bounds__(THREADS, 2) k_pnet_conv(ConvArgs a) {
     }
 }
 
+// ------------------------------------------------------------ tcgen05 convolution
+constexpr int TC_TY = 2, TC_TZ = 2, TC_HX = 130, TC_HY = TC_TY + 2, TC_HZ = TC_TZ + 2;
+constexpr int TC_NP = TC_HX * TC_HY * TC_HZ;            // 2080 halo points
+constexpr int TC_HALF = TC_NP * 16;                     // one 8-channel plane of the halo tile (bytes)
+constexpr int TC_ROWS = TC_TY * TC_TZ;                  // MMA tiles (rows of 128 x-points) per CTA
+constexpr int TC_SMEM = 2 * TC_HALF + 27 * 512 + 16;    // halo + weights + mbarrier + TMEM slot
+constexpr int TC_TMEM_COLS = 64;                        // 16 FP32 columns per row tile
+
+// Shared-memory matrix descriptor (no swizzle, K-major): start address, leading byte offset
+// (step between the two K halves), stride byte offset (step between 8-row core matrices).
+__device__ __forceinline__ unsigned long long tc_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+    return (unsigned long long)((addr >> 4) & 0x3FFF) | ((unsigned long long)((lbo >> 4) & 0x3FFF) << 16) |
+           ((unsigned long long)((sbo >> 4) & 0x3FFF) << 32) | (1ull << 46);
+}
+// Instruction descriptor of kind::f16: FP32 accumulator, bf16 A and B, both K-major, N = 16, M = 128.
+constexpr uint32_t TC_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((16u >> 3) << 17) | ((128u >> 4) << 24);
+
+__device__ __forceinline__ bool tc_mbar_try(uint32_t m, uint32_t par) {
+    uint32_t ok;
+    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+                 : "=r"(ok) : "r"(m), "r"(par) : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ void tc_ld16(uint32_t taddr, float (&v)[16]) {
+    uint32_t r[16];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+__device__ __forceinline__ float tc_ld1(uint32_t taddr) {
+    uint32_t r;
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];" : "=r"(r) : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    return __uint_as_float(r);
+}
+
+// Same epilogues as k_pnet_conv (EPI 0 hidden, 1 inference output, 2 training output,
+// 3 masked gradient).  A CTA of 256 threads computes 2 (y) x 2 (z) rows of 128 x-points; lane l of
+// warp w owns x-point 32 (w % 4) + l (tensor-memory lane 32 (w % 4) + l) of the rows r with
+// r % 2 == w / 4.
+constexpr int TC_THREADS = 256;
+template <int EPI>
+__global__ void __launch_bounds__(TC_THREADS, 2) k_pnet_conv_tc(ConvArgs a) {
+    extern __shared__ __align__(1024) unsigned char sm[];
+    unsigned char* shalo = sm;
+    unsigned char* sw = sm + 2 * TC_HALF;
+    unsigned long long* mbar = reinterpret_cast<unsigned long long*>(sw + 27 * 512);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(sw + 27 * 512 + 8);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int tnx = a.nx / 128, tny = a.ny / TC_TY;
+    const int b = blockIdx.x;
+    const int x0 = (b % tnx) * 128, y0 = ((b / tnx) % tny) * TC_TY, z0 = (b / (tnx * tny)) * TC_TZ;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                     "r"(TC_TMEM_COLS) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(mbar)), "r"(1) : "memory");
+    {
+        // halo tile: loads issued in batches of 8 per thread before the shared-memory stores
+        const uint4* src = reinterpret_cast<const uint4*>(a.in);
+        constexpr int NC = TC_NP * 2, BT = 8;
+        for (int c0 = tid; c0 < NC; c0 += TC_THREADS * BT) {
+            uint4 v[BT];
+            uint32_t dst[BT];
+#pragma unroll
+            for (int q = 0; q < BT; ++q) {
+                const int c = c0 + q * TC_THREADS;
+                if (c < NC) {
+                    const int pp = c >> 1, h = c & 1;
+                    const int xx = pp % TC_HX, t = pp / TC_HX;
+                    const int yy = t % TC_HY, zz = t / TC_HY;
+                    const int gx = wrapc(x0 + xx - 1, a.nx), gy = wrapc(y0 + yy - 1, a.ny), gz = wrapc(z0 + zz - 1, a.nz);
+                    const long long pt = ((long long)gz * a.ny + gy) * a.nx + gx;
+                    v[q] = __ldg(src + pt * 2 + h);
+                    dst[q] = (uint32_t)(h * TC_HALF + pp * 16);
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < BT; ++q)
+                if (c0 + q * TC_THREADS < NC) *reinterpret_cast<uint4*>(shalo + dst[q]) = v[q];
+        }
+        const uint4* wsrc = reinterpret_cast<const uint4*>(a.wtc);
+        for (int c = tid; c < 27 * 32; c += TC_THREADS) reinterpret_cast<uint4*>(sw)[c] = __ldg(wsrc + c);
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tslot;
+    if (tid == 0) {
+        const uint32_t hb = smem_u32(shalo), wb = smem_u32(sw);
+        for (int r = 0; r < TC_ROWS; ++r) {
+            const int zl = r / TC_TY, yl = r - zl * TC_TY;
+            for (int tap = 0; tap < 27; ++tap) {
+                const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
+                const uint32_t aaddr = hb + (uint32_t)((((zl + dz + 1) * TC_HY + (yl + dy + 1)) * TC_HX + dx + 1) * 16);
+                const unsigned long long ad = tc_desc(aaddr, TC_HALF, 128);
+                const unsigned long long bd = tc_desc(wb + tap * 512, 256, 128);
+                asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                             " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+                             ::"r"(tmem + 16 * r), "l"(ad), "l"(bd), "r"(TC_IDESC), "r"(tap) : "memory");
+            }
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(mbar))
+                     : "memory");
+    }
+    bool done = false;
+    for (int i = 0; i < (1 << 22) && !done; ++i) done = tc_mbar_try(smem_u32(mbar), 0);
+    const bool ok = __syncthreads_and(done);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    double sq = 0.0;
+    if (ok) {
+        const int wq = warp & 3;                 // lane quadrant of tensor memory this warp may read
+        const uint32_t tl = tmem + ((uint32_t)(32 * wq) << 16);
+        const int x = x0 + 32 * wq + lane;
+        float bias[16];
+        if (EPI == 0) {
+#pragma unroll
+            for (int n = 0; n < 16; ++n) bias[n] = __ldg(a.bias + n);
+        }
+        for (int r = warp >> 2; r < TC_ROWS; r += 2) {
+            const int zl = r / TC_TY, yl = r - zl * TC_TY;
+            const long long pt = ((long long)(z0 + zl) * a.ny + (y0 + yl)) * a.nx + x;
+            if (EPI == 0 || EPI == 3) {
+                float v[16];
+                tc_ld16(tl + 16 * r, v);
+                if (EPI == 0) {
+#pragma unroll
+                    for (int n = 0; n < 16; ++n) v[n] = fmaxf(v[n] + bias[n], 0.0f);
+                } else {
+                    const uint4* mk4 = reinterpret_cast<const uint4*>(a.mask + pt * 16);
+                    const uint4 m0 = __ldg(mk4), m1 = __ldg(mk4 + 1);
+                    const uint32_t mw[8] = {m0.x, m0.y, m0.z, m0.w, m1.x, m1.y, m1.z, m1.w};
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        if (!(mw[q] & 0x7fffu)) v[2 * q] = 0.0f;
+                        if (!(mw[q] & 0x7fff0000u)) v[2 * q + 1] = 0.0f;
+                    }
+                }
+                uint32_t o[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    __nv_bfloat162 h2 = __floats2bfloat162_rn(v[2 * q], v[2 * q + 1]);
+                    o[q] = *reinterpret_cast<uint32_t*>(&h2);
+                }
+                uint4* dst = reinterpret_cast<uint4*>(a.out + pt * 16);
+                dst[0] = make_uint4(o[0], o[1], o[2], o[3]);
+                dst[1] = make_uint4(o[4], o[5], o[6], o[7]);
+            } else {
+                const double y = (double)(tc_ld1(tl + 16 * r) + __ldg(a.bias));
+                const double pn = a.pn[pt], pm = a.pnm1[pt];
+                if (EPI == 1) {
+                    a.phat[pt] = 2.0 * pn - pm + a.sc[0] * y;
+                } else {
+                    const double e = y - (a.pnext[pt] - (2.0 * pn - pm)) * a.sc[1];
+                    sq += e * e;
+                    a.out[pt * 16] = __double2bfloat16(a.gscale * e);
+                }
+            }
+        }
+    } else if (tid == 0) {
+        atomicExch(a.err, 1);
+    }
+    if (EPI == 2) {
+        __shared__ double ws[TC_THREADS / 32];
+        for (int s2 = 16; s2 > 0; s2 >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, s2);
+        if (lane == 0) ws[warp] = sq;
+        __syncthreads();
+        if (tid == 0) {
+            double t = 0.0;
+            for (int w = 0; w < TC_THREADS / 32; ++w) t += ws[w];
+            a.red[blockIdx.x] = t;
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_TMEM_COLS) : "memory");
+}
+
+// tcgen05 convolution marching in z.  A CTA owns a column of 4 (y) x 128 (x) points through ZC
+// planes.  Input planes (rows y0-1 .. y0+4, x0-1 .. x0+128, both 8-channel halves as planes of
+// 16-byte points) sit in a ring of four shared-memory buffers: output plane o reads input planes
+// o-1, o, o+1 (ring slots o, o+1, o+2 of the local input index), and one new input plane is
+// loaded per output plane.  Tensor memory holds two accumulator sets (4 rows x 16 columns each):
+// the MMAs of plane o run while the threads store plane o-1 and load input plane o+3.
+constexpr int TZ_TY = 4, TZ_HX = 130, TZ_HY = TZ_TY + 2;
+constexpr int TZ_PHALF = TZ_HY * TZ_HX * 16;          // one 8-channel half of an input plane (12480 B)
+constexpr int TZ_PLANE = 2 * TZ_PHALF;                // 24960 B
+constexpr int TZ_SMEM = 4 * TZ_PLANE + 27 * 512 + 32; // ring + weights + 2 mbarriers + TMEM slot
+constexpr int TZ_THREADS = 256;
+constexpr int TZ_TMEM_COLS = 128;                     // 2 sets x 4 rows x 16 columns
+
+__device__ __forceinline__ void tz_load_plane(const uint4* __restrict__ src, unsigned char* dstp, int x0, int y0,
+                                              int gz, int nx, int ny) {
+    constexpr int NC = TZ_HY * TZ_HX * 2, BT = 8;
+    for (int c0 = threadIdx.x; c0 < NC; c0 += TZ_THREADS * BT) {
+        uint4 v[BT];
+        uint32_t dst[BT];
+#pragma unroll
+        for (int q = 0; q < BT; ++q) {
+            const int c = c0 + q * TZ_THREADS;
+            if (c < NC) {
+                const int pp = c >> 1, h = c & 1;
+                const int yy = pp / TZ_HX, xx = pp - yy * TZ_HX;
+                const int gx = wrapc(x0 + xx - 1, nx), gy = wrapc(y0 + yy - 1, ny);
+                const long long pt = ((long long)gz * ny + gy) * nx + gx;
+                v[q] = __ldg(src + pt * 2 + h);
+                dst[q] = (uint32_t)(h * TZ_PHALF + pp * 16);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < BT; ++q)
+            if (c0 + q * TZ_THREADS < NC) *reinterpret_cast<uint4*>(dstp + dst[q]) = v[q];
+    }
+}
+
+template <int EPI>
+__global__ void __launch_bounds__(TZ_THREADS, 2) k_pnet_conv_tcz(ConvArgs a, int zc) {
+    extern __shared__ __align__(1024) unsigned char sm[];
+    unsigned char* ring = sm;
+    unsigned char* sw = sm + 4 * TZ_PLANE;
+    unsigned long long* mbar = reinterpret_cast<unsigned long long*>(sw + 27 * 512);   // [2]
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(sw + 27 * 512 + 16);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int tnx = a.nx / 128, tny = a.ny / TZ_TY;
+    const int b = blockIdx.x;
+    const int x0 = (b % tnx) * 128, y0 = ((b / tnx) % tny) * TZ_TY, z0 = (b / (tnx * tny)) * zc;
+    const uint4* src = reinterpret_cast<const uint4*>(a.in);
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                     "r"(TZ_TMEM_COLS) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {   // one commit per output row: lane 0 of warps 0-3 issues one row's MMAs
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(mbar)), "r"(TZ_TY) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(mbar + 1)), "r"(TZ_TY) : "memory");
+    }
+    {
+        const uint4* wsrc = reinterpret_cast<const uint4*>(a.wtc);
+        for (int c = tid; c < 27 * 32; c += TZ_THREADS) reinterpret_cast<uint4*>(sw)[c] = __ldg(wsrc + c);
+    }
+    for (int lp = 0; lp < 3; ++lp) tz_load_plane(src, ring + lp * TZ_PLANE, x0, y0, wrapc(z0 - 1 + lp, a.nz), a.nx, a.ny);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tslot;
+    const uint32_t rb = smem_u32(ring), wb = smem_u32(sw);
+    const int wq = warp & 3;                  // tensor-memory lane quadrant of this warp
+    const int x = x0 + 32 * wq + lane;
+    float bias[16];
+    if (EPI == 0) {
+#pragma unroll
+        for (int n = 0; n < 16; ++n) bias[n] = __ldg(a.bias + n);
+    }
+    uint32_t ph0 = 0u, ph1 = 0u;
+    bool fail = false;
+    double sq = 0.0;
+    // epilogue of output plane o (accumulator set o & 1); warps 0-3 take rows 0, 2, warps 4-7 rows 1, 3
+    auto epilogue = [&](int o) {
+        const uint32_t tl = tmem + ((uint32_t)(32 * wq) << 16) + (uint32_t)((o & 1) * 64);
+        const int z = z0 + o;
+        for (int r = warp >> 2; r < TZ_TY; r += 2) {
+            const long long pt = ((long long)z * a.ny + (y0 + r)) * a.nx + x;
+            if (EPI == 0 || EPI == 3) {
+                float v[16];
+                tc_ld16(tl + 16 * r, v);
+                if (EPI == 0) {
+#pragma unroll
+                    for (int n = 0; n < 16; ++n) v[n] = fmaxf(v[n] + bias[n], 0.0f);
+                } else {
+                    const uint4* mk4 = reinterpret_cast<const uint4*>(a.mask + pt * 16);
+                    const uint4 m0 = __ldg(mk4), m1 = __ldg(mk4 + 1);
+                    const uint32_t mw[8] = {m0.x, m0.y, m0.z, m0.w, m1.x, m1.y, m1.z, m1.w};
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        if (!(mw[q] & 0x7fffu)) v[2 * q] = 0.0f;
+                        if (!(mw[q] & 0x7fff0000u)) v[2 * q + 1] = 0.0f;
+                    }
+                }
+                uint32_t o2[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    __nv_bfloat162 h2 = __floats2bfloat162_rn(v[2 * q], v[2 * q + 1]);
+                    o2[q] = *reinterpret_cast<uint32_t*>(&h2);
+                }
+                uint4* dst = reinterpret_cast<uint4*>(a.out + pt * 16);
+                dst[0] = make_uint4(o2[0], o2[1], o2[2], o2[3]);
+                dst[1] = make_uint4(o2[4], o2[5], o2[6], o2[7]);
+            } else {
+                const double y = (double)(tc_ld1(tl + 16 * r) + __ldg(a.bias));
+                const double pn = a.pn[pt], pm = a.pnm1[pt];
+                if (EPI == 1) {
+                    a.phat[pt] = 2.0 * pn - pm + a.sc[0] * y;
+                } else {
+                    const double e = y - (a.pnext[pt] - (2.0 * pn - pm)) * a.sc[1];
+                    sq += e * e;
+                    a.out[pt * 16] = __double2bfloat16(a.gscale * e);
+                }
+            }
+        }
+    };
+    auto wait_set = [&](int o) -> bool {      // MMAs of output plane o are complete (bounded)
+        const uint32_t m = smem_u32(mbar + (o & 1));
+        const uint32_t par = (o & 1) ? ph1 : ph0;
+        bool done = false;
+        for (int i = 0; i < (1 << 22) && !done; ++i) done = tc_mbar_try(m, par);
+        if (o & 1) ph1 ^= 1u; else ph0 ^= 1u;
+        const bool ok = __syncthreads_and(done);
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        return ok;
+    };
+    // descriptors: one per ring slot (row 0, tap offset 0) and per weight tap; the tap and row
+    // offsets are added to the 16-byte address field (no carry: shared addresses < 2^18)
+    const unsigned long long adesc0 = tc_desc(rb, TZ_PHALF, 128), bdesc0 = tc_desc(wb, 256, 128);
+    const bool issuer = lane == 0 && warp < TZ_TY;     // issues the MMAs of output row r = warp
+    for (int o = 0; o < zc; ++o) {
+        if (issuer) {
+            const int r = warp;
+            const uint32_t dcol = tmem + (uint32_t)((o & 1) * 64 + 16 * r);
+#pragma unroll
+            for (int tap = 0; tap < 27; ++tap) {
+                const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
+                const int slot = (o + 1 + dz) & 3;
+                const unsigned long long ad =
+                    adesc0 + (unsigned long long)((slot * TZ_PLANE) / 16 + (r + dy + 1) * TZ_HX + dx + 1);
+                const unsigned long long bd = bdesc0 + (unsigned long long)(tap * 32);
+                asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                             " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+                             ::"r"(dcol), "l"(ad), "l"(bd), "r"(TC_IDESC), "r"(tap) : "memory");
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                         ::"r"(smem_u32(mbar + (o & 1))) : "memory");
+        }
+        __syncwarp();
+        if (o > 0) {
+            // plane o-1 is done: store it; its last input plane's slot is free for input plane o+3
+            if (wait_set(o - 1)) epilogue(o - 1);
+            else fail = true;
+        }
+        if (o + 3 <= zc + 1)
+            tz_load_plane(src, ring + ((o + 3) & 3) * TZ_PLANE, x0, y0, wrapc(z0 + o + 2, a.nz), a.nx, a.ny);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    }
+    if (wait_set(zc - 1)) epilogue(zc - 1);
+    else fail = true;
+    if (fail && tid == 0) atomicExch(a.err, 1);
+    if (EPI == 2) {
+        __shared__ double ws[TZ_THREADS / 32];
+        for (int s2 = 16; s2 > 0; s2 >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, s2);
+        if (lane == 0) ws[warp] = sq;
+        __syncthreads();
+        if (tid == 0) {
+            double t = 0.0;
+            for (int w = 0; w < TZ_THREADS / 32; ++w) t += ws[w];
+            a.red[blockIdx.x] = t;
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TZ_TMEM_COLS) : "memory");
+}
+
 // Weight gradient of one layer over the CTA's tile:
 //   part[cta][tap][o][i] = sum_v dz(v)[o] act(v + tap)[i],  part[cta][6912 + o] = sum_v dz(v)[o]
 __global__ void __launch_bounds__(THREADS, 2) k_pnet_wgrad(const __nv_bfloat16* __restrict__ dz,
@@ -337,7 +738,8 @@ __global__ void k_pnet_reduce(const float* __restrict__ part, int ncta, float* _
 // Adam step (optional) and packing of the bfloat16 weights.
 __global__ void k_pnet_adam_pack(float* __restrict__ w, float* __restrict__ m, float* __restrict__ v,
                                  const float* __restrict__ grad, int adam, float lr, float bc1, float bc2,
-                                 __nv_bfloat16* __restrict__ wf, __nv_bfloat16* __restrict__ wb) {
+                                 __nv_bfloat16* __restrict__ wf, __nv_bfloat16* __restrict__ wb,
+                                 __nv_bfloat16* __restrict__ wtf, __nv_bfloat16* __restrict__ wtb) {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= PN_NP) return;
     float x = w[p];
@@ -358,6 +760,10 @@ __global__ void k_pnet_adam_pack(float* __restrict__ w, float* __restrict__ m, f
     const __nv_bfloat16 h = __float2bfloat16_rn(x);
     wf[(size_t)l * PN_WPK + (tap * 16 + oc) * 24 + ic] = h;
     if (l > 0) wb[(size_t)l * PN_WPK + ((26 - tap) * 16 + ic) * 24 + oc] = h;
+    // tcgen05 layout [tap][K half][row n][8 k]: forward rows = output channels, k = inputs;
+    // backward-data rows = input channels, k = output channels, taps reversed
+    wtf[(size_t)l * PN_TCW + tap * 256 + (ic >> 3) * 128 + oc * 8 + (ic & 7)] = h;
+    if (l > 0) wtb[(size_t)l * PN_TCW + (26 - tap) * 256 + (oc >> 3) * 128 + ic * 8 + (oc & 7)] = h;
 }
 
 __global__ void k_pnet_sumsq(const double* __restrict__ x, long long n, double* __restrict__ red) {
@@ -422,6 +828,10 @@ struct flups_pnet_s {
     cudaStream_t stream;
     float* w; float* m; float* v; float* grad;    // FP32 master weights, Adam moments, gradient
     __nv_bfloat16* wf; __nv_bfloat16* wb;         // packed bfloat16 weights (4 layers each)
+    __nv_bfloat16* wtf; __nv_bfloat16* wtb;       // the same in the tcgen05 layout
+    int* err;                                     // device error word (bounded waits)
+    int use_tc;                                   // nx % 128 == 0: convolutions on tcgen05
+    int last_red;                                 // CTAs of the last loss partials
     __nv_bfloat16* feat; __nv_bfloat16* act[3]; __nv_bfloat16* dy; __nv_bfloat16* g[2];
     float* part;                                  // weight-gradient partials [4][ncta][PN_PART]
     double* red;                                  // per-CTA scalar partials
@@ -486,6 +896,14 @@ cudaError_t set_smem_attrs() {
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_pnet_conv<1, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, CONV_SMEM);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_pnet_conv<1, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, CONV_SMEM);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_pnet_wgrad, cudaFuncAttributeMaxDynamicSharedMemorySize, WGRAD_SMEM);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_pnet_conv_tcz<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, TZ_SMEM);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_pnet_conv_tcz<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, TZ_SMEM);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_pnet_conv_tcz<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, TZ_SMEM);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_pnet_conv_tcz<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, TZ_SMEM);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_pnet_conv_tc<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_pnet_conv_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_pnet_conv_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_pnet_conv_tc<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
     if (e == cudaSuccess) done = dev;
     return e;
 }
@@ -495,6 +913,7 @@ ConvArgs conv_args(flups_pnet N) {
     std::memset(&a, 0, sizeof(a));
     a.sc = N->sc;
     a.red = N->red;
+    a.err = N->err;
     a.nx = N->nx; a.ny = N->ny; a.nz = N->nz;
     return a;
 }
@@ -502,7 +921,15 @@ ConvArgs conv_args(flups_pnet N) {
 template <int NT, int EPI>
 void conv(flups_pnet N, const ConvArgs& a) {
     pk_begin(N, EPI == 0 ? PK_CONV_HIDDEN : (EPI == 3 ? PK_CONV_BWD : PK_CONV_OUT));
-    k_pnet_conv<NT, EPI><<<N->ncta, THREADS, CONV_SMEM, N->stream>>>(a);
+    if (N->use_tc) {
+        const int zc = N->nz % 8 == 0 ? 8 : 4;
+        const int nb = (N->nx / 128) * (N->ny / TZ_TY) * (N->nz / zc);
+        k_pnet_conv_tcz<EPI><<<nb, TZ_THREADS, TZ_SMEM, N->stream>>>(a, zc);
+        if (EPI == 2) N->last_red = nb;
+    } else {
+        k_pnet_conv<NT, EPI><<<N->ncta, THREADS, CONV_SMEM, N->stream>>>(a);
+        if (EPI == 2) N->last_red = N->ncta;
+    }
     pk_end(N);
     N->launches++;
 }
@@ -516,7 +943,7 @@ void pack(flups_pnet N, int adam, float lr) {
     }
     pk_begin(N, PK_UPDATE);
     k_pnet_adam_pack<<<(PN_NP + 255) / 256, 256, 0, N->stream>>>(N->w, N->m, N->v, N->grad, adam, lr, bc1, bc2, N->wf,
-                                                                 N->wb);
+                                                                 N->wb, N->wtf, N->wtb);
     pk_end(N);
     N->launches++;
 }
@@ -535,6 +962,7 @@ void forward_hidden(flups_pnet N, const double* rho, double rho0, const double* 
         ConvArgs a = conv_args(N);
         a.in = in;
         a.w = N->wf + (size_t)l * PN_WPK;
+        a.wtc = N->wtf + (size_t)l * PN_TCW;
         a.bias = N->w + lay_b(l);
         a.out = N->act[l];
         conv<2, 0>(N, a);
@@ -548,6 +976,19 @@ void wgrad(flups_pnet N, int l, const __nv_bfloat16* dz, const __nv_bfloat16* ac
                                                               N->ny, N->nz);
     pk_end(N);
     N->launches++;
+}
+
+// Reads (and clears) the device error word: FLUPS_ETIMEOUT if a bounded wait gave up.  Synchronises.
+flups_status check_err(flups_pnet N) {
+    int h = 0;
+    cudaError_t e = cudaMemcpyAsync(&h, N->err, sizeof(int), cudaMemcpyDeviceToHost, N->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(N->stream);
+    if (e != cudaSuccess) return pn_status(e);
+    if (h) {
+        cudaMemsetAsync(N->err, 0, sizeof(int), N->stream);
+        return FLUPS_ETIMEOUT;
+    }
+    return FLUPS_OK;
 }
 
 flups_status check_fields(flups_pnet N, const double* rho, double rho0, const double* pn, const double* pnm1) {
@@ -583,10 +1024,13 @@ flups_status flups_pnet_create(flups_pnet* out, int nx, int ny, int nz, const fl
     const size_t fbytes = (size_t)N->n * 16 * sizeof(__nv_bfloat16);
     const size_t off_w = 0, off_wf = 4 * (size_t)16384 * 4;
     const size_t off_wb = off_wf + 4 * (size_t)PN_WPK * 2;
-    const size_t off_feat = (off_wb + 4 * (size_t)PN_WPK * 2 + 255) / 256 * 256;
+    const size_t off_wtf = off_wb + 4 * (size_t)PN_WPK * 2;
+    const size_t off_wtb = off_wtf + 4 * (size_t)PN_TCW * 2;
+    const size_t off_err = off_wtb + 4 * (size_t)PN_TCW * 2;
+    const size_t off_feat = (off_err + 16 + 255) / 256 * 256;
     const size_t off_part = off_feat + 7 * fbytes;
     const size_t off_red = off_part + 4 * (size_t)N->ncta * PN_PART * sizeof(float);
-    const size_t off_sc = off_red + (size_t)std::max(N->nred, N->ncta) * sizeof(double);
+    const size_t off_sc = off_red + (size_t)std::max(N->nred, 2 * N->ncta) * sizeof(double);
     const size_t total = off_sc + 8 * sizeof(double);
     e = cudaMalloc(&N->base, total);
     if (e != cudaSuccess) { delete N; return pn_status(e); }
@@ -597,6 +1041,11 @@ flups_status flups_pnet_create(flups_pnet* out, int nx, int ny, int nz, const fl
     N->grad = N->v + 16384;
     N->wf = (__nv_bfloat16*)(b + off_wf);
     N->wb = (__nv_bfloat16*)(b + off_wb);
+    N->wtf = (__nv_bfloat16*)(b + off_wtf);
+    N->wtb = (__nv_bfloat16*)(b + off_wtb);
+    N->err = (int*)(b + off_err);
+    N->use_tc = nx % 128 == 0;
+    N->last_red = N->ncta;
     __nv_bfloat16* f = (__nv_bfloat16*)(b + off_feat);
     const size_t fe = (size_t)N->n * 16;
     N->feat = f;
@@ -700,16 +1149,16 @@ flups_status flups_pnet_get_params(flups_pnet N, float* params) {
     if (!N || !params) return FLUPS_EINVAL;
     PnGuard dg(N->dev);
     cudaError_t e = cudaMemcpyAsync(params, N->w, PN_NP * sizeof(float), cudaMemcpyDeviceToHost, N->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(N->stream);
-    return pn_status(e);
+    if (e != cudaSuccess) return pn_status(e);
+    return check_err(N);
 }
 
 flups_status flups_pnet_get_grads(flups_pnet N, float* grads) {
     if (!N || !grads) return FLUPS_EINVAL;
     PnGuard dg(N->dev);
     cudaError_t e = cudaMemcpyAsync(grads, N->grad, PN_NP * sizeof(float), cudaMemcpyDeviceToHost, N->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(N->stream);
-    return pn_status(e);
+    if (e != cudaSuccess) return pn_status(e);
+    return check_err(N);
 }
 
 flups_status flups_pnet_predict(flups_pnet N, const double* rho, double rho0, const double* p_n, const double* p_nm1,
@@ -722,6 +1171,7 @@ flups_status flups_pnet_predict(flups_pnet N, const double* rho, double rho0, co
     ConvArgs a = conv_args(N);
     a.in = N->act[2];
     a.w = N->wf + 3 * (size_t)PN_WPK;
+    a.wtc = N->wtf + 3 * (size_t)PN_TCW;
     a.bias = N->w + lay_b(3);
     a.pn = p_n; a.pnm1 = p_nm1; a.phat = p_hat;
     conv<1, 1>(N, a);
@@ -740,13 +1190,14 @@ static flups_status pnet_loss(flups_pnet N, const double* rho, double rho0, cons
     ConvArgs a = conv_args(N);
     a.in = N->act[2];
     a.w = N->wf + 3 * (size_t)PN_WPK;
+    a.wtc = N->wtf + 3 * (size_t)PN_TCW;
     a.bias = N->w + lay_b(3);
     a.pn = p_n; a.pnm1 = p_nm1; a.pnext = p_next;
     a.out = N->dy;
     a.gscale = 2.0 / (double)N->n;
     conv<1, 2>(N, a);
     pk_begin(N, PK_UPDATE);
-    k_pnet_fin<<<1, 1024, 0, N->stream>>>(N->red, N->ncta, N->sc, 1, 1.0 / (double)N->n);
+    k_pnet_fin<<<1, 1024, 0, N->stream>>>(N->red, N->last_red, N->sc, 1, 1.0 / (double)N->n);
     pk_end(N);
     N->launches++;
     if (train) {
@@ -757,6 +1208,7 @@ static flups_status pnet_loss(flups_pnet N, const double* rho, double rho0, cons
             ConvArgs b = conv_args(N);
             b.in = dzl;
             b.w = N->wb + (size_t)l * PN_WPK;
+            b.wtc = N->wtb + (size_t)l * PN_TCW;
             b.mask = N->act[l - 1];
             b.out = gout;
             conv<2, 3>(N, b);
@@ -775,8 +1227,9 @@ static flups_status pnet_loss(flups_pnet N, const double* rho, double rho0, cons
     if (e != cudaSuccess) return pn_status(e);
     if (loss) {
         e = cudaMemcpyAsync(N->sc_host, N->sc, 3 * sizeof(double), cudaMemcpyDeviceToHost, N->stream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(N->stream);
         if (e != cudaSuccess) return pn_status(e);
+        st = check_err(N);
+        if (st != FLUPS_OK) return st;
         *loss = N->sc_host[2];
         if (!std::isfinite(*loss)) return FLUPS_ENONFINITE;
     }

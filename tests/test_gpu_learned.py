@@ -132,7 +132,8 @@ def check_close(y_gpu, y_ref, what):
     assert np.mean(err) <= 1e-4 * scale, (what, np.mean(err) / scale)
 
 
-@pytest.mark.parametrize("shape", [(8, 16, 32), (12, 8, 64)])
+# nx = 32, 64: mma.sync kernels; nx = 128, 256: tcgen05 kernels (tensor-memory accumulators)
+@pytest.mark.parametrize("shape", [(8, 16, 32), (12, 8, 64), (4, 8, 128), (8, 8, 256)])
 def test_forward_matches_oracle(shape):
     rho, pn, pnm1, _ = net_inputs(shape, 5)
     params = rand_params(50)
@@ -159,11 +160,12 @@ def test_zero_pressure_uses_unit_scale():
     check_close(ph.cpu().numpy(), y_o[0], "y")
 
 
-def test_gradients_match_oracle():
-    shape = (8, 16, 32)
+@pytest.mark.parametrize("shape", [(8, 16, 32), (4, 8, 128)])
+def test_gradients_match_oracle(shape):
     rho, pn, pnm1, pnext = net_inputs(shape, 7)
     params = rand_params(52)
-    with flups.PNet(32, 16, 8, params) as net:
+    nz, ny, nx = shape
+    with flups.PNet(nx, ny, nz, params) as net:
         loss = net.train_step(dev(rho), 1.0, dev(pn), dev(pnm1), dev(pnext), 0.0)
         grads = net.grads()
         assert np.array_equal(net.params(), params)            # lr = 0 leaves the weights alone
