@@ -400,7 +400,8 @@ def run_learned(args):
                      "achieved": round(achieved, 2), "peak": pk["bf16_tflops"], "unit": "TFLOP/s",
                      "frac": round(achieved / pk["bf16_tflops"], 4), "traffic": None,
                      "algorithmic": f"{PNET_FLOPS['hidden']} flops/pt (layers 3->16, 16->16, 16->16)",
-                     "peak_source": f"MEASURED_PEAKS.json bf16_tflops ({pk_kind}); mma.sync bf16 path"},
+                     "peak_source": f"MEASURED_PEAKS.json bf16_tflops ({pk_kind}); tcgen05 bf16 MMA, FP32 in "
+                                    "tensor memory"},
     }
 
 
