@@ -296,14 +296,14 @@ def run_ensemble(args):
     t0 = time.perf_counter()
     with flups.Batch(specs, nstreams=8, autotune=True) as b:
         t_tune = time.perf_counter() - t0
-        infos = b.solve(fs, ps, rtol=args.rtol, max_iter=6)           # capture + first launch
+        infos = b.solve(fs, ps, rtol=args.rtol, max_iter=GRAPH_MAX_ITER)   # capture + first launch
         for _ in range(2):
-            b.solve(fs, ps, rtol=args.rtol, max_iter=6, info=False)
+            b.solve(fs, ps, rtol=args.rtol, max_iter=GRAPH_MAX_ITER, info=False)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
         e0.record()
         for _ in range(args.steps):
-            b.solve(fs, ps, rtol=args.rtol, max_iter=6, info=False)
+            b.solve(fs, ps, rtol=args.rtol, max_iter=GRAPH_MAX_ITER, info=False)
         e1.record()
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / args.steps

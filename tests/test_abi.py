@@ -87,3 +87,29 @@ def test_no_cpu_fallback_when_library_missing(monkeypatch, tmp_path):
     monkeypatch.setattr(flups, "LIB_PATH", str(tmp_path / "missing.so"))
     with pytest.raises(RuntimeError):
         flups.lib()
+
+
+def test_pnet_create_rejects_bad_sizes_and_params(lib):
+    """Size and parameter checks of flups_pnet_create happen before any GPU work."""
+    params = np.zeros(flups.PNET_NPARAMS, np.float32)
+    pp = params.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+    h = ctypes.c_void_p()
+    for nx, ny, nz in ((16, 8, 4), (48, 8, 4), (32, 12, 4), (32, 8, 6), (32, 8, 2)):
+        assert lib.flups_pnet_create(ctypes.byref(h), nx, ny, nz, pp, None) == flups.EUNSUPPORTED, (nx, ny, nz)
+    assert lib.flups_pnet_create(ctypes.byref(h), 32, 8, 4, None, None) == flups.EINVAL
+    bad = params.copy()
+    bad[7] = np.nan
+    assert lib.flups_pnet_create(ctypes.byref(h), 32, 8, 4, bad.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                 None) == flups.EINVAL
+    assert lib.flups_pnet_create(None, 32, 8, 4, pp, None) == flups.EINVAL
+
+
+def test_null_handles_are_rejected(lib):
+    assert lib.flups_varcoef_solve(None, None, None, None, 1e-12, 10, None) == flups.EINVAL
+    for fn in ("flups_pnet_destroy", "flups_pnet_set_profiling"):
+        args = (None,) if fn == "flups_pnet_destroy" else (None, 1)
+        assert getattr(lib, fn)(*args) == flups.EINVAL
+    assert lib.flups_pnet_predict(None, None, 1.0, None, None, None) == flups.EINVAL
+    assert lib.flups_pnet_launch_count(None) == 0
+    assert lib.flups_pnet_kernel_name(99).decode() == "unknown"
+    assert lib.flups_selftest_wait_timeout(None, 0) == flups.EINVAL
