@@ -17,15 +17,24 @@ namespace {
 
 // 1/s for s in the normal FP32 range: FP32 hardware seed (rcp.approx) refined by two
 // Newton-Raphson steps y <- y + y (1 - s y) in FP64 (each step squares the relative error).
+// The FP64 <-> FP32 conversions of the seed are done on the bit patterns with integer
+// operations (truncating s to 24 bits and widening y exactly), since GB300's conversion
+// instructions run on the narrow FP64 pipe; the seed only needs ~2^-22 relative accuracy.
 __device__ __forceinline__ double recip64(double s) {
-    const float sf = __double2float_rn(s);
+    const unsigned long long b = (unsigned long long)__double_as_longlong(s);
+    const unsigned int hi = (unsigned int)(b >> 32);
+    const unsigned int e = (hi >> 20) & 0x7FFu;                    // 897 <= e <= 1150 (normal FP32)
+    const float sf = __uint_as_float((hi & 0x80000000u) | ((e - 896u) << 23) | ((unsigned int)(b >> 29) & 0x7FFFFFu));
     float yf;
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(yf) : "f"(sf));
-    double y = (double)yf;
-    double e = fma(-s, y, 1.0);
-    y = fma(y, e, y);
-    e = fma(-s, y, 1.0);
-    return fma(y, e, y);
+    const unsigned int yb = __float_as_uint(yf);
+    const unsigned int ye = (yb >> 23) & 0xFFu;
+    double y = __hiloint2double((int)((yb & 0x80000000u) | ((ye + 896u) << 20) | ((yb & 0x7FFFFFu) >> 3)),
+                                (int)((yb & 7u) << 29));
+    double e1 = fma(-s, y, 1.0);
+    y = fma(y, e1, y);
+    e1 = fma(-s, y, 1.0);
+    return fma(y, e1, y);
 }
 
 // Valid densities: finite and within [1e-30, 1e30] (so the FP32 seed above is normal).
