@@ -994,10 +994,11 @@ FftLen packed(FftLen L) {
     return L;
 }
 
-// Tile of the pipelined kernel: B columns with B * N * 8 bytes <= 64 KB, B <= 16, B <= M.
+// Tile of the pipelined kernel: B columns with B * N * 8 bytes <= 32 KB, B <= 16, B <= M (tiles
+// small enough for two CTAs per SM, which overlap one's FFT with the other's copies).
 int pipe_lgB(int N, int M) {
     int B = 16;
-    while (B > 1 && ((long)B * N * 8 > 64 * 1024 || B > M)) B >>= 1;
+    while (B > 1 && ((long)B * N * 8 > 32 * 1024 || B > M)) B >>= 1;
     return ilog2i(B);
 }
 // The pipelined path needs its tensor map (built with the plan), rows of at least 16 bytes
@@ -1019,7 +1020,12 @@ void run_cols_pipe(flups_plan P, float2* S, const Geo& g, const FftLen& L, const
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     const int ntiles = (g.M / B) * (KIND == 0 ? g.nz : g.ny);
-    const int grid = ntiles < nsm ? ntiles : nsm;
+    // persistent CTAs: as many per SM as threads (1024 at 64 registers) and shared memory allow
+    const int thr = B * N / 8;
+    int per_sm = 1024 / thr;
+    while (per_sm > 1 && (size_t)per_sm * (sm + 1024) > 220 * 1024) --per_sm;
+    if (per_sm < 1) per_sm = 1;
+    const int grid = ntiles < per_sm * nsm ? ntiles : per_sm * nsm;
     kern<<<grid, B * N / 8, sm, P->stream>>>(S, KIND == 0 ? P->tm_y : P->tm_z, g, L, tw, (const float*)P->lamx,
                                              (const float*)P->lamy, (const float*)P->lamz, lgB, N < 256 ? N : 256,
                                              &P->sc->err);
