@@ -902,50 +902,81 @@ __global__ void __launch_bounds__(128) k_ztri(typename cplx<T>::t* __restrict__ 
     }
 }
 
-// Deterministic final reduction of the per-block partial sums (one block).
-__global__ void k_finalize(const double* __restrict__ part, int nblk, DevScalars* sc, int what, double nrm_w,
-                           double npts, int fixed, double thr2) {
-    if (fixed && sc->done) return;   // fixed-iteration solve: the member converged earlier
-    __shared__ double red[3][32];
-    double a = 0.0, b = 0.0, c = 0.0;
-#pragma unroll 8
-    for (int i = threadIdx.x; i < nblk; i += blockDim.x) {
-        a += __ldg(part + 3 * i + 0);
-        b += __ldg(part + 3 * i + 1);
-        c += __ldg(part + 3 * i + 2);
-    }
+// Deterministic final reduction of the per-block partial sums in one launch: block g of G sums
+// a contiguous chunk of the partials into fin[3 g + q]; the last block to finish (atomic
+// ticket) adds the G chunk sums in a fixed order and derives the scalars.  The ticket is reset
+// by that block, so the kernel can be replayed (graphs).
+constexpr int FIN_THREADS = 256;
+__device__ __forceinline__ void fin_block_sum(double& a, double& b, double& c, double (*red)[FIN_THREADS / 32]) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         a += __shfl_down_sync(0xffffffffu, a, o);
         b += __shfl_down_sync(0xffffffffu, b, o);
         c += __shfl_down_sync(0xffffffffu, c, o);
     }
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     if (lane == 0) { red[0][wid] = a; red[1][wid] = b; red[2][wid] = c; }
     __syncthreads();
-    if (wid == 0) {
-        a = lane < nw ? red[0][lane] : 0.0;
-        b = lane < nw ? red[1][lane] : 0.0;
-        c = lane < nw ? red[2][lane] : 0.0;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            a += __shfl_down_sync(0xffffffffu, a, o);
-            b += __shfl_down_sync(0xffffffffu, b, o);
-            c += __shfl_down_sync(0xffffffffu, c, o);
-        }
-        if (lane == 0) {
-            if (what == 0) {          // a = sum dzf f, b = sum f^2, c = sum f
-                const double m = a * nrm_w;
-                sc->mean_f = m;
-                sc->f2 = b - 2.0 * m * c + npts * m * m;
-            } else if (what == 1) {   // b = sum r^2
-                sc->r2 = b;
-                if (fixed && b <= thr2 * sc->f2) sc->done = 1;
-            } else {                  // a = sum dzf p
-                sc->mean_p = a * nrm_w;
-            }
+    if (threadIdx.x == 0) {
+        a = red[0][0]; b = red[1][0]; c = red[2][0];
+        for (int w = 1; w < FIN_THREADS / 32; ++w) { a += red[0][w]; b += red[1][w]; c += red[2][w]; }
+    }
+}
+
+__global__ void __launch_bounds__(FIN_THREADS) k_finalize(const double* __restrict__ part, int nblk, DevScalars* sc,
+                                                        int what, double nrm_w, double npts, int fixed, double thr2,
+                                                        double* __restrict__ fin) {
+    if (fixed && sc->done) return;   // fixed-iteration solve: the member converged earlier
+    __shared__ double red[3][FIN_THREADS / 32];
+    __shared__ int last;
+    const int G = gridDim.x;
+    const int chunk = (nblk + G - 1) / G;
+    const int i0 = blockIdx.x * chunk, i1 = min(nblk, i0 + chunk);
+    double a = 0.0, b = 0.0, c = 0.0;
+#pragma unroll 4
+    for (int i = i0 + threadIdx.x; i < i1; i += FIN_THREADS) {
+        a += __ldcg(part + 3 * i + 0);
+        b += __ldcg(part + 3 * i + 1);
+        c += __ldcg(part + 3 * i + 2);
+    }
+    fin_block_sum(a, b, c, red);
+    if (threadIdx.x == 0) {
+        fin[3 * blockIdx.x + 0] = a;
+        fin[3 * blockIdx.x + 1] = b;
+        fin[3 * blockIdx.x + 2] = c;
+        __threadfence();
+        last = atomicAdd(&sc->fin_count, 1u) == (unsigned)(G - 1);
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    a = b = c = 0.0;
+    if (threadIdx.x < G) {
+        a = __ldcg(fin + 3 * threadIdx.x + 0);
+        b = __ldcg(fin + 3 * threadIdx.x + 1);
+        c = __ldcg(fin + 3 * threadIdx.x + 2);
+    }
+    __syncthreads();
+    fin_block_sum(a, b, c, red);
+    if (threadIdx.x == 0) {
+        sc->fin_count = 0u;
+        if (what == 0) {          // a = sum dzf f, b = sum f^2, c = sum f
+            const double m = a * nrm_w;
+            sc->mean_f = m;
+            sc->f2 = b - 2.0 * m * c + npts * m * m;
+        } else if (what == 1) {   // b = sum r^2
+            sc->r2 = b;
+            if (fixed && b <= thr2 * sc->f2) sc->done = 1;
+        } else {                  // a = sum dzf p
+            sc->mean_p = a * nrm_w;
         }
     }
+}
+
+// Blocks of the final reduction for nblk partials (at most FIN_THREADS).
+int fin_grid(int nblk) {
+    int g = nblk / 64;
+    return g < 1 ? 1 : (g > FIN_THREADS ? FIN_THREADS : g);
 }
 
 // ------------------------------------------------------------------- host helpers
@@ -1199,8 +1230,9 @@ cudaError_t launch_xfwd32_from_f(flups_plan P, const double* f) {
 cudaError_t launch_finalize_f(flups_plan P) {
     const int nblk = xfwd_blocks(P, 8, 0);
     flups_prof_begin(P, FK_FINALIZE);
-    k_finalize<<<1, 1024, 0, P->stream>>>(P->part, nblk, P->sc, 0, 1.0 / ((double)P->nx * P->ny * P->sum_dzf),
-                                          (double)P->npts, 0, 0.0);
+    k_finalize<<<fin_grid(nblk), FIN_THREADS, 0, P->stream>>>(P->part, nblk, P->sc, 0,
+                                                              1.0 / ((double)P->nx * P->ny * P->sum_dzf),
+                                                              (double)P->npts, 0, 0.0, P->fin);
     flups_prof_end(P);
     FLUPS_COUNT(P, 1);
     return cudaGetLastError();
@@ -1216,7 +1248,7 @@ cudaError_t launch_xfwd32_residual(flups_plan P, const double* f, const double* 
 cudaError_t launch_finalize_r(flups_plan P) {
     const int nblk = xfwd_blocks(P, 8, 1);
     flups_prof_begin(P, FK_FINALIZE);
-    k_finalize<<<1, 1024, 0, P->stream>>>(P->part, nblk, P->sc, 1, 0.0, 0.0, 0, 0.0);
+    k_finalize<<<fin_grid(nblk), FIN_THREADS, 0, P->stream>>>(P->part, nblk, P->sc, 1, 0.0, 0.0, 0, 0.0, P->fin);
     flups_prof_end(P);
     FLUPS_COUNT(P, 1);
     return cudaGetLastError();
@@ -1237,7 +1269,9 @@ cudaError_t launch_xinv32(flups_plan P, double* p, int mode) {
         run_xinv<float, 0, true, false>(P, p, g);
         const int nblk = xfwd_blocks(P, 8, 0);
         flups_prof_begin(P, FK_FINALIZE);
-        k_finalize<<<1, 1024, 0, P->stream>>>(P->part, nblk, P->sc, 2, 1.0 / ((double)P->nx * P->ny * P->sum_dzf), 0.0, 0, 0.0);
+        k_finalize<<<fin_grid(nblk), FIN_THREADS, 0, P->stream>>>(P->part, nblk, P->sc, 2,
+                                                                  1.0 / ((double)P->nx * P->ny * P->sum_dzf), 0.0, 0,
+                                                                  0.0, P->fin);
         flups_prof_end(P);
         FLUPS_COUNT(P, 1);
     } else if (mode == 1) {                // p += delta - <p_0>
@@ -1287,7 +1321,8 @@ cudaError_t launch_solve32_fixed(flups_plan P, const double* f, double* p, doubl
         launch_xfwd32_residual(P, f, p);
         {
             const int nblk = xfwd_blocks(P, 8, 1);
-            k_finalize<<<1, 1024, 0, P->stream>>>(P->part, nblk, P->sc, 1, nrm_w, 0.0, 1, thr2);
+            k_finalize<<<fin_grid(nblk), FIN_THREADS, 0, P->stream>>>(P->part, nblk, P->sc, 1, nrm_w, 0.0, 1, thr2,
+                                                                      P->fin);
             FLUPS_COUNT(P, 1);
         }
         if (it == max_iter) break;

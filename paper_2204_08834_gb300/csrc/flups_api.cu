@@ -318,6 +318,7 @@ flups_status flups_plan_create(flups_plan* out, int nx, int ny, int nz, double d
         P->npart = std::max<size_t>(3 * std::max<size_t>(flups_part_blocks_needed(nx, ny, nz), 2048), 2 * ntiles);
     }
     P->part = (double*)A.get(P->npart * sizeof(double));
+    P->fin = (double*)A.get(3 * 256 * sizeof(double));
     P->tabs64 = (double*)A.get(6 * (size_t)nz * sizeof(double));
     bool ok = A.ok;
     if (ok) {

@@ -50,6 +50,7 @@ struct DevScalars {
     int    pexp;        // largest binary64 exponent field of p written by the last FP32 inverse-x pass
     int    err;         // nonzero: a bounded device-side wait timed out (the result is invalid)
     int    done;        // graph-capturable solve: the defect reached rtol, later iterations skip
+    unsigned int fin_count;   // blocks of the running final reduction that have finished
 };
 
 // Geometry and tables handed to kernels by value.
@@ -99,6 +100,7 @@ struct flups_plan_s {
     DevScalars* sc;              // device scalars
     DevScalars* sc_host;         // pinned host mirror
     double* part;                // reduction partials
+    double* fin;                 // per-block sums of the final reduction (3 x 256)
     size_t npart;
     // tables (device)
     void* twx; void* twxr; void* twy; void* twz;   // W_M, W_nx (k<=M), W_ny, W_nz in compute type
