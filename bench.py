@@ -58,8 +58,12 @@ KERNEL_WORK = {
     "k_zper32": {"bound": "hbm", "bytes": 4 + 4},
     "k_ztri32": {"bound": "hbm", "bytes": 4 + 4},
     "k_xinv32": {"bound": "hbm", "bytes": 4 + 12},   # mean of p = (first) and p += (later)
-    "k_face_coeffs": {"bound": "hbm", "bytes": 8 + 24},
+    "k_face_coeffs": {"bound": "hbm", "bytes": None},   # works only in tiles where the density varies
     "k_rho_tiles": {"bound": "hbm", "bytes": 8},
+    # constant-density tiles: rhs reads u, v, w and writes f; correct reads p and u, v, w and
+    # writes u, v, w (p_n, p_{n-1} and the face coefficients only where the density varies)
+    "k_rhs": {"bound": "hbm", "bytes": 32},
+    "k_correct": {"bound": "hbm", "bytes": 56},
 }
 
 
@@ -238,6 +242,13 @@ def run_ours(args, rank, world, dev):
         t32, t64 = float(tt[0]), float(tt[1])
 
     out = {"c": c, "npts": npts, "res": res, "t32": t32, "t64": t64, "clocks": clk.summary(), "prof": prof}
+    if not args.no_cufft and c.bc == "periodic":
+        with flups.Plan(nx, ny, nz, c.dx, c.dy, c.dzf, c.bc, "fp64", stream) as plan:
+            plan.set_density(d0["rho"])
+            plan.rhs(d0["u"], d0["v"], d0["w"], d0["pn"], d0["pnm1"], 2.0, 1.0, c.dt, f)
+            plan.solve(f, p, rtol=0.0, info=False)
+        torch.cuda.synchronize()
+        out["cufft"] = cufft_baseline(c, f, p, max(args.steps, 5))
     if not args.no_ensemble:
         out["ensemble"] = run_ensemble(args)
     if not args.no_learned:
@@ -312,6 +323,53 @@ def run_ensemble(args):
             "mpts_per_s": round(pts / (ms * 1e-3) / 1e6, 2), "graph_kernels": int(kernels),
             "max_rel_res": max(i.rel_res for i in infos), "autotune_s": round(t_tune, 2),
             "sizes": "{32,48,64,96,128}^3, periodic (even m) / z walls (odd m), density ratio U[1,20]"}
+
+
+def cufft_baseline(c, f, p_ours, steps):
+    """The periodic direct solve with cuFFT (torch.fft: D2Z/Z2D or R2C/C2R over three axes,
+    division by the discrete Laplacian's eigenvalues, zero mode set to 0) on the same right-hand
+    side, timed with CUDA events like our solve; a reported baseline only (cuFFT is run and
+    timed, nothing of it is on the library's path).  Also the largest difference of its FP64 p
+    from ours, relative to max |p|."""
+    import torch
+
+    if c.bc != "periodic":
+        return None
+    nz, ny, nx = c.shape
+    out = {}
+    for name, dt in (("fp64", torch.float64), ("fp32", torch.float32)):
+        kx = torch.arange(nx // 2 + 1, device="cuda", dtype=torch.float64)
+        ky = torch.arange(ny, device="cuda", dtype=torch.float64)
+        kz = torch.arange(nz, device="cuda", dtype=torch.float64)
+        lam = (-4.0 * torch.sin(torch.pi * kx / nx) ** 2 / c.dx ** 2)[None, None, :] \
+            + (-4.0 * torch.sin(torch.pi * ky / ny) ** 2 / c.dy ** 2)[None, :, None] \
+            + (-4.0 * torch.sin(torch.pi * kz / nz) ** 2 / c.dzf[0] ** 2)[:, None, None]
+        inv = torch.where(lam == 0, torch.zeros_like(lam), 1.0 / lam).to(dt)
+        del lam
+        fi = f.to(dt)
+
+        def solve():
+            return torch.fft.irfftn(torch.fft.rfftn(fi) * inv, s=(nz, ny, nx))
+
+        for _ in range(2):
+            pc = solve()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            pc = solve()
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        entry = {"ms_per_solve": round(ms, 4), "mpts_per_s": round(c.npts / (ms * 1e-3) / 1e6, 2)}
+        if name == "fp64" and p_ours is not None:
+            pc = pc - pc.mean()
+            entry["max_diff_vs_ours_rel"] = float((pc - p_ours).abs().max() / p_ours.abs().max())
+        out[name] = entry
+        del pc, fi, inv
+        torch.cuda.empty_cache()
+    out["kind"] = "cuFFT through torch.fft, periodic direct solve (reported baseline, not on the library path)"
+    return out
 
 
 # Algorithmic flops per grid point of the learned p_hat's convolutions (FMA = 2): 27 taps x
@@ -467,6 +525,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-ensemble", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
+    ap.add_argument("--no-cufft", action="store_true")
     ap.add_argument("--learned-windows", type=int, default=100,
                     help="64^3 training windows of 20 samples (default 100: 2000 samples)")
     ap.add_argument("--learned-epochs", type=int, default=3)
@@ -504,8 +563,18 @@ def main():
     pk, pk_kind = peaks()
     prof = out["prof"]
     tot_prof = sum(ms for ms, n in prof.values()) or 1.0
-    kernels = {k: {"ms_per_step": round(ms, 4), "launch_regions_per_step": n, "share": round(ms / tot_prof, 4)}
-               for k, (ms, n) in sorted(prof.items(), key=lambda kv: -kv[1][0])}
+    pk0, _ = peaks()
+
+    def kernel_entry(k, ms, n):
+        e = {"ms_per_step": round(ms, 4), "launch_regions_per_step": n, "share": round(ms / tot_prof, 4)}
+        w = KERNEL_WORK.get(k)
+        if w and w.get("bytes") and n:
+            gbs = w["bytes"] * npts / (ms / n * 1e-3) / 1e9
+            e["algorithmic_GBps"] = round(gbs, 1)
+            e["hbm_frac"] = round(gbs / pk0["hbm_gbs"], 4)
+        return e
+
+    kernels = {k: kernel_entry(k, ms, n) for k, (ms, n) in sorted(prof.items(), key=lambda kv: -kv[1][0])}
     dom = max(prof, key=lambda k: prof[k][0])
     work = KERNEL_WORK.get(dom, {"bound": "hbm", "bytes": None})
     dom_ms_per_region = prof[dom][0] / max(prof[dom][1], 1e-9)
@@ -579,6 +648,11 @@ def main():
         line["e2e"] = {"value": round(world * npts * ne / t_e2e / 1e6, 2), "unit": "Mpts/s",
                        "h2d_bytes_per_step": 6 * 8 * npts, "d2h_bytes_per_step": 4 * 8 * npts,
                        "steps": ne, "call": "flups_project_host (pinned host buffers)"}
+    if out.get("cufft"):
+        cu = out["cufft"]
+        cu["ours_fp64_solve_mpts"] = line["fp64"]["solve_mpts"]
+        cu["ours_fp32_refine_solve_mpts"] = line["solve_mpts"]
+        line["cufft_baseline"] = cu
     if "ensemble" in out:
         line["ensemble"] = out["ensemble"]
     if "learned" in out:
