@@ -99,7 +99,7 @@ unsigned long long flups_launch_count(flups_plan plan);
  * total milliseconds ms[k] and the number of timed regions n[k] (HOST arrays) recorded
  * since the previous read.  flups_kernel_name(k) names kernel id k (static string).
  */
-#define FLUPS_NKERNELS 18
+#define FLUPS_NKERNELS 20
 flups_status flups_set_profiling(flups_plan plan, int on);
 flups_status flups_profile_read(flups_plan plan, double* ms, long long* n);
 const char*  flups_kernel_name(int id);
@@ -315,6 +315,35 @@ unsigned long long flups_pnet_launch_count(flups_pnet net);
 flups_status flups_pnet_set_profiling(flups_pnet net, int on);
 flups_status flups_pnet_profile_read(flups_pnet net, double* ms, long long* n);
 const char* flups_pnet_kernel_name(int id);
+
+/*
+ * flups_momentum_predict - the momentum predictor of one phase (Sec. 3.3, Eq. uss_predic),
+ * the step before flups_rhs, on the plan's grid (z must be periodic):
+ *   M^n = -D(u^n u^n) + nu L u^n,   u** = u^n + dt (f1 M^n - f2 M^{n-1} + g),
+ *   f1 = 1 + dt/(2 dt_prev), f2 = dt/(2 dt_prev)  (second-order Adams-Bashforth, Sec. 3.2/3.3).
+ * The convective flux is in divergence form from two-point averages (u u at cell centres,
+ * u v, u w, v w on cell edges), L the 7-point Laplacian; constant density and viscosity,
+ * so surface tension vanishes and the body force is the constant acceleration g.
+ *   u, v, w    : u^n, DEVICE, read only (layout above).
+ *   us, vs, ws : u**, DEVICE, written.  No output may overlap another argument.
+ *   m_state    : DEVICE, 3 x nz*ny*nx pairs of float32 (hi, lo) = 24 bytes per cell, 16-byte
+ *                aligned, [component][nz][ny][nx]: M^{n-1} on entry (read only when
+ *                dt_prev > 0), M^n on return (hi + lo carries 48 significant bits).
+ *   nu         : kinematic viscosity >= 0;  gx, gy, gz : body acceleration.
+ *   dt > 0; dt_prev <= 0 marks the first step (forward Euler, M^{n-1} not read).
+ *   arith      : FLUPS_MOM_PAIR - M in pairs of float32 on a fixed-point grid set by
+ *                max(|u|,|v|,|w|) (an extra pass over u, v, w), error ~2^-38 max|u|^2/h in M;
+ *                needs dx = dy = dz; velocities whose maximum lies outside the range the
+ *                pair arithmetic covers are computed in float64 by the same launch.
+ *                FLUPS_MOM_FP64 - float64 throughout, any spacings.
+ * Returns FLUPS_EUNSUPPORTED for z walls or FLUPS_MOM_PAIR on unequal spacings,
+ * FLUPS_EINVAL for bad arguments.  Stream-ordered, no synchronisation, graph capturable.
+ */
+#define FLUPS_MOM_PAIR 0
+#define FLUPS_MOM_FP64 1
+flups_status flups_momentum_predict(flups_plan plan, const double* u, const double* v, const double* w,
+                                    double* us, double* vs, double* ws, void* m_state, double nu,
+                                    double gx, double gy, double gz, double dt, double dt_prev, int arith);
 
 /* flups_selftest_wait_timeout - diagnostic of the library's failure detection (no paper
  * counterpart): launches one kernel whose thread waits, through the same bounded wait the

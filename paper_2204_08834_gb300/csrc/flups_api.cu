@@ -189,7 +189,7 @@ flups_status sync_scalars(flups_plan P) {
 static const char* kKernelNames[FK_COUNT] = {
     "k_rho_tiles", "k_face_coeffs", "k_rhs", "k_correct", "k_xfwd_f32", "k_xfwd_residual32", "k_ycol32",
     "k_zper32", "k_ztri32", "k_xinv32", "k_finalize", "k_xfwd64", "k_ycol64", "k_zper64", "k_ztri64", "k_xinv64",
-    "k_res64", "k_rho_finalize"};
+    "k_res64", "k_rho_finalize", "k_mom_umax", "k_momentum"};
 
 void flups_prof_begin(flups_plan P, int kid) {
     P->prof_open = 0;
@@ -292,6 +292,7 @@ flups_status flups_plan_create(flups_plan* out, int nx, int ny, int nz, double d
     P->npts = (size_t)nx * ny * nz;
     P->nspec = (size_t)P->ldS * ny * nz;
     P->sum_dzf = sum;
+    P->dz0 = dz[0];
     P->uniform_h = dx == dy;
     for (int k = 0; k < nz; ++k) P->uniform_h = P->uniform_h && dz[k] == dx;
     if (!make_len(P->M, &P->lx) || !make_len(ny, &P->ly) || (bc == FLUPS_BC_PERIODIC && !make_len(nz, &P->lz))) {

@@ -51,6 +51,7 @@ struct DevScalars {
     int    err;         // nonzero: a bounded device-side wait timed out (the result is invalid)
     int    done;        // graph-capturable solve: the defect reached rtol, later iterations skip
     unsigned int fin_count;   // blocks of the running final reduction that have finished
+    unsigned int mom_hmax;    // momentum predictor: high word of max(|u|, |v|, |w|)
 };
 
 // Geometry and tables handed to kernels by value.
@@ -82,7 +83,7 @@ struct Geo {
 enum FlupsKernelId {
     FK_RHO_MINMAX = 0, FK_FACE_COEFFS, FK_RHS, FK_CORRECT, FK_XFWD_F32, FK_XFWD_RES32, FK_YCOL32, FK_ZPER32,
     FK_ZTRI32, FK_XINV32, FK_FINALIZE, FK_XFWD64, FK_YCOL64, FK_ZPER64, FK_ZTRI64, FK_XINV64, FK_RES64,
-    FK_TILE_FLAGS, FK_COUNT
+    FK_TILE_FLAGS, FK_MOM_UMAX, FK_MOMENTUM, FK_COUNT
 };
 
 struct flups_plan_s {
@@ -108,6 +109,7 @@ struct flups_plan_s {
     void* lamx; void* lamy; void* lamz;             // eigenvalues / norm, compute type
     void* tri;                   // walls: a_k/norm, b_k/norm, c_k/norm, compute type (3*nz)
     double sum_dzf;
+    double dz0;                  // dzf[0] (the spacing of a periodic z)
     int uniform_h;               // dx == dy == every dzf: the exact fixed-point defect applies
     int density_set;
     // host-buffer (end-to-end) path, allocated on first use

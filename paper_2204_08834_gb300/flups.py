@@ -31,11 +31,13 @@ SYMBOLS = [
     "flups_pnet_create", "flups_pnet_destroy", "flups_pnet_set_params", "flups_pnet_get_params",
     "flups_pnet_get_grads", "flups_pnet_predict", "flups_pnet_train_step", "flups_pnet_eval_loss",
     "flups_pnet_launch_count", "flups_pnet_set_profiling", "flups_pnet_profile_read", "flups_pnet_kernel_name",
-    "flups_selftest_wait_timeout",
+    "flups_selftest_wait_timeout", "flups_momentum_predict",
 ]
 PNET_NKERNELS = 6
 PNET_NPARAMS = 15601
-NKERNELS = 18
+NKERNELS = 20
+MOM_PAIR = 0
+MOM_FP64 = 1
 
 
 class FlupsError(RuntimeError):
@@ -92,6 +94,7 @@ def lib():
         L.flups_batch_graph_kernels.restype = ctypes.c_ulonglong
         L.flups_batch_member_tuning.argtypes = [P, I, IP, IP]
         L.flups_varcoef_solve.argtypes = [P, V, V, V, D, I, ctypes.POINTER(Info)]
+        L.flups_momentum_predict.argtypes = [P, V, V, V, V, V, V, V, D, D, D, D, D, D, I]
         FP = ctypes.POINTER(ctypes.c_float)
         L.flups_pnet_create.argtypes = [ctypes.POINTER(P), I, I, I, FP, V]
         L.flups_pnet_destroy.argtypes = [P]
@@ -143,6 +146,21 @@ def ptr(x):
             raise ValueError("expected a contiguous float64 CUDA tensor")
         return x.data_ptr()
     raise TypeError(f"cannot pass {type(x)} as a device pointer")
+
+
+def ptr32(x):
+    """Device address of a contiguous float32 CUDA tensor (or an int address)."""
+    if isinstance(x, int):
+        return x
+    if not (hasattr(x, "data_ptr") and x.is_cuda and x.dtype.__repr__() == "torch.float32" and x.is_contiguous()):
+        raise ValueError("expected a contiguous float32 CUDA tensor")
+    return x.data_ptr()
+
+
+def momentum_state(nz, ny, nx, device="cuda"):
+    """Zeroed M state for Plan.momentum_predict: [3][nz][ny][nx] pairs (hi, lo) of float32."""
+    import torch
+    return torch.zeros((3, nz, ny, nx, 2), dtype=torch.float32, device=device)
 
 
 def hptr(a):
@@ -256,6 +274,14 @@ class Plan:
         if check:
             _check(st, "flups_varcoef_solve")
         return inf if check else (st, inf)
+
+    def momentum_predict(self, u, v, w, us, vs, ws, m_state, nu, g, dt, dt_prev, arith=MOM_PAIR):
+        """u** = u^n + dt (f1 M^n - f2 M^{n-1} + g) (Sec. 3.3, Eq. uss_predic); m_state (see
+        momentum_state) holds M^{n-1} on entry (read when dt_prev > 0) and M^n on return."""
+        st = lib().flups_momentum_predict(self._h, ptr(u), ptr(v), ptr(w), ptr(us), ptr(vs), ptr(ws), ptr32(m_state),
+                                          float(nu), float(g[0]), float(g[1]), float(g[2]), float(dt),
+                                          float(dt_prev), int(arith))
+        _check(st, "flups_momentum_predict")
 
     def project_host(self, u, v, w, rho, pn, pnm1, c1, c2, dt, p_out, rtol=1e-10, max_iter=16):
         """Whole projection on HOST numpy arrays (u, v, w updated in place; p_out written)."""

@@ -10,6 +10,9 @@ and the z grid, with the shapes and structure of the paper's workloads:
   * two_layer   - a heavy layer under a light one between walls with a perturbed flat
                   interface and tanh-stretched z, the shape of the two-layer
                   Rayleigh-Benard run (Sec. 7.2: 1024x1024x512, aspect ratio 2, walls in z).
+  * solenoidal_velocity - a single-phase velocity u^n for the momentum predictor: the MAC
+                  curl of a Gaussian-filtered random vector potential (discretely
+                  divergence-free), rescaled to a given rms; taylor_green - the 2-D vortex.
   * droplet_density + velocity_series - windows of a time series for the learned p_hat:
                   a fixed droplet field (density ratio 20) and a velocity predictor that
                   evolves as an AR(1) sequence u^{m+1} = a u^m + sqrt(1 - a^2) xi with smooth
@@ -28,7 +31,7 @@ numpy PCG64 generator keyed by a fixed seed per field.
 import numpy as np
 
 __all__ = ["Case", "stretched_dzf", "sphere", "emulsion", "two_layer", "ensemble_member", "random_fields",
-           "droplet_density", "smooth_noise", "velocity_series"]
+           "droplet_density", "smooth_noise", "velocity_series", "solenoidal_velocity", "taylor_green"]
 
 
 class Case(dict):
@@ -294,3 +297,36 @@ def learned_window(kind, w, n=None):
     n = n or 128
     rho = droplet_density(n, 50, 4.0, 12.0, 20.0, [32, w])
     return rho, [33, w], n, 1e-3
+
+
+def solenoidal_velocity(n, seed=50, sigma_cells=4.0, urms=1.0, nz=None, ny=None):
+    """(u, v, w) on an n^3 (or nz x ny x n) periodic MAC grid: the discrete curl of a vector
+    potential of Gaussian-filtered noise (smooth_noise), so the discrete divergence is zero up to
+    rounding; scaled so that the rms over the three components is `urms`.  Cell width 1/n."""
+    nz, ny = nz or n, ny or n
+    rng = _rng(seed)
+    if nz == ny == n:
+        psi = [smooth_noise(rng, n, sigma_cells) for _ in range(3)]
+    else:
+        psi = [rng.standard_normal((nz, ny, n)) for _ in range(3)]
+
+    def d(a, ax):
+        return a - np.roll(a, 1, axis=ax)
+    u = d(psi[2], 1) - d(psi[1], 0)
+    v = d(psi[0], 0) - d(psi[2], 2)
+    w = d(psi[1], 2) - d(psi[0], 1)
+    del psi
+    s = urms / np.sqrt((np.mean(u * u) + np.mean(v * v) + np.mean(w * w)) / 3.0)
+    return tuple(np.ascontiguousarray(q * s) for q in (u, v, w))
+
+
+def taylor_green(nx, ny, nz, amplitude=1.0):
+    """2-D Taylor-Green vortex u = A sin x cos y, v = -A cos x sin y, w = 0 on the MAC grid of a
+    2 pi-periodic box (uniform in z): each component at its own face positions."""
+    L = 2.0 * np.pi
+    dx, dy = L / nx, L / ny
+    xc = (np.arange(nx) + 0.5) * dx
+    yc = (np.arange(ny) + 0.5) * dy
+    u = amplitude * np.sin(xc + 0.5 * dx)[None, None, :] * np.cos(yc)[None, :, None] * np.ones((nz, 1, 1))
+    v = -amplitude * np.cos(xc)[None, None, :] * np.sin(yc + 0.5 * dy)[None, :, None] * np.ones((nz, 1, 1))
+    return np.ascontiguousarray(u), np.ascontiguousarray(v), np.zeros((nz, ny, nx))
