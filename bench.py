@@ -64,6 +64,10 @@ KERNEL_WORK = {
     # writes u, v, w (p_n, p_{n-1} and the face coefficients only where the density varies)
     "k_rhs": {"bound": "hbm", "bytes": 32},
     "k_correct": {"bound": "hbm", "bytes": 56},
+    # momentum predictor (AB2 call): reads u, v, w (FP64) and the M state (3 x 8 B), writes
+    # u**, v**, w** and the state; the pre-pass reads u, v, w for max|u|
+    "k_momentum": {"bound": "hbm", "bytes": 24 + 24 + 24 + 24},
+    "k_mom_umax": {"bound": "hbm", "bytes": 24},
 }
 
 
@@ -253,6 +257,8 @@ def run_ours(args, rank, world, dev):
         out["ensemble"] = run_ensemble(args)
     if not args.no_learned:
         out["learned"] = run_learned(args)
+    if not args.no_momentum:
+        out["momentum"] = run_momentum(args)
 
     # end to end: the same projection through flups_project_host on pinned host buffers
     if not args.no_e2e:
@@ -463,6 +469,119 @@ def run_learned(args):
     }
 
 
+def run_momentum(args):
+    """The momentum predictor in front of the projection (Sec. 3.3, Eq. uss_predic) on a 512^3
+    single-phase field (MAC curl of filtered noise, rms 1, nu = 1e-3, dt at CFL 0.5): the
+    predictor alone in binary32-pair and binary64 arithmetic, per-kernel times from the
+    library's events, and whole time steps (predictor, rhs, graph-capturable solve, correct)
+    that advance the flow, all timed with CUDA events on the launch stream."""
+    import torch
+
+    from paper_2204_08834_gb300 import flups, synth
+
+    n = 512
+    h = 1.0 / n
+    npts = n ** 3
+    vel = synth.solenoidal_velocity(n, seed=50)
+    U = max(float(np.max(np.abs(q))) for q in vel)
+    nu, g = 1e-3, (0.0, 0.0, -1.0)
+    dt = 0.5 * h / U
+    stream = torch.cuda.current_stream().cuda_stream
+    d = [torch.from_numpy(q).cuda() for q in vel]
+    del vel
+    o = [torch.empty_like(d[0]) for _ in range(3)]
+    st = flups.momentum_state(n, n, n)
+    out = {"workload": f"single-phase {n}^3 triply periodic, solenoidal u^n (MAC curl of Gaussian-filtered "
+                       f"noise, sigma 4 cells, rms 1), nu = {nu}, dt = 0.5 h / max|u|, g = {g}",
+           "points": npts}
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn, k):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(k):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / k
+
+    with flups.Plan(n, n, n, h, h, h, "periodic", "fp32_refine", stream) as plan:
+        plan.momentum_predict(*d, *o, st, nu, g, dt, 0.0)          # first step: M^{n-1} for the AB2 calls
+        for name, arith in (("pair", flups.MOM_PAIR), ("fp64", flups.MOM_FP64)):
+            k = args.steps if arith == flups.MOM_PAIR else max(2, args.steps // 2)
+            ms = timed(lambda: plan.momentum_predict(*d, *o, st, nu, g, dt, dt, arith), k)
+            out[f"predictor_{name}"] = {"ms": round(ms, 4), "mpts_per_s": round(npts / (ms * 1e-3) / 1e6, 1),
+                                        "calls": k}
+        # per-kernel times of the pair path (library events)
+        plan.set_profiling(True)
+        for _ in range(3):
+            plan.momentum_predict(*d, *o, st, nu, g, dt, dt)
+        prof = {kk: (ms / 3.0, cnt / 3.0) for kk, (ms, cnt) in plan.profile().items()}
+        plan.set_profiling(False)
+        pk, pk_kind = peaks()
+        kern = {}
+        for kk, (ms, cnt) in prof.items():
+            e = {"ms": round(ms, 4)}
+            w = KERNEL_WORK.get(kk)
+            if w and w.get("bytes"):
+                gbs = w["bytes"] * npts / (ms / max(cnt, 1e-9) * 1e-3) / 1e9
+                e["algorithmic_GBps"] = round(gbs, 1)
+                e["hbm_frac"] = round(gbs / pk["hbm_gbs"], 4)
+            kern[kk] = e
+        out["kernels"] = kern
+        km = kern.get("k_momentum", {})
+        out["roofline"] = {"kernel": "k_momentum", "bound": "hbm", "achieved": km.get("algorithmic_GBps"),
+                           "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": km.get("hbm_frac"),
+                           "bytes_per_point": KERNEL_WORK["k_momentum"]["bytes"], "peak_source": pk_kind}
+        # full-size accuracy of the pair path against the binary64 path (same input, Euler step)
+        plan.momentum_predict(*d, *o, st, nu, g, dt, 0.0, flups.MOM_FP64)
+        m64 = st.double().sum(dim=-1)
+        plan.momentum_predict(*d, *o, st, nu, g, dt, 0.0, flups.MOM_PAIR)
+        mp = st.double().sum(dim=-1)
+        S = U * U / h + nu * U / h ** 2
+        out["pair_vs_fp64_max_abs_M_over_S"] = float((mp - m64).abs().max()) / S
+        del m64, mp
+        # whole time steps: u^n -> u** -> projection -> u^{n+1}, the next step's u^n
+        zero = torch.zeros_like(d[0])
+        f = torch.empty_like(d[0])
+        p = torch.empty_like(d[0])
+        plan.set_density(torch.ones_like(d[0]))
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        tp = tq = 0.0
+        ksteps = args.steps
+        rel = []
+        l0 = None
+        for s in range(args.warmup + ksteps):
+            if s == args.warmup:
+                torch.cuda.synchronize()
+                l0 = plan.launches
+            ev[0].record()
+            plan.momentum_predict(*d, *o, st, nu, g, dt, dt if s else 0.0)
+            ev[1].record()
+            plan.rhs(*o, zero, zero, 0.0, 0.0, dt, f)
+            plan.solve_graphable(f, p, rtol=args.rtol, max_iter=GRAPH_MAX_ITER)
+            plan.correct(p, zero, zero, 0.0, 0.0, dt, *o)
+            ev[2].record()
+            torch.cuda.synchronize()
+            if s >= args.warmup:
+                tp += ev[0].elapsed_time(ev[1])
+                tq += ev[1].elapsed_time(ev[2])
+                rel.append(plan.solve_result(rtol=args.rtol).rel_res)
+            d, o = o, d
+        launches = plan.launches - l0
+    ms = (tp + tq) / ksteps
+    out["time_step"] = {"ms": round(ms, 4), "mpts_per_s": round(npts / (ms * 1e-3) / 1e6, 1),
+                        "predictor_ms": round(tp / ksteps, 4), "projection_ms": round(tq / ksteps, 4),
+                        "steps": ksteps, "max_rel_res": max(rel), "gpu_launches_per_step": launches / ksteps,
+                        "step": "momentum_predict (pair, AB2) + rhs + solve_graphable (FP32+refine, "
+                                f"rtol {args.rtol:g}) + correct; u^(n+1) feeds the next step"}
+    del d, o, st
+    torch.cuda.empty_cache()
+    return out
+
+
 def cpu_baseline():
     """The FP64 oracle (numpy, as it stands) on a bounded sample: three 256^3 emulsion
     projections (the 256^3 size of the same emulsion configuration)."""
@@ -526,6 +645,7 @@ def main():
     ap.add_argument("--no-ensemble", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--no-cufft", action="store_true")
+    ap.add_argument("--no-momentum", action="store_true")
     ap.add_argument("--learned-windows", type=int, default=100,
                     help="64^3 training windows of 20 samples (default 100: 2000 samples)")
     ap.add_argument("--learned-epochs", type=int, default=3)
@@ -657,6 +777,8 @@ def main():
         line["ensemble"] = out["ensemble"]
     if "learned" in out:
         line["learned"] = out["learned"]
+    if "momentum" in out:
+        line["momentum"] = out["momentum"]
     if world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line))

@@ -9,9 +9,10 @@
 // as Sec. 3.3 states.  Constant density and viscosity, so the surface-tension term vanishes
 // and the body force is the constant acceleration g.
 //
-// Tiling: a CTA covers RX x 8 columns (RX = min(32, nx)) and marches MOM_KC planes up z
-// with a three-plane ring of u, v, w (tile plus a one-cell halo) in shared memory; the
-// global loads of plane k+3 are in flight while plane k is computed.
+// Tiling: a CTA covers RX x 8 columns (RX = min(32, nx)) and marches MOM_KC planes up z.
+// u, v, w planes (tile plus a one-cell halo) and the own cells' M^{n-1} arrive by cp.async
+// in a four-plane shared-memory ring two planes ahead of the computation (no register
+// staging), are converted into a three-plane work ring, and each thread computes its column.
 //
 // Arithmetic.  GB300 issues binary64 at about 1/64 of the binary32 rate, and a binary64
 // stencil of this size (~66 FP64 operations per cell) would run several times longer than
@@ -42,7 +43,7 @@
 namespace {
 
 constexpr int MOM_TY = 8;
-constexpr int MOM_KC = 16;
+constexpr int MOM_KC = 32;
 constexpr int MOM_EMIN = -40;
 
 struct Pf { float h, l; };
@@ -154,12 +155,34 @@ __device__ __forceinline__ Pf ab2_pair(Pf m, float2 mp, int ab2, Pf F1, Pf MF2, 
 
 // ------------------------------------------------------------------------------- the march
 
+__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
+    const unsigned int d = (unsigned int)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+template <int RX> struct MomTile {
+    static constexpr int TY = MOM_TY, RS = RX + 2, FS = (TY + 2) * RS, NT = RX * TY, NH = 2 * RS + 2 * TY;
+    // raw ring: 4 planes of u, v, w (tile + halo, binary64) filled by cp.async two planes ahead;
+    // work ring: 3 planes in the arithmetic's form; M ring: 3 planes of the own cells' M^{n-1}
+    static constexpr int RAW = 4 * 3 * FS * 8, WORK = 3 * 3 * FS * 8, MST = 3 * 3 * NT * 8;
+    static constexpr int BYTES = RAW + WORK + MST;
+};
+
+// Shared-memory pipeline per CTA (planes p = k0-1 .. k0+kc): raw slot (p - k0 + 1) % 4, work
+// slot (p - k0 + 1) % 3, M slot (p - k0) % 3.  Iteration kk (plane k = k0 + kk): wait until
+// the copies of plane k+1 (and M of plane k) have landed, convert plane k+1 into the work ring,
+// issue the copies of plane k+3 (and M of plane k+2), compute plane k.
 template <int RX, bool PAIR>
 __device__ __forceinline__ void mom_march(const MomArgs& a, unsigned char* smem, int E) {
     using Tv = typename std::conditional<PAIR, float2, double>::type;
-    constexpr int TY = MOM_TY, RS = RX + 2, FS = (TY + 2) * RS, NH = 2 * RS + 2 * TY;
-    static_assert(NH <= RX * TY, "one halo cell per thread");
-    Tv* T = reinterpret_cast<Tv*>(smem);          // [3 slots][3 fields][FS]
+    using G = MomTile<RX>;
+    constexpr int TY = G::TY, RS = G::RS, FS = G::FS, NT = G::NT, NH = G::NH;
+    static_assert(NH <= NT, "one halo cell per thread");
+    double* R = reinterpret_cast<double*>(smem);                       // [4][3][FS]
+    Tv* T = reinterpret_cast<Tv*>(smem + G::RAW);                      // [3][3][FS]
+    float2* Ms = reinterpret_cast<float2*>(smem + G::RAW + G::WORK);   // [3][3][NT]
     const int tid = threadIdx.x, tx = tid % RX, ty = tid / RX;
     const int i0 = blockIdx.x * RX, j0 = blockIdx.y * TY, k0 = blockIdx.z * a.kc;
     const int c = (ty + 1) * RS + tx + 1;
@@ -175,50 +198,70 @@ __device__ __forceinline__ void mom_march(const MomArgs& a, unsigned char* smem,
     }
     const int og = (j0 + ty) * a.nx + i0 + tx;
     const long long plane = (long long)a.nx * a.ny;
-    const double* __restrict__ F0 = a.u;
-    const double* __restrict__ F1p = a.v;
-    const double* __restrict__ F2p = a.w;
     float Kq = 0.f, KQ = 0.f;
     if constexpr (PAIR) {
         Kq = __uint_as_float(((unsigned int)(E + 3 + 127) << 23) | 0x400000u);       // 1.5 * 2^23 q
         KQ = __uint_as_float(((unsigned int)(2 * E + 4 + 127) << 23) | 0x400000u);   // 1.5 * 2^23 Q
     }
-    double po[3], ph[3] = {0.0, 0.0, 0.0};
-    auto fetch = [&](int k) {
-        const long long base = (long long)(k & (a.nz - 1)) * plane;
-        po[0] = __ldg(F0 + base + og); po[1] = __ldg(F1p + base + og); po[2] = __ldg(F2p + base + og);
-        if (tid < NH) { ph[0] = __ldg(F0 + base + hg); ph[1] = __ldg(F1p + base + hg); ph[2] = __ldg(F2p + base + hg); }
+    auto issue_raw = [&](int p) {                  // plane p (unwrapped) into its raw slot
+        const long long base = (long long)(p & (a.nz - 1)) * plane;
+        double* dst = R + ((p - k0 + 1) & 3) * 3 * FS;
+        cp_async8(dst + c, a.u + base + og);
+        cp_async8(dst + FS + c, a.v + base + og);
+        cp_async8(dst + 2 * FS + c, a.w + base + og);
+        if (tid < NH) {
+            cp_async8(dst + hl, a.u + base + hg);
+            cp_async8(dst + FS + hl, a.v + base + hg);
+            cp_async8(dst + 2 * FS + hl, a.w + base + hg);
+        }
+    };
+    auto issue_m = [&](int p) {                    // M^{n-1} of the own cells of plane p
+        if (!a.ab2) return;
+        float2* dst = Ms + ((p - k0) % 3) * 3 * NT + tid;
+        const long long o = (long long)p * plane + og;
+#pragma unroll
+        for (int f = 0; f < 3; ++f) cp_async8(dst + f * NT, a.ms + f * a.n + o);
     };
     auto cvt = [&](double x) -> Tv {
         if constexpr (PAIR) return quant(split_d(x), Kq);
         else return x;
     };
-    auto put = [&](int slot) {
+    auto convert = [&](int p) {                    // raw plane p -> work ring
+        const double* src = R + ((p - k0 + 1) & 3) * 3 * FS;
+        Tv* dst = T + ((p - k0 + 1) % 3) * 3 * FS;
 #pragma unroll
-        for (int f = 0; f < 3; ++f) T[(slot * 3 + f) * FS + c] = cvt(po[f]);
+        for (int f = 0; f < 3; ++f) dst[f * FS + c] = cvt(src[f * FS + c]);
         if (tid < NH) {
 #pragma unroll
-            for (int f = 0; f < 3; ++f) T[(slot * 3 + f) * FS + hl] = cvt(ph[f]);
+            for (int f = 0; f < 3; ++f) dst[f * FS + hl] = cvt(src[f * FS + hl]);
         }
     };
-    double own[3], own1[3];
-    fetch(k0 - 1); put(0);
-    fetch(k0);     put(1);
-#pragma unroll
-    for (int f = 0; f < 3; ++f) own[f] = po[f];
-    fetch(k0 + 1); put(2);
-#pragma unroll
-    for (int f = 0; f < 3; ++f) own1[f] = po[f];
-    if (a.kc > 1) fetch(k0 + 2);
+    // products on the k-1/2 faces, carried from the previous plane's k+1/2 ones
+    Pf c_uw = {0.f, 0.f}, c_vw = {0.f, 0.f}, c_ww = {0.f, 0.f};
+    double d_uw = 0.0, d_vw = 0.0, d_ww = 0.0;
+    issue_raw(k0 - 1); cp_commit();
+    issue_raw(k0); cp_commit();
+    issue_raw(k0 + 1); issue_m(k0); cp_commit();
+    issue_raw(k0 + 2); issue_m(k0 + 1); cp_commit();
+    cp_wait<2>();
     __syncthreads();
+    convert(k0 - 1);
+    convert(k0);
 
     for (int kk = 0; kk < a.kc; ++kk) {
         const int k = k0 + kk;
-        const int sm = kk % 3, s0 = (kk + 1) % 3, sp = (kk + 2) % 3;
+        cp_wait<1>();                              // raw plane k+1 and M of plane k have landed
+        __syncthreads();                           // ... for every thread; plane k-2's work slot is free
+        convert(k + 1);
+        if (kk + 3 <= a.kc) { issue_raw(k + 3); issue_m(k + 2); }
+        cp_commit();
+        __syncthreads();
         const long long o = (long long)k * plane + og;
-        const Tv* Xm = T + sm * 3 * FS + c;
-        const Tv* X0 = T + s0 * 3 * FS + c;
-        const Tv* Xp = T + sp * 3 * FS + c;
+        const Tv* Xm = T + (kk % 3) * 3 * FS + c;
+        const Tv* X0 = T + ((kk + 1) % 3) * 3 * FS + c;
+        const Tv* Xp = T + ((kk + 2) % 3) * 3 * FS + c;
+        const double* own = R + ((kk + 1) & 3) * 3 * FS + c;
+        const float2* mprev = Ms + (kk % 3) * 3 * NT + tid;
         // u: field 0, v: field 1, w: field 2
         const Tv U0 = X0[0], Uxm = X0[-1], Uxp = X0[1], Uym = X0[-RS], Uyp = X0[RS], Uzm = Xm[0], Uzp = Xp[0];
         const Tv Uxm_yp = X0[RS - 1], Uxm_zp = Xp[-1];
@@ -230,7 +273,7 @@ __device__ __forceinline__ void mom_march(const MomArgs& a, unsigned char* smem,
         float2 mp[3] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
         if (a.ab2) {
 #pragma unroll
-            for (int f = 0; f < 3; ++f) mp[f] = a.ms[f * a.n + o];
+            for (int f = 0; f < 3; ++f) mp[f] = mprev[f * NT];
         }
         double res[3];
         float2 mout[3];
@@ -238,16 +281,22 @@ __device__ __forceinline__ void mom_march(const MomArgs& a, unsigned char* smem,
             // fluxes (products of two-point sums; the 1/4 of the averages is in sc)
             const Pf uu_i = sq2(Uxm, U0, KQ), uu_ip = sq2(U0, Uxp, KQ);
             const Pf vv_j = sq2(Vym, V0, KQ), vv_jp = sq2(V0, Vyp, KQ);
-            const Pf ww_k = sq2(Wzm, W0, KQ), ww_kp = sq2(W0, Wzp, KQ);
+            if (kk == 0) {
+                c_ww = sq2(Wzm, W0, KQ);
+                c_uw = prod2(Uzm, U0, Wzm, Wxp_zm, KQ);            // (i+1/2, k-1/2)
+                c_vw = prod2(Vzm, V0, Wzm, Wyp_zm, KQ);            // (j+1/2, k-1/2)
+            }
+            const Pf ww_k = c_ww, ww_kp = sq2(W0, Wzp, KQ);
             const Pf uv_pp = prod2(U0, Uyp, V0, Vxp, KQ);          // edge (i+1/2, j+1/2)
             const Pf uv_pm = prod2(Uym, U0, Vym, Vxp_ym, KQ);      // (i+1/2, j-1/2)
             const Pf uv_mp = prod2(Uxm, Uxm_yp, Vxm, V0, KQ);      // (i-1/2, j+1/2)
             const Pf uw_pp = prod2(U0, Uzp, W0, Wxp, KQ);          // (i+1/2, k+1/2)
-            const Pf uw_pm = prod2(Uzm, U0, Wzm, Wxp_zm, KQ);      // (i+1/2, k-1/2)
+            const Pf uw_pm = c_uw;
             const Pf uw_mp = prod2(Uxm, Uxm_zp, Wxm, W0, KQ);      // (i-1/2, k+1/2)
             const Pf vw_pp = prod2(V0, Vzp, W0, Wyp, KQ);          // (j+1/2, k+1/2)
-            const Pf vw_pm = prod2(Vzm, V0, Wzm, Wyp_zm, KQ);      // (j+1/2, k-1/2)
+            const Pf vw_pm = c_vw;
             const Pf vw_mp = prod2(Vym, Vym_zp, Wym, W0, KQ);      // (j-1/2, k+1/2)
+            c_ww = ww_kp; c_uw = uw_pp; c_vw = vw_pp;
             auto div3 = [](Pf a1, Pf b1, Pf a2, Pf b2, Pf a3, Pf b3) -> Pf {
                 const float H = __fadd_rn(__fadd_rn(__fsub_rn(a1.h, b1.h), __fsub_rn(a2.h, b2.h)), __fsub_rn(a3.h, b3.h));
                 return {H, ((a1.l - b1.l) + (a2.l - b2.l)) + (a3.l - b3.l)};
@@ -263,19 +312,25 @@ __device__ __forceinline__ void mom_march(const MomArgs& a, unsigned char* smem,
 #pragma unroll
             for (int f = 0; f < 3; ++f) {
                 const Pf d = ab2_pair(M[f], mp[f], a.ab2, a.F1, a.MF2, a.G[f], a.DT);
-                res[f] = (own[f] + f2d_int(d.h)) + f2d_int(d.l);
+                res[f] = (own[f * FS] + f2d_int(d.h)) + f2d_int(d.l);
                 mout[f] = make_float2(M[f].h, M[f].l);
             }
         } else {
             const double uu_i = (Uxm + U0) * (Uxm + U0), uu_ip = (U0 + Uxp) * (U0 + Uxp);
             const double vv_j = (Vym + V0) * (Vym + V0), vv_jp = (V0 + Vyp) * (V0 + Vyp);
-            const double ww_k = (Wzm + W0) * (Wzm + W0), ww_kp = (W0 + Wzp) * (W0 + Wzp);
+            if (kk == 0) {
+                d_ww = (Wzm + W0) * (Wzm + W0);
+                d_uw = (Uzm + U0) * (Wzm + Wxp_zm);
+                d_vw = (Vzm + V0) * (Wzm + Wyp_zm);
+            }
+            const double ww_k = d_ww, ww_kp = (W0 + Wzp) * (W0 + Wzp);
             const double uv_pp = (U0 + Uyp) * (V0 + Vxp), uv_pm = (Uym + U0) * (Vym + Vxp_ym);
             const double uv_mp = (Uxm + Uxm_yp) * (Vxm + V0);
-            const double uw_pp = (U0 + Uzp) * (W0 + Wxp), uw_pm = (Uzm + U0) * (Wzm + Wxp_zm);
+            const double uw_pp = (U0 + Uzp) * (W0 + Wxp), uw_pm = d_uw;
             const double uw_mp = (Uxm + Uxm_zp) * (Wxm + W0);
-            const double vw_pp = (V0 + Vzp) * (W0 + Wyp), vw_pm = (Vzm + V0) * (Wzm + Wyp_zm);
+            const double vw_pp = (V0 + Vzp) * (W0 + Wyp), vw_pm = d_vw;
             const double vw_mp = (Vym + Vym_zp) * (Wym + W0);
+            d_ww = ww_kp; d_uw = uw_pp; d_vw = vw_pp;
             const double M[3] = {
                 (uu_ip - uu_i) * a.idx4 + (uv_pp - uv_pm) * a.idy4 + (uw_pp - uw_pm) * a.idz4 +
                     (Uxm + Uxp - 2.0 * U0) * a.nsx + (Uym + Uyp - 2.0 * U0) * a.nsy + (Uzm + Uzp - 2.0 * U0) * a.nsz,
@@ -287,7 +342,7 @@ __device__ __forceinline__ void mom_march(const MomArgs& a, unsigned char* smem,
             for (int f = 0; f < 3; ++f) {
                 double acc = a.f1 * M[f];
                 if (a.ab2) acc += a.mf2 * ((double)mp[f].x + (double)mp[f].y);
-                res[f] = own[f] + a.dt * (acc + a.g[f]);
+                res[f] = own[f * FS] + a.dt * (acc + a.g[f]);
                 const float h = __double2float_rn(M[f]);
                 mout[f] = make_float2(h, __double2float_rn(M[f] - (double)h));
             }
@@ -295,20 +350,13 @@ __device__ __forceinline__ void mom_march(const MomArgs& a, unsigned char* smem,
         a.us[o] = res[0]; a.vs[o] = res[1]; a.ws[o] = res[2];
 #pragma unroll
         for (int f = 0; f < 3; ++f) a.ms[f * a.n + o] = mout[f];
-        if (kk + 1 < a.kc) {
-            __syncthreads();                  // every thread is done with the slot of plane k-1
-            put(sm);                          // plane k+2
-#pragma unroll
-            for (int f = 0; f < 3; ++f) { own[f] = own1[f]; own1[f] = po[f]; }
-            if (kk + 2 < a.kc) fetch(k + 3);
-            __syncthreads();
-        }
     }
+    cp_wait<0>();
 }
 
 template <int RX, bool PAIR>
-__global__ void __launch_bounds__(RX * MOM_TY) k_momentum(MomArgs a) {
-    __shared__ __align__(16) unsigned char smem[9 * (MOM_TY + 2) * (RX + 2) * 8];
+__global__ void __launch_bounds__(RX * MOM_TY, RX == 32 ? 3 : 4) k_momentum(MomArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
     if constexpr (PAIR) {
         const unsigned int hm = *a.hmax;
         const int E = hm == 0u ? 0 : (int)(hm >> 20) - 1022;
@@ -358,8 +406,13 @@ bool overlaps(const void* a, const void* b, size_t bytes_a, size_t bytes_b) {
 template <int RX>
 cudaError_t launch_mom(flups_plan P, const MomArgs& a, bool pair) {
     const dim3 grid(P->nx / RX, P->ny / MOM_TY, P->nz / a.kc);
-    if (pair) k_momentum<RX, true><<<grid, RX * MOM_TY, 0, P->stream>>>(a);
-    else k_momentum<RX, false><<<grid, RX * MOM_TY, 0, P->stream>>>(a);
+    constexpr int bytes = MomTile<RX>::BYTES;
+    cudaError_t e = cudaFuncSetAttribute(k_momentum<RX, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_momentum<RX, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e != cudaSuccess) return e;
+    if (pair) k_momentum<RX, true><<<grid, RX * MOM_TY, bytes, P->stream>>>(a);
+    else k_momentum<RX, false><<<grid, RX * MOM_TY, bytes, P->stream>>>(a);
     return cudaGetLastError();
 }
 
