@@ -212,7 +212,7 @@ Geo plan_geo(flups_plan P) {
     Geo g;
     g.nx = P->nx; g.ny = P->ny; g.nz = P->nz; g.M = P->M; g.nxh = P->nxh; g.ldS = P->ldS;
     g.walls = P->bc == FLUPS_BC_WALLS;
-    g.uniform_z = 0;
+    g.iso = P->uniform_h;
     g.dx = P->dx; g.dy = P->dy;
     g.sx = 1.0 / (P->dx * P->dx); g.sy = 1.0 / (P->dy * P->dy);
     g.idx = 1.0 / P->dx; g.idy = 1.0 / P->dy;

@@ -63,7 +63,7 @@ struct DevScalars {
 #define FLUPS_KC 16
 
 struct Geo {
-    int nx, ny, nz, M, nxh, ldS, walls, uniform_z;
+    int nx, ny, nz, M, nxh, ldS, walls, iso;   // iso: dx == dy == every dzf
     double dx, dy;
     double idx, idy;             // 1/dx, 1/dy
     double sx, sy;               // 1/dx^2, 1/dy^2
