@@ -52,6 +52,10 @@ typedef enum {
 
 typedef enum { FLUPS_BC_PERIODIC = 0, FLUPS_BC_WALLS = 1 } flups_bc;
 
+/* Ends of the x and y directions (flups_plan_create_bc): periodic, or homogeneous Neumann
+ * (dp/dn = 0) or homogeneous Dirichlet (p = 0) on both boundary faces of the direction. */
+typedef enum { FLUPS_XY_PERIODIC = 0, FLUPS_XY_NEUMANN = 1, FLUPS_XY_DIRICHLET = 2 } flups_xy_bc;
+
 typedef enum {
     FLUPS_FP64 = 0,          /* FFTs and z solve in FP64, one direct pass                  */
     FLUPS_FP32_REFINE = 1    /* FFTs and z solve in FP32; FP64 residual f - L p, FP64
@@ -84,6 +88,24 @@ typedef struct {
  */
 flups_status flups_plan_create(flups_plan* out, int nx, int ny, int nz, double dx, double dy,
                                const double* dzf, int bc, int prec, void* stream);
+/*
+ * flups_plan_create_bc - as flups_plan_create, with Neumann or Dirichlet ends in x and/or y
+ * (Sec. 3.3.1: the eigen-expansion along x and y holds for any homogeneous boundary
+ * conditions; cosine and sine series by FFTs with pre/post-processing).
+ *   bcx, bcy : flups_xy_bc.  Neumann at both ends: cosine series (DCT-II/III), modes
+ *              cos(pi k (2i+1)/(2n)), eigenvalues -4 sin^2(pi k/(2n))/h^2; Dirichlet at both
+ *              ends (p = 0 on the boundary face): sine series (DST-II/III), modes
+ *              sin(pi (k+1)(2i+1)/(2n)), eigenvalues -4 sin^2(pi (k+1)/(2n))/h^2.
+ *   bc       : the z treatment, as in flups_plan_create.
+ * A plan with any non-periodic x/y end takes prec = FLUPS_FP64 only (FLUPS_EUNSUPPORTED
+ * otherwise) and only flups_solve: set_density, rhs, correct and the host-buffer projection
+ * return FLUPS_EUNSUPPORTED.  Its solve is L p = f when an end is Dirichlet (L is then
+ * nonsingular and the mean of f is kept), and L p = f - <f>_V with <p>_V = 0 otherwise; it
+ * does not evaluate its residual (info->rel_res stays -1).  Mixed ends (Neumann at one face,
+ * Dirichlet at the other) are not provided.
+ */
+flups_status flups_plan_create_bc(flups_plan* out, int nx, int ny, int nz, double dx, double dy,
+                                  const double* dzf, int bcx, int bcy, int bc, int prec, void* stream);
 flups_status flups_plan_destroy(flups_plan plan);
 flups_status flups_set_stream(flups_plan plan, void* stream);
 size_t       flups_workspace_bytes(flups_plan plan);

@@ -580,6 +580,189 @@ __global__ void __launch_bounds__(512) k_xinv(const typename cplx<T>::t* __restr
     if (MEAN) block_sum_abc<true, false, false>(accw, 0.f, 0.f, part);
 }
 
+// -------------------------------------------- x transforms with Neumann or Dirichlet ends
+// KIND 1 (Neumann at both ends): X_k = sum_j x_j cos(pi k (2j+1)/(2 nx)), k < nx (DCT-II);
+// KIND 2 (Dirichlet at both ends): Y_k = sum_j x_j sin(pi (k+1)(2j+1)/(2 nx)), the DCT-II of
+// (-1)^j x_j read backwards (DST-II).  Makhoul's construction: v_n = x_{2n}, v_{nx-1-n} = x_{2n+1};
+// V = the real FFT of v (half-length complex FFT and split, as in k_xfwd); X_k = Re(q_k V_k) and
+// X_{nx-k} = -Im(q_k V_k) with q_k = exp(-i pi k/(2 nx)), k = 0..M.  The nx real coefficients go
+// to S[row][k] as (X_k, 0).  INV: V_k = conj(q_k) (X_k - i X_{nx-k}) (X_nx = 0), the merge and
+// half-length inverse FFT of k_xinv, and the inverse permutation; unnormalised like k_xinv (a
+// round trip gives M x).  ACC = 1 adds the result to p.
+template <typename T, int E, int KIND, bool INV, int ACC>
+__global__ void __launch_bounds__(512) k_xdct(typename cplx<T>::t* __restrict__ S, const double* __restrict__ fin,
+                                               double* __restrict__ pout, Geo g, FftLen L,
+                                               const typename cplx<T>::t* __restrict__ tw,
+                                               const typename cplx<T>::t* __restrict__ twr,
+                                               const typename cplx<T>::t* __restrict__ twq, int lgB, int nrows) {
+    typedef typename cplx<T>::t C;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    C* s = reinterpret_cast<C*>(smraw);
+    T* sT = reinterpret_cast<T*>(smraw);
+    const int B = 1 << lgB, pitch = B + 1, M = g.M, nx = g.nx;
+    const int row0 = blockIdx.x * B, tid = threadIdx.x, nthr = blockDim.x;
+    const int H = M / 2 + 1;
+    // v_m lives in packed element m/2 of line c, real part for even m
+    auto vat = [&](int m, int c) -> T& { return sT[((m >> 1) * pitch + c) * 2 + (m & 1)]; };
+    if (!INV) {
+        for (int idx = tid; idx < B * M; idx += nthr) {
+            const int c = idx / M, n = idx - c * M;
+            const int row = row0 + c;
+            const double2 xv = row < nrows ? __ldg(reinterpret_cast<const double2*>(fin + (size_t)row * nx) + n)
+                                           : make_double2(0.0, 0.0);
+            vat(n, c) = from_double<T>(xv.x);
+            vat(nx - 1 - n, c) = from_double<T>(KIND == 2 ? -xv.y : xv.y);
+        }
+        __syncthreads();
+        fft_tile<C, E, false>(s, pitch, lgB, L, tw);
+        for (int idx = tid; idx < B * H; idx += nthr) {
+            const int c = idx / H, k = idx - c * H;
+            const int row = row0 + c;
+            if (row >= nrows) continue;
+            const C zk = s[k * pitch + c];
+            const C zm = s[(k == 0 ? 0 : M - k) * pitch + c];
+            const T ax = (zk.x + zm.x) * (T)0.5, ay = (zk.y - zm.y) * (T)0.5;
+            const T bxx = (zk.y + zm.y) * (T)0.5, byy = (zm.x - zk.x) * (T)0.5;
+            const C w = __ldg(&twr[k]);
+            const T tx = w.x * bxx - w.y * byy, ty = w.x * byy + w.y * bxx;
+            C* out = S + (size_t)row * g.ldS;
+            auto emit = [&](int kk, T vx, T vy) {   // X_kk and X_{nx-kk} from V_kk
+                const C q = __ldg(&twq[kk]);
+                const T re = q.x * vx - q.y * vy, im = q.x * vy + q.y * vx;
+                out[KIND == 2 ? nx - 1 - kk : kk] = mk<T>(re, (T)0);
+                if (kk != 0 && kk != M) out[KIND == 2 ? kk - 1 : nx - kk] = mk<T>(-im, (T)0);
+            };
+            emit(k, ax + tx, ay + ty);                         // V_k
+            if (k != M - k) emit(M - k, ax - tx, ty - ay);     // V_{M-k} (k = 0: V_M)
+        }
+        return;
+    }
+    for (int idx = tid; idx < B * H; idx += nthr) {
+        const int c = idx / H, k = idx - c * H;
+        const int row = row0 + c;
+        C xk = mk<T>((T)0, (T)0), xm = xk;
+        if (row < nrows) {
+            const C* in = S + (size_t)row * g.ldS;
+            auto X = [&](int j) -> T { return in[KIND == 2 ? nx - 1 - j : j].x; };
+            auto vk = [&](int kk) -> C {                       // conj(q_kk) (X_kk - i X_{nx-kk})
+                const T a = X(kk), b = kk == 0 ? (T)0 : X(nx - kk);
+                const C q = __ldg(&twq[kk]);
+                return mk<T>(q.x * a - q.y * b, -(q.x * b + q.y * a));
+            };
+            xk = vk(k);
+            xm = vk(M - k);
+        }
+        if (k == 0) { xk.y = (T)0; xm.y = (T)0; }
+        const T ax = (xk.x + xm.x) * (T)0.5, ay = (xk.y - xm.y) * (T)0.5;
+        const T dx = (xk.x - xm.x) * (T)0.5, dy = (xk.y + xm.y) * (T)0.5;
+        const C w = __ldg(&twr[k]);
+        const T bxx = dx * w.x + dy * w.y, byy = dy * w.x - dx * w.y;
+        s[k * pitch + c] = mk<T>(ax - byy, ay + bxx);
+        if (k != 0 && k != M - k) s[(M - k) * pitch + c] = mk<T>(ax + byy, bxx - ay);
+    }
+    __syncthreads();
+    fft_tile<C, E, true>(s, pitch, lgB, L, tw);
+    for (int idx = tid; idx < B * M; idx += nthr) {
+        const int c = idx / M, n = idx - c * M;
+        const int row = row0 + c;
+        if (row >= nrows) continue;
+        const T a = vat(n, c), b = vat(nx - 1 - n, c);
+        double2* dst = reinterpret_cast<double2*>(pout + (size_t)row * nx) + n;
+        double2 o = make_double2(to_double<T>(a), to_double<T>(KIND == 2 ? -b : b));
+        if (ACC) { const double2 old = *dst; o.x += old.x; o.y += old.y; }
+        *dst = o;
+    }
+}
+
+// ------------------------------------------- y transforms with Neumann or Dirichlet ends
+// On complex columns (kx fixed): the cosine (KIND 1) or sine (KIND 2) series of the real and of
+// the imaginary part together, from one complex FFT of length ny of the permuted column
+// (v_m = z_{2m}, v_{ny-1-m} = z_{2m+1}; odd entries negated for KIND 2):
+//   X_k = (Re(q_k (V_k + conj V_{ny-k})) + i Im(q_k (V_k - conj V_{ny-k}))) / 2,  q_k = exp(-i pi k/(2 ny)),
+// stored backwards for KIND 2.  INV: V_k = conj(q_k)[(Re X_k - i Re X_{ny-k}) + i (Im X_k - i Im X_{ny-k})],
+// the unnormalised inverse FFT and the inverse permutation.  A tile is B columns of one plane.
+template <typename T, int E, int KIND, bool INV>
+__global__ void __launch_bounds__(1024) k_ydct(typename cplx<T>::t* __restrict__ S, Geo g, FftLen L,
+                                               const typename cplx<T>::t* __restrict__ tw,
+                                               const typename cplx<T>::t* __restrict__ twq, int lgB, int ncols) {
+    typedef typename cplx<T>::t C;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    C* s = reinterpret_cast<C*>(smraw);
+    const int B = 1 << lgB, pitch = B + 1;
+    const int kxa = blockIdx.x * B;
+    C* base = S + (size_t)blockIdx.y * g.ny * g.ldS + kxa;
+    const int N = g.ny, tid = threadIdx.x, nthr = blockDim.x;
+    const int c = tid & (B - 1), j0 = tid >> lgB, NE = N / E;
+    const bool live = kxa + c < ncols;
+    auto vpos = [&](int j) { return (j & 1) ? N - 1 - (j >> 1) : (j >> 1); };   // z_j -> v_vpos(j)
+    const int HP = N / 2 + 1;
+    {
+        C r[E];
+#pragma unroll
+        for (int t = 0; t < E; ++t) {
+            const int j = j0 + t * NE;
+            const int src = INV && KIND == 2 ? N - 1 - j : j;
+            r[t] = live ? base[(size_t)src * g.ldS + c] : mk<T>((T)0, (T)0);
+        }
+#pragma unroll
+        for (int t = 0; t < E; ++t) {
+            const int j = j0 + t * NE;
+            C z = r[t];
+            if (!INV && KIND == 2 && (j & 1)) { z.x = -z.x; z.y = -z.y; }
+            s[(INV ? j : vpos(j)) * pitch + c] = z;
+        }
+    }
+    __syncthreads();
+    if (!INV) fft_tile<C, E, false>(s, pitch, lgB, L, tw);
+    __syncthreads();
+    for (int idx = tid; idx < B * HP; idx += nthr) {   // the pair (k, N-k) of one column
+        const int cc = idx % B, k = idx / B;
+        const int km = k == 0 ? 0 : N - k;
+        const C a = s[k * pitch + cc], b = s[km * pitch + cc];
+        const C qk = __ldg(&twq[k]);
+        if (!INV) {
+            // X_k from (V_k, V_{N-k}); X_{N-k} from (V_{N-k}, V_k)
+            const T sx = a.x + b.x, sy = a.y - b.y, dx = a.x - b.x, dy = a.y + b.y;
+            const C xk = mk<T>((T)0.5 * (qk.x * sx - qk.y * sy), (T)0.5 * (qk.x * dy + qk.y * dx));
+            if (k != 0 && k != km) {
+                const C qm = __ldg(&twq[km]);
+                const T sx2 = b.x + a.x, sy2 = b.y - a.y, dx2 = b.x - a.x, dy2 = b.y + a.y;
+                s[km * pitch + cc] = mk<T>((T)0.5 * (qm.x * sx2 - qm.y * sy2), (T)0.5 * (qm.x * dy2 + qm.y * dx2));
+            }
+            s[k * pitch + cc] = xk;
+        } else {
+            // V_k = conj(q_k) (Re X_k - i Re X_{N-k}) + i conj(q_k) (Im X_k - i Im X_{N-k}), X_N = 0
+            const C bb = k == 0 ? mk<T>((T)0, (T)0) : b;
+            auto vk = [&](C q, C x1, C x2) -> C {
+                const C A = mk<T>(q.x * x1.x - q.y * x2.x, -(q.x * x2.x + q.y * x1.x));   // conj(q)(x1.x - i x2.x)
+                const C Bq = mk<T>(q.x * x1.y - q.y * x2.y, -(q.x * x2.y + q.y * x1.y));  // conj(q)(x1.y - i x2.y)
+                return mk<T>(A.x - Bq.y, A.y + Bq.x);                                     // A + i B
+            };
+            const C vkk = vk(qk, a, bb);
+            if (k != 0 && k != km) s[km * pitch + cc] = vk(__ldg(&twq[km]), bb, a);
+            s[k * pitch + cc] = vkk;
+        }
+    }
+    __syncthreads();
+    if (INV) {
+        fft_tile<C, E, true>(s, pitch, lgB, L, tw);
+        __syncthreads();
+    }
+    if (live) {
+#pragma unroll
+        for (int t = 0; t < E; ++t) {
+            const int j = j0 + t * NE;
+            if (!INV) {
+                base[(size_t)(KIND == 2 ? N - 1 - j : j) * g.ldS + c] = s[j * pitch + c];
+            } else {
+                C z = s[vpos(j) * pitch + c];
+                if (KIND == 2 && (j & 1)) { z.x = -z.x; z.y = -z.y; }
+                base[(size_t)j * g.ldS + c] = z;
+            }
+        }
+    }
+}
+
 // ------------------------------------------------------- column transform along y
 // TAIL = false: a tile of B consecutive kx columns of plane blockIdx.y.
 // TAIL = true : the Nyquist column kx = M of B consecutive planes (blockIdx.x * B + c), so
@@ -863,16 +1046,32 @@ __global__ void __launch_bounds__(128) k_ztri(typename cplx<T>::t* __restrict__ 
     C* x = S + (size_t)ky * g.ldS + kx;
     T* cp = cps + col;
     const size_t cs = (size_t)ncols;
-    const bool sing = (col == 0);
+    const bool sing = (col == 0) && g.sing00;   // (kx, ky) = (0, 0) has lam_x + lam_y = 0
     const T lam = sing ? (T)0 : __ldg(&lamx[kx]) + __ldg(&lamy[ky]);
     const int k0 = sing ? 1 : 0;
+    // Singular column: remove the dzf-weighted mean of F over z first (= nx ny <f>_V in the
+    // unnormalised spectrum), so that dropping row 0 solves L p = f - <f>_V for any f (R3).
+    C fmean = mk<T>((T)0, (T)0);
+    if (sing) {
+        double sw = 0.0, sx0 = 0.0, sy0 = 0.0;
+        for (int k = 0; k < nz; ++k) {
+            const C F = x[k * zs];
+            const double w = g.dzf[k];
+            sw += w;
+            sx0 += w * (double)F.x;
+            sy0 += w * (double)F.y;
+        }
+        fmean = mk<T>((T)(sx0 / sw), (T)(sy0 / sw));
+    }
     T cprev = (T)0;
     C dprev = mk<T>((T)0, (T)0);
     for (int k = k0; k < nz; ++k) {
         const T a = k > k0 ? __ldg(&ta[k]) : (T)0;
         const T m = (__ldg(&tb[k]) + lam) - a * cprev;
         const T inv = (T)1 / m;
-        const C F = x[k * zs];
+        C F = x[k * zs];
+        F.x -= fmean.x;
+        F.y -= fmean.y;
         cprev = __ldg(&tc[k]) * inv;
         dprev = mk<T>((F.x - a * dprev.x) * inv, (F.y - a * dprev.y) * inv);
         cp[k * cs] = cprev;
@@ -1063,7 +1262,7 @@ void run_cols_pipe(flups_plan P, float2* S, const Geo& g, const FftLen& L, const
 }
 
 template <typename T, int E, bool INV>
-void run_ycol_e(flups_plan P, typename cplx<T>::t* S, const Geo& g) {
+void run_ycol_e(flups_plan P, typename cplx<T>::t* S, const Geo& g, bool tail_col = true) {
     typedef typename cplx<T>::t C;
     const int N = g.ny;
     const int lgB = pick_lgB(N, sizeof(C), E, sizeof(T) == 4 ? 32 : 16, g.M, g.cta);
@@ -1078,35 +1277,37 @@ void run_ycol_e(flups_plan P, typename cplx<T>::t* S, const Geo& g) {
     if (sizeof(T) == 4 && E == 8 && pipe_ok(P, N)) run_cols_pipe<0, INV>(P, (float2*)S, g, L, (const float2*)P->twy);
     else kern<<<dim3((g.M + B - 1) / B, g.nz), B * N / E, sm, P->stream>>>(S, g, L, (const C*)P->twy, lgB, 0);
     // the Nyquist column kx = M of every plane, B planes per tile
-    const int lgT = pick_lgB(N, sizeof(C), E, sizeof(T) == 4 ? 32 : 16, g.nz, g.cta);
-    const int BT = 1 << lgT;
-    tail<<<dim3((g.nz + BT - 1) / BT, 1), BT * N / E, (size_t)N * (BT + 1) * sizeof(C), P->stream>>>(
-        S, g, L, (const C*)P->twy, lgT, g.M);
+    if (tail_col) {
+        const int lgT = pick_lgB(N, sizeof(C), E, sizeof(T) == 4 ? 32 : 16, g.nz, g.cta);
+        const int BT = 1 << lgT;
+        tail<<<dim3((g.nz + BT - 1) / BT, 1), BT * N / E, (size_t)N * (BT + 1) * sizeof(C), P->stream>>>(
+            S, g, L, (const C*)P->twy, lgT, g.M);
+    }
     flups_prof_end(P);
-    FLUPS_COUNT(P, 2);
+    FLUPS_COUNT(P, tail_col ? 2 : 1);
 }
 
 template <typename T, bool INV>
-void run_ycol(flups_plan P, typename cplx<T>::t* S, const Geo& g) {
+void run_ycol(flups_plan P, typename cplx<T>::t* S, const Geo& g, bool tail_col = true) {
     const int e = e_for<T>(g.ny);
-    if (e == 4) run_ycol_e<T, 4, INV>(P, S, g);
-    else if (e == 8) run_ycol_e<T, 8, INV>(P, S, g);
-    else if (e == 12) run_ycol_e<T, 12, INV>(P, S, g);
-    else run_ycol_e<T, Ebig<T>::E, INV>(P, S, g);
+    if (e == 4) run_ycol_e<T, 4, INV>(P, S, g, tail_col);
+    else if (e == 8) run_ycol_e<T, 8, INV>(P, S, g, tail_col);
+    else if (e == 12) run_ycol_e<T, 12, INV>(P, S, g, tail_col);
+    else run_ycol_e<T, Ebig<T>::E, INV>(P, S, g, tail_col);
 }
 
 template <typename T, int E>
-void run_zper_e(flups_plan P, typename cplx<T>::t* S, const Geo& g);
+void run_zper_e(flups_plan P, typename cplx<T>::t* S, const Geo& g, bool tail_col);
 
 template <typename T>
-void run_zsolve(flups_plan P, typename cplx<T>::t* S, const Geo& g) {
+void run_zsolve(flups_plan P, typename cplx<T>::t* S, const Geo& g, bool tail_col = true) {
     typedef typename cplx<T>::t C;
     if (!g.walls) {
         const int e = e_for<T>(g.nz);
-        if (e == 4) run_zper_e<T, 4>(P, S, g);
-        else if (e == 8) run_zper_e<T, 8>(P, S, g);
-        else if (e == 12) run_zper_e<T, 12>(P, S, g);
-        else run_zper_e<T, Ebig<T>::E>(P, S, g);
+        if (e == 4) run_zper_e<T, 4>(P, S, g, tail_col);
+        else if (e == 8) run_zper_e<T, 8>(P, S, g, tail_col);
+        else if (e == 12) run_zper_e<T, 12>(P, S, g, tail_col);
+        else run_zper_e<T, Ebig<T>::E>(P, S, g, tail_col);
     } else {
         const int ncols = g.nxh * g.ny;
         flups_prof_begin(P, sizeof(T) == 4 ? FK_ZTRI32 : FK_ZTRI64);
@@ -1118,7 +1319,7 @@ void run_zsolve(flups_plan P, typename cplx<T>::t* S, const Geo& g) {
 }
 
 template <typename T, int E>
-void run_zper_e(flups_plan P, typename cplx<T>::t* S, const Geo& g) {
+void run_zper_e(flups_plan P, typename cplx<T>::t* S, const Geo& g, bool tail_col) {
     typedef typename cplx<T>::t C;
     if (!g.walls) {
         const int N = g.nz;
@@ -1135,12 +1336,14 @@ void run_zper_e(flups_plan P, typename cplx<T>::t* S, const Geo& g) {
         else
             kern<<<dim3((g.M + B - 1) / B, g.ny), B * N / E, (size_t)N * (B + 1) * sizeof(C), P->stream>>>(
                 S, g, L, (const C*)P->twz, (const T*)P->lamx, (const T*)P->lamy, (const T*)P->lamz, lgB, 0);
-        const int lgT = pick_lgB(N, sizeof(C), E, sizeof(T) == 4 ? 32 : 16, g.ny, g.cta);
-        const int BT = 1 << lgT;
-        tail<<<dim3((g.ny + BT - 1) / BT, 1), BT * N / E, (size_t)N * (BT + 1) * sizeof(C), P->stream>>>(
-            S, g, L, (const C*)P->twz, (const T*)P->lamx, (const T*)P->lamy, (const T*)P->lamz, lgT, g.M);
+        if (tail_col) {
+            const int lgT = pick_lgB(N, sizeof(C), E, sizeof(T) == 4 ? 32 : 16, g.ny, g.cta);
+            const int BT = 1 << lgT;
+            tail<<<dim3((g.ny + BT - 1) / BT, 1), BT * N / E, (size_t)N * (BT + 1) * sizeof(C), P->stream>>>(
+                S, g, L, (const C*)P->twz, (const T*)P->lamx, (const T*)P->lamy, (const T*)P->lamz, lgT, g.M);
+        }
         flups_prof_end(P);
-        FLUPS_COUNT(P, 2);
+        FLUPS_COUNT(P, tail_col ? 2 : 1);
     }
 }
 
@@ -1198,6 +1401,93 @@ void run_xinv(flups_plan P, double* p, const Geo& g) {
     else run_xinv_e<T, Ebig<T>::E, ACC, MEAN, SUBM>(P, p, g);
 }
 
+template <typename T, int E, int KIND, bool INV, int ACC>
+void run_xdct_e(flups_plan P, const double* fin, double* pout, const Geo& g) {
+    typedef typename cplx<T>::t C;
+    const int N = g.M, nrows = g.ny * g.nz;
+    const int lgB = pick_lgB(N, sizeof(C), E, sizeof(T) == 4 ? 32 : 16, nrows, x_cap(g.cta));
+    const int B = 1 << lgB;
+    auto kern = k_xdct<T, E, KIND, INV, ACC>;
+    allow_smem(kern);
+    flups_prof_begin(P, INV ? (sizeof(T) == 4 ? FK_XINV32 : FK_XINV64) : (sizeof(T) == 4 ? FK_XFWD_F32 : FK_XFWD64));
+    kern<<<(nrows + B - 1) / B, B * N / E, (size_t)N * (B + 1) * sizeof(C), P->stream>>>(
+        (C*)P->spec, fin, pout, g, packed(P->lx), (const C*)P->twx, (const C*)P->twxr, (const C*)P->twqx, lgB,
+        nrows);
+    flups_prof_end(P);
+    FLUPS_COUNT(P, 1);
+}
+
+template <typename T, bool INV, int ACC>
+void run_xdct(flups_plan P, const double* fin, double* pout, const Geo& g) {
+    const bool e4 = e_for<T>(g.M) == 4;
+    if (P->bcx == FLUPS_XY_NEUMANN) {
+        if (e4) run_xdct_e<T, 4, 1, INV, ACC>(P, fin, pout, g);
+        else run_xdct_e<T, 8, 1, INV, ACC>(P, fin, pout, g);
+    } else {
+        if (e4) run_xdct_e<T, 4, 2, INV, ACC>(P, fin, pout, g);
+        else run_xdct_e<T, 8, 2, INV, ACC>(P, fin, pout, g);
+    }
+}
+
+template <typename T, int E, int KIND, bool INV>
+void run_ydct_e(flups_plan P, typename cplx<T>::t* S, const Geo& g, int ncols) {
+    typedef typename cplx<T>::t C;
+    const int N = g.ny;
+    const int lgB = pick_lgB(N, sizeof(C), E, sizeof(T) == 4 ? 32 : 16, ncols, g.cta);
+    const int B = 1 << lgB;
+    auto kern = k_ydct<T, E, KIND, INV>;
+    allow_smem(kern);
+    flups_prof_begin(P, sizeof(T) == 4 ? FK_YCOL32 : FK_YCOL64);
+    kern<<<dim3((ncols + B - 1) / B, g.nz), B * N / E, (size_t)N * (B + 1) * sizeof(C), P->stream>>>(
+        S, g, packed(P->ly), (const C*)P->twy, (const C*)P->twqy, lgB, ncols);
+    flups_prof_end(P);
+    FLUPS_COUNT(P, 1);
+}
+
+template <typename T, bool INV>
+void run_ydct(flups_plan P, typename cplx<T>::t* S, const Geo& g, int ncols) {
+    const bool e4 = e_for<T>(g.ny) == 4;
+    if (P->bcy == FLUPS_XY_NEUMANN) {
+        if (e4) run_ydct_e<T, 4, 1, INV>(P, S, g, ncols);
+        else run_ydct_e<T, 8, 1, INV>(P, S, g, ncols);
+    } else {
+        if (e4) run_ydct_e<T, 4, 2, INV>(P, S, g, ncols);
+        else run_ydct_e<T, 8, 2, INV>(P, S, g, ncols);
+    }
+}
+
+// The transforms along x and y of a plan with Neumann or Dirichlet ends in x or y: forward
+// (INV = false) from the real field f into the spectrum, or backward into p (ACC: p += .).
+// Along x the spectrum then holds nx real coefficients per row, so the column passes take nx
+// columns and no Nyquist column.
+template <typename T>
+void r2r_forward(flups_plan P, const double* f, const Geo& g, Geo& gc, int& ncols) {
+    typedef typename cplx<T>::t C;
+    const bool rx = P->bcx != FLUPS_XY_PERIODIC, ry = P->bcy != FLUPS_XY_PERIODIC;
+    gc = g;
+    ncols = P->M + 1;
+    if (rx) {
+        run_xdct<T, false, 0>(P, f, nullptr, g);
+        gc.M = P->nx;
+        gc.nxh = P->nx;
+        ncols = P->nx;
+    } else {
+        run_xfwd<T, 0, false>(P, f, nullptr, g);
+    }
+    if (ry) run_ydct<T, false>(P, (C*)P->spec, gc, ncols);
+    else run_ycol<T, false>(P, (C*)P->spec, gc, !rx);
+}
+
+template <typename T, int ACC>
+void r2r_backward(flups_plan P, double* p, const Geo& g, const Geo& gc, int ncols) {
+    typedef typename cplx<T>::t C;
+    const bool rx = P->bcx != FLUPS_XY_PERIODIC, ry = P->bcy != FLUPS_XY_PERIODIC;
+    if (ry) run_ydct<T, true>(P, (C*)P->spec, gc, ncols);
+    else run_ycol<T, true>(P, (C*)P->spec, gc, !rx);
+    if (rx) run_xdct<T, true, ACC>(P, nullptr, p, g);
+    else run_xinv<T, ACC, false, false>(P, p, g);
+}
+
 // CTAs of the x passes (one partial sum each) for a complex element of csize bytes; with
 // residual != 0, of the FP32 residual pass (which may use the tiled fixed-point layout).
 int xfwd_blocks(flups_plan P, int csize, int residual) {
@@ -1218,6 +1508,16 @@ cudaError_t launch_solve64(flups_plan P, const double* f, double* p) {
     run_zsolve<double>(P, (double2*)P->spec, g);
     run_ycol<double, true>(P, (double2*)P->spec, g);
     run_xinv<double, 0, false, false>(P, p, g);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_solve64_r2r(flups_plan P, const double* f, double* p) {
+    const Geo g = plan_geo(P);
+    Geo gc;
+    int ncols;
+    r2r_forward<double>(P, f, g, gc, ncols);
+    run_zsolve<double>(P, (double2*)P->spec, gc, P->bcx == FLUPS_XY_PERIODIC);
+    r2r_backward<double, 0>(P, p, g, gc, ncols);
     return cudaGetLastError();
 }
 

@@ -54,6 +54,26 @@ double eig(int k, int n, double h) {
     return -4.0 * s * s / (h * h);
 }
 
+// Eigenvalue of mode k along a direction of n cells with the given ends: periodic
+// -4 sin^2(pi k/n)/h^2; Neumann at both ends -4 sin^2(pi k/(2n))/h^2 (cosine modes);
+// Dirichlet at both ends -4 sin^2(pi (k+1)/(2n))/h^2 (sine modes), Sec. 3.3.1.
+double eig_bc(int k, int n, double h, int bc) {
+    if (bc == FLUPS_XY_PERIODIC) return eig(k, n, h);
+    const double s = std::sin(M_PI * (double)(bc == FLUPS_XY_NEUMANN ? k : k + 1) / (2.0 * (double)n));
+    return -4.0 * s * s / (h * h);
+}
+
+// exp(-i pi k/(2n)), k < count (the quarter-wave twiddle of the cosine/sine transforms)
+template <typename T>
+void quarter_twiddles(std::vector<T>& out, int n, int count) {
+    out.resize(2 * (size_t)count);
+    for (int m = 0; m < count; ++m) {
+        const double a = M_PI * (double)m / (2.0 * (double)n);
+        out[2 * m] = (T)std::cos(a);
+        out[2 * m + 1] = (T)(-std::sin(a));
+    }
+}
+
 struct DevAlloc {
     std::vector<void*> ptrs;
     bool ok = true;
@@ -94,10 +114,18 @@ bool build_tables(flups_plan P, const std::vector<double>& dzf, DevAlloc& A) {
     const bool walls = P->bc == FLUPS_BC_WALLS;
     // inverse of the overall normalisation of the unnormalised transforms
     const double scale = (double)P->M * P->ny * (walls ? 1.0 : (double)P->nz);
-    std::vector<T> lx(P->nxh), ly(P->ny);
-    for (int k = 0; k < P->nxh; ++k) lx[k] = (T)(eig(k, P->nx, P->dx) * scale);
-    for (int k = 0; k < P->ny; ++k) ly[k] = (T)(eig(k, P->ny, P->dy) * scale);
+    std::vector<T> lx(P->Wx), ly(P->ny);
+    for (int k = 0; k < P->Wx; ++k) lx[k] = (T)(eig_bc(k, P->nx, P->dx, P->bcx) * scale);
+    for (int k = 0; k < P->ny; ++k) ly[k] = (T)(eig_bc(k, P->ny, P->dy, P->bcy) * scale);
     if (!upload(&P->lamx, lx, A) || !upload(&P->lamy, ly, A)) return false;
+    if (P->bcx != FLUPS_XY_PERIODIC) {
+        quarter_twiddles(tw, P->nx, P->M + 1);
+        if (!upload(&P->twqx, tw, A)) return false;
+    }
+    if (P->bcy != FLUPS_XY_PERIODIC) {
+        quarter_twiddles(tw, P->ny, P->ny);
+        if (!upload(&P->twqy, tw, A)) return false;
+    }
     if (!walls) {
         twiddles(tw, P->nz, P->nz);
         if (!upload(&P->twz, tw, A)) return false;
@@ -115,7 +143,7 @@ bool build_tables(flups_plan P, const std::vector<double>& dzf, DevAlloc& A) {
             tri[2 * nz + k] = (T)(c * scale);
         }
         if (!upload(&P->tri, tri, A)) return false;
-        P->zscr = A.get((size_t)P->nxh * P->ny * nz * sizeof(T));
+        P->zscr = A.get((size_t)P->Wx * P->ny * nz * sizeof(T));
         if (!P->zscr) return false;
     }
     return true;
@@ -213,6 +241,7 @@ Geo plan_geo(flups_plan P) {
     g.nx = P->nx; g.ny = P->ny; g.nz = P->nz; g.M = P->M; g.nxh = P->nxh; g.ldS = P->ldS;
     g.walls = P->bc == FLUPS_BC_WALLS;
     g.iso = P->uniform_h;
+    g.sing00 = P->bcx != FLUPS_XY_DIRICHLET && P->bcy != FLUPS_XY_DIRICHLET;
     g.dx = P->dx; g.dy = P->dy;
     g.sx = 1.0 / (P->dx * P->dx); g.sy = 1.0 / (P->dy * P->dy);
     g.idx = 1.0 / P->dx; g.idy = 1.0 / P->dy;
@@ -255,8 +284,17 @@ const char* flups_status_string(int s) {
 
 flups_status flups_plan_create(flups_plan* out, int nx, int ny, int nz, double dx, double dy,
                                const double* dzf, int bc, int prec, void* stream) {
+    return flups_plan_create_bc(out, nx, ny, nz, dx, dy, dzf, FLUPS_XY_PERIODIC, FLUPS_XY_PERIODIC, bc, prec, stream);
+}
+
+flups_status flups_plan_create_bc(flups_plan* out, int nx, int ny, int nz, double dx, double dy,
+                                  const double* dzf, int bcx, int bcy, int bc, int prec, void* stream) {
     if (!out) return FLUPS_EINVAL;
     *out = nullptr;
+    if (bcx < FLUPS_XY_PERIODIC || bcx > FLUPS_XY_DIRICHLET || bcy < FLUPS_XY_PERIODIC || bcy > FLUPS_XY_DIRICHLET)
+        return FLUPS_EINVAL;
+    const bool ends = bcx != FLUPS_XY_PERIODIC || bcy != FLUPS_XY_PERIODIC;
+    if (ends && prec != FLUPS_FP64) return FLUPS_EUNSUPPORTED;
     if (!dzf || !(dx > 0.0) || !(dy > 0.0) || !std::isfinite(dx) || !std::isfinite(dy)) return FLUPS_EINVAL;
     if (bc != FLUPS_BC_PERIODIC && bc != FLUPS_BC_WALLS) return FLUPS_EINVAL;
     if (prec != FLUPS_FP64 && prec != FLUPS_FP32_REFINE) return FLUPS_EINVAL;
@@ -286,9 +324,12 @@ flups_status flups_plan_create(flups_plan* out, int nx, int ny, int nz, double d
     cudaGetDevice(&P->dev);
     P->M = nx / 2;
     P->nxh = nx / 2 + 1;
+    P->bcx = bcx;
+    P->bcy = bcy;
+    P->Wx = bcx == FLUPS_XY_PERIODIC ? P->nxh : nx;
     const int csize = prec == FLUPS_FP64 ? 16 : 8;
     const int align = 128 / csize;
-    P->ldS = (P->nxh + align - 1) / align * align;
+    P->ldS = (P->Wx + align - 1) / align * align;
     P->npts = (size_t)nx * ny * nz;
     P->nspec = (size_t)P->ldS * ny * nz;
     P->sum_dzf = sum;
@@ -365,13 +406,13 @@ flups_status flups_plan_create(flups_plan* out, int nx, int ny, int nz, double d
     }
     for (size_t q = 0; q < A.ptrs.size(); ++q) P->allocs[q] = A.ptrs[q];
     P->total_bytes = P->nspec * csize + 3 * P->npts * sizeof(double) +
-                     (bc == FLUPS_BC_WALLS ? (size_t)P->nxh * ny * nz * (csize / 2) : 0);
+                     (bc == FLUPS_BC_WALLS ? (size_t)P->Wx * ny * nz * (csize / 2) : 0);
     P->density_set = 0;
     P->launches = 0;
     P->tma_ok = 0;
     P->skip_ptr = nullptr;
     P->cta_cap = flups_default_cta();
-    if (prec == FLUPS_FP32_REFINE) {
+    if (prec == FLUPS_FP32_REFINE && !ends) {
         const int By = 1 << flups_pipe_lgB(ny, P->M), Bz = 1 << flups_pipe_lgB(nz, P->M);
         P->tma_ok = make_spec_map(&P->tm_y, P->spec, P->ldS, ny, nz, By, ny < 256 ? ny : 256, 1) &&
                     (bc == FLUPS_BC_WALLS || make_spec_map(&P->tm_z, P->spec, P->ldS, ny, nz, Bz, 1, nz < 256 ? nz : 256));
@@ -454,8 +495,12 @@ flups_status flups_profile_read(flups_plan P, double* ms, long long* n) {
     return FLUPS_OK;
 }
 
+// Plans with Neumann or Dirichlet ends in x or y take only the Poisson solve.
+bool has_ends(flups_plan P) { return P->bcx != FLUPS_XY_PERIODIC || P->bcy != FLUPS_XY_PERIODIC; }
+
 flups_status flups_set_density(flups_plan P, const double* rho, double rho0) {
     if (!P || !rho || !aligned16(rho) || std::isnan(rho0)) return FLUPS_EINVAL;
+    if (has_ends(P)) return FLUPS_EUNSUPPORTED;
     DeviceGuard dg(P->dev);
     const flups_status st = cuda_status(launch_set_density(P, rho, rho0));
     if (st == FLUPS_OK) P->density_set = 1;
@@ -475,6 +520,7 @@ flups_status flups_get_rho0(flups_plan P, double* rho0_host) {
 flups_status flups_rhs(flups_plan P, const double* u, const double* v, const double* w, const double* p_n,
                        const double* p_nm1, double c1, double c2, double dt, double* f) {
     if (!P || !u || !v || !w || !p_n || !f) return FLUPS_EINVAL;
+    if (has_ends(P)) return FLUPS_EUNSUPPORTED;
     if (!aligned16(u) || !aligned16(v) || !aligned16(w) || !aligned16(p_n) || !aligned16(f) ||
         (p_nm1 && !aligned16(p_nm1)))
         return FLUPS_EINVAL;
@@ -488,6 +534,7 @@ flups_status flups_rhs(flups_plan P, const double* u, const double* v, const dou
 flups_status flups_correct(flups_plan P, const double* p, const double* p_n, const double* p_nm1, double c1,
                            double c2, double dt, double* u, double* v, double* w) {
     if (!P || !p || !p_n || !u || !v || !w) return FLUPS_EINVAL;
+    if (has_ends(P)) return FLUPS_EUNSUPPORTED;
     if (!aligned16(p) || !aligned16(p_n) || !aligned16(u) || !aligned16(v) || !aligned16(w) ||
         (p_nm1 && !aligned16(p_nm1)))
         return FLUPS_EINVAL;
@@ -505,6 +552,11 @@ flups_status flups_solve(flups_plan P, const double* f, double* p, double rtol, 
         info->iters = 0;
         info->rel_res = -1.0;
         for (int q = 0; q < FLUPS_HIST; ++q) info->rel_res_hist[q] = -1.0;
+    }
+    if (has_ends(P)) {   // FP64 plans only; the residual of these ends is not evaluated here
+        const flups_status st = cuda_status(launch_solve64_r2r(P, f, p));
+        if (st == FLUPS_OK && info) info->iters = 1;
+        return st;
     }
     if (P->prec == FLUPS_FP64) {
         flups_status st = cuda_status(launch_solve64(P, f, p));
@@ -584,6 +636,7 @@ flups_status flups_project_host(flups_plan P, double* u, double* v, double* w, c
                                 const double* p_n, const double* p_nm1, double c1, double c2, double dt,
                                 double rtol, int max_iter, double* p_out, flups_info* info) {
     if (!P || !u || !v || !w || !rho || !p_n || !p_out) return FLUPS_EINVAL;
+    if (has_ends(P)) return FLUPS_EUNSUPPORTED;
     DeviceGuard dg(P->dev);
     const size_t n = P->npts, b = n * sizeof(double);
     if (!P->hbuf) {

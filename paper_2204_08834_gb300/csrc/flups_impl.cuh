@@ -64,6 +64,7 @@ struct DevScalars {
 
 struct Geo {
     int nx, ny, nz, M, nxh, ldS, walls, iso;   // iso: dx == dy == every dzf
+    int sing00;                  // the (kx, ky) = (0, 0) z column is singular (no Dirichlet end in x, y)
     double dx, dy;
     double idx, idy;             // 1/dx, 1/dy
     double sx, sy;               // 1/dx^2, 1/dy^2
@@ -88,6 +89,8 @@ enum FlupsKernelId {
 
 struct flups_plan_s {
     int nx, ny, nz, bc, prec, dev;
+    int bcx, bcy;                // flups_xy_bc of the x and y ends (FLUPS_XY_PERIODIC unless created with ends)
+    int Wx;                      // spectral columns along x: nx/2+1 (periodic x) or nx (Neumann/Dirichlet x)
     double dx, dy;
     cudaStream_t stream;
     int M, nxh, ldS;
@@ -107,6 +110,7 @@ struct flups_plan_s {
     void* twx; void* twxr; void* twy; void* twz;   // W_M, W_nx (k<=M), W_ny, W_nz in compute type
     double* tabs64;              // [6][nz]: idzf, az, cz, idzc, dzf, dd = 2sx + 2sy + az + cz
     void* lamx; void* lamy; void* lamz;             // eigenvalues / norm, compute type
+    void* twqx; void* twqy;      // exp(-i pi k/(2 nx)), k <= nx/2, and exp(-i pi k/(2 ny)), k < ny (ends in x, y)
     void* tri;                   // walls: a_k/norm, b_k/norm, c_k/norm, compute type (3*nz)
     double sum_dzf;
     double dz0;                  // dzf[0] (the spacing of a periodic z)
@@ -151,6 +155,8 @@ cudaError_t launch_correct(flups_plan P, const double* p, const double* pn, cons
                            double c1, double c2, double dt, double* u, double* v, double* w);
 // FP64 direct solve
 cudaError_t launch_solve64(flups_plan P, const double* f, double* p);
+// FP64 direct solve of a plan with Neumann or Dirichlet ends in x or y
+cudaError_t launch_solve64_r2r(flups_plan P, const double* f, double* p);
 // FP32 pipeline pieces
 cudaError_t launch_xfwd32_from_f(flups_plan P, const double* f);            // S = FFTx(f), partial sums of f
 cudaError_t launch_finalize_f(flups_plan P);                                 // mean_f, ||f - mean||^2

@@ -435,7 +435,8 @@ extern "C" flups_status flups_momentum_predict(flups_plan P, const double* u, co
         !std::isfinite(gx) || !std::isfinite(gy) || !std::isfinite(gz))
         return FLUPS_EINVAL;
     if (arith != FLUPS_MOM_PAIR && arith != FLUPS_MOM_FP64) return FLUPS_EINVAL;
-    if (P->bc != FLUPS_BC_PERIODIC) return FLUPS_EUNSUPPORTED;
+    if (P->bc != FLUPS_BC_PERIODIC || P->bcx != FLUPS_XY_PERIODIC || P->bcy != FLUPS_XY_PERIODIC)
+        return FLUPS_EUNSUPPORTED;
     const double dz = P->dz0;             // periodic z: uniform spacing
     const double h = P->dx;
     if (arith == FLUPS_MOM_PAIR && !P->uniform_h) return FLUPS_EUNSUPPORTED;

@@ -16,6 +16,7 @@ LIB_PATH = os.path.join(_HERE, "libflups.so")
 
 OK, EINVAL, EUNSUPPORTED, ENOMEM, ECUDA, ENONFINITE, ENOCONV, ESTATE, ETIMEOUT = range(9)
 BC = {"periodic": 0, "walls": 1}
+XY_BC = {"periodic": 0, "neumann": 1, "dirichlet": 2}
 PREC = {"fp64": 0, "fp32_refine": 1}
 HIST = 16
 
@@ -31,7 +32,7 @@ SYMBOLS = [
     "flups_pnet_create", "flups_pnet_destroy", "flups_pnet_set_params", "flups_pnet_get_params",
     "flups_pnet_get_grads", "flups_pnet_predict", "flups_pnet_train_step", "flups_pnet_eval_loss",
     "flups_pnet_launch_count", "flups_pnet_set_profiling", "flups_pnet_profile_read", "flups_pnet_kernel_name",
-    "flups_selftest_wait_timeout", "flups_momentum_predict",
+    "flups_selftest_wait_timeout", "flups_momentum_predict", "flups_plan_create_bc",
 ]
 PNET_NKERNELS = 6
 PNET_NPARAMS = 15601
@@ -68,6 +69,7 @@ def lib():
         L = ctypes.CDLL(LIB_PATH)
         P, D, I, V = ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.c_void_p
         L.flups_plan_create.argtypes = [ctypes.POINTER(P), I, I, I, D, D, ctypes.POINTER(D), I, I, V]
+        L.flups_plan_create_bc.argtypes = [ctypes.POINTER(P), I, I, I, D, D, ctypes.POINTER(D), I, I, I, I, V]
         L.flups_plan_destroy.argtypes = [P]
         L.flups_set_stream.argtypes = [P, V]
         L.flups_workspace_bytes.argtypes = [P]
@@ -178,16 +180,17 @@ def current_stream():
 class Plan:
     """One projection plan (flups_plan_create).  Fields are [nz][ny][nx] float64."""
 
-    def __init__(self, nx, ny, nz, dx, dy, dzf, bc="periodic", prec="fp32_refine", stream=None):
+    def __init__(self, nx, ny, nz, dx, dy, dzf, bc="periodic", prec="fp32_refine", stream=None, bcx="periodic",
+                 bcy="periodic"):
         self.shape = (nz, ny, nx)
-        self.bc, self.prec = bc, prec
+        self.bc, self.prec, self.bcx, self.bcy = bc, prec, bcx, bcy
         dz = np.ascontiguousarray(np.broadcast_to(np.asarray(dzf, dtype=np.float64), (nz,)))
         self._dz = dz
         h = ctypes.c_void_p()
-        st = lib().flups_plan_create(ctypes.byref(h), int(nx), int(ny), int(nz), float(dx), float(dy),
-                                     dz.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), BC[bc], PREC[prec],
-                                     stream)
-        _check(st, "flups_plan_create")
+        st = lib().flups_plan_create_bc(ctypes.byref(h), int(nx), int(ny), int(nz), float(dx), float(dy),
+                                        dz.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), XY_BC[bcx], XY_BC[bcy],
+                                        BC[bc], PREC[prec], stream)
+        _check(st, "flups_plan_create_bc")
         self._h = h
 
     @classmethod

@@ -1,0 +1,117 @@
+"""GPU parity of the Poisson solve with Neumann or Dirichlet ends in x and/or y (Sec. 3.3.1,
+cosine/sine series; oracle/r2r.py, readings B1-B4) against the FP64 oracle.
+
+Tolerance: both sides are FP64 eigen-expansion solves (GPU: Makhoul's construction around the
+library's FFTs; oracle: scipy's DCT/DST), so p agrees to the rounding of the transforms
+amplified by the condition number of the smallest retained mode: relative L2 error <= 1e-11
+(as the periodic FP64 solve), and the oracle's residual of the GPU's p <= 1e-12.
+"""
+
+import itertools
+import zlib
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import r2r
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_2204_08834_gb300 import flups  # noqa: E402
+
+NAME = {"P": "periodic", "NN": "neumann", "DD": "dirichlet"}
+ENDS = [e for e in itertools.product(("P", "NN", "DD"), repeat=2) if e != ("P", "P")]
+
+
+def run(f, nx, ny, nz, dx, dy, dzf, bcz, bcx, bcy):
+    with flups.Plan(nx, ny, nz, dx, dy, dzf, bcz, "fp64", flups.current_stream(), bcx=NAME[bcx], bcy=NAME[bcy]) as plan:
+        fd = torch.from_numpy(f).cuda()
+        p = torch.empty_like(fd)
+        plan.solve(fd, p, rtol=0.0)
+        torch.cuda.synchronize()
+        return p.cpu().numpy()
+
+
+@pytest.mark.parametrize("bcz", ["periodic", "walls"])
+@pytest.mark.parametrize("shape", [(8, 16, 32), (16, 32, 8), (8, 8, 64)])
+@pytest.mark.parametrize("bcx,bcy", ENDS)
+def test_solve_with_ends_matches_oracle(bcx, bcy, shape, bcz):
+    nz, ny, nx = shape
+    dx, dy = 1.0 / nx, 1.3 / ny
+    if bcz == "periodic":
+        dzf = 0.7 / nz
+    else:
+        beta = 1.5
+        zf = 0.5 * (1 + np.tanh(beta * (2 * np.arange(nz + 1) / nz - 1)) / np.tanh(beta))
+        dzf = np.diff(zf)
+    g = oracle.make_grid(nx, ny, nz, dx, dy, dzf, bcz)
+    f = np.random.default_rng(zlib.crc32(repr((bcx, bcy, shape, bcz)).encode())).standard_normal(shape)
+    p = run(f, nx, ny, nz, dx, dy, dzf, bcz, bcx, bcy)
+    po = r2r.solve(f, g, bcx, bcy)
+    err = np.linalg.norm(p - po) / np.linalg.norm(po)
+    assert err <= 1e-11, err
+    assert r2r.rel_residual(f, p, g, bcx, bcy) <= 1e-12
+
+
+def test_single_mode_with_ends():
+    """A cosine mode in x (Neumann) times a sine mode in y (Dirichlet) times a Fourier mode in z:
+    p = f / (lam_x + lam_y + lam_z) exactly, with the closed-form eigenvalues."""
+    nz, ny, nx = 8, 16, 32
+    dx, dy, dz = 0.1, 0.07, 0.2
+    i, j, k = np.arange(nx), np.arange(ny), np.arange(nz)
+    kx, ky, kz = 5, 3, 2
+    f = (np.cos(np.pi * kx * (2 * i + 1) / (2 * nx))[None, None, :]
+         * np.sin(np.pi * (ky + 1) * (2 * j + 1) / (2 * ny))[None, :, None]
+         * np.cos(2 * np.pi * kz * k / nz + 0.3)[:, None, None])
+    lam = (-4 * np.sin(np.pi * kx / (2 * nx)) ** 2 / dx ** 2 - 4 * np.sin(np.pi * (ky + 1) / (2 * ny)) ** 2 / dy ** 2
+           - 4 * np.sin(np.pi * kz / nz) ** 2 / dz ** 2)
+    p = run(f, nx, ny, nz, dx, dy, dz, "periodic", "NN", "DD")
+    assert np.max(np.abs(p - f / lam)) <= 1e-12 * np.max(np.abs(f / lam))
+
+
+def test_periodic_ends_through_the_new_entry_point_equal_the_old():
+    nz, ny, nx = 8, 16, 32
+    f = np.random.default_rng(5).standard_normal((nz, ny, nx))
+    p1 = run(f, nx, ny, nz, 0.1, 0.1, 0.1, "periodic", "P", "P")
+    with flups.Plan(nx, ny, nz, 0.1, 0.1, 0.1, "periodic", "fp64", flups.current_stream()) as plan:
+        fd = torch.from_numpy(f).cuda()
+        p = torch.empty_like(fd)
+        plan.solve(fd, p, rtol=0.0)
+        p2 = p.cpu().numpy()
+    assert np.array_equal(p1, p2)
+
+
+def test_unsupported_uses_of_plans_with_ends():
+    with pytest.raises(flups.FlupsError) as e:
+        flups.Plan(32, 16, 8, 0.1, 0.1, 0.1, "periodic", "fp32_refine", bcx="neumann")
+    assert e.value.status == flups.EUNSUPPORTED
+    with flups.Plan(32, 16, 8, 0.1, 0.1, 0.1, "periodic", "fp64", bcx="neumann") as plan:
+        z = torch.zeros((8, 16, 32), dtype=torch.float64, device="cuda")
+        with pytest.raises(flups.FlupsError) as e:
+            plan.set_density(z + 1.0)
+        assert e.value.status == flups.EUNSUPPORTED
+        with pytest.raises(flups.FlupsError) as e:
+            plan.rhs(z, z, z, z, z, 2.0, 1.0, 1e-3, z.clone())
+        assert e.value.status == flups.EUNSUPPORTED
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32_refine"])
+def test_walls_solve_removes_the_mean_of_f(prec):
+    """z walls, periodic x and y, f with a large mean: the solve returns L^-1 (f - <f>_V) with zero
+    mean (R3) in both precisions (the singular column subtracts the mean before dropping its
+    first row)."""
+    nz, ny, nx = 12, 16, 32
+    beta = 1.5
+    zf = 0.5 * (1 + np.tanh(beta * (2 * np.arange(nz + 1) / nz - 1)) / np.tanh(beta))
+    dzf = np.diff(zf)
+    g = oracle.make_grid(nx, ny, nz, 1 / nx, 1 / ny, dzf, "walls")
+    f = np.random.default_rng(8).standard_normal((nz, ny, nx)) + 3.7
+    with flups.Plan(nx, ny, nz, 1 / nx, 1 / ny, dzf, "walls", prec, flups.current_stream()) as plan:
+        fd = torch.from_numpy(f).cuda()
+        p = torch.empty_like(fd)
+        plan.solve(fd, p, rtol=1e-12 if prec == "fp32_refine" else 0.0, max_iter=12)
+        p = p.cpu().numpy()
+    po = oracle.solve(f, g)
+    assert np.linalg.norm(p - po) / np.linalg.norm(po) <= (1e-11 if prec == "fp64" else 1e-9)
