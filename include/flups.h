@@ -97,12 +97,13 @@ flups_status flups_plan_create(flups_plan* out, int nx, int ny, int nz, double d
  *              ends (p = 0 on the boundary face): sine series (DST-II/III), modes
  *              sin(pi (k+1)(2i+1)/(2n)), eigenvalues -4 sin^2(pi (k+1)/(2n))/h^2.
  *   bc       : the z treatment, as in flups_plan_create.
- * A plan with any non-periodic x/y end takes prec = FLUPS_FP64 only (FLUPS_EUNSUPPORTED
- * otherwise) and only flups_solve: set_density, rhs, correct and the host-buffer projection
- * return FLUPS_EUNSUPPORTED.  Its solve is L p = f when an end is Dirichlet (L is then
- * nonsingular and the mean of f is kept), and L p = f - <f>_V with <p>_V = 0 otherwise; it
- * does not evaluate its residual (info->rel_res stays -1).  Mixed ends (Neumann at one face,
- * Dirichlet at the other) are not provided.
+ A plan with any non-periodic x/y end takes only flups_solve (set_density, rhs, correct and
+ * the host-buffer projection return FLUPS_EUNSUPPORTED).  Its solve is L p = f when an end is
+ * Dirichlet (L is then nonsingular and the mean of f is kept), and L p = f - <f>_V with
+ * <p>_V = 0 otherwise.  FLUPS_FP64: one direct pass, residual not evaluated (info->rel_res
+ * stays -1).  FLUPS_FP32_REFINE: FP32 transforms, the FP64 defect f - <f> - L p with the ends'
+ * ghost rules, repeated to rtol by a host-driven loop (synchronises; not graph capturable).
+ * Mixed ends (Neumann at one face, Dirichlet at the other) are not provided.
  */
 flups_status flups_plan_create_bc(flups_plan* out, int nx, int ny, int nz, double dx, double dy,
                                   const double* dzf, int bcx, int bcy, int bc, int prec, void* stream);

@@ -1488,6 +1488,54 @@ void r2r_backward(flups_plan P, double* p, const Geo& g, const Geo& gc, int ncol
     else run_xinv<T, ACC, false, false>(P, p, g);
 }
 
+// FP64 defect of a plan with Neumann or Dirichlet ends: r = f - mf - L p (p null: r = f - mf),
+// with the ghost rules of the ends in x and y (periodic wrap, p_ghost = p for Neumann, -p for
+// Dirichlet) and the z coefficients az, cz of the plan; part[b] = block sum of r^2.  With
+// pass 0, r and p are not touched and part[b] = block sum of dzf_k f (the volume mean).
+__global__ void __launch_bounds__(256) k_res_ends(const double* __restrict__ f, const double* __restrict__ p,
+                                                  double* __restrict__ r, Geo g, int bcx, int bcy, double mf,
+                                                  int pass, double* __restrict__ part) {
+    const size_t n = (size_t)g.nx * g.ny * g.nz;
+    double acc = 0.0;
+    for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n; q += (size_t)gridDim.x * blockDim.x) {
+        const int i = (int)(q % g.nx);
+        const size_t rr = q / g.nx;
+        const int j = (int)(rr % g.ny), k = (int)(rr / g.ny);
+        const double fv = f[q];
+        if (pass == 0) { acc = fma(fv, g.dzf[k], acc); continue; }
+        double rv = fv - mf;
+        if (p) {
+            const double pc = p[q];
+            const size_t row = rr * g.nx;
+            auto nb = [&](int bc, int t, int nn, size_t idx_in, size_t idx_wrap) -> double {
+                if (t >= 0 && t < nn) return p[idx_in];
+                if (bc == FLUPS_XY_PERIODIC) return p[idx_wrap];
+                return bc == FLUPS_XY_NEUMANN ? pc : -pc;
+            };
+            const double pw = nb(bcx, i - 1, g.nx, row + i - 1, row + g.nx - 1);
+            const double pe = nb(bcx, i + 1, g.nx, row + i + 1, row);
+            const size_t pl = (size_t)k * g.ny;
+            const double ps = nb(bcy, j - 1, g.ny, (pl + j - 1) * g.nx + i, (pl + g.ny - 1) * g.nx + i);
+            const double pn = nb(bcy, j + 1, g.ny, (pl + j + 1) * g.nx + i, pl * g.nx + i);
+            int km, kp;
+            if (g.walls) { km = k > 0 ? k - 1 : 0; kp = k < g.nz - 1 ? k + 1 : g.nz - 1; }
+            else { km = k == 0 ? g.nz - 1 : k - 1; kp = k + 1 == g.nz ? 0 : k + 1; }
+            const double pb = p[((size_t)km * g.ny + j) * g.nx + i], pt = p[((size_t)kp * g.ny + j) * g.nx + i];
+            const double lp = g.sx * (pw + pe - 2.0 * pc) + g.sy * (ps + pn - 2.0 * pc) + g.az[k] * (pb - pc) +
+                              g.cz[k] * (pt - pc);
+            rv -= lp;
+        }
+        r[q] = rv;
+        acc = fma(rv, rv, acc);
+    }
+    block_sum_abc<true, false, false>(acc, 0.f, 0.f, part);
+}
+
+__global__ void k_add_const(double* __restrict__ a, size_t n, double c) {
+    for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n; q += (size_t)gridDim.x * blockDim.x)
+        a[q] += c;
+}
+
 // CTAs of the x passes (one partial sum each) for a complex element of csize bytes; with
 // residual != 0, of the FP32 residual pass (which may use the tiled fixed-point layout).
 int xfwd_blocks(flups_plan P, int csize, int residual) {
@@ -1518,6 +1566,33 @@ cudaError_t launch_solve64_r2r(flups_plan P, const double* f, double* p) {
     r2r_forward<double>(P, f, g, gc, ncols);
     run_zsolve<double>(P, (double2*)P->spec, gc, P->bcx == FLUPS_XY_PERIODIC);
     r2r_backward<double, 0>(P, p, g, gc, ncols);
+    return cudaGetLastError();
+}
+
+int ends_res_blocks(flups_plan P) { return (int)std::min<size_t>((P->npts + 255) / 256, 2048); }
+
+cudaError_t launch_ends_residual(flups_plan P, const double* f, const double* p, double* r, double mf, int pass) {
+    const Geo g = plan_geo(P);
+    k_res_ends<<<ends_res_blocks(P), 256, 0, P->stream>>>(f, p, r, g, P->bcx, P->bcy, mf, pass, P->part);
+    FLUPS_COUNT(P, 1);
+    return cudaGetLastError();
+}
+
+// One FP32 solve of L d = r for a plan with ends; p = d (acc = 0) or p += d (acc = 1).
+cudaError_t launch_ends_solve32(flups_plan P, const double* r, double* p, int acc) {
+    const Geo g = plan_geo(P);
+    Geo gc;
+    int ncols;
+    r2r_forward<float>(P, r, g, gc, ncols);
+    run_zsolve<float>(P, (float2*)P->spec, gc, P->bcx == FLUPS_XY_PERIODIC);
+    if (acc) r2r_backward<float, 1>(P, p, g, gc, ncols);
+    else r2r_backward<float, 0>(P, p, g, gc, ncols);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_add_const(flups_plan P, double* a, double c) {
+    k_add_const<<<1024, 256, 0, P->stream>>>(a, P->npts, c);
+    FLUPS_COUNT(P, 1);
     return cudaGetLastError();
 }
 

@@ -294,7 +294,6 @@ flups_status flups_plan_create_bc(flups_plan* out, int nx, int ny, int nz, doubl
     if (bcx < FLUPS_XY_PERIODIC || bcx > FLUPS_XY_DIRICHLET || bcy < FLUPS_XY_PERIODIC || bcy > FLUPS_XY_DIRICHLET)
         return FLUPS_EINVAL;
     const bool ends = bcx != FLUPS_XY_PERIODIC || bcy != FLUPS_XY_PERIODIC;
-    if (ends && prec != FLUPS_FP64) return FLUPS_EUNSUPPORTED;
     if (!dzf || !(dx > 0.0) || !(dy > 0.0) || !std::isfinite(dx) || !std::isfinite(dy)) return FLUPS_EINVAL;
     if (bc != FLUPS_BC_PERIODIC && bc != FLUPS_BC_WALLS) return FLUPS_EINVAL;
     if (prec != FLUPS_FP64 && prec != FLUPS_FP32_REFINE) return FLUPS_EINVAL;
@@ -362,6 +361,7 @@ flups_status flups_plan_create_bc(flups_plan* out, int nx, int ny, int nz, doubl
     P->part = (double*)A.get(P->npart * sizeof(double));
     P->fin = (double*)A.get(3 * 256 * sizeof(double));
     P->tabs64 = (double*)A.get(6 * (size_t)nz * sizeof(double));
+    if (ends && prec == FLUPS_FP32_REFINE) P->rbuf = (double*)A.get(P->npts * sizeof(double));
     bool ok = A.ok;
     if (ok) {
         std::vector<double> t(6 * (size_t)nz);
@@ -498,6 +498,67 @@ flups_status flups_profile_read(flups_plan P, double* ms, long long* n) {
 // Plans with Neumann or Dirichlet ends in x or y take only the Poisson solve.
 bool has_ends(flups_plan P) { return P->bcx != FLUPS_XY_PERIODIC || P->bcy != FLUPS_XY_PERIODIC; }
 
+// Sum of the FP64 block partials (3 per block, the first used) of the last defect pass, in a
+// fixed order on the host (synchronises the plan's stream).
+flups_status ends_part_sum(flups_plan P, double* out) {
+    const int nb = ends_res_blocks(P);
+    std::vector<double> h(3 * (size_t)nb);
+    cudaError_t e = cudaMemcpyAsync(h.data(), P->part, h.size() * sizeof(double), cudaMemcpyDeviceToHost, P->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(P->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    double a = 0.0;
+    for (int b = 0; b < nb; ++b) a += h[3 * (size_t)b];
+    *out = a;
+    return FLUPS_OK;
+}
+
+// FP32 solves with FP64 defect correction for a plan with ends: r = f - <f> (singular L) or f,
+// then d = L32^-1 r, p += d, r = f - <f> - L p in FP64, until ||r|| <= rtol ||f - <f>||; a
+// singular L finally gets p shifted to zero volume-weighted mean.
+flups_status ends_refine(flups_plan P, const double* f, double* p, double rtol, int max_iter, flups_info* info) {
+    if (max_iter < 1 || max_iter > 64 || !(rtol >= 0.0)) return FLUPS_EINVAL;
+    const bool sing = P->bcx != FLUPS_XY_DIRICHLET && P->bcy != FLUPS_XY_DIRICHLET;
+    const double vol = (double)P->nx * P->ny * P->sum_dzf;
+    double mf = 0.0, f2 = 0.0, r2 = 0.0, s = 0.0;
+    flups_status st = FLUPS_OK;
+    if (sing) {
+        st = cuda_status(launch_ends_residual(P, f, nullptr, nullptr, 0.0, 0));
+        if (st == FLUPS_OK) st = ends_part_sum(P, &s);
+        if (st != FLUPS_OK) return st;
+        mf = s / vol;
+    }
+    st = cuda_status(launch_ends_residual(P, f, nullptr, P->rbuf, mf, 1));
+    if (st == FLUPS_OK) st = ends_part_sum(P, &f2);
+    if (st != FLUPS_OK) return st;
+    if (!std::isfinite(f2)) return FLUPS_ENONFINITE;
+    if (f2 == 0.0) {
+        if (info) info->rel_res = 0.0;
+        return cuda_status(cudaMemsetAsync(p, 0, P->npts * sizeof(double), P->stream));
+    }
+    double rel = 1.0;
+    for (int it = 1; it <= max_iter; ++it) {
+        st = cuda_status(launch_ends_solve32(P, P->rbuf, p, it > 1));
+        if (st == FLUPS_OK) st = cuda_status(launch_ends_residual(P, f, p, P->rbuf, mf, 1));
+        if (st == FLUPS_OK) st = ends_part_sum(P, &r2);
+        if (st != FLUPS_OK) return st;
+        rel = std::sqrt(r2 / f2);
+        if (info) {
+            info->iters = it;
+            info->rel_res = rel;
+            if (it - 1 < FLUPS_HIST) info->rel_res_hist[it - 1] = rel;
+        }
+        if (!std::isfinite(rel)) return FLUPS_ENONFINITE;
+        if (rel <= rtol) break;
+    }
+    if (sing) {
+        st = cuda_status(launch_ends_residual(P, p, nullptr, nullptr, 0.0, 0));
+        if (st == FLUPS_OK) st = ends_part_sum(P, &s);
+        if (st == FLUPS_OK) st = cuda_status(launch_add_const(P, p, -s / vol));
+        if (st != FLUPS_OK) return st;
+    }
+    return rel <= rtol ? FLUPS_OK : FLUPS_ENOCONV;
+}
+
 flups_status flups_set_density(flups_plan P, const double* rho, double rho0) {
     if (!P || !rho || !aligned16(rho) || std::isnan(rho0)) return FLUPS_EINVAL;
     if (has_ends(P)) return FLUPS_EUNSUPPORTED;
@@ -553,10 +614,13 @@ flups_status flups_solve(flups_plan P, const double* f, double* p, double rtol, 
         info->rel_res = -1.0;
         for (int q = 0; q < FLUPS_HIST; ++q) info->rel_res_hist[q] = -1.0;
     }
-    if (has_ends(P)) {   // FP64 plans only; the residual of these ends is not evaluated here
-        const flups_status st = cuda_status(launch_solve64_r2r(P, f, p));
-        if (st == FLUPS_OK && info) info->iters = 1;
-        return st;
+    if (has_ends(P)) {
+        if (P->prec == FLUPS_FP64) {   // direct; the residual is not evaluated here
+            const flups_status st = cuda_status(launch_solve64_r2r(P, f, p));
+            if (st == FLUPS_OK && info) info->iters = 1;
+            return st;
+        }
+        return ends_refine(P, f, p, rtol, max_iter, info);
     }
     if (P->prec == FLUPS_FP64) {
         flups_status st = cuda_status(launch_solve64(P, f, p));
@@ -609,6 +673,7 @@ flups_status flups_solve(flups_plan P, const double* f, double* p, double rtol, 
 flups_status flups_solve_graphable(flups_plan P, const double* f, double* p, double rtol, int max_iter) {
     if (!P || !f || !p || f == p || !aligned16(f) || !aligned16(p)) return FLUPS_EINVAL;
     if (P->prec != FLUPS_FP32_REFINE) return FLUPS_EINVAL;
+    if (has_ends(P)) return FLUPS_EUNSUPPORTED;
     if (max_iter < 1 || max_iter > 64 || !(rtol >= 0.0)) return FLUPS_EINVAL;
     DeviceGuard dg(P->dev);
     P->last_max_iter = max_iter;

@@ -111,6 +111,7 @@ struct flups_plan_s {
     double* tabs64;              // [6][nz]: idzf, az, cz, idzc, dzf, dd = 2sx + 2sy + az + cz
     void* lamx; void* lamy; void* lamz;             // eigenvalues / norm, compute type
     void* twqx; void* twqy;      // exp(-i pi k/(2 nx)), k <= nx/2, and exp(-i pi k/(2 ny)), k < ny (ends in x, y)
+    double* rbuf;                // FP64 defect of the FP32+refine solve with ends (npts)
     void* tri;                   // walls: a_k/norm, b_k/norm, c_k/norm, compute type (3*nz)
     double sum_dzf;
     double dz0;                  // dzf[0] (the spacing of a periodic z)
@@ -157,6 +158,12 @@ cudaError_t launch_correct(flups_plan P, const double* p, const double* pn, cons
 cudaError_t launch_solve64(flups_plan P, const double* f, double* p);
 // FP64 direct solve of a plan with Neumann or Dirichlet ends in x or y
 cudaError_t launch_solve64_r2r(flups_plan P, const double* f, double* p);
+// FP32+refine pieces of such plans: the FP64 defect (pass 1; pass 0: volume sum of f) with one
+// partial sum per block in P->part, the FP32 solve of L d = r into p (or p += d), p += c.
+int ends_res_blocks(flups_plan P);
+cudaError_t launch_ends_residual(flups_plan P, const double* f, const double* p, double* r, double mf, int pass);
+cudaError_t launch_ends_solve32(flups_plan P, const double* r, double* p, int acc);
+cudaError_t launch_add_const(flups_plan P, double* a, double c);
 // FP32 pipeline pieces
 cudaError_t launch_xfwd32_from_f(flups_plan P, const double* f);            // S = FFTx(f), partial sums of f
 cudaError_t launch_finalize_f(flups_plan P);                                 // mean_f, ||f - mean||^2

@@ -25,13 +25,13 @@ NAME = {"P": "periodic", "NN": "neumann", "DD": "dirichlet"}
 ENDS = [e for e in itertools.product(("P", "NN", "DD"), repeat=2) if e != ("P", "P")]
 
 
-def run(f, nx, ny, nz, dx, dy, dzf, bcz, bcx, bcy):
-    with flups.Plan(nx, ny, nz, dx, dy, dzf, bcz, "fp64", flups.current_stream(), bcx=NAME[bcx], bcy=NAME[bcy]) as plan:
+def run(f, nx, ny, nz, dx, dy, dzf, bcz, bcx, bcy, prec="fp64", rtol=0.0):
+    with flups.Plan(nx, ny, nz, dx, dy, dzf, bcz, prec, flups.current_stream(), bcx=NAME[bcx], bcy=NAME[bcy]) as plan:
         fd = torch.from_numpy(f).cuda()
         p = torch.empty_like(fd)
-        plan.solve(fd, p, rtol=0.0)
+        info = plan.solve(fd, p, rtol=rtol, max_iter=12)
         torch.cuda.synchronize()
-        return p.cpu().numpy()
+        return p.cpu().numpy(), info
 
 
 @pytest.mark.parametrize("bcz", ["periodic", "walls"])
@@ -48,11 +48,17 @@ def test_solve_with_ends_matches_oracle(bcx, bcy, shape, bcz):
         dzf = np.diff(zf)
     g = oracle.make_grid(nx, ny, nz, dx, dy, dzf, bcz)
     f = np.random.default_rng(zlib.crc32(repr((bcx, bcy, shape, bcz)).encode())).standard_normal(shape)
-    p = run(f, nx, ny, nz, dx, dy, dzf, bcz, bcx, bcy)
     po = r2r.solve(f, g, bcx, bcy)
+    p, _ = run(f, nx, ny, nz, dx, dy, dzf, bcz, bcx, bcy)
     err = np.linalg.norm(p - po) / np.linalg.norm(po)
     assert err <= 1e-11, err
     assert r2r.rel_residual(f, p, g, bcx, bcy) <= 1e-12
+    # FP32 transforms with FP64 defect correction to 1e-10: the oracle's residual of the GPU's p
+    # meets rtol, and p is within the residual times the conditioning of the smallest mode
+    p32, info = run(f, nx, ny, nz, dx, dy, dzf, bcz, bcx, bcy, "fp32_refine", 1e-10)
+    assert info.rel_res <= 1e-10
+    assert r2r.rel_residual(f, p32, g, bcx, bcy) <= 1e-10
+    assert np.linalg.norm(p32 - po) / np.linalg.norm(po) <= 1e-7
 
 
 def test_single_mode_with_ends():
@@ -67,14 +73,14 @@ def test_single_mode_with_ends():
          * np.cos(2 * np.pi * kz * k / nz + 0.3)[:, None, None])
     lam = (-4 * np.sin(np.pi * kx / (2 * nx)) ** 2 / dx ** 2 - 4 * np.sin(np.pi * (ky + 1) / (2 * ny)) ** 2 / dy ** 2
            - 4 * np.sin(np.pi * kz / nz) ** 2 / dz ** 2)
-    p = run(f, nx, ny, nz, dx, dy, dz, "periodic", "NN", "DD")
+    p, _ = run(f, nx, ny, nz, dx, dy, dz, "periodic", "NN", "DD")
     assert np.max(np.abs(p - f / lam)) <= 1e-12 * np.max(np.abs(f / lam))
 
 
 def test_periodic_ends_through_the_new_entry_point_equal_the_old():
     nz, ny, nx = 8, 16, 32
     f = np.random.default_rng(5).standard_normal((nz, ny, nx))
-    p1 = run(f, nx, ny, nz, 0.1, 0.1, 0.1, "periodic", "P", "P")
+    p1, _ = run(f, nx, ny, nz, 0.1, 0.1, 0.1, "periodic", "P", "P")
     with flups.Plan(nx, ny, nz, 0.1, 0.1, 0.1, "periodic", "fp64", flups.current_stream()) as plan:
         fd = torch.from_numpy(f).cuda()
         p = torch.empty_like(fd)
@@ -84,9 +90,11 @@ def test_periodic_ends_through_the_new_entry_point_equal_the_old():
 
 
 def test_unsupported_uses_of_plans_with_ends():
-    with pytest.raises(flups.FlupsError) as e:
-        flups.Plan(32, 16, 8, 0.1, 0.1, 0.1, "periodic", "fp32_refine", bcx="neumann")
-    assert e.value.status == flups.EUNSUPPORTED
+    with flups.Plan(32, 16, 8, 0.1, 0.1, 0.1, "periodic", "fp32_refine", bcx="neumann") as plan:
+        z = torch.zeros((8, 16, 32), dtype=torch.float64, device="cuda")
+        with pytest.raises(flups.FlupsError) as e:
+            plan.solve_graphable(z, z.clone(), rtol=1e-10, max_iter=3)
+        assert e.value.status == flups.EUNSUPPORTED
     with flups.Plan(32, 16, 8, 0.1, 0.1, 0.1, "periodic", "fp64", bcx="neumann") as plan:
         z = torch.zeros((8, 16, 32), dtype=torch.float64, device="cuda")
         with pytest.raises(flups.FlupsError) as e:
