@@ -68,6 +68,8 @@ KERNEL_WORK = {
     # u**, v**, w** and the state; the pre-pass reads u, v, w for max|u|
     "k_momentum": {"bound": "hbm", "bytes": 24 + 24 + 24 + 24},
     "k_mom_umax": {"bound": "hbm", "bytes": 24},
+    # FP64 defect with the ends' ghost rules: reads f, p, writes r (neighbours from caches)
+    "k_res_ends": {"bound": "hbm", "bytes": 24},
 }
 
 
@@ -259,6 +261,8 @@ def run_ours(args, rank, world, dev):
         out["learned"] = run_learned(args)
     if not args.no_momentum:
         out["momentum"] = run_momentum(args)
+    if not args.no_ends:
+        out["ends"] = run_ends(args)
 
     # end to end: the same projection through flups_project_host on pinned host buffers
     if not args.no_e2e:
@@ -582,6 +586,63 @@ def run_momentum(args):
     return out
 
 
+def run_ends(args):
+    """The Poisson solve in the generality of Sec. 3.3.1: a closed box with homogeneous Neumann
+    ends in x and y (cosine series along x and y) and walls in z with tanh-stretched spacing
+    (beta 1.5), 512 x 512 x 256 (the two-layer Rayleigh-Benard shape in a closed cell), f ~ N(0,1)
+    seeded; FP32 transforms + FP64 defect correction to rtol vs the FP64 direct solve, CUDA
+    events around whole solves on the launch stream."""
+    import torch
+
+    from paper_2204_08834_gb300 import flups, synth
+
+    nx, ny, nz = 512, 512, 256
+    dzf = synth.stretched_dzf(nz, 1.0, 1.5)
+    dx = dy = 2.0 / nx
+    npts = nx * ny * nz
+    stream = torch.cuda.current_stream().cuda_stream
+    f = torch.from_numpy(np.random.default_rng(60).standard_normal((nz, ny, nx))).cuda()
+    p = torch.empty_like(f)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    out = {"workload": "closed box 512x512x256: Neumann ends in x and y (cosine series), z walls with "
+                       "tanh-stretched dz (beta 1.5), dx = dy = 2/512, f ~ N(0,1) seeded", "points": npts}
+    pk, pk_kind = peaks()
+    for prec in ("fp32_refine", "fp64"):
+        rtol = args.rtol if prec == "fp32_refine" else 0.0
+        k = args.steps if prec == "fp32_refine" else max(2, args.steps // 2)
+        with flups.Plan(nx, ny, nz, dx, dy, dzf, "walls", prec, stream, bcx="neumann", bcy="neumann") as plan:
+            for _ in range(args.warmup):
+                info = plan.solve(f, p, rtol=rtol, max_iter=12)
+            torch.cuda.synchronize()
+            e0.record()
+            for _ in range(k):
+                info = plan.solve(f, p, rtol=rtol, max_iter=12)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / k
+            entry = {"ms_per_solve": round(ms, 4), "mpts_per_s": round(npts / (ms * 1e-3) / 1e6, 1), "solves": k,
+                     "iters": info.iters, "rel_res": info.rel_res}
+            if prec == "fp32_refine":
+                plan.set_profiling(True)
+                plan.solve(f, p, rtol=rtol, max_iter=12)
+                prof = plan.profile()
+                plan.set_profiling(False)
+                kern = {}
+                for kk, (kms, cnt) in sorted(prof.items(), key=lambda kv: -kv[1][0]):
+                    e = {"ms": round(kms, 4), "regions": cnt}
+                    w = KERNEL_WORK.get(kk)
+                    if kk == "k_res_ends" and cnt:
+                        gbs = w["bytes"] * npts / (kms / cnt * 1e-3) / 1e9
+                        e["algorithmic_GBps"] = round(gbs, 1)
+                        e["hbm_frac"] = round(gbs / pk["hbm_gbs"], 4)
+                    kern[kk] = e
+                entry["kernels"] = kern
+            out[prec] = entry
+    del f, p
+    torch.cuda.empty_cache()
+    return out
+
+
 def cpu_baseline():
     """The FP64 oracle (numpy, as it stands) on a bounded sample: three 256^3 emulsion
     projections (the 256^3 size of the same emulsion configuration)."""
@@ -646,6 +707,7 @@ def main():
     ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--no-cufft", action="store_true")
     ap.add_argument("--no-momentum", action="store_true")
+    ap.add_argument("--no-ends", action="store_true")
     ap.add_argument("--learned-windows", type=int, default=100,
                     help="64^3 training windows of 20 samples (default 100: 2000 samples)")
     ap.add_argument("--learned-epochs", type=int, default=3)
@@ -779,6 +841,8 @@ def main():
         line["learned"] = out["learned"]
     if "momentum" in out:
         line["momentum"] = out["momentum"]
+    if "ends" in out:
+        line["ends"] = out["ends"]
     if world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line))

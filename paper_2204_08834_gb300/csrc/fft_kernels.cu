@@ -1494,39 +1494,62 @@ void r2r_backward(flups_plan P, double* p, const Geo& g, const Geo& gc, int ncol
 // pass 0, r and p are not touched and part[b] = block sum of dzf_k f (the volume mean).
 __global__ void __launch_bounds__(256) k_res_ends(const double* __restrict__ f, const double* __restrict__ p,
                                                   double* __restrict__ r, Geo g, int bcx, int bcy, double mf,
-                                                  int pass, double* __restrict__ part) {
-    const size_t n = (size_t)g.nx * g.ny * g.nz;
+                                                  int pass, const double* __restrict__ dd,
+                                                  double* __restrict__ part) {
+    // One row (fixed j, k) per CTA iteration, x across the threads: no 64-bit index division.
+    const int nrows = g.ny * g.nz, nx = g.nx;
     double acc = 0.0;
-    for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n; q += (size_t)gridDim.x * blockDim.x) {
-        const int i = (int)(q % g.nx);
-        const size_t rr = q / g.nx;
-        const int j = (int)(rr % g.ny), k = (int)(rr / g.ny);
-        const double fv = f[q];
-        if (pass == 0) { acc = fma(fv, g.dzf[k], acc); continue; }
-        double rv = fv - mf;
-        if (p) {
-            const double pc = p[q];
-            const size_t row = rr * g.nx;
-            auto nb = [&](int bc, int t, int nn, size_t idx_in, size_t idx_wrap) -> double {
-                if (t >= 0 && t < nn) return p[idx_in];
-                if (bc == FLUPS_XY_PERIODIC) return p[idx_wrap];
-                return bc == FLUPS_XY_NEUMANN ? pc : -pc;
-            };
-            const double pw = nb(bcx, i - 1, g.nx, row + i - 1, row + g.nx - 1);
-            const double pe = nb(bcx, i + 1, g.nx, row + i + 1, row);
-            const size_t pl = (size_t)k * g.ny;
-            const double ps = nb(bcy, j - 1, g.ny, (pl + j - 1) * g.nx + i, (pl + g.ny - 1) * g.nx + i);
-            const double pn = nb(bcy, j + 1, g.ny, (pl + j + 1) * g.nx + i, pl * g.nx + i);
-            int km, kp;
-            if (g.walls) { km = k > 0 ? k - 1 : 0; kp = k < g.nz - 1 ? k + 1 : g.nz - 1; }
-            else { km = k == 0 ? g.nz - 1 : k - 1; kp = k + 1 == g.nz ? 0 : k + 1; }
-            const double pb = p[((size_t)km * g.ny + j) * g.nx + i], pt = p[((size_t)kp * g.ny + j) * g.nx + i];
-            const double lp = g.sx * (pw + pe - 2.0 * pc) + g.sy * (ps + pn - 2.0 * pc) + g.az[k] * (pb - pc) +
-                              g.cz[k] * (pt - pc);
-            rv -= lp;
+    for (int row = blockIdx.x; row < nrows; row += gridDim.x) {
+        const int k = row / g.ny, j = row - k * g.ny;
+        const double* fr = f + (size_t)row * nx;
+        if (pass == 0) {
+            const double w = __ldg(g.dzf + k);
+            for (int i = threadIdx.x; i < nx; i += blockDim.x) acc = fma(__ldg(fr + i), w, acc);
+            continue;
         }
-        r[q] = rv;
-        acc = fma(rv, rv, acc);
+        double* rr = r + (size_t)row * nx;
+        if (!p) {
+            for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+                const double rv = __ldg(fr + i) - mf;
+                rr[i] = rv;
+                acc = fma(rv, rv, acc);
+            }
+            continue;
+        }
+        // neighbour rows (y: periodic wrap or the ghost row itself with sign; z: walls clamp with
+        // a zero coefficient, or periodic wrap)
+        const double* pr = p + (size_t)row * nx;
+        const int js = j - 1, jn = j + 1;
+        const bool ys_in = js >= 0, yn_in = jn < g.ny;
+        const double sgs = ys_in || bcy == FLUPS_XY_PERIODIC ? 1.0 : (bcy == FLUPS_XY_NEUMANN ? 1.0 : -1.0);
+        const double sgn = yn_in || bcy == FLUPS_XY_PERIODIC ? 1.0 : (bcy == FLUPS_XY_NEUMANN ? 1.0 : -1.0);
+        const double* ps = (ys_in || bcy == FLUPS_XY_PERIODIC) ? p + ((size_t)k * g.ny + (ys_in ? js : g.ny - 1)) * nx : pr;
+        const double* pn = (yn_in || bcy == FLUPS_XY_PERIODIC) ? p + ((size_t)k * g.ny + (yn_in ? jn : 0)) * nx : pr;
+        int km, kp;
+        if (g.walls) { km = k > 0 ? k - 1 : 0; kp = k < g.nz - 1 ? k + 1 : g.nz - 1; }
+        else { km = k == 0 ? g.nz - 1 : k - 1; kp = k + 1 == g.nz ? 0 : k + 1; }
+        const double* pb = p + ((size_t)km * g.ny + j) * nx;
+        const double* pt = p + ((size_t)kp * g.ny + j) * nx;
+        const double azk = __ldg(g.az + k), czk = __ldg(g.cz + k), dk = __ldg(dd + k);
+        const double sxw = bcx == FLUPS_XY_DIRICHLET ? -1.0 : 1.0;
+        for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+            const double pc = __ldg(pr + i);
+            double pw, pe;
+            if (i > 0) pw = __ldg(pr + i - 1);
+            else pw = bcx == FLUPS_XY_PERIODIC ? __ldg(pr + nx - 1) : sxw * pc;
+            if (i + 1 < nx) pe = __ldg(pr + i + 1);
+            else pe = bcx == FLUPS_XY_PERIODIC ? __ldg(pr) : sxw * pc;
+            // L p + mf = sx (pw + pe) + sy (ps + pn) + az pb + cz pt - dd pc + mf,
+            // dd = 2 sx + 2 sy + az + cz (the diagonal of the periodic/wall operator)
+            double a = fma(g.sx, pw + pe, mf);
+            a = fma(g.sy, sgs * __ldg(ps + i) + sgn * __ldg(pn + i), a);
+            a = fma(azk, __ldg(pb + i), a);
+            a = fma(czk, __ldg(pt + i), a);
+            a = fma(-dk, pc, a);
+            const double rv = __ldg(fr + i) - a;
+            rr[i] = rv;
+            acc = fma(rv, rv, acc);
+        }
     }
     block_sum_abc<true, false, false>(acc, 0.f, 0.f, part);
 }
@@ -1569,11 +1592,14 @@ cudaError_t launch_solve64_r2r(flups_plan P, const double* f, double* p) {
     return cudaGetLastError();
 }
 
-int ends_res_blocks(flups_plan P) { return (int)std::min<size_t>((P->npts + 255) / 256, 2048); }
+int ends_res_blocks(flups_plan P) { return std::min(P->ny * P->nz, 2048); }
 
 cudaError_t launch_ends_residual(flups_plan P, const double* f, const double* p, double* r, double mf, int pass) {
     const Geo g = plan_geo(P);
-    k_res_ends<<<ends_res_blocks(P), 256, 0, P->stream>>>(f, p, r, g, P->bcx, P->bcy, mf, pass, P->part);
+    flups_prof_begin(P, FK_RES_ENDS);
+    k_res_ends<<<ends_res_blocks(P), 256, 0, P->stream>>>(f, p, r, g, P->bcx, P->bcy, mf, pass, P->tabs64 + 5 * g.nz,
+                                                          P->part);
+    flups_prof_end(P);
     FLUPS_COUNT(P, 1);
     return cudaGetLastError();
 }

@@ -123,3 +123,25 @@ def test_walls_solve_removes_the_mean_of_f(prec):
         p = p.cpu().numpy()
     po = oracle.solve(f, g)
     assert np.linalg.norm(p - po) / np.linalg.norm(po) <= (1e-11 if prec == "fp64" else 1e-9)
+
+
+@pytest.mark.slow
+def test_fullsize_closed_box_512x512x256():
+    """The measured workload (Neumann ends in x and y, stretched z walls, f ~ N(0,1) seed 60): the
+    oracle's residual of the GPU's p (FP32+refine to 1e-10, and FP64 direct), and both against
+    the oracle's own solve at full size."""
+    from paper_2204_08834_gb300 import synth
+    nx, ny, nz = 512, 512, 256
+    dzf = synth.stretched_dzf(nz, 1.0, 1.5)
+    g = oracle.make_grid(nx, ny, nz, 2.0 / nx, 2.0 / ny, dzf, "walls")
+    f = np.random.default_rng(60).standard_normal((nz, ny, nx))
+    p32, info = run(f, nx, ny, nz, 2.0 / nx, 2.0 / ny, dzf, "walls", "NN", "NN", "fp32_refine", 1e-10)
+    torch.cuda.empty_cache()
+    p64, _ = run(f, nx, ny, nz, 2.0 / nx, 2.0 / ny, dzf, "walls", "NN", "NN")
+    torch.cuda.empty_cache()
+    assert info.rel_res <= 1e-10
+    assert r2r.rel_residual(f, p32, g, "NN", "NN") <= 1e-10
+    assert r2r.rel_residual(f, p64, g, "NN", "NN") <= 1e-12
+    po = r2r.solve(f, g, "NN", "NN")
+    assert np.linalg.norm(p64 - po) / np.linalg.norm(po) <= 1e-11
+    assert np.linalg.norm(p32 - po) / np.linalg.norm(po) <= 1e-7
