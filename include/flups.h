@@ -53,8 +53,15 @@ typedef enum {
 typedef enum { FLUPS_BC_PERIODIC = 0, FLUPS_BC_WALLS = 1 } flups_bc;
 
 /* Ends of the x and y directions (flups_plan_create_bc): periodic, or homogeneous Neumann
- * (dp/dn = 0) or homogeneous Dirichlet (p = 0) on both boundary faces of the direction. */
-typedef enum { FLUPS_XY_PERIODIC = 0, FLUPS_XY_NEUMANN = 1, FLUPS_XY_DIRICHLET = 2 } flups_xy_bc;
+ * (dp/dn = 0) / homogeneous Dirichlet (p = 0) on the low (index -1/2) and high (n-1/2) boundary
+ * faces of the direction. */
+typedef enum {
+    FLUPS_XY_PERIODIC = 0,
+    FLUPS_XY_NEUMANN = 1,     /* Neumann at both faces   */
+    FLUPS_XY_DIRICHLET = 2,   /* Dirichlet at both faces */
+    FLUPS_XY_NEU_DIR = 3,     /* Neumann low, Dirichlet high */
+    FLUPS_XY_DIR_NEU = 4      /* Dirichlet low, Neumann high */
+} flups_xy_bc;
 
 typedef enum {
     FLUPS_FP64 = 0,          /* FFTs and z solve in FP64, one direct pass                  */
@@ -95,7 +102,9 @@ flups_status flups_plan_create(flups_plan* out, int nx, int ny, int nz, double d
  *   bcx, bcy : flups_xy_bc.  Neumann at both ends: cosine series (DCT-II/III), modes
  *              cos(pi k (2i+1)/(2n)), eigenvalues -4 sin^2(pi k/(2n))/h^2; Dirichlet at both
  *              ends (p = 0 on the boundary face): sine series (DST-II/III), modes
- *              sin(pi (k+1)(2i+1)/(2n)), eigenvalues -4 sin^2(pi (k+1)/(2n))/h^2.
+ *              sin(pi (k+1)(2i+1)/(2n)), eigenvalues -4 sin^2(pi (k+1)/(2n))/h^2; mixed ends:
+ *              modes cos (Neumann low) or sin (Dirichlet low) of pi (2k+1)(2i+1)/(4n) (DCT-IV,
+ *              DST-IV), eigenvalues -4 sin^2(pi (2k+1)/(4n))/h^2.
  *   bc       : the z treatment, as in flups_plan_create.
  A plan with any non-periodic x/y end takes only flups_solve (set_density, rhs, correct and
  * the host-buffer projection return FLUPS_EUNSUPPORTED).  Its solve is L p = f when an end is
@@ -103,7 +112,6 @@ flups_status flups_plan_create(flups_plan* out, int nx, int ny, int nz, double d
  * <p>_V = 0 otherwise.  FLUPS_FP64: one direct pass, residual not evaluated (info->rel_res
  * stays -1).  FLUPS_FP32_REFINE: FP32 transforms, the FP64 defect f - <f> - L p with the ends'
  * ghost rules, repeated to rtol by a host-driven loop (synchronises; not graph capturable).
- * Mixed ends (Neumann at one face, Dirichlet at the other) are not provided.
  */
 flups_status flups_plan_create_bc(flups_plan* out, int nx, int ny, int nz, double dx, double dy,
                                   const double* dzf, int bcx, int bcy, int bc, int prec, void* stream);

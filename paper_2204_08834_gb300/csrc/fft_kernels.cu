@@ -589,6 +589,76 @@ __global__ void __launch_bounds__(512) k_xinv(const typename cplx<T>::t* __restr
 // to S[row][k] as (X_k, 0).  INV: V_k = conj(q_k) (X_k - i X_{nx-k}) (X_nx = 0), the merge and
 // half-length inverse FFT of k_xinv, and the inverse permutation; unnormalised like k_xinv (a
 // round trip gives M x).  ACC = 1 adds the result to p.
+// KIND 3 (Neumann at the low face, Dirichlet at the high face): X_k = sum_j x_j
+// cos(pi (2j+1)(2k+1)/(4 nx)) (DCT-IV); KIND 4 (Dirichlet low, Neumann high): the sine kind
+// (DST-IV) = (-1)^k DCT-IV of x read backwards.  An nx/2-point complex FFT of
+// u_m = (x_{2m} + i x_{nx-1-2m}) exp(-i pi (4m+1)/(4 nx)), then y_k = U_k exp(-i pi k/nx),
+// X_{2k} = Re y_k, X_{nx-1-2k} = -Im y_k.  The kind is its own inverse up to nx/2 = M, the
+// scaling of the other x transforms, so INV runs the same steps on the coefficients.
+template <typename T, int E, int KIND, int ACC>
+__device__ __forceinline__ void xdct4_row_tile(typename cplx<T>::t* __restrict__ S, const double* __restrict__ fin,
+                                               double* __restrict__ pout, bool inv, const Geo& g, const FftLen& L,
+                                               const typename cplx<T>::t* __restrict__ tw,
+                                               const typename cplx<T>::t* __restrict__ pre,
+                                               const typename cplx<T>::t* __restrict__ post, int lgB, int nrows,
+                                               unsigned char* smraw) {
+    typedef typename cplx<T>::t C;
+    C* s = reinterpret_cast<C*>(smraw);
+    T* sT = reinterpret_cast<T*>(smraw);
+    const int B = 1 << lgB, pitch = B + 1, M = g.M, nx = g.nx;
+    const int row0 = blockIdx.x * B, tid = threadIdx.x, nthr = blockDim.x;
+    constexpr bool SINE = KIND == 4;
+    for (int idx = tid; idx < B * M; idx += nthr) {
+        const int c = idx / M, n = idx - c * M;
+        const int row = row0 + c;
+        double a = 0.0, b = 0.0;                          // x_{2n}, x_{2n+1}
+        if (row < nrows) {
+            if (!inv) {
+                const double2 xv = __ldg(reinterpret_cast<const double2*>(fin + (size_t)row * nx) + n);
+                a = xv.x;
+                b = xv.y;
+            } else {
+                const C* in = S + (size_t)row * g.ldS;
+                a = (double)in[2 * n].x;
+                b = (double)in[2 * n + 1].x;
+            }
+        }
+        // x_{2n} is u_n's real part (cosine kind) and x_{2n+1} = x_{nx-1-2m} for m = M-1-n its
+        // imaginary part; the sine kind reads x backwards, which swaps the two.
+        sT[(n * pitch + c) * 2 + (SINE ? 1 : 0)] = from_double<T>(a);
+        sT[((M - 1 - n) * pitch + c) * 2 + (SINE ? 0 : 1)] = from_double<T>(b);
+    }
+    __syncthreads();
+    for (int idx = tid; idx < B * M; idx += nthr) {
+        const int c = idx % B, m = idx / B;
+        const C w = __ldg(&pre[m]);
+        const C u = s[m * pitch + c];
+        s[m * pitch + c] = mk<T>(u.x * w.x - u.y * w.y, u.x * w.y + u.y * w.x);
+    }
+    __syncthreads();
+    fft_tile<C, E, false>(s, pitch, lgB, L, tw);
+    for (int idx = tid; idx < B * M; idx += nthr) {
+        const int c = idx / M, k = idx - c * M;
+        const int row = row0 + c;
+        if (row >= nrows) continue;
+        const C w = __ldg(&post[k]);
+        const C U = s[k * pitch + c];
+        const T yr = U.x * w.x - U.y * w.y, yi = U.x * w.y + U.y * w.x;
+        const T xe = yr, xo = SINE ? yi : -yi;           // X_{2k}, X_{nx-1-2k} (sine: times (-1)^index)
+        if (!inv) {
+            C* out = S + (size_t)row * g.ldS;
+            out[2 * k] = mk<T>(xe, (T)0);
+            out[nx - 1 - 2 * k] = mk<T>(xo, (T)0);
+        } else {
+            double* dst = pout + (size_t)row * nx;
+            double ve = to_double<T>(xe), vo = to_double<T>(xo);
+            if (ACC) { ve += dst[2 * k]; vo += dst[nx - 1 - 2 * k]; }
+            dst[2 * k] = ve;
+            dst[nx - 1 - 2 * k] = vo;
+        }
+    }
+}
+
 template <typename T, int E, int KIND, bool INV, int ACC>
 __global__ void __launch_bounds__(512) k_xdct(typename cplx<T>::t* __restrict__ S, const double* __restrict__ fin,
                                                double* __restrict__ pout, Geo g, FftLen L,
@@ -597,6 +667,10 @@ __global__ void __launch_bounds__(512) k_xdct(typename cplx<T>::t* __restrict__ 
                                                const typename cplx<T>::t* __restrict__ twq, int lgB, int nrows) {
     typedef typename cplx<T>::t C;
     extern __shared__ __align__(16) unsigned char smraw[];
+    if constexpr (KIND >= 3) {   // twr: pre-twiddles, twq: post-twiddles of the DCT-IV kind
+        xdct4_row_tile<T, E, KIND, ACC>(S, fin, pout, INV, g, L, tw, twr, twq, lgB, nrows, smraw);
+        return;
+    }
     C* s = reinterpret_cast<C*>(smraw);
     T* sT = reinterpret_cast<T*>(smraw);
     const int B = 1 << lgB, pitch = B + 1, M = g.M, nx = g.nx;
@@ -760,6 +834,61 @@ __global__ void __launch_bounds__(1024) k_ydct(typename cplx<T>::t* __restrict__
                 base[(size_t)j * g.ldS + c] = z;
             }
         }
+    }
+}
+
+// ------------------------------------- y transforms with mixed ends (Neumann / Dirichlet)
+// KIND 3 (Neumann low, Dirichlet high: DCT-IV) and KIND 4 (Dirichlet low, Neumann high: DST-IV)
+// on complex columns: the real and the imaginary part of a column are two real sequences of
+// length ny, each transformed with the ny/2-point construction of xdct4_row_tile; a tile of B
+// complex columns is 2B sub-columns of ny/2 complex points (2c: real parts, 2c+1: imaginary
+// parts).  The kind is its own inverse up to ny/2; INV doubles the result so that a round trip
+// gives ny z like the other y transforms.
+template <typename T, int E, int KIND, bool INV>
+__global__ void __launch_bounds__(1024) k_ydct4(typename cplx<T>::t* __restrict__ S, Geo g, FftLen L2,
+                                                const typename cplx<T>::t* __restrict__ tw2,
+                                                const typename cplx<T>::t* __restrict__ pre,
+                                                const typename cplx<T>::t* __restrict__ post, int lgB, int ncols) {
+    typedef typename cplx<T>::t C;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    C* s = reinterpret_cast<C*>(smraw);
+    T* sT = reinterpret_cast<T*>(smraw);
+    constexpr bool SINE = KIND == 4;
+    const int B = 1 << lgB, B2 = 2 * B, pitch = B2 + 1;
+    const int N = g.ny, H = N / 2, tid = threadIdx.x, nthr = blockDim.x;
+    const int kxa = blockIdx.x * B;
+    C* base = S + (size_t)blockIdx.y * g.ny * g.ldS + kxa;
+    for (int idx = tid; idx < B * N; idx += nthr) {
+        const int c = idx % B, j = idx / B;
+        const C z = kxa + c < ncols ? base[(size_t)j * g.ldS + c] : mk<T>((T)0, (T)0);
+        // element j of a sequence: even j = 2m -> u_m real part (sine: imaginary), odd j -> u_m
+        // with m = (N-1-j)/2, imaginary part (sine: real)
+        const bool even = (j & 1) == 0;
+        const int m = even ? (j >> 1) : ((N - 1 - j) >> 1);
+        const int comp = (even != SINE) ? 0 : 1;
+        sT[(m * pitch + 2 * c) * 2 + comp] = z.x;
+        sT[(m * pitch + 2 * c + 1) * 2 + comp] = z.y;
+    }
+    __syncthreads();
+    for (int idx = tid; idx < B2 * H; idx += nthr) {
+        const int cc = idx % B2, m = idx / B2;
+        const C w = __ldg(&pre[m]);
+        const C u = s[m * pitch + cc];
+        s[m * pitch + cc] = mk<T>(u.x * w.x - u.y * w.y, u.x * w.y + u.y * w.x);
+    }
+    __syncthreads();
+    fft_tile<C, E, false>(s, pitch, lgB + 1, L2, tw2);
+    __syncthreads();
+    const T sc = INV ? (T)2 : (T)1;
+    for (int idx = tid; idx < B * H; idx += nthr) {
+        const int c = idx % B, k = idx / B;
+        if (kxa + c >= ncols) continue;
+        const C w = __ldg(&post[k]);
+        const C Ua = s[k * pitch + 2 * c], Ub = s[k * pitch + 2 * c + 1];
+        const T ar = Ua.x * w.x - Ua.y * w.y, ai = Ua.x * w.y + Ua.y * w.x;
+        const T br = Ub.x * w.x - Ub.y * w.y, bi = Ub.x * w.y + Ub.y * w.x;
+        base[(size_t)(2 * k) * g.ldS + c] = mk<T>(sc * ar, sc * br);
+        base[(size_t)(N - 1 - 2 * k) * g.ldS + c] = SINE ? mk<T>(sc * ai, sc * bi) : mk<T>(-sc * ai, -sc * bi);
     }
 }
 
@@ -1410,22 +1539,28 @@ void run_xdct_e(flups_plan P, const double* fin, double* pout, const Geo& g) {
     auto kern = k_xdct<T, E, KIND, INV, ACC>;
     allow_smem(kern);
     flups_prof_begin(P, INV ? (sizeof(T) == 4 ? FK_XINV32 : FK_XINV64) : (sizeof(T) == 4 ? FK_XFWD_F32 : FK_XFWD64));
+    // KIND 1, 2: the split twiddles and the quarter-wave table; KIND 3, 4: pre- and post-twiddles
+    const C* t1 = KIND >= 3 ? (const C*)P->twqx : (const C*)P->twxr;
+    const C* t2 = KIND >= 3 ? (const C*)P->twqx + P->M : (const C*)P->twqx;
     kern<<<(nrows + B - 1) / B, B * N / E, (size_t)N * (B + 1) * sizeof(C), P->stream>>>(
-        (C*)P->spec, fin, pout, g, packed(P->lx), (const C*)P->twx, (const C*)P->twxr, (const C*)P->twqx, lgB,
-        nrows);
+        (C*)P->spec, fin, pout, g, packed(P->lx), (const C*)P->twx, t1, t2, lgB, nrows);
     flups_prof_end(P);
     FLUPS_COUNT(P, 1);
 }
 
+template <typename T, int KIND, bool INV, int ACC>
+void run_xdct_k(flups_plan P, const double* fin, double* pout, const Geo& g) {
+    if (e_for<T>(g.M) == 4) run_xdct_e<T, 4, KIND, INV, ACC>(P, fin, pout, g);
+    else run_xdct_e<T, 8, KIND, INV, ACC>(P, fin, pout, g);
+}
+
 template <typename T, bool INV, int ACC>
 void run_xdct(flups_plan P, const double* fin, double* pout, const Geo& g) {
-    const bool e4 = e_for<T>(g.M) == 4;
-    if (P->bcx == FLUPS_XY_NEUMANN) {
-        if (e4) run_xdct_e<T, 4, 1, INV, ACC>(P, fin, pout, g);
-        else run_xdct_e<T, 8, 1, INV, ACC>(P, fin, pout, g);
-    } else {
-        if (e4) run_xdct_e<T, 4, 2, INV, ACC>(P, fin, pout, g);
-        else run_xdct_e<T, 8, 2, INV, ACC>(P, fin, pout, g);
+    switch (P->bcx) {
+        case FLUPS_XY_NEUMANN: run_xdct_k<T, 1, INV, ACC>(P, fin, pout, g); break;
+        case FLUPS_XY_DIRICHLET: run_xdct_k<T, 2, INV, ACC>(P, fin, pout, g); break;
+        case FLUPS_XY_NEU_DIR: run_xdct_k<T, 3, INV, ACC>(P, fin, pout, g); break;
+        default: run_xdct_k<T, 4, INV, ACC>(P, fin, pout, g); break;
     }
 }
 
@@ -1444,15 +1579,40 @@ void run_ydct_e(flups_plan P, typename cplx<T>::t* S, const Geo& g, int ncols) {
     FLUPS_COUNT(P, 1);
 }
 
+template <typename T, int E, int KIND, bool INV>
+void run_ydct4_e(flups_plan P, typename cplx<T>::t* S, const Geo& g, int ncols) {
+    typedef typename cplx<T>::t C;
+    const int N = g.ny, H = N / 2;
+    // B complex columns: 2B sub-columns of H points; threads 2B H / E, shared memory H (2B+1)
+    int lgB = pick_lgB(N, sizeof(C), E, sizeof(T) == 4 ? 32 : 16, ncols, g.cta);
+    while (lgB > 0 && (long)(2 << lgB) * H / E > 1024) --lgB;
+    const int B = 1 << lgB;
+    auto kern = k_ydct4<T, E, KIND, INV>;
+    allow_smem(kern);
+    flups_prof_begin(P, sizeof(T) == 4 ? FK_YCOL32 : FK_YCOL64);
+    const C* tq = (const C*)P->twqy;
+    kern<<<dim3((ncols + B - 1) / B, g.nz), 2 * B * H / E, (size_t)H * (2 * B + 1) * sizeof(C), P->stream>>>(
+        S, g, packed(P->ly2), (const C*)P->twy2, tq, tq + H, lgB, ncols);
+    flups_prof_end(P);
+    FLUPS_COUNT(P, 1);
+}
+
 template <typename T, bool INV>
 void run_ydct(flups_plan P, typename cplx<T>::t* S, const Geo& g, int ncols) {
-    const bool e4 = e_for<T>(g.ny) == 4;
-    if (P->bcy == FLUPS_XY_NEUMANN) {
-        if (e4) run_ydct_e<T, 4, 1, INV>(P, S, g, ncols);
-        else run_ydct_e<T, 8, 1, INV>(P, S, g, ncols);
-    } else {
-        if (e4) run_ydct_e<T, 4, 2, INV>(P, S, g, ncols);
-        else run_ydct_e<T, 8, 2, INV>(P, S, g, ncols);
+    const bool e4 = e_for<T>(g.ny) == 4, h4 = e_for<T>(g.ny / 2) == 4;
+    switch (P->bcy) {
+        case FLUPS_XY_NEUMANN:
+            if (e4) run_ydct_e<T, 4, 1, INV>(P, S, g, ncols); else run_ydct_e<T, 8, 1, INV>(P, S, g, ncols);
+            break;
+        case FLUPS_XY_DIRICHLET:
+            if (e4) run_ydct_e<T, 4, 2, INV>(P, S, g, ncols); else run_ydct_e<T, 8, 2, INV>(P, S, g, ncols);
+            break;
+        case FLUPS_XY_NEU_DIR:
+            if (h4) run_ydct4_e<T, 4, 3, INV>(P, S, g, ncols); else run_ydct4_e<T, 8, 3, INV>(P, S, g, ncols);
+            break;
+        default:
+            if (h4) run_ydct4_e<T, 4, 4, INV>(P, S, g, ncols); else run_ydct4_e<T, 8, 4, INV>(P, S, g, ncols);
+            break;
     }
 }
 
@@ -1521,8 +1681,11 @@ __global__ void __launch_bounds__(256) k_res_ends(const double* __restrict__ f, 
         const double* pr = p + (size_t)row * nx;
         const int js = j - 1, jn = j + 1;
         const bool ys_in = js >= 0, yn_in = jn < g.ny;
-        const double sgs = ys_in || bcy == FLUPS_XY_PERIODIC ? 1.0 : (bcy == FLUPS_XY_NEUMANN ? 1.0 : -1.0);
-        const double sgn = yn_in || bcy == FLUPS_XY_PERIODIC ? 1.0 : (bcy == FLUPS_XY_NEUMANN ? 1.0 : -1.0);
+        // ghost sign of the low and high faces: +1 Neumann, -1 Dirichlet
+        const double ylo = (bcy == FLUPS_XY_DIRICHLET || bcy == FLUPS_XY_DIR_NEU) ? -1.0 : 1.0;
+        const double yhi = (bcy == FLUPS_XY_DIRICHLET || bcy == FLUPS_XY_NEU_DIR) ? -1.0 : 1.0;
+        const double sgs = ys_in || bcy == FLUPS_XY_PERIODIC ? 1.0 : ylo;
+        const double sgn = yn_in || bcy == FLUPS_XY_PERIODIC ? 1.0 : yhi;
         const double* ps = (ys_in || bcy == FLUPS_XY_PERIODIC) ? p + ((size_t)k * g.ny + (ys_in ? js : g.ny - 1)) * nx : pr;
         const double* pn = (yn_in || bcy == FLUPS_XY_PERIODIC) ? p + ((size_t)k * g.ny + (yn_in ? jn : 0)) * nx : pr;
         int km, kp;
@@ -1531,14 +1694,15 @@ __global__ void __launch_bounds__(256) k_res_ends(const double* __restrict__ f, 
         const double* pb = p + ((size_t)km * g.ny + j) * nx;
         const double* pt = p + ((size_t)kp * g.ny + j) * nx;
         const double azk = __ldg(g.az + k), czk = __ldg(g.cz + k), dk = __ldg(dd + k);
-        const double sxw = bcx == FLUPS_XY_DIRICHLET ? -1.0 : 1.0;
+        const double xlo = (bcx == FLUPS_XY_DIRICHLET || bcx == FLUPS_XY_DIR_NEU) ? -1.0 : 1.0;
+        const double xhi = (bcx == FLUPS_XY_DIRICHLET || bcx == FLUPS_XY_NEU_DIR) ? -1.0 : 1.0;
         for (int i = threadIdx.x; i < nx; i += blockDim.x) {
             const double pc = __ldg(pr + i);
             double pw, pe;
             if (i > 0) pw = __ldg(pr + i - 1);
-            else pw = bcx == FLUPS_XY_PERIODIC ? __ldg(pr + nx - 1) : sxw * pc;
+            else pw = bcx == FLUPS_XY_PERIODIC ? __ldg(pr + nx - 1) : xlo * pc;
             if (i + 1 < nx) pe = __ldg(pr + i + 1);
-            else pe = bcx == FLUPS_XY_PERIODIC ? __ldg(pr) : sxw * pc;
+            else pe = bcx == FLUPS_XY_PERIODIC ? __ldg(pr) : xhi * pc;
             // L p + mf = sx (pw + pe) + sy (ps + pn) + az pb + cz pt - dd pc + mf,
             // dd = 2 sx + 2 sy + az + cz (the diagonal of the periodic/wall operator)
             double a = fma(g.sx, pw + pe, mf);

@@ -59,8 +59,28 @@ double eig(int k, int n, double h) {
 // Dirichlet at both ends -4 sin^2(pi (k+1)/(2n))/h^2 (sine modes), Sec. 3.3.1.
 double eig_bc(int k, int n, double h, int bc) {
     if (bc == FLUPS_XY_PERIODIC) return eig(k, n, h);
-    const double s = std::sin(M_PI * (double)(bc == FLUPS_XY_NEUMANN ? k : k + 1) / (2.0 * (double)n));
+    double s;
+    if (bc == FLUPS_XY_NEUMANN || bc == FLUPS_XY_DIRICHLET)
+        s = std::sin(M_PI * (double)(bc == FLUPS_XY_NEUMANN ? k : k + 1) / (2.0 * (double)n));
+    else
+        s = std::sin(M_PI * (double)(2 * k + 1) / (4.0 * (double)n));   // mixed ends
     return -4.0 * s * s / (h * h);
+}
+
+bool mixed_bc(int bc) { return bc == FLUPS_XY_NEU_DIR || bc == FLUPS_XY_DIR_NEU; }
+
+// pre-twiddles exp(-i pi (4m+1)/(4n)), m < n/2, then post-twiddles exp(-i pi k/n), k < n/2
+template <typename T>
+void mixed_twiddles(std::vector<T>& out, int n) {
+    const int h = n / 2;
+    out.resize(4 * (size_t)h);
+    for (int m = 0; m < h; ++m) {
+        const double a = M_PI * (4.0 * m + 1.0) / (4.0 * n), b = M_PI * (double)m / (double)n;
+        out[2 * m] = (T)std::cos(a);
+        out[2 * m + 1] = (T)(-std::sin(a));
+        out[2 * (h + m)] = (T)std::cos(b);
+        out[2 * (h + m) + 1] = (T)(-std::sin(b));
+    }
 }
 
 // exp(-i pi k/(2n)), k < count (the quarter-wave twiddle of the cosine/sine transforms)
@@ -119,12 +139,20 @@ bool build_tables(flups_plan P, const std::vector<double>& dzf, DevAlloc& A) {
     for (int k = 0; k < P->ny; ++k) ly[k] = (T)(eig_bc(k, P->ny, P->dy, P->bcy) * scale);
     if (!upload(&P->lamx, lx, A) || !upload(&P->lamy, ly, A)) return false;
     if (P->bcx != FLUPS_XY_PERIODIC) {
-        quarter_twiddles(tw, P->nx, P->M + 1);
+        if (mixed_bc(P->bcx)) mixed_twiddles(tw, P->nx);
+        else quarter_twiddles(tw, P->nx, P->M + 1);
         if (!upload(&P->twqx, tw, A)) return false;
     }
     if (P->bcy != FLUPS_XY_PERIODIC) {
-        quarter_twiddles(tw, P->ny, P->ny);
-        if (!upload(&P->twqy, tw, A)) return false;
+        if (mixed_bc(P->bcy)) {
+            mixed_twiddles(tw, P->ny);
+            if (!upload(&P->twqy, tw, A)) return false;
+            twiddles(tw, P->ny / 2, P->ny / 2);
+            if (!upload(&P->twy2, tw, A)) return false;
+        } else {
+            quarter_twiddles(tw, P->ny, P->ny);
+            if (!upload(&P->twqy, tw, A)) return false;
+        }
     }
     if (!walls) {
         twiddles(tw, P->nz, P->nz);
@@ -241,7 +269,8 @@ Geo plan_geo(flups_plan P) {
     g.nx = P->nx; g.ny = P->ny; g.nz = P->nz; g.M = P->M; g.nxh = P->nxh; g.ldS = P->ldS;
     g.walls = P->bc == FLUPS_BC_WALLS;
     g.iso = P->uniform_h;
-    g.sing00 = P->bcx != FLUPS_XY_DIRICHLET && P->bcy != FLUPS_XY_DIRICHLET;
+    g.sing00 = (P->bcx == FLUPS_XY_PERIODIC || P->bcx == FLUPS_XY_NEUMANN) &&
+               (P->bcy == FLUPS_XY_PERIODIC || P->bcy == FLUPS_XY_NEUMANN);
     g.dx = P->dx; g.dy = P->dy;
     g.sx = 1.0 / (P->dx * P->dx); g.sy = 1.0 / (P->dy * P->dy);
     g.idx = 1.0 / P->dx; g.idy = 1.0 / P->dy;
@@ -291,7 +320,7 @@ flups_status flups_plan_create_bc(flups_plan* out, int nx, int ny, int nz, doubl
                                   const double* dzf, int bcx, int bcy, int bc, int prec, void* stream) {
     if (!out) return FLUPS_EINVAL;
     *out = nullptr;
-    if (bcx < FLUPS_XY_PERIODIC || bcx > FLUPS_XY_DIRICHLET || bcy < FLUPS_XY_PERIODIC || bcy > FLUPS_XY_DIRICHLET)
+    if (bcx < FLUPS_XY_PERIODIC || bcx > FLUPS_XY_DIR_NEU || bcy < FLUPS_XY_PERIODIC || bcy > FLUPS_XY_DIR_NEU)
         return FLUPS_EINVAL;
     const bool ends = bcx != FLUPS_XY_PERIODIC || bcy != FLUPS_XY_PERIODIC;
     if (!dzf || !(dx > 0.0) || !(dy > 0.0) || !std::isfinite(dx) || !std::isfinite(dy)) return FLUPS_EINVAL;
@@ -335,7 +364,8 @@ flups_status flups_plan_create_bc(flups_plan* out, int nx, int ny, int nz, doubl
     P->dz0 = dz[0];
     P->uniform_h = dx == dy;
     for (int k = 0; k < nz; ++k) P->uniform_h = P->uniform_h && dz[k] == dx;
-    if (!make_len(P->M, &P->lx) || !make_len(ny, &P->ly) || (bc == FLUPS_BC_PERIODIC && !make_len(nz, &P->lz))) {
+    if (!make_len(P->M, &P->lx) || !make_len(ny, &P->ly) || (bc == FLUPS_BC_PERIODIC && !make_len(nz, &P->lz)) ||
+        (mixed_bc(bcy) && !make_len(ny / 2, &P->ly2))) {
         delete P;
         return FLUPS_EUNSUPPORTED;
     }
@@ -517,7 +547,7 @@ flups_status ends_part_sum(flups_plan P, double* out) {
 // singular L finally gets p shifted to zero volume-weighted mean.
 flups_status ends_refine(flups_plan P, const double* f, double* p, double rtol, int max_iter, flups_info* info) {
     if (max_iter < 1 || max_iter > 64 || !(rtol >= 0.0)) return FLUPS_EINVAL;
-    const bool sing = P->bcx != FLUPS_XY_DIRICHLET && P->bcy != FLUPS_XY_DIRICHLET;
+    const bool sing = plan_geo(P).sing00 != 0;
     const double vol = (double)P->nx * P->ny * P->sum_dzf;
     double mf = 0.0, f2 = 0.0, r2 = 0.0, s = 0.0;
     flups_status st = FLUPS_OK;

@@ -96,6 +96,7 @@ struct flups_plan_s {
     int M, nxh, ldS;
     size_t npts, nspec;
     FftLen lx, ly, lz;           // lengths M (complex along x), ny, nz
+    FftLen ly2;                  // ny/2 (mixed ends along y)
     // workspace
     void* spec;                  // spectrum, float2 or double2
     void* zscr;                  // z Thomas multipliers (walls)
@@ -110,7 +111,9 @@ struct flups_plan_s {
     void* twx; void* twxr; void* twy; void* twz;   // W_M, W_nx (k<=M), W_ny, W_nz in compute type
     double* tabs64;              // [6][nz]: idzf, az, cz, idzc, dzf, dd = 2sx + 2sy + az + cz
     void* lamx; void* lamy; void* lamz;             // eigenvalues / norm, compute type
-    void* twqx; void* twqy;      // exp(-i pi k/(2 nx)), k <= nx/2, and exp(-i pi k/(2 ny)), k < ny (ends in x, y)
+    void* twqx; void* twqy;      // ends in x, y: exp(-i pi k/(2n)) (k <= n/2 along x, k < ny along y), or for mixed
+                                 // ends the pre-twiddles exp(-i pi (4m+1)/(4n)) then the post-twiddles exp(-i pi k/n)
+    void* twy2;                  // W_{ny/2} twiddles (mixed ends along y)
     double* rbuf;                // FP64 defect of the FP32+refine solve with ends (npts)
     void* tri;                   // walls: a_k/norm, b_k/norm, c_k/norm, compute type (3*nz)
     double sum_dzf;

@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(_HERE, "libflups.so")
 
 OK, EINVAL, EUNSUPPORTED, ENOMEM, ECUDA, ENONFINITE, ENOCONV, ESTATE, ETIMEOUT = range(9)
 BC = {"periodic": 0, "walls": 1}
-XY_BC = {"periodic": 0, "neumann": 1, "dirichlet": 2}
+XY_BC = {"periodic": 0, "neumann": 1, "dirichlet": 2, "neumann_dirichlet": 3, "dirichlet_neumann": 4}
 PREC = {"fp64": 0, "fp32_refine": 1}
 HIST = 16
 

@@ -21,8 +21,8 @@ pytestmark = pytest.mark.gpu
 
 from paper_2204_08834_gb300 import flups  # noqa: E402
 
-NAME = {"P": "periodic", "NN": "neumann", "DD": "dirichlet"}
-ENDS = [e for e in itertools.product(("P", "NN", "DD"), repeat=2) if e != ("P", "P")]
+NAME = {"P": "periodic", "NN": "neumann", "DD": "dirichlet", "ND": "neumann_dirichlet", "DN": "dirichlet_neumann"}
+ENDS = [e for e in itertools.product(r2r.KINDS, repeat=2) if e != ("P", "P")]
 
 
 def run(f, nx, ny, nz, dx, dy, dzf, bcz, bcx, bcy, prec="fp64", rtol=0.0):
@@ -59,6 +59,27 @@ def test_solve_with_ends_matches_oracle(bcx, bcy, shape, bcz):
     assert info.rel_res <= 1e-10
     assert r2r.rel_residual(f, p32, g, bcx, bcy) <= 1e-10
     assert np.linalg.norm(p32 - po) / np.linalg.norm(po) <= 1e-7
+
+
+@pytest.mark.parametrize("bcx,bcy", [("ND", "DN"), ("DN", "NN")])
+def test_single_mixed_mode(bcx, bcy):
+    """Mixed ends: cos/sin(pi (2k+1)(2i+1)/(4n)) modes with eigenvalues -4 sin^2(pi (2k+1)/(4n))/h^2."""
+    nz, ny, nx = 8, 16, 32
+    dx, dy, dz = 0.1, 0.07, 0.2
+    i, j, k = np.arange(nx), np.arange(ny), np.arange(nz)
+    kx, ky = 6, 2
+
+    def mode(bc, kk, ii, n):
+        if bc == "ND":
+            return np.cos(np.pi * (2 * kk + 1) * (2 * ii + 1) / (4 * n))
+        if bc == "DN":
+            return np.sin(np.pi * (2 * kk + 1) * (2 * ii + 1) / (4 * n))
+        return np.cos(np.pi * kk * (2 * ii + 1) / (2 * n))
+    f = mode(bcx, kx, i, nx)[None, None, :] * mode(bcy, ky, j, ny)[None, :, None] * np.ones((nz, 1, 1))
+    lx = -4 * np.sin(np.pi * (2 * kx + 1) / (4 * nx)) ** 2 / dx ** 2
+    ly = (-4 * np.sin(np.pi * (2 * ky + 1) / (4 * ny)) ** 2 if bcy != "NN" else -4 * np.sin(np.pi * ky / (2 * ny)) ** 2) / dy ** 2
+    p, _ = run(f, nx, ny, nz, dx, dy, dz, "periodic", bcx, bcy)
+    assert np.max(np.abs(p - f / (lx + ly))) <= 1e-12 * np.max(np.abs(f / (lx + ly)))
 
 
 def test_single_mode_with_ends():
