@@ -1659,6 +1659,7 @@ __global__ void __launch_bounds__(256) k_res_ends(const double* __restrict__ f, 
     // One row (fixed j, k) per CTA iteration, x across the threads: no 64-bit index division.
     const int nrows = g.ny * g.nz, nx = g.nx;
     double acc = 0.0;
+    float acc2 = 0.f;
     for (int row = blockIdx.x; row < nrows; row += gridDim.x) {
         const int k = row / g.ny, j = row - k * g.ny;
         const double* fr = f + (size_t)row * nx;
@@ -1696,6 +1697,27 @@ __global__ void __launch_bounds__(256) k_res_ends(const double* __restrict__ f, 
         const double azk = __ldg(g.az + k), czk = __ldg(g.cz + k), dk = __ldg(dd + k);
         const double xlo = (bcx == FLUPS_XY_DIRICHLET || bcx == FLUPS_XY_DIR_NEU) ? -1.0 : 1.0;
         const double xhi = (bcx == FLUPS_XY_DIRICHLET || bcx == FLUPS_XY_NEU_DIR) ? -1.0 : 1.0;
+        if (sgs == 1.0 && sgn == 1.0 && g.sx == g.sy) {
+            // rows with both y neighbours in place and dx = dy: eight FP64 instructions per
+            // point; the stopping test's sum of r^2 in binary32 (r rounded by integer operations)
+            for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+                const double pc = __ldg(pr + i);
+                double pw, pe;
+                if (i > 0) pw = __ldg(pr + i - 1);
+                else pw = bcx == FLUPS_XY_PERIODIC ? __ldg(pr + nx - 1) : xlo * pc;
+                if (i + 1 < nx) pe = __ldg(pr + i + 1);
+                else pe = bcx == FLUPS_XY_PERIODIC ? __ldg(pr) : xhi * pc;
+                double a = fma(g.sx, (pw + pe) + (__ldg(ps + i) + __ldg(pn + i)), mf);
+                a = fma(azk, __ldg(pb + i), a);
+                a = fma(czk, __ldg(pt + i), a);
+                a = fma(-dk, pc, a);
+                const double rv = __ldg(fr + i) - a;
+                rr[i] = rv;
+                const float rf = d2f_bits(rv);
+                acc2 = fmaf(rf, rf, acc2);
+            }
+            continue;
+        }
         for (int i = threadIdx.x; i < nx; i += blockDim.x) {
             const double pc = __ldg(pr + i);
             double pw, pe;
@@ -1715,7 +1737,9 @@ __global__ void __launch_bounds__(256) k_res_ends(const double* __restrict__ f, 
             acc = fma(rv, rv, acc);
         }
     }
-    block_sum_abc<true, false, false>(acc, 0.f, 0.f, part);
+    // part[3b] = block sum of dzf f (pass 0) or of r^2 in FP64; part[3b+1] = the binary32 sums
+    // of r^2 from the fast rows (per thread, added in FP64 across the block)
+    block_sum_abc<true, true, false>(acc, acc2, 0.f, part);
 }
 
 __global__ void k_add_const(double* __restrict__ a, size_t n, double c) {

@@ -528,7 +528,8 @@ flups_status flups_profile_read(flups_plan P, double* ms, long long* n) {
 // Plans with Neumann or Dirichlet ends in x or y take only the Poisson solve.
 bool has_ends(flups_plan P) { return P->bcx != FLUPS_XY_PERIODIC || P->bcy != FLUPS_XY_PERIODIC; }
 
-// Sum of the FP64 block partials (3 per block, the first used) of the last defect pass, in a
+// Sum of the block partials of the last defect pass (3 per block: FP64 sums, binary32 per-thread
+// sums of r^2 from the fast rows, zero), in a
 // fixed order on the host (synchronises the plan's stream).
 flups_status ends_part_sum(flups_plan P, double* out) {
     const int nb = ends_res_blocks(P);
@@ -537,7 +538,7 @@ flups_status ends_part_sum(flups_plan P, double* out) {
     if (e == cudaSuccess) e = cudaStreamSynchronize(P->stream);
     if (e != cudaSuccess) return cuda_status(e);
     double a = 0.0;
-    for (int b = 0; b < nb; ++b) a += h[3 * (size_t)b];
+    for (int b = 0; b < nb; ++b) a += h[3 * (size_t)b] + h[3 * (size_t)b + 1];
     *out = a;
     return FLUPS_OK;
 }
