@@ -619,8 +619,13 @@ __device__ __forceinline__ void xdct4_row_tile(typename cplx<T>::t* __restrict__
                 b = xv.y;
             } else {
                 const C* in = S + (size_t)row * g.ldS;
-                a = (double)in[2 * n].x;
-                b = (double)in[2 * n + 1].x;
+                if (g.xpack) {   // X_k is the k-th real of the row
+                    a = (double)reinterpret_cast<const T*>(in)[2 * n];
+                    b = (double)reinterpret_cast<const T*>(in)[2 * n + 1];
+                } else {
+                    a = (double)in[2 * n].x;
+                    b = (double)in[2 * n + 1].x;
+                }
             }
         }
         // x_{2n} is u_n's real part (cosine kind) and x_{2n+1} = x_{nx-1-2m} for m = M-1-n its
@@ -647,8 +652,13 @@ __device__ __forceinline__ void xdct4_row_tile(typename cplx<T>::t* __restrict__
         const T xe = yr, xo = SINE ? yi : -yi;           // X_{2k}, X_{nx-1-2k} (sine: times (-1)^index)
         if (!inv) {
             C* out = S + (size_t)row * g.ldS;
-            out[2 * k] = mk<T>(xe, (T)0);
-            out[nx - 1 - 2 * k] = mk<T>(xo, (T)0);
+            if (g.xpack) {
+                reinterpret_cast<T*>(out)[2 * k] = xe;
+                reinterpret_cast<T*>(out)[nx - 1 - 2 * k] = xo;
+            } else {
+                out[2 * k] = mk<T>(xe, (T)0);
+                out[nx - 1 - 2 * k] = mk<T>(xo, (T)0);
+            }
         } else {
             double* dst = pout + (size_t)row * nx;
             double ve = to_double<T>(xe), vo = to_double<T>(xo);
@@ -700,11 +710,15 @@ __global__ void __launch_bounds__(512) k_xdct(typename cplx<T>::t* __restrict__ 
             const C w = __ldg(&twr[k]);
             const T tx = w.x * bxx - w.y * byy, ty = w.x * byy + w.y * bxx;
             C* out = S + (size_t)row * g.ldS;
+            auto put = [&](int idx, T v) {           // X_idx: (X, 0), or the idx-th real when packed
+                if (g.xpack) reinterpret_cast<T*>(out)[idx] = v;
+                else out[idx] = mk<T>(v, (T)0);
+            };
             auto emit = [&](int kk, T vx, T vy) {   // X_kk and X_{nx-kk} from V_kk
                 const C q = __ldg(&twq[kk]);
                 const T re = q.x * vx - q.y * vy, im = q.x * vy + q.y * vx;
-                out[KIND == 2 ? nx - 1 - kk : kk] = mk<T>(re, (T)0);
-                if (kk != 0 && kk != M) out[KIND == 2 ? kk - 1 : nx - kk] = mk<T>(-im, (T)0);
+                put(KIND == 2 ? nx - 1 - kk : kk, re);
+                if (kk != 0 && kk != M) put(KIND == 2 ? kk - 1 : nx - kk, -im);
             };
             emit(k, ax + tx, ay + ty);                         // V_k
             if (k != M - k) emit(M - k, ax - tx, ty - ay);     // V_{M-k} (k = 0: V_M)
@@ -717,7 +731,10 @@ __global__ void __launch_bounds__(512) k_xdct(typename cplx<T>::t* __restrict__ 
         C xk = mk<T>((T)0, (T)0), xm = xk;
         if (row < nrows) {
             const C* in = S + (size_t)row * g.ldS;
-            auto X = [&](int j) -> T { return in[KIND == 2 ? nx - 1 - j : j].x; };
+            auto X = [&](int j) -> T {
+                const int jj = KIND == 2 ? nx - 1 - j : j;
+                return g.xpack ? reinterpret_cast<const T*>(in)[jj] : in[jj].x;
+            };
             auto vk = [&](int kk) -> C {                       // conj(q_kk) (X_kk - i X_{nx-kk})
                 const T a = X(kk), b = kk == 0 ? (T)0 : X(nx - kk);
                 const C q = __ldg(&twq[kk]);
@@ -1230,6 +1247,83 @@ __global__ void __launch_bounds__(128) k_ztri(typename cplx<T>::t* __restrict__ 
     }
 }
 
+// Thomas along z for the packed all-real spectrum (Geo::xpack): complex column (m, ky) holds the
+// real x modes 2m (real part) and 2m+1 (imaginary part), two real systems with the eigenvalues
+// lam_x[2m] + lam_y[ky] and lam_x[2m+1] + lam_y[ky]; the real part of column 0 is the singular
+// (0, 0) mode when no end is Dirichlet (mean of F removed, row 0 dropped, P_0 = 0, zero-mean shift).
+template <typename T>
+__global__ void __launch_bounds__(128) k_ztri_packed(typename cplx<T>::t* __restrict__ S, T* __restrict__ cps,
+                                                     Geo g, const T* __restrict__ lamx, const T* __restrict__ lamy,
+                                                     const T* __restrict__ tri) {
+    typedef typename cplx<T>::t C;
+    const int ncols = g.nxh * g.ny;
+    const int col = blockIdx.x * blockDim.x + threadIdx.x;
+    if (col >= ncols) return;
+    const int ky = col / g.nxh, m = col - ky * g.nxh;
+    const int nz = g.nz;
+    const T* ta = tri;
+    const T* tb = tri + nz;
+    const T* tc = tri + 2 * nz;
+    const size_t zs = (size_t)g.ny * g.ldS;
+    C* x = S + (size_t)ky * g.ldS + m;
+    T* cp = cps + 2 * (size_t)col;
+    const size_t cs = 2 * (size_t)ncols;
+    const bool sing = (col == 0) && g.sing00;
+    const T la = __ldg(&lamx[2 * m]) + __ldg(&lamy[ky]), lb = __ldg(&lamx[2 * m + 1]) + __ldg(&lamy[ky]);
+    const int k0a = sing ? 1 : 0;
+    T fmean = (T)0;
+    if (sing) {
+        double sw = 0.0, sx0 = 0.0;
+        for (int k = 0; k < nz; ++k) {
+            const double w = g.dzf[k];
+            sw += w;
+            sx0 += w * (double)x[k * zs].x;
+        }
+        fmean = (T)(sx0 / sw);
+    }
+    T ca = (T)0, cb = (T)0, da = (T)0, db = (T)0;
+    for (int k = 0; k < nz; ++k) {
+        const C F = x[k * zs];
+        const T tbk = __ldg(&tb[k]), tck = __ldg(&tc[k]);
+        {
+            const T a_ = k > 0 ? __ldg(&ta[k]) : (T)0;
+            const T inv = (T)1 / ((tbk + lb) - a_ * cb);
+            cb = tck * inv;
+            db = (F.y - a_ * db) * inv;
+        }
+        if (k >= k0a) {
+            const T a_ = k > k0a ? __ldg(&ta[k]) : (T)0;
+            const T inv = (T)1 / ((tbk + la) - a_ * ca);
+            ca = tck * inv;
+            da = ((F.x - fmean) - a_ * da) * inv;
+        }
+        cp[k * cs] = ca;
+        cp[k * cs + 1] = cb;
+        x[k * zs] = mk<T>(da, db);
+    }
+    T xa = da, xb = db, sxa = (T)0;
+    if (sing) sxa = (T)g.dzf[nz - 1] * xa;
+    for (int k = nz - 2; k >= 0; --k) {
+        const C d = x[k * zs];
+        xb = d.y - cp[k * cs + 1] * xb;
+        if (k >= k0a) {
+            xa = d.x - cp[k * cs] * xa;
+            if (sing) sxa += (T)g.dzf[k] * xa;
+        }
+        x[k * zs] = mk<T>(k >= k0a ? xa : (T)0, xb);
+    }
+    if (sing) {
+        T sw = (T)0;
+        for (int k = 0; k < nz; ++k) sw += (T)g.dzf[k];
+        const T mx = sxa / sw;
+        for (int k = 0; k < nz; ++k) {
+            C v = x[k * zs];
+            v.x -= mx;
+            x[k * zs] = v;
+        }
+    }
+}
+
 // Deterministic final reduction of the per-block partial sums in one launch: block g of G sums
 // a contiguous chunk of the partials into fin[3 g + q]; the last block to finish (atomic
 // ticket) adds the G chunk sums in a fixed order and derives the scalars.  The ticket is reset
@@ -1440,8 +1534,12 @@ void run_zsolve(flups_plan P, typename cplx<T>::t* S, const Geo& g, bool tail_co
     } else {
         const int ncols = g.nxh * g.ny;
         flups_prof_begin(P, sizeof(T) == 4 ? FK_ZTRI32 : FK_ZTRI64);
-        k_ztri<T><<<(ncols + 127) / 128, 128, 0, P->stream>>>(S, (T*)P->zscr, g, (const T*)P->lamx,
-                                                                (const T*)P->lamy, (const T*)P->tri);
+        if (g.xpack)
+            k_ztri_packed<T><<<(ncols + 127) / 128, 128, 0, P->stream>>>(S, (T*)P->zscr, g, (const T*)P->lamx,
+                                                                       (const T*)P->lamy, (const T*)P->tri);
+        else
+            k_ztri<T><<<(ncols + 127) / 128, 128, 0, P->stream>>>(S, (T*)P->zscr, g, (const T*)P->lamx,
+                                                                    (const T*)P->lamy, (const T*)P->tri);
         flups_prof_end(P);
         FLUPS_COUNT(P, 1);
     }
@@ -1628,9 +1726,9 @@ void r2r_forward(flups_plan P, const double* f, const Geo& g, Geo& gc, int& ncol
     ncols = P->M + 1;
     if (rx) {
         run_xdct<T, false, 0>(P, f, nullptr, g);
-        gc.M = P->nx;
-        gc.nxh = P->nx;
-        ncols = P->nx;
+        ncols = g.xpack ? P->nx / 2 : P->nx;   // two real x modes per column when packed
+        gc.M = ncols;
+        gc.nxh = ncols;
     } else {
         run_xfwd<T, 0, false>(P, f, nullptr, g);
     }

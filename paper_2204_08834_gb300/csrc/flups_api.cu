@@ -269,6 +269,7 @@ Geo plan_geo(flups_plan P) {
     g.nx = P->nx; g.ny = P->ny; g.nz = P->nz; g.M = P->M; g.nxh = P->nxh; g.ldS = P->ldS;
     g.walls = P->bc == FLUPS_BC_WALLS;
     g.iso = P->uniform_h;
+    g.xpack = P->xpack;
     g.sing00 = (P->bcx == FLUPS_XY_PERIODIC || P->bcx == FLUPS_XY_NEUMANN) &&
                (P->bcy == FLUPS_XY_PERIODIC || P->bcy == FLUPS_XY_NEUMANN);
     g.dx = P->dx; g.dy = P->dy;
@@ -355,6 +356,8 @@ flups_status flups_plan_create_bc(flups_plan* out, int nx, int ny, int nz, doubl
     P->bcx = bcx;
     P->bcy = bcy;
     P->Wx = bcx == FLUPS_XY_PERIODIC ? P->nxh : nx;
+    // all-real spectrum (ends in x and y, walls in z): two real x modes per complex column
+    P->xpack = bcx != FLUPS_XY_PERIODIC && bcy != FLUPS_XY_PERIODIC && bc == FLUPS_BC_WALLS;
     const int csize = prec == FLUPS_FP64 ? 16 : 8;
     const int align = 128 / csize;
     P->ldS = (P->Wx + align - 1) / align * align;

@@ -65,6 +65,8 @@ struct DevScalars {
 struct Geo {
     int nx, ny, nz, M, nxh, ldS, walls, iso;   // iso: dx == dy == every dzf
     int sing00;                  // the (kx, ky) = (0, 0) z column is singular (no Dirichlet end in x, y)
+    int xpack;                   // x coefficients real and packed two per complex column: X_k is the k-th
+                                 // real of the spectrum row (ends in x and y, z walls)
     double dx, dy;
     double idx, idy;             // 1/dx, 1/dy
     double sx, sy;               // 1/dx^2, 1/dy^2
@@ -91,6 +93,7 @@ struct flups_plan_s {
     int nx, ny, nz, bc, prec, dev;
     int bcx, bcy;                // flups_xy_bc of the x and y ends (FLUPS_XY_PERIODIC unless created with ends)
     int Wx;                      // spectral columns along x: nx/2+1 (periodic x) or nx (Neumann/Dirichlet x)
+    int xpack;                   // see Geo::xpack
     double dx, dy;
     cudaStream_t stream;
     int M, nxh, ldS;
