@@ -113,3 +113,18 @@ def test_null_handles_are_rejected(lib):
     assert lib.flups_pnet_launch_count(None) == 0
     assert lib.flups_pnet_kernel_name(99).decode() == "unknown"
     assert lib.flups_selftest_wait_timeout(None, 0) == flups.EINVAL
+
+
+def test_plan_with_ends_rejects_bad_ends(lib):
+    h = ctypes.c_void_p()
+    dz = np.full(16, 0.1)
+    for bcx, bcy in ((5, 0), (0, -1), (9, 9)):
+        st = lib.flups_plan_create_bc(ctypes.byref(h), 16, 16, 16, 0.1, 0.1,
+                                      dz.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), bcx, bcy, 0, 1, None)
+        assert st == flups.EINVAL
+        assert not h.value
+
+
+def test_momentum_predict_rejects_null_plan(lib):
+    assert lib.flups_momentum_predict(None, None, None, None, None, None, None, None, 0.01, 0.0, 0.0, 0.0,
+                                      1e-3, 0.0, 0) == flups.EINVAL
