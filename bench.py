@@ -158,6 +158,24 @@ class ClockSampler:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
+def max_over_ranks(values):
+    """Element-wise maximum over the ranks of the default process group (the slowest replica
+    sets the job time); the identity without a group or with one rank."""
+    import torch
+    dist = torch.distributed
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return [float(v) for v in values]
+    device = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t.cpu()]
+
+
+def job_mpts(world, npts, ms):
+    """Whole-job throughput of `world` replicas, each processing npts points in ms (weak scaling)."""
+    return world * npts / (ms * 1e-3) / 1e6
+
+
 def run_ours(args, rank, world, dev):
     import torch
 
@@ -242,10 +260,7 @@ def run_ours(args, rank, world, dev):
     # max over ranks of the timed sum
     t32 = res["fp32_refine"][0]["step"]
     t64 = res["fp64"][0]["step"]
-    if world > 1:
-        tt = torch.tensor([t32, t64], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t32, t64 = float(tt[0]), float(tt[1])
+    t32, t64 = max_over_ranks([t32, t64])
 
     out = {"c": c, "npts": npts, "res": res, "t32": t32, "t64": t64, "clocks": clk.summary(), "prof": prof}
     if not args.no_cufft and c.bc == "periodic":
@@ -283,10 +298,7 @@ def run_ours(args, rank, world, dev):
                 t1 = time.perf_counter()
                 if s >= 1:
                     t_e2e += t1 - t0
-        if world > 1:
-            tt = torch.tensor([t_e2e], dtype=torch.float64, device="cuda")
-            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-            t_e2e = float(tt[0])
+        t_e2e = max_over_ranks([t_e2e])[0]
         out["e2e"] = (t_e2e, e2e_steps)
     return out
 
@@ -741,7 +753,7 @@ def main():
     tot64, it64, rel64, l64, k64 = res["fp64"]
     ms32 = out["t32"] / k32
     ms64 = out["t64"] / k64
-    value = world * npts / (ms32 * 1e-3) / 1e6
+    value = job_mpts(world, npts, ms32)
     pk, pk_kind = peaks()
     prof = out["prof"]
     tot_prof = sum(ms for ms, n in prof.values()) or 1.0
