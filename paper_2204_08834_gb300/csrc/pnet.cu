@@ -24,7 +24,7 @@
 // Padding columns/rows are zero.
 //
 // On grids with nx a multiple of 128 the convolutions run on the 5th-generation tensor cores
-// instead (k_pnet_conv_tc): each MMA computes 128 consecutive x-points x 16 output channels
+// instead (k_pnet_conv_tcz): each MMA computes 128 consecutive x-points x 16 output channels
 // with K = 16 input channels of one tap (tcgen05.mma kind::f16, bf16 operands from shared
 // memory, FP32 accumulator in tensor memory); the 27 taps accumulate into the same tensor-memory
 // columns.  The A operand is read straight out of the halo tile with one descriptor per tap:
@@ -257,13 +257,6 @@ __global__ void __launch_bounds__(THREADS, 2) k_pnet_conv(ConvArgs a) {
 }
 
 // ------------------------------------------------------------ tcgen05 convolution
-constexpr int TC_TY = 2, TC_TZ = 2, TC_HX = 130, TC_HY = TC_TY + 2, TC_HZ = TC_TZ + 2;
-constexpr int TC_NP = TC_HX * TC_HY * TC_HZ;            // 2080 halo points
-constexpr int TC_HALF = TC_NP * 16;                     // one 8-channel plane of the halo tile (bytes)
-constexpr int TC_ROWS = TC_TY * TC_TZ;                  // MMA tiles (rows of 128 x-points) per CTA
-constexpr int TC_SMEM = 2 * TC_HALF + 27 * 512 + 16;    // halo + weights + mbarrier + TMEM slot
-constexpr int TC_TMEM_COLS = 64;                        // 16 FP32 columns per row tile
-
 // Shared-memory matrix descriptor (no swizzle, K-major): start address, leading byte offset
 // (step between the two K halves), stride byte offset (step between 8-row core matrices).
 __device__ __forceinline__ unsigned long long tc_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
@@ -296,151 +289,6 @@ __device__ __forceinline__ float tc_ld1(uint32_t taddr) {
     asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];" : "=r"(r) : "r"(taddr));
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
     return __uint_as_float(r);
-}
-
-// Same epilogues as k_pnet_conv (EPI 0 hidden, 1 inference output, 2 training output,
-// 3 masked gradient).  A CTA of 256 threads computes 2 (y) x 2 (z) rows of 128 x-points; lane l of
-// warp w owns x-point 32 (w % 4) + l (tensor-memory lane 32 (w % 4) + l) of the rows r with
-// r % 2 == w / 4.
-constexpr int TC_THREADS = 256;
-template <int EPI>
-__global__ void __launch_bounds__(TC_THREADS, 2) k_pnet_conv_tc(ConvArgs a) {
-    extern __shared__ __align__(1024) unsigned char sm[];
-    unsigned char* shalo = sm;
-    unsigned char* sw = sm + 2 * TC_HALF;
-    unsigned long long* mbar = reinterpret_cast<unsigned long long*>(sw + 27 * 512);
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(sw + 27 * 512 + 8);
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int tnx = a.nx / 128, tny = a.ny / TC_TY;
-    const int b = blockIdx.x;
-    const int x0 = (b % tnx) * 128, y0 = ((b / tnx) % tny) * TC_TY, z0 = (b / (tnx * tny)) * TC_TZ;
-    if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
-                     "r"(TC_TMEM_COLS) : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-    }
-    if (tid == 0) asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(mbar)), "r"(1) : "memory");
-    {
-        // halo tile: loads issued in batches of 8 per thread before the shared-memory stores
-        const uint4* src = reinterpret_cast<const uint4*>(a.in);
-        constexpr int NC = TC_NP * 2, BT = 8;
-        for (int c0 = tid; c0 < NC; c0 += TC_THREADS * BT) {
-            uint4 v[BT];
-            uint32_t dst[BT];
-#pragma unroll
-            for (int q = 0; q < BT; ++q) {
-                const int c = c0 + q * TC_THREADS;
-                if (c < NC) {
-                    const int pp = c >> 1, h = c & 1;
-                    const int xx = pp % TC_HX, t = pp / TC_HX;
-                    const int yy = t % TC_HY, zz = t / TC_HY;
-                    const int gx = wrapc(x0 + xx - 1, a.nx), gy = wrapc(y0 + yy - 1, a.ny), gz = wrapc(z0 + zz - 1, a.nz);
-                    const long long pt = ((long long)gz * a.ny + gy) * a.nx + gx;
-                    v[q] = __ldg(src + pt * 2 + h);
-                    dst[q] = (uint32_t)(h * TC_HALF + pp * 16);
-                }
-            }
-#pragma unroll
-            for (int q = 0; q < BT; ++q)
-                if (c0 + q * TC_THREADS < NC) *reinterpret_cast<uint4*>(shalo + dst[q]) = v[q];
-        }
-        const uint4* wsrc = reinterpret_cast<const uint4*>(a.wtc);
-        for (int c = tid; c < 27 * 32; c += TC_THREADS) reinterpret_cast<uint4*>(sw)[c] = __ldg(wsrc + c);
-    }
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    const uint32_t tmem = *tslot;
-    if (tid == 0) {
-        const uint32_t hb = smem_u32(shalo), wb = smem_u32(sw);
-        for (int r = 0; r < TC_ROWS; ++r) {
-            const int zl = r / TC_TY, yl = r - zl * TC_TY;
-            for (int tap = 0; tap < 27; ++tap) {
-                const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
-                const uint32_t aaddr = hb + (uint32_t)((((zl + dz + 1) * TC_HY + (yl + dy + 1)) * TC_HX + dx + 1) * 16);
-                const unsigned long long ad = tc_desc(aaddr, TC_HALF, 128);
-                const unsigned long long bd = tc_desc(wb + tap * 512, 256, 128);
-                asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                             " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
-                             ::"r"(tmem + 16 * r), "l"(ad), "l"(bd), "r"(TC_IDESC), "r"(tap) : "memory");
-            }
-        }
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(mbar))
-                     : "memory");
-    }
-    bool done = false;
-    for (int i = 0; i < (1 << 22) && !done; ++i) done = tc_mbar_try(smem_u32(mbar), 0);
-    const bool ok = __syncthreads_and(done);
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    double sq = 0.0;
-    if (ok) {
-        const int wq = warp & 3;                 // lane quadrant of tensor memory this warp may read
-        const uint32_t tl = tmem + ((uint32_t)(32 * wq) << 16);
-        const int x = x0 + 32 * wq + lane;
-        float bias[16];
-        if (EPI == 0) {
-#pragma unroll
-            for (int n = 0; n < 16; ++n) bias[n] = __ldg(a.bias + n);
-        }
-        for (int r = warp >> 2; r < TC_ROWS; r += 2) {
-            const int zl = r / TC_TY, yl = r - zl * TC_TY;
-            const long long pt = ((long long)(z0 + zl) * a.ny + (y0 + yl)) * a.nx + x;
-            if (EPI == 0 || EPI == 3) {
-                float v[16];
-                tc_ld16(tl + 16 * r, v);
-                if (EPI == 0) {
-#pragma unroll
-                    for (int n = 0; n < 16; ++n) v[n] = fmaxf(v[n] + bias[n], 0.0f);
-                } else {
-                    const uint4* mk4 = reinterpret_cast<const uint4*>(a.mask + pt * 16);
-                    const uint4 m0 = __ldg(mk4), m1 = __ldg(mk4 + 1);
-                    const uint32_t mw[8] = {m0.x, m0.y, m0.z, m0.w, m1.x, m1.y, m1.z, m1.w};
-#pragma unroll
-                    for (int q = 0; q < 8; ++q) {
-                        if (!(mw[q] & 0x7fffu)) v[2 * q] = 0.0f;
-                        if (!(mw[q] & 0x7fff0000u)) v[2 * q + 1] = 0.0f;
-                    }
-                }
-                uint32_t o[8];
-#pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    __nv_bfloat162 h2 = __floats2bfloat162_rn(v[2 * q], v[2 * q + 1]);
-                    o[q] = *reinterpret_cast<uint32_t*>(&h2);
-                }
-                uint4* dst = reinterpret_cast<uint4*>(a.out + pt * 16);
-                dst[0] = make_uint4(o[0], o[1], o[2], o[3]);
-                dst[1] = make_uint4(o[4], o[5], o[6], o[7]);
-            } else {
-                const double y = (double)(tc_ld1(tl + 16 * r) + __ldg(a.bias));
-                const double pn = a.pn[pt], pm = a.pnm1[pt];
-                if (EPI == 1) {
-                    a.phat[pt] = 2.0 * pn - pm + a.sc[0] * y;
-                } else {
-                    const double e = y - (a.pnext[pt] - (2.0 * pn - pm)) * a.sc[1];
-                    sq += e * e;
-                    a.out[pt * 16] = __double2bfloat16(a.gscale * e);
-                }
-            }
-        }
-    } else if (tid == 0) {
-        atomicExch(a.err, 1);
-    }
-    if (EPI == 2) {
-        __shared__ double ws[TC_THREADS / 32];
-        for (int s2 = 16; s2 > 0; s2 >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, s2);
-        if (lane == 0) ws[warp] = sq;
-        __syncthreads();
-        if (tid == 0) {
-            double t = 0.0;
-            for (int w = 0; w < TC_THREADS / 32; ++w) t += ws[w];
-            a.red[blockIdx.x] = t;
-        }
-    }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    if (warp == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_TMEM_COLS) : "memory");
 }
 
 // tcgen05 convolution marching in z.  A CTA owns a column of 4 (y) x 128 (x) points through ZC
@@ -900,10 +748,6 @@ cudaError_t set_smem_attrs() {
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_pnet_conv_tcz<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, TZ_SMEM);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_pnet_conv_tcz<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, TZ_SMEM);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_pnet_conv_tcz<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, TZ_SMEM);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_pnet_conv_tc<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_pnet_conv_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_pnet_conv_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_pnet_conv_tc<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
     if (e == cudaSuccess) done = dev;
     return e;
 }
