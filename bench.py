@@ -53,6 +53,8 @@ KERNEL_WORK = {
     # FP32 half spectrum.  On one-spacing grids the defect is an exact fixed-point sum, so
     # few FP64 flops remain and the kernel is held to its compulsory bytes.
     "k_xfwd_residual32": {"bound": "hbm", "bytes": 8 + 8 + 4},
+    # the stopping test of the graph-capturable solve: the same defect, norm only
+    "k_xres_norm32": {"bound": "hbm", "bytes": 8 + 8},
     "k_xfwd_f32": {"bound": "hbm", "bytes": 8 + 4},
     "k_ycol32": {"bound": "hbm", "bytes": 4 + 4},
     "k_zper32": {"bound": "hbm", "bytes": 4 + 4},

@@ -130,7 +130,7 @@ unsigned long long flups_launch_count(flups_plan plan);
  * total milliseconds ms[k] and the number of timed regions n[k] (HOST arrays) recorded
  * since the previous read.  flups_kernel_name(k) names kernel id k (static string).
  */
-#define FLUPS_NKERNELS 21
+#define FLUPS_NKERNELS 22
 flups_status flups_set_profiling(flups_plan plan, int on);
 flups_status flups_profile_read(flups_plan plan, double* ms, long long* n);
 const char*  flups_kernel_name(int id);

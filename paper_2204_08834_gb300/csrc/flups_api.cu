@@ -245,7 +245,7 @@ flups_status sync_scalars(flups_plan P) {
 static const char* kKernelNames[FK_COUNT] = {
     "k_rho_tiles", "k_face_coeffs", "k_rhs", "k_correct", "k_xfwd_f32", "k_xfwd_residual32", "k_ycol32",
     "k_zper32", "k_ztri32", "k_xinv32", "k_finalize", "k_xfwd64", "k_ycol64", "k_zper64", "k_ztri64", "k_xinv64",
-    "k_res64", "k_rho_finalize", "k_mom_umax", "k_momentum", "k_res_ends"};
+    "k_res64", "k_rho_finalize", "k_mom_umax", "k_momentum", "k_res_ends", "k_xres_norm32"};
 
 void flups_prof_begin(flups_plan P, int kid) {
     P->prof_open = 0;

@@ -86,7 +86,7 @@ struct Geo {
 enum FlupsKernelId {
     FK_RHO_MINMAX = 0, FK_FACE_COEFFS, FK_RHS, FK_CORRECT, FK_XFWD_F32, FK_XFWD_RES32, FK_YCOL32, FK_ZPER32,
     FK_ZTRI32, FK_XINV32, FK_FINALIZE, FK_XFWD64, FK_YCOL64, FK_ZPER64, FK_ZTRI64, FK_XINV64, FK_RES64,
-    FK_TILE_FLAGS, FK_MOM_UMAX, FK_MOMENTUM, FK_RES_ENDS, FK_COUNT
+    FK_TILE_FLAGS, FK_MOM_UMAX, FK_MOMENTUM, FK_RES_ENDS, FK_XRES_NORM32, FK_COUNT
 };
 
 struct flups_plan_s {

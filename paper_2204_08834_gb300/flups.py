@@ -36,7 +36,7 @@ SYMBOLS = [
 ]
 PNET_NKERNELS = 6
 PNET_NPARAMS = 15601
-NKERNELS = 21
+NKERNELS = 22
 MOM_PAIR = 0
 MOM_FP64 = 1
 
