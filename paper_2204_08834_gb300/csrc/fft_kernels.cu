@@ -2018,9 +2018,10 @@ cudaError_t launch_solve32_fixed(flups_plan P, const double* f, double* p, doubl
     // is the fused defect + transform.  From the second solve on the defect has usually reached
     // rtol: its norm is taken alone first, and the fused pass (skipped once converged) runs only
     // when another solve follows.
-    // (One-spacing grids, where the exact fixed-point defect has a norm-only form; other grids
-    // take the fused pass every time.)
-    const bool norm_first = P->uniform_h;
+    // (One-spacing grids of 2^24 points or more, where the exact fixed-point defect has a
+    // norm-only form and the saved transform outweighs one more launch; other grids take the
+    // fused pass every time.)
+    const bool norm_first = P->uniform_h && P->npts >= ((size_t)1 << 24);
     for (int it = 1; it <= max_iter; ++it) {
         const bool last = it == max_iter;
         if (norm_first && (it >= 2 || last)) {
