@@ -65,7 +65,7 @@ KERNEL_WORK = {
     # constant-density tiles: rhs reads u, v, w and writes f; correct reads p and u, v, w and
     # writes u, v, w (p_n, p_{n-1} and the face coefficients only where the density varies)
     "k_rhs": {"bound": "hbm", "bytes": 32},
-    "k_correct": {"bound": "hbm", "bytes": 56},
+    "k_correct": {"bound": "hbm", "bytes": 56, "fp64_instr": 6},   # 3 differences + 3 FMAs per cell
     # momentum predictor (AB2 call): reads u, v, w (FP64) and the M state (3 x 8 B), writes
     # u**, v**, w** and the state; the pre-pass reads u, v, w for max|u|
     "k_momentum": {"bound": "hbm", "bytes": 24 + 24 + 24 + 24},
@@ -75,11 +75,14 @@ KERNEL_WORK = {
 }
 
 
-# DRAM bytes per point of one launch from an ncu capture (dram__bytes_read.sum +
-# dram__bytes_write.sum) of the 256^3 emulsion, scaled to any size by the point count.
-# Only valid for the kernel code that was captured; remove the entry when the kernel changes.
-MEASURED_TRAFFIC_PER_POINT = {
-    "k_xfwd_residual32": (271.068 + 52.295) * 1e6 / 256 ** 3,
+# DRAM bytes of one launch (dram__bytes_read.sum + dram__bytes_write.sum) from an ncu capture
+# of the named workload and kernel.  Only valid for the kernel code that was captured: remove
+# the entry when the kernel changes.
+MEASURED_TRAFFIC_PER_LAUNCH = {
+    # emulsion 512^3, the bench step's third k_correct launch: 5.03 GB read + 3.18 GB written
+    # (61.2 B/point; constant-density tiles take 56 B/point, the 11.2 % of tiles with density
+    # variation 40 B/point more: 60.5 B/point)
+    ("emulsion512", "k_correct"): (5.03 + 3.18) * 1e9,
 }
 
 
@@ -254,7 +257,8 @@ def run_ours(args, rank, world, dev):
                 res[prec] = timed_steps(plan, steps, args.warmup, args.rtol) + (steps,)
                 if prec == "fp32_refine":
                     # two more steps with per-kernel CUDA events inside the library (host-driven
-                    # solve: every launched kernel does its full work, so the per-launch times hold)
+                    # solve: the kernel sequence of the graph-capturable one without the launches
+                    # that return at once after convergence, so the per-launch times hold)
                     plan.set_profiling(True)
                     timed_steps(plan, 2, 0, args.rtol, graphable=False)
                     prof = {k: (ms / 2.0, n / 2.0) for k, (ms, n) in plan.profile().items()}
@@ -825,10 +829,9 @@ def main():
             "peak": peak,
             "unit": unit,
             "frac": round(achieved / peak, 4),
-            "traffic": (round(MEASURED_TRAFFIC_PER_POINT[dom] * npts) if dom in MEASURED_TRAFFIC_PER_POINT
-                        else None),
-            "traffic_note": ("bytes per launch: ncu DRAM read + write of the 256^3 capture scaled by points"
-                             if dom in MEASURED_TRAFFIC_PER_POINT else None),
+            "traffic": MEASURED_TRAFFIC_PER_LAUNCH.get((args.workload, dom)),
+            "traffic_note": ("bytes per launch: ncu DRAM read + write of this workload's launch"
+                             if (args.workload, dom) in MEASURED_TRAFFIC_PER_LAUNCH else None),
             "per_launch_ms": round(dom_ms_per_region, 4),
             "peak_source": psrc,
             "algorithmic": {k: v for k, v in work.items() if k != "bound"},
@@ -839,6 +842,13 @@ def main():
         "gpu_launches": int(l32),
         "clocks": out["clocks"],
     }
+    if work.get("fp64_instr"):
+        # the kernel's other ceiling: its FP64 instructions at the measured FP64 pipe rate
+        floor_ms = work["fp64_instr"] * npts / (FP64_TFLOPS_MEASURED / 2.0 * 1e12) * 1e3
+        line["roofline"]["fp64_pipe"] = {"instr_per_point": work["fp64_instr"], "floor_ms": round(floor_ms, 4),
+                                         "frac": round(floor_ms / dom_ms_per_region, 4),
+                                         "rate": "FP64 pipe instructions at the DFMA rate measured by "
+                                                 "microbench/peaks.cu"}
     if "e2e" in out:
         t_e2e, ne = out["e2e"]
         line["e2e"] = {"value": round(world * npts * ne / t_e2e / 1e6, 2), "unit": "Mpts/s",

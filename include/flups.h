@@ -208,7 +208,10 @@ flups_status flups_correct(flups_plan plan, const double* p, const double* p_n,
  * flups_project_host - one whole projection with HOST buffers (end-to-end form):
  * copies u, v, w, rho, p_n, p_nm1 to plan-owned device buffers, runs set_density(rho,
  * rho0 = min), rhs, solve and correct, and copies u, v, w (in place) and p back.
- * Host buffers should be page-locked for full copy bandwidth.  Synchronises.
+ * The inputs travel on a plan-owned copy stream, rho first, so the density pass overlaps
+ * the other copies; p travels back on it while the correction runs.  Host buffers should
+ * be page-locked for full copy bandwidth.  Synchronises both streams before returning
+ * (also on error), so no copy touches the caller's buffers afterwards.
  */
 flups_status flups_project_host(flups_plan plan, double* u, double* v, double* w,
                                 const double* rho, const double* p_n, const double* p_nm1,

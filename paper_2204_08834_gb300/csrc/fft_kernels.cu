@@ -217,6 +217,33 @@ __device__ __forceinline__ long long fixq(double x, int sh) {
     return ((long long)v ^ sg) - sg;
 }
 
+// As fixq at the scale x * 2^(1075 - sh), but for values up to 2^61 (three bits of left
+// shift past fixq's range); ok = false (value unusable) at or beyond 2^61 and for infinities
+// and NaNs.  Integer operations only.
+__device__ __forceinline__ long long fixw(double x, int sh, bool& ok) {
+    const long long b = __double_as_longlong(x);
+    const int e = (int)((b >> 52) & 0x7FF);
+    unsigned long long m = ((unsigned long long)(b & 0xFFFFFFFFFFFFFLL) | 0x10000000000000ULL) << 5;
+    m = e == 0 ? 0ull : m;                  // |value| = m 2^l, m < 2^58
+    const int l = e - sh - 5;
+    ok = e == 0 || l <= 3;
+    const unsigned r = l < 0 ? (unsigned)(l < -64 ? 64 : -l) : 0u;
+    const unsigned q = l > 0 ? (unsigned)(l > 3 ? 3 : l) : 0u;
+    unsigned long long v;
+    asm("shr.b64 %0, %1, %2;" : "=l"(v) : "l"(m), "r"(r));
+    asm("shl.b64 %0, %1, %2;" : "=l"(v) : "l"(v), "r"(q));
+    const long long sg = b >> 63;
+    return ((long long)v ^ sg) - sg;
+}
+
+// |D| < 2^63 to binary32 from two 32-bit halves of |D| (at most two roundings, within 2^-23
+// relative), with integer-to-float conversions of 32-bit values only.
+__device__ __forceinline__ float i64_to_f32(long long D) {
+    const unsigned long long a = D < 0 ? (unsigned long long)(-D) : (unsigned long long)D;
+    const float m = fmaf(__uint2float_rn((unsigned)(a >> 32)), 4294967296.f, __uint2float_rn((unsigned)a));
+    return D < 0 ? -m : m;
+}
+
 template <typename T> __device__ __forceinline__ T from_double(double x) {
     if constexpr (sizeof(T) == 4) return d2f_bits(x);
     else return x;
@@ -317,6 +344,23 @@ __global__ void __launch_bounds__(512) k_xfwd(const double* __restrict__ f, cons
     // Every thread handles exactly E elements (nthr = B M / E): compile-time trip counts let
     // the loads of a thread be issued before they are used.
     if (MODE >= 2 && xres_tiled(E, B, M, g.ny)) {
+        // On a grid whose spacing is a power of two, h^2 (f - <f>) is taken to the same fixed
+        // point as the 7-point sum S (F, MF: truncated, 2^-58 of the scale of p or finer), so
+        // r = 2^(pexp-1080)/h^2 (F - MF - S) needs no FP64 instruction: the integer difference
+        // is exact and is rounded to binary32 once more than the FP64 form's result is, and the
+        // power-of-two scale is exact.  Points whose F would reach 2^61 take the FP64 form.
+        bool ipath = false;
+        int shf = 0;
+        long long mfq = 0;
+        float rscale = 0.f;
+        if (sizeof(T) == 4 && g.h2e != H2E_NONE && sc->pexp < 2047 && sc->pexp - 57 >= 1) {
+            const int es = sc->pexp - 1080 - g.h2e;
+            shf = sh - g.h2e;
+            bool okm;
+            mfq = fixw(mf, shf, okm);
+            ipath = okm && es >= -126 && es <= 60;
+            if (ipath) rscale = __int_as_float((es + 127) << 23);
+        }
         // B = E rows row0 .. row0+B-1 (consecutive y of one plane), one pair position n = tid
         // per thread.  The rows and their two y-halo rows are converted to fixed point once into
         // shared memory (rows 0 .. B+1 = j0-1 .. j0+B): each value then serves as the centre and
@@ -351,8 +395,18 @@ __global__ void __launch_bounds__(512) k_xfwd(const double* __restrict__ f, cons
             long long s1 = qc.x + qe + qs.y + qn.y - nd * qc.y;
             if (hb) { s0 += fixq(vb.x, sh); s1 += fixq(vb.y, sh); }
             if (ht) { s0 += fixq(vt.x, sh); s1 += fixq(vt.y, sh); }
-            zr[c] = mk<T>(from_double<T>(fma(-cfix, __ll2double_rn(s0), fv.x - mf)),
-                          from_double<T>(fma(-cfix, __ll2double_rn(s1), fv.y - mf)));
+            bool ok0 = false, ok1 = false;
+            long long F0 = 0, F1 = 0;
+            if (ipath) {
+                F0 = fixw(fv.x, shf, ok0);
+                F1 = fixw(fv.y, shf, ok1);
+            }
+            if (ok0 && ok1) {
+                zr[c] = mk<T>((T)(rscale * i64_to_f32(F0 - mfq - s0)), (T)(rscale * i64_to_f32(F1 - mfq - s1)));
+            } else {
+                zr[c] = mk<T>(from_double<T>(fma(-cfix, __ll2double_rn(s0), fv.x - mf)),
+                              from_double<T>(fma(-cfix, __ll2double_rn(s1), fv.y - mf)));
+            }
             acc2 = fmaf((float)zr[c].x, (float)zr[c].x, fmaf((float)zr[c].y, (float)zr[c].y, acc2));
         }
         if (MODE == 2) {
@@ -1937,6 +1991,17 @@ cudaError_t launch_xfwd32_residual(flups_plan P, const double* f, const double* 
     return cudaGetLastError();
 }
 
+cudaError_t launch_xres_norm32(flups_plan P, const double* f, const double* p) {
+    run_xfwd<float, 3, false>(P, f, p, plan_geo(P));
+    return cudaGetLastError();
+}
+
+// Stopping tests after the second FP32 solve take the defect norm alone (the fused defect +
+// transform pass runs only when another solve follows) on one-spacing grids of 2^24 points or
+// more: there the exact fixed-point defect has a norm-only form and the transform it saves
+// outweighs one more launch.  Other grids take the fused pass every time.
+bool xres_norm_first(flups_plan P) { return P->uniform_h && P->npts >= ((size_t)1 << 24); }
+
 cudaError_t launch_finalize_r(flups_plan P) {
     const int nblk = xfwd_blocks(P, 8, 1);
     flups_prof_begin(P, FK_FINALIZE);
@@ -2016,16 +2081,13 @@ cudaError_t launch_solve32_fixed(flups_plan P, const double* f, double* p, doubl
     };
     // After the first FP32 solve the defect is ~1e-7 and always feeds a second solve, so its pass
     // is the fused defect + transform.  From the second solve on the defect has usually reached
-    // rtol: its norm is taken alone first, and the fused pass (skipped once converged) runs only
-    // when another solve follows.
-    // (One-spacing grids of 2^24 points or more, where the exact fixed-point defect has a
-    // norm-only form and the saved transform outweighs one more launch; other grids take the
-    // fused pass every time.)
-    const bool norm_first = P->uniform_h && P->npts >= ((size_t)1 << 24);
+    // rtol: where xres_norm_first holds, its norm is taken alone first, and the fused pass
+    // (skipped once converged) runs only when another solve follows.
+    const bool norm_first = xres_norm_first(P);
     for (int it = 1; it <= max_iter; ++it) {
         const bool last = it == max_iter;
         if (norm_first && (it >= 2 || last)) {
-            run_xfwd<float, 3, false>(P, f, p, plan_geo(P));
+            launch_xres_norm32(P, f, p);
             finalize_r();
             if (last) break;
         }

@@ -269,6 +269,11 @@ Geo plan_geo(flups_plan P) {
     g.nx = P->nx; g.ny = P->ny; g.nz = P->nz; g.M = P->M; g.nxh = P->nxh; g.ldS = P->ldS;
     g.walls = P->bc == FLUPS_BC_WALLS;
     g.iso = P->uniform_h;
+    g.h2e = H2E_NONE;
+    if (P->uniform_h) {                          // h = 2^t exactly: frexp gives 0.5 * 2^(t+1)
+        int ex = 0;
+        if (std::frexp(P->dx, &ex) == 0.5) g.h2e = 2 * (ex - 1);
+    }
     g.xpack = P->xpack;
     g.sing00 = (P->bcx == FLUPS_XY_PERIODIC || P->bcx == FLUPS_XY_NEUMANN) &&
                (P->bcy == FLUPS_XY_PERIODIC || P->bcy == FLUPS_XY_NEUMANN);
@@ -451,6 +456,8 @@ flups_status flups_plan_create_bc(flups_plan* out, int nx, int ny, int nz, doubl
                     (bc == FLUPS_BC_WALLS || make_spec_map(&P->tm_z, P->spec, P->ldS, ny, nz, Bz, 1, nz < 256 ? nz : 256));
     }
     P->hbuf = nullptr;
+    P->cstream = nullptr;
+    for (int q = 0; q < 3; ++q) P->hev[q] = nullptr;
     P->vcbuf = nullptr;
     P->vcs_host = nullptr;
     *out = P;
@@ -469,6 +476,12 @@ flups_status flups_plan_destroy(flups_plan P) {
     }
     std::free(P->allocs);
     if (P->hbuf) cudaFree(P->hbuf);
+    if (P->cstream) {
+        cudaStreamSynchronize(P->cstream);
+        cudaStreamDestroy(P->cstream);
+    }
+    for (int q = 0; q < 3; ++q)
+        if (P->hev[q]) cudaEventDestroy(P->hev[q]);
     if (P->vcbuf) cudaFree(P->vcbuf);
     if (P->vcs_host) cudaFreeHost(P->vcs_host);
     if (P->sc_host) cudaFreeHost(P->sc_host);
@@ -681,9 +694,13 @@ flups_status flups_solve(flups_plan P, const double* f, double* p, double rtol, 
     if (st != FLUPS_OK) return st;
     double rr = -1.0;
     int it = 1;
+    const bool norm_first = xres_norm_first(P);
     for (;; ++it) {
-        // FP64 defect r = f - <f> - L p, fused with the forward x transform of r.
-        st = cuda_status(launch_xfwd32_residual(P, f, p));
+        // FP64 defect r = f - <f> - L p, fused with the forward x transform of r; from the
+        // second solve on (where xres_norm_first holds) its norm alone first, the same kernel
+        // sequence as the graph-capturable solve.
+        const bool alone = norm_first && it >= 2;
+        st = cuda_status(alone ? launch_xres_norm32(P, f, p) : launch_xfwd32_residual(P, f, p));
         if (st == FLUPS_OK) st = cuda_status(launch_finalize_r(P));
         if (st == FLUPS_OK) st = sync_scalars(P);
         if (st != FLUPS_OK) return st;
@@ -698,7 +715,8 @@ flups_status flups_solve(flups_plan P, const double* f, double* p, double rtol, 
         if (rr <= rtol) return FLUPS_OK;
         if (it >= max_iter) return FLUPS_ENOCONV;
         // delta = L^-1 r in FP32, p += delta in FP64.
-        st = cuda_status(launch_yz_solve32(P));
+        if (alone) st = cuda_status(launch_xfwd32_residual(P, f, p));
+        if (st == FLUPS_OK) st = cuda_status(launch_yz_solve32(P));
         if (st == FLUPS_OK) st = cuda_status(launch_xinv32(P, p, it == 1 ? 1 : 2));
         if (st != FLUPS_OK) return st;
     }
@@ -741,6 +759,19 @@ flups_status flups_project_host(flups_plan P, double* u, double* v, double* w, c
     if (!P->hbuf) {
         if (cudaMalloc(&P->hbuf, 8 * b) != cudaSuccess) { cudaGetLastError(); P->hbuf = nullptr; return FLUPS_ENOMEM; }
     }
+    if (!P->cstream) {
+        cudaError_t e = cudaStreamCreateWithFlags(&P->cstream, cudaStreamNonBlocking);
+        for (int q = 0; q < 3 && e == cudaSuccess; ++q) e = cudaEventCreateWithFlags(&P->hev[q], cudaEventDisableTiming);
+        if (e != cudaSuccess) {          // leave nothing half made: the next call starts over
+            for (int q = 0; q < 3; ++q) {
+                if (P->hev[q]) cudaEventDestroy(P->hev[q]);
+                P->hev[q] = nullptr;
+            }
+            if (P->cstream) cudaStreamDestroy(P->cstream);
+            P->cstream = nullptr;
+            return cuda_status(e);
+        }
+    }
     double* du = P->hbuf;
     double* dv = du + n;
     double* dw = dv + n;
@@ -749,25 +780,38 @@ flups_status flups_project_host(flups_plan P, double* u, double* v, double* w, c
     double* dpm = dpn + n;
     double* df = dpm + n;
     double* dp = df + n;
-    cudaStream_t s = P->stream;
-    cudaError_t e = cudaMemcpyAsync(du, u, b, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(dv, v, b, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(dw, w, b, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(dr, rho, b, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(dpn, p_n, b, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess && p_nm1) e = cudaMemcpyAsync(dpm, p_nm1, b, cudaMemcpyHostToDevice, s);
-    if (e != cudaSuccess) return cuda_status(e);
-    flups_status st = flups_set_density(P, dr, 0.0);
+    cudaStream_t s = P->stream, cs = P->cstream;
+    // Inputs go over the copy stream, rho first: the density pass runs on the plan stream
+    // while u, v, w, p_n, p_nm1 are still in flight.
+    cudaError_t e = cudaEventRecord(P->hev[0], s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, P->hev[0], 0);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dr, rho, b, cudaMemcpyHostToDevice, cs);
+    if (e == cudaSuccess) e = cudaEventRecord(P->hev[1], cs);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(du, u, b, cudaMemcpyHostToDevice, cs);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dv, v, b, cudaMemcpyHostToDevice, cs);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dw, w, b, cudaMemcpyHostToDevice, cs);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dpn, p_n, b, cudaMemcpyHostToDevice, cs);
+    if (e == cudaSuccess && p_nm1) e = cudaMemcpyAsync(dpm, p_nm1, b, cudaMemcpyHostToDevice, cs);
+    if (e == cudaSuccess) e = cudaEventRecord(P->hev[2], cs);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, P->hev[1], 0);
+    flups_status st = cuda_status(e);
+    if (st == FLUPS_OK) st = flups_set_density(P, dr, 0.0);
+    if (st == FLUPS_OK) st = cuda_status(cudaStreamWaitEvent(s, P->hev[2], 0));
     if (st == FLUPS_OK) st = flups_rhs(P, du, dv, dw, dpn, p_nm1 ? dpm : nullptr, c1, c2, dt, df);
     if (st == FLUPS_OK) st = flups_solve(P, df, dp, rtol, max_iter, info);
+    // p goes back over the copy stream while the correction runs (both only read p).
+    if (st == FLUPS_OK) st = cuda_status(cudaEventRecord(P->hev[0], s));
+    if (st == FLUPS_OK) st = cuda_status(cudaStreamWaitEvent(cs, P->hev[0], 0));
+    if (st == FLUPS_OK) st = cuda_status(cudaMemcpyAsync(p_out, dp, b, cudaMemcpyDeviceToHost, cs));
     if (st == FLUPS_OK) st = flups_correct(P, dp, dpn, p_nm1 ? dpm : nullptr, c1, c2, dt, du, dv, dw);
+    if (st == FLUPS_OK) st = cuda_status(cudaMemcpyAsync(u, du, b, cudaMemcpyDeviceToHost, s));
+    if (st == FLUPS_OK) st = cuda_status(cudaMemcpyAsync(v, dv, b, cudaMemcpyDeviceToHost, s));
+    if (st == FLUPS_OK) st = cuda_status(cudaMemcpyAsync(w, dw, b, cudaMemcpyDeviceToHost, s));
+    // No copy touches the caller's buffers after return, whatever the outcome.
+    const cudaError_t e1 = cudaStreamSynchronize(cs);
+    const cudaError_t e2 = cudaStreamSynchronize(s);
     if (st != FLUPS_OK) return st;
-    e = cudaMemcpyAsync(u, du, b, cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(v, dv, b, cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(w, dw, b, cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(p_out, dp, b, cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    return cuda_status(e);
+    return cuda_status(e1 != cudaSuccess ? e1 : e2);
 }
 
 }  // extern "C"

@@ -62,9 +62,12 @@ struct DevScalars {
 #define FLUPS_TY 8
 #define FLUPS_KC 16
 
+#define H2E_NONE (-100000)
+
 struct Geo {
     int nx, ny, nz, M, nxh, ldS, walls, iso;   // iso: dx == dy == every dzf
     int sing00;                  // the (kx, ky) = (0, 0) z column is singular (no Dirichlet end in x, y)
+    int h2e;                     // iso with h = 2^t: 2t (h^2 = 2^h2e), else H2E_NONE
     int xpack;                   // x coefficients real and packed two per complex column: X_k is the k-th
                                  // real of the spectrum row (ends in x and y, z walls)
     double dx, dy;
@@ -125,6 +128,8 @@ struct flups_plan_s {
     int density_set;
     // host-buffer (end-to-end) path, allocated on first use
     double* hbuf;                // 8 fields: u v w rho pn pnm1 f p
+    cudaStream_t cstream;        // copies that overlap the plan stream's kernels
+    cudaEvent_t hev[3];          // call start, rho copied, every input copied (then: p ready)
     size_t total_bytes;
     void** allocs;               // every workspace allocation, freed by destroy
     int nallocs;
@@ -174,6 +179,8 @@ cudaError_t launch_add_const(flups_plan P, double* a, double c);
 cudaError_t launch_xfwd32_from_f(flups_plan P, const double* f);            // S = FFTx(f), partial sums of f
 cudaError_t launch_finalize_f(flups_plan P);                                 // mean_f, ||f - mean||^2
 cudaError_t launch_xfwd32_residual(flups_plan P, const double* f, const double* p);  // S = FFTx(r), ||r||^2 partials
+cudaError_t launch_xres_norm32(flups_plan P, const double* f, const double* p);     // ||r||^2 partials only
+bool xres_norm_first(flups_plan P);     // later stopping tests take the norm-only pass first
 cudaError_t launch_finalize_r(flups_plan P);
 cudaError_t launch_yz_solve32(flups_plan P);                                 // y fwd, z solve, y inv on S
 cudaError_t launch_xinv32(flups_plan P, double* p, int mode);  // 0: p = FFTx^-1(S) (+ mean); 1: p += . - mean; 2: p += .

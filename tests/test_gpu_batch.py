@@ -55,6 +55,28 @@ def test_graphable_solve_equals_host_loop(case, rtol):
         assert info.iters >= 3
 
 
+@pytest.mark.parametrize("rtol", [1e-10, 1e-15])
+def test_graphable_solve_equals_host_loop_at_2_24_points(rtol):
+    """At 2^24 points with one spacing both solves take the norm-only stopping test from the
+    second FP32 solve on; rtol 1e-15 makes that test fail, so the fused defect pass and further
+    solves follow it.  Same bits and the same final defect norm either way."""
+    n = 256
+    h = 1.0 / n
+    f = torch.from_numpy(np.random.default_rng(7).standard_normal((n, n, n))).cuda()
+    p1 = torch.empty_like(f)
+    p2 = torch.full_like(f, np.nan)
+    with flups.Plan(n, n, n, h, h, h, "periodic", "fp32_refine") as plan:
+        st, info = plan.solve(f, p1, rtol=rtol, max_iter=5, check=False)
+        plan.solve_graphable(f, p2, rtol=rtol, max_iter=5)
+        st2, res = plan.solve_result(rtol=rtol, check=False)
+    torch.cuda.synchronize()
+    assert torch.equal(p1, p2)
+    assert res.rel_res == info.rel_res and st2 == st
+    assert info.iters >= (3 if rtol < 1e-14 else 2)
+    if rtol > 1e-14:
+        assert st == flups.OK and info.rel_res <= rtol
+
+
 def small_members():
     cases = []
     for m in range(10):

@@ -177,6 +177,69 @@ def test_project_host_matches_device_path():
     assert oracle.div_rel(u, v, w, c.u, c.v, c.w, g) <= 1e-12
 
 
+def test_project_host_equals_device_path_bitwise_at_2_24_points():
+    """The host-buffer projection (inputs on the plan's copy stream, rho first; p copied back
+    while the correction runs) returns the bits of the device-resident sequence, call after
+    call, also after a call that failed (refinement stopped by max_iter)."""
+    n = 256
+    h, dt = 1.0 / n, 1e-3
+    rng = np.random.default_rng(11)
+    u, v, w = (rng.standard_normal((n, n, n)) for _ in range(3))
+    rho = np.where(rng.random((n, n, n)) < 0.05, 10.0, 1.0)
+    pn, pm = (0.01 * rng.standard_normal((n, n, n)) for _ in range(2))
+    with flups.Plan(n, n, n, h, h, h, "periodic", "fp32_refine") as plan:
+        d = {k: dev(a) for k, a in (("u", u), ("v", v), ("w", w), ("rho", rho), ("pn", pn), ("pm", pm))}
+        f = torch.empty_like(d["u"])
+        p = torch.empty_like(f)
+        plan.set_density(d["rho"])
+        plan.rhs(d["u"], d["v"], d["w"], d["pn"], d["pm"], 2.0, 1.0, dt, f)
+        info = plan.solve(f, p, rtol=1e-10, max_iter=6)
+        plan.correct(p, d["pn"], d["pm"], 2.0, 1.0, dt, d["u"], d["v"], d["w"])
+        ref = [host(t) for t in (p, d["u"], d["v"], d["w"])]
+        del d, f, p
+        uh, vh, wh, ph = u.copy(), v.copy(), w.copy(), np.zeros_like(u)
+        with pytest.raises(flups.FlupsError) as e:
+            plan.project_host(uh, vh, wh, rho, pn, pm, 2.0, 1.0, dt, ph, rtol=1e-30, max_iter=1)
+        assert e.value.status == flups.ENOCONV
+        assert np.array_equal(uh, u) and not ph.any()      # nothing copied back on failure
+        for _ in range(2):
+            uh, vh, wh, ph = u.copy(), v.copy(), w.copy(), np.empty_like(u)
+            inf = plan.project_host(uh, vh, wh, rho, pn, pm, 2.0, 1.0, dt, ph, rtol=1e-10, max_iter=6)
+            assert inf.iters == info.iters and inf.rel_res == info.rel_res
+            for a, b in zip((ph, uh, vh, wh), ref):
+                assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("frac", [7.5, 100.0])
+def test_refine_integer_defect_and_its_fp64_fallbacks(frac):
+    """On a grid whose spacing is a power of two the defect is formed in 64-bit integers at the
+    fixed-point scale of p, whose bound is B = 2^e with e the frexp exponent of max|p|: h^2 f
+    must stay below 8 B.  f = c + g with h^2 <f> = 7.5 B puts the points where h^2 g > B/2
+    past that bound (those points take the FP64 form, their neighbours the integer form);
+    h^2 <f> = 100 B sends every point to the FP64 form.  Both refine to rtol against the
+    oracle."""
+    n = 32
+    h = 1.0 / n
+    g = oracle.make_grid(n, n, n, h, h, h, "periodic")
+    gz = np.random.default_rng(21).standard_normal((n, n, n))
+    gz -= oracle.volume_mean(gz, g)
+    po = oracle.solve(gz, g)
+    m, ex = np.frexp(np.max(np.abs(po)))
+    assert 0.5005 < m < 0.9995                        # the FP32 iterate has the same exponent
+    B = 2.0 ** ex
+    f = gz + frac * B / h ** 2
+    if frac < 8:
+        over = h ** 2 * f >= 8 * B
+        assert 0 < over.sum() < over.size // 2        # some points past the bound, most below
+    p = torch.empty(n, n, n, dtype=torch.float64, device="cuda")
+    with flups.Plan(n, n, n, h, h, h, "periodic", "fp32_refine") as plan:
+        info = plan.solve(dev(f), p, rtol=1e-10, max_iter=10)
+    pg = host(p)
+    assert info.rel_res <= 1e-10
+    assert oracle.rel_residual(f, pg, g) <= 1.5e-10
+    assert np.linalg.norm(pg - po) / np.linalg.norm(po) <= 1e-8
+
+
 def test_refine_reports_noconv():
     c, g, (fo, _, _, _, _) = case("sphere32")
     f = dev(fo)
