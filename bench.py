@@ -82,7 +82,7 @@ MEASURED_TRAFFIC_PER_LAUNCH = {
     # emulsion 512^3, the bench step's third k_correct launch: 5.03 GB read + 3.18 GB written
     # (61.2 B/point; constant-density tiles take 56 B/point, the 11.2 % of tiles with density
     # variation 40 B/point more: 60.5 B/point)
-    ("emulsion512", "k_correct"): (5.03 + 3.18) * 1e9,
+    ("emulsion512", "k_correct"): 5_030_000_000 + 3_180_000_000,
 }
 
 
