@@ -738,89 +738,89 @@ __global__ void __launch_bounds__(512) k_xdct(typename cplx<T>::t* __restrict__ 
     extern __shared__ __align__(16) unsigned char smraw[];
     if constexpr (KIND >= 3) {   // twr: pre-twiddles, twq: post-twiddles of the DCT-IV kind
         xdct4_row_tile<T, E, KIND, ACC>(S, fin, pout, INV, g, L, tw, twr, twq, lgB, nrows, smraw);
-        return;
-    }
-    C* s = reinterpret_cast<C*>(smraw);
-    T* sT = reinterpret_cast<T*>(smraw);
-    const int B = 1 << lgB, pitch = B + 1, M = g.M, nx = g.nx;
-    const int row0 = blockIdx.x * B, tid = threadIdx.x, nthr = blockDim.x;
-    const int H = M / 2 + 1;
-    // v_m lives in packed element m/2 of line c, real part for even m
-    auto vat = [&](int m, int c) -> T& { return sT[((m >> 1) * pitch + c) * 2 + (m & 1)]; };
-    if (!INV) {
-        for (int idx = tid; idx < B * M; idx += nthr) {
-            const int c = idx / M, n = idx - c * M;
-            const int row = row0 + c;
-            const double2 xv = row < nrows ? __ldg(reinterpret_cast<const double2*>(fin + (size_t)row * nx) + n)
-                                           : make_double2(0.0, 0.0);
-            vat(n, c) = from_double<T>(xv.x);
-            vat(nx - 1 - n, c) = from_double<T>(KIND == 2 ? -xv.y : xv.y);
+    } else {
+        C* s = reinterpret_cast<C*>(smraw);
+        T* sT = reinterpret_cast<T*>(smraw);
+        const int B = 1 << lgB, pitch = B + 1, M = g.M, nx = g.nx;
+        const int row0 = blockIdx.x * B, tid = threadIdx.x, nthr = blockDim.x;
+        const int H = M / 2 + 1;
+        // v_m lives in packed element m/2 of line c, real part for even m
+        auto vat = [&](int m, int c) -> T& { return sT[((m >> 1) * pitch + c) * 2 + (m & 1)]; };
+        if constexpr (!INV) {
+            for (int idx = tid; idx < B * M; idx += nthr) {
+                const int c = idx / M, n = idx - c * M;
+                const int row = row0 + c;
+                const double2 xv = row < nrows ? __ldg(reinterpret_cast<const double2*>(fin + (size_t)row * nx) + n)
+                                               : make_double2(0.0, 0.0);
+                vat(n, c) = from_double<T>(xv.x);
+                vat(nx - 1 - n, c) = from_double<T>(KIND == 2 ? -xv.y : xv.y);
+            }
+            __syncthreads();
+            fft_tile<C, E, false>(s, pitch, lgB, L, tw);
+            for (int idx = tid; idx < B * H; idx += nthr) {
+                const int c = idx / H, k = idx - c * H;
+                const int row = row0 + c;
+                if (row >= nrows) continue;
+                const C zk = s[k * pitch + c];
+                const C zm = s[(k == 0 ? 0 : M - k) * pitch + c];
+                const T ax = (zk.x + zm.x) * (T)0.5, ay = (zk.y - zm.y) * (T)0.5;
+                const T bxx = (zk.y + zm.y) * (T)0.5, byy = (zm.x - zk.x) * (T)0.5;
+                const C w = __ldg(&twr[k]);
+                const T tx = w.x * bxx - w.y * byy, ty = w.x * byy + w.y * bxx;
+                C* out = S + (size_t)row * g.ldS;
+                auto put = [&](int idx, T v) {           // X_idx: (X, 0), or the idx-th real when packed
+                    if (g.xpack) reinterpret_cast<T*>(out)[idx] = v;
+                    else out[idx] = mk<T>(v, (T)0);
+                };
+                auto emit = [&](int kk, T vx, T vy) {   // X_kk and X_{nx-kk} from V_kk
+                    const C q = __ldg(&twq[kk]);
+                    const T re = q.x * vx - q.y * vy, im = q.x * vy + q.y * vx;
+                    put(KIND == 2 ? nx - 1 - kk : kk, re);
+                    if (kk != 0 && kk != M) put(KIND == 2 ? kk - 1 : nx - kk, -im);
+                };
+                emit(k, ax + tx, ay + ty);                         // V_k
+                if (k != M - k) emit(M - k, ax - tx, ty - ay);     // V_{M-k} (k = 0: V_M)
+            }
+        } else {
+            for (int idx = tid; idx < B * H; idx += nthr) {
+                const int c = idx / H, k = idx - c * H;
+                const int row = row0 + c;
+                C xk = mk<T>((T)0, (T)0), xm = xk;
+                if (row < nrows) {
+                    const C* in = S + (size_t)row * g.ldS;
+                    auto X = [&](int j) -> T {
+                        const int jj = KIND == 2 ? nx - 1 - j : j;
+                        return g.xpack ? reinterpret_cast<const T*>(in)[jj] : in[jj].x;
+                    };
+                    auto vk = [&](int kk) -> C {                       // conj(q_kk) (X_kk - i X_{nx-kk})
+                        const T a = X(kk), b = kk == 0 ? (T)0 : X(nx - kk);
+                        const C q = __ldg(&twq[kk]);
+                        return mk<T>(q.x * a - q.y * b, -(q.x * b + q.y * a));
+                    };
+                    xk = vk(k);
+                    xm = vk(M - k);
+                }
+                if (k == 0) { xk.y = (T)0; xm.y = (T)0; }
+                const T ax = (xk.x + xm.x) * (T)0.5, ay = (xk.y - xm.y) * (T)0.5;
+                const T dx = (xk.x - xm.x) * (T)0.5, dy = (xk.y + xm.y) * (T)0.5;
+                const C w = __ldg(&twr[k]);
+                const T bxx = dx * w.x + dy * w.y, byy = dy * w.x - dx * w.y;
+                s[k * pitch + c] = mk<T>(ax - byy, ay + bxx);
+                if (k != 0 && k != M - k) s[(M - k) * pitch + c] = mk<T>(ax + byy, bxx - ay);
+            }
+            __syncthreads();
+            fft_tile<C, E, true>(s, pitch, lgB, L, tw);
+            for (int idx = tid; idx < B * M; idx += nthr) {
+                const int c = idx / M, n = idx - c * M;
+                const int row = row0 + c;
+                if (row >= nrows) continue;
+                const T a = vat(n, c), b = vat(nx - 1 - n, c);
+                double2* dst = reinterpret_cast<double2*>(pout + (size_t)row * nx) + n;
+                double2 o = make_double2(to_double<T>(a), to_double<T>(KIND == 2 ? -b : b));
+                if (ACC) { const double2 old = *dst; o.x += old.x; o.y += old.y; }
+                *dst = o;
+            }
         }
-        __syncthreads();
-        fft_tile<C, E, false>(s, pitch, lgB, L, tw);
-        for (int idx = tid; idx < B * H; idx += nthr) {
-            const int c = idx / H, k = idx - c * H;
-            const int row = row0 + c;
-            if (row >= nrows) continue;
-            const C zk = s[k * pitch + c];
-            const C zm = s[(k == 0 ? 0 : M - k) * pitch + c];
-            const T ax = (zk.x + zm.x) * (T)0.5, ay = (zk.y - zm.y) * (T)0.5;
-            const T bxx = (zk.y + zm.y) * (T)0.5, byy = (zm.x - zk.x) * (T)0.5;
-            const C w = __ldg(&twr[k]);
-            const T tx = w.x * bxx - w.y * byy, ty = w.x * byy + w.y * bxx;
-            C* out = S + (size_t)row * g.ldS;
-            auto put = [&](int idx, T v) {           // X_idx: (X, 0), or the idx-th real when packed
-                if (g.xpack) reinterpret_cast<T*>(out)[idx] = v;
-                else out[idx] = mk<T>(v, (T)0);
-            };
-            auto emit = [&](int kk, T vx, T vy) {   // X_kk and X_{nx-kk} from V_kk
-                const C q = __ldg(&twq[kk]);
-                const T re = q.x * vx - q.y * vy, im = q.x * vy + q.y * vx;
-                put(KIND == 2 ? nx - 1 - kk : kk, re);
-                if (kk != 0 && kk != M) put(KIND == 2 ? kk - 1 : nx - kk, -im);
-            };
-            emit(k, ax + tx, ay + ty);                         // V_k
-            if (k != M - k) emit(M - k, ax - tx, ty - ay);     // V_{M-k} (k = 0: V_M)
-        }
-        return;
-    }
-    for (int idx = tid; idx < B * H; idx += nthr) {
-        const int c = idx / H, k = idx - c * H;
-        const int row = row0 + c;
-        C xk = mk<T>((T)0, (T)0), xm = xk;
-        if (row < nrows) {
-            const C* in = S + (size_t)row * g.ldS;
-            auto X = [&](int j) -> T {
-                const int jj = KIND == 2 ? nx - 1 - j : j;
-                return g.xpack ? reinterpret_cast<const T*>(in)[jj] : in[jj].x;
-            };
-            auto vk = [&](int kk) -> C {                       // conj(q_kk) (X_kk - i X_{nx-kk})
-                const T a = X(kk), b = kk == 0 ? (T)0 : X(nx - kk);
-                const C q = __ldg(&twq[kk]);
-                return mk<T>(q.x * a - q.y * b, -(q.x * b + q.y * a));
-            };
-            xk = vk(k);
-            xm = vk(M - k);
-        }
-        if (k == 0) { xk.y = (T)0; xm.y = (T)0; }
-        const T ax = (xk.x + xm.x) * (T)0.5, ay = (xk.y - xm.y) * (T)0.5;
-        const T dx = (xk.x - xm.x) * (T)0.5, dy = (xk.y + xm.y) * (T)0.5;
-        const C w = __ldg(&twr[k]);
-        const T bxx = dx * w.x + dy * w.y, byy = dy * w.x - dx * w.y;
-        s[k * pitch + c] = mk<T>(ax - byy, ay + bxx);
-        if (k != 0 && k != M - k) s[(M - k) * pitch + c] = mk<T>(ax + byy, bxx - ay);
-    }
-    __syncthreads();
-    fft_tile<C, E, true>(s, pitch, lgB, L, tw);
-    for (int idx = tid; idx < B * M; idx += nthr) {
-        const int c = idx / M, n = idx - c * M;
-        const int row = row0 + c;
-        if (row >= nrows) continue;
-        const T a = vat(n, c), b = vat(nx - 1 - n, c);
-        double2* dst = reinterpret_cast<double2*>(pout + (size_t)row * nx) + n;
-        double2 o = make_double2(to_double<T>(a), to_double<T>(KIND == 2 ? -b : b));
-        if (ACC) { const double2 old = *dst; o.x += old.x; o.y += old.y; }
-        *dst = o;
     }
 }
 
@@ -1142,16 +1142,16 @@ __global__ void __launch_bounds__(1024, 1) k_cols_pipe(float2* __restrict__ S, c
     if (g.skip && *g.skip) return;   // graph-capturable solve: this member already converged
     constexpr int E = 8;
     typedef float2 C;
-    extern __shared__ __align__(1024) unsigned char smraw[];   // [tile 0][tile 1][2 mbarriers]
+    extern __shared__ __align__(128) unsigned char smpipe[];   // [tile 0][tile 1][2 mbarriers]
     const int B = 1 << lgB;
     const int N = KIND == 0 ? g.ny : g.nz;
     const size_t rs = KIND == 0 ? (size_t)g.ldS : (size_t)g.ny * g.ldS;    // row stride (elements)
     const int tiles_x = g.M >> lgB;
     const int ntiles = tiles_x * (KIND == 0 ? g.nz : g.ny);
     const unsigned tile_bytes = (unsigned)(N * B * sizeof(C));
-    C* buf0 = reinterpret_cast<C*>(smraw);
-    C* buf1 = reinterpret_cast<C*>(smraw + tile_bytes);
-    unsigned long long* mbar = reinterpret_cast<unsigned long long*>(smraw + 2 * (size_t)tile_bytes);
+    C* buf0 = reinterpret_cast<C*>(smpipe);
+    C* buf1 = reinterpret_cast<C*>(smpipe + tile_bytes);
+    unsigned long long* mbar = reinterpret_cast<unsigned long long*>(smpipe + 2 * (size_t)tile_bytes);
     const int tid = threadIdx.x;
     const int c = tid & (B - 1), j0 = tid >> lgB, NE = N / E;
 
@@ -1172,7 +1172,7 @@ __global__ void __launch_bounds__(1024, 1) k_cols_pipe(float2* __restrict__ S, c
         }
     };
 
-    if (smem_u32(smraw) & 127u) {   // TMA box destinations must be 128-byte aligned
+    if (smem_u32(smpipe) & 127u) {   // TMA box destinations must be 128-byte aligned
         if (tid == 0) atomicExch(err, 2);
         return;
     }

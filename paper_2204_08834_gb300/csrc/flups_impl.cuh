@@ -136,8 +136,8 @@ struct flups_plan_s {
     unsigned long long launches; // kernels launched on this plan so far
     // TMA descriptors of the FP32 spectrum [nz][ny][ldS] for the pipelined column passes:
     // boxes of (B kx, up to 256 ky, 1 k) and (B kx, 1 ky, up to 256 k)
-    alignas(64) CUtensorMap tm_y;
-    alignas(64) CUtensorMap tm_z;
+    CUtensorMap tm_y;            // (the type carries the 128-byte alignment TMA needs)
+    CUtensorMap tm_z;
     int tma_ok;
     int* skip_ptr;               // passed to kernels as Geo::skip (set by the fixed-iteration solve)
     int cta_cap;                 // thread cap of the transform CTAs (autotuned per size in batches)

@@ -330,7 +330,7 @@ __device__ __forceinline__ void tz_load_plane(const uint4* __restrict__ src, uns
 
 template <int EPI>
 __global__ void __launch_bounds__(TZ_THREADS, 2) k_pnet_conv_tcz(ConvArgs a, int zc) {
-    extern __shared__ __align__(1024) unsigned char sm[];
+    extern __shared__ __align__(128) unsigned char sm[];
     unsigned char* ring = sm;
     unsigned char* sw = sm + 4 * TZ_PLANE;
     unsigned long long* mbar = reinterpret_cast<unsigned long long*>(sw + 27 * 512);   // [2]

@@ -115,13 +115,12 @@ __global__ void k_vc_apply(const double* __restrict__ d, double* __restrict__ q,
     block_part(acc, part);
 }
 
-// mode 0: part = (a, 1)_w;  mode 1: r = a - mean, part = (r, r)_w;  mode 2: part = (a, b)_w;
-// mode 3: a -= mean (no partials).
+// mode 0: part = (a, 1)_w;  mode 1: r = a - mean, part = (r, r)_w;  mode 2: part = (a, b)_w.
 template <int MODE>
 __global__ void k_vc_vec(const double* __restrict__ a, const double* __restrict__ b, double* __restrict__ out,
                          const VcScalars* __restrict__ vs, VcGeo g, double* __restrict__ part) {
     double acc = 0.0;
-    const double mean = (MODE == 1 || MODE == 3) ? vs->mean : 0.0;
+    const double mean = MODE == 1 ? vs->mean : 0.0;
     const long long plane = (long long)g.nx * g.ny;
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < g.n; c += (long long)gridDim.x * blockDim.x) {
         const double w = g.dzf[c / plane];
@@ -131,13 +130,18 @@ __global__ void k_vc_vec(const double* __restrict__ a, const double* __restrict_
             const double r = a[c] - mean;
             out[c] = r;
             acc += w * r * r;
-        } else if (MODE == 2) {
-            acc += w * a[c] * b[c];
         } else {
-            out[c] = a[c] - mean;
+            acc += w * a[c] * b[c];
         }
     }
-    if (MODE != 3) block_part(acc, part);
+    block_part(acc, part);
+}
+
+// x -= mean, in place.
+__global__ void k_vc_shift(double* __restrict__ x, const VcScalars* __restrict__ vs, long long n) {
+    const double mean = vs->mean;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x)
+        x[c] -= mean;
 }
 
 // x += alpha d; r -= alpha q; part = (r, r)_w.
@@ -319,7 +323,7 @@ extern "C" flups_status flups_varcoef_solve(flups_plan P, const double* rho, con
     // p -= <p>_V
     k_vc_vec<0><<<nb, VC_THREADS, 0, s>>>(p, nullptr, nullptr, W.vs, g, W.part);
     fin(0);
-    k_vc_vec<3><<<nb, VC_THREADS, 0, s>>>(p, nullptr, p, W.vs, g, W.part);
+    k_vc_shift<<<nb, VC_THREADS, 0, s>>>(p, W.vs, g.n);
     FLUPS_COUNT(P, 2);
     e = cudaGetLastError();
     if (e != cudaSuccess) { flups_note_cuda_error(e); return FLUPS_ECUDA; }
