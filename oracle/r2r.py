@@ -11,17 +11,17 @@ Boundary conditions per direction x, y: 'P' periodic, or two letters for the low
 or 'D' (homogeneous Dirichlet on the boundary face, ghost p_{-1} = -p_0).  z is periodic or
 walls (Neumann) as in oracle/projection.py.
 
-Readings (B1-B4):
-  B1  Cell-centred p with the boundary on the outer cell faces, so the ghost rules above give
+Readings (E1-E4):
+  E1  Cell-centred p with the boundary on the outer cell faces, so the ghost rules above give
       the eigenvectors cos(pi k (2i+1)/(2n)) (NN), sin(pi (k+1)(2i+1)/(2n)) (DD),
       cos(pi (2k+1)(2i+1)/(4n)) (ND) and sin(pi (2k+1)(2i+1)/(4n)) (DN): the DCT-II, DST-II,
       DCT-IV and DST-IV kinds.
-  B2  Eigenvalues of the 3-point operator: -4 sin^2(pi k/(2n))/h^2 (NN), -4 sin^2(pi (k+1)/(2n))/h^2
+  E2  Eigenvalues of the 3-point operator: -4 sin^2(pi k/(2n))/h^2 (NN), -4 sin^2(pi (k+1)/(2n))/h^2
       (DD), -4 sin^2(pi (2k+1)/(4n))/h^2 (ND, DN).
-  B3  The operator is singular only when no end is Dirichlet (x, y each 'P' or 'NN', z periodic
+  E3  The operator is singular only when no end is Dirichlet (x, y each 'P' or 'NN', z periodic
       or walls); then R3/R4 of oracle/projection.py apply (mean of f removed, zero-mean p).
       Otherwise the solve is plain: f is used as given and p is unique.
-  B4  Only the Poisson solve (and its residual) takes these ends; the projection stencils of
+  E4  Only the Poisson solve (and its residual) takes these ends; the projection stencils of
       oracle/projection.py stay periodic in x and y.
 """
 
@@ -70,7 +70,7 @@ def lap(p, g, bcx, bcy):
 
 
 def eigenvalues(n, h, bc):
-    """Eigenvalues of the 3-point operator along one direction, in transform order (B2)."""
+    """Eigenvalues of the 3-point operator along one direction, in transform order (E2)."""
     k = np.arange(n)
     if bc == "P":
         return P.eigenvalues(n, h)
@@ -83,7 +83,7 @@ def eigenvalues(n, h, bc):
 
 def forward(a, bc, axis, real_input):
     """Forward series along `axis`: real FFT (x, periodic), complex FFT (y, periodic) or the
-    cosine/sine kind of B1 (real and imaginary parts transformed alike)."""
+    cosine/sine kind of E1 (real and imaginary parts transformed alike)."""
     if bc == "P":
         return np.fft.rfft(a, axis=axis) if real_input else np.fft.fft(a, axis=axis)
     typ = 2 if bc in ("NN", "DD") else 4
@@ -98,7 +98,7 @@ def backward(a, bc, axis, n, real_output):
 
 
 def singular(g, bcx, bcy):
-    """No Dirichlet end anywhere (B3)."""
+    """No Dirichlet end anywhere (E3)."""
     return bcx in ("P", "NN") and bcy in ("P", "NN")
 
 

@@ -1,5 +1,5 @@
 """GPU parity of the Poisson solve with Neumann or Dirichlet ends in x and/or y (Sec. 3.3.1,
-cosine/sine series; oracle/r2r.py, readings B1-B4) against the FP64 oracle.
+cosine/sine series; oracle/r2r.py, readings E1-E4) against the FP64 oracle.
 
 Tolerance: both sides are FP64 eigen-expansion solves (GPU: Makhoul's construction around the
 library's FFTs; oracle: scipy's DCT/DST), so p agrees to the rounding of the transforms

@@ -1,4 +1,4 @@
-"""Pins of the Neumann/Dirichlet-end Poisson oracle (Sec. 3.3.1 eigen-expansion, readings B1-B4
+"""Pins of the Neumann/Dirichlet-end Poisson oracle (Sec. 3.3.1 eigen-expansion, readings E1-E4
 in oracle/r2r.py) against constructions that do not use the oracle: an operator assembled
 cell by cell from the ghost rules, dense solves, explicit cosine/sine sums, closed-form modes."""
 
@@ -128,7 +128,7 @@ def test_single_modes_and_eigenvalues_closed_form(bc):
 
 @pytest.mark.parametrize("bc", ["NN", "DD", "ND", "DN"])
 def test_library_transform_kind_is_the_eigenvector_projection(bc):
-    """forward(x)_k equals 2 sum_i x_i v_k(i) with the eigenvectors of B1 (explicit sums)."""
+    """forward(x)_k equals 2 sum_i x_i v_k(i) with the eigenvectors of E1 (explicit sums)."""
     n = 10
     x = np.random.default_rng(3).standard_normal(n)
     i = np.arange(n)
