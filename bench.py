@@ -21,6 +21,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -120,7 +121,10 @@ class ClockSampler:
     def __init__(self, index):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+        # the raw samples go to FLUPS_BENCH_CLOCKS_DIR when set (else the temp directory); the
+        # JSON line carries their summary
+        d = os.environ.get("FLUPS_BENCH_CLOCKS_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(d, f"flups_clocks_rank{index}.csv")
 
     def __enter__(self):
         try:

@@ -1,6 +1,6 @@
 """Parity at the full workload sizes, in the launch configuration bench.py times.
 
-Checks per case (host RAM on the GPU machine bounds what the oracle can do at 1024x1024x512,
+Checks per case (host RAM of the machine running the GPU tests bounds what the oracle can do at 1024x1024x512,
 so that case skips the oracle's direct solve and its correction):
   * rhs: element-wise against the oracle's rhs on the full arrays, max |diff| <= 1e-12 max |f|;
   * solve (FP32+refine, rtol 1e-10): the oracle's FP64 residual of the GPU's p against the
