@@ -201,6 +201,20 @@ def test_forward_steps_are_explicit_dft_sums():
         assert abs(F[ky, kx] - s) < 1e-12
 
 
+@pytest.mark.parametrize("n", [2, 3, 4, 6, 8, 12, 16, 48, 96])
+def test_transform_lengths_of_the_path_are_explicit_dft_sums(n):
+    """Every length the GPU path factors (radix 2, 3, 4, 8, the ensemble's 48 and 96): the
+    library's real and complex forward transforms and their inverses equal the O(n^2) sums."""
+    x = rand((n,), 7 + n)
+    z = x + 1j * rand((n,), 8 + n)
+    k = np.arange(n)
+    W = np.exp(-2j * np.pi * np.outer(k, k) / n)
+    assert np.max(np.abs(np.fft.fft(z) - W @ z)) < 1e-12 * n
+    assert np.max(np.abs(np.fft.rfft(x) - (W @ x)[: n // 2 + 1])) < 1e-12 * n
+    assert np.max(np.abs(np.fft.ifft(z) - (W.conj() @ z) / n)) < 1e-13 * n
+    assert np.max(np.abs(np.fft.irfft(np.fft.rfft(x), n=n) - x)) < 1e-13 * n
+
+
 def test_eigenvalues_match_dft_of_stencil():
     """(2 cos(2 pi k/n) - 2)/h^2 is the DFT of the periodic 3-point stencil."""
     n, h = 12, 0.3
