@@ -324,6 +324,12 @@ flups_status flups_varcoef_solve(flups_plan plan, const double* rho, const doubl
  * flups_pnet_set_params / get_params - HOST copies of the FP32 master parameters; set resets
  *                      the Adam state; both synchronise.
  * flups_pnet_get_grads - the parameter gradient of the last train step (HOST); synchronises.
+ * flups_pnet_get_adam / set_adam - HOST copies of the Adam moments m, v (FLUPS_PNET_NPARAMS
+ *                      floats each, v >= 0) and the number of Adam steps taken (0 .. 2^31-1);
+ *                      with the master parameters they are the whole training state, so
+ *                      set_params followed by set_adam resumes training exactly (set_params
+ *                      resets them, so set_adam comes second).  Both synchronise; set_adam
+ *                      returns FLUPS_EINVAL for non-finite or negative entries.
  * flups_pnet_launch_count - kernels this net has launched so far.
  * flups_pnet_set_profiling / profile_read / kernel_name - optional CUDA-event timing of the
  *                      net's kernel groups (FLUPS_PNET_NKERNELS entries: features, hidden
@@ -338,6 +344,8 @@ flups_status flups_pnet_destroy(flups_pnet net);
 flups_status flups_pnet_set_params(flups_pnet net, const float* params);
 flups_status flups_pnet_get_params(flups_pnet net, float* params);
 flups_status flups_pnet_get_grads(flups_pnet net, float* grads);
+flups_status flups_pnet_get_adam(flups_pnet net, float* m, float* v, long long* step);
+flups_status flups_pnet_set_adam(flups_pnet net, const float* m, const float* v, long long step);
 flups_status flups_pnet_predict(flups_pnet net, const double* rho, double rho0, const double* p_n,
                                 const double* p_nm1, double* p_hat);
 flups_status flups_pnet_train_step(flups_pnet net, const double* rho, double rho0, const double* p_n,

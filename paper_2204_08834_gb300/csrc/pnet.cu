@@ -997,6 +997,28 @@ flups_status flups_pnet_get_params(flups_pnet N, float* params) {
     return check_err(N);
 }
 
+flups_status flups_pnet_get_adam(flups_pnet N, float* m, float* v, long long* step) {
+    if (!N || !m || !v || !step) return FLUPS_EINVAL;
+    PnGuard dg(N->dev);
+    cudaError_t e = cudaMemcpyAsync(m, N->m, PN_NP * sizeof(float), cudaMemcpyDeviceToHost, N->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(v, N->v, PN_NP * sizeof(float), cudaMemcpyDeviceToHost, N->stream);
+    if (e != cudaSuccess) return pn_status(e);
+    *step = N->step;
+    return check_err(N);
+}
+
+flups_status flups_pnet_set_adam(flups_pnet N, const float* m, const float* v, long long step) {
+    if (!N || !m || !v || step < 0 || step > 0x7FFFFFFFLL) return FLUPS_EINVAL;
+    for (int p = 0; p < PN_NP; ++p)
+        if (!std::isfinite(m[p]) || !std::isfinite(v[p]) || v[p] < 0.0f) return FLUPS_EINVAL;
+    PnGuard dg(N->dev);
+    cudaError_t e = cudaMemcpyAsync(N->m, m, PN_NP * sizeof(float), cudaMemcpyHostToDevice, N->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(N->v, v, PN_NP * sizeof(float), cudaMemcpyHostToDevice, N->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(N->stream);   // m, v may be freed on return
+    if (e == cudaSuccess) N->step = (int)step;
+    return pn_status(e);
+}
+
 flups_status flups_pnet_get_grads(flups_pnet N, float* grads) {
     if (!N || !grads) return FLUPS_EINVAL;
     PnGuard dg(N->dev);

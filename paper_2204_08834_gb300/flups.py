@@ -30,7 +30,7 @@ SYMBOLS = [
     "flups_batch_create", "flups_batch_solve", "flups_batch_destroy", "flups_batch_graph_kernels",
     "flups_batch_member_tuning", "flups_last_cuda_error", "flups_varcoef_solve",
     "flups_pnet_create", "flups_pnet_destroy", "flups_pnet_set_params", "flups_pnet_get_params",
-    "flups_pnet_get_grads", "flups_pnet_predict", "flups_pnet_train_step", "flups_pnet_eval_loss",
+    "flups_pnet_get_grads", "flups_pnet_get_adam", "flups_pnet_set_adam", "flups_pnet_predict", "flups_pnet_train_step", "flups_pnet_eval_loss",
     "flups_pnet_launch_count", "flups_pnet_set_profiling", "flups_pnet_profile_read", "flups_pnet_kernel_name",
     "flups_selftest_wait_timeout", "flups_momentum_predict", "flups_plan_create_bc",
 ]
@@ -103,6 +103,8 @@ def lib():
         L.flups_pnet_set_params.argtypes = [P, FP]
         L.flups_pnet_get_params.argtypes = [P, FP]
         L.flups_pnet_get_grads.argtypes = [P, FP]
+        L.flups_pnet_get_adam.argtypes = [P, FP, FP, ctypes.POINTER(ctypes.c_longlong)]
+        L.flups_pnet_set_adam.argtypes = [P, FP, FP, ctypes.c_longlong]
         L.flups_pnet_predict.argtypes = [P, V, D, V, V, V]
         L.flups_pnet_train_step.argtypes = [P, V, D, V, V, V, ctypes.c_float, DP]
         L.flups_pnet_eval_loss.argtypes = [P, V, D, V, V, V, DP]
@@ -447,6 +449,23 @@ class PNet:
         _check(lib().flups_pnet_get_grads(self._h, a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))),
                "flups_pnet_get_grads")
         return a
+
+    def adam_state(self):
+        """(m, v, step): the Adam moments and the number of steps taken."""
+        m = np.empty(PNET_NPARAMS, np.float32)
+        v = np.empty(PNET_NPARAMS, np.float32)
+        step = ctypes.c_longlong()
+        fp = ctypes.POINTER(ctypes.c_float)
+        _check(lib().flups_pnet_get_adam(self._h, m.ctypes.data_as(fp), v.ctypes.data_as(fp), ctypes.byref(step)),
+               "flups_pnet_get_adam")
+        return m, v, int(step.value)
+
+    def set_adam_state(self, m, v, step):
+        """Restore the Adam moments and step count (after set_params, which resets them)."""
+        m, v = _fparams(m), _fparams(v)
+        fp = ctypes.POINTER(ctypes.c_float)
+        _check(lib().flups_pnet_set_adam(self._h, m.ctypes.data_as(fp), v.ctypes.data_as(fp), int(step)),
+               "flups_pnet_set_adam")
 
     def predict(self, rho, rho0, pn, pnm1, p_hat):
         _check(lib().flups_pnet_predict(self._h, ptr(rho), float(rho0), ptr(pn), ptr(pnm1), ptr(p_hat)),

@@ -15,6 +15,9 @@ e_u = ||u_split - u_ex|| / ||u_ex||, and relative to the pressure correction its
 e_du = ||u_split - u_ex|| / ||u_ex - u**||.
 """
 
+import json
+import struct
+
 import numpy as np
 
 from . import flups, synth
@@ -83,15 +86,19 @@ def samples(windows):
     return [(i, m) for i, win in enumerate(windows) for m in range(1, len(win.p) - 1)]
 
 
-def train(net, windows, steps, lr=1e-3, seed=41, log_every=0):
-    """`steps` Adam steps on samples drawn uniformly (seeded) from the windows; returns losses."""
+def train(net, windows, steps, lr=1e-3, seed=41, log_every=0, start=0):
+    """`steps` Adam steps on samples drawn uniformly (seeded) from the windows; returns losses.
+    `start` > 0 continues a run that stopped after `start` steps (restored from a checkpoint):
+    the same seed then draws the samples the uninterrupted run would have drawn."""
     rng = np.random.Generator(np.random.PCG64(seed))
     idx = samples(windows)
+    for _ in range(start):
+        rng.integers(len(idx))
     losses = []
-    for s in range(steps):
+    for s in range(start, start + steps):
         i, m = idx[rng.integers(len(idx))]
         win = windows[i]
-        want = log_every and (s % log_every == 0 or s == steps - 1)
+        want = log_every and (s % log_every == 0 or s == start + steps - 1)
         loss = net.train_step(win.rho, win.rho0, win.p[m], win.p[m - 1], win.p[m + 1], lr, want_loss=bool(want))
         if want:
             losses.append((s, loss))
@@ -144,3 +151,107 @@ def compare_predictors(net, win, dt, plan):
         out["net"].append(splitting_errors(win, m, dt, p_hat, None, 1.0, 0.0, plan))
         out["lin"].append(splitting_errors(win, m, dt, win.p[m - 1], win.p[m - 2], 2.0, 1.0, plan))
     return out
+
+
+# ------------------------------------------------------- checkpoints and saved datasets
+#
+# File layout: the 8 bytes b"FLUPSARR", the header length as a little-endian uint64, a UTF-8
+# JSON header {"version": 1, "arrays": [{"name", "dtype", "shape", "offset", "nbytes"}, ...],
+# "meta": {...}}, then the arrays' raw little-endian bytes, offsets counted from the end of
+# the header.
+
+ARRAY_MAGIC = b"FLUPSARR"
+
+
+def write_arrays(path, arrays, meta=None):
+    """Named arrays (dict name -> ndarray) and a JSON-able `meta` dict in one file."""
+    entries, blobs, off = [], [], 0
+    for name, a in arrays.items():
+        a = np.ascontiguousarray(a)
+        le = a.astype(a.dtype.newbyteorder("<"), copy=False)
+        b = le.tobytes()
+        entries.append({"name": name, "dtype": le.dtype.str, "shape": list(a.shape), "offset": off,
+                        "nbytes": len(b)})
+        blobs.append(b)
+        off += len(b)
+    hdr = json.dumps({"version": 1, "arrays": entries, "meta": meta or {}}).encode()
+    with open(path, "wb") as fh:
+        fh.write(ARRAY_MAGIC)
+        fh.write(struct.pack("<Q", len(hdr)))
+        fh.write(hdr)
+        for b in blobs:
+            fh.write(b)
+
+
+def read_arrays(path):
+    """(dict name -> ndarray in native byte order, meta) of a file written by write_arrays."""
+    with open(path, "rb") as fh:
+        if fh.read(8) != ARRAY_MAGIC:
+            raise ValueError(f"{path}: not an array file")
+        raw = fh.read(8)
+        if len(raw) != 8:
+            raise ValueError(f"{path}: truncated header")
+        (n,) = struct.unpack("<Q", raw)
+        hdr = fh.read(n)
+        if len(hdr) != n:
+            raise ValueError(f"{path}: truncated header")
+        hdr = json.loads(hdr.decode())
+        data = fh.read()
+    if hdr.get("version") != 1:
+        raise ValueError(f"{path}: unknown version {hdr.get('version')}")
+    out = {}
+    for e in hdr["arrays"]:
+        dt = np.dtype(e["dtype"])
+        count = int(np.prod(e["shape"], dtype=np.int64))
+        if e["offset"] + e["nbytes"] > len(data) or count * dt.itemsize != e["nbytes"]:
+            raise ValueError(f"{path}: array {e['name']} truncated or inconsistent")
+        a = np.frombuffer(data, dtype=dt, count=count, offset=e["offset"]).reshape(e["shape"])
+        out[e["name"]] = a.astype(dt.newbyteorder("="))
+    return out, hdr["meta"]
+
+
+def save_checkpoint(net, path, meta=None):
+    """The whole training state of a flups.PNet: FP32 master parameters, Adam moments, step
+    count (in meta["step"]) and the caller's `meta` (learning rate, seed, ...)."""
+    m, v, step = net.adam_state()
+    write_arrays(path, {"params": net.params(), "m": m, "v": v},
+                 dict(meta or {}, kind="pnet-checkpoint", step=step, nparams=flups.PNET_NPARAMS))
+
+
+def load_checkpoint(path):
+    """(arrays, meta) of a checkpoint written by save_checkpoint."""
+    arrays, meta = read_arrays(path)
+    if meta.get("kind") != "pnet-checkpoint" or meta.get("nparams") != flups.PNET_NPARAMS:
+        raise ValueError(f"{path}: not a checkpoint of this net")
+    return arrays, meta
+
+
+def restore(net, arrays, meta):
+    """Puts a loaded checkpoint into `net`; training then continues as if never stopped."""
+    net.set_params(arrays["params"])
+    net.set_adam_state(arrays["m"], arrays["v"], meta["step"])
+
+
+def save_windows(path, windows, dt):
+    """A dataset of windows (density and the exact pressure series; FP64) with dt."""
+    arrays, info = {}, []
+    for i, win in enumerate(windows):
+        arrays[f"w{i}/rho"] = win.rho.cpu().numpy()
+        for m, p in enumerate(win.p):
+            arrays[f"w{i}/p{m}"] = p.cpu().numpy()
+        info.append({"rho0": win.rho0, "steps": len(win.p)})
+    write_arrays(path, arrays, {"kind": "learned-windows", "dt": dt, "windows": info})
+
+
+def load_windows(path, device="cuda"):
+    """(windows, dt) of a dataset written by save_windows, on `device`."""
+    import torch
+    arrays, meta = read_arrays(path)
+    if meta.get("kind") != "learned-windows":
+        raise ValueError(f"{path}: not a saved dataset")
+    wins = []
+    for i, wi in enumerate(meta["windows"]):
+        rho = torch.from_numpy(arrays[f"w{i}/rho"]).to(device)
+        ps = [torch.from_numpy(arrays[f"w{i}/p{m}"]).to(device) for m in range(wi["steps"])]
+        wins.append(Window(rho, wi["rho0"], ps))
+    return wins, meta["dt"]

@@ -111,6 +111,8 @@ def test_null_handles_are_rejected(lib):
         assert getattr(lib, fn)(*args) == flups.EINVAL
     assert lib.flups_pnet_predict(None, None, 1.0, None, None, None) == flups.EINVAL
     assert lib.flups_pnet_launch_count(None) == 0
+    assert lib.flups_pnet_get_adam(None, None, None, None) == flups.EINVAL
+    assert lib.flups_pnet_set_adam(None, None, None, 0) == flups.EINVAL
     assert lib.flups_pnet_kernel_name(99).decode() == "unknown"
     assert lib.flups_selftest_wait_timeout(None, 0) == flups.EINVAL
 

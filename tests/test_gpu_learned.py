@@ -195,6 +195,48 @@ def test_adam_steps_match_oracle():
             ref = after.copy()                              # continue from the GPU's FP32 state
 
 
+def test_checkpoint_resume_equals_uninterrupted_training(tmp_path):
+    """Parameters, Adam moments and step count saved after two steps and restored into a fresh
+    net (created with other weights) continue exactly like the uninterrupted run: the same
+    losses and the same state, bit for bit."""
+    shape = (4, 8, 32)
+    batches = [tuple(dev(a) for a in net_inputs(shape, 60 + k)) for k in range(4)]
+    params = rand_params(54)
+    lr = 1e-2
+
+    def step(net, b):
+        rho, pn, pnm1, pnext = b
+        return net.train_step(rho, 1.0, pn, pnm1, pnext, lr)
+
+    with flups.PNet(32, 8, 4, params) as a:
+        la = [step(a, b) for b in batches]
+        pa, (ma, va, sa) = a.params(), a.adam_state()
+    path = tmp_path / "ckpt.bin"
+    with flups.PNet(32, 8, 4, params) as b:
+        lb = [step(b, x) for x in batches[:2]]
+        learned.save_checkpoint(b, path, meta={"lr": lr})
+    arrays, meta = learned.load_checkpoint(path)
+    assert meta["step"] == 2 and meta["lr"] == lr
+    with flups.PNet(32, 8, 4, learned.init_params(99)) as c:
+        learned.restore(c, arrays, meta)
+        assert c.adam_state()[2] == 2
+        lc = [step(c, x) for x in batches[2:]]
+        pc, (mc, vc, sc) = c.params(), c.adam_state()
+    assert lb == la[:2] and lc == la[2:]
+    assert np.array_equal(pc, pa) and np.array_equal(mc, ma) and np.array_equal(vc, va)
+    assert sa == sc == 4
+
+
+def test_adam_state_rejects_invalid_moments():
+    m = np.zeros(flups.PNET_NPARAMS, np.float32)
+    v = np.zeros(flups.PNET_NPARAMS, np.float32)
+    with flups.PNet(32, 8, 4, rand_params(55)) as net:
+        for mm, vv, st in ((m, -np.ones_like(v), 1), (np.full_like(m, np.nan), v, 1), (m, v, -1)):
+            with pytest.raises(flups.FlupsError) as e:
+                net.set_adam_state(mm, vv, st)
+            assert e.value.status == flups.EINVAL
+
+
 @pytest.mark.slow
 def test_fullsize_inference_sampled():
     """128^3 inference window (ratio 20, 50 droplets): 48 sampled outputs against the oracle."""
