@@ -249,6 +249,7 @@ flups_status flups_batch_create(flups_batch* out, int n, const int* nx, const in
 
 flups_status flups_batch_solve(flups_batch B, const double* const* f, double* const* p, double rtol, int max_iter,
                                flups_info* info) {
+    NvtxRange nvtx_("flups_batch_solve");
     if (!B || !f || !p || max_iter < 1 || max_iter > 64 || !(rtol >= 0.0)) return FLUPS_EINVAL;
     for (int m = 0; m < B->n; ++m)
         if (!f[m] || !p[m] || f[m] == p[m] || ((uintptr_t)f[m] & 15u) || ((uintptr_t)p[m] & 15u)) return FLUPS_EINVAL;

@@ -607,6 +607,7 @@ flups_status ends_refine(flups_plan P, const double* f, double* p, double rtol, 
 }
 
 flups_status flups_set_density(flups_plan P, const double* rho, double rho0) {
+    NvtxRange nvtx_("flups_set_density");
     if (!P || !rho || !aligned16(rho) || std::isnan(rho0)) return FLUPS_EINVAL;
     if (has_ends(P)) return FLUPS_EUNSUPPORTED;
     DeviceGuard dg(P->dev);
@@ -627,6 +628,7 @@ flups_status flups_get_rho0(flups_plan P, double* rho0_host) {
 
 flups_status flups_rhs(flups_plan P, const double* u, const double* v, const double* w, const double* p_n,
                        const double* p_nm1, double c1, double c2, double dt, double* f) {
+    NvtxRange nvtx_("flups_rhs");
     if (!P || !u || !v || !w || !p_n || !f) return FLUPS_EINVAL;
     if (has_ends(P)) return FLUPS_EUNSUPPORTED;
     if (!aligned16(u) || !aligned16(v) || !aligned16(w) || !aligned16(p_n) || !aligned16(f) ||
@@ -641,6 +643,7 @@ flups_status flups_rhs(flups_plan P, const double* u, const double* v, const dou
 
 flups_status flups_correct(flups_plan P, const double* p, const double* p_n, const double* p_nm1, double c1,
                            double c2, double dt, double* u, double* v, double* w) {
+    NvtxRange nvtx_("flups_correct");
     if (!P || !p || !p_n || !u || !v || !w) return FLUPS_EINVAL;
     if (has_ends(P)) return FLUPS_EUNSUPPORTED;
     if (!aligned16(p) || !aligned16(p_n) || !aligned16(u) || !aligned16(v) || !aligned16(w) ||
@@ -653,6 +656,7 @@ flups_status flups_correct(flups_plan P, const double* p, const double* p_n, con
 }
 
 flups_status flups_solve(flups_plan P, const double* f, double* p, double rtol, int max_iter, flups_info* info) {
+    NvtxRange nvtx_("flups_solve");
     if (!P || !f || !p || f == p || !aligned16(f) || !aligned16(p)) return FLUPS_EINVAL;
     if (std::isnan(rtol)) return FLUPS_EINVAL;
     DeviceGuard dg(P->dev);
@@ -723,6 +727,7 @@ flups_status flups_solve(flups_plan P, const double* f, double* p, double rtol, 
 }
 
 flups_status flups_solve_graphable(flups_plan P, const double* f, double* p, double rtol, int max_iter) {
+    NvtxRange nvtx_("flups_solve_graphable");
     if (!P || !f || !p || f == p || !aligned16(f) || !aligned16(p)) return FLUPS_EINVAL;
     if (P->prec != FLUPS_FP32_REFINE) return FLUPS_EINVAL;
     if (has_ends(P)) return FLUPS_EUNSUPPORTED;
@@ -752,6 +757,7 @@ flups_status flups_solve_result(flups_plan P, double rtol, flups_info* info) {
 flups_status flups_project_host(flups_plan P, double* u, double* v, double* w, const double* rho,
                                 const double* p_n, const double* p_nm1, double c1, double c2, double dt,
                                 double rtol, int max_iter, double* p_out, flups_info* info) {
+    NvtxRange nvtx_("flups_project_host");
     if (!P || !u || !v || !w || !rho || !p_n || !p_out) return FLUPS_EINVAL;
     if (has_ends(P)) return FLUPS_EUNSUPPORTED;
     DeviceGuard dg(P->dev);

@@ -17,6 +17,17 @@
 #include <stddef.h>
 
 #include "../../include/flups.h"
+#include <nvtx3/nvToolsExt.h>
+
+// One NVTX range per public call, named after it, so that a profiler can attribute kernels to
+// calls (for instance `ncu --nvtx --nvtx-include "flups_solve/"`); with no tool attached the
+// push and the pop return at once.
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 #define FLUPS_MAX_STAGES 14
 

@@ -422,6 +422,7 @@ extern "C" flups_status flups_momentum_predict(flups_plan P, const double* u, co
                                                double* us, double* vs, double* ws, void* m_state, double nu,
                                                double gx, double gy, double gz, double dt, double dt_prev,
                                                int arith) {
+    NvtxRange nvtx_("flups_momentum_predict");
     if (!P || !u || !v || !w || !us || !vs || !ws || !m_state) return FLUPS_EINVAL;
     const void* ptrs[7] = {u, v, w, us, vs, ws, m_state};
     for (const void* p : ptrs)

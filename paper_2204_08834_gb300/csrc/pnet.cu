@@ -1029,6 +1029,7 @@ flups_status flups_pnet_get_grads(flups_pnet N, float* grads) {
 
 flups_status flups_pnet_predict(flups_pnet N, const double* rho, double rho0, const double* p_n, const double* p_nm1,
                                 double* p_hat) {
+    NvtxRange nvtx_("flups_pnet_predict");
     flups_status st = check_fields(N, rho, rho0, p_n, p_nm1);
     if (st != FLUPS_OK) return st;
     if (!p_hat || !al16(p_hat) || p_hat == p_n || p_hat == p_nm1 || p_hat == rho) return FLUPS_EINVAL;
@@ -1104,6 +1105,7 @@ static flups_status pnet_loss(flups_pnet N, const double* rho, double rho0, cons
 
 flups_status flups_pnet_train_step(flups_pnet N, const double* rho, double rho0, const double* p_n,
                                    const double* p_nm1, const double* p_next, float lr, double* loss) {
+    NvtxRange nvtx_("flups_pnet_train_step");
     return pnet_loss(N, rho, rho0, p_n, p_nm1, p_next, 1, lr, loss);
 }
 

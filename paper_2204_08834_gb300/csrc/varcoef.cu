@@ -246,6 +246,7 @@ static void vc_precond(flups_plan P, const double* r, double* z) {
 
 extern "C" flups_status flups_varcoef_solve(flups_plan P, const double* rho, const double* f, double* p, double rtol,
                                             int max_iter, flups_info* info) {
+    NvtxRange nvtx_("flups_varcoef_solve");
     if (!P || !rho || !f || !p || f == p || rho == p) return FLUPS_EINVAL;
     if (((uintptr_t)rho & 15u) || ((uintptr_t)f & 15u) || ((uintptr_t)p & 15u)) return FLUPS_EINVAL;
     if (!(rtol >= 0.0) || max_iter < 1 || max_iter > 100000) return FLUPS_EINVAL;
