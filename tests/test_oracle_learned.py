@@ -1,7 +1,8 @@
 """Pins of the learned-p_hat oracle (CPU): the variable-coefficient solve against a dense
 solve of an independently looped operator and the constant-density limit; the conv net
 against finite differences, periodic shift equivariance and single-tap kernels; Adam against
-its closed form on the first step."""
+its closed form on the first step; the density feature against the split coefficient that
+oracle.correct applies, and the predictor's zero-net limit against oracle.p_hat."""
 
 import numpy as np
 import pytest
@@ -146,3 +147,41 @@ def test_rounded_forward_backward_stay_close_to_fp64():
     assert abs(l1 - l0) <= 2e-2 * l0
     for (a, _), (b, _) in zip(g0, g1):
         assert np.linalg.norm(a - b) <= 5e-2 * np.linalg.norm(a)
+
+
+def test_density_feature_is_the_split_coefficient_of_the_correction():
+    """The density feature (reading L2) is the factor the split puts in front of G p_hat:
+    oracle.correct with p = 0, u** = 0 gives u = (dt/rho0)(1 - rho0/rho_f) G_x p_hat, and at
+    x faces between two cells of equal density that ratio must equal the cells' feature."""
+    n = 8
+    g = oracle.make_grid(n, n, n, 1.0 / n, 1.0 / n, 1.0 / n, "periodic")
+    rho = np.ones((n, n, n))
+    rho[:, :, 2:6] = 3.0                                    # a slab of density 3 in 1
+    rho[:, 5:, 3:5] = 7.0                                   # and a block of density 7 in it
+    x = (np.arange(n) + 0.5) / n
+    ph = np.broadcast_to(np.sin(2 * np.pi * x), (n, n, n)).copy()
+    zero = np.zeros_like(rho)
+    dt = 0.01
+    u1, _, _ = oracle.correct(zero, zero, zero, zero, ph, zero, rho, 1.0, 0.0, dt, g)
+    gx = (np.roll(ph, -1, axis=2) - ph) / g.dx
+    same = (rho == np.roll(rho, -1, axis=2)) & (np.abs(gx) > 1e-3)
+    ratio = u1[same] / (dt / oracle.min_density(rho) * gx[same])
+    feat, _ = L.features(rho, ph, ph, oracle.min_density(rho))
+    assert same.sum() > 100
+    assert np.max(np.abs(ratio - feat[0][same])) < 1e-12
+    assert {round(v, 12) for v in feat[0][same]} == {0.0, round(2 / 3, 12), round(6 / 7, 12)}
+
+
+def test_zero_net_predicts_the_method_extrapolation_and_a_bias_net_adds_s_times_it():
+    """All weights zero: the prediction is the method's own p_hat = 2 p^n - p^{n-1} (Sec. 3.3,
+    constant dt, as oracle.p_hat); a last-layer bias c alone adds s c with s = rms(p^n)."""
+    rng = np.random.default_rng(4)
+    shape = (4, 6, 8)
+    rho = 1.0 + rng.random(shape)
+    pn, pnm1 = rng.standard_normal(shape), rng.standard_normal(shape)
+    layers = [(np.zeros((co, ci, 27)), np.zeros(co)) for ci, co in ((3, 16), (16, 16), (16, 16), (16, 1))]
+    base = oracle.p_hat(pn, pnm1, 2.0, 1.0)
+    assert np.array_equal(L.predict(layers, rho, pn, pnm1, 1.0), base)
+    layers[-1] = (layers[-1][0], np.array([0.25]))
+    s = np.linalg.norm(pn) / np.sqrt(pn.size)
+    assert np.allclose(L.predict(layers, rho, pn, pnm1, 1.0), base + 0.25 * s, rtol=0, atol=1e-14)
