@@ -80,9 +80,10 @@ typedef struct {
 
 /*
  * flups_plan_create - plan a projection on an nx x ny x nz grid (Sec. 3, MAC grid).
- *   nx, ny : even powers of two in [8, 4096] (x, y periodic).
- *   nz     : power of two in [8, 4096] when bc = FLUPS_BC_PERIODIC; any value in
- *            [2, 8192] with bc = FLUPS_BC_WALLS.
+ *   nx, ny : 2^a >= 8, or 3 * 2^a >= 24 and a multiple of 8 (radix-2/4/8 and radix-3
+ *            transforms), at most 4096 (x, y periodic).
+ *   nz     : the same rule when bc = FLUPS_BC_PERIODIC; any value in [2, 8192] with
+ *            bc = FLUPS_BC_WALLS.  nx ny nz < 2^31.
  *            With prec = FLUPS_FP64, ny and a periodic nz are at most 2048.
  *   dx, dy : uniform spacings (> 0).
  *   dzf    : HOST array of nz cell widths along z (> 0), copied; must be uniform when

@@ -49,7 +49,7 @@ def _create(lib, nx, ny, nz, dzf, bc=0, prec=1, dx=0.1, dy=0.1):
 
 
 @pytest.mark.parametrize("nx,ny,nz,bc,want", [
-    (12, 16, 16, 0, flups.EUNSUPPORTED),   # nx not a power of two
+    (12, 16, 16, 0, flups.EUNSUPPORTED),   # nx = 3*4: radix-3 sizes start at 24
     (16, 4, 16, 0, flups.EUNSUPPORTED),    # ny below 8
     (16, 16, 40, 0, flups.EUNSUPPORTED),   # periodic nz must be 2^a or 3*2^a
     (20, 16, 16, 0, flups.EUNSUPPORTED),   # nx = 5*4
