@@ -107,7 +107,7 @@ flups_status flups_plan_create(flups_plan* out, int nx, int ny, int nz, double d
  *              modes cos (Neumann low) or sin (Dirichlet low) of pi (2k+1)(2i+1)/(4n) (DCT-IV,
  *              DST-IV), eigenvalues -4 sin^2(pi (2k+1)/(4n))/h^2.
  *   bc       : the z treatment, as in flups_plan_create.
- A plan with any non-periodic x/y end takes only flups_solve (set_density, rhs, correct and
+ * A plan with any non-periodic x/y end takes only flups_solve (set_density, rhs, correct and
  * the host-buffer projection return FLUPS_EUNSUPPORTED).  Its solve is L p = f when an end is
  * Dirichlet (L is then nonsingular and the mean of f is kept), and L p = f - <f>_V with
  * <p>_V = 0 otherwise.  FLUPS_FP64: one direct pass, residual not evaluated (info->rel_res
