@@ -106,7 +106,7 @@ def peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
-# FP64 pipe peak: 499.3 G DFMA lane-ops/s measured on this machine's GB300 by the committed
+# FP64 pipe peak: 499.3 G DFMA lane-ops/s measured on a GB300 by the committed
 # micro-benchmark (paper_2204_08834_gb300/microbench/peaks.cu) = 0.999 TFLOP/s with FMA = 2.
 FP64_TFLOPS_MEASURED = 0.9986
 
@@ -785,7 +785,7 @@ def main():
     if work["bound"] == "alu":
         achieved = work["flops"] * npts / (dom_ms_per_region * 1e-3) / 1e12
         peak, unit, psrc = FP64_TFLOPS_MEASURED, "TFLOP/s", ("FP64 DFMA rate measured by "
-                                                              "microbench/peaks.cu on this pool")
+                                                              "microbench/peaks.cu on a GB300")
     else:
         achieved = (work["bytes"] or 0) * npts / (dom_ms_per_region * 1e-3) / 1e9
         peak, unit, psrc = pk["hbm_gbs"], "GB/s", f"MEASURED_PEAKS.json hbm_gbs ({pk_kind})"
