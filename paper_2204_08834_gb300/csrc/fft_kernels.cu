@@ -312,7 +312,9 @@ __host__ __device__ __forceinline__ size_t xres_smem(int M) { return (size_t)10 
 // MODE 2: the same defect on a grid with one spacing h in x, y and z: h^2 L p is an integer
 //         combination of the seven p values, summed exactly in 64-bit fixed point (scale
 //         2^(58-E), E from the largest exponent of p recorded when p was written), then
-//         r = (f - <f>) - (2^(E-58)/h^2) S with one conversion and one FMA in FP64.
+//         r = (f - <f>) - (2^(E-58)/h^2) S with one conversion and one FMA in FP64, or, when
+//         h is a power of two, from the exact integer F - MF - S with f and <f> taken to the
+//         same fixed point (no FP64 instruction; see the tiled branch).
 // MODE 3: as MODE 2, but only the partial sums of r^2 (no transform, nothing written): the
 //         stopping test of a refinement that has most likely converged.
 template <typename T, int E, int MODE, bool STATS>
