@@ -131,7 +131,7 @@ unsigned long long flups_launch_count(flups_plan plan);
  * total milliseconds ms[k] and the number of timed regions n[k] (HOST arrays) recorded
  * since the previous read.  flups_kernel_name(k) names kernel id k (static string).
  */
-#define FLUPS_NKERNELS 22
+#define FLUPS_NKERNELS 23
 flups_status flups_set_profiling(flups_plan plan, int on);
 flups_status flups_profile_read(flups_plan plan, double* ms, long long* n);
 const char*  flups_kernel_name(int id);
@@ -149,6 +149,20 @@ flups_status flups_set_density(flups_plan plan, const double* rho, double rho0);
 
 /* flups_get_rho0 - copy rho0 to *rho0_host (HOST); synchronises the plan's stream. */
 flups_status flups_get_rho0(flups_plan plan, double* rho0_host);
+
+/*
+ * flups_plan_sync - wait for every call queued on the plan's stream and return the errors
+ * the device latched meanwhile (no counterpart in the paper; the library's error exit):
+ * FLUPS_ETIMEOUT when a bounded device-side wait gave up (the time-out is cleared once
+ * reported), FLUPS_ENONFINITE when the density registered by flups_set_density holds a
+ * non-finite or non-positive value, FLUPS_ECUDA when the stream reports a CUDA error
+ * (flups_last_cuda_error names it), FLUPS_OK otherwise.
+ */
+flups_status flups_plan_sync(flups_plan plan);
+
+/* flups_last_cuda_error - name of the last CUDA error a call of this thread observed
+ * ("cudaSuccess" if none); a static string. */
+const char* flups_last_cuda_error(void);
 
 /*
  * flups_rhs - right-hand side of the split Poisson equation (Eqs. us_predic + poisson):
@@ -220,20 +234,36 @@ flups_status flups_project_host(flups_plan plan, double* u, double* v, double* w
                                 double* p_out, flups_info* info);
 
 /*
+ * flups_solve_host - flups_solve with HOST buffers (end-to-end form of the solve): copies f
+ * (nz*ny*nx float64) to a plan-owned device buffer (allocated on the first call), solves as
+ * flups_solve, copies p back to p_out.  Host buffers should be page-locked for full copy
+ * bandwidth.  Synchronises the plan's stream before returning (also on error), so no copy
+ * touches the caller's buffers afterwards.  With FLUPS_ENOCONV p_out holds the last iterate.
+ */
+flups_status flups_solve_host(flups_plan plan, const double* f, double* p_out, double rtol, int max_iter,
+                              flups_info* info);
+
+/*
  * flups_solve_fp64_noalloc - the FP64 direct solve of flups_solve (FLUPS_FP64 mode) for
  * callers that cannot allocate device memory, for example a solver plug-in inside a host
  * application that owns and pre-reserves the whole device memory budget, or code running
  * under a memory manager that forbids allocations once a run has started.  The paper has
  * no counterpart to this entry point.
- *   nx, ny, nz, dx, dy, dzf (HOST), bc : as in flups_plan_create; ny and a periodic nz are
- *              at most 2048.
+ *   nx, ny   : powers of two, 8 <= nx <= 4096, 8 <= ny <= 2048 (the 3 * 2^a lengths that
+ *              flups_plan_create also takes are not supported here: FLUPS_EUNSUPPORTED).
+ *   nz       : bc = FLUPS_BC_PERIODIC: a power of two in [8, 2048]; FLUPS_BC_WALLS: any
+ *              value in [2, 8192].
+ *   dx, dy, bc: as in flups_plan_create.
+ *   dzf      : HOST array of nz cell widths as in flups_plan_create; read during the call
+ *              only, so it need not outlive it.
  *   f, p     : DEVICE input and output, as in flups_solve (p may not alias f).
  *   stream   : cudaStream_t (NULL = legacy default stream).
  * No plan is needed and nothing is allocated: the workspace (spectrum, z multipliers,
  * tables) lives in one static device array of FLUPS_NOALLOC_MAX_BYTES that every GPU
  * loading the library holds until exit.  A grid whose workspace does not fit (about
  * 16 MiB: e.g. 64^3 or 128x128x32 periodic fit, 128^3 does not) returns
- * FLUPS_EUNSUPPORTED before any GPU work.  The first call on a device looks up the array's
+ * FLUPS_EUNSUPPORTED before any GPU work.  The first call on a device (and the first call
+ * after that device's context was replaced, e.g. by cudaDeviceReset) looks up the array's
  * device address (cudaGetSymbolAddress) with that device current; make that first call
  * before any stream capture.  Every call reuses the same array, so calls that overlap on
  * the GPU race: serialise them.  Stream-ordered; does not synchronise.

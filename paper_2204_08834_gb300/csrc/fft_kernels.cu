@@ -16,6 +16,7 @@
 #include <cstdlib>
 
 #include "flups_impl.cuh"
+#include "tma_pipe.cuh"
 
 namespace {
 
@@ -1092,37 +1093,9 @@ __global__ void __launch_bounds__(1024) k_zper(typename cplx<T>::t* __restrict__
 // complex = 128 bytes per row, 16-byte aligned) that complete on an mbarrier.  Tile rows are
 // stored with coalesced 128-byte writes.  Every mbarrier wait is bounded: on time-out the
 // CTA records an error and leaves (after a bounded wait for its own copies in flight).
-__device__ __forceinline__ unsigned smem_u32(const void* p) {
-    return (unsigned)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ void mbar_init(unsigned long long* m, unsigned count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(m)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(unsigned long long* m, unsigned bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(m)), "r"(bytes) : "memory");
-}
-// 3-D tiled TMA load of one box of the spectrum (coordinates x = kx, y = ky, z = k).
-__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* tm, int x, int y, int z,
-                                            unsigned long long* m) {
-    asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
-        ::"r"(smem_u32(dst)), "l"(reinterpret_cast<unsigned long long>(tm)), "r"(x), "r"(y), "r"(z),
-          "r"(smem_u32(m)) : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(unsigned long long* m, unsigned parity) {
-    unsigned ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok) : "r"(smem_u32(m)), "r"(parity) : "memory");
-    return ok != 0;
-}
-__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* m, unsigned parity, int limit = 1 << 22) {
-    for (int i = 0; i < limit; ++i)
-        if (mbar_try_wait(m, parity)) return true;
-    return false;
-}
+// The TMA and mbarrier helpers are in tma_pipe.cuh.
 
-// Self-test of the bounded wait above: one thread waits on an mbarrier that nothing ever
+// Self-test of the bounded wait (mbar_wait_bounded): one thread waits on an mbarrier that nothing ever
 // arrives at, gives up after `limit` polls, records err = 3 and returns (no trap, no hang).
 __global__ void k_selftest_wait(int limit, int* __restrict__ err) {
     __shared__ __align__(8) unsigned long long m;
@@ -1510,23 +1483,27 @@ FftLen packed(FftLen L) {
 
 // Tile of the pipelined kernel: B columns with B * N * 8 bytes <= 32 KB, B <= 16, B <= M (tiles
 // small enough for two CTAs per SM, which overlap one's FFT with the other's copies).
-int pipe_lgB(int N, int M) {
+int pipe_lgB(int N, int M, int kind) {
+    const int l4 = cols4_lgB(N, M, kind);      // the four-step kernel's tile where it applies
+    if (l4 >= 0) return l4;
     int B = 16;
     while (B > 1 && ((long)B * N * 8 > 32 * 1024 || B > M)) B >>= 1;
     return ilog2i(B);
 }
 // The pipelined path needs its tensor map (built with the plan), rows of at least 16 bytes
 // (B >= 2) and at most 1024 threads (B N / 8).
-bool pipe_ok(flups_plan P, int N) {
+bool pipe_ok(flups_plan P, int N, int kind) {
     if (!P->tma_ok || (N & (N - 1)) != 0) return false;
-    const int B = 1 << pipe_lgB(N, P->M);
+    if (cols4_lgB(N, P->M, kind) >= 0) return true;
+    const int B = 1 << pipe_lgB(N, P->M, kind);
     return B >= 2 && P->M % B == 0 && (long)B * N / 8 <= 1024 && N >= 8;
 }
 
 template <int KIND, bool INV>
 void run_cols_pipe(flups_plan P, float2* S, const Geo& g, const FftLen& L, const float2* tw) {
+    if (launch_cols4(P, S, g, KIND, INV)) return;     // four-step kernel (cols_kernels.cu)
     const int N = KIND == 0 ? g.ny : g.nz;
-    const int lgB = pipe_lgB(N, g.M), B = 1 << lgB;
+    const int lgB = pipe_lgB(N, g.M, KIND), B = 1 << lgB;
     const size_t sm = 2 * (size_t)N * B * sizeof(float2) + 2 * sizeof(unsigned long long);
     auto kern = k_cols_pipe<KIND, INV>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
@@ -1558,7 +1535,7 @@ void run_ycol_e(flups_plan P, typename cplx<T>::t* S, const Geo& g, bool tail_co
     allow_smem(tail);
     flups_prof_begin(P, sizeof(T) == 4 ? FK_YCOL32 : FK_YCOL64);
     const size_t sm = (size_t)N * (B + 1) * sizeof(C);
-    if (sizeof(T) == 4 && E == 8 && pipe_ok(P, N)) run_cols_pipe<0, INV>(P, (float2*)S, g, L, (const float2*)P->twy);
+    if (sizeof(T) == 4 && E == 8 && pipe_ok(P, N, 0)) run_cols_pipe<0, INV>(P, (float2*)S, g, L, (const float2*)P->twy);
     else kern<<<dim3((g.M + B - 1) / B, g.nz), B * N / E, sm, P->stream>>>(S, g, L, (const C*)P->twy, lgB, 0);
     // the Nyquist column kx = M of every plane, B planes per tile
     if (tail_col) {
@@ -1595,6 +1572,14 @@ void run_zsolve(flups_plan P, typename cplx<T>::t* S, const Geo& g, bool tail_co
     } else {
         const int ncols = g.nxh * g.ny;
         flups_prof_begin(P, sizeof(T) == 4 ? FK_ZTRI32 : FK_ZTRI64);
+        if (sizeof(T) == 4 && !g.xpack) {   // tiles in shared memory, no HBM scratch (cols_kernels.cu)
+            const int n = launch_ztri_tile(P, (float2*)S, g);
+            if (n > 0) {
+                flups_prof_end(P);
+                FLUPS_COUNT(P, n);
+                return;
+            }
+        }
         if (g.xpack)
             k_ztri_packed<T><<<(ncols + 127) / 128, 128, 0, P->stream>>>(S, (T*)P->zscr, g, (const T*)P->lamx,
                                                                        (const T*)P->lamy, (const T*)P->tri);
@@ -1619,7 +1604,7 @@ void run_zper_e(flups_plan P, typename cplx<T>::t* S, const Geo& g, bool tail_co
         allow_smem(kern);
         allow_smem(tail);
         flups_prof_begin(P, sizeof(T) == 4 ? FK_ZPER32 : FK_ZPER64);
-        if (sizeof(T) == 4 && E == 8 && pipe_ok(P, N))
+        if (sizeof(T) == 4 && E == 8 && pipe_ok(P, N, 1))
             run_cols_pipe<1, false>(P, (float2*)S, g, L, (const float2*)P->twz);
         else
             kern<<<dim3((g.M + B - 1) / B, g.ny), B * N / E, (size_t)N * (B + 1) * sizeof(C), P->stream>>>(
@@ -1672,7 +1657,7 @@ void run_xinv_e(flups_plan P, double* p, const Geo& g) {
     const int B = 1 << lgB;
     auto kern = k_xinv<T, E, ACC, MEAN, SUBM>;
     allow_smem(kern);
-    flups_prof_begin(P, sizeof(T) == 4 ? FK_XINV32 : FK_XINV64);
+    flups_prof_begin(P, sizeof(T) == 4 ? (ACC ? FK_XINV_ACC32 : FK_XINV32) : FK_XINV64);
     const int nblk = (nrows + B - 1) / B;
     kern<<<nblk, B * N / E, (size_t)N * (B + 1) * sizeof(C), P->stream>>>(
         (const C*)P->spec, p, g, packed(P->lx), (const C*)P->twx, (const C*)P->twxr, lgB, nrows, P->sc, P->part);
@@ -1697,7 +1682,8 @@ void run_xdct_e(flups_plan P, const double* fin, double* pout, const Geo& g) {
     const int B = 1 << lgB;
     auto kern = k_xdct<T, E, KIND, INV, ACC>;
     allow_smem(kern);
-    flups_prof_begin(P, INV ? (sizeof(T) == 4 ? FK_XINV32 : FK_XINV64) : (sizeof(T) == 4 ? FK_XFWD_F32 : FK_XFWD64));
+    flups_prof_begin(P, INV ? (sizeof(T) == 4 ? (ACC ? FK_XINV_ACC32 : FK_XINV32) : FK_XINV64)
+                             : (sizeof(T) == 4 ? FK_XFWD_F32 : FK_XFWD64));
     // KIND 1, 2: the split twiddles and the quarter-wave table; KIND 3, 4: pre- and post-twiddles
     const C* t1 = KIND >= 3 ? (const C*)P->twqx : (const C*)P->twxr;
     const C* t2 = KIND >= 3 ? (const C*)P->twqx + P->M : (const C*)P->twqx;
@@ -2041,7 +2027,7 @@ cudaError_t launch_xinv32(flups_plan P, double* p, int mode) {
     return cudaGetLastError();
 }
 
-int flups_pipe_lgB(int N, int M) { return pipe_lgB(N, M); }
+int flups_pipe_lgB(int N, int M, int kind) { return pipe_lgB(N, M, kind); }
 
 int flups_default_cta() { return cta_threads(); }
 

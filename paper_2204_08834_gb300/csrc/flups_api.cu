@@ -245,7 +245,7 @@ flups_status sync_scalars(flups_plan P) {
 static const char* kKernelNames[FK_COUNT] = {
     "k_rho_tiles", "k_face_coeffs", "k_rhs", "k_correct", "k_xfwd_f32", "k_xfwd_residual32", "k_ycol32",
     "k_zper32", "k_ztri32", "k_xinv32", "k_finalize", "k_xfwd64", "k_ycol64", "k_zper64", "k_ztri64", "k_xinv64",
-    "k_res64", "k_rho_finalize", "k_mom_umax", "k_momentum", "k_res_ends", "k_xres_norm32"};
+    "k_res64", "k_rho_finalize", "k_mom_umax", "k_momentum", "k_res_ends", "k_xres_norm32", "k_xinv_acc32"};
 
 void flups_prof_begin(flups_plan P, int kid) {
     P->prof_open = 0;
@@ -451,11 +451,15 @@ flups_status flups_plan_create_bc(flups_plan* out, int nx, int ny, int nz, doubl
     P->skip_ptr = nullptr;
     P->cta_cap = flups_default_cta();
     if (prec == FLUPS_FP32_REFINE && !ends) {
-        const int By = 1 << flups_pipe_lgB(ny, P->M), Bz = 1 << flups_pipe_lgB(nz, P->M);
+        const int By = 1 << flups_pipe_lgB(ny, P->M, 0);
+        // z boxes: the periodic column transform's tile, or the walls Thomas kernel's tile
+        const int lw = ztri_tile_lgB(nz);
+        const int Bz = bc == FLUPS_BC_WALLS ? (lw >= 0 ? 1 << lw : 0) : 1 << flups_pipe_lgB(nz, P->M, 1);
         P->tma_ok = make_spec_map(&P->tm_y, P->spec, P->ldS, ny, nz, By, ny < 256 ? ny : 256, 1) &&
-                    (bc == FLUPS_BC_WALLS || make_spec_map(&P->tm_z, P->spec, P->ldS, ny, nz, Bz, 1, nz < 256 ? nz : 256));
+                    (Bz == 0 || make_spec_map(&P->tm_z, P->spec, P->ldS, ny, nz, Bz, 1, nz < 256 ? nz : 256));
     }
     P->hbuf = nullptr;
+    P->hsol = nullptr;
     P->cstream = nullptr;
     for (int q = 0; q < 3; ++q) P->hev[q] = nullptr;
     P->vcbuf = nullptr;
@@ -476,6 +480,7 @@ flups_status flups_plan_destroy(flups_plan P) {
     }
     std::free(P->allocs);
     if (P->hbuf) cudaFree(P->hbuf);
+    if (P->hsol) cudaFree(P->hsol);
     if (P->cstream) {
         cudaStreamSynchronize(P->cstream);
         cudaStreamDestroy(P->cstream);
@@ -614,6 +619,14 @@ flups_status flups_set_density(flups_plan P, const double* rho, double rho0) {
     const flups_status st = cuda_status(launch_set_density(P, rho, rho0));
     if (st == FLUPS_OK) P->density_set = 1;
     return st;
+}
+
+flups_status flups_plan_sync(flups_plan P) {
+    if (!P) return FLUPS_EINVAL;
+    DeviceGuard dg(P->dev);
+    const flups_status st = sync_scalars(P);
+    if (st != FLUPS_OK) return st;
+    return (P->density_set && P->sc_host->bad_rho) ? FLUPS_ENONFINITE : FLUPS_OK;
 }
 
 flups_status flups_get_rho0(flups_plan P, double* rho0_host) {
@@ -818,6 +831,30 @@ flups_status flups_project_host(flups_plan P, double* u, double* v, double* w, c
     const cudaError_t e2 = cudaStreamSynchronize(s);
     if (st != FLUPS_OK) return st;
     return cuda_status(e1 != cudaSuccess ? e1 : e2);
+}
+
+flups_status flups_solve_host(flups_plan P, const double* f, double* p_out, double rtol, int max_iter,
+                              flups_info* info) {
+    NvtxRange nvtx_("flups_solve_host");
+    if (!P || !f || !p_out) return FLUPS_EINVAL;
+    DeviceGuard dg(P->dev);
+    const size_t n = P->npts, b = n * sizeof(double);
+    if (!P->hsol) {
+        if (cudaMalloc(&P->hsol, 2 * b) != cudaSuccess) { cudaGetLastError(); P->hsol = nullptr; return FLUPS_ENOMEM; }
+    }
+    double* df = P->hsol;
+    double* dp = df + n;
+    cudaStream_t s = P->stream;
+    flups_status st = cuda_status(cudaMemcpyAsync(df, f, b, cudaMemcpyHostToDevice, s));
+    if (st == FLUPS_OK) st = flups_solve(P, df, dp, rtol, max_iter, info);
+    if (st == FLUPS_OK || st == FLUPS_ENOCONV) {
+        const flups_status sc = cuda_status(cudaMemcpyAsync(p_out, dp, b, cudaMemcpyDeviceToHost, s));
+        if (st == FLUPS_OK) st = sc;
+    }
+    // No copy touches the caller's buffers after return, whatever the outcome.
+    const cudaError_t e = cudaStreamSynchronize(s);
+    if (st != FLUPS_OK) return st;
+    return cuda_status(e);
 }
 
 }  // extern "C"

@@ -100,7 +100,7 @@ struct Geo {
 enum FlupsKernelId {
     FK_RHO_MINMAX = 0, FK_FACE_COEFFS, FK_RHS, FK_CORRECT, FK_XFWD_F32, FK_XFWD_RES32, FK_YCOL32, FK_ZPER32,
     FK_ZTRI32, FK_XINV32, FK_FINALIZE, FK_XFWD64, FK_YCOL64, FK_ZPER64, FK_ZTRI64, FK_XINV64, FK_RES64,
-    FK_TILE_FLAGS, FK_MOM_UMAX, FK_MOMENTUM, FK_RES_ENDS, FK_XRES_NORM32, FK_COUNT
+    FK_TILE_FLAGS, FK_MOM_UMAX, FK_MOMENTUM, FK_RES_ENDS, FK_XRES_NORM32, FK_XINV_ACC32, FK_COUNT
 };
 
 struct flups_plan_s {
@@ -139,6 +139,7 @@ struct flups_plan_s {
     int density_set;
     // host-buffer (end-to-end) path, allocated on first use
     double* hbuf;                // 8 fields: u v w rho pn pnm1 f p
+    double* hsol;                // host-buffer solve: 2 fields f p (allocated on first use)
     cudaStream_t cstream;        // copies that overlap the plan stream's kernels
     cudaEvent_t hev[3];          // call start, rho copied, every input copied (then: p ready)
     size_t total_bytes;
@@ -205,5 +206,17 @@ cudaError_t launch_residual64_norm(flups_plan P, const double* f, const double* 
 Geo plan_geo(flups_plan P);
 // Remembers the last CUDA error the library observed (flups_last_cuda_error).
 void flups_note_cuda_error(cudaError_t e);
-// Tile width (log2) of the pipelined column passes for length N and M = nx/2 columns.
-int flups_pipe_lgB(int N, int M);
+// Tile width (log2) of the pipelined column passes for length N and M = nx/2 columns (kind 0:
+// y transform, 1: periodic z solve).
+int flups_pipe_lgB(int N, int M, int kind);
+// Four-step FP32 column transforms (cols_kernels.cu): tile width (log2) for length N, or -1
+// where the kernel does not apply; launch_cols4 runs the y transform (kind 0, inv picks the
+// direction) or the periodic z solve (kind 1) on the plan's spectrum and returns false
+// without launching where the kernel does not apply.
+int cols4_lgB(int N, int M, int kind);
+bool launch_cols4(flups_plan P, float2* S, const Geo& g, int kind, bool inv);
+// Walls z solve in FP32 without HBM scratch (cols_kernels.cu): tile width (log2) of its TMA
+// boxes for nz rows, or -1 where it does not apply; launch_ztri_tile returns the number of
+// kernels it launched (0: not applicable, nothing launched).
+int ztri_tile_lgB(int nz);
+int launch_ztri_tile(flups_plan P, float2* S, const Geo& g);

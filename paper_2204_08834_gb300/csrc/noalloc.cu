@@ -25,22 +25,63 @@ namespace {
 
 constexpr int kMaxDevices = 64;
 std::mutex g_noalloc_mu;
-void* g_noalloc_addr[kMaxDevices];   // device address of g_noalloc_scratch, per device
 
-// Host address of the scratch array on the current device, looked up once per device.
+// Device address of g_noalloc_scratch per device, with the id of the context it was looked
+// up in: a context that replaced it (cudaDeviceReset, then any runtime call) may place the
+// array elsewhere, so a changed id repeats the look-up.
+struct ScratchSlot {
+    unsigned long long ctx_id;
+    void* addr;
+};
+ScratchSlot g_noalloc_slot[kMaxDevices];
+
+// Id of the current context through the driver entry points (no link to libcuda); 0 when it
+// cannot be read or no context is current yet.
+unsigned long long current_ctx_id() {
+    typedef CUresult (*GetCurrentFn)(CUcontext*);
+    typedef CUresult (*GetIdFn)(CUcontext, unsigned long long*);
+    static GetCurrentFn get_current = nullptr;
+    static GetIdFn get_id = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void* a = nullptr;
+        void* b = nullptr;
+        cudaDriverEntryPointQueryResult qa, qb;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &a, 12000, cudaEnableDefault, &qa) == cudaSuccess &&
+            qa == cudaDriverEntryPointSuccess &&
+            cudaGetDriverEntryPointByVersion("cuCtxGetId", &b, 12000, cudaEnableDefault, &qb) == cudaSuccess &&
+            qb == cudaDriverEntryPointSuccess) {
+            get_current = (GetCurrentFn)a;
+            get_id = (GetIdFn)b;
+        }
+        cudaGetLastError();
+    }
+    if (!get_current || !get_id) return 0;
+    CUcontext ctx = nullptr;
+    unsigned long long id = 0;
+    if (get_current(&ctx) != CUDA_SUCCESS || !ctx || get_id(ctx, &id) != CUDA_SUCCESS) return 0;
+    return id;
+}
+
+// Set-up of the current device: the device address of the scratch array, looked up with that
+// device current by cudaGetSymbolAddress once per device and context.
 cudaError_t scratch_address(void** out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
     std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (!g_noalloc_addr[dev]) {
+    ScratchSlot& slot = g_noalloc_slot[dev];
+    const unsigned long long id = current_ctx_id();
+    if (!slot.addr || id == 0 || id != slot.ctx_id) {
         void* a = nullptr;
         e = cudaGetSymbolAddress(&a, g_noalloc_scratch);
         if (e != cudaSuccess) return e;
-        g_noalloc_addr[dev] = a;
+        slot.addr = a;
+        slot.ctx_id = current_ctx_id();   // the look-up made the device's context current
     }
-    *out = g_noalloc_addr[dev];
+    *out = slot.addr;
     return cudaSuccess;
 }
 
@@ -126,7 +167,9 @@ __global__ void k_noalloc_tables(NaTables t) {
 size_t up256(size_t b) { return (b + 255) & ~(size_t)255; }
 
 flups_status status_of(cudaError_t e) {
-    return e == cudaSuccess ? FLUPS_OK : FLUPS_ECUDA;
+    if (e == cudaSuccess) return FLUPS_OK;
+    flups_note_cuda_error(e);     // reported by flups_last_cuda_error, as for the plan calls
+    return FLUPS_ECUDA;
 }
 
 }  // namespace

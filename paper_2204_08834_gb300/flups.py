@@ -32,11 +32,12 @@ SYMBOLS = [
     "flups_pnet_create", "flups_pnet_destroy", "flups_pnet_set_params", "flups_pnet_get_params",
     "flups_pnet_get_grads", "flups_pnet_get_adam", "flups_pnet_set_adam", "flups_pnet_predict", "flups_pnet_train_step", "flups_pnet_eval_loss",
     "flups_pnet_launch_count", "flups_pnet_set_profiling", "flups_pnet_profile_read", "flups_pnet_kernel_name",
-    "flups_selftest_wait_timeout", "flups_momentum_predict", "flups_plan_create_bc",
+    "flups_selftest_wait_timeout", "flups_momentum_predict", "flups_plan_create_bc", "flups_plan_sync",
+    "flups_solve_host",
 ]
 PNET_NKERNELS = 6
 PNET_NPARAMS = 15601
-NKERNELS = 22
+NKERNELS = 23
 MOM_PAIR = 0
 MOM_FP64 = 1
 
@@ -78,10 +79,12 @@ def lib():
         L.flups_launch_count.restype = ctypes.c_ulonglong
         L.flups_set_density.argtypes = [P, V, D]
         L.flups_get_rho0.argtypes = [P, ctypes.POINTER(D)]
+        L.flups_plan_sync.argtypes = [P]
         L.flups_rhs.argtypes = [P, V, V, V, V, V, D, D, D, V]
         L.flups_solve.argtypes = [P, V, V, D, I, ctypes.POINTER(Info)]
         L.flups_correct.argtypes = [P, V, V, V, D, D, D, V, V, V]
         L.flups_project_host.argtypes = [P, V, V, V, V, V, V, D, D, D, D, I, V, ctypes.POINTER(Info)]
+        L.flups_solve_host.argtypes = [P, V, V, D, I, ctypes.POINTER(Info)]
         L.flups_solve_fp64_noalloc.argtypes = [I, I, I, D, D, ctypes.POINTER(D), I, V, V, V]
         L.flups_set_profiling.argtypes = [P, I]
         L.flups_profile_read.argtypes = [P, ctypes.POINTER(D), ctypes.POINTER(ctypes.c_longlong)]
@@ -244,6 +247,13 @@ class Plan:
         _check(lib().flups_get_rho0(self._h, ctypes.byref(r)), "flups_get_rho0")
         return r.value
 
+    def sync(self, check=True):
+        """Wait for the plan's stream; raise on (or, with check=False, return) a latched device error."""
+        st = lib().flups_plan_sync(self._h)
+        if check:
+            _check(st, "flups_plan_sync")
+        return st
+
     def rhs(self, u, v, w, pn, pnm1, c1, c2, dt, f):
         _check(lib().flups_rhs(self._h, ptr(u), ptr(v), ptr(w), ptr(pn), ptr(pnm1), float(c1), float(c2),
                                float(dt), ptr(f)), "flups_rhs")
@@ -295,6 +305,14 @@ class Plan:
                                       hptr(pnm1) if pnm1 is not None else None, float(c1), float(c2),
                                       float(dt), float(rtol), int(max_iter), hptr(p_out), ctypes.byref(inf))
         _check(st, "flups_project_host")
+        return inf
+
+    def solve_host(self, f, p_out, rtol=1e-10, max_iter=16, check=True):
+        """flups_solve on HOST numpy arrays f (read) and p_out (written)."""
+        inf = Info()
+        st = lib().flups_solve_host(self._h, hptr(f), hptr(p_out), float(rtol), int(max_iter), ctypes.byref(inf))
+        if check:
+            _check(st, "flups_solve_host")
         return inf
 
 

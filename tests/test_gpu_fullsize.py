@@ -95,3 +95,24 @@ def test_fullsize_two_layer_1024x1024x512():
     rho0 = float(np.min(c.rho))
     fm = fo - oracle.volume_mean(fo, g)
     assert np.linalg.norm(div) * rho0 / c.dt <= 2e-10 * np.linalg.norm(fm)
+
+
+@pytest.mark.parametrize("name", ["emulsion512", "two_layer512x512x256"])
+def test_fullsize_fp64_solve_matches_oracle(name):
+    """The FP64 direct solve at the bench's full sizes (the other half of the headline
+    comparison) against the oracle's direct solve of the same f: relative L2 error <= 1e-11
+    (both are FP64 eigen-expansion solves with different rounding orders)."""
+    c = synth.emulsion(512) if name == "emulsion512" else synth.two_layer(512, 512, 256)
+    g = grid_of(c)
+    fo = oracle.rhs(c.u, c.v, c.w, c.rho, c.pn, c.pnm1, 2.0, 1.0, c.dt, g)
+    f = torch.from_numpy(fo).cuda()
+    p = torch.empty_like(f)
+    with flups.Plan.for_case(c, "fp64") as plan:
+        info = plan.solve(f, p, rtol=1e-12)
+    pg = p.cpu().numpy()
+    del f, p
+    torch.cuda.empty_cache()
+    assert info.rel_res <= 1e-12
+    po = oracle.solve(fo, g)
+    assert np.linalg.norm(pg - po) / np.linalg.norm(po) <= 1e-11
+

@@ -175,6 +175,15 @@ def test_gradients_match_oracle(shape):
         ow, ob = grads_o[li]
         assert np.linalg.norm(gw - ow) <= 1e-2 * np.linalg.norm(ow), li
         assert np.linalg.norm(gb - ob) <= 1e-2 * np.linalg.norm(ob) + 1e-30, li
+        # element by element: every weight and bias gradient within 2 % of the layer's largest
+        # (bf16 operands rounded from FP32 on the GPU and from FP64 in the oracle can round
+        # apart by one bf16 unit, 2^-8, at a few points; the sums over points are FP32 on the
+        # GPU), and the mean difference a tenth of that
+        for what, a, o in (("w", gw, ow), ("b", gb, ob)):
+            scale = np.max(np.abs(o))
+            d = np.abs(np.asarray(a, dtype=np.float64) - o)
+            assert np.max(d) <= 2e-2 * scale + 1e-30, (li, what, np.max(d) / scale)
+            assert np.mean(d) <= 2e-3 * scale + 1e-30, (li, what, np.mean(d) / scale)
 
 
 def test_adam_steps_match_oracle():

@@ -56,6 +56,11 @@ CASES = {
     "per_48x24x96": lambda: synth.random_fields(48, 24, 96, "periodic", seed=97),
     "walls_str_96x48x30": lambda: synth.random_fields(96, 48, 30, "walls", True, seed=98),
     "emulsion48": lambda: synth.emulsion(48, ndrops=6, rmin_cells=2.0, rmax_cells=5.0),
+    # long periodic columns: the four-step column transforms of every length they take
+    # (y 256 and z 512 with 8-column tiles; y 1024 and z 128 with 4-column tiles)
+    "per_16x256x512": lambda: synth.random_fields(16, 256, 512, "periodic", seed=99),
+    "per_8x1024x128": lambda: synth.random_fields(8, 1024, 128, "periodic", seed=100),
+    "per_32x128x1024": lambda: synth.random_fields(32, 128, 1024, "periodic", seed=101),
 }
 _cache = {}
 
@@ -177,6 +182,22 @@ def test_project_host_matches_device_path():
     assert oracle.div_rel(u, v, w, c.u, c.v, c.w, g) <= 1e-12
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp32_refine"])
+def test_solve_host_equals_device_solve(prec):
+    c, g, (fo, po, _, _, _) = case("emulsion64")
+    fh = torch.empty(c.shape, dtype=torch.float64, pin_memory=True).numpy()
+    np.copyto(fh, fo)
+    ph = np.full(c.shape, np.nan)
+    fd = dev(fo)
+    pd = torch.empty_like(fd)
+    with flups.Plan.for_case(c, prec) as plan:
+        i1 = plan.solve_host(fh, ph, rtol=1e-10, max_iter=12)
+        i2 = plan.solve(fd, pd, rtol=1e-10, max_iter=12)
+    assert np.array_equal(ph, host(pd))
+    assert i1.iters == i2.iters
+    assert np.linalg.norm(ph - po) / np.linalg.norm(po) <= (1e-11 if prec == "fp64" else 1e-8)
+
+
 def test_project_host_equals_device_path_bitwise_at_2_24_points():
     """The host-buffer projection (inputs on the plan's copy stream, rho first; p copied back
     while the correction runs) returns the bits of the device-resident sequence, call after
@@ -259,6 +280,10 @@ def test_bad_density_is_reported():
         with pytest.raises(flups.FlupsError) as e:
             plan.rho0()
         assert e.value.status == flups.ENONFINITE
+        # the documented error exit reports the same latched state without reading rho0
+        assert plan.sync(check=False) == flups.ENONFINITE
+        plan.set_density(dev(c.rho))
+        assert plan.sync(check=False) == flups.OK
 
 
 def test_state_errors():
@@ -298,7 +323,10 @@ def test_profiling_reports_every_launched_kernel():
               "k_ycol32", "k_zper32", "k_xinv32"):
         assert k in prof and prof[k][0] > 0.0, k
     assert prof["k_xfwd_residual32"][1] == info.iters
-    assert prof["k_xinv32"][1] == info.iters
+    # the first inverse x pass writes p, each later one adds the correction to it
+    assert info.iters >= 2
+    assert prof["k_xinv32"][1] == 1
+    assert prof["k_xinv_acc32"][1] == info.iters - 1
 
 
 def test_bounded_device_wait_reports_timeout():
