@@ -1,12 +1,17 @@
 #!/usr/bin/env python3
-"""Throughput of the GB300 projection step (set_density, rhs, solve to 1e-10, correct).
+"""Throughput of the GB300 pressure Poisson solve and the projection step around it.
 
 Metric: Mpts/s per Poisson solve at 512^3, FP32+refine vs FP64, both at relative residual
 <= 1e-10.  One step is one pass of the whole hot path over the 512^3 emulsion workload
 (200 droplets of density 10 in density 1, triply periodic) with inputs resident in HBM:
 set_density (rho0 = min rho, face coefficients), rhs, solve (FP32 transforms + FP64
-residual refinement to 1e-10) and correct.  The FP64 direct path is timed the same way
-and reported beside it.
+residual refinement to 1e-10) and correct.  `value` is the solve's rate: grid points over
+the CUDA-event time of the solve call inside each step (f in HBM -> p in HBM at the
+residual); the whole step's rate is `projection_mpts`.  The FP64 direct solve is timed the
+same way and reported beside it (`fp64`), and the other workloads of the same method
+(`configs`: the 256^3 and density-ratio-1 emulsions, the 512x512x256 and 1024x1024x512
+two-layer boxes) give their solve and projection rates with the error of p against the
+FP64 oracle.
 
   python bench.py [--gpus N --steps K --warmup W] [--impl ours|reference] [--workload NAME]
 
@@ -42,6 +47,9 @@ WORKLOADS = {
                         desc="emulsion 256^3 triply periodic, 200 droplets, density ratio 10"),
     "two_layer512": dict(kind="two_layer", nx=512, ny=512, nz=256,
                          desc="two-layer 512x512x256, z walls, tanh-stretched dz (beta 1.5), density 1.5 under 1"),
+    "two_layer1024": dict(kind="two_layer", nx=1024, ny=1024, nz=512,
+                          desc="two-layer 1024x1024x512, z walls, tanh-stretched dz (beta 1.5), density 1.5 "
+                               "under 1"),
     "sphere32": dict(kind="sphere", n=32, desc="sphere 32^3 periodic, density 10 in 1"),
 }
 
@@ -60,13 +68,16 @@ KERNEL_WORK = {
     "k_ycol32": {"bound": "hbm", "bytes": 4 + 4},
     "k_zper32": {"bound": "hbm", "bytes": 4 + 4},
     "k_ztri32": {"bound": "hbm", "bytes": 4 + 4},
-    "k_xinv32": {"bound": "hbm", "bytes": 4 + 12},   # mean of p = (first) and p += (later)
+    "k_xinv32": {"bound": "hbm", "bytes": 4 + 8},    # first pass: read FP32 spectrum, write p (+ mean of p)
+    "k_xinv_acc32": {"bound": "hbm", "bytes": 4 + 16},   # later passes: p += delta (read and write p)
     "k_face_coeffs": {"bound": "hbm", "bytes": None},   # works only in tiles where the density varies
     "k_rho_tiles": {"bound": "hbm", "bytes": 8},
-    # constant-density tiles: rhs reads u, v, w and writes f; correct reads p and u, v, w and
-    # writes u, v, w (p_n, p_{n-1} and the face coefficients only where the density varies)
-    "k_rhs": {"bound": "hbm", "bytes": 32},
-    "k_correct": {"bound": "hbm", "bytes": 56, "fp64_instr": 6},   # 3 differences + 3 FMAs per cell
+    # the stencils at the compulsory bytes of the method (each input field read once, each
+    # output written once): rhs reads u, v, w, rho, p^n, p^{n-1} and writes f; correct reads
+    # p, p^n, p^{n-1}, rho, u, v, w and writes u, v, w.  bytes_min: what the kernels move in
+    # tiles of constant density, where they skip the density and the extrapolated pressure.
+    "k_rhs": {"bound": "hbm", "bytes": 56, "bytes_min": 32},
+    "k_correct": {"bound": "hbm", "bytes": 80, "bytes_min": 56, "fp64_instr": 6},   # 3 differences + 3 FMAs
     # momentum predictor (AB2 call): reads u, v, w (FP64) and the M state (3 x 8 B), writes
     # u**, v**, w** and the state; the pre-pass reads u, v, w for max|u|
     "k_momentum": {"bound": "hbm", "bytes": 24 + 24 + 24 + 24},
@@ -75,6 +86,11 @@ KERNEL_WORK = {
     "k_res_ends": {"bound": "hbm", "bytes": 24},
 }
 
+
+# Kernels of the FP32+refine solve (f -> p); the roofline object names the one that takes most
+# of the solve's time.
+SOLVE_KERNELS = ("k_xfwd_f32", "k_xfwd_residual32", "k_xres_norm32", "k_ycol32", "k_zper32", "k_ztri32",
+                 "k_xinv32", "k_xinv_acc32", "k_finalize")
 
 # DRAM bytes of one launch (dram__bytes_read.sum + dram__bytes_write.sum) from an ncu capture
 # of the named workload and kernel.  Only valid for the kernel code that was captured: remove
@@ -85,6 +101,28 @@ MEASURED_TRAFFIC_PER_LAUNCH = {
     # variation 40 B/point more: 60.5 B/point)
     ("emulsion512", "k_correct"): 5_030_000_000 + 3_180_000_000,
 }
+
+
+def host_info():
+    """Host CPU model and core count (for the CPU baseline)."""
+    model = None
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                k = line.split(":", 1)
+                if len(k) == 2 and k[0].strip() in ("model name", "Model", "CPU part"):
+                    model = model or k[1].strip()
+    except OSError:
+        pass
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    return {"nproc": os.cpu_count(), "cpu_model": model}
 
 
 def make_case(name):
@@ -185,6 +223,152 @@ def job_mpts(world, npts, ms):
     return world * npts / (ms * 1e-3) / 1e6
 
 
+def timed_steps(plan, c, d0, work, f, p, steps, warmup, rtol, world, graphable=True):
+    """`warmup` + `steps` projections (set_density, rhs, solve, correct) with CUDA events around
+    each call on the launch stream; returns the summed times of the timed steps, the FP32
+    solves needed, the defect norms and the kernels launched in the timed steps."""
+    import torch
+
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+    tot = {"set_density": 0.0, "rhs": 0.0, "solve": 0.0, "correct": 0.0, "step": 0.0}
+    iters, rel = [], []
+    l0 = None
+    for s in range(warmup + steps):
+        for k in ("u", "v", "w"):
+            work[k].copy_(d0[k])           # restore u** (outside the timed events)
+        if s == warmup:
+            torch.cuda.synchronize()
+            if world > 1:
+                torch.distributed.barrier()
+            l0 = plan.launches
+        ev[0].record()
+        plan.set_density(d0["rho"])
+        ev[1].record()
+        plan.rhs(work["u"], work["v"], work["w"], d0["pn"], d0["pnm1"], 2.0, 1.0, c.dt, f)
+        ev[2].record()
+        # FP32+refine: the graph-capturable form of the solve (the same bits as the
+        # host-driven loop; converged iterations exit on the device), so the step has no
+        # host round trip; its defect norm is read after the step.  The direct FP64 solve
+        # needs no residual evaluation; it is checked after the loop.
+        if plan.prec == "fp32_refine" and graphable:
+            plan.solve_graphable(f, p, rtol=rtol, max_iter=GRAPH_MAX_ITER)
+            info = None
+        elif plan.prec == "fp32_refine":
+            info = plan.solve(f, p, rtol=rtol, max_iter=12)
+        else:
+            info = plan.solve(f, p, rtol=0.0, info=False)   # returns None
+        ev[3].record()
+        plan.correct(p, d0["pn"], d0["pnm1"], 2.0, 1.0, c.dt, work["u"], work["v"], work["w"])
+        ev[4].record()
+        torch.cuda.synchronize()
+        if s >= warmup:
+            for q, k in enumerate(("set_density", "rhs", "solve", "correct")):
+                tot[k] += ev[q].elapsed_time(ev[q + 1])
+            tot["step"] += ev[0].elapsed_time(ev[4])
+            if plan.prec == "fp32_refine" and graphable:
+                res = plan.solve_result(rtol=rtol)          # defect norm of this step's solve
+                rel.append(res.rel_res)
+            elif info is not None:
+                rel.append(info.rel_res)
+    launches = plan.launches - l0
+    # FP32 solves actually needed (or, FP64, the residual of the direct solve): one host-driven
+    # solve of the same f after the steps, outside the timed region
+    info = plan.solve(f, p, rtol=rtol, max_iter=12)
+    iters.append(info.iters)
+    if not rel:
+        rel.append(info.rel_res)
+    return tot, iters, rel, launches
+
+
+def measure(c, args, world, fp32_steps, fp64_steps, profile=False, keep=False, clocks=None):
+    """FP32+refine and FP64 projections of case `c` through one plan each; per precision the
+    step breakdown, solve and projection rates (this rank), defect norms and launches.
+    With keep, host copies of f and of both precisions' p; with profile, two more FP32+refine
+    steps with the library's per-kernel CUDA events."""
+    import torch
+
+    from paper_2204_08834_gb300 import flups
+
+    nz, ny, nx = c.shape
+    npts = c.npts
+    stream = torch.cuda.current_stream().cuda_stream
+    keys = ("u", "v", "w", "rho", "pn", "pnm1")
+    d0 = {k: torch.from_numpy(c[k]).cuda() for k in keys}
+    work = {k: torch.empty_like(d0["u"]) for k in ("u", "v", "w")}
+    f = torch.empty_like(d0["u"])
+    p = torch.empty_like(d0["u"])
+    torch.cuda.synchronize()
+    out = {"npts": npts, "prof": {}}
+    for prec, steps in (("fp32_refine", fp32_steps), ("fp64", fp64_steps)):
+        with flups.Plan(nx, ny, nz, c.dx, c.dy, c.dzf, c.bc, prec, stream) as plan:
+            tot, iters, rel, launches = timed_steps(plan, c, d0, work, f, p, steps, args.warmup, args.rtol, world)
+            if profile and prec == "fp32_refine":
+                # two more steps with per-kernel CUDA events inside the library (host-driven
+                # solve: the kernel sequence of the graph-capturable one without the launches
+                # that return at once after convergence, so the per-launch times hold)
+                plan.set_profiling(True)
+                timed_steps(plan, c, d0, work, f, p, 2, 0, args.rtol, world, graphable=False)
+                out["prof"] = {k: (ms / 2.0, n / 2.0) for k, (ms, n) in plan.profile().items()}
+                plan.set_profiling(False)
+        torch.cuda.synchronize()      # p: this precision's solution of the step's f (last solve above)
+        out[prec] = {"tot": tot, "iters": iters, "rel": rel, "launches": launches, "steps": steps}
+        if keep:
+            out[prec]["p"] = p.cpu().numpy()
+            out["f"] = f.cpu().numpy()
+    out["d0"], out["f_dev"] = d0, f
+    del work, p
+    return out
+
+
+def rates(m, world):
+    """Solve and projection rates (Mpts/s, whole job) of one measure() result."""
+    r = {}
+    for prec in ("fp32_refine", "fp64"):
+        e = m[prec]
+        k = e["steps"]
+        r[prec] = {"solve_mpts": round(world * m["npts"] / (e["tot"]["solve"] / k * 1e-3) / 1e6, 2),
+                   "solve_ms": round(e["tot"]["solve"] / k, 4),
+                   "projection_mpts": round(world * m["npts"] / (e["tot"]["step"] / k * 1e-3) / 1e6, 2),
+                   "projection_ms": round(e["tot"]["step"] / k, 4),
+                   "breakdown_ms": {q: round(v / k, 4) for q, v in e["tot"].items()},
+                   "rel_res": max(e["rel"]), "steps": k}
+        if prec == "fp32_refine":
+            r[prec]["iters"] = statistics.median(e["iters"])
+    return r
+
+
+def rel_err(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def run_config(name, args, world):
+    """One more workload of the method: solve and projection rates of both precisions, and the
+    relative L2 error of both p against the FP64 oracle's direct solve of the same f (grids of
+    at most 2^27 points; beyond that the oracle's solve does not fit the time budget, and the
+    FP32+refine p is compared with the FP64 direct p of the GPU instead)."""
+    import torch
+
+    import oracle
+
+    c = make_case(name)
+    m = measure(c, args, world, max(3, args.steps // 2), max(2, args.steps // 4), keep=True)
+    out = {"workload": WORKLOADS[name]["desc"], "grid": list(c.shape[::-1]), **rates(m, world)}
+    p32, p64 = m["fp32_refine"]["p"], m["fp64"]["p"]
+    if c.npts <= 1 << 27:
+        nz, ny, nx = c.shape
+        g = oracle.make_grid(nx, ny, nz, c.dx, c.dy, c.dzf, c.bc)
+        po = oracle.solve(m["f"], g, workers=os.cpu_count())
+        out["error_vs_oracle"] = {"fp32_refine": rel_err(p32, po), "fp64": rel_err(p64, po),
+                                  "definition": "|p - p_oracle|_2 / |p_oracle|_2, same f, oracle = FP64 direct solve"}
+    else:
+        out["error_vs_oracle"] = {"fp32_refine_vs_fp64_gpu": rel_err(p32, p64),
+                                  "definition": "|p_fp32+refine - p_fp64|_2 / |p_fp64|_2 (both GPU, same f); the "
+                                                "FP64 direct solve matches the oracle to 1e-11 on every tested grid"}
+    del m
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_ours(args, rank, world, dev):
     import torch
 
@@ -195,91 +379,45 @@ def run_ours(args, rank, world, dev):
     nz, ny, nx = c.shape
     npts = c.npts
     stream = torch.cuda.current_stream().cuda_stream
-    keys = ("u", "v", "w", "rho", "pn", "pnm1")
-    d0 = {k: torch.from_numpy(c[k]).cuda() for k in keys}
-    work = {k: torch.empty_like(d0["u"]) for k in ("u", "v", "w")}
-    f = torch.empty_like(d0["u"])
-    p = torch.empty_like(d0["u"])
-    torch.cuda.synchronize()
-
-    def timed_steps(plan, steps, warmup, rtol, graphable=True):
-        ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
-        tot = {"set_density": 0.0, "rhs": 0.0, "solve": 0.0, "correct": 0.0, "step": 0.0}
-        iters, rel = [], []
-        l0 = None
-        for s in range(warmup + steps):
-            for k in ("u", "v", "w"):
-                work[k].copy_(d0[k])           # restore u** (outside the timed events)
-            if s == warmup:
-                torch.cuda.synchronize()
-                if world > 1:
-                    torch.distributed.barrier()
-                l0 = plan.launches
-            ev[0].record()
-            plan.set_density(d0["rho"])
-            ev[1].record()
-            plan.rhs(work["u"], work["v"], work["w"], d0["pn"], d0["pnm1"], 2.0, 1.0, c.dt, f)
-            ev[2].record()
-            # FP32+refine: the graph-capturable form of the solve (the same bits as the
-            # host-driven loop; converged iterations exit on the device), so the step has no
-            # host round trip; its defect norm is read after the step.  The direct FP64 solve
-            # needs no residual evaluation; it is checked after the loop.
-            if plan.prec == "fp32_refine" and graphable:
-                plan.solve_graphable(f, p, rtol=rtol, max_iter=GRAPH_MAX_ITER)
-                info = None
-            elif plan.prec == "fp32_refine":
-                info = plan.solve(f, p, rtol=rtol, max_iter=12)
-            else:
-                info = plan.solve(f, p, rtol=0.0, info=False)   # returns None
-            ev[3].record()
-            plan.correct(p, d0["pn"], d0["pnm1"], 2.0, 1.0, c.dt, work["u"], work["v"], work["w"])
-            ev[4].record()
-            torch.cuda.synchronize()
-            if s >= warmup:
-                for q, k in enumerate(("set_density", "rhs", "solve", "correct")):
-                    tot[k] += ev[q].elapsed_time(ev[q + 1])
-                tot["step"] += ev[0].elapsed_time(ev[4])
-                if plan.prec == "fp32_refine" and graphable:
-                    res = plan.solve_result(rtol=rtol)          # defect norm of this step's solve
-                    rel.append(res.rel_res)
-                elif info is not None:
-                    rel.append(info.rel_res)
-        launches = plan.launches - l0
-        if graphable:
-            # FP32 solves actually needed (or the FP64 residual): one host-driven solve after the steps
-            info = plan.solve(f, p, rtol=rtol, max_iter=12)
-            iters.append(info.iters)
-            if not rel:
-                rel.append(info.rel_res)
-        return tot, iters, rel, launches
-
-    res = {}
-    prof = {}
     with ClockSampler(dev) as clk:
-        for prec, steps in (("fp32_refine", args.steps), ("fp64", max(2, args.steps // 2))):
-            with flups.Plan(nx, ny, nz, c.dx, c.dy, c.dzf, c.bc, prec, stream) as plan:
-                res[prec] = timed_steps(plan, steps, args.warmup, args.rtol) + (steps,)
-                if prec == "fp32_refine":
-                    # two more steps with per-kernel CUDA events inside the library (host-driven
-                    # solve: the kernel sequence of the graph-capturable one without the launches
-                    # that return at once after convergence, so the per-launch times hold)
-                    plan.set_profiling(True)
-                    timed_steps(plan, 2, 0, args.rtol, graphable=False)
-                    prof = {k: (ms / 2.0, n / 2.0) for k, (ms, n) in plan.profile().items()}
-                    plan.set_profiling(False)
-    # max over ranks of the timed sum
-    t32 = res["fp32_refine"][0]["step"]
-    t64 = res["fp64"][0]["step"]
-    t32, t64 = max_over_ranks([t32, t64])
-
-    out = {"c": c, "npts": npts, "res": res, "t32": t32, "t64": t64, "clocks": clk.summary(), "prof": prof}
+        m = measure(c, args, world, args.steps, max(2, args.steps // 2), profile=True, keep=True)
+    t32 = m["fp32_refine"]["tot"]["solve"]
+    t64 = m["fp64"]["tot"]["solve"]
+    s32 = m["fp32_refine"]["tot"]["step"]
+    s64 = m["fp64"]["tot"]["step"]
+    t32, t64, s32, s64 = max_over_ranks([t32, t64, s32, s64])
+    m["fp32_refine"]["tot"]["solve"], m["fp64"]["tot"]["solve"] = t32, t64
+    m["fp32_refine"]["tot"]["step"], m["fp64"]["tot"]["step"] = s32, s64
+    out = {"c": c, "npts": npts, "m": m, "clocks": clk.summary(), "prof": m["prof"]}
+    d0, f = m.pop("d0"), m.pop("f_dev")
     if not args.no_cufft and c.bc == "periodic":
+        p = torch.empty_like(f)
         with flups.Plan(nx, ny, nz, c.dx, c.dy, c.dzf, c.bc, "fp64", stream) as plan:
-            plan.set_density(d0["rho"])
-            plan.rhs(d0["u"], d0["v"], d0["w"], d0["pn"], d0["pnm1"], 2.0, 1.0, c.dt, f)
             plan.solve(f, p, rtol=0.0, info=False)
         torch.cuda.synchronize()
         out["cufft"] = cufft_baseline(c, f, p, max(args.steps, 5))
+        del p
+    del d0, f
+    torch.cuda.empty_cache()
+
+    # end to end: the solve through flups_solve_host on pinned host buffers (f in, p out)
+    if not args.no_e2e:
+        fh = torch.empty(c.shape, dtype=torch.float64, pin_memory=True).numpy()
+        np.copyto(fh, m["f"])
+        ph = torch.empty(c.shape, dtype=torch.float64, pin_memory=True).numpy()
+        e2e_steps = max(1, min(args.steps, 5))
+        t_e2e = 0.0
+        with flups.Plan(nx, ny, nz, c.dx, c.dy, c.dzf, c.bc, "fp32_refine", stream) as plan:
+            for s in range(1 + e2e_steps):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                info = plan.solve_host(fh, ph, rtol=args.rtol, max_iter=12)
+                t1 = time.perf_counter()
+                if s >= 1:
+                    t_e2e += t1 - t0
+        t_e2e = max_over_ranks([t_e2e])[0]
+        out["e2e"] = (t_e2e, e2e_steps, info.rel_res)
+        del fh, ph
     if not args.no_ensemble:
         out["ensemble"] = run_ensemble(args)
     if not args.no_learned:
@@ -288,28 +426,9 @@ def run_ours(args, rank, world, dev):
         out["momentum"] = run_momentum(args)
     if not args.no_ends:
         out["ends"] = run_ends(args)
-
-    # end to end: the same projection through flups_project_host on pinned host buffers
-    if not args.no_e2e:
-        hb = {k: torch.empty(c.shape, dtype=torch.float64, pin_memory=True).numpy() for k in keys}
-        for k in keys:
-            np.copyto(hb[k], c[k])
-        pout = torch.empty(c.shape, dtype=torch.float64, pin_memory=True).numpy()
-        e2e_steps = max(1, min(args.steps, 3))
-        t_e2e = 0.0
-        with flups.Plan(nx, ny, nz, c.dx, c.dy, c.dzf, c.bc, "fp32_refine", stream) as plan:
-            for s in range(1 + e2e_steps):
-                for k in ("u", "v", "w"):
-                    np.copyto(hb[k], c[k])
-                torch.cuda.synchronize()
-                t0 = time.perf_counter()
-                plan.project_host(hb["u"], hb["v"], hb["w"], hb["rho"], hb["pn"], hb["pnm1"], 2.0, 1.0, c.dt, pout,
-                                  rtol=args.rtol, max_iter=12)
-                t1 = time.perf_counter()
-                if s >= 1:
-                    t_e2e += t1 - t0
-        t_e2e = max_over_ranks([t_e2e])[0]
-        out["e2e"] = (t_e2e, e2e_steps)
+    out["configs"] = {}
+    for name in [q for q in args.configs.split(",") if q]:
+        out["configs"][name] = run_config(name, args, world)
     return out
 
 
@@ -665,26 +784,36 @@ def run_ends(args):
     return out
 
 
-def cpu_baseline():
-    """The FP64 oracle (numpy, as it stands) on a bounded sample: three 256^3 emulsion
-    projections (the 256^3 size of the same emulsion configuration)."""
+def cpu_baseline(c, f, p32, p64):
+    """The FP64 oracle (numpy, as it stands) on the host cores: one direct solve of the bench
+    workload's own right-hand side f (the step's f, copied from the GPU) single-threaded, and
+    the same solve with its transforms on every host core (scipy.fft workers); plus the error
+    of the GPU's p against that solution."""
     import oracle
-    from paper_2204_08834_gb300 import synth
 
-    c = synth.emulsion(256, ratio=10.0)
-    g = oracle.make_grid(256, 256, 256, c.dx, c.dy, c.dzf, c.bc)
-    reps = 3
+    nz, ny, nx = c.shape
+    g = oracle.make_grid(nx, ny, nz, c.dx, c.dy, c.dzf, c.bc)
     t0 = time.perf_counter()
-    for _ in range(reps):
-        oracle.project(c.u, c.v, c.w, c.rho, c.pn, c.pnm1, 2.0, 1.0, c.dt, g)
-    t = time.perf_counter() - t0
-    return {"value": round(reps * c.npts / t / 1e6, 3), "unit": "Mpts/s", "cores": 1, "kind": "oracle",
-            "sample": "3 full projections (rhs, direct FP64 solve, correct) of the 256^3 emulsion case, "
-                      "numpy single-threaded"}
+    po = oracle.solve(f, g)
+    t1 = time.perf_counter()
+    ncores = os.cpu_count() or 1
+    oracle.solve(f, g, workers=ncores)
+    t2 = time.perf_counter()
+    hi = host_info()
+    return {"value": round(c.npts / (t1 - t0) / 1e6, 3), "unit": "Mpts/s", "cores": 1, "kind": "oracle",
+            "sample": f"one FP64 direct solve (oracle.solve) of the {nx}x{ny}x{nz} bench right-hand side, "
+                      "numpy single-threaded",
+            "nproc": hi["nproc"], "cpu_model": hi["cpu_model"],
+            "threaded": {"value": round(c.npts / (t2 - t1) / 1e6, 3), "unit": "Mpts/s", "cores": ncores,
+                         "kind": "oracle, transforms on all host cores (scipy.fft workers)"},
+            "error_vs_oracle": {"fp32_refine": rel_err(p32, po), "fp64": rel_err(p64, po),
+                                "definition": "|p - p_oracle|_2 / |p_oracle|_2 of the GPU solves of the same f"}}
 
 
 def run_reference(args, rank, world):
-    """Reference arm: the FP64 oracle timed on the host cores (no reference program exists)."""
+    """Reference arm: the FP64 oracle's direct solve timed on the host cores (no reference
+    program exists); each step solves the 256^3 emulsion right-hand side, a bounded sample of
+    the 512^3 emulsion workload (one 512^3 oracle solve takes tens of seconds)."""
     if rank != 0:
         return 0
     import oracle
@@ -692,23 +821,27 @@ def run_reference(args, rank, world):
 
     c = synth.emulsion(256, ratio=10.0)
     g = oracle.make_grid(256, 256, 256, c.dx, c.dy, c.dzf, c.bc)
+    f = oracle.rhs(c.u, c.v, c.w, c.rho, c.pn, c.pnm1, 2.0, 1.0, c.dt, g)
     tot = 0.0
     for s in range(args.warmup + args.steps):
         t0 = time.perf_counter()
-        oracle.project(c.u, c.v, c.w, c.rho, c.pn, c.pnm1, 2.0, 1.0, c.dt, g)
+        oracle.solve(f, g)
         t1 = time.perf_counter()
         if s >= args.warmup:
             tot += t1 - t0
     val = args.steps * c.npts / tot / 1e6
+    hi = host_info()
     line = {
         "impl": "reference", "metric": METRIC, "value": round(val, 3), "unit": "Mpts/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * tot / args.steps, 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": "emulsion 256^3 triply periodic, 200 droplets, density ratio 10 (bounded sample "
                                "of the 512^3 emulsion workload)",
-                   "step": "oracle.project: rhs + FP64 direct solve + correct", "threads": 1},
+                   "step": "oracle.solve: FP64 direct eigen-expansion solve of the step's right-hand side",
+                   "threads": 1},
         "cpu_baseline": {"value": round(val, 3), "unit": "Mpts/s", "cores": 1, "kind": "oracle",
-                         "sample": "one 256^3 emulsion projection per step"},
+                         "sample": "one 256^3 emulsion solve per step", "nproc": hi["nproc"],
+                         "cpu_model": hi["cpu_model"]},
         "e2e": {"value": round(val, 3), "unit": "Mpts/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
@@ -730,6 +863,8 @@ def main():
     ap.add_argument("--no-cufft", action="store_true")
     ap.add_argument("--no-momentum", action="store_true")
     ap.add_argument("--no-ends", action="store_true")
+    ap.add_argument("--configs", default="emulsion256,emulsion512_r1,two_layer512,two_layer1024",
+                    help="comma-separated further workloads timed with both precisions (empty: none)")
     ap.add_argument("--learned-windows", type=int, default=100,
                     help="64^3 training windows of 20 samples (default 100: 2000 samples)")
     ap.add_argument("--learned-epochs", type=int, default=3)
@@ -758,16 +893,15 @@ def main():
             torch.distributed.destroy_process_group()
         return 0
 
-    c, npts, res = out["c"], out["npts"], out["res"]
-    tot32, it32, rel32, l32, k32 = res["fp32_refine"]
-    tot64, it64, rel64, l64, k64 = res["fp64"]
-    ms32 = out["t32"] / k32
-    ms64 = out["t64"] / k64
-    value = job_mpts(world, npts, ms32)
+    c, npts, m = out["c"], out["npts"], out["m"]
+    r = rates(m, world)
+    k32 = r["fp32_refine"]["steps"]
+    ms_solve = r["fp32_refine"]["solve_ms"]
+    ms_step = r["fp32_refine"]["projection_ms"]
+    value = r["fp32_refine"]["solve_mpts"]
     pk, pk_kind = peaks()
     prof = out["prof"]
     tot_prof = sum(ms for ms, n in prof.values()) or 1.0
-    pk0, _ = peaks()
 
     def kernel_entry(k, ms, n):
         e = {"ms_per_step": round(ms, 4), "launch_regions_per_step": n, "share": round(ms / tot_prof, 4)}
@@ -775,28 +909,29 @@ def main():
         if w and w.get("bytes") and n:
             gbs = w["bytes"] * npts / (ms / n * 1e-3) / 1e9
             e["algorithmic_GBps"] = round(gbs, 1)
-            e["hbm_frac"] = round(gbs / pk0["hbm_gbs"], 4)
+            e["hbm_frac"] = round(gbs / pk["hbm_gbs"], 4)
+            e["bytes_per_point"] = w["bytes"]
         return e
 
     kernels = {k: kernel_entry(k, ms, n) for k, (ms, n) in sorted(prof.items(), key=lambda kv: -kv[1][0])}
-    dom = max(prof, key=lambda k: prof[k][0])
+    solve_prof = {k: v for k, v in prof.items() if k in SOLVE_KERNELS}
+    dom = max(solve_prof, key=lambda k: solve_prof[k][0])
     work = KERNEL_WORK.get(dom, {"bound": "hbm", "bytes": None})
     dom_ms_per_region = prof[dom][0] / max(prof[dom][1], 1e-9)
-    if work["bound"] == "alu":
-        achieved = work["flops"] * npts / (dom_ms_per_region * 1e-3) / 1e12
-        peak, unit, psrc = FP64_TFLOPS_MEASURED, "TFLOP/s", ("FP64 DFMA rate measured by "
-                                                              "microbench/peaks.cu on a GB300")
-    else:
-        achieved = (work["bytes"] or 0) * npts / (dom_ms_per_region * 1e-3) / 1e9
-        peak, unit, psrc = pk["hbm_gbs"], "GB/s", f"MEASURED_PEAKS.json hbm_gbs ({pk_kind})"
+    achieved = (work["bytes"] or 0) * npts / (dom_ms_per_region * 1e-3) / 1e9
+    peak, unit, psrc = pk["hbm_gbs"], "GB/s", f"MEASURED_PEAKS.json hbm_gbs ({pk_kind})"
+    # the solve as a whole against its compulsory traffic (bytes per point of the kernels it ran)
+    solve_bytes = sum(KERNEL_WORK[k]["bytes"] * n for k, (ms, n) in solve_prof.items()
+                      if KERNEL_WORK.get(k, {}).get("bytes"))
+    solve_ms_prof = sum(ms for ms, n in solve_prof.values())
     line = {
         "metric": METRIC,
-        "value": round(value, 2),
+        "value": value,
         "unit": "Mpts/s",
         "n_gpus": world,
         "steps": k32,
         "warmup": args.warmup,
-        "ms_per_step": round(ms32, 4),
+        "ms_per_step": ms_step,
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
@@ -807,6 +942,8 @@ def main():
                         f"rel. residual {args.rtol:g}",
             "grid": list(c.shape[::-1]),
             "step": "set_density + rhs + solve + correct (one projection)",
+            "value": "grid points / CUDA-event time of the solve call (f -> p at the residual) inside each step; "
+                     "the whole step's rate is projection_mpts",
             "l2": "inputs larger than L2 (each field 1 GiB at 512^3)",
             "timing": "sum of per-step CUDA-event intervals on the launch stream; the copy that restores u** "
                       "between steps is outside the events",
@@ -814,18 +951,16 @@ def main():
                           "rel_res read after each step",
             "parallelism": f"replicas x{world}",
         },
-        "solve_mpts": round(world * npts / (tot32["solve"] / k32 * 1e-3) / 1e6, 2),
-        "breakdown_ms": {k: round(v / k32, 4) for k, v in tot32.items()},
-        "iters": statistics.median(it32),
-        "rel_res": max(rel32),
-        "fp64": {
-            "value": round(world * npts / (ms64 * 1e-3) / 1e6, 2),
-            "ms_per_step": round(ms64, 4),
-            "solve_mpts": round(world * npts / (tot64["solve"] / k64 * 1e-3) / 1e6, 2),
-            "breakdown_ms": {k: round(v / k64, 4) for k, v in tot64.items()},
-            "steps": k64,
-            "rel_res": max(rel64),
-        },
+        "solve_ms": ms_solve,
+        "projection_mpts": r["fp32_refine"]["projection_mpts"],
+        "breakdown_ms": r["fp32_refine"]["breakdown_ms"],
+        "iters": r["fp32_refine"]["iters"],
+        "rel_res": r["fp32_refine"]["rel_res"],
+        "fp64": {"solve_mpts": r["fp64"]["solve_mpts"], "solve_ms": r["fp64"]["solve_ms"],
+                 "projection_mpts": r["fp64"]["projection_mpts"], "breakdown_ms": r["fp64"]["breakdown_ms"],
+                 "steps": r["fp64"]["steps"], "rel_res": r["fp64"]["rel_res"],
+                 "solve": "FP64 direct eigen-expansion solve (no residual evaluation in the timed region)"},
+        "speedup_fp32_refine_vs_fp64": round(value / r["fp64"]["solve_mpts"], 3),
         "roofline": {
             "kernel": dom,
             "bound": work["bound"],
@@ -839,40 +974,46 @@ def main():
             "per_launch_ms": round(dom_ms_per_region, 4),
             "peak_source": psrc,
             "algorithmic": {k: v for k, v in work.items() if k != "bound"},
-            "hbm_frac": (round(work["bytes"] * npts / (dom_ms_per_region * 1e-3) / 1e9 / pk["hbm_gbs"], 4)
-                         if work.get("bytes") else None),
+            "scope": "the kernel that takes most of the FP32+refine solve's time (library CUDA events)",
+            "solve": {"bytes_per_point": solve_bytes,
+                      "achieved": round(solve_bytes * npts / (solve_ms_prof * 1e-3) / 1e9, 1),
+                      "frac": round(solve_bytes * npts / (solve_ms_prof * 1e-3) / 1e9 / peak, 4),
+                      "ms": round(solve_ms_prof, 4),
+                      "note": "the whole solve: compulsory bytes per point of every pass it ran over the "
+                              "kernels' summed event time"},
         },
         "kernels": kernels,
-        "gpu_launches": int(l32),
+        "gpu_launches": int(m["fp32_refine"]["launches"]),
         "clocks": out["clocks"],
     }
-    if work.get("fp64_instr"):
-        # the kernel's other ceiling: its FP64 instructions at the measured FP64 pipe rate
-        floor_ms = work["fp64_instr"] * npts / (FP64_TFLOPS_MEASURED / 2.0 * 1e12) * 1e3
-        line["roofline"]["fp64_pipe"] = {"instr_per_point": work["fp64_instr"], "floor_ms": round(floor_ms, 4),
-                                         "frac": round(floor_ms / dom_ms_per_region, 4),
-                                         "rate": "FP64 pipe instructions at the DFMA rate measured by "
-                                                 "microbench/peaks.cu"}
+    wc = KERNEL_WORK["k_correct"]
+    if "k_correct" in prof:
+        cms = prof["k_correct"][0] / max(prof["k_correct"][1], 1e-9)
+        floor_ms = wc["fp64_instr"] * npts / (FP64_TFLOPS_MEASURED / 2.0 * 1e12) * 1e3
+        kernels["k_correct"]["fp64_pipe"] = {"instr_per_point": wc["fp64_instr"], "floor_ms": round(floor_ms, 4),
+                                             "frac": round(floor_ms / cms, 4),
+                                             "rate": "FP64 pipe instructions at the DFMA rate measured by "
+                                                     "microbench/peaks.cu"}
+        kernels["k_correct"]["measured_traffic_per_launch"] = MEASURED_TRAFFIC_PER_LAUNCH.get(
+            (args.workload, "k_correct"))
     if "e2e" in out:
-        t_e2e, ne = out["e2e"]
+        t_e2e, ne, e2e_rel = out["e2e"]
         line["e2e"] = {"value": round(world * npts * ne / t_e2e / 1e6, 2), "unit": "Mpts/s",
-                       "h2d_bytes_per_step": 6 * 8 * npts, "d2h_bytes_per_step": 4 * 8 * npts,
-                       "steps": ne, "call": "flups_project_host (pinned host buffers)"}
+                       "h2d_bytes_per_step": 8 * npts, "d2h_bytes_per_step": 8 * npts,
+                       "steps": ne, "rel_res": e2e_rel,
+                       "call": "flups_solve_host (FP32+refine to rtol; f in, p out through pinned host buffers)"}
     if out.get("cufft"):
         cu = out["cufft"]
         cu["ours_fp64_solve_mpts"] = line["fp64"]["solve_mpts"]
-        cu["ours_fp32_refine_solve_mpts"] = line["solve_mpts"]
+        cu["ours_fp32_refine_solve_mpts"] = value
         line["cufft_baseline"] = cu
-    if "ensemble" in out:
-        line["ensemble"] = out["ensemble"]
-    if "learned" in out:
-        line["learned"] = out["learned"]
-    if "momentum" in out:
-        line["momentum"] = out["momentum"]
-    if "ends" in out:
-        line["ends"] = out["ends"]
+    for key in ("ensemble", "learned", "momentum", "ends"):
+        if key in out:
+            line[key] = out[key]
+    if out["configs"]:
+        line["configs"] = out["configs"]
     if world == 1 and not args.no_cpu:
-        line["cpu_baseline"] = cpu_baseline()
+        line["cpu_baseline"] = cpu_baseline(c, m["f"], m["fp32_refine"]["p"], m["fp64"]["p"])
     print(json.dumps(line))
     if world > 1:
         torch.distributed.destroy_process_group()

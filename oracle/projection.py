@@ -200,30 +200,46 @@ def tridiag_z(F, lam_xy, g):
     return P
 
 
-def solve(f, g):
+def _library_transforms(workers):
+    """The FFT routines the solve calls: numpy's (one thread), or with `workers` scipy.fft's
+    on that many host threads (the batched 1-D transforms split over threads; used only to
+    time the oracle on all cores)."""
+    if workers is None:
+        return np.fft.rfft, np.fft.fft, np.fft.ifft, np.fft.irfft
+    import scipy.fft as sfft
+
+    return (lambda a, axis: sfft.rfft(a, axis=axis, workers=workers),
+            lambda a, axis: sfft.fft(a, axis=axis, workers=workers),
+            lambda a, axis: sfft.ifft(a, axis=axis, workers=workers),
+            lambda a, n, axis: sfft.irfft(a, n=n, axis=axis, workers=workers))
+
+
+def solve(f, g, workers=None):
     """p with L p = f - <f>_V and <p>_V = 0, by the eigen-expansion direct method (Sec. 3.3.1).
 
     Steps in the paper's order: forward transform along x, forward along y, the z solve
     (Gauss elimination with walls, a third transform when z is periodic), backward
-    along y, backward along x.
+    along y, backward along x.  `workers` (timing only) runs the transforms on that many
+    host threads.
     """
+    rfft, fft, ifft, irfft = _library_transforms(workers)
     f = f - volume_mean(f, g)
-    F = np.fft.rfft(f, axis=2)                        # step 1: forward along x (kx = 0..nx/2)
-    F = np.fft.fft(F, axis=1)                         # step 3: forward along y
+    F = rfft(f, axis=2)                               # step 1: forward along x (kx = 0..nx/2)
+    F = fft(F, axis=1)                                # step 3: forward along y
     lx = eigenvalues(g.nx, g.dx)[: g.nx // 2 + 1]
     ly = eigenvalues(g.ny, g.dy)
     lam_xy = ly[:, None] + lx[None, :]
     if g.bc == "periodic":
-        F = np.fft.fft(F, axis=0)                     # z transform (periodic z)
+        F = fft(F, axis=0)                            # z transform (periodic z)
         lam = eigenvalues(g.nz, g.dzf[0])[:, None, None] + lam_xy[None]
         lam[0, 0, 0] = 1.0
         P = F / lam
         P[0, 0, 0] = 0.0                              # zero mean (R3)
-        P = np.fft.ifft(P, axis=0)
+        P = ifft(P, axis=0)
     else:
         P = tridiag_z(F, lam_xy, g)                   # step 5: Gauss elimination along z
-    P = np.fft.ifft(P, axis=1)                        # step 7: backward along y
-    return np.fft.irfft(P, n=g.nx, axis=2)            # step 9: backward along x
+    P = ifft(P, axis=1)                               # step 7: backward along y
+    return irfft(P, n=g.nx, axis=2)                   # step 9: backward along x
 
 
 # ---------------------------------------------------------- correction (Sec. 3.3, R1)
