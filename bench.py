@@ -100,6 +100,9 @@ MEASURED_TRAFFIC_PER_LAUNCH = {
     # (61.2 B/point; constant-density tiles take 56 B/point, the 11.2 % of tiles with density
     # variation 40 B/point more: 60.5 B/point)
     ("emulsion512", "k_correct"): 5_030_000_000 + 3_180_000_000,
+    # the fused defect + forward x pass (MODE 2, integer defect): 540 MB read + 119 MB written
+    # per launch on 512x128x512 (19.7 B/point against 20 algorithmic), scaled by points to 512^3
+    ("emulsion512", "k_xfwd_residual32"): 2_640_000_000,
 }
 
 
@@ -223,7 +226,7 @@ def job_mpts(world, npts, ms):
     return world * npts / (ms * 1e-3) / 1e6
 
 
-def timed_steps(plan, c, d0, work, f, p, steps, warmup, rtol, world, graphable=True):
+def timed_steps(plan, c, d0, work, f, p, steps, warmup, rtol, world, graphable=True, final_solve=True):
     """`warmup` + `steps` projections (set_density, rhs, solve, correct) with CUDA events around
     each call on the launch stream; returns the summed times of the timed steps, the FP32
     solves needed, the defect norms and the kernels launched in the timed steps."""
@@ -273,10 +276,11 @@ def timed_steps(plan, c, d0, work, f, p, steps, warmup, rtol, world, graphable=T
     launches = plan.launches - l0
     # FP32 solves actually needed (or, FP64, the residual of the direct solve): one host-driven
     # solve of the same f after the steps, outside the timed region
-    info = plan.solve(f, p, rtol=rtol, max_iter=12)
-    iters.append(info.iters)
-    if not rel:
-        rel.append(info.rel_res)
+    if final_solve:
+        info = plan.solve(f, p, rtol=rtol, max_iter=12)
+        iters.append(info.iters)
+        if not rel:
+            rel.append(info.rel_res)
     return tot, iters, rel, launches
 
 
@@ -307,7 +311,7 @@ def measure(c, args, world, fp32_steps, fp64_steps, profile=False, keep=False, c
                 # solve: the kernel sequence of the graph-capturable one without the launches
                 # that return at once after convergence, so the per-launch times hold)
                 plan.set_profiling(True)
-                timed_steps(plan, c, d0, work, f, p, 2, 0, args.rtol, world, graphable=False)
+                timed_steps(plan, c, d0, work, f, p, 2, 0, args.rtol, world, graphable=False, final_solve=False)
                 out["prof"] = {k: (ms / 2.0, n / 2.0) for k, (ms, n) in plan.profile().items()}
                 plan.set_profiling(False)
         torch.cuda.synchronize()      # p: this precision's solution of the step's f (last solve above)
@@ -920,10 +924,12 @@ def main():
     dom_ms_per_region = prof[dom][0] / max(prof[dom][1], 1e-9)
     achieved = (work["bytes"] or 0) * npts / (dom_ms_per_region * 1e-3) / 1e9
     peak, unit, psrc = pk["hbm_gbs"], "GB/s", f"MEASURED_PEAKS.json hbm_gbs ({pk_kind})"
-    # the solve as a whole against its compulsory traffic (bytes per point of the kernels it ran)
+    # the solve as a whole against its compulsory traffic (bytes per point of the passes it ran,
+    # per solve: the first forward x pass runs once per solve)
+    nsolve = max(solve_prof.get("k_xfwd_f32", (0.0, 1.0))[1], 1e-9)
     solve_bytes = sum(KERNEL_WORK[k]["bytes"] * n for k, (ms, n) in solve_prof.items()
-                      if KERNEL_WORK.get(k, {}).get("bytes"))
-    solve_ms_prof = sum(ms for ms, n in solve_prof.values())
+                      if KERNEL_WORK.get(k, {}).get("bytes")) / nsolve
+    solve_ms_prof = sum(ms for ms, n in solve_prof.values()) / nsolve
     line = {
         "metric": METRIC,
         "value": value,
@@ -969,13 +975,14 @@ def main():
             "unit": unit,
             "frac": round(achieved / peak, 4),
             "traffic": MEASURED_TRAFFIC_PER_LAUNCH.get((args.workload, dom)),
-            "traffic_note": ("bytes per launch: ncu DRAM read + write of this workload's launch"
+            "traffic_note": ("bytes per launch: ncu DRAM read + write (dram__bytes_read.sum + "
+                             "dram__bytes_write.sum), see MEASURED_TRAFFIC_PER_LAUNCH"
                              if (args.workload, dom) in MEASURED_TRAFFIC_PER_LAUNCH else None),
             "per_launch_ms": round(dom_ms_per_region, 4),
             "peak_source": psrc,
             "algorithmic": {k: v for k, v in work.items() if k != "bound"},
             "scope": "the kernel that takes most of the FP32+refine solve's time (library CUDA events)",
-            "solve": {"bytes_per_point": solve_bytes,
+            "solve": {"bytes_per_point": round(solve_bytes, 2),
                       "achieved": round(solve_bytes * npts / (solve_ms_prof * 1e-3) / 1e9, 1),
                       "frac": round(solve_bytes * npts / (solve_ms_prof * 1e-3) / 1e9 / peak, 4),
                       "ms": round(solve_ms_prof, 4),

@@ -13,7 +13,8 @@
 // transform) needs two exchanges in all and ends in the layout it was loaded in.
 //
 // Tiles of B consecutive kx columns by N rows arrive by TMA (tma_pipe.cuh) in one of two
-// shared-memory buffers of a persistent CTA while the other tile is transformed.  Once a
+// shared-memory buffers of a persistent CTA while the other tile is transformed; the twiddle
+// table W_N^j (and, for the z solve, the eigenvalues along z) is staged in shared memory once.  Once a
 // tile sits in registers its buffer is the exchange area: column c at offset c xp, entry
 // (k1, n2) at k1 (N2 + 1) + n2, with xp chosen so that neither exchange has bank conflicts.
 // Results go from registers straight to HBM, B consecutive complex values per row.
@@ -201,7 +202,11 @@ __global__ void __launch_bounds__(N1 * N2 == 256 ? 256 : 128, N1 * N2 == 256 ? 2
     const int tiles_x = g.M >> lgB;
     const int ntiles = tiles_x * (KIND == 0 ? g.nz : g.ny);
     const unsigned tile_bytes = (unsigned)(N * B * sizeof(float2));
-    unsigned long long* mbar = reinterpret_cast<unsigned long long*>(smc + 2 * (size_t)buf_bytes);
+    // after the two buffers: the twiddles W_N^j and (z solve) the eigenvalues lam_z, staged once
+    float2* tws = reinterpret_cast<float2*>(smc + 2 * (size_t)buf_bytes);
+    float* lzs = reinterpret_cast<float*>(tws + N);
+    unsigned long long* mbar = reinterpret_cast<unsigned long long*>(smc + 2 * (size_t)buf_bytes +
+                                                                    (size_t)N * (KIND == 1 ? 12 : 8));
     const int tid = threadIdx.x;
     const int c = tid & (B - 1), t = tid >> lgB;
 
@@ -227,6 +232,10 @@ __global__ void __launch_bounds__(N1 * N2 == 256 ? 256 : 128, N1 * N2 == 256 ? 2
         mbar_init(&mbar[0], 1);
         mbar_init(&mbar[1], 1);
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    for (int j = tid; j < N; j += blockDim.x) {
+        tws[j] = __ldg(&tw[j]);
+        if (KIND == 1) lzs[j] = __ldg(&lamz[j]);
     }
     __syncthreads();
     unsigned parity[2] = {0u, 0u};
@@ -257,7 +266,7 @@ __global__ void __launch_bounds__(N1 * N2 == 256 ? 256 : 128, N1 * N2 == 256 ? 2
 #pragma unroll
             for (int k1 = 1; k1 < N1; ++k1) {
                 idx = (idx + t) & (N - 1);
-                v[k1] = tmul<FWD_INV>(v[k1], __ldg(&tw[idx]));
+                v[k1] = tmul<FWD_INV>(v[k1], tws[idx]);
             }
         }
         float2* X = s + c * xp;
@@ -283,7 +292,7 @@ __global__ void __launch_bounds__(N1 * N2 == 256 ? 256 : 128, N1 * N2 == 256 ? 2
             for (int q = 0; q < Q; ++q) {
 #pragma unroll
                 for (int k2 = 0; k2 < N2; ++k2) {
-                    const float lam = lxy + __ldg(&lamz[t + N2 * q + N1 * k2]);
+                    const float lam = lxy + lzs[t + N2 * q + N1 * k2];
                     const float inv = lam != 0.f ? rcp_approx(lam) : 0.f;
                     u[q][k2].x *= inv;
                     u[q][k2].y *= inv;
@@ -294,7 +303,7 @@ __global__ void __launch_bounds__(N1 * N2 == 256 ? 256 : 128, N1 * N2 == 256 ? 2
 #pragma unroll
                 for (int n2 = 1; n2 < N2; ++n2) {
                     idx = (idx + k1) & (N - 1);
-                    u[q][n2] = tmul<true>(u[q][n2], __ldg(&tw[idx]));
+                    u[q][n2] = tmul<true>(u[q][n2], tws[idx]);
                 }
             }
             __syncthreads();                   // every thread has read the first exchange
@@ -336,7 +345,7 @@ cudaError_t launch_k(flups_plan P, float2* S, const Geo& g, int lgB) {
     const size_t xbytes = (size_t)B * xp * sizeof(float2);
     if (xbytes > bytes) bytes = xbytes;
     const unsigned buf_bytes = (unsigned)((bytes + 127) / 128 * 128);
-    const size_t sm = 2 * (size_t)buf_bytes + 2 * sizeof(unsigned long long);
+    const size_t sm = 2 * (size_t)buf_bytes + (size_t)N * (KIND == 1 ? 12 : 8) + 2 * sizeof(unsigned long long);
     const int threads = B * N2;
     auto kern = k_cols4<N1, N2, KIND, INV>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
