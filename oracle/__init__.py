@@ -7,6 +7,9 @@ nothing from the product package; only `tests/`, `__graft_entry__.smoke()` and t
 `cpu_baseline` / `--impl reference` legs of `bench.py` may import it.  The product
 path never calls it and has no CPU fallback.
 
+The volume-of-fluid step (MTHINC reconstruction and directional-split advection, Sec. 3.1
+and Appendix A) is in oracle/vof.py (`from oracle import vof`).
+
 Pins (see tests/test_oracle_*.py): single Fourier modes against the closed-form
 discrete eigenvalues, a dense (bordered) LU solve of the assembled 7-point
 operator on grids of 8^3 or smaller, brute-force DFT sums for the spectral steps,
