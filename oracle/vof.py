@@ -39,7 +39,9 @@ Readings of what the paper leaves open or prints garbled (V1-V10):
       the same quadrature as V5 (exact along the upwind cell's p over its interval, Gauss over
       the others).  The printed prefactor Delta x~ is the interval length that the Gauss
       weights carry.  F is a fraction of the cell volume, the f/dl of Eq. phi_split.
-  V7  Case: p = x if |n_x| >= |n_y| and |n_x| >= |n_z|, else p = y if |n_y| >= |n_z|, else z.
+  V7  Case: p = x if |n_x| >= |n_y| and |n_x| >= |n_z|, else p = y if |n_y| >= |n_z|, else z,
+      decided on the components of the Youngs gradient m (n = m / |m|, the same comparisons)
+      so that the decision carries no rounding of the normalisation.
   V8  A cell with phi <= eps or phi >= 1 - eps (eps = 1e-8), or with a zero Youngs gradient,
       is uniform: H = phi on the whole cell.
   V9  The splits run in the fixed order x, y, z; n, K and d_th are recomputed from phi^x before
@@ -116,11 +118,13 @@ def curvature(phi):
 
 # ------------------------------------------------------ reconstruction polynomial (App. A.1)
 
-def polynomial(n, K):
-    """Case p (V7) and the coefficients of T (Eqs. qud_fun, q1_comp, q2_comp, l_comp with the
-    flags of V3): T = sum_a q_a x~_a^2 + sum_{a<b} r_ab x~_a x~_b + sum_a L_a x~_a.
+def polynomial(n, K, m=None):
+    """Case p (V7, on the gradient m when given, else on n) and the coefficients of T
+    (Eqs. qud_fun, q1_comp, q2_comp, l_comp with the flags of V3):
+    T = sum_a q_a x~_a^2 + sum_{a<b} r_ab x~_a x~_b + sum_a L_a x~_a.
     Returns (p, q[3], r{(a,b)}, L[3])."""
-    ax_, ay_, az_ = np.abs(n[0]), np.abs(n[1]), np.abs(n[2])
+    v = n if m is None else m
+    ax_, ay_, az_ = np.abs(v[0]), np.abs(v[1]), np.abs(v[2])
     p = np.where((ax_ >= ay_) & (ax_ >= az_), 0, np.where(ay_ >= az_, 1, 2))
     c = [(p != a).astype(np.float64) for a in range(3)]
     q = [c[a] * 0.5 * K[(a, a)] for a in range(3)]
@@ -201,9 +205,10 @@ def reconstruct(phi, beta, eps=EPS_PURE):
     # uniform cells never use T; give them a plane normal to x so that no division by a zero
     # slope occurs in the vectorised quadrature
     n = [np.where(uniform, 1.0 if a == 0 else 0.0, n[a]) for a in range(3)]
+    m = [np.where(uniform, 1.0 if a == 0 else 0.0, m[a]) for a in range(3)]
     K = {k: np.where(uniform, 0.0, v) for k, v in K.items()}
-    p, q, r, L = polynomial(n, K)
-    rec = {"p": p, "q": q, "r": r, "L": L, "n": n, "K": K, "uniform": uniform, "phi": phi}
+    p, q, r, L = polynomial(n, K, m)
+    rec = {"p": p, "q": q, "r": r, "L": L, "n": n, "m": m, "K": K, "uniform": uniform, "phi": phi}
     # bracket: |T| on the unit cell is at most the sum of the coefficients' magnitudes
     tmax = sum(np.abs(q[a]) + np.abs(L[a]) for a in range(3)) + sum(np.abs(v) for v in r.values())
     lo = -tmax - 40.0 / beta
