@@ -84,6 +84,13 @@ KERNEL_WORK = {
     "k_mom_umax": {"bound": "hbm", "bytes": 24},
     # FP64 defect with the ends' ghost rules: reads f, p, writes r (neighbours from caches)
     "k_res_ends": {"bound": "hbm", "bytes": 24},
+    # VoF step (per split): reconstruction reads phi (halo re-reads from L2) and writes the
+    # 32-byte cell record; the flux pass reads the velocity, the upwind record and phi and writes
+    # F; the update reads phi, F, the velocity and writes the stage (the final correction, timed
+    # with the updates, reads three stages and u, v, w and writes phi: 56 B)
+    "k_vof_rec": {"bound": "alu", "bytes": 8 + 32},
+    "k_vof_flux": {"bound": "hbm", "bytes": 8 + 32 + 8 + 8},
+    "k_vof_update": {"bound": "hbm", "bytes": 32},
 }
 
 
@@ -430,6 +437,8 @@ def run_ours(args, rank, world, dev):
         out["momentum"] = run_momentum(args)
     if not args.no_ends:
         out["ends"] = run_ends(args)
+    if not args.no_vof:
+        out["vof"] = run_vof(args)
     out["configs"] = {}
     for name in [q for q in args.configs.split(",") if q]:
         out["configs"][name] = run_config(name, args, world)
@@ -731,6 +740,73 @@ def run_momentum(args):
     return out
 
 
+def run_vof(args):
+    """The VoF step (Sec. 3.1, App. A: MTHINC reconstruction, split advection x, y, z, the
+    divergence correction) on a 256^3 periodic box of 30 droplets (r U[4,12] cells, tanh
+    profile 1.5 cells wide) in the solenoidal single-phase velocity of the momentum leg, CFL
+    0.5, beta_th = 2; time per step with CUDA events, per-kernel times from the library's events,
+    and the change of sum(phi) over the timed steps."""
+    import torch
+
+    from paper_2204_08834_gb300 import flups, synth
+
+    n = 256
+    h = 1.0 / n
+    rng = np.random.default_rng(70)
+    x = np.arange(n) + 0.5
+    phi = np.zeros((n, n, n))
+    for _ in range(30):
+        c = rng.uniform(0, n, 3)
+        rad = rng.uniform(4.0, 12.0)
+        dd = [np.minimum(np.abs(x - c[a]), n - np.abs(x - c[a])) for a in range(3)]
+        r = np.sqrt(dd[0][None, None, :] ** 2 + dd[1][None, :, None] ** 2 + dd[2][:, None, None] ** 2)
+        phi = np.maximum(phi, 0.5 * (1.0 - np.tanh((r - rad) / 0.75)))
+    vel = synth.solenoidal_velocity(n, seed=71)
+    U = max(float(np.max(np.abs(q))) for q in vel)
+    dt = 0.5 * h / U
+    d = torch.from_numpy(phi).cuda()
+    v = [torch.from_numpy(q).cuda() for q in vel]
+    del phi, vel
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with flups.Plan(n, n, n, h, h, np.full(n, h), "periodic", "fp32_refine", torch.cuda.current_stream().cuda_stream) \
+            as plan:
+        for _ in range(args.warmup):
+            plan.vof_step(d, *v, dt, 2.0)
+        torch.cuda.synchronize()
+        m0 = float(d.sum())
+        k = args.steps
+        e0.record()
+        for _ in range(k):
+            plan.vof_step(d, *v, dt, 2.0)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / k
+        m1 = float(d.sum())
+        status = plan.sync(check=False)
+        plan.set_profiling(True)
+        plan.vof_step(d, *v, dt, 2.0)
+        prof = plan.profile()
+        plan.set_profiling(False)
+        lo, hi = float(d.min()), float(d.max())
+    pk, pk_kind = peaks()
+    kern = {}
+    for kk, (kms, cnt) in prof.items():
+        e = {"ms": round(kms, 4), "launches": cnt}
+        w = KERNEL_WORK.get(kk)
+        if w and w.get("bytes") and cnt:
+            per = 3 if kk != "k_vof_update" else 4
+            gbs = w["bytes"] * n ** 3 * per / (kms * 1e-3) / 1e9
+            e["algorithmic_GBps"] = round(gbs, 1)
+            e["hbm_frac"] = round(gbs / pk["hbm_gbs"], 4)
+        kern[kk] = e
+    return {"workload": "VoF step, 256^3 periodic, 30 droplets r U[4,12] cells (tanh profile 1.5 cells), "
+                        "solenoidal velocity (MAC curl of filtered noise), CFL 0.5, beta_th = 2",
+            "ms_per_step": round(ms, 4), "mcells_per_s": round(n ** 3 / (ms * 1e-3) / 1e6, 1), "steps": k,
+            "mass_rel_change": (m1 - m0) / m0, "phi_range": [lo, hi], "status": flups.status_string(status),
+            "kernels": kern,
+            "arithmetic": "reconstruction and fluxes FP32 (d_th by Newton on the volume equation), updates FP64"}
+
+
 def run_ends(args):
     """The Poisson solve in the generality of Sec. 3.3.1: a closed box with homogeneous Neumann
     ends in x and y (cosine series along x and y) and walls in z with tanh-stretched spacing
@@ -867,6 +943,7 @@ def main():
     ap.add_argument("--no-cufft", action="store_true")
     ap.add_argument("--no-momentum", action="store_true")
     ap.add_argument("--no-ends", action="store_true")
+    ap.add_argument("--no-vof", action="store_true")
     ap.add_argument("--configs", default="emulsion256,emulsion512_r1,two_layer512,two_layer1024",
                     help="comma-separated further workloads timed with both precisions (empty: none)")
     ap.add_argument("--learned-windows", type=int, default=100,
@@ -1014,7 +1091,7 @@ def main():
         cu["ours_fp64_solve_mpts"] = line["fp64"]["solve_mpts"]
         cu["ours_fp32_refine_solve_mpts"] = value
         line["cufft_baseline"] = cu
-    for key in ("ensemble", "learned", "momentum", "ends"):
+    for key in ("ensemble", "learned", "momentum", "ends", "vof"):
         if key in out:
             line[key] = out[key]
     if out["configs"]:

@@ -131,7 +131,7 @@ unsigned long long flups_launch_count(flups_plan plan);
  * total milliseconds ms[k] and the number of timed regions n[k] (HOST arrays) recorded
  * since the previous read.  flups_kernel_name(k) names kernel id k (static string).
  */
-#define FLUPS_NKERNELS 23
+#define FLUPS_NKERNELS 26
 flups_status flups_set_profiling(flups_plan plan, int on);
 flups_status flups_profile_read(flups_plan plan, double* ms, long long* n);
 const char*  flups_kernel_name(int id);
@@ -417,6 +417,32 @@ const char* flups_pnet_kernel_name(int id);
 flups_status flups_momentum_predict(flups_plan plan, const double* u, const double* v, const double* w,
                                     double* us, double* vs, double* ws, void* m_state, double nu,
                                     double gx, double gy, double gz, double dt, double dt_prev, int arith);
+
+/*
+ * flups_vof_step - one step of the volume fraction (Sec. 3.1, Eqs. phi_split and vof_corr_step;
+ * Appendix A): MTHINC reconstruction of the interface in every cell,
+ *     H = (1 + tanh(beta (T(x~) + d_th))) / 2,  x~ in [0, 1]^3 the cell's local coordinates,
+ * T the quadratic built from the Youngs normal n and K = grad n (linear along the direction of
+ * the largest normal component, where the cell integral of H is taken exactly; two-point
+ * Gauss-Legendre along the other two), d_th such that the cell integral of H is phi; then the
+ * split updates x, y, z, each with fluxes that integrate H of the upwind cell over the volume
+ * swept through the face in dt, phi^p = (phi^s - (F_{i+1/2} - F_{i-1/2})) /
+ * (1 - dt/h (u_{i+1/2} - u_{i-1/2})), and the divergence correction
+ * phi^{n+1} = phi^z - sum_p dt/h_p phi^p (u_{i+1/2} - u_{i-1/2})_p, which conserves sum(phi).
+ *   plan   : the grid (triply periodic, uniform z spacing, nx, ny, nz multiples of 8)
+ *   phi    : DEVICE [nz][ny][nx] float64, phi^n on entry, phi^{n+1} on return (in place)
+ *   u, v, w: DEVICE face velocities at t^n (layout as for flups_rhs), read only
+ *   dt > 0 with |u| dt / dx <= 1 (likewise v, w); beta > 0 the sharpness beta_th
+ *   stages : DEVICE 3 nz ny nx float64 for phi^x, phi^y, phi^z (or NULL: plan workspace)
+ * Reconstruction and fluxes run in FP32, the updates in FP64 (sum(phi) is conserved to FP64
+ * rounding).  A
+ * face with |u| dt / h > 1 (or a non-finite velocity) is latched and reported by the next
+ * flups_plan_sync as FLUPS_EINVAL (its flux is taken as 0).  Allocates 56 bytes per cell of
+ * plan workspace on the first call.  Stream-ordered, no synchronisation.  Returns
+ * FLUPS_EUNSUPPORTED for walls, ends in x or y, or sizes that are not multiples of 8.
+ */
+flups_status flups_vof_step(flups_plan plan, double* phi, const double* u, const double* v, const double* w,
+                            double dt, double beta, double* stages);
 
 /* flups_selftest_wait_timeout - diagnostic of the library's failure detection (no paper
  * counterpart): launches one kernel whose thread waits, through the same bounded wait the

@@ -40,8 +40,11 @@ Readings of what the paper leaves open or prints garbled (V1-V10):
       the others).  The printed prefactor Delta x~ is the interval length that the Gauss
       weights carry.  F is a fraction of the cell volume, the f/dl of Eq. phi_split.
   V7  Case: p = x if |n_x| >= |n_y| and |n_x| >= |n_z|, else p = y if |n_y| >= |n_z|, else z,
-      decided on the components of the Youngs gradient m (n = m / |m|, the same comparisons)
-      so that the decision carries no rounding of the normalisation.
+      decided on the components of the Youngs gradient m (n = m / |m|, the same comparisons).
+      The paper states no precision; this integer decision (and the zero-gradient test of V8)
+      is taken in binary32 arithmetic, the precision of the GPU kernel, with the operations of
+      youngs() in the same order (youngs_m32), so that both sides decide alike.  n, K and T
+      stay binary64.
   V8  A cell with phi <= eps or phi >= 1 - eps (eps = 1e-8), or with a zero Youngs gradient,
       is uniform: H = phi on the whole cell.
   V9  The splits run in the fixed order x, y, z; n, K and d_th are recomputed from phi^x before
@@ -108,6 +111,25 @@ def youngs(phi):
         for b in range(a, 3):
             K[(a, b)] = 0.5 * (dn[(a, b)] + dn[(b, a)])
     return m, n, K
+
+
+def youngs_m32(phi):
+    """The cell gradient m of youngs() in binary32 arithmetic, the same operations in the same
+    order (phi rounded to binary32 first): the input of the case decision (V7)."""
+    f = phi.astype(np.float32)
+    q = np.float32(0.25)
+    mc = []
+    for a in range(3):
+        d = sh(f, 1, a) - f
+        o1, o2 = [b for b in range(3) if b != a]
+        mc.append(q * (((d + sh(d, 1, o1)) + sh(d, 1, o2)) + sh(sh(d, 1, o1), 1, o2)))
+    m = []
+    for a in range(3):
+        s = mc[a]
+        for b in range(3):
+            s = s + sh(s, -1, b)
+        m.append(s * np.float32(0.125))
+    return m
 
 
 def curvature(phi):
@@ -199,9 +221,10 @@ def cell_volume_of_h(rec, d, beta):
 def reconstruct(phi, beta, eps=EPS_PURE):
     """The MTHINC reconstruction of every cell (App. A.1): uniform mask (V8), case p,
     coefficients of T and d_th (V5, by bisection on the monotone volume equation)."""
-    m, n, K = youngs(phi)
-    mm = np.sqrt(m[0] ** 2 + m[1] ** 2 + m[2] ** 2)
-    uniform = (phi <= eps) | (phi >= 1.0 - eps) | (mm == 0.0)
+    _, n, K = youngs(phi)
+    m = youngs_m32(phi)
+    zero = (m[0] == 0) & (m[1] == 0) & (m[2] == 0)
+    uniform = (phi <= eps) | (phi >= 1.0 - eps) | zero
     # uniform cells never use T; give them a plane normal to x so that no division by a zero
     # slope occurs in the vectorised quadrature
     n = [np.where(uniform, 1.0 if a == 0 else 0.0, n[a]) for a in range(3)]

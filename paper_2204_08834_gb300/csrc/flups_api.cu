@@ -245,7 +245,8 @@ flups_status sync_scalars(flups_plan P) {
 static const char* kKernelNames[FK_COUNT] = {
     "k_rho_tiles", "k_face_coeffs", "k_rhs", "k_correct", "k_xfwd_f32", "k_xfwd_residual32", "k_ycol32",
     "k_zper32", "k_ztri32", "k_xinv32", "k_finalize", "k_xfwd64", "k_ycol64", "k_zper64", "k_ztri64", "k_xinv64",
-    "k_res64", "k_rho_finalize", "k_mom_umax", "k_momentum", "k_res_ends", "k_xres_norm32", "k_xinv_acc32"};
+    "k_res64", "k_rho_finalize", "k_mom_umax", "k_momentum", "k_res_ends", "k_xres_norm32", "k_xinv_acc32",
+    "k_vof_rec", "k_vof_flux", "k_vof_update"};
 
 void flups_prof_begin(flups_plan P, int kid) {
     P->prof_open = 0;
@@ -460,6 +461,7 @@ flups_status flups_plan_create_bc(flups_plan* out, int nx, int ny, int nz, doubl
     }
     P->hbuf = nullptr;
     P->hsol = nullptr;
+    P->vofbuf = nullptr;
     P->cstream = nullptr;
     for (int q = 0; q < 3; ++q) P->hev[q] = nullptr;
     P->vcbuf = nullptr;
@@ -481,6 +483,7 @@ flups_status flups_plan_destroy(flups_plan P) {
     std::free(P->allocs);
     if (P->hbuf) cudaFree(P->hbuf);
     if (P->hsol) cudaFree(P->hsol);
+    if (P->vofbuf) cudaFree(P->vofbuf);
     if (P->cstream) {
         cudaStreamSynchronize(P->cstream);
         cudaStreamDestroy(P->cstream);
@@ -626,6 +629,10 @@ flups_status flups_plan_sync(flups_plan P) {
     DeviceGuard dg(P->dev);
     const flups_status st = sync_scalars(P);
     if (st != FLUPS_OK) return st;
+    if (P->sc_host->vof_bad) {           // reported once, then cleared
+        cudaMemsetAsync(&P->sc->vof_bad, 0, sizeof(int), P->stream);
+        return FLUPS_EINVAL;
+    }
     return (P->density_set && P->sc_host->bad_rho) ? FLUPS_ENONFINITE : FLUPS_OK;
 }
 

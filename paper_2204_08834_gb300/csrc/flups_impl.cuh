@@ -63,6 +63,7 @@ struct DevScalars {
     int    done;        // graph-capturable solve: the defect reached rtol, later iterations skip
     unsigned int fin_count;   // blocks of the running final reduction that have finished
     unsigned int mom_hmax;    // momentum predictor: high word of max(|u|, |v|, |w|)
+    int    vof_bad;     // VoF step: a face had |u| dt / h above 1 (or not finite)
 };
 
 // Geometry and tables handed to kernels by value.
@@ -100,7 +101,8 @@ struct Geo {
 enum FlupsKernelId {
     FK_RHO_MINMAX = 0, FK_FACE_COEFFS, FK_RHS, FK_CORRECT, FK_XFWD_F32, FK_XFWD_RES32, FK_YCOL32, FK_ZPER32,
     FK_ZTRI32, FK_XINV32, FK_FINALIZE, FK_XFWD64, FK_YCOL64, FK_ZPER64, FK_ZTRI64, FK_XINV64, FK_RES64,
-    FK_TILE_FLAGS, FK_MOM_UMAX, FK_MOMENTUM, FK_RES_ENDS, FK_XRES_NORM32, FK_XINV_ACC32, FK_COUNT
+    FK_TILE_FLAGS, FK_MOM_UMAX, FK_MOMENTUM, FK_RES_ENDS, FK_XRES_NORM32, FK_XINV_ACC32,
+    FK_VOF_REC, FK_VOF_FLUX, FK_VOF_UPDATE, FK_COUNT
 };
 
 struct flups_plan_s {
@@ -140,6 +142,7 @@ struct flups_plan_s {
     // host-buffer (end-to-end) path, allocated on first use
     double* hbuf;                // 8 fields: u v w rho pn pnm1 f p
     double* hsol;                // host-buffer solve: 2 fields f p (allocated on first use)
+    void* vofbuf;                // VoF step: cell records, face fluxes, three stages (first use)
     cudaStream_t cstream;        // copies that overlap the plan stream's kernels
     cudaEvent_t hev[3];          // call start, rho copied, every input copied (then: p ready)
     size_t total_bytes;

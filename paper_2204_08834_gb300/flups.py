@@ -33,11 +33,11 @@ SYMBOLS = [
     "flups_pnet_get_grads", "flups_pnet_get_adam", "flups_pnet_set_adam", "flups_pnet_predict", "flups_pnet_train_step", "flups_pnet_eval_loss",
     "flups_pnet_launch_count", "flups_pnet_set_profiling", "flups_pnet_profile_read", "flups_pnet_kernel_name",
     "flups_selftest_wait_timeout", "flups_momentum_predict", "flups_plan_create_bc", "flups_plan_sync",
-    "flups_solve_host",
+    "flups_solve_host", "flups_vof_step",
 ]
 PNET_NKERNELS = 6
 PNET_NPARAMS = 15601
-NKERNELS = 23
+NKERNELS = 26
 MOM_PAIR = 0
 MOM_FP64 = 1
 
@@ -85,6 +85,7 @@ def lib():
         L.flups_correct.argtypes = [P, V, V, V, D, D, D, V, V, V]
         L.flups_project_host.argtypes = [P, V, V, V, V, V, V, D, D, D, D, I, V, ctypes.POINTER(Info)]
         L.flups_solve_host.argtypes = [P, V, V, D, I, ctypes.POINTER(Info)]
+        L.flups_vof_step.argtypes = [P, V, V, V, V, D, D, V]
         L.flups_solve_fp64_noalloc.argtypes = [I, I, I, D, D, ctypes.POINTER(D), I, V, V, V]
         L.flups_set_profiling.argtypes = [P, I]
         L.flups_profile_read.argtypes = [P, ctypes.POINTER(D), ctypes.POINTER(ctypes.c_longlong)]
@@ -306,6 +307,11 @@ class Plan:
                                       float(dt), float(rtol), int(max_iter), hptr(p_out), ctypes.byref(inf))
         _check(st, "flups_project_host")
         return inf
+
+    def vof_step(self, phi, u, v, w, dt, beta=2.0, stages=None):
+        """One VoF step (flups_vof_step): phi (DEVICE float64) updated in place."""
+        _check(lib().flups_vof_step(self._h, ptr(phi), ptr(u), ptr(v), ptr(w), float(dt), float(beta),
+                                    ptr(stages) if stages is not None else None), "flups_vof_step")
 
     def solve_host(self, f, p_out, rtol=1e-10, max_iter=16, check=True):
         """flups_solve on HOST numpy arrays f (read) and p_out (written)."""
