@@ -17,6 +17,7 @@
 
 #include "flups_impl.cuh"
 #include "tma_pipe.cuh"
+#include "fp_bits.cuh"
 
 namespace {
 
@@ -165,41 +166,6 @@ __device__ __forceinline__ void fft_tile(C* s, int pitch, int lgB, const FftLen&
     }
 }
 
-// FP64 -> FP32 with round-to-nearest-even, built from the IEEE-754 binary64/binary32
-// layouts with integer operations only (on GB300 the F2F conversion instruction runs on the
-// narrow FP64 pipe).  Outside the normal binary32 range the result is chosen with integer
-// selects, so no conversion instruction is issued for any lane: |x| < 2^-126 gives a signed
-// zero (binary32 subnormal results are flushed), |x| >= 2^128 and infinities give a signed
-// infinity, NaN gives a quiet NaN.  Rounding up at the top of the range carries into the
-// exponent and gives infinity, as IEEE rounding does.
-__device__ __forceinline__ float d2f_bits(double x) {
-    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-    const unsigned int hi = (unsigned int)(b >> 32);
-    const int e = (int)((hi >> 20) & 0x7FFu);
-    unsigned int r = ((unsigned int)(e - 896) << 23) | ((unsigned int)(b >> 29) & 0x7FFFFFu);
-    const unsigned int rem = (unsigned int)b & 0x1FFFFFFFu;
-    r += (rem > 0x10000000u) | ((rem == 0x10000000u) & (r & 1u));
-    const bool nan = e == 2047 && (b & 0xFFFFFFFFFFFFFull) != 0ull;
-    r = e < 897 ? 0u : r;
-    r = e > 1150 ? (nan ? 0x7FC00000u : 0x7F800000u) : r;
-    return __uint_as_float(r | (hi & 0x80000000u));
-}
-
-// FP32 -> FP64 (exact for normal numbers) from the bit layouts with integer operations only:
-// zero and binary32 subnormals give a signed zero (flushed), infinities and NaNs keep their
-// class (the low mantissa bits of a NaN stay in the low word).
-__device__ __forceinline__ double f2d_bits(float x) {
-    const unsigned int b = __float_as_uint(x);
-    const unsigned int e = (b >> 23) & 0xFFu;
-    const unsigned int sg = b & 0x80000000u;
-    unsigned int hi = sg | ((e + 896u) << 20) | ((b & 0x7FFFFFu) >> 3);
-    unsigned int lo = (b & 7u) << 29;
-    hi = e == 0u ? sg : hi;
-    lo = e == 0u ? 0u : lo;
-    hi = e == 255u ? (sg | 0x7FF00000u | ((b & 0x7FFFFFu) >> 3)) : hi;
-    return __hiloint2double((int)hi, (int)lo);
-}
-
 // x * 2^(58 - E) as a 64-bit integer, truncated toward zero, for |x| < 2^E; sh = 1017 + E.
 // Built from the binary64 layout with integer operations only: the 53-bit significand is
 // placed 5 bits up and shifted right by 5 - (e - sh) >= 0 (a shift of 64 or more gives 0);
@@ -302,8 +268,45 @@ __device__ void block_sum_abc(double a, float b, float c, double* __restrict__ p
 __host__ __device__ __forceinline__ bool xres_tiled(int E, int B, int M, int ny) {
     return E == 8 && B == 8 && M % 32 == 0 && M <= 512 && ny % 8 == 0;
 }
-// Shared memory of that path: B + 2 rows of M fixed-point pairs (16 bytes each).
-__host__ __device__ __forceinline__ size_t xres_smem(int M) { return (size_t)10 * M * 16; }
+// Shared memory of that path: B + 2 rows of M fixed-point pairs (16 bytes each), and the B
+// rows of the plane below.
+__host__ __device__ __forceinline__ size_t xres_smem(int M) { return (size_t)18 * M * 16; }
+// Planes per CTA of the z-marching defect kernel: up to 16, fewer while the grid of
+// (ny / 8) x ceil(nz / kz) CTAs would hold under three waves of two CTAs on each of 152 SMs.
+inline int xres_kz(int ny, int nz) {
+    int kz = 16;
+    while (kz > 1 && (long)(ny / 8) * ((nz + kz - 1) / kz) < 3 * 2 * 152) kz >>= 1;
+    return kz;
+}
+
+// The transform of a tile of B rows (Z in shared memory, pair index n of row c at
+// s[n pitch + c]) and the real-to-complex split into the spectrum rows row0 .. row0+B-1:
+// X_k = A_k + W_nx^k B_k and X_{M-k} = conj(A_k - W_nx^k B_k), k = 0..M/2, with
+// A_k = (Z_k + conj Z_{M-k})/2 and B_k = (Z_k - conj Z_{M-k})/(2i).  All threads take part.
+template <typename T, int E>
+__device__ __forceinline__ void xfwd_tile_out(typename cplx<T>::t* s, int pitch, int lgB, const FftLen& L,
+                                              const typename cplx<T>::t* __restrict__ tw,
+                                              const typename cplx<T>::t* __restrict__ twr,
+                                              typename cplx<T>::t* __restrict__ S, const Geo& g, int row0,
+                                              int nrows) {
+    typedef typename cplx<T>::t C;
+    fft_tile<C, E, false>(s, pitch, lgB, L, tw);
+    const int B = 1 << lgB, M = g.M, H = M / 2 + 1;
+    for (int idx = threadIdx.x; idx < B * H; idx += blockDim.x) {
+        const int c = idx / H, k = idx - c * H;
+        const int row = row0 + c;
+        if (row >= nrows) continue;
+        const C zk = s[k * pitch + c];
+        const C zm = s[(k == 0 ? 0 : M - k) * pitch + c];
+        const T ax = (zk.x + zm.x) * (T)0.5, ay = (zk.y - zm.y) * (T)0.5;
+        const T bxx = (zk.y + zm.y) * (T)0.5, byy = (zm.x - zk.x) * (T)0.5;
+        const C w = __ldg(&twr[k]);
+        const T tx = w.x * bxx - w.y * byy, ty = w.x * byy + w.y * bxx;
+        C* out = S + (size_t)row * g.ldS;
+        out[k] = mk<T>(ax + tx, ay + ty);
+        if (k != M - k) out[M - k] = mk<T>(ax - tx, ty - ay);
+    }
+}
 
 // ------------------------------------------------------------- forward along x (R2C)
 // MODE 0: input f (FP64).  With STATS, also the partial sums
@@ -313,9 +316,8 @@ __host__ __device__ __forceinline__ size_t xres_smem(int M) { return (size_t)10 
 // MODE 2: the same defect on a grid with one spacing h in x, y and z: h^2 L p is an integer
 //         combination of the seven p values, summed exactly in 64-bit fixed point (scale
 //         2^(58-E), E from the largest exponent of p recorded when p was written), then
-//         r = (f - <f>) - (2^(E-58)/h^2) S with one conversion and one FMA in FP64, or, when
-//         h is a power of two, from the exact integer F - MF - S with f and <f> taken to the
-//         same fixed point (no FP64 instruction; see the tiled branch).
+//         r = (f - <f>) - (2^(E-58)/h^2) S with one conversion and one FMA in FP64 (FP32 tiles
+//         of 8 rows with M a multiple of 32 up to 512 and ny % 8 == 0 go to k_xres_zm instead).
 // MODE 3: as MODE 2, but only the partial sums of r^2 (no transform, nothing written): the
 //         stopping test of a refinement that has most likely converged.
 template <typename T, int E, int MODE, bool STATS>
@@ -346,78 +348,7 @@ __global__ void __launch_bounds__(512) k_xfwd(const double* __restrict__ f, cons
     }
     // Every thread handles exactly E elements (nthr = B M / E): compile-time trip counts let
     // the loads of a thread be issued before they are used.
-    if (MODE >= 2 && xres_tiled(E, B, M, g.ny)) {
-        // On a grid whose spacing is a power of two, h^2 (f - <f>) is taken to the same fixed
-        // point as the 7-point sum S (F, MF: truncated, 2^-58 of the scale of p or finer), so
-        // r = 2^(pexp-1080)/h^2 (F - MF - S) needs no FP64 instruction: the integer difference
-        // is exact and is rounded to binary32 once more than the FP64 form's result is, and the
-        // power-of-two scale is exact.  Points whose F would reach 2^61 take the FP64 form.
-        bool ipath = false;
-        int shf = 0;
-        long long mfq = 0;
-        float rscale = 0.f;
-        if (sizeof(T) == 4 && g.h2e != H2E_NONE && sc->pexp < 2047 && sc->pexp - 57 >= 1) {
-            const int es = sc->pexp - 1080 - g.h2e;
-            shf = sh - g.h2e;
-            bool okm;
-            mfq = fixw(mf, shf, okm);
-            ipath = okm && es >= -126 && es <= 60;
-            if (ipath) rscale = __int_as_float((es + 127) << 23);
-        }
-        // B = E rows row0 .. row0+B-1 (consecutive y of one plane), one pair position n = tid
-        // per thread.  The rows and their two y-halo rows are converted to fixed point once into
-        // shared memory (rows 0 .. B+1 = j0-1 .. j0+B): each value then serves as the centre and
-        // as the x and y neighbour of the cells beside it; the z neighbours are converted per
-        // row.  The FFT tile reuses the same shared memory after the stencil.
-        longlong2* Q = reinterpret_cast<longlong2*>(smraw);
-        const int n = tid;
-        const int k = row0 / g.ny, j0 = row0 - k * g.ny;
-        const double2* P2 = reinterpret_cast<const double2*>(p);
-#pragma unroll
-        for (int r = 0; r < E + 2; ++r) {
-            const double2 v = __ldg(P2 + ((size_t)k * g.ny + wrapm(j0 - 1 + r, g.ny)) * M + n);
-            Q[r * M + n] = make_longlong2(fixq(v.x, sh), fixq(v.y, sh));
-        }
-        int km, kp;
-        if (g.walls) { km = k > 0 ? k - 1 : 0; kp = k < g.nz - 1 ? k + 1 : g.nz - 1; }
-        else { km = k == 0 ? g.nz - 1 : k - 1; kp = k + 1 == g.nz ? 0 : k + 1; }
-        const bool hb = !g.walls || k > 0, ht = !g.walls || k < g.nz - 1;
-        const long long nd = 4 + (hb ? 1 : 0) + (ht ? 1 : 0);
-        const int nw_ = n == 0 ? M - 1 : n - 1, ne_ = n + 1 == M ? 0 : n + 1;
-        __syncthreads();
-        C zr[E];
-#pragma unroll
-        for (int c = 0; c < E; ++c) {
-            const size_t jrow = (size_t)j0 + c;
-            const double2 fv = __ldg(reinterpret_cast<const double2*>(f + (size_t)(row0 + c) * nx) + n);
-            const double2 vb = __ldg(P2 + ((size_t)km * g.ny + jrow) * M + n);
-            const double2 vt = __ldg(P2 + ((size_t)kp * g.ny + jrow) * M + n);
-            const longlong2 qc = Q[(c + 1) * M + n], qs = Q[c * M + n], qn = Q[(c + 2) * M + n];
-            const long long qw = Q[(c + 1) * M + nw_].y, qe = Q[(c + 1) * M + ne_].x;
-            long long s0 = qw + qc.y + qs.x + qn.x - nd * qc.x;
-            long long s1 = qc.x + qe + qs.y + qn.y - nd * qc.y;
-            if (hb) { s0 += fixq(vb.x, sh); s1 += fixq(vb.y, sh); }
-            if (ht) { s0 += fixq(vt.x, sh); s1 += fixq(vt.y, sh); }
-            bool ok0 = false, ok1 = false;
-            long long F0 = 0, F1 = 0;
-            if (ipath) {
-                F0 = fixw(fv.x, shf, ok0);
-                F1 = fixw(fv.y, shf, ok1);
-            }
-            if (ok0 && ok1) {
-                zr[c] = mk<T>((T)(rscale * i64_to_f32(F0 - mfq - s0)), (T)(rscale * i64_to_f32(F1 - mfq - s1)));
-            } else {
-                zr[c] = mk<T>(from_double<T>(fma(-cfix, __ll2double_rn(s0), fv.x - mf)),
-                              from_double<T>(fma(-cfix, __ll2double_rn(s1), fv.y - mf)));
-            }
-            acc2 = fmaf((float)zr[c].x, (float)zr[c].x, fmaf((float)zr[c].y, (float)zr[c].y, acc2));
-        }
-        if (MODE == 2) {
-            __syncthreads();              // every Q read is done: the tile may overwrite it
-#pragma unroll
-            for (int c = 0; c < E; ++c) s[n * pitch + c] = zr[c];
-        }
-    } else if (MODE == 0) {
+    if (MODE == 0) {
         double2 fvs[E];
 #pragma unroll
         for (int q = 0; q < E; ++q) {
@@ -522,24 +453,139 @@ __global__ void __launch_bounds__(512) k_xfwd(const double* __restrict__ f, cons
     else if (MODE >= 1) block_sum_abc<false, true, false>(0.0, acc2, 0.f, part);
     if (MODE == 3) return;               // the defect norm only (the stopping test)
     __syncthreads();
-    fft_tile<C, E, false>(s, pitch, lgB, L, tw);
-    // X_k = A_k + W_nx^k B_k and X_{M-k} = conj(A_k - W_nx^k B_k), k = 0..M/2, with
-    // A_k = (Z_k + conj Z_{M-k})/2 and B_k = (Z_k - conj Z_{M-k})/(2i).
-    const int H = M / 2 + 1;
-    for (int idx = tid; idx < B * H; idx += nthr) {
-        const int c = idx / H, k = idx - c * H;
-        const int row = row0 + c;
-        if (row >= nrows) continue;
-        const C zk = s[k * pitch + c];
-        const C zm = s[(k == 0 ? 0 : M - k) * pitch + c];
-        const T ax = (zk.x + zm.x) * (T)0.5, ay = (zk.y - zm.y) * (T)0.5;
-        const T bxx = (zk.y + zm.y) * (T)0.5, byy = (zm.x - zk.x) * (T)0.5;
-        const C w = __ldg(&twr[k]);
-        const T tx = w.x * bxx - w.y * byy, ty = w.x * byy + w.y * bxx;
-        C* out = S + (size_t)row * g.ldS;
-        out[k] = mk<T>(ax + tx, ay + ty);
-        if (k != M - k) out[M - k] = mk<T>(ax - tx, ty - ay);
+    xfwd_tile_out<T, E>(s, pitch, lgB, L, tw, twr, S, g, row0, nrows);
+}
+
+// The FP32 refinement's exact defect on one-spacing grids (MODE 2: with the forward transform
+// of r; MODE 3: the partial sums of r^2 only), marching up through z.  A CTA owns a block of
+// E = 8 consecutive rows j0 .. j0+7 of the planes k0 .. k1-1, one thread per pair position n.
+// The 7-point sum S of p is exact in 64-bit fixed point (fixq at the scale of the largest
+// exponent of p).  On a grid whose spacing is a power of two, h^2 (f - <f>) is taken to the
+// same fixed point (F, MF: truncated, 2^-58 of the scale of p or finer), so
+// r = 2^(pexp-1080)/h^2 (F - MF - S) needs no FP64 instruction: the integer difference is
+// exact and is rounded to binary32 once, and the power-of-two scale is exact.  Points whose F
+// would reach 2^61, and every point when h^2 <f> would, take r = (f - <f>) - cfix S in FP64.
+// Each p is converted to fixed point about once: plane k+1's centre rows are converted, serve
+// as the upper z neighbours of plane k, then move into shared memory (with the two y-halo
+// rows, converted there) as the centre of plane k+1, while the centre of plane k stays in
+// registers as the lower neighbour of plane k+1: 1.25 conversions per point plus one plane
+// per chunk of kz planes (3.25 when every row converts its own z neighbours).  With MODE 2 the
+// transform tile reuses the shared rows after each plane's stencil.  part[b]
+// (b = blockIdx.x + gridDim.x blockIdx.y) takes the block sums of r^2.
+template <int E, int MODE>
+__global__ void __launch_bounds__(512, 1) k_xres_zm(const double* __restrict__ f, const double* __restrict__ p,
+                                                   float2* __restrict__ S, Geo g, FftLen L,
+                                                   const float2* __restrict__ tw, const float2* __restrict__ twr,
+                                                   int kz, const DevScalars* __restrict__ sc,
+                                                   double* __restrict__ part) {
+    static_assert(E == 8, "one pair position per thread over 8 rows");
+    if (g.skip && *g.skip) return;   // graph-capturable solve: this member already converged
+    extern __shared__ __align__(16) unsigned char smraw[];
+    longlong2* Q = reinterpret_cast<longlong2*>(smraw);
+    float2* s = reinterpret_cast<float2*>(smraw);
+    const int M = g.M, n = threadIdx.x, pitch = E + 1;
+    const int j0 = blockIdx.x * E, k0 = blockIdx.y * kz;
+    const int k1 = min(k0 + kz, g.nz);
+    const double mf = sc->mean_f;
+    const int pe_ = sc->pexp, sh = pe_ - 5;
+    double cfix = 0.0;
+    if (pe_ >= 2047) cfix = __longlong_as_double(0x7FF8000000000000LL);           // NaN: p not finite
+    else if (pe_ - 57 >= 1) cfix = __hiloint2double((pe_ - 57) << 20, 0) * g.sx;   // 2^(pexp-1080) / h^2
+    bool ipath = false;
+    int shf = 0;
+    long long mfq = 0;
+    float rscale = 0.f;
+    if (g.h2e != H2E_NONE && pe_ < 2047 && pe_ - 57 >= 1) {
+        const int es = pe_ - 1080 - g.h2e;
+        shf = sh - g.h2e;
+        bool okm;
+        mfq = fixw(mf, shf, okm);
+        ipath = okm && es >= -126 && es <= 60;
+        if (ipath) rscale = __int_as_float((es + 127) << 23);
     }
+    const double2* P2 = reinterpret_cast<const double2*>(p);
+    const double2* F2 = reinterpret_cast<const double2*>(f);
+    const int nw_ = n == 0 ? M - 1 : n - 1, ne_ = n + 1 == M ? 0 : n + 1;
+    auto prow = [&](int k, int j) { return P2 + ((size_t)k * g.ny + j) * M + n; };
+    // LO[c M + n]: the centre of the plane below (thread n alone reads and writes column n)
+    longlong2* LO = Q + (E + 2) * M;
+    // the centre of plane k0 with its y halo into shared memory, the plane below into LO
+#pragma unroll
+    for (int r = 0; r < E + 2; ++r) {
+        const double2 v = __ldg(prow(k0, wrapm(j0 - 1 + r, g.ny)));
+        Q[r * M + n] = make_longlong2(fixq(v.x, sh), fixq(v.y, sh));
+    }
+    {
+        const bool has = !g.walls || k0 > 0;
+        const int kb = k0 == 0 ? g.nz - 1 : k0 - 1;
+#pragma unroll
+        for (int c = 0; c < E; ++c) {
+            longlong2 q = make_longlong2(0, 0);
+            if (has) {
+                const double2 v = __ldg(prow(kb, j0 + c));
+                q = make_longlong2(fixq(v.x, sh), fixq(v.y, sh));
+            }
+            LO[c * M + n] = q;
+        }
+    }
+    float acc2 = 0.f;
+    __syncthreads();
+    for (int k = k0; k < k1; ++k) {
+        const bool hb = !g.walls || k > 0, ht = !g.walls || k < g.nz - 1;
+        const int kt = k + 1 == g.nz ? 0 : k + 1;
+        const long long nd = 4 + (hb ? 1 : 0) + (ht ? 1 : 0);
+        const size_t row0 = (size_t)k * g.ny + j0;
+        // every global load of the plane first (p of plane k+1 with its y halo, f of plane k),
+        // so that one memory latency per plane is exposed
+        double2 pu[E + 2], fv[E];
+#pragma unroll
+        for (int c = 0; c < E; ++c) fv[c] = __ldg(F2 + (row0 + c) * M + n);
+        const bool more = k + 1 < k1;
+#pragma unroll
+        for (int r = 0; r < E + 2; ++r) {
+            pu[r] = make_double2(0.0, 0.0);
+            if ((r >= 1 && r <= E && ht) || more) pu[r] = __ldg(prow(kt, wrapm(j0 - 1 + r, g.ny)));
+        }
+        float2 zr[E];
+#pragma unroll
+        for (int c = 0; c < E; ++c) {
+            const longlong2 qc = Q[(c + 1) * M + n], qs = Q[c * M + n], qn = Q[(c + 2) * M + n];
+            const long long qw = Q[(c + 1) * M + nw_].y, qe = Q[(c + 1) * M + ne_].x;
+            const longlong2 ql = LO[c * M + n];
+            const long long u0 = fixq(pu[c + 1].x, sh), u1 = fixq(pu[c + 1].y, sh);  // 0 for a wall's ghost
+            long long s0 = qw + qc.y + qs.x + qn.x - nd * qc.x + ql.x + u0;
+            long long s1 = qc.x + qe + qs.y + qn.y - nd * qc.y + ql.y + u1;
+            LO[c * M + n] = qc;                // the lower neighbour of plane k+1
+            bool ok0 = false, ok1 = false;
+            long long F0 = 0, F1 = 0;
+            if (ipath) {
+                F0 = fixw(fv[c].x, shf, ok0);
+                F1 = fixw(fv[c].y, shf, ok1);
+            }
+            if (ok0 && ok1) {
+                zr[c] = make_float2(rscale * i64_to_f32(F0 - mfq - s0), rscale * i64_to_f32(F1 - mfq - s1));
+            } else {
+                zr[c] = make_float2(d2f_bits(fma(-cfix, __ll2double_rn(s0), fv[c].x - mf)),
+                                    d2f_bits(fma(-cfix, __ll2double_rn(s1), fv[c].y - mf)));
+            }
+            acc2 = fmaf(zr[c].x, zr[c].x, fmaf(zr[c].y, zr[c].y, acc2));
+        }
+        __syncthreads();                      // every read of plane k's shared rows is done
+        if (MODE == 2) {
+#pragma unroll
+            for (int c = 0; c < E; ++c) s[n * pitch + c] = zr[c];
+            __syncthreads();
+            xfwd_tile_out<float, E>(s, pitch, 3, L, tw, twr, S, g, (int)row0, g.ny * g.nz);
+            __syncthreads();                  // the tile is read out: the rows of plane k+1 may go in
+        }
+        if (more) {
+#pragma unroll
+            for (int r = 0; r < E + 2; ++r) Q[r * M + n] = make_longlong2(fixq(pu[r].x, sh), fixq(pu[r].y, sh));
+            __syncthreads();
+        }
+    }
+    // one partial sum per CTA (block_sum_abc writes part[blockIdx.x * 3 + q]: fold the grid)
+    block_sum_abc<false, true, false>(0.0, acc2, 0.f, part + (size_t)3 * blockIdx.y * gridDim.x);
 }
 
 // ------------------------------------------------------------- inverse along x (C2R)
@@ -1625,6 +1671,20 @@ void run_xfwd_e(flups_plan P, const double* f, const double* p, const Geo& g) {
     typedef typename cplx<T>::t C;
     const int N = g.M, nrows = g.ny * g.nz;
     const bool tiled = MODE >= 2 && xres_tiled(E, E, N, g.ny);
+    if constexpr (MODE >= 2 && E == 8 && sizeof(T) == 4) {
+        if (tiled) {                       // the z-marching form of the tiled defect
+            auto kern = k_xres_zm<E, MODE>;
+            allow_smem(kern);
+            const int kz = xres_kz(g.ny, g.nz);
+            flups_prof_begin(P, MODE == 3 ? FK_XRES_NORM32 : FK_XFWD_RES32);
+            kern<<<dim3(g.ny / E, (g.nz + kz - 1) / kz), N, xres_smem(N), P->stream>>>(
+                f, p, (float2*)P->spec, g, packed(P->lx), (const float2*)P->twx, (const float2*)P->twxr, kz, P->sc,
+                P->part);
+            flups_prof_end(P);
+            FLUPS_COUNT(P, 1);
+            return;
+        }
+    }
     const int lgB = tiled ? 3 : pick_lgB(N, sizeof(C), E, sizeof(T) == 4 ? 32 : 16, nrows, x_cap(g.cta));
     const int B = 1 << lgB;
     auto kern = k_xfwd<T, E, MODE, STATS>;
@@ -1897,7 +1957,10 @@ __global__ void k_add_const(double* __restrict__ a, size_t n, double c) {
 int xfwd_blocks(flups_plan P, int csize, int residual) {
     const int nrows = P->ny * P->nz;
     const int E = P->M % 3 == 0 ? 12 : (P->M >= 8 ? 8 : 4);
-    if (residual && csize == 8 && P->uniform_h && xres_tiled(E, E, P->M, P->ny)) return (nrows + 7) >> 3;
+    if (residual && csize == 8 && P->uniform_h && xres_tiled(E, E, P->M, P->ny)) {
+        const int kz = xres_kz(P->ny, P->nz);
+        return (P->ny / 8) * ((P->nz + kz - 1) / kz);
+    }
     const int lgB = pick_lgB(P->M, csize, E, csize == 8 ? 32 : 16, nrows, x_cap(P->cta_cap));
     return (nrows + (1 << lgB) - 1) >> lgB;
 }

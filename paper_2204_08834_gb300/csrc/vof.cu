@@ -15,8 +15,9 @@
 //                definition, the same operations a binary32 evaluation of the formula performs.
 //                An 8^3 tile of cells shares its 9^3 corner gradients through shared memory.
 //   k_vof_flux   per face i+1/2 along s: the integral of H of the upwind cell over the box swept
-//                in dt (exact along the cell's p, Gauss over the other two intervals), FP32, stored
-//                as one FP64 number per face.
+//                in dt (exact along the cell's p, Gauss over the other two intervals), FP32 (the
+//                swept fraction too), stored as one FP64 number per face; for a uniform upwind
+//                cell phi u dt / h in FP64.
 //   k_vof_update phi^p = (phi^s - (F_{i+1/2} - F_{i-1/2})) / (1 - dt/h (u_{i+1/2} - u_{i-1/2})),
 //                FP64 (the division as a product with a Newton-refined reciprocal).
 // then k_vof_final: phi^{n+1} = phi^z - sum_p dt/h_p phi^p (u_{i+1/2} - u_{i-1/2})_p, FP64.
@@ -25,6 +26,7 @@
 #include <cmath>
 
 #include "flups_impl.cuh"
+#include "fp_bits.cuh"
 
 namespace {
 
@@ -38,14 +40,16 @@ struct VofGeo {
     double dt;
     double h[3];       // dx, dy, dz
     double c[3];       // dt / dx, dt / dy, dt / dz
+    float cf[3];       // the same in FP32 (the flux pass's swept fractions)
     float beta;
 };
 
 // 1/x in FP64 from the binary32 reciprocal refined by two Newton steps (each doubles the
-// correct bits: 24 -> 48 -> beyond 53), five FP64-pipe instructions against an IEEE division's
-// longer sequence on GB300's narrow FP64 pipe; within one unit in the last place of 1/x.
+// correct bits: 24 -> 48 -> beyond 53): four FMAs on GB300's narrow FP64 pipe (the conversions
+// by integer operations), against an IEEE division's longer sequence; within one unit in the
+// last place of 1/x.
 __device__ __forceinline__ double rcp64(double x) {
-    double r = (double)(1.0f / (float)x);
+    double r = f2d_bits(1.0f / d2f_bits(x));
     double e = fma(-x, r, 1.0);
     r = fma(r, e, r);
     e = fma(-x, r, 1.0);
@@ -63,7 +67,7 @@ __device__ __forceinline__ float rcp_approx(float x) {
 
 // The cell record: case p (-1: uniform) and T = q1 x1^2 + q2 x2^2 + r x1 x2 + Lp xp + L1 x1 + L2 x2
 // in the case frame (x1, x2 the two other directions in increasing order), d = d_th.
-struct VofRec {
+struct __align__(16) VofRec {
     float p, q1, q2, r, Lp, L1, L2, d;
 };
 
@@ -302,14 +306,17 @@ __global__ void __launch_bounds__(512) k_vof_flux(const double* __restrict__ phi
     int ix, iy, iz;
     tile_cell(ix, iy, iz);
     const size_t cell = ((size_t)iz * g.ny + iy) * g.nx + ix;
-    const double c = vel[cell] * (s == 0 ? g.c[0] : (s == 1 ? g.c[1] : g.c[2]));
-    if (!(fabs(c) <= 1.0)) {               // CFL above 1 (or not finite) along the split direction
+    // swept fraction c = u dt / h in FP32 (binary64 -> binary32 by integer operations: the flux of
+    // an interface cell is an FP32 quantity, and its path then runs nothing on the narrow FP64
+    // pipe); the CFL test in FP32 too, so a |c| within FP32 rounding above 1 passes as 1
+    const float c = d2f_bits(__ldg(&vel[cell])) * (s == 0 ? g.cf[0] : (s == 1 ? g.cf[1] : g.cf[2]));
+    if (!(fabsf(c) <= 1.f)) {              // CFL above 1 (or not finite) along the split direction
         atomicExch(bad, 1);
         F[cell] = 0.0;
         return;
     }
     size_t up = cell;
-    if (c < 0.0) {                          // the cell above the face
+    if (c < 0.f) {                          // the cell above the face
         int jx = ix, jy = iy, jz = iz;
         if (s == 0) jx = ix + 1 == g.nx ? 0 : ix + 1;
         else if (s == 1) jy = iy + 1 == g.ny ? 0 : iy + 1;
@@ -317,18 +324,24 @@ __global__ void __launch_bounds__(512) k_vof_flux(const double* __restrict__ phi
         up = ((size_t)jz * g.ny + jy) * g.nx + jx;
     }
     const VofRec R = rec[up];
-    const double frac = fabs(c);
-    if (R.p < 0.f) {                        // uniform upwind cell
-        F[cell] = (c >= 0.0 ? 1.0 : -1.0) * __ldg(&phi[up]) * frac;
+    if (R.p < 0.f) {
+        // uniform upwind cell: phi_up u dt / h in FP64 (two products), so that a run of full or
+        // empty cells gives F_{i+1/2} - F_{i-1/2} = phi (c_{i+1/2} - c_{i-1/2}) to FP64 rounding,
+        // the same number the split update divides out, and phi stays in [0, 1] there
+        const double cs = s == 0 ? g.c[0] : (s == 1 ? g.c[1] : g.c[2]);
+        F[cell] = __ldg(&phi[up]) * (__ldg(&vel[cell]) * cs);
         return;
     }
-    const int p = (int)R.p;
-    const int o1 = p == 0 ? 1 : 0, o2 = p == 2 ? 1 : 2;
-    // the swept interval along s, [0, 1] along the two other directions
-    const float slo = c >= 0.0 ? (float)(1.0 - c) : 0.f, shi = c >= 0.0 ? 1.f : (float)(-c);
-    const float v = box_int(R, g.beta, p == s ? slo : 0.f, p == s ? shi : 1.f, o1 == s ? slo : 0.f,
-                            o1 == s ? shi : 1.f, o2 == s ? slo : 0.f, o2 == s ? shi : 1.f);
-    F[cell] = c >= 0.0 ? (double)v : -(double)v;
+    float v;
+    {
+        const int p = (int)R.p;
+        const int o1 = p == 0 ? 1 : 0, o2 = p == 2 ? 1 : 2;
+        // the swept interval along s, [0, 1] along the two other directions
+        const float slo = c >= 0.f ? 1.f - c : 0.f, shi = c >= 0.f ? 1.f : -c;
+        v = box_int(R, g.beta, p == s ? slo : 0.f, p == s ? shi : 1.f, o1 == s ? slo : 0.f, o1 == s ? shi : 1.f,
+                    o2 == s ? slo : 0.f, o2 == s ? shi : 1.f);
+    }
+    F[cell] = f2d_bits(c >= 0.f ? v : -v);
 }
 
 // phi^p = (phi^s - (F_{i+1/2} - F_{i-1/2})) / (1 - dt/h (u_{i+1/2} - u_{i-1/2})).
@@ -405,7 +418,10 @@ extern "C" flups_status flups_vof_step(flups_plan P, double* phi, const double* 
     g.nx = P->nx; g.ny = P->ny; g.nz = P->nz;
     g.dt = dt;
     g.h[0] = P->dx; g.h[1] = P->dy; g.h[2] = P->dz0;
-    for (int a = 0; a < 3; ++a) g.c[a] = dt / g.h[a];
+    for (int a = 0; a < 3; ++a) {
+        g.c[a] = dt / g.h[a];
+        g.cf[a] = (float)g.c[a];
+    }
     g.beta = (float)beta;
     const double* vel[3] = {u, v, w};
     const dim3 rgrid(P->nx / VT, P->ny / VT, P->nz / VT);

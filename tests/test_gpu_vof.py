@@ -5,13 +5,16 @@ Each split is compared with the oracle's split of the same input: phi^x with the
 split of phi^n, phi^y with its y split of the GPU's phi^x, phi^z with its z split of the GPU's
 phi^y, and phi^{n+1} with the correction formula on the GPU's stages.  Both sides then
 reconstruct from identical arrays, and both take the case decision (the largest Youngs
-gradient component) in FP64 from sums in the same order, so the integer decision agrees.
+gradient component) and the uniform-cell test in binary32 from sums rounded in the same order,
+so the integer decisions agree.
 Tolerance of a split (derived from the arithmetic): the GPU's reconstruction and fluxes run in
 FP32; a flux is a fraction of a cell volume at most |c| <= 1, so each face flux carries about
 1e-6 of rounding (FP32 d_th solve, softplus differences of arguments up to ~40), i.e. at most
 a few 1e-6 on phi per split; 2e-5 absolute bounds it, with a mean below 5e-7.  The FP64
 updates conserve sum(phi) to rounding for any velocity; zero velocity leaves phi unchanged
 bit for bit; a CFL of exactly 1 shifts phi by one cell up to the FP32 cell integral (5e-6).
+A full (or empty) domain stays full (empty) to FP64 rounding under a discretely solenoidal
+velocity: the flux of a uniform cell is phi u dt / h in FP64, the number the update divides out.
 """
 
 import numpy as np
@@ -110,6 +113,16 @@ def test_zero_velocity_and_cfl_one():
     out, _, _ = gpu_step(phi, [one, -one, one], 1.0, 1.0, 2.0)
     ref = np.roll(np.roll(np.roll(phi, 1, axis=2), -1, axis=1), 1, axis=0)
     assert np.max(np.abs(out - ref)) <= 5e-6
+
+
+def test_full_and_empty_domains_stay_so():
+    vel = solenoidal((24, 16, 32), 13, 0.45, 1.0, 1.0)
+    for val in (0.0, 1.0):
+        phi = np.full((24, 16, 32), val)
+        out, st, status = gpu_step(phi, vel, 1.0, 1.0, 2.0)
+        assert status == flups.OK
+        assert np.max(np.abs(out - val)) <= 1e-13, val
+        assert np.max(np.abs(st - val)) <= 1e-13, val
 
 
 def test_cfl_above_one_is_reported():
