@@ -11,7 +11,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libflups.so")
-SOURCES = ["flups_api.cu", "fft_kernels.cu", "cols_kernels.cu", "stencil_kernels.cu", "noalloc.cu", "batch.cu", "varcoef.cu", "pnet.cu", "momentum.cu", "vof.cu"]
+SOURCES = ["flups_api.cu", "fft_kernels.cu", "cols_kernels.cu", "xrow_kernels.cu", "stencil_kernels.cu", "noalloc.cu", "batch.cu", "varcoef.cu", "pnet.cu", "momentum.cu", "vof.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]
 

@@ -18,6 +18,8 @@
 #include "flups_impl.cuh"
 #include "tma_pipe.cuh"
 #include "fp_bits.cuh"
+#include "blocksum.cuh"
+#include "xrow.cuh"
 
 namespace {
 
@@ -224,44 +226,6 @@ template <typename T> __device__ __forceinline__ typename cplx<T>::t mk(T a, T b
     typename cplx<T>::t r; r.x = a; r.y = b; return r;
 }
 
-
-// Block sums into part[blockIdx.x * 3 + q] of the partials a (FP64, reduced only when
-// HAS_A), b and c (FP32, reduced in FP32 within each warp, only when HAS_B / HAS_C); absent
-// partials are written as 0.  Warp values are added in FP64 by warp 0.  Per thread this costs
-// 5 FP64 adds for a and none for b, c (FP64 instructions run on GB300's narrow FP64 pipe).
-template <bool HAS_A, bool HAS_B, bool HAS_C>
-__device__ void block_sum_abc(double a, float b, float c, double* __restrict__ part) {
-    __shared__ double red[3][32];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        if (HAS_A) a += __shfl_xor_sync(0xffffffffu, a, o);
-        if (HAS_B) b += __shfl_xor_sync(0xffffffffu, b, o);
-        if (HAS_C) c += __shfl_xor_sync(0xffffffffu, c, o);
-    }
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
-    if (lane == 0) {
-        red[0][wid] = HAS_A ? a : 0.0;
-        red[1][wid] = HAS_B ? (double)b : 0.0;
-        red[2][wid] = HAS_C ? (double)c : 0.0;
-    }
-    __syncthreads();
-    if (wid == 0) {
-        double x = lane < nw ? red[0][lane] : 0.0;
-        double y = lane < nw ? red[1][lane] : 0.0;
-        double z = lane < nw ? red[2][lane] : 0.0;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            x += __shfl_down_sync(0xffffffffu, x, o);
-            y += __shfl_down_sync(0xffffffffu, y, o);
-            z += __shfl_down_sync(0xffffffffu, z, o);
-        }
-        if (lane == 0) {
-            part[blockIdx.x * 3 + 0] = x;
-            part[blockIdx.x * 3 + 1] = y;
-            part[blockIdx.x * 3 + 2] = z;
-        }
-    }
-}
 
 // The residual pass (MODE 2) uses shared-memory fixed-point rows when one thread per pair
 // position covers B = E rows of one plane: E = 8, M a multiple of 32 up to 512, ny % 8 == 0.
@@ -472,7 +436,7 @@ __global__ void __launch_bounds__(512) k_xfwd(const double* __restrict__ f, cons
 // per chunk of kz planes (3.25 when every row converts its own z neighbours).  With MODE 2 the
 // transform tile reuses the shared rows after each plane's stencil.  part[b]
 // (b = blockIdx.x + gridDim.x blockIdx.y) takes the block sums of r^2.
-template <int E, int MODE>
+template <int E, int MODE, int N1, int N2>
 __global__ void __launch_bounds__(512, 1) k_xres_zm(const double* __restrict__ f, const double* __restrict__ p,
                                                    float2* __restrict__ S, Geo g, FftLen L,
                                                    const float2* __restrict__ tw, const float2* __restrict__ twr,
@@ -571,12 +535,38 @@ __global__ void __launch_bounds__(512, 1) k_xres_zm(const double* __restrict__ f
             acc2 = fmaf(zr[c].x, zr[c].x, fmaf(zr[c].y, zr[c].y, acc2));
         }
         __syncthreads();                      // every read of plane k's shared rows is done
-        if (MODE == 2) {
+        if (MODE == 2 && N1 == 0) {
 #pragma unroll
             for (int c = 0; c < E; ++c) s[n * pitch + c] = zr[c];
             __syncthreads();
             xfwd_tile_out<float, E>(s, pitch, 3, L, tw, twr, S, g, (int)row0, g.ny * g.nz);
             __syncthreads();                  // the tile is read out: the rows of plane k+1 may go in
+        } else if constexpr (MODE == 2 && N1 > 0) {
+            // the register four-step rows, in their own area T after the rows of Q and LO: the
+            // 8 rows go through T (pitch TP, 8 (mod 16) when N2 = 8 so that the two rows of a
+            // half-warp fall on distinct banks) to the 8 N2 threads that hold z[N2 n1 + t] of
+            // row c = tid / N2 (the other warps pass the barriers only); plane k+1 moves into
+            // Q first, so that its prefetched rows are not held through the transform
+            constexpr int TP = N1 * N2 + (N2 == 8 ? 8 : 0);
+            float2* T = reinterpret_cast<float2*>(smraw + xres_smem(M));
+#pragma unroll
+            for (int c = 0; c < E; ++c) T[c * TP + n] = zr[c];
+            if (more) {
+#pragma unroll
+                for (int r = 0; r < E + 2; ++r) Q[r * M + n] = make_longlong2(fixq(pu[r].x, sh), fixq(pu[r].y, sh));
+            }
+            __syncthreads();
+            const bool active = n < E * N2;
+            const int c = n / N2, t = n % N2;
+            float2 v[N1];
+            if (active) {
+#pragma unroll
+                for (int n1 = 0; n1 < N1; ++n1) v[n1] = T[c * TP + N2 * n1 + t];
+            }
+            __syncthreads();                  // T is read out: the exchange may take its place
+            xrow4_fwd_tail<N1, N2>(v, T, active ? c : 0, t, active, true, tw, twr,
+                                   S + (row0 + (active ? c : 0)) * g.ldS);
+            continue;                         // T is next written after the next plane's stencil
         }
         if (more) {
 #pragma unroll
@@ -1512,8 +1502,8 @@ int pick_lgB(int N, int csize, int E, int bmax, int ncols, int cap) {
 // registers (E complex values) fit without spills (launch bound 512: up to 128 registers).
 int x_cap(int cta) { return std::min(cta > 0 ? cta : cta_threads(), 512); }
 
-template <typename K> void allow_smem(K kern) {
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+template <typename K> void allow_smem(K kern, size_t bytes = 96 * 1024) {
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(bytes, 96 * 1024));
 }
 
 // Elements per thread: 16 (FP32) or 8 (FP64) complex values; 4 for transforms shorter than that.
@@ -1673,11 +1663,20 @@ void run_xfwd_e(flups_plan P, const double* f, const double* p, const Geo& g) {
     const bool tiled = MODE >= 2 && xres_tiled(E, E, N, g.ny);
     if constexpr (MODE >= 2 && E == 8 && sizeof(T) == 4) {
         if (tiled) {                       // the z-marching form of the tiled defect
-            auto kern = k_xres_zm<E, MODE>;
-            allow_smem(kern);
+            // its transform tail: the register four-step rows where M is 64, 128 or 256; the
+            // shared-memory Stockham passes otherwise
+            auto kern = k_xres_zm<E, MODE, 0, 0>;
+            size_t xp = 0;
+            if constexpr (MODE == 2) {
+                if (N == 64) { kern = k_xres_zm<E, MODE, 8, 8>; xp = XRow<8, 8>::XP; }
+                else if (N == 128) { kern = k_xres_zm<E, MODE, 16, 8>; xp = XRow<16, 8>::XP; }
+                else if (N == 256) { kern = k_xres_zm<E, MODE, 16, 16>; xp = XRow<16, 16>::XP; }
+            }
+            const size_t smem = xres_smem(N) + (size_t)E * xp * sizeof(float2);
+            allow_smem(kern, smem);
             const int kz = xres_kz(g.ny, g.nz);
             flups_prof_begin(P, MODE == 3 ? FK_XRES_NORM32 : FK_XFWD_RES32);
-            kern<<<dim3(g.ny / E, (g.nz + kz - 1) / kz), N, xres_smem(N), P->stream>>>(
+            kern<<<dim3(g.ny / E, (g.nz + kz - 1) / kz), N, smem, P->stream>>>(
                 f, p, (float2*)P->spec, g, packed(P->lx), (const float2*)P->twx, (const float2*)P->twxr, kz, P->sc,
                 P->part);
             flups_prof_end(P);
@@ -1702,6 +1701,12 @@ void run_xfwd_e(flups_plan P, const double* f, const double* p, const Geo& g) {
 
 template <typename T, int MODE, bool STATS>
 void run_xfwd(flups_plan P, const double* f, const double* p, const Geo& g) {
+    if (sizeof(T) == 4 && MODE == 0 && xrow4_rows(g.M) > 0) {   // the register four-step rows
+        flups_prof_begin(P, FK_XFWD_F32);
+        const bool ok = launch_xrow4_fwd(P, f, g, STATS);
+        flups_prof_end(P);
+        if (ok) { FLUPS_COUNT(P, 1); return; }
+    }
     const int e = e_for<T>(g.M);
     if (e == 4) run_xfwd_e<T, 4, MODE, STATS>(P, f, p, g);
     else if (e == 8) run_xfwd_e<T, 8, MODE, STATS>(P, f, p, g);
@@ -1727,6 +1732,12 @@ void run_xinv_e(flups_plan P, double* p, const Geo& g) {
 
 template <typename T, int ACC, bool MEAN, bool SUBM>
 void run_xinv(flups_plan P, double* p, const Geo& g) {
+    if (sizeof(T) == 4 && xrow4_rows(g.M) > 0) {               // the register four-step rows
+        flups_prof_begin(P, ACC ? FK_XINV_ACC32 : FK_XINV32);
+        const bool ok = launch_xrow4_inv(P, p, g, ACC ? (SUBM ? 1 : 2) : (MEAN ? 0 : 3));
+        flups_prof_end(P);
+        if (ok) { FLUPS_COUNT(P, 1); return; }
+    }
     const int e = e_for<T>(g.M);
     if (e == 4) run_xinv_e<T, 4, ACC, MEAN, SUBM>(P, p, g);
     else if (e == 8) run_xinv_e<T, 8, ACC, MEAN, SUBM>(P, p, g);
@@ -1956,6 +1967,7 @@ __global__ void k_add_const(double* __restrict__ a, size_t n, double c) {
 // residual != 0, of the FP32 residual pass (which may use the tiled fixed-point layout).
 int xfwd_blocks(flups_plan P, int csize, int residual) {
     const int nrows = P->ny * P->nz;
+    if (!residual && csize == 8 && xrow4_rows(P->M) > 0) return (nrows + xrow4_rows(P->M) - 1) / xrow4_rows(P->M);
     const int E = P->M % 3 == 0 ? 12 : (P->M >= 8 ? 8 : 4);
     if (residual && csize == 8 && P->uniform_h && xres_tiled(E, E, P->M, P->ny)) {
         const int kz = xres_kz(P->ny, P->nz);

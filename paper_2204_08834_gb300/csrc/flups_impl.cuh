@@ -216,6 +216,12 @@ int flups_pipe_lgB(int N, int M, int kind);
 // where the kernel does not apply; launch_cols4 runs the y transform (kind 0, inv picks the
 // direction) or the periodic z solve (kind 1) on the plan's spectrum and returns false
 // without launching where the kernel does not apply.
+// Register four-step x-row kernels (xrow_kernels.cu) for M = nx / 2 in {64, ..., 1024}: rows
+// per CTA (0: not available); forward from f (stats: the partial sums of the first pass) and
+// inverse (mode 0: p = x with the mean's partial sums, 1: p += x - <p_0>, 2: p += x, 3: p = x).
+int xrow4_rows(int M);
+bool launch_xrow4_fwd(flups_plan P, const double* f, const Geo& g, bool stats);
+bool launch_xrow4_inv(flups_plan P, double* p, const Geo& g, int mode);
 int cols4_lgB(int N, int M, int kind);
 bool launch_cols4(flups_plan P, float2* S, const Geo& g, int kind, bool inv);
 // Walls z solve in FP32 without HBM scratch (cols_kernels.cu): tile width (log2) of its TMA
