@@ -1,14 +1,19 @@
 // batch.cu - ensembles of independent FP32-refine Poisson solves of mixed sizes, run as one
 // CUDA graph launch.
 //
-// Every member has its own plan (workspace, tables, TMA descriptors).  The members' fixed
-// kernel sequences (launch_solve32_fixed: no host synchronisation, device-side early exit
-// once a member's FP64 defect reaches rtol) are captured round-robin on several worker
-// streams forked from one origin stream, so independent members overlap on the GPU; the
-// resulting graph is replayed by every later flups_batch_solve with the same arguments.
-// An optional autotuner times, per distinct member size, the CTA thread cap of the
-// transform kernels and the radix sequence of the power-of-two transforms, and keeps the
-// fastest combination for all members of that size.
+// Every member has its own plan (workspace, tables).  The fixed sequence of the FP32 solve
+// with FP64 defect correction (no host synchronisation; a member whose FP64 defect reached
+// rtol skips every later stage) runs with one kernel per stage for all members together:
+// each stage kernel walks the concatenated (member, tile) list of the ensemble
+// (capture_batch_graph, fft_kernels.cu), so the graph holds 7 max_iter + 3 kernels whatever
+// the number of members; every iteration after the first sits in a conditional node that
+// runs only while some member has not converged.  Ensembles with a member that the stage kernels do not take
+// (ends in x or y, lengths other than 8 2^a and 12 2^a) capture each member's own kernel
+// sequence instead, round-robin on worker streams forked from the origin stream.  The graph
+// is replayed by every later flups_batch_solve with the same arguments.  An optional
+// autotuner keeps, per distinct member size, the fastest radix sequence of the power-of-two
+// transforms (and, on the per-member path, the CTA thread cap of the transform kernels).
+#include <algorithm>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
@@ -33,6 +38,12 @@ struct flups_batch_s {
     int maxit_cap = 0;
     unsigned long long graph_kernels = 0;
     std::vector<int> tuned_cta, tuned_radix;
+    // the stage kernels' path
+    bool staged = false;
+    BatchMember* dmem = nullptr;        // device: the members' descriptors
+    unsigned* dwork = nullptr;          // device: the stages' work lists
+    size_t nwork = 0;
+    BatchLaunch bl{};
 };
 
 namespace {
@@ -118,6 +129,114 @@ flups_status autotune(flups_plan P, int* best_cta, int* best_radix) {
     return cst(cudaGetLastError());
 }
 
+// Uploads the members' descriptors and the stages' work lists, and sets B->bl.
+cudaError_t staged_setup(flups_batch B, const double* const* f, double* const* p) {
+    const int n = B->n;
+    std::vector<BatchMember> hm(n);
+    std::vector<unsigned> wl[4];
+    size_t sx = 0, sy = 0, sz = 0, sd = 0;
+    for (int m = 0; m < n; ++m) {
+        flups_plan P = B->plans[m];
+        batch_member_fill(P, f ? f[m] : nullptr, p ? p[m] : nullptr, &hm[m]);
+        const BatchMember& D = hm[m];
+        // every stage must cover the member (a member with no defect tiles would read a zero
+        // norm); tiles and members must fit the item encoding
+        const int t[4] = {D.tx, D.ty, D.tz, D.td};
+        for (int q = 0; q < 4; ++q) {
+            if (t[q] < 1 || t[q] > (1 << 20) || m >= (1 << 12)) return cudaErrorInvalidValue;
+            for (int i = 0; i < t[q]; ++i) wl[q].push_back(((unsigned)m << 20) | (unsigned)i);
+        }
+        sx = std::max(sx, (size_t)D.smx);
+        sy = std::max(sy, (size_t)D.smy);
+        sz = std::max(sz, (size_t)D.smz);
+        sd = std::max(sd, (size_t)D.smd);
+    }
+    const size_t tot = wl[0].size() + wl[1].size() + wl[2].size() + wl[3].size();
+    if (tot > B->nwork) {
+        if (B->dwork) cudaFree(B->dwork);
+        B->dwork = nullptr;
+        B->nwork = 0;
+        cudaError_t e = cudaMalloc(&B->dwork, tot * sizeof(unsigned));
+        if (e != cudaSuccess) return e;
+        B->nwork = tot;
+    }
+    cudaError_t e = cudaMemcpy(B->dmem, hm.data(), n * sizeof(BatchMember), cudaMemcpyHostToDevice);
+    size_t off = 0;
+    const unsigned* base[4];
+    for (int q = 0; q < 4 && e == cudaSuccess; ++q) {
+        e = cudaMemcpy(B->dwork + off, wl[q].data(), wl[q].size() * sizeof(unsigned), cudaMemcpyHostToDevice);
+        base[q] = B->dwork + off;
+        off += wl[q].size();
+    }
+    if (e != cudaSuccess) return e;
+    BatchLaunch& L = B->bl;
+    L.mem = B->dmem;
+    L.ox = base[0];
+    L.oy = base[1];
+    L.oz = base[2];
+    L.od = base[3];
+    L.n = n;
+    L.total_x = (int)wl[0].size();
+    L.total_y = (int)wl[1].size();
+    L.total_z = (int)wl[2].size();
+    L.total_d = (int)wl[3].size();
+    L.smem_x = sx;
+    L.smem_y = sy;
+    L.smem_z = sz;
+    L.smem_d = sd;
+    L.stream = B->origin;
+    return e;
+}
+
+// Stage-kernel path: per distinct member size, the radix variant whose batched solve of that
+// member alone is fastest (timed on the member's own workspace with a seeded right-hand side).
+flups_status autotune_staged(flups_batch B, int m) {
+    flups_plan P = B->plans[m];
+    const size_t n = P->npts;
+    double *f = nullptr, *p = nullptr;
+    if (cudaMalloc(&f, n * sizeof(double)) != cudaSuccess) return FLUPS_ENOMEM;
+    if (cudaMalloc(&p, n * sizeof(double)) != cudaSuccess) { cudaFree(f); return FLUPS_ENOMEM; }
+    k_fill_hash<<<256, 256, 0, B->origin>>>(f, n);
+    // a one-member view of the batch: the member's plan alone, on the batch's own buffers
+    flups_batch_s one;
+    one.n = 1;
+    one.plans = &B->plans[m];
+    one.origin = B->origin;
+    one.dmem = B->dmem;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const FftLen saved[3] = {P->lx, P->ly, P->lz};
+    float best = 1e30f;
+    int bestv = 0;
+    for (int variant = 0; variant < 2; ++variant) {
+        set_radix(P, saved, variant);
+        const double* fa[1] = {f};
+        double* pa[1] = {p};
+        if (staged_setup(&one, fa, pa) != cudaSuccess) break;
+        launch_batch_fixed(one.bl, 1e-10, 3);      // warm-up
+        cudaEventRecord(e0, B->origin);
+        for (int r = 0; r < 3; ++r) launch_batch_fixed(one.bl, 1e-10, 3);
+        cudaEventRecord(e1, B->origin);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (cudaGetLastError() == cudaSuccess && ms < best) { best = ms; bestv = variant; }
+    }
+    set_radix(P, saved, bestv);
+    B->tuned_radix[m] = bestv;
+    B->tuned_cta[m] = FLUPS_BATCH_THREADS;
+    cudaStreamSynchronize(B->origin);
+    if (one.dwork) cudaFree(one.dwork);
+    one.plans = nullptr;                // not owned by the view
+    one.dmem = nullptr;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(f);
+    cudaFree(p);
+    return cst(cudaGetLastError());
+}
+
 void destroy_graph(flups_batch B) {
     if (B->exec) cudaGraphExecDestroy(B->exec);
     B->exec = nullptr;
@@ -125,6 +244,32 @@ void destroy_graph(flups_batch B) {
 
 flups_status capture(flups_batch B, const double* const* f, double* const* p, double rtol, int max_iter) {
     destroy_graph(B);
+    if (B->staged) {
+        cudaError_t e = staged_setup(B, f, p);
+        if (e != cudaSuccess) return cst(e);
+        cudaGraph_t graph = nullptr;
+        int k = capture_batch_graph(B->bl, B->streams[0], rtol, max_iter, &graph);
+        if (k < 0) {
+            // no conditional nodes: the plain sequence (later iterations skip member by member)
+            cudaGetLastError();
+            e = cudaStreamBeginCapture(B->origin, cudaStreamCaptureModeThreadLocal);
+            if (e != cudaSuccess) return cst(e);
+            k = launch_batch_fixed(B->bl, rtol, max_iter);
+            e = cudaStreamEndCapture(B->origin, &graph);
+            if (e == cudaSuccess && k < 0) e = cudaErrorLaunchFailure;
+            if (e != cudaSuccess) { if (graph) cudaGraphDestroy(graph); return cst(e); }
+        }
+        e = cudaGraphInstantiate(&B->exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) { B->exec = nullptr; return cst(e); }
+        for (int m = 0; m < B->n; ++m) B->plans[m]->last_max_iter = max_iter;
+        B->graph_kernels = (unsigned long long)k;
+        B->f_cap.assign(f, f + B->n);
+        B->p_cap.assign(p, p + B->n);
+        B->rtol_cap = rtol;
+        B->maxit_cap = max_iter;
+        return FLUPS_OK;
+    }
     cudaError_t e = cudaStreamBeginCapture(B->origin, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return cst(e);
     cudaEventRecord(B->fork, B->origin);
@@ -174,6 +319,8 @@ flups_status flups_batch_destroy(flups_batch B) {
         if (B->joins && B->joins[s]) cudaEventDestroy(B->joins[s]);
     }
     if (B->fork) cudaEventDestroy(B->fork);
+    if (B->dmem) cudaFree(B->dmem);
+    if (B->dwork) cudaFree(B->dwork);
     if (B->in_ev) cudaEventDestroy(B->in_ev);
     if (B->out_ev) cudaEventDestroy(B->out_ev);
     if (B->origin) cudaStreamDestroy(B->origin);
@@ -225,6 +372,31 @@ flups_status flups_batch_create(flups_batch* out, int n, const int* nx, const in
     }
     B->tuned_cta.assign(n, B->plans[0]->cta_cap);
     B->tuned_radix.assign(n, 0);
+    B->staged = true;
+    for (int m = 0; m < n; ++m) B->staged = B->staged && batch_member_ok(B->plans[m]);
+    if (B->staged) {
+        if (cudaMalloc(&B->dmem, n * sizeof(BatchMember)) != cudaSuccess) {
+            flups_batch_destroy(B);
+            return FLUPS_ENOMEM;
+        }
+        B->tuned_cta.assign(n, FLUPS_BATCH_THREADS);
+        for (int m = 0; autotune_on && m < n; ++m) {
+            int first = -1;   // an earlier member of the same size and boundary condition
+            for (int q = 0; q < m && first < 0; ++q)
+                if (nx[q] == nx[m] && ny[q] == ny[m] && nz[q] == nz[m] && bc[q] == bc[m]) first = q;
+            if (first >= 0) {
+                B->plans[m]->lx = B->plans[first]->lx;
+                B->plans[m]->ly = B->plans[first]->ly;
+                B->plans[m]->lz = B->plans[first]->lz;
+                B->tuned_radix[m] = B->tuned_radix[first];
+                continue;
+            }
+            const flups_status st = autotune_staged(B, m);
+            if (st != FLUPS_OK) { flups_batch_destroy(B); return st; }
+        }
+        *out = B;
+        return FLUPS_OK;
+    }
     if (autotune_on) {
         for (int m = 0; m < n; ++m) {
             int first = -1;   // an earlier member of the same size and boundary condition

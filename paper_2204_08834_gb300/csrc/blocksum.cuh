@@ -4,12 +4,13 @@
 
 namespace {
 
-// Block sums into part[blockIdx.x * 3 + q] of the partials a (FP64, reduced only when
+// Block sums into part[bi * 3 + q] (bi = blockIdx.x unless given) of the partials a (FP64, reduced only when
 // HAS_A), b and c (FP32, reduced in FP32 within each warp, only when HAS_B / HAS_C); absent
 // partials are written as 0.  Warp values are added in FP64 by warp 0.  Per thread this costs
 // 5 FP64 adds for a and none for b, c (FP64 instructions run on GB300's narrow FP64 pipe).
 template <bool HAS_A, bool HAS_B, bool HAS_C>
-__device__ void block_sum_abc(double a, float b, float c, double* __restrict__ part) {
+__device__ void block_sum_abc(double a, float b, float c, double* __restrict__ part, int bi = -1) {
+    if (bi < 0) bi = blockIdx.x;
     __shared__ double red[3][32];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -35,9 +36,9 @@ __device__ void block_sum_abc(double a, float b, float c, double* __restrict__ p
             z += __shfl_down_sync(0xffffffffu, z, o);
         }
         if (lane == 0) {
-            part[blockIdx.x * 3 + 0] = x;
-            part[blockIdx.x * 3 + 1] = y;
-            part[blockIdx.x * 3 + 2] = z;
+            part[bi * 3 + 0] = x;
+            part[bi * 3 + 1] = y;
+            part[bi * 3 + 2] = z;
         }
     }
 }

@@ -14,6 +14,7 @@
 // Transforms are unnormalised; the whole 1/(M ny nz) (or 1/(M ny) with walls) factor is
 // folded into the eigenvalue / tridiagonal tables, M = nx/2.
 #include <cstdlib>
+#include <cstring>
 
 #include "flups_impl.cuh"
 #include "tma_pipe.cuh"
@@ -243,6 +244,8 @@ inline int xres_kz(int ny, int nz) {
     return kz;
 }
 
+__device__ __forceinline__ int ilog2_dev(int x) { return 31 - __clz(x); }
+
 // The transform of a tile of B rows (Z in shared memory, pair index n of row c at
 // s[n pitch + c]) and the real-to-complex split into the spectrum rows row0 .. row0+B-1:
 // X_k = A_k + W_nx^k B_k and X_{M-k} = conj(A_k - W_nx^k B_k), k = 0..M/2, with
@@ -285,18 +288,18 @@ __device__ __forceinline__ void xfwd_tile_out(typename cplx<T>::t* s, int pitch,
 // MODE 3: as MODE 2, but only the partial sums of r^2 (no transform, nothing written): the
 //         stopping test of a refinement that has most likely converged.
 template <typename T, int E, int MODE, bool STATS>
-__global__ void __launch_bounds__(512) k_xfwd(const double* __restrict__ f, const double* __restrict__ p,
-                                               typename cplx<T>::t* __restrict__ S, Geo g, FftLen L,
-                                               const typename cplx<T>::t* __restrict__ tw,
-                                               const typename cplx<T>::t* __restrict__ twr,
-                                               const double* __restrict__ dd, int lgB, int nrows,
-                                               const DevScalars* __restrict__ sc, double* __restrict__ part) {
+__device__ __forceinline__ void xfwd_body(int bx, const double* __restrict__ f, const double* __restrict__ p,
+                                          typename cplx<T>::t* __restrict__ S, const Geo& g, const FftLen& L,
+                                          const typename cplx<T>::t* __restrict__ tw,
+                                          const typename cplx<T>::t* __restrict__ twr,
+                                          const double* __restrict__ dd, int lgB, int nrows,
+                                          const DevScalars* __restrict__ sc, double* __restrict__ part) {
     if (g.skip && *g.skip) return;   // graph-capturable solve: this member already converged
     typedef typename cplx<T>::t C;
     extern __shared__ __align__(16) unsigned char smraw[];
     C* s = reinterpret_cast<C*>(smraw);
     const int B = 1 << lgB, pitch = B + 1, M = g.M;
-    const int row0 = blockIdx.x * B, tid = threadIdx.x, nthr = blockDim.x;
+    const int row0 = bx * B, tid = threadIdx.x, nthr = blockDim.x;
     const int nx = g.nx;
     double accw = 0.0;
     float acc2 = 0.f, acc1 = 0.f;
@@ -304,14 +307,30 @@ __global__ void __launch_bounds__(512) k_xfwd(const double* __restrict__ f, cons
     if (MODE >= 1) mf = sc->mean_f;
     int sh = 0;
     double cfix = 0.0;
+    // power-of-two spacing: r = 2^(pexp-1080)/h^2 (F - MF - S) from the exact integer difference
+    // (F, MF: h^2 f and h^2 <f> at the fixed point of S), no FP64 instruction (as k_xres_zm)
+    bool ipath = false;
+    int shf = 0;
+    long long mfq = 0;
+    float rscale = 0.f;
     if (MODE >= 2) {
         const int pe_ = sc->pexp;
         sh = pe_ - 5;
         if (pe_ >= 2047) cfix = __longlong_as_double(0x7FF8000000000000LL);           // NaN: p not finite
         else if (pe_ - 57 >= 1) cfix = __hiloint2double((pe_ - 57) << 20, 0) * g.sx;   // 2^(pexp-1080) / h^2
+        if (sizeof(T) == 4 && g.h2e != H2E_NONE && pe_ < 2047 && pe_ - 57 >= 1) {
+            const int es = pe_ - 1080 - g.h2e;
+            shf = sh - g.h2e;
+            bool okm;
+            mfq = fixw(mf, shf, okm);
+            ipath = okm && es >= -126 && es <= 60;
+            if (ipath) rscale = __int_as_float((es + 127) << 23);
+        }
     }
     // Every thread handles exactly E elements (nthr = B M / E): compile-time trip counts let
     // the loads of a thread be issued before they are used.
+    float fh = 0.f, fl = 0.f;   // FP32 mode, STATS: the plane's sum of f in binary32 pairs
+    int kcur = -1;
     if (MODE == 0) {
         double2 fvs[E];
 #pragma unroll
@@ -331,7 +350,23 @@ __global__ void __launch_bounds__(512) k_xfwd(const double* __restrict__ f, cons
             const C z = mk<T>(from_double<T>(fv.x), from_double<T>(fv.y));
             if (STATS && row < nrows) {
                 const int k = row / g.ny;
-                accw = fma(fv.x + fv.y, __ldg(g.dzf + k), accw);
+                if constexpr (sizeof(T) == 4) {
+                    // split f = xh + xl (bit operations), xh added by exact two-sums; flushed to
+                    // FP64 with the plane's dzf only when the row moves to another plane
+                    if (k != kcur) {
+                        if (kcur >= 0) accw = fma(f2d_bits(fh) + f2d_bits(fl), __ldg(g.dzf + kcur), accw);
+                        fh = fl = 0.f;
+                        kcur = k;
+                    }
+                    float h0, l0, h1, l1;
+                    split_d(fv.x, h0, l0);
+                    split_d(fv.y, h1, l1);
+                    two_sum_acc(fh, fl, h0);
+                    two_sum_acc(fh, fl, h1);
+                    fl += l0 + l1;
+                } else {
+                    accw = fma(fv.x + fv.y, __ldg(g.dzf + k), accw);
+                }
                 acc2 = fmaf((float)z.x, (float)z.x, fmaf((float)z.y, (float)z.y, acc2));
                 acc1 += (float)z.x + (float)z.y;
             }
@@ -377,8 +412,17 @@ __global__ void __launch_bounds__(512) k_xfwd(const double* __restrict__ f, cons
                 if (!g.walls || k < g.nz - 1) { s0 += fixq(pt.x, sh); s1 += fixq(pt.y, sh); ++nd; }
                 s0 -= (long long)nd * q0;
                 s1 -= (long long)nd * q1;
-                z = mk<T>(from_double<T>(fma(-cfix, __ll2double_rn(s0), fv.x - mf)),
-                          from_double<T>(fma(-cfix, __ll2double_rn(s1), fv.y - mf)));
+                bool ok0 = false, ok1 = false;
+                long long F0 = 0, F1 = 0;
+                if (ipath) {
+                    F0 = fixw(fv.x, shf, ok0);
+                    F1 = fixw(fv.y, shf, ok1);
+                }
+                if (ok0 && ok1)
+                    z = mk<T>((T)(rscale * i64_to_f32(F0 - mfq - s0)), (T)(rscale * i64_to_f32(F1 - mfq - s1)));
+                else
+                    z = mk<T>(from_double<T>(fma(-cfix, __ll2double_rn(s0), fv.x - mf)),
+                              from_double<T>(fma(-cfix, __ll2double_rn(s1), fv.y - mf)));
                 acc2 = fmaf((float)z.x, (float)z.x, fmaf((float)z.y, (float)z.y, acc2));
             } else {
                 const int k = row / g.ny, j = row - k * g.ny;
@@ -413,11 +457,23 @@ __global__ void __launch_bounds__(512) k_xfwd(const double* __restrict__ f, cons
         s[n * pitch + c] = z;
     }
     }
-    if (STATS) block_sum_abc<true, true, true>(accw, acc2, acc1, part);
-    else if (MODE >= 1) block_sum_abc<false, true, false>(0.0, acc2, 0.f, part);
+    if (STATS) {
+        if (sizeof(T) == 4 && kcur >= 0) accw = fma(f2d_bits(fh) + f2d_bits(fl), __ldg(g.dzf + kcur), accw);
+        block_sum_abc<true, true, true>(accw, acc2, acc1, part, bx);
+    }
+    else if (MODE >= 1) block_sum_abc<false, true, false>(0.0, acc2, 0.f, part, bx);
     if (MODE == 3) return;               // the defect norm only (the stopping test)
     __syncthreads();
     xfwd_tile_out<T, E>(s, pitch, lgB, L, tw, twr, S, g, row0, nrows);
+}
+template <typename T, int E, int MODE, bool STATS>
+__global__ void __launch_bounds__(512) k_xfwd(const double* __restrict__ f, const double* __restrict__ p,
+                                               typename cplx<T>::t* __restrict__ S, Geo g, FftLen L,
+                                               const typename cplx<T>::t* __restrict__ tw,
+                                               const typename cplx<T>::t* __restrict__ twr,
+                                               const double* __restrict__ dd, int lgB, int nrows,
+                                               const DevScalars* __restrict__ sc, double* __restrict__ part) {
+    xfwd_body<T, E, MODE, STATS>(blockIdx.x, f, p, S, g, L, tw, twr, dd, lgB, nrows, sc, part);
 }
 
 // The FP32 refinement's exact defect on one-spacing grids (MODE 2: with the forward transform
@@ -436,19 +492,24 @@ __global__ void __launch_bounds__(512) k_xfwd(const double* __restrict__ f, cons
 // per chunk of kz planes (3.25 when every row converts its own z neighbours).  With MODE 2 the
 // transform tile reuses the shared rows after each plane's stencil.  part[b]
 // (b = blockIdx.x + gridDim.x blockIdx.y) takes the block sums of r^2.
+// As a body: G groups of M threads (the CTA's G row blocks j0 = (bx G + grp) 8 .. +7, consecutive,
+// of the planes by kz .. by kz + kz - 1), each group with its own shared rows; the Stockham tail
+// transforms the 8 G rows together (the four-step tail, N1 > 0, takes G = 1).  part[pidx]
+// takes the CTA's sum of r^2.
 template <int E, int MODE, int N1, int N2>
-__global__ void __launch_bounds__(512, 1) k_xres_zm(const double* __restrict__ f, const double* __restrict__ p,
-                                                   float2* __restrict__ S, Geo g, FftLen L,
-                                                   const float2* __restrict__ tw, const float2* __restrict__ twr,
-                                                   int kz, const DevScalars* __restrict__ sc,
-                                                   double* __restrict__ part) {
+__device__ __forceinline__ void xres_zm_body(int bx, int by, int G, const double* __restrict__ f,
+                                             const double* __restrict__ p, float2* __restrict__ S, const Geo& g,
+                                             const FftLen& L, const float2* __restrict__ tw,
+                                             const float2* __restrict__ twr, int kz,
+                                             const DevScalars* __restrict__ sc, double* __restrict__ part,
+                                             int pidx) {
     static_assert(E == 8, "one pair position per thread over 8 rows");
     if (g.skip && *g.skip) return;   // graph-capturable solve: this member already converged
     extern __shared__ __align__(16) unsigned char smraw[];
-    longlong2* Q = reinterpret_cast<longlong2*>(smraw);
+    const int M = g.M, grp = threadIdx.x / M, n = threadIdx.x - grp * M, pitch = E * G + 1;
+    longlong2* Q = reinterpret_cast<longlong2*>(smraw) + (size_t)grp * (E + 2) * M;
     float2* s = reinterpret_cast<float2*>(smraw);
-    const int M = g.M, n = threadIdx.x, pitch = E + 1;
-    const int j0 = blockIdx.x * E, k0 = blockIdx.y * kz;
+    const int j0 = (bx * G + grp) * E, k0 = by * kz, jc = bx * G * E;
     const int k1 = min(k0 + kz, g.nz);
     const double mf = sc->mean_f;
     const int pe_ = sc->pexp, sh = pe_ - 5;
@@ -472,7 +533,7 @@ __global__ void __launch_bounds__(512, 1) k_xres_zm(const double* __restrict__ f
     const int nw_ = n == 0 ? M - 1 : n - 1, ne_ = n + 1 == M ? 0 : n + 1;
     auto prow = [&](int k, int j) { return P2 + ((size_t)k * g.ny + j) * M + n; };
     // LO[c M + n]: the centre of the plane below (thread n alone reads and writes column n)
-    longlong2* LO = Q + (E + 2) * M;
+    longlong2* LO = reinterpret_cast<longlong2*>(smraw) + (size_t)G * (E + 2) * M + (size_t)grp * E * M;
     // the centre of plane k0 with its y halo into shared memory, the plane below into LO
 #pragma unroll
     for (int r = 0; r < E + 2; ++r) {
@@ -537,9 +598,10 @@ __global__ void __launch_bounds__(512, 1) k_xres_zm(const double* __restrict__ f
         __syncthreads();                      // every read of plane k's shared rows is done
         if (MODE == 2 && N1 == 0) {
 #pragma unroll
-            for (int c = 0; c < E; ++c) s[n * pitch + c] = zr[c];
+            for (int c = 0; c < E; ++c) s[n * pitch + grp * E + c] = zr[c];
             __syncthreads();
-            xfwd_tile_out<float, E>(s, pitch, 3, L, tw, twr, S, g, (int)row0, g.ny * g.nz);
+            xfwd_tile_out<float, E>(s, pitch, ilog2_dev(E * G), L, tw, twr, S, g, (int)((size_t)k * g.ny + jc),
+                                    g.ny * g.nz);
             __syncthreads();                  // the tile is read out: the rows of plane k+1 may go in
         } else if constexpr (MODE == 2 && N1 > 0) {
             // the register four-step rows, in their own area T after the rows of Q and LO: the
@@ -548,7 +610,7 @@ __global__ void __launch_bounds__(512, 1) k_xres_zm(const double* __restrict__ f
             // row c = tid / N2 (the other warps pass the barriers only); plane k+1 moves into
             // Q first, so that its prefetched rows are not held through the transform
             constexpr int TP = N1 * N2 + (N2 == 8 ? 8 : 0);
-            float2* T = reinterpret_cast<float2*>(smraw + xres_smem(M));
+            float2* T = reinterpret_cast<float2*>(smraw + (size_t)G * xres_smem(M));
 #pragma unroll
             for (int c = 0; c < E; ++c) T[c * TP + n] = zr[c];
             if (more) {
@@ -574,8 +636,17 @@ __global__ void __launch_bounds__(512, 1) k_xres_zm(const double* __restrict__ f
             __syncthreads();
         }
     }
-    // one partial sum per CTA (block_sum_abc writes part[blockIdx.x * 3 + q]: fold the grid)
-    block_sum_abc<false, true, false>(0.0, acc2, 0.f, part + (size_t)3 * blockIdx.y * gridDim.x);
+    block_sum_abc<false, true, false>(0.0, acc2, 0.f, part, pidx);
+}
+
+template <int E, int MODE, int N1, int N2>
+__global__ void __launch_bounds__(512, 1) k_xres_zm(const double* __restrict__ f, const double* __restrict__ p,
+                                                   float2* __restrict__ S, Geo g, FftLen L,
+                                                   const float2* __restrict__ tw, const float2* __restrict__ twr,
+                                                   int kz, const DevScalars* __restrict__ sc,
+                                                   double* __restrict__ part) {
+    xres_zm_body<E, MODE, N1, N2>(blockIdx.x, blockIdx.y, 1, f, p, S, g, L, tw, twr, kz, sc, part,
+                                  blockIdx.y * gridDim.x + blockIdx.x);
 }
 
 // ------------------------------------------------------------- inverse along x (C2R)
@@ -584,16 +655,16 @@ __global__ void __launch_bounds__(512, 1) k_xres_zm(const double* __restrict__ f
 // first FP32 iterate, whose rounding leaves a constant of order eps32 |p| that the
 // residual cannot see; SUBM (with ACC = 1) removes that constant in the first update.
 template <typename T, int E, int ACC, bool MEAN, bool SUBM>
-__global__ void __launch_bounds__(512) k_xinv(const typename cplx<T>::t* __restrict__ S, double* __restrict__ p,
-                                               Geo g, FftLen L, const typename cplx<T>::t* __restrict__ tw,
-                                               const typename cplx<T>::t* __restrict__ twr, int lgB, int nrows,
-                                               DevScalars* __restrict__ sc, double* __restrict__ part) {
+__device__ __forceinline__ void xinv_body(int bx, const typename cplx<T>::t* __restrict__ S, double* __restrict__ p,
+                                          const Geo& g, const FftLen& L, const typename cplx<T>::t* __restrict__ tw,
+                                          const typename cplx<T>::t* __restrict__ twr, int lgB, int nrows,
+                                          DevScalars* __restrict__ sc, double* __restrict__ part) {
     if (g.skip && *g.skip) return;   // graph-capturable solve: this member already converged
     typedef typename cplx<T>::t C;
     extern __shared__ __align__(16) unsigned char smraw[];
     C* s = reinterpret_cast<C*>(smraw);
     const int B = 1 << lgB, pitch = B + 1, M = g.M;
-    const int row0 = blockIdx.x * B, tid = threadIdx.x, nthr = blockDim.x;
+    const int row0 = bx * B, tid = threadIdx.x, nthr = blockDim.x;
     const int H = M / 2 + 1;
     // Z_k = A_k + i B_k, Z_{M-k} = conj(A_k) + i conj(B_k) with A_k = (X_k + conj X_{M-k})/2,
     // B_k = (X_k - conj X_{M-k}) conj(W_nx^k)/2; X_0 and X_M are taken real.
@@ -631,6 +702,8 @@ __global__ void __launch_bounds__(512) k_xinv(const typename cplx<T>::t* __restr
     fft_tile<C, E, true>(s, pitch, lgB, L, tw);
     const int nx = g.nx;
     double accw = 0.0;
+    float mh = 0.f, ml = 0.f;   // FP32 mode: the plane's sum of p in binary32 pairs (two-sums)
+    int kcur = -1;
     int emax = 0;       // largest binary64 exponent field written (FP32 mode: scale of the next defect)
     T msub = (T)0;
     if (SUBM) msub = (T)sc->mean_p;
@@ -662,7 +735,21 @@ __global__ void __launch_bounds__(512) k_xinv(const typename cplx<T>::t* __restr
         } else {
             o.x = to_double<T>(z.x);
             o.y = to_double<T>(z.y);
-            if (MEAN) accw = fma(o.x + o.y, __ldg(g.dzf + row / g.ny), accw);
+            if (MEAN) {
+                if constexpr (sizeof(T) == 4) {
+                    // flushed to FP64 with the plane's dzf only when the row moves to another plane
+                    const int k = row / g.ny;
+                    if (k != kcur) {
+                        if (kcur >= 0) accw = fma(f2d_bits(mh) + f2d_bits(ml), __ldg(g.dzf + kcur), accw);
+                        mh = ml = 0.f;
+                        kcur = k;
+                    }
+                    two_sum_acc(mh, ml, (float)z.x);
+                    two_sum_acc(mh, ml, (float)z.y);
+                } else {
+                    accw = fma(o.x + o.y, __ldg(g.dzf + row / g.ny), accw);
+                }
+            }
         }
         *dst = o;
         if (sizeof(T) == 4) {
@@ -675,7 +762,17 @@ __global__ void __launch_bounds__(512) k_xinv(const typename cplx<T>::t* __restr
         emax = __reduce_max_sync(0xffffffffu, emax);
         if ((tid & 31) == 0) atomicMax(&sc->pexp, emax);
     }
-    if (MEAN) block_sum_abc<true, false, false>(accw, 0.f, 0.f, part);
+    if (MEAN) {
+        if (sizeof(T) == 4 && kcur >= 0) accw = fma(f2d_bits(mh) + f2d_bits(ml), __ldg(g.dzf + kcur), accw);
+        block_sum_abc<true, false, false>(accw, 0.f, 0.f, part, bx);
+    }
+}
+template <typename T, int E, int ACC, bool MEAN, bool SUBM>
+__global__ void __launch_bounds__(512) k_xinv(const typename cplx<T>::t* __restrict__ S, double* __restrict__ p,
+                                               Geo g, FftLen L, const typename cplx<T>::t* __restrict__ tw,
+                                               const typename cplx<T>::t* __restrict__ twr, int lgB, int nrows,
+                                               DevScalars* __restrict__ sc, double* __restrict__ part) {
+    xinv_body<T, E, ACC, MEAN, SUBM>(blockIdx.x, S, p, g, L, tw, twr, lgB, nrows, sc, part);
 }
 
 // -------------------------------------------- x transforms with Neumann or Dirichlet ends
@@ -1012,8 +1109,9 @@ __global__ void __launch_bounds__(1024) k_ydct4(typename cplx<T>::t* __restrict_
 // TAIL = true : the Nyquist column kx = M of B consecutive planes (blockIdx.x * B + c), so
 //               that this ragged column is transformed by full tiles too.
 template <typename T, int E, bool INV, bool TAIL>
-__global__ void __launch_bounds__(1024) k_ycol(typename cplx<T>::t* __restrict__ S, Geo g, FftLen L,
-                                               const typename cplx<T>::t* __restrict__ tw, int lgB, int kx0) {
+__device__ __forceinline__ void ycol_body(int bx, int by, typename cplx<T>::t* __restrict__ S, const Geo& g,
+                                          const FftLen& L, const typename cplx<T>::t* __restrict__ tw, int lgB,
+                                          int kx0) {
     if (g.skip && *g.skip) return;   // graph-capturable solve: this member already converged
     typedef typename cplx<T>::t C;
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -1024,12 +1122,12 @@ __global__ void __launch_bounds__(1024) k_ycol(typename cplx<T>::t* __restrict__
     size_t cs;
     int ncol;
     if (TAIL) {
-        base = S + (size_t)blockIdx.x * B * plane + g.M;
+        base = S + (size_t)bx * B * plane + g.M;
         cs = plane;
-        ncol = min(B, g.nz - (int)blockIdx.x * B);
+        ncol = min(B, g.nz - (int)bx * B);
     } else {
-        const int kxa = kx0 + blockIdx.x * B;
-        base = S + (size_t)blockIdx.y * plane + kxa;
+        const int kxa = kx0 + bx * B;
+        base = S + (size_t)by * plane + kxa;
         cs = 1;
         ncol = min(B, g.M - kxa);   // kx = M is the TAIL launch's
     }
@@ -1053,16 +1151,21 @@ __global__ void __launch_bounds__(1024) k_ycol(typename cplx<T>::t* __restrict__
         for (int t = 0; t < E; ++t) dst[(size_t)t * NE * g.ldS] = s[(j0 + t * NE) * pitch + c];
     }
 }
+template <typename T, int E, bool INV, bool TAIL>
+__global__ void __launch_bounds__(1024) k_ycol(typename cplx<T>::t* __restrict__ S, Geo g, FftLen L,
+                                               const typename cplx<T>::t* __restrict__ tw, int lgB, int kx0) {
+    ycol_body<T, E, INV, TAIL>(blockIdx.x, blockIdx.y, S, g, L, tw, lgB, kx0);
+}
 
 // -------------------------------------- periodic z: forward z FFT, divide, inverse z FFT
 // lam tables hold eigenvalue / norm; the (0,0,0) mode is set to zero (zero-mean p).
 // TAIL = false: B consecutive kx columns at ky = blockIdx.y; TAIL = true: the Nyquist column
 // kx = M at B consecutive ky (blockIdx.x * B + c).
 template <typename T, int E, bool TAIL>
-__global__ void __launch_bounds__(1024) k_zper(typename cplx<T>::t* __restrict__ S, Geo g, FftLen L,
-                                               const typename cplx<T>::t* __restrict__ tw,
-                                               const T* __restrict__ lamx, const T* __restrict__ lamy,
-                                               const T* __restrict__ lamz, int lgB, int kx0) {
+__device__ __forceinline__ void zper_body(int bx, int by, typename cplx<T>::t* __restrict__ S, const Geo& g,
+                                          const FftLen& L, const typename cplx<T>::t* __restrict__ tw,
+                                          const T* __restrict__ lamx, const T* __restrict__ lamy,
+                                          const T* __restrict__ lamz, int lgB, int kx0) {
     if (g.skip && *g.skip) return;   // graph-capturable solve: this member already converged
     typedef typename cplx<T>::t C;
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -1073,14 +1176,14 @@ __global__ void __launch_bounds__(1024) k_zper(typename cplx<T>::t* __restrict__
     size_t cs;
     int ncol, kxa, ky0;
     if (TAIL) {
-        ky0 = blockIdx.x * B;
+        ky0 = bx * B;
         kxa = g.M;
         base = S + (size_t)ky0 * g.ldS + g.M;
         cs = g.ldS;
         ncol = min(B, g.ny - ky0);
     } else {
-        ky0 = blockIdx.y;
-        kxa = kx0 + blockIdx.x * B;
+        ky0 = by;
+        kxa = kx0 + bx * B;
         base = S + (size_t)ky0 * g.ldS + kxa;
         cs = 1;
         ncol = min(B, g.M - kxa);   // kx = M is the TAIL launch's
@@ -1119,6 +1222,13 @@ __global__ void __launch_bounds__(1024) k_zper(typename cplx<T>::t* __restrict__
 #pragma unroll
         for (int t = 0; t < E; ++t) dst[(size_t)t * NE * zs] = s[(j0 + t * NE) * pitch + c];
     }
+}
+template <typename T, int E, bool TAIL>
+__global__ void __launch_bounds__(1024) k_zper(typename cplx<T>::t* __restrict__ S, Geo g, FftLen L,
+                                               const typename cplx<T>::t* __restrict__ tw,
+                                               const T* __restrict__ lamx, const T* __restrict__ lamy,
+                                               const T* __restrict__ lamz, int lgB, int kx0) {
+    zper_body<T, E, TAIL>(blockIdx.x, blockIdx.y, S, g, L, tw, lamx, lamy, lamz, lgB, kx0);
 }
 
 // ------------------------------------- persistent, double-buffered column transforms
@@ -1245,13 +1355,13 @@ __global__ void __launch_bounds__(1024, 1) k_cols_pipe(float2* __restrict__ S, c
 // Column (0, 0) is singular: its row 0 is dropped, P_0 = 0, and the column is shifted
 // to zero dzf-weighted mean.
 template <typename T>
-__global__ void __launch_bounds__(128) k_ztri(typename cplx<T>::t* __restrict__ S, T* __restrict__ cps, Geo g,
-                                              const T* __restrict__ lamx, const T* __restrict__ lamy,
-                                              const T* __restrict__ tri) {
+__device__ __forceinline__ void ztri_body(int bx, typename cplx<T>::t* __restrict__ S, T* __restrict__ cps,
+                                          const Geo& g, const T* __restrict__ lamx, const T* __restrict__ lamy,
+                                          const T* __restrict__ tri) {
     if (g.skip && *g.skip) return;   // graph-capturable solve: this member already converged
     typedef typename cplx<T>::t C;
     const int ncols = g.nxh * g.ny;
-    const int col = blockIdx.x * blockDim.x + threadIdx.x;
+    const int col = bx * blockDim.x + threadIdx.x;
     if (col >= ncols) return;
     const int ky = col / g.nxh, kx = col - ky * g.nxh;
     const int nz = g.nz;
@@ -1279,29 +1389,51 @@ __global__ void __launch_bounds__(128) k_ztri(typename cplx<T>::t* __restrict__ 
         }
         fmean = mk<T>((T)(sx0 / sw), (T)(sy0 / sw));
     }
+    // Both sweeps take the column in chunks of ZQ rows whose loads are issued before the
+    // chunk's recurrence steps (the steps depend on each other, the loads do not).
+    constexpr int ZQ = 8;
     T cprev = (T)0;
     C dprev = mk<T>((T)0, (T)0);
-    for (int k = k0; k < nz; ++k) {
-        const T a = k > k0 ? __ldg(&ta[k]) : (T)0;
-        const T m = (__ldg(&tb[k]) + lam) - a * cprev;
-        const T inv = (T)1 / m;
-        C F = x[k * zs];
-        F.x -= fmean.x;
-        F.y -= fmean.y;
-        cprev = __ldg(&tc[k]) * inv;
-        dprev = mk<T>((F.x - a * dprev.x) * inv, (F.y - a * dprev.y) * inv);
-        cp[k * cs] = cprev;
-        x[k * zs] = dprev;
+    for (int kb = k0; kb < nz; kb += ZQ) {
+        C Fq[ZQ];
+#pragma unroll
+        for (int q = 0; q < ZQ; ++q) Fq[q] = kb + q < nz ? x[(size_t)(kb + q) * zs] : mk<T>((T)0, (T)0);
+#pragma unroll
+        for (int q = 0; q < ZQ; ++q) {
+            const int k = kb + q;
+            if (k >= nz) break;
+            const T a = k > k0 ? __ldg(&ta[k]) : (T)0;
+            const T m = (__ldg(&tb[k]) + lam) - a * cprev;
+            const T inv = (T)1 / m;
+            C F = Fq[q];
+            F.x -= fmean.x;
+            F.y -= fmean.y;
+            cprev = __ldg(&tc[k]) * inv;
+            dprev = mk<T>((F.x - a * dprev.x) * inv, (F.y - a * dprev.y) * inv);
+            cp[(size_t)k * cs] = cprev;
+            x[(size_t)k * zs] = dprev;
+        }
     }
     C xv = dprev;
     T sx = (T)0, sy = (T)0;
     if (sing) { const T w = (T)g.dzf[nz - 1]; sx = w * xv.x; sy = w * xv.y; }
-    for (int k = nz - 2; k >= k0; --k) {
-        const T c = cp[k * cs];
-        const C d = x[k * zs];
-        xv = mk<T>(d.x - c * xv.x, d.y - c * xv.y);
-        x[k * zs] = xv;
-        if (sing) { const T w = (T)g.dzf[k]; sx += w * xv.x; sy += w * xv.y; }
+    for (int kt = nz - 2; kt >= k0; kt -= ZQ) {
+        T cq[ZQ];
+        C dq[ZQ];
+#pragma unroll
+        for (int q = 0; q < ZQ; ++q) {
+            const int k = kt - q;
+            cq[q] = k >= k0 ? cp[(size_t)k * cs] : (T)0;
+            dq[q] = k >= k0 ? x[(size_t)k * zs] : mk<T>((T)0, (T)0);
+        }
+#pragma unroll
+        for (int q = 0; q < ZQ; ++q) {
+            const int k = kt - q;
+            if (k < k0) break;
+            xv = mk<T>(dq[q].x - cq[q] * xv.x, dq[q].y - cq[q] * xv.y);
+            x[(size_t)k * zs] = xv;
+            if (sing) { const T w = (T)g.dzf[k]; sx += w * xv.x; sy += w * xv.y; }
+        }
     }
     if (sing) {
         x[0] = mk<T>((T)0, (T)0);
@@ -1315,6 +1447,12 @@ __global__ void __launch_bounds__(128) k_ztri(typename cplx<T>::t* __restrict__ 
             x[k * zs] = v;
         }
     }
+}
+template <typename T>
+__global__ void __launch_bounds__(128) k_ztri(typename cplx<T>::t* __restrict__ S, T* __restrict__ cps, Geo g,
+                                              const T* __restrict__ lamx, const T* __restrict__ lamy,
+                                              const T* __restrict__ tri) {
+    ztri_body<T>(blockIdx.x, S, cps, g, lamx, lamy, tri);
 }
 
 // Thomas along z for the packed all-real spectrum (Geo::xpack): complex column (m, ky) holds the
@@ -1977,6 +2115,181 @@ int xfwd_blocks(flups_plan P, int csize, int residual) {
     return (nrows + (1 << lgB) - 1) >> lgB;
 }
 
+// ------------------------------------------------------------ batched ensemble stages
+// One launch per stage of the fixed FP32 + FP64-defect sequence covers every member of an
+// ensemble: CTA b takes item b of the stage's work list, own[b] = (member m << 20) | tile
+// (one load; the members' tiles are listed member after member).  The stage bodies are those
+// of the single-plan kernels: Stockham passes with runtime length (E = 8 or 12 elements per
+// thread and 256 threads, so a member's tile width is 256 E / N), the register four-step rows
+// for the forward pass of M = 64, the z-marching fixed-point defect where its layout fits, the
+// z Thomas solve of one column per thread for walls, and per-member reductions.  A member whose
+// defect reached rtol skips every later stage (its done flag, read before anything else).
+__device__ __forceinline__ bool batch_skip(const BatchMember* __restrict__ mem, int m) {
+    const int* sk = mem[m].g.skip;
+    return sk && *(volatile const int*)sk;
+}
+
+// The member's descriptor into shared memory (all threads copy; one barrier).
+__device__ __forceinline__ const BatchMember& batch_member(const BatchMember* __restrict__ mem, int m) {
+    __shared__ __align__(16) BatchMember sD;
+    static_assert(sizeof(BatchMember) % 4 == 0, "word copy");
+    const int* src = reinterpret_cast<const int*>(mem + m);
+    int* dst = reinterpret_cast<int*>(&sD);
+    for (int i = threadIdx.x; i < (int)(sizeof(BatchMember) / 4); i += blockDim.x) dst[i] = __ldg(src + i);
+    __syncthreads();
+    return sD;
+}
+
+__global__ void k_b_reset(const BatchMember* __restrict__ mem, int n) {
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= n) return;
+    DevScalars* sc = mem[m].sc;
+    sc->done = 0;
+    sc->fin_count = 0u;
+    sc->pexp = 0;
+}
+
+// KIND 0: the transform of f with the first pass's partial sums; KIND 1: the defect of the
+// member's p with its transform (z-marching fixed point, or the untiled body: fixed point on
+// one-spacing grids, else FP64).
+template <int KIND>
+__global__ void __launch_bounds__(FLUPS_BATCH_THREADS, KIND == 1 ? 2 : 3) k_b_xfwd(const BatchMember* __restrict__ mem,
+                                                                                   const unsigned* __restrict__ own,
+                                                                                   int n) {
+    const unsigned w = __ldg(&own[blockIdx.x]);
+    const int m = (int)(w >> 20), tile = (int)(w & 0xFFFFFu);
+    if (batch_skip(mem, m)) return;
+    const BatchMember& D = batch_member(mem, m);
+    const int nrows = D.g.ny * D.g.nz;
+    if (KIND == 0) {
+        if (D.xr4) xrow4_fwd_body<8, 8, true>(tile, D.f, D.spec, D.g, D.twx, D.twxr, nrows, D.part);
+        else if (D.ex == 12)
+            xfwd_body<float, 12, 0, true>(tile, D.f, nullptr, D.spec, D.g, D.lx, D.twx, D.twxr, D.dd, D.lgx, nrows,
+                                          D.sc, D.part);
+        else
+            xfwd_body<float, 8, 0, true>(tile, D.f, nullptr, D.spec, D.g, D.lx, D.twx, D.twxr, D.dd, D.lgx, nrows,
+                                         D.sc, D.part);
+    } else if (D.zm) {
+        xres_zm_body<8, 2, 0, 0>(tile % D.zbx, tile / D.zbx, D.zg, D.f, D.p, D.spec, D.g, D.lx, D.twx, D.twxr,
+                                 D.zkz, D.sc, D.part, tile);
+    } else if (D.dmode == 2) {
+        if (D.ex == 12)
+            xfwd_body<float, 12, 2, false>(tile, D.f, D.p, D.spec, D.g, D.lx, D.twx, D.twxr, D.dd, D.lgx, nrows,
+                                           D.sc, D.part);
+        else
+            xfwd_body<float, 8, 2, false>(tile, D.f, D.p, D.spec, D.g, D.lx, D.twx, D.twxr, D.dd, D.lgx, nrows,
+                                          D.sc, D.part);
+    } else {
+        if (D.ex == 12)
+            xfwd_body<float, 12, 1, false>(tile, D.f, D.p, D.spec, D.g, D.lx, D.twx, D.twxr, D.dd, D.lgx, nrows,
+                                           D.sc, D.part);
+        else
+            xfwd_body<float, 8, 1, false>(tile, D.f, D.p, D.spec, D.g, D.lx, D.twx, D.twxr, D.dd, D.lgx, nrows,
+                                          D.sc, D.part);
+    }
+}
+
+template <bool INV>
+__global__ void __launch_bounds__(FLUPS_BATCH_THREADS) k_b_ycol(const BatchMember* __restrict__ mem,
+                                                               const unsigned* __restrict__ own, int n) {
+    const unsigned w = __ldg(&own[blockIdx.x]);
+    const int m = (int)(w >> 20), tile = (int)(w & 0xFFFFFu);
+    if (batch_skip(mem, m)) return;
+    const BatchMember& D = batch_member(mem, m);
+    const int B = 1 << D.lgy, nb = (D.g.M + B - 1) / B;
+    if (tile < D.ymain) {
+        if (D.ey == 12) ycol_body<float, 12, INV, false>(tile % nb, tile / nb, D.spec, D.g, D.ly, D.twy, D.lgy, 0);
+        else ycol_body<float, 8, INV, false>(tile % nb, tile / nb, D.spec, D.g, D.ly, D.twy, D.lgy, 0);
+    } else {                                // the Nyquist column kx = M, B planes per tile
+        if (D.ey == 12) ycol_body<float, 12, INV, true>(tile - D.ymain, 0, D.spec, D.g, D.ly, D.twy, D.lgy, D.g.M);
+        else ycol_body<float, 8, INV, true>(tile - D.ymain, 0, D.spec, D.g, D.ly, D.twy, D.lgy, D.g.M);
+    }
+}
+
+__global__ void __launch_bounds__(FLUPS_BATCH_THREADS) k_b_z(const BatchMember* __restrict__ mem,
+                                                            const unsigned* __restrict__ own, int n) {
+    const unsigned w = __ldg(&own[blockIdx.x]);
+    const int m = (int)(w >> 20), tile = (int)(w & 0xFFFFFu);
+    if (batch_skip(mem, m)) return;
+    const BatchMember& D = batch_member(mem, m);
+    if (D.g.walls) {                        // one column per thread
+        ztri_body<float>(tile, D.spec, D.zscr, D.g, D.lamx, D.lamy, D.tri);
+        return;
+    }
+    const int B = 1 << D.lgz, nb = (D.g.M + B - 1) / B;
+    if (tile < D.zmain) {
+        if (D.ez == 12)
+            zper_body<float, 12, false>(tile % nb, tile / nb, D.spec, D.g, D.lz, D.twz, D.lamx, D.lamy, D.lamz, D.lgz, 0);
+        else
+            zper_body<float, 8, false>(tile % nb, tile / nb, D.spec, D.g, D.lz, D.twz, D.lamx, D.lamy, D.lamz, D.lgz, 0);
+    } else {                                // the Nyquist column kx = M, B values of ky per tile
+        if (D.ez == 12)
+            zper_body<float, 12, true>(tile - D.zmain, 0, D.spec, D.g, D.lz, D.twz, D.lamx, D.lamy, D.lamz, D.lgz,
+                                       D.g.M);
+        else
+            zper_body<float, 8, true>(tile - D.zmain, 0, D.spec, D.g, D.lz, D.twz, D.lamx, D.lamy, D.lamz, D.lgz,
+                                      D.g.M);
+    }
+}
+
+// KIND 0: p = x with the mean's partial sums; 1: p += x - <p_0>; 2: p += x.
+template <int KIND>
+__global__ void __launch_bounds__(FLUPS_BATCH_THREADS) k_b_xinv(const BatchMember* __restrict__ mem,
+                                                               const unsigned* __restrict__ own, int n) {
+    constexpr int ACC = KIND == 0 ? 0 : 1;
+    constexpr bool MEAN = KIND == 0, SUBM = KIND == 1;
+    const unsigned w = __ldg(&own[blockIdx.x]);
+    const int m = (int)(w >> 20), tile = (int)(w & 0xFFFFFu);
+    if (batch_skip(mem, m)) return;
+    const BatchMember& D = batch_member(mem, m);
+    const int nrows = D.g.ny * D.g.nz;
+    if (D.ex == 12)
+        xinv_body<float, 12, ACC, MEAN, SUBM>(tile, D.spec, D.p, D.g, D.lx, D.twx, D.twxr, D.lgx, nrows, D.sc, D.part);
+    else
+        xinv_body<float, 8, ACC, MEAN, SUBM>(tile, D.spec, D.p, D.g, D.lx, D.twx, D.twxr, D.lgx, nrows, D.sc, D.part);
+}
+
+// One CTA per member: the sums of its x or defect stage's partials.  WHAT 0: mean and norm of
+// f; 1: the defect norm and the stopping test (sets done); 2: the mean of the first iterate.
+// WHAT 0 and 1 also clear pexp for the inverse pass that follows.
+template <int WHAT>
+__global__ void __launch_bounds__(FIN_THREADS) k_b_fin(const BatchMember* __restrict__ mem, double thr2) {
+    __shared__ double red[3][FIN_THREADS / 32];
+    const BatchMember& D = mem[blockIdx.x];
+    DevScalars* sc = D.sc;
+    if (WHAT == 1 && sc->done) return;
+    double a = 0.0, b = 0.0, c = 0.0;
+    const int np = WHAT == 1 ? D.td : D.tx;   // partials of the defect stage, or of the x stage
+    for (int i = threadIdx.x; i < np; i += FIN_THREADS) {
+        a += __ldcg(D.part + 3 * i + 0);
+        b += __ldcg(D.part + 3 * i + 1);
+        c += __ldcg(D.part + 3 * i + 2);
+    }
+    fin_block_sum(a, b, c, red);
+    if (threadIdx.x == 0) {
+        if (WHAT == 0) {
+            const double mv = a * D.nrm_w;
+            sc->mean_f = mv;
+            sc->f2 = b - 2.0 * mv * c + D.npts * mv * mv;
+            sc->pexp = 0;
+        } else if (WHAT == 1) {
+            sc->r2 = b;
+            if (b <= thr2 * sc->f2) sc->done = 1;
+            sc->pexp = 0;
+        } else {
+            sc->mean_p = a * D.nrm_w;
+        }
+    }
+}
+
+// Sets the conditional handle h to whether some member has not converged (one CTA).
+__global__ void k_b_any(const BatchMember* __restrict__ mem, int n, cudaGraphConditionalHandle h) {
+    int act = 0;
+    for (int m = threadIdx.x; m < n; m += blockDim.x) act |= !batch_skip(mem, m);
+    act = __syncthreads_or(act);
+    if (threadIdx.x == 0) cudaGraphSetConditional(h, act ? 1u : 0u);
+}
+
 }  // namespace
 
 // ------------------------------------------------------------------ launchers
@@ -2181,4 +2494,188 @@ extern "C" flups_status flups_selftest_wait_timeout(void* stream, int limit) {
     cudaFree(err);
     if (e != cudaSuccess) { flups_note_cuda_error(e); return FLUPS_ECUDA; }
     return h ? FLUPS_ETIMEOUT : FLUPS_OK;
+}
+
+// ------------------------------------------------------------ batched ensemble: host side
+bool batch_member_ok(flups_plan P) {
+    if (P->prec != FLUPS_FP32_REFINE || P->bcx != FLUPS_XY_PERIODIC || P->bcy != FLUPS_XY_PERIODIC) return false;
+    auto len_ok = [](int N) {                 // 8 2^a or 12 2^a, at most 256 E points
+        const int E = N % 3 == 0 ? 12 : 8;
+        if (N < E || N > 256 * E) return false;
+        int q = N % 3 == 0 ? N / 3 : N;
+        while (q % 2 == 0) q /= 2;
+        return q == 1;
+    };
+    return len_ok(P->M) && len_ok(P->ny) && (P->bc == FLUPS_BC_WALLS || len_ok(P->nz));
+}
+
+void batch_member_fill(flups_plan P, const double* f, double* p, BatchMember* D) {
+    std::memset(D, 0, sizeof(*D));
+    D->g = plan_geo(P);
+    D->g.skip = &P->sc->done;
+    D->lx = packed(P->lx);
+    D->ly = packed(P->ly);
+    D->lz = packed(P->lz);
+    D->twx = (const float2*)P->twx;
+    D->twxr = (const float2*)P->twxr;
+    D->twy = (const float2*)P->twy;
+    D->twz = (const float2*)P->twz;
+    D->lamx = (const float*)P->lamx;
+    D->lamy = (const float*)P->lamy;
+    D->lamz = (const float*)P->lamz;
+    D->tri = (const float*)P->tri;
+    D->spec = (float2*)P->spec;
+    D->zscr = (float*)P->zscr;
+    D->f = f;
+    D->p = p;
+    D->sc = P->sc;
+    D->part = P->part;
+    D->dd = P->tabs64 + 5 * P->nz;
+    D->nrm_w = 1.0 / ((double)P->nx * P->ny * P->sum_dzf);
+    D->npts = (double)P->npts;
+    auto ecls = [](int N) { return N % 3 == 0 ? 12 : 8; };
+    auto lgw = [](int N, int E) { return ilog2i(FLUPS_BATCH_THREADS * E / N); };
+    D->ex = ecls(P->M);
+    D->ey = ecls(P->ny);
+    D->ez = P->bc == FLUPS_BC_WALLS ? 8 : ecls(P->nz);
+    D->lgx = lgw(P->M, D->ex);
+    D->lgy = lgw(P->ny, D->ey);
+    D->lgz = P->bc == FLUPS_BC_WALLS ? 0 : lgw(P->nz, D->ez);
+    D->dmode = P->uniform_h ? 2 : 1;
+    // M = 64: the register four-step rows take the same 32-row tile as the Stockham body (the
+    // forward pass from f; the inverse stays on the Stockham body, whose registers set the
+    // occupancy of the batched inverse kernel)
+    D->xr4 = P->M == 64 && XRow<8, 8>::B == (1 << D->lgx);
+    D->smx = (unsigned)std::max<size_t>((size_t)P->M * ((1 << D->lgx) + 1) * sizeof(float2),
+                                        D->xr4 ? XRow<8, 8>::SMEM : 0);   // the x stages' largest
+    D->smy = (unsigned)((size_t)P->ny * ((1 << D->lgy) + 1) * sizeof(float2));
+    D->smz = P->bc == FLUPS_BC_WALLS ? 0u : (unsigned)((size_t)P->nz * ((1 << D->lgz) + 1) * sizeof(float2));
+    const int nrows = P->ny * P->nz, bx = 1 << D->lgx, by = 1 << D->lgy, bz = 1 << D->lgz;
+    D->tx = (nrows + bx - 1) / bx;
+    D->ymain = (P->M + by - 1) / by * P->nz;
+    D->ty = D->ymain + (P->nz + by - 1) / by;
+    // the z-marching defect where its layout fits: M a multiple of 32 dividing 256, 8 G | ny
+    const int G = P->M > 0 && FLUPS_BATCH_THREADS % P->M == 0 ? FLUPS_BATCH_THREADS / P->M : 0;
+    D->zm = P->uniform_h && P->M % 32 == 0 && G >= 1 && P->ny % (8 * G) == 0 && P->M <= 256;
+    if (D->zm) {
+        D->zg = G;
+        D->zkz = std::min(8, P->nz);
+        D->zbx = P->ny / (8 * G);
+        D->td = D->zbx * ((P->nz + D->zkz - 1) / D->zkz);
+        D->smd = (unsigned)((size_t)G * xres_smem(P->M));
+    } else {
+        D->td = D->tx;
+        D->smd = D->smx;
+    }
+    if (P->bc == FLUPS_BC_WALLS) {
+        D->zmain = 0;
+        D->tz = (P->nxh * P->ny + FLUPS_BATCH_THREADS - 1) / FLUPS_BATCH_THREADS;
+    } else {
+        D->zmain = (P->M + bz - 1) / bz * P->ny;
+        D->tz = D->zmain + (P->ny + bz - 1) / bz;
+    }
+}
+
+namespace {
+
+void batch_smem_attrs(const BatchLaunch& L) {
+    auto smem_attr = [](auto kern, size_t bytes) {
+        if (bytes > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    };
+    smem_attr(k_b_xfwd<0>, L.smem_x);
+    smem_attr(k_b_xfwd<1>, L.smem_d);
+    smem_attr(k_b_xinv<0>, L.smem_x);
+    smem_attr(k_b_xinv<1>, L.smem_x);
+    smem_attr(k_b_xinv<2>, L.smem_x);
+    smem_attr(k_b_ycol<false>, L.smem_y);
+    smem_attr(k_b_ycol<true>, L.smem_y);
+    smem_attr(k_b_z, L.smem_z);
+}
+
+// The first FP32 solve and the first defect test (8 kernels).
+int batch_first(const BatchLaunch& L, cudaStream_t st, double thr2) {
+    const int T = FLUPS_BATCH_THREADS, n = L.n;
+    k_b_reset<<<(n + 127) / 128, 128, 0, st>>>(L.mem, n);
+    k_b_xfwd<0><<<L.total_x, T, L.smem_x, st>>>(L.mem, L.ox, n);
+    k_b_fin<0><<<n, FIN_THREADS, 0, st>>>(L.mem, thr2);
+    k_b_ycol<false><<<L.total_y, T, L.smem_y, st>>>(L.mem, L.oy, n);
+    k_b_z<<<L.total_z, T, L.smem_z, st>>>(L.mem, L.oz, n);
+    k_b_ycol<true><<<L.total_y, T, L.smem_y, st>>>(L.mem, L.oy, n);
+    k_b_xinv<0><<<L.total_x, T, L.smem_x, st>>>(L.mem, L.ox, n);
+    k_b_fin<2><<<n, FIN_THREADS, 0, st>>>(L.mem, thr2);
+    k_b_xfwd<1><<<L.total_d, T, L.smem_d, st>>>(L.mem, L.od, n);
+    k_b_fin<1><<<n, FIN_THREADS, 0, st>>>(L.mem, thr2);
+    return 10;
+}
+
+// One more FP32 solve of the defect (it = 1: with the mean correction) and the next defect test.
+int batch_iteration(const BatchLaunch& L, cudaStream_t st, double thr2, int it) {
+    const int T = FLUPS_BATCH_THREADS, n = L.n;
+    k_b_ycol<false><<<L.total_y, T, L.smem_y, st>>>(L.mem, L.oy, n);
+    k_b_z<<<L.total_z, T, L.smem_z, st>>>(L.mem, L.oz, n);
+    k_b_ycol<true><<<L.total_y, T, L.smem_y, st>>>(L.mem, L.oy, n);
+    if (it == 1) k_b_xinv<1><<<L.total_x, T, L.smem_x, st>>>(L.mem, L.ox, n);
+    else k_b_xinv<2><<<L.total_x, T, L.smem_x, st>>>(L.mem, L.ox, n);
+    k_b_xfwd<1><<<L.total_d, T, L.smem_d, st>>>(L.mem, L.od, n);
+    k_b_fin<1><<<n, FIN_THREADS, 0, st>>>(L.mem, thr2);
+    return 6;
+}
+
+}  // namespace
+
+int launch_batch_fixed(const BatchLaunch& L, double rtol, int max_iter) {
+    batch_smem_attrs(L);
+    const double thr2 = rtol * rtol;
+    int k = batch_first(L, L.stream, thr2);
+    for (int it = 1; it < max_iter; ++it) k += batch_iteration(L, L.stream, thr2, it);
+    return cudaGetLastError() == cudaSuccess ? k : -1;
+}
+
+int capture_batch_graph(const BatchLaunch& L, cudaStream_t aux, double rtol, int max_iter, cudaGraph_t* out) {
+    *out = nullptr;
+    batch_smem_attrs(L);
+    const double thr2 = rtol * rtol;
+    cudaStream_t st = L.stream;
+    cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return -1;
+    int k = batch_first(L, st, thr2);
+    for (int it = 1; it < max_iter && e == cudaSuccess; ++it) {
+        // iteration it runs only while some member is active: k_b_any sets the handle, an IF
+        // node holds the iteration's kernels (captured on aux into the node's body graph)
+        cudaStreamCaptureStatus cs;
+        cudaGraph_t g = nullptr;
+        const cudaGraphNode_t* deps = nullptr;
+        size_t nd = 0;
+        e = cudaStreamGetCaptureInfo(st, &cs, nullptr, &g, nullptr, nullptr, nullptr);
+        cudaGraphConditionalHandle h = 0;
+        if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&h, g, 0u, cudaGraphCondAssignDefault);
+        if (e != cudaSuccess) break;
+        k_b_any<<<1, 256, 0, st>>>(L.mem, L.n, h);
+        ++k;
+        e = cudaStreamGetCaptureInfo(st, &cs, nullptr, &g, &deps, nullptr, &nd);
+        if (e != cudaSuccess) break;
+        cudaGraphNodeParams np = {};
+        np.type = cudaGraphNodeTypeConditional;
+        np.conditional.handle = h;
+        np.conditional.type = cudaGraphCondTypeIf;
+        np.conditional.size = 1;
+        cudaGraphNode_t node = nullptr;
+        e = cudaGraphAddNode(&node, g, deps, nullptr, nd, &np);
+        if (e != cudaSuccess) break;
+        cudaGraph_t body = np.conditional.phGraph_out[0];
+        e = cudaStreamBeginCaptureToGraph(aux, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) break;
+        k += batch_iteration(L, aux, thr2, it);
+        cudaGraph_t bg = nullptr;
+        e = cudaStreamEndCapture(aux, &bg);
+        if (e == cudaSuccess) e = cudaStreamUpdateCaptureDependencies(st, &node, nullptr, 1, cudaStreamSetCaptureDependencies);
+    }
+    cudaGraph_t g = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(st, &g);
+    if (e != cudaSuccess || e2 != cudaSuccess || cudaGetLastError() != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return -1;
+    }
+    *out = g;
+    return k;
 }

@@ -216,6 +216,57 @@ int flups_pipe_lgB(int N, int M, int kind);
 // where the kernel does not apply; launch_cols4 runs the y transform (kind 0, inv picks the
 // direction) or the periodic z solve (kind 1) on the plan's spectrum and returns false
 // without launching where the kernel does not apply.
+// One member of a batched ensemble solve (the stage kernels of fft_kernels.cu walk the
+// concatenated (member, tile) lists of all members; 256 threads per CTA).  Filled on the host
+// from the member's plan.
+#define FLUPS_BATCH_THREADS 256
+struct BatchMember {
+    Geo g;                              // g.skip = &sc->done
+    FftLen lx, ly, lz;                  // packed radix codes
+    const float2 *twx, *twxr, *twy, *twz;
+    const float *lamx, *lamy, *lamz, *tri;
+    float2* spec;
+    float* zscr;
+    const double* f;
+    double* p;
+    DevScalars* sc;
+    double* part;
+    const double* dd;                   // diagonal of the z operator (FP64 defect)
+    double nrm_w, npts;                 // 1 / (nx ny sum dzf), nx ny nz
+    int ex, ey, ez;                     // elements per thread of the x, y, z transforms (8 or 12)
+    int lgx, lgy, lgz;                  // log2 tile widths: 2^lg N / e = FLUPS_BATCH_THREADS
+    int dmode;                          // defect: 2 (one spacing, fixed point) or 1 (FP64)
+    int xr4;                            // forward x transform by the register four-step rows (M = 64)
+    unsigned smx, smy, smz;             // dynamic shared memory of a tile of the x, y, z stages
+    // the defect stage: z-marching fixed-point rows (zm = 1: G = zg groups of M threads, kz planes
+    // per tile, zbx row blocks of 8 G rows per plane) or the untiled body (zm = 0, tiles as x)
+    int zm, zg, zkz, zbx, td;
+    unsigned smd;
+    int tx, ty, tz;                     // tiles of the x, y, z stages
+    int ymain, zmain, xq;               // main tiles of the y and z stages; x tiles per plane row set
+};
+// Batched stages (fft_kernels.cu).  o*: the work list of the x, y, z and defect stages (device
+// memory), item b = (member << 20) | tile, members in order; smem_*: the largest dynamic shared
+// memory a member's tile of that stage needs.
+struct BatchLaunch {
+    const BatchMember* mem;
+    const unsigned *ox, *oy, *oz, *od;
+    int n, total_x, total_y, total_z, total_d;
+    size_t smem_x, smem_y, smem_z, smem_d;
+    cudaStream_t stream;
+};
+// The fixed FP32 + FP64-defect sequence of every member (as launch_solve32_fixed) with one
+// kernel per stage; returns the kernels launched, or -1 on a launch error.
+int launch_batch_fixed(const BatchLaunch& L, double rtol, int max_iter);
+// The same sequence captured as a graph in which every iteration after the first sits in a
+// conditional (IF) node that runs only while some member has not converged (aux: a second
+// stream for the nodes' bodies).  Returns the kernels in the graph, or -1 (nothing captured).
+int capture_batch_graph(const BatchLaunch& L, cudaStream_t aux, double rtol, int max_iter, cudaGraph_t* out);
+// Whether a plan's member can take the batched stages (x, y periodic; lengths 8 * 2^a or 12 * 2^a;
+// FP32 + refine).
+bool batch_member_ok(flups_plan P);
+void batch_member_fill(flups_plan P, const double* f, double* p, BatchMember* out);
+
 // Register four-step x-row kernels (xrow_kernels.cu) for M = nx / 2 in {64, ..., 1024}: rows
 // per CTA (0: not available); forward from f (stats: the partial sums of the first pass) and
 // inverse (mode 0: p = x with the mean's partial sums, 1: p += x - <p_0>, 2: p += x, 3: p = x).

@@ -1,10 +1,8 @@
-// xrow_kernels.cu - FP32 transforms along x held in registers (FluTAS Sec. 3.3.1, steps 2 and
-// 8: the real-to-complex transform of each x row of the right-hand side, and its inverse
-// into p), for rows of nx = 2M points with M = N1 N2 a power of two from 64 to 1024.  The
-// forward transform and the row layout are those of xrow.cuh.  The inverse forms
-// Z_k = A_k + i conj(W_nx^k) D_k, A_k = (X_k + conj X_{M-k})/2, D_k = (X_k - conj X_{M-k})/2,
-// with X_0 and X_M taken real, through shared memory (the partner of X_0 is X_M, not a lane's
-// value), then runs the four steps backwards and ends in the layout the forward loads from.
+// xrow_kernels.cu - kernels and launchers of the FP32 transforms along x held in registers
+// (FluTAS Sec. 3.3.1, steps 2 and 8: the real-to-complex transform of each x row of the
+// right-hand side, and its inverse into p), for rows of nx = 2M points with M = N1 N2 a power
+// of two from 64 to 1024.  The row layout, the forward and inverse bodies and their algebra
+// are in xrow.cuh (shared with the defect pass and the batched ensemble stages).
 #include "blocksum.cuh"
 #include "flups_impl.cuh"
 #include "fp_bits.cuh"
@@ -13,180 +11,20 @@
 
 namespace {
 
-// x = xh + xl for a binary64 x, by integer operations: xh = x with the low 29 significand bits
-// cleared (exactly a binary32 number), xl = those 29 bits, rounded to binary32 (relative error
-// 2^-24 of xl, so 2^-48 of x).  For |x| below 2^-126 both are 0 (the value is dropped); for
-// |x| at or above 2^128, infinities and NaNs, xh is x rounded to binary32 (infinite or NaN).
-__device__ __forceinline__ void split_d(double x, float& xh, float& xl) {
-    const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
-    const int e = (int)((hi >> 20) & 0x7FFu);
-    const unsigned sgn = hi & 0x80000000u;
-    if ((unsigned)(e - 897) <= 253u) {
-        xh = __uint_as_float(sgn | ((unsigned)(e - 896) << 23) | ((hi & 0xFFFFFu) << 3) | (lo >> 29));
-        const int es = e - 948;             // the binary32 exponent field of 2^(e - 1075)
-        const float sc = es >= 1 ? __uint_as_float((unsigned)es << 23) : 0.f;
-        xl = __uint_as_float(__float_as_uint(__uint2float_rn(lo & 0x1FFFFFFFu) * sc) | sgn);
-    } else {
-        xh = e < 897 ? 0.f : d2f_bits(x);
-        xl = 0.f;
-    }
-}
-
-// (sh, sl) += a with an exact two-sum of sh and a (sl collects the rounding error).
-__device__ __forceinline__ void two_sum_acc(float& sh, float& sl, float a) {
-    const float s = sh + a, bb = s - sh;
-    sl += (sh - (s - bb)) + (a - bb);
-    sh = s;
-}
-
-// Forward: f (nx reals per row) -> the half spectrum S (M + 1 values per row, pitch ldS).
-// STATS: also the partial sums sum_k dzf_k sum_ij f, sum f^2 and sum f of each CTA into part:
-// a thread's row sum of f as a pair of binary32 numbers (f split into xh + xl, xh added by exact
-// two-sums), so no FP64 instruction runs per point; sums of f^2 and f in FP32 per thread; all
-// three in FP64 across threads.
 template <int N1, int N2, bool STATS>
 __global__ void __launch_bounds__(XROW_THREADS, N1 >= 32 ? 2 : 3) k_xrow4_fwd(const double* __restrict__ f, float2* __restrict__ S,
-                                                          Geo g, const float2* __restrict__ tw,
-                                                          const float2* __restrict__ twr, int nrows,
-                                                          double* __restrict__ part) {
-    if (g.skip && *g.skip) return;   // graph-capturable solve: this member already converged
-    using X = XRow<N1, N2>;
-    extern __shared__ __align__(16) float2 ex[];
-    const int tid = threadIdx.x, c = tid / N2, t = tid % N2;
-    const int row = blockIdx.x * X::B + c;
-    const bool live = row < nrows;
-    const double2* src = reinterpret_cast<const double2*>(f + (size_t)(live ? row : 0) * g.nx) + t;
-    float2 v[N1];
-    float sh = 0.f, sl = 0.f, acc2 = 0.f, acc1 = 0.f;
-    // f in chunks of up to 16 loads (the row sums of a chunk are formed before the next loads)
-    constexpr int CH = N1 < 16 ? N1 : 16;
-#pragma unroll
-    for (int h = 0; h < N1; h += CH) {
-        double2 fv[CH];
-#pragma unroll
-        for (int i = 0; i < CH; ++i) fv[i] = live ? __ldg(src + N2 * (h + i)) : make_double2(0.0, 0.0);
-#pragma unroll
-        for (int i = 0; i < CH; ++i) {
-            v[h + i] = make_float2(d2f_bits(fv[i].x), d2f_bits(fv[i].y));
-            if (STATS) {
-                float h0, l0, h1, l1;
-                split_d(fv[i].x, h0, l0);
-                split_d(fv[i].y, h1, l1);
-                two_sum_acc(sh, sl, h0);
-                two_sum_acc(sh, sl, h1);
-                sl += l0 + l1;
-                acc2 = fmaf(v[h + i].x, v[h + i].x, fmaf(v[h + i].y, v[h + i].y, acc2));
-                acc1 += v[h + i].x + v[h + i].y;
-            }
-        }
-    }
-    xrow4_fwd_tail<N1, N2>(v, ex, c, t, true, live, tw, twr, S + (size_t)(live ? row : 0) * g.ldS);
-    if (STATS) {
-        const double wz = live ? __ldg(g.dzf + row / g.ny) : 0.0;
-        block_sum_abc<true, true, true>((f2d_bits(sh) + f2d_bits(sl)) * wz, acc2, acc1, part);
-    }
+                                                                             Geo g, const float2* __restrict__ tw,
+                                                                             const float2* __restrict__ twr, int nrows,
+                                                                             double* __restrict__ part) {
+    xrow4_fwd_body<N1, N2, STATS>(blockIdx.x, f, S, g, tw, twr, nrows, part);
 }
 
-// Inverse: S -> p (ACC = 0: p = x; ACC = 1: p += x, in FP64).  MEAN (with ACC = 0): the
-// partial sums of dzf * p (the values are binary32 numbers: summed per thread in pairs of
-// binary32 with exact two-sums, then in FP64); SUBM (with ACC = 1): x - <p_0> is added.  The
-// largest binary64 exponent written goes to sc->pexp (the scale of the next defect).
 template <int N1, int N2, int ACC, bool MEAN, bool SUBM>
 __global__ void __launch_bounds__(XROW_THREADS) k_xrow4_inv(const float2* __restrict__ S, double* __restrict__ p,
                                                           Geo g, const float2* __restrict__ tw,
                                                           const float2* __restrict__ twr, int nrows,
                                                           DevScalars* __restrict__ sc, double* __restrict__ part) {
-    if (g.skip && *g.skip) return;   // graph-capturable solve: this member already converged
-    using X = XRow<N1, N2>;
-    constexpr int M = X::M, Q = X::Q, XP = X::XP;
-    extern __shared__ __align__(16) float2 ex[];
-    const int tid = threadIdx.x, c = tid / N2, t = tid % N2;
-    const int row = blockIdx.x * X::B + c;
-    const bool live = row < nrows;
-    const float2* in = S + (size_t)(live ? row : 0) * g.ldS;
-    float2* e = ex + c * XP;
-    float2 w[Q][N2];
-#pragma unroll
-    for (int q = 0; q < Q; ++q)
-#pragma unroll
-        for (int k2 = 0; k2 < N2; ++k2) {
-            const int k = t + N2 * q + N1 * k2;
-            w[q][k2] = live ? in[k] : make_float2(0.f, 0.f);
-            e[k] = w[q][k2];
-        }
-    if (t == 0) e[M] = live ? in[M] : make_float2(0.f, 0.f);
-    __syncthreads();
-#pragma unroll
-    for (int q = 0; q < Q; ++q)
-#pragma unroll
-        for (int k2 = 0; k2 < N2; ++k2) {
-            const int k = t + N2 * q + N1 * k2;
-            float2 xk = w[q][k2], xm = e[M - k];
-            if (k == 0) { xk.y = 0.f; xm.y = 0.f; }
-            const float ax = (xk.x + xm.x) * 0.5f, ay = (xk.y - xm.y) * 0.5f;
-            const float dx = (xk.x - xm.x) * 0.5f, dy = (xk.y + xm.y) * 0.5f;
-            const float2 wt = wsplit<M>(twr, k);
-            const float bxx = dx * wt.x + dy * wt.y, byy = dy * wt.x - dx * wt.y;
-            w[q][k2] = make_float2(ax - byy, ay + bxx);
-        }
-#pragma unroll
-    for (int q = 0; q < Q; ++q) RegDft<N2, true>::run(w[q]);
-    __syncthreads();                        // every pairing read is done: the area takes the exchange
-    sfor<Q>([&](auto qc) {
-        constexpr int q = decltype(qc)::value;
-        const int k1 = t + N2 * q;
-        sfor<N2>([&](auto n2c) {
-            constexpr int n2 = decltype(n2c)::value;
-            float2 a = w[q][n2];
-            if (n2 > 0) a = tmul<true>(a, __ldg(&tw[(n2 * k1) & (M - 1)]));
-            e[k1 * (N2 + 1) + n2] = a;
-        });
-    });
-    double2* dst = reinterpret_cast<double2*>(p + (size_t)(live ? row : 0) * g.nx) + t;
-    // p += x: the old p is loaded before the last exchange and DFT (where the registers allow)
-    constexpr bool PRE = ACC && N1 <= 16;
-    double2 pold[PRE ? N1 : 1];
-    if (PRE) {
-#pragma unroll
-        for (int n1 = 0; n1 < N1; ++n1) pold[PRE ? n1 : 0] = live ? dst[N2 * n1] : make_double2(0.0, 0.0);
-    }
-    __syncthreads();
-    float2 v[N1];
-#pragma unroll
-    for (int k1 = 0; k1 < N1; ++k1) v[k1] = e[k1 * (N2 + 1) + t];
-    RegDft<N1, true>::run(v);
-    float msub = 0.f;
-    if (SUBM) msub = (float)sc->mean_p;
-    int emax = 0;
-    float sh = 0.f, sl = 0.f;               // the binary32 pair sum of MEAN
-#pragma unroll
-    for (int n1 = 0; n1 < N1; ++n1) {
-        float2 z = v[n1];
-        if (SUBM) { z.x -= msub; z.y -= msub; }
-        double2 o;
-        if (ACC) {
-            if (PRE) o = pold[PRE ? n1 : 0];
-            else o = live ? dst[N2 * n1] : make_double2(0.0, 0.0);
-            o.x += f2d_bits(z.x);
-            o.y += f2d_bits(z.y);
-        } else {
-            o = make_double2(f2d_bits(z.x), f2d_bits(z.y));
-            if (MEAN) {
-                two_sum_acc(sh, sl, z.x);
-                two_sum_acc(sh, sl, z.y);
-            }
-        }
-        if (live) dst[N2 * n1] = o;
-        const int ex_ = (int)((__double_as_longlong(o.x) >> 52) & 0x7FF);
-        const int ey_ = (int)((__double_as_longlong(o.y) >> 52) & 0x7FF);
-        emax = max(emax, max(ex_, ey_));
-    }
-    emax = __reduce_max_sync(0xffffffffu, emax);
-    if ((tid & 31) == 0) atomicMax(&sc->pexp, emax);
-    if (MEAN) {
-        const double wz = live ? __ldg(g.dzf + row / g.ny) : 0.0;
-        block_sum_abc<true, false, false>((f2d_bits(sh) + f2d_bits(sl)) * wz, 0.f, 0.f, part);
-    }
+    xrow4_inv_body<N1, N2, ACC, MEAN, SUBM>(blockIdx.x, S, p, g, tw, twr, nrows, sc, part);
 }
 
 template <typename K, typename... A>

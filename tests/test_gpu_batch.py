@@ -7,6 +7,11 @@
   oracle direct solve; a graph replay must reproduce the first launch bit for bit.
 * The mixed-size ensemble of 64 members {32, 48, 64, 96, 128}^3 (periodic and z walls,
   density ratios in [1, 20]) at full size.
+* Ensembles whose members all have transform lengths 8 2^a or 12 2^a run one kernel per stage
+  for all members (7 max_iter + 3 graph kernels whatever the member count: 10 for the first
+  solve and defect test, then per iteration a conditional node's 6 and the kernel that sets
+  its condition); an ensemble with a shorter length captures each member's own kernel
+  sequence instead, and must solve to the same bar.
 """
 
 import numpy as np
@@ -131,3 +136,27 @@ def test_mixed_size_ensemble_of_64():
         if m % 7 == 0:      # a sample of ten members (every size, both z treatments): p itself
             po = oracle.solve(fo, grid_of(c))
             assert np.linalg.norm(pg - po) / np.linalg.norm(po) <= 1e-8, c.name
+
+
+def test_stage_kernels_graph_size_and_per_member_fallback():
+    cases = small_members()[:4]
+    fs = [torch.from_numpy(member_rhs(c)).cuda() for c in cases]
+    ps = [torch.empty_like(f) for f in fs]
+    with flups.Batch([spec(c) for c in cases], nstreams=4, autotune=False) as b:
+        b.solve(fs, ps, rtol=1e-10, max_iter=5)
+        assert b.graph_kernels == 7 * 5 + 3          # one kernel per stage for all members
+    # a member of nx = 8 (a 4-point complex x transform) takes the per-member sequences
+    small = synth.random_fields(8, 16, 12, "walls", False, seed=97)
+    cases2 = [cases[0], small]
+    fs2 = [torch.from_numpy(member_rhs(c)).cuda() for c in cases2]
+    ps2 = [torch.empty_like(f) for f in fs2]
+    with flups.Batch([spec(c) for c in cases2], nstreams=2, autotune=False) as b:
+        infos = b.solve(fs2, ps2, rtol=1e-10, max_iter=5)
+        assert b.graph_kernels > 7 * 5 + 3
+    for c, f, p, inf in zip(cases2, fs2, ps2, infos):
+        g = grid_of(c)
+        fo, pg = f.cpu().numpy(), p.cpu().numpy()
+        assert inf.rel_res <= 1e-10
+        assert oracle.rel_residual(fo, pg, g) <= 1.5e-10
+        po = oracle.solve(fo, g)
+        assert np.linalg.norm(pg - po) / np.linalg.norm(po) <= 1e-8
