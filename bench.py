@@ -107,9 +107,10 @@ MEASURED_TRAFFIC_PER_LAUNCH = {
     # (61.2 B/point; constant-density tiles take 56 B/point, the 11.2 % of tiles with density
     # variation 40 B/point more: 60.5 B/point)
     ("emulsion512", "k_correct"): 5_030_000_000 + 3_180_000_000,
-    # the fused defect + forward x pass (MODE 2, integer defect): 540 MB read + 119 MB written
-    # per launch on 512x128x512 (19.7 B/point against 20 algorithmic), scaled by points to 512^3
-    ("emulsion512", "k_xfwd_residual32"): 2_640_000_000,
+    # the fused defect + forward x pass (k_xres_zm: z-marching integer defect, register
+    # four-step transform): 600 MB read + 126 MB written per launch on 512x128x512 (21.6 B/point
+    # against 20 algorithmic), scaled by points to 512^3
+    ("emulsion512", "k_xfwd_residual32"): 2_905_000_000,
 }
 
 
