@@ -94,6 +94,31 @@ KERNEL_WORK = {
 }
 
 
+# On one-spacing grids where the z-marching defect and the register x rows apply, the first FP32
+# iterate is held in binary32 until the first update: the first inverse writes 4 B a point
+# instead of 8, the first defect and the first update read 4 B of p instead of 8.
+P32_FIRST = {"k_xinv32": 4 + 4, "k_xfwd_residual32": 8 + 4 + 4, "k_xinv_acc32": 4 + 4 + 8}
+
+
+def p32_first(c):
+    """Whether the plan of case c keeps its first FP32 iterate in binary32."""
+    nz, ny, nx = c.shape
+    uniform = c.dx == c.dy and all(float(d) == c.dx for d in np.atleast_1d(c.dzf))
+    return uniform and nx // 2 in (64, 128, 256, 512) and ny % 8 == 0
+
+
+def solve_bytes_per_point(k, launches_per_solve, p32):
+    """Compulsory bytes per point of one launch of solve kernel k (averaged over its launches in
+    one solve: with p32 only the first launch takes the binary32 iterate)."""
+    b = KERNEL_WORK[k]["bytes"]
+    if not p32 or k not in P32_FIRST or not b:
+        return b
+    if k == "k_xinv32":
+        return P32_FIRST[k]
+    n = max(launches_per_solve, 1.0)
+    return (P32_FIRST[k] + b * (n - 1.0)) / n
+
+
 # Kernels of the FP32+refine solve (f -> p); the roofline object names the one that takes most
 # of the solve's time.
 SOLVE_KERNELS = ("k_xfwd_f32", "k_xfwd_residual32", "k_xres_norm32", "k_ycol32", "k_zper32", "k_ztri32",
@@ -107,10 +132,6 @@ MEASURED_TRAFFIC_PER_LAUNCH = {
     # (61.2 B/point; constant-density tiles take 56 B/point, the 11.2 % of tiles with density
     # variation 40 B/point more: 60.5 B/point)
     ("emulsion512", "k_correct"): 5_030_000_000 + 3_180_000_000,
-    # the fused defect + forward x pass (k_xres_zm: z-marching integer defect, register
-    # four-step transform): 600 MB read + 126 MB written per launch on 512x128x512 (21.6 B/point
-    # against 20 algorithmic), scaled by points to 512^3
-    ("emulsion512", "k_xfwd_residual32"): 2_905_000_000,
 }
 
 
@@ -985,28 +1006,37 @@ def main():
     prof = out["prof"]
     tot_prof = sum(ms for ms, n in prof.values()) or 1.0
 
+    # solves in the profiled steps: the first forward x pass runs once per solve
+    nsolve = max(prof.get("k_xfwd_f32", (0.0, 1.0))[1], 1e-9)
+    p32 = p32_first(c)
+
+    def kbytes(k, n):
+        w = KERNEL_WORK.get(k)
+        if not w or not w.get("bytes"):
+            return None
+        return solve_bytes_per_point(k, n / nsolve, p32) if k in SOLVE_KERNELS else w["bytes"]
+
     def kernel_entry(k, ms, n):
         e = {"ms_per_step": round(ms, 4), "launch_regions_per_step": n, "share": round(ms / tot_prof, 4)}
-        w = KERNEL_WORK.get(k)
-        if w and w.get("bytes") and n:
-            gbs = w["bytes"] * npts / (ms / n * 1e-3) / 1e9
+        b = kbytes(k, n)
+        if b and n:
+            gbs = b * npts / (ms / n * 1e-3) / 1e9
             e["algorithmic_GBps"] = round(gbs, 1)
             e["hbm_frac"] = round(gbs / pk["hbm_gbs"], 4)
-            e["bytes_per_point"] = w["bytes"]
+            e["bytes_per_point"] = round(b, 2)
         return e
 
     kernels = {k: kernel_entry(k, ms, n) for k, (ms, n) in sorted(prof.items(), key=lambda kv: -kv[1][0])}
     solve_prof = {k: v for k, v in prof.items() if k in SOLVE_KERNELS}
     dom = max(solve_prof, key=lambda k: solve_prof[k][0])
-    work = KERNEL_WORK.get(dom, {"bound": "hbm", "bytes": None})
+    work = dict(KERNEL_WORK.get(dom, {"bound": "hbm", "bytes": None}))
+    if work.get("bytes"):
+        work["bytes"] = round(kbytes(dom, prof[dom][1]), 2)
     dom_ms_per_region = prof[dom][0] / max(prof[dom][1], 1e-9)
     achieved = (work["bytes"] or 0) * npts / (dom_ms_per_region * 1e-3) / 1e9
     peak, unit, psrc = pk["hbm_gbs"], "GB/s", f"MEASURED_PEAKS.json hbm_gbs ({pk_kind})"
-    # the solve as a whole against its compulsory traffic (bytes per point of the passes it ran,
-    # per solve: the first forward x pass runs once per solve)
-    nsolve = max(solve_prof.get("k_xfwd_f32", (0.0, 1.0))[1], 1e-9)
-    solve_bytes = sum(KERNEL_WORK[k]["bytes"] * n for k, (ms, n) in solve_prof.items()
-                      if KERNEL_WORK.get(k, {}).get("bytes")) / nsolve
+    # the solve as a whole against its compulsory traffic (bytes per point of the passes it ran)
+    solve_bytes = sum(kbytes(k, n) * n for k, (ms, n) in solve_prof.items() if kbytes(k, n)) / nsolve
     solve_ms_prof = sum(ms for ms, n in solve_prof.values()) / nsolve
     line = {
         "metric": METRIC,

@@ -15,6 +15,7 @@
 // folded into the eigenvalue / tridiagonal tables, M = nx/2.
 #include <cstdlib>
 #include <cstring>
+#include <type_traits>
 
 #include "flups_impl.cuh"
 #include "tma_pipe.cuh"
@@ -476,6 +477,15 @@ __global__ void __launch_bounds__(512) k_xfwd(const double* __restrict__ f, cons
     xfwd_body<T, E, MODE, STATS>(blockIdx.x, f, p, S, g, L, tw, twr, dd, lgB, nrows, sc, part);
 }
 
+// fixq of a binary32 value at sh = pexp - 5, i.e. x * 2^(1080 - pexp) truncated toward zero, with
+// two binary32 products by ka = 2^a, kb = 2^b (a + b = 1080 - pexp, each within the binary32
+// exponent range) and one conversion to a 64-bit integer.  Both products are exact while the
+// value stays a normal number; a product in the subnormal range has magnitude below 2^-126 and
+// truncates to 0 either way, and |x| < 2^(pexp - 1022) keeps the result below 2^58.
+__device__ __forceinline__ long long fixf(float x, float ka, float kb) {
+    return __float2ll_rz(__fmul_rn(__fmul_rn(x, ka), kb));
+}
+
 // The FP32 refinement's exact defect on one-spacing grids (MODE 2: with the forward transform
 // of r; MODE 3: the partial sums of r^2 only), marching up through z.  A CTA owns a block of
 // E = 8 consecutive rows j0 .. j0+7 of the planes k0 .. k1-1, one thread per pair position n.
@@ -492,13 +502,16 @@ __global__ void __launch_bounds__(512) k_xfwd(const double* __restrict__ f, cons
 // per chunk of kz planes (3.25 when every row converts its own z neighbours).  With MODE 2 the
 // transform tile reuses the shared rows after each plane's stencil.  part[b]
 // (b = blockIdx.x + gridDim.x blockIdx.y) takes the block sums of r^2.
+// PT = float: p is the first FP32 iterate held in binary32 (rows of nx values, as p), read at
+// 4 bytes a point and taken to fixed point by fixf, the same integers as fixq of its binary64
+// value.
 // As a body: G groups of M threads (the CTA's G row blocks j0 = (bx G + grp) 8 .. +7, consecutive,
 // of the planes by kz .. by kz + kz - 1), each group with its own shared rows; the Stockham tail
 // transforms the 8 G rows together (the four-step tail, N1 > 0, takes G = 1).  part[pidx]
 // takes the CTA's sum of r^2.
-template <int E, int MODE, int N1, int N2>
+template <int E, int MODE, int N1, int N2, typename PT>
 __device__ __forceinline__ void xres_zm_body(int bx, int by, int G, const double* __restrict__ f,
-                                             const double* __restrict__ p, float2* __restrict__ S, const Geo& g,
+                                             const PT* __restrict__ p, float2* __restrict__ S, const Geo& g,
                                              const FftLen& L, const float2* __restrict__ tw,
                                              const float2* __restrict__ twr, int kz,
                                              const DevScalars* __restrict__ sc, double* __restrict__ part,
@@ -528,7 +541,19 @@ __device__ __forceinline__ void xres_zm_body(int bx, int by, int G, const double
         ipath = okm && es >= -126 && es <= 60;
         if (ipath) rscale = __int_as_float((es + 127) << 23);
     }
-    const double2* P2 = reinterpret_cast<const double2*>(p);
+    constexpr bool PF = sizeof(PT) == 4;
+    typedef typename cplx<PT>::t P2T;        // one pair of p: float2 or double2
+    float ka = 1.f, kb = 1.f;                // fixf's factors (PF): 2^a 2^b = 2^(1080 - pexp)
+    if (PF) {
+        const int s2 = 1080 - pe_, a2 = s2 >> 1;
+        ka = __int_as_float((min(max(a2, -126), 127) + 127) << 23);
+        kb = __int_as_float((min(max(s2 - a2, -126), 127) + 127) << 23);
+    }
+    auto fix2 = [&](const P2T& v) {
+        if constexpr (PF) return make_longlong2(fixf(v.x, ka, kb), fixf(v.y, ka, kb));
+        else return make_longlong2(fixq(v.x, sh), fixq(v.y, sh));
+    };
+    const P2T* P2 = reinterpret_cast<const P2T*>(p);
     const double2* F2 = reinterpret_cast<const double2*>(f);
     const int nw_ = n == 0 ? M - 1 : n - 1, ne_ = n + 1 == M ? 0 : n + 1;
     auto prow = [&](int k, int j) { return P2 + ((size_t)k * g.ny + j) * M + n; };
@@ -537,8 +562,7 @@ __device__ __forceinline__ void xres_zm_body(int bx, int by, int G, const double
     // the centre of plane k0 with its y halo into shared memory, the plane below into LO
 #pragma unroll
     for (int r = 0; r < E + 2; ++r) {
-        const double2 v = __ldg(prow(k0, wrapm(j0 - 1 + r, g.ny)));
-        Q[r * M + n] = make_longlong2(fixq(v.x, sh), fixq(v.y, sh));
+        Q[r * M + n] = fix2(__ldg(prow(k0, wrapm(j0 - 1 + r, g.ny))));
     }
     {
         const bool has = !g.walls || k0 > 0;
@@ -546,10 +570,7 @@ __device__ __forceinline__ void xres_zm_body(int bx, int by, int G, const double
 #pragma unroll
         for (int c = 0; c < E; ++c) {
             longlong2 q = make_longlong2(0, 0);
-            if (has) {
-                const double2 v = __ldg(prow(kb, j0 + c));
-                q = make_longlong2(fixq(v.x, sh), fixq(v.y, sh));
-            }
+            if (has) q = fix2(__ldg(prow(kb, j0 + c)));
             LO[c * M + n] = q;
         }
     }
@@ -562,24 +583,26 @@ __device__ __forceinline__ void xres_zm_body(int bx, int by, int G, const double
         const size_t row0 = (size_t)k * g.ny + j0;
         // every global load of the plane first (p of plane k+1 with its y halo, f of plane k),
         // so that one memory latency per plane is exposed
-        double2 pu[E + 2], fv[E];
+        P2T pu[E + 2];
+        double2 fv[E];
 #pragma unroll
         for (int c = 0; c < E; ++c) fv[c] = __ldg(F2 + (row0 + c) * M + n);
         const bool more = k + 1 < k1;
 #pragma unroll
         for (int r = 0; r < E + 2; ++r) {
-            pu[r] = make_double2(0.0, 0.0);
+            pu[r] = P2T{};
             if ((r >= 1 && r <= E && ht) || more) pu[r] = __ldg(prow(kt, wrapm(j0 - 1 + r, g.ny)));
         }
         float2 zr[E];
+        longlong2 uq[E];                      // plane k+1's centre rows, converted once
 #pragma unroll
         for (int c = 0; c < E; ++c) {
             const longlong2 qc = Q[(c + 1) * M + n], qs = Q[c * M + n], qn = Q[(c + 2) * M + n];
             const long long qw = Q[(c + 1) * M + nw_].y, qe = Q[(c + 1) * M + ne_].x;
             const longlong2 ql = LO[c * M + n];
-            const long long u0 = fixq(pu[c + 1].x, sh), u1 = fixq(pu[c + 1].y, sh);  // 0 for a wall's ghost
-            long long s0 = qw + qc.y + qs.x + qn.x - nd * qc.x + ql.x + u0;
-            long long s1 = qc.x + qe + qs.y + qn.y - nd * qc.y + ql.y + u1;
+            uq[c] = fix2(pu[c + 1]);           // 0 for a wall's ghost
+            long long s0 = qw + qc.y + qs.x + qn.x - nd * qc.x + ql.x + uq[c].x;
+            long long s1 = qc.x + qe + qs.y + qn.y - nd * qc.y + ql.y + uq[c].y;
             LO[c * M + n] = qc;                // the lower neighbour of plane k+1
             bool ok0 = false, ok1 = false;
             long long F0 = 0, F1 = 0;
@@ -615,7 +638,8 @@ __device__ __forceinline__ void xres_zm_body(int bx, int by, int G, const double
             for (int c = 0; c < E; ++c) T[c * TP + n] = zr[c];
             if (more) {
 #pragma unroll
-                for (int r = 0; r < E + 2; ++r) Q[r * M + n] = make_longlong2(fixq(pu[r].x, sh), fixq(pu[r].y, sh));
+                for (int r = 0; r < E + 2; ++r)
+                    Q[r * M + n] = r >= 1 && r <= E ? uq[r - 1] : fix2(pu[r]);
             }
             __syncthreads();
             const bool active = n < E * N2;
@@ -632,21 +656,22 @@ __device__ __forceinline__ void xres_zm_body(int bx, int by, int G, const double
         }
         if (more) {
 #pragma unroll
-            for (int r = 0; r < E + 2; ++r) Q[r * M + n] = make_longlong2(fixq(pu[r].x, sh), fixq(pu[r].y, sh));
+            for (int r = 0; r < E + 2; ++r)
+                Q[r * M + n] = r >= 1 && r <= E ? uq[r - 1] : fix2(pu[r]);
             __syncthreads();
         }
     }
     block_sum_abc<false, true, false>(0.0, acc2, 0.f, part, pidx);
 }
 
-template <int E, int MODE, int N1, int N2>
-__global__ void __launch_bounds__(512, 1) k_xres_zm(const double* __restrict__ f, const double* __restrict__ p,
+template <int E, int MODE, int N1, int N2, typename PT>
+__global__ void __launch_bounds__(512, 1) k_xres_zm(const double* __restrict__ f, const PT* __restrict__ p,
                                                    float2* __restrict__ S, Geo g, FftLen L,
                                                    const float2* __restrict__ tw, const float2* __restrict__ twr,
                                                    int kz, const DevScalars* __restrict__ sc,
                                                    double* __restrict__ part) {
-    xres_zm_body<E, MODE, N1, N2>(blockIdx.x, blockIdx.y, 1, f, p, S, g, L, tw, twr, kz, sc, part,
-                                  blockIdx.y * gridDim.x + blockIdx.x);
+    xres_zm_body<E, MODE, N1, N2, PT>(blockIdx.x, blockIdx.y, 1, f, p, S, g, L, tw, twr, kz, sc, part,
+                                      blockIdx.y * gridDim.x + blockIdx.x);
 }
 
 // ------------------------------------------------------------- inverse along x (C2R)
@@ -1803,22 +1828,31 @@ void run_xfwd_e(flups_plan P, const double* f, const double* p, const Geo& g) {
         if (tiled) {                       // the z-marching form of the tiled defect
             // its transform tail: the register four-step rows where M is 64, 128 or 256; the
             // shared-memory Stockham passes otherwise
-            auto kern = k_xres_zm<E, MODE, 0, 0>;
-            size_t xp = 0;
+            auto launch = [&](auto kern, size_t xp, const auto* pp) {
+                const size_t smem = xres_smem(N) + (size_t)E * xp * sizeof(float2);
+                allow_smem(kern, smem);
+                const int kz = xres_kz(g.ny, g.nz);
+                flups_prof_begin(P, MODE == 3 ? FK_XRES_NORM32 : FK_XFWD_RES32);
+                kern<<<dim3(g.ny / E, (g.nz + kz - 1) / kz), N, smem, P->stream>>>(
+                    f, pp, (float2*)P->spec, g, packed(P->lx), (const float2*)P->twx, (const float2*)P->twxr, kz,
+                    P->sc, P->part);
+                flups_prof_end(P);
+                FLUPS_COUNT(P, 1);
+            };
+            auto pick = [&](const auto* pp) {
+                typedef typename std::remove_cv<typename std::remove_pointer<decltype(pp)>::type>::type PT;
+                if constexpr (MODE == 2) {
+                    if (N == 64) return launch(k_xres_zm<E, MODE, 8, 8, PT>, XRow<8, 8>::XP, pp);
+                    if (N == 128) return launch(k_xres_zm<E, MODE, 16, 8, PT>, XRow<16, 8>::XP, pp);
+                    if (N == 256) return launch(k_xres_zm<E, MODE, 16, 16, PT>, XRow<16, 16>::XP, pp);
+                }
+                launch(k_xres_zm<E, MODE, 0, 0, PT>, 0, pp);
+            };
+            // p from the binary32 copy of the first FP32 iterate where the inverse pass left one
             if constexpr (MODE == 2) {
-                if (N == 64) { kern = k_xres_zm<E, MODE, 8, 8>; xp = XRow<8, 8>::XP; }
-                else if (N == 128) { kern = k_xres_zm<E, MODE, 16, 8>; xp = XRow<16, 8>::XP; }
-                else if (N == 256) { kern = k_xres_zm<E, MODE, 16, 16>; xp = XRow<16, 16>::XP; }
+                if (P->p32_live) { pick((const float*)P->p32); return; }
             }
-            const size_t smem = xres_smem(N) + (size_t)E * xp * sizeof(float2);
-            allow_smem(kern, smem);
-            const int kz = xres_kz(g.ny, g.nz);
-            flups_prof_begin(P, MODE == 3 ? FK_XRES_NORM32 : FK_XFWD_RES32);
-            kern<<<dim3(g.ny / E, (g.nz + kz - 1) / kz), N, smem, P->stream>>>(
-                f, p, (float2*)P->spec, g, packed(P->lx), (const float2*)P->twx, (const float2*)P->twxr, kz, P->sc,
-                P->part);
-            flups_prof_end(P);
-            FLUPS_COUNT(P, 1);
+            pick(p);
             return;
         }
     }
@@ -2170,7 +2204,7 @@ __global__ void __launch_bounds__(FLUPS_BATCH_THREADS, KIND == 1 ? 2 : 3) k_b_xf
             xfwd_body<float, 8, 0, true>(tile, D.f, nullptr, D.spec, D.g, D.lx, D.twx, D.twxr, D.dd, D.lgx, nrows,
                                          D.sc, D.part);
     } else if (D.zm) {
-        xres_zm_body<8, 2, 0, 0>(tile % D.zbx, tile / D.zbx, D.zg, D.f, D.p, D.spec, D.g, D.lx, D.twx, D.twxr,
+        xres_zm_body<8, 2, 0, 0, double>(tile % D.zbx, tile / D.zbx, D.zg, D.f, D.p, D.spec, D.g, D.lx, D.twx, D.twxr,
                                  D.zkz, D.sc, D.part, tile);
     } else if (D.dmode == 2) {
         if (D.ex == 12)
@@ -2290,6 +2324,18 @@ __global__ void k_b_any(const BatchMember* __restrict__ mem, int n, cudaGraphCon
     if (threadIdx.x == 0) cudaGraphSetConditional(h, act ? 1u : 0u);
 }
 
+// p = the binary32 first iterate p32 (exact) where the solve ends at its first defect; with done
+// set, only once the stopping test has passed (*done != 0), so that a fixed kernel sequence can
+// hold the copy.  n2 pairs of points.
+__global__ void k_p_from32(const float2* __restrict__ p32, double2* __restrict__ p, size_t n2,
+                           const int* __restrict__ done) {
+    if (done && !*done) return;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n2; i += (size_t)gridDim.x * blockDim.x) {
+        const float2 v = p32[i];
+        p[i] = make_double2((double)v.x, (double)v.y);
+    }
+}
+
 }  // namespace
 
 // ------------------------------------------------------------------ launchers
@@ -2345,6 +2391,7 @@ cudaError_t launch_add_const(flups_plan P, double* a, double c) {
 
 cudaError_t launch_xfwd32_from_f(flups_plan P, const double* f) {
     const Geo g = plan_geo(P);
+    P->p32_live = 0;                       // a new solve: no binary32 iterate yet
     run_xfwd<float, 0, true>(P, f, nullptr, g);
     return cudaGetLastError();
 }
@@ -2367,7 +2414,19 @@ cudaError_t launch_xfwd32_residual(flups_plan P, const double* f, const double* 
     return cudaGetLastError();
 }
 
+cudaError_t launch_p_from32(flups_plan P, double* p, bool cond) {
+    if (!P->p32_live) return cudaSuccess;
+    k_p_from32<<<8 * 152, 256, 0, P->stream>>>((const float2*)P->p32, reinterpret_cast<double2*>(p), P->npts / 2,
+                                              cond ? &P->sc->done : nullptr);
+    FLUPS_COUNT(P, 1);
+    if (!cond) P->p32_live = 0;
+    return cudaGetLastError();
+}
+
+bool p32_path(int M, int ny) { return xrow4_rows(M) > 0 && e_for<float>(M) == 8 && xres_tiled(8, 8, M, ny); }
+
 cudaError_t launch_xres_norm32(flups_plan P, const double* f, const double* p) {
+    launch_p_from32(P, const_cast<double*>(p), false);   // the norm pass reads the binary64 p
     run_xfwd<float, 3, false>(P, f, p, plan_geo(P));
     return cudaGetLastError();
 }
@@ -2398,8 +2457,26 @@ cudaError_t launch_yz_solve32(flups_plan P) {
 cudaError_t launch_xinv32(flups_plan P, double* p, int mode) {
     const Geo g = plan_geo(P);
     cudaMemsetAsync(&P->sc->pexp, 0, sizeof(int), P->stream);
-    if (mode == 0) {                       // p = delta, and the volume-weighted mean of p
-        run_xinv<float, 0, true, false>(P, p, g);
+    if (mode == 4 && !P->p32) mode = 0;
+    if (mode == 4) {                       // as 0, the iterate kept in binary32 in P->p32
+        flups_prof_begin(P, FK_XINV32);
+        const bool ok = launch_xrow4_inv(P, p, g, 4);
+        flups_prof_end(P);
+        if (!ok) return cudaErrorInvalidValue;
+        FLUPS_COUNT(P, 1);
+        P->p32_live = 1;
+    }
+    if (mode == 1 && P->p32_live) {        // as 1, the old iterate read from P->p32
+        flups_prof_begin(P, FK_XINV_ACC32);
+        const bool ok = launch_xrow4_inv(P, p, g, 5);
+        flups_prof_end(P);
+        if (!ok) return cudaErrorInvalidValue;
+        FLUPS_COUNT(P, 1);
+        P->p32_live = 0;
+        return cudaGetLastError();
+    }
+    if (mode == 0 || mode == 4) {          // p = delta, and the volume-weighted mean of p
+        if (mode == 0) run_xinv<float, 0, true, false>(P, p, g);
         const int nblk = xfwd_blocks(P, 8, 0);
         flups_prof_begin(P, FK_FINALIZE);
         k_finalize<<<fin_grid(nblk), FIN_THREADS, 0, P->stream>>>(P->part, nblk, P->sc, 2,
@@ -2448,7 +2525,7 @@ cudaError_t launch_solve32_fixed(flups_plan P, const double* f, double* p, doubl
     launch_xfwd32_from_f(P, f);
     launch_finalize_f(P);
     launch_yz_solve32(P);
-    launch_xinv32(P, p, 0);
+    launch_xinv32(P, p, max_iter >= 2 ? 4 : 0);
     P->skip_ptr = &P->sc->done;
     const int nblk = xfwd_blocks(P, 8, 1);
     auto finalize_r = [&]() {
@@ -2470,6 +2547,7 @@ cudaError_t launch_solve32_fixed(flups_plan P, const double* f, double* p, doubl
         launch_xfwd32_residual(P, f, p);
         if (!norm_first || it == 1) finalize_r();
         if (last) break;
+        if (it == 1) launch_p_from32(P, p, true);    // p from the binary32 iterate if the test passed
         launch_yz_solve32(P);
         launch_xinv32(P, p, it == 1 ? 1 : 2);
     }

@@ -401,6 +401,8 @@ flups_status flups_plan_create_bc(flups_plan* out, int nx, int ny, int nz, doubl
     P->fin = (double*)A.get(3 * 256 * sizeof(double));
     P->tabs64 = (double*)A.get(6 * (size_t)nz * sizeof(double));
     if (ends && prec == FLUPS_FP32_REFINE) P->rbuf = (double*)A.get(P->npts * sizeof(double));
+    if (!ends && prec == FLUPS_FP32_REFINE && P->uniform_h && p32_path(P->M, ny))
+        P->p32 = (float*)A.get(P->npts * sizeof(float));
     bool ok = A.ok;
     if (ok) {
         std::vector<double> t(6 * (size_t)nz);
@@ -714,8 +716,13 @@ flups_status flups_solve(flups_plan P, const double* f, double* p, double rtol, 
     flups_status st = cuda_status(launch_xfwd32_from_f(P, f));
     if (st == FLUPS_OK) st = cuda_status(launch_finalize_f(P));
     if (st == FLUPS_OK) st = cuda_status(launch_yz_solve32(P));
-    if (st == FLUPS_OK) st = cuda_status(launch_xinv32(P, p, 0));
+    if (st == FLUPS_OK) st = cuda_status(launch_xinv32(P, p, max_iter >= 2 ? 4 : 0));
     if (st != FLUPS_OK) return st;
+    // a solve that ends at its first defect takes p from the binary32 iterate
+    auto finish = [&](flups_status s) {
+        const flups_status c = cuda_status(launch_p_from32(P, p, false));
+        return s != FLUPS_OK ? s : c;
+    };
     double rr = -1.0;
     int it = 1;
     const bool norm_first = xres_norm_first(P);
@@ -735,9 +742,9 @@ flups_status flups_solve(flups_plan P, const double* f, double* p, double rtol, 
             info->rel_res = rr;
             if (it - 1 < FLUPS_HIST) info->rel_res_hist[it - 1] = rr;
         }
-        if (!std::isfinite(rr)) return FLUPS_ENONFINITE;
-        if (rr <= rtol) return FLUPS_OK;
-        if (it >= max_iter) return FLUPS_ENOCONV;
+        if (!std::isfinite(rr)) return finish(FLUPS_ENONFINITE);
+        if (rr <= rtol) return finish(FLUPS_OK);
+        if (it >= max_iter) return finish(FLUPS_ENOCONV);
         // delta = L^-1 r in FP32, p += delta in FP64.
         if (alone) st = cuda_status(launch_xfwd32_residual(P, f, p));
         if (st == FLUPS_OK) st = cuda_status(launch_yz_solve32(P));

@@ -134,6 +134,8 @@ struct flups_plan_s {
                                  // ends the pre-twiddles exp(-i pi (4m+1)/(4n)) then the post-twiddles exp(-i pi k/n)
     void* twy2;                  // W_{ny/2} twiddles (mixed ends along y)
     double* rbuf;                // FP64 defect of the FP32+refine solve with ends (npts)
+    float* p32;                  // the first FP32 iterate in binary32 (npts), where p32_path holds
+    int p32_live;                // p32 holds the current iterate (p not yet written); host-side state
     void* tri;                   // walls: a_k/norm, b_k/norm, c_k/norm, compute type (3*nz)
     double sum_dzf;
     double dz0;                  // dzf[0] (the spacing of a periodic z)
@@ -198,7 +200,11 @@ cudaError_t launch_xres_norm32(flups_plan P, const double* f, const double* p); 
 bool xres_norm_first(flups_plan P);     // later stopping tests take the norm-only pass first
 cudaError_t launch_finalize_r(flups_plan P);
 cudaError_t launch_yz_solve32(flups_plan P);                                 // y fwd, z solve, y inv on S
-cudaError_t launch_xinv32(flups_plan P, double* p, int mode);  // 0: p = FFTx^-1(S) (+ mean); 1: p += . - mean; 2: p += .
+// 0: p = FFTx^-1(S) (+ mean); 1: p += . - mean; 2: p += .; 4: as 0, kept in binary32 in P->p32
+// where the plan has one (mode 1 then reads it from there)
+cudaError_t launch_xinv32(flups_plan P, double* p, int mode);
+// p = P->p32 while the binary32 iterate is live (cond: only once the stopping test passed)
+cudaError_t launch_p_from32(flups_plan P, double* p, bool cond);
 // FP32+refine solve with a fixed sequence of kernels and no host synchronisation (graph
 // capturable): after max_iter FP32 solves at most, the last defect norm is in P->sc.
 cudaError_t launch_solve32_fixed(flups_plan P, const double* f, double* p, double rtol, int max_iter);
@@ -269,8 +275,12 @@ void batch_member_fill(flups_plan P, const double* f, double* p, BatchMember* ou
 
 // Register four-step x-row kernels (xrow_kernels.cu) for M = nx / 2 in {64, ..., 1024}: rows
 // per CTA (0: not available); forward from f (stats: the partial sums of the first pass) and
-// inverse (mode 0: p = x with the mean's partial sums, 1: p += x - <p_0>, 2: p += x, 3: p = x).
+// inverse (mode 0: p = x with the mean's partial sums, 1: p += x - <p_0>, 2: p += x, 3: p = x;
+// 4: as 0 with x stored in binary32 to P->p32, 5: as 1 with the old iterate read from P->p32).
 int xrow4_rows(int M);
+// Whether the FP32+refine solve keeps its first iterate in binary32 (P->p32): one-spacing grids
+// whose first defect takes the z-marching kernel and whose inverse x takes the register rows.
+bool p32_path(int M, int ny);
 bool launch_xrow4_fwd(flups_plan P, const double* f, const Geo& g, bool stats);
 bool launch_xrow4_inv(flups_plan P, double* p, const Geo& g, int mode);
 int cols4_lgB(int N, int M, int kind);

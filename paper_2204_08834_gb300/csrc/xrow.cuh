@@ -176,9 +176,12 @@ __device__ __forceinline__ void xrow4_fwd_body(int bx, const double* __restrict_
 // partial sums of dzf * p (the values are binary32 numbers: summed per thread in pairs of
 // binary32 with exact two-sums, then in FP64); SUBM (with ACC = 1): x - <p_0> is added.  The
 // largest binary64 exponent written goes to sc->pexp (the scale of the next defect).
-template <int N1, int N2, int ACC, bool MEAN, bool SUBM>
+// F32: the iterate is held in binary32 in p32 (rows of nx values, as p): with ACC = 0 x is
+// stored there instead of in p (the values are binary32 numbers: nothing is lost), with ACC = 1
+// the old iterate is read from there and the sum goes to p.
+template <int N1, int N2, int ACC, bool MEAN, bool SUBM, bool F32>
 __device__ __forceinline__ void xrow4_inv_body(int bx, const float2* __restrict__ S, double* __restrict__ p,
-                                               const Geo& g, const float2* __restrict__ tw,
+                                               float* __restrict__ p32, const Geo& g, const float2* __restrict__ tw,
                                                const float2* __restrict__ twr, int nrows,
                                                DevScalars* __restrict__ sc, double* __restrict__ part) {
     if (g.skip && *g.skip) return;   // graph-capturable solve: this member already converged
@@ -228,12 +231,20 @@ __device__ __forceinline__ void xrow4_inv_body(int bx, const float2* __restrict_
         });
     });
     double2* dst = reinterpret_cast<double2*>(p + (size_t)(live ? row : 0) * g.nx) + t;
+    float2* d32 = reinterpret_cast<float2*>(p32 + (size_t)(live ? row : 0) * g.nx) + t;
+    auto old_p = [&](int n1) {
+        if (F32) {
+            const float2 o = live ? d32[N2 * n1] : make_float2(0.f, 0.f);
+            return make_double2(f2d_bits(o.x), f2d_bits(o.y));
+        }
+        return live ? dst[N2 * n1] : make_double2(0.0, 0.0);
+    };
     // p += x: the old p is loaded before the last exchange and DFT (where the registers allow)
     constexpr bool PRE = ACC && N1 <= 16;
     double2 pold[PRE ? N1 : 1];
     if (PRE) {
 #pragma unroll
-        for (int n1 = 0; n1 < N1; ++n1) pold[PRE ? n1 : 0] = live ? dst[N2 * n1] : make_double2(0.0, 0.0);
+        for (int n1 = 0; n1 < N1; ++n1) pold[PRE ? n1 : 0] = old_p(n1);
     }
     __syncthreads();
     float2 v[N1];
@@ -251,7 +262,7 @@ __device__ __forceinline__ void xrow4_inv_body(int bx, const float2* __restrict_
         double2 o;
         if (ACC) {
             if (PRE) o = pold[PRE ? n1 : 0];
-            else o = live ? dst[N2 * n1] : make_double2(0.0, 0.0);
+            else o = old_p(n1);
             o.x += f2d_bits(z.x);
             o.y += f2d_bits(z.y);
         } else {
@@ -261,7 +272,10 @@ __device__ __forceinline__ void xrow4_inv_body(int bx, const float2* __restrict_
                 two_sum_acc(sh, sl, z.y);
             }
         }
-        if (live) dst[N2 * n1] = o;
+        if (live) {
+            if (F32 && !ACC) d32[N2 * n1] = z;
+            else dst[N2 * n1] = o;
+        }
         const int ex_ = (int)((__double_as_longlong(o.x) >> 52) & 0x7FF);
         const int ey_ = (int)((__double_as_longlong(o.y) >> 52) & 0x7FF);
         emax = max(emax, max(ex_, ey_));

@@ -19,12 +19,13 @@ __global__ void __launch_bounds__(XROW_THREADS, N1 >= 32 ? 2 : 3) k_xrow4_fwd(co
     xrow4_fwd_body<N1, N2, STATS>(blockIdx.x, f, S, g, tw, twr, nrows, part);
 }
 
-template <int N1, int N2, int ACC, bool MEAN, bool SUBM>
+template <int N1, int N2, int ACC, bool MEAN, bool SUBM, bool F32>
 __global__ void __launch_bounds__(XROW_THREADS) k_xrow4_inv(const float2* __restrict__ S, double* __restrict__ p,
-                                                          Geo g, const float2* __restrict__ tw,
+                                                          float* __restrict__ p32, Geo g,
+                                                          const float2* __restrict__ tw,
                                                           const float2* __restrict__ twr, int nrows,
                                                           DevScalars* __restrict__ sc, double* __restrict__ part) {
-    xrow4_inv_body<N1, N2, ACC, MEAN, SUBM>(blockIdx.x, S, p, g, tw, twr, nrows, sc, part);
+    xrow4_inv_body<N1, N2, ACC, MEAN, SUBM, F32>(blockIdx.x, S, p, p32, g, tw, twr, nrows, sc, part);
 }
 
 template <typename K, typename... A>
@@ -54,17 +55,21 @@ bool inv_n(flups_plan P, double* p, const Geo& g, int mode) {
     const float2* S = (const float2*)P->spec;
     const float2* tw = (const float2*)P->twx;
     const float2* twr = (const float2*)P->twxr;
-    if (mode == 0)
-        return launch_rows(k_xrow4_inv<N1, N2, 0, true, false>, X::SMEM, nrows, X::B, P->stream, S, p, g, tw,
-                           twr, nrows, P->sc, P->part);
-    if (mode == 1)
-        return launch_rows(k_xrow4_inv<N1, N2, 1, false, true>, X::SMEM, nrows, X::B, P->stream, S, p, g, tw,
-                           twr, nrows, P->sc, P->part);
-    if (mode == 2)
-        return launch_rows(k_xrow4_inv<N1, N2, 1, false, false>, X::SMEM, nrows, X::B, P->stream, S, p, g, tw,
-                           twr, nrows, P->sc, P->part);
-    return launch_rows(k_xrow4_inv<N1, N2, 0, false, false>, X::SMEM, nrows, X::B, P->stream, S, p, g, tw,
-                       twr, nrows, P->sc, P->part);
+    float* p32 = P->p32;
+    switch (mode) {
+        case 0: return launch_rows(k_xrow4_inv<N1, N2, 0, true, false, false>, X::SMEM, nrows, X::B, P->stream, S,
+                                   p, p32, g, tw, twr, nrows, P->sc, P->part);
+        case 1: return launch_rows(k_xrow4_inv<N1, N2, 1, false, true, false>, X::SMEM, nrows, X::B, P->stream, S,
+                                   p, p32, g, tw, twr, nrows, P->sc, P->part);
+        case 2: return launch_rows(k_xrow4_inv<N1, N2, 1, false, false, false>, X::SMEM, nrows, X::B, P->stream, S,
+                                   p, p32, g, tw, twr, nrows, P->sc, P->part);
+        case 4: return p32 && launch_rows(k_xrow4_inv<N1, N2, 0, true, false, true>, X::SMEM, nrows, X::B,
+                                          P->stream, S, p, p32, g, tw, twr, nrows, P->sc, P->part);
+        case 5: return p32 && launch_rows(k_xrow4_inv<N1, N2, 1, false, true, true>, X::SMEM, nrows, X::B,
+                                          P->stream, S, p, p32, g, tw, twr, nrows, P->sc, P->part);
+        default: return launch_rows(k_xrow4_inv<N1, N2, 0, false, false, false>, X::SMEM, nrows, X::B, P->stream,
+                                    S, p, p32, g, tw, twr, nrows, P->sc, P->part);
+    }
 }
 
 }  // namespace
