@@ -27,13 +27,14 @@
 // instead (k_pnet_conv_tcz), and on grids of nx = 64 the output layer does (k_pnet_conv_tcz64:
 // two y rows of 64 points per MMA, from dx-rotated copies of each input row; the 16-channel
 // layers measured faster on mma.sync there).  In k_pnet_conv_tcz each MMA computes 128
-// consecutive x-points x 16 output channels
-// with K = 16 input channels of one tap (tcgen05.mma kind::f16, bf16 operands from shared
-// memory, FP32 accumulator in tensor memory); the 27 taps accumulate into the same tensor-memory
-// columns.  The A operand is read straight out of the halo tile with one descriptor per tap:
-// the tile stores each point's two 8-channel halves in two planes (point stride 16 bytes), so
-// an x-shifted window of 128 points is again a K-major operand (core matrices of 8 points x 16
-// bytes 128 bytes apart, the two K halves one plane apart).
+// consecutive x-points of one input row against the 16 output channels of up to three output
+// rows (N = 16, 32 or 48: the row's dy taps) with K = 16 input channels (tcgen05.mma kind::f16,
+// bf16 operands from shared memory, FP32 accumulators in tensor memory); the taps accumulate
+// into the same tensor-memory columns.  The A operand is read straight out of the halo tile with
+// one descriptor per input row and x shift: the tile stores each point's two 8-channel halves in
+// two planes (point stride 16 bytes), so an x-shifted window of 128 points is again a K-major
+// operand (core matrices of 8 points x 16 bytes 128 bytes apart, the two K halves one plane
+// apart).  Loads, MMAs and the epilogue run in separate warps, linked by mbarriers.
 
 #include "flups_impl.cuh"
 
@@ -265,8 +266,11 @@ __device__ __forceinline__ unsigned long long tc_desc(uint32_t addr, uint32_t lb
     return (unsigned long long)((addr >> 4) & 0x3FFF) | ((unsigned long long)((lbo >> 4) & 0x3FFF) << 16) |
            ((unsigned long long)((sbo >> 4) & 0x3FFF) << 32) | (1ull << 46);
 }
-// Instruction descriptor of kind::f16: FP32 accumulator, bf16 A and B, both K-major, N = 16, M = 128.
-constexpr uint32_t TC_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((16u >> 3) << 17) | ((128u >> 4) << 24);
+// Instruction descriptor of kind::f16: FP32 accumulator, bf16 A and B, both K-major, M = 128, N.
+__host__ __device__ constexpr uint32_t tc_idesc(uint32_t n) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((n >> 3) << 17) | ((128u >> 4) << 24);
+}
+constexpr uint32_t TC_IDESC = tc_idesc(16);
 
 __device__ __forceinline__ bool tc_mbar_try(uint32_t m, uint32_t par) {
     uint32_t ok;
@@ -286,6 +290,34 @@ __device__ __forceinline__ void tc_ld16(uint32_t taddr, float (&v)[16]) {
     for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
 }
 
+// tcgen05.ld of 16 columns without the wait; tc_wait16 completes it (the registers pass through
+// the wait, so that no use of them is scheduled before it)
+__device__ __forceinline__ void tc_ld16_async(uint32_t taddr, uint32_t (&r)[16]) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+                 : "r"(taddr));
+}
+__device__ __forceinline__ void tc_wait16(uint32_t (&r)[16]) {
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                   "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15])
+                 :: "memory");
+}
+__device__ __forceinline__ uint32_t tc_ld1_async(uint32_t taddr) {
+    uint32_t r;
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];" : "=r"(r) : "r"(taddr));
+    return r;
+}
+__device__ __forceinline__ void tc_wait4(uint32_t (&r)[4]) {
+    asm volatile("tcgen05.wait::ld.sync.aligned;" : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]) :: "memory");
+}
+
+__device__ __forceinline__ void tc_st16_zero(uint32_t taddr) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1};"
+                 ::"r"(taddr), "r"(0u) : "memory");
+}
+
 __device__ __forceinline__ float tc_ld1(uint32_t taddr) {
     uint32_t r;
     asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];" : "=r"(r) : "r"(taddr));
@@ -293,65 +325,53 @@ __device__ __forceinline__ float tc_ld1(uint32_t taddr) {
     return __uint_as_float(r);
 }
 
-// tcgen05 convolution marching in z.  A CTA owns a column of 4 (y) x 128 (x) points through ZC
-// planes.  Input planes (rows y0-1 .. y0+4, x0-1 .. x0+128, both 8-channel halves as planes of
-// 16-byte points) sit in a ring of four shared-memory buffers: output plane o reads input planes
-// o-1, o, o+1 (ring slots o, o+1, o+2 of the local input index), and one new input plane is
-// loaded per output plane.  Tensor memory holds two accumulator sets (4 rows x 16 columns each):
-// the MMAs of plane o run while the threads store plane o-1 and load input plane o+3.
+// tcgen05 convolution marching in z, warp-specialized.  A CTA owns a column of 4 (y) x 128 (x)
+// points through zc planes.  Input planes (rows y0-1 .. y0+4, x0-1 .. x0+128, both 8-channel
+// halves as planes of 16-byte points) pass through a ring of TW_R shared-memory slots: local input
+// i (global plane z0 - 1 + i) sits in slot i mod TW_R, and output plane o reads inputs o, o+1, o+2.
+//   warps 1-3 (producers): 16-byte asynchronous copies of input i once slot i mod TW_R is free
+//     (mbarrier empty, arrived by the MMAs of plane i - TW_R), then full[slot] when they landed
+//     (TW_LAG planes behind their issue: input i - TW_LAG is published after input i is issued,
+//     which needs the MMAs of plane i - TW_R, which need input i - TW_R + 2 <= i - TW_LAG - 1;
+//     the issuer can then run TW_R - 2 - TW_LAG planes ahead of the MMAs' completion);
+//   warp 0 lane 0 (MMA issuer): for plane o, waits for input o + 2 and for accumulator set o mod
+//     TW_S to be drained, issues the plane's 54 MMAs, commits to the set's full barrier and to
+//     the empty barrier of input o's slot;
+//   warps 4-7 (epilogue, one tensor-memory lane quadrant each, one x point per thread): read the
+//     set's 4 rows x 16 columns, store the layer output, clear the set, arrive on its empty barrier.
+// Each MMA takes one x-shifted input row (A, 128 points x 16 channels) against the weights of
+// every output row it feeds: input row ri (y0 - 1 + ri) enters output rows ri - 2 .. ri (those
+// inside the tile) through the taps dy = +1, 0, -1, whose accumulators are adjacent 16-column
+// blocks, so one MMA of N = 16, 32 or 48 covers them (B: the three dy blocks of one (dz, dx)
+// stacked as 48 rows): 54 MMAs per plane (6 rows x 3 dx x 3 dz) instead of 108 of N = 16, and
+// half the A-operand reads.  Every MMA accumulates; the epilogue clears a set after reading it.
+// Every wait is bounded: on a timeout the CTA stops its roles, lets its copies and MMAs finish,
+// and sets a.err.
 constexpr int TZ_TY = 4, TZ_HX = 130, TZ_HY = TZ_TY + 2;
 constexpr int TZ_PHALF = TZ_HY * TZ_HX * 16;          // one 8-channel half of an input plane (12480 B)
 constexpr int TZ_PLANE = 2 * TZ_PHALF;                // 24960 B
-constexpr int TZ_SMEM = 4 * TZ_PLANE + 27 * 512 + 32; // ring + weights + 2 mbarriers + TMEM slot
+constexpr int TZ_WQ = 1536;                           // weights of one (dz, dx): 2 K halves x 48 rows
 constexpr int TZ_THREADS = 256;
-constexpr int TZ_TMEM_COLS = 128;                     // 2 sets x 4 rows x 16 columns
-
-__device__ __forceinline__ void tz_load_plane(const uint4* __restrict__ src, unsigned char* dstp, int x0, int y0,
-                                              int gz, int nx, int ny) {
-    constexpr int NC = TZ_HY * TZ_HX * 2, BT = 8;
-    for (int c0 = threadIdx.x; c0 < NC; c0 += TZ_THREADS * BT) {
-        uint4 v[BT];
-        uint32_t dst[BT];
-#pragma unroll
-        for (int q = 0; q < BT; ++q) {
-            const int c = c0 + q * TZ_THREADS;
-            if (c < NC) {
-                const int pp = c >> 1, h = c & 1;
-                const int yy = pp / TZ_HX, xx = pp - yy * TZ_HX;
-                const int gx = wrapc(x0 + xx - 1, nx), gy = wrapc(y0 + yy - 1, ny);
-                const long long pt = ((long long)gz * ny + gy) * nx + gx;
-                v[q] = __ldg(src + pt * 2 + h);
-                dst[q] = (uint32_t)(h * TZ_PHALF + pp * 16);
-            }
-        }
-#pragma unroll
-        for (int q = 0; q < BT; ++q)
-            if (c0 + q * TZ_THREADS < NC) *reinterpret_cast<uint4*>(dstp + dst[q]) = v[q];
-    }
-}
-
-// The same plane by asynchronous 16-byte copies (cp.async: no registers, no wait at issue); the
-// caller completes them with cp.async.wait_all before the barrier that publishes the plane.
-__device__ __forceinline__ void tz_load_plane_async(const uint4* __restrict__ src, uint32_t dst_smem, int x0, int y0,
-                                                    int gz, int nx, int ny) {
-    constexpr int NC = TZ_HY * TZ_HX * 2;
-    for (int c = threadIdx.x; c < NC; c += TZ_THREADS) {
-        const int pp = c >> 1, h = c & 1;
-        const int yy = pp / TZ_HX, xx = pp - yy * TZ_HX;
-        const int gx = wrapc(x0 + xx - 1, nx), gy = wrapc(y0 + yy - 1, ny);
-        const long long pt = ((long long)gz * ny + gy) * nx + gx;
-        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;"
-                     ::"r"(dst_smem + (uint32_t)(h * TZ_PHALF + pp * 16)), "l"(src + pt * 2 + h) : "memory");
-    }
-}
+constexpr int TW_R = 8;                               // input ring slots
+constexpr int TW_S = 4;                               // accumulator sets (4 rows x 16 columns)
+constexpr int TW_PROD = 96;                           // producer threads (warps 1-3)
+constexpr int TW_LAG = 2;                             // planes between a copy's issue and its publication
+static_assert(TW_LAG >= 1 && TW_R - 2 - TW_LAG >= 1, "the producer must publish an input before it waits on "
+                                                     "the MMAs that read it");
+constexpr int TW_NBAR = 2 * TW_R + 2 * TW_S;          // full, empty, set full, set empty
+constexpr int TZ_SMEM = TW_R * TZ_PLANE + 27 * 512 + TW_NBAR * 8 + 16;
+constexpr int TZ_TMEM_COLS = TW_S * 64;
+constexpr int TW_CPT = (TZ_HY * TZ_HX * 2 + TW_PROD - 1) / TW_PROD;   // copies per producer thread
 
 template <int EPI>
-__global__ void __launch_bounds__(TZ_THREADS, 2) k_pnet_conv_tcz(ConvArgs a, int zc) {
+__global__ void __launch_bounds__(TZ_THREADS, 1) k_pnet_conv_tcz(ConvArgs a, int zc) {
     extern __shared__ __align__(128) unsigned char sm[];
-    unsigned char* ring = sm;
-    unsigned char* sw = sm + 4 * TZ_PLANE;
-    unsigned long long* mbar = reinterpret_cast<unsigned long long*>(sw + 27 * 512);   // [2]
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(sw + 27 * 512 + 16);
+    unsigned char* sw = sm + TW_R * TZ_PLANE;
+    unsigned long long* bar = reinterpret_cast<unsigned long long*>(sw + 27 * 512);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + TW_NBAR);
+    __shared__ int abort_;
+    __shared__ double ws[4];
+    constexpr int FULL = 0, EMPTY = TW_R, SETF = 2 * TW_R, SETE = 2 * TW_R + TW_S;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int tnx = a.nx / 128, tny = a.ny / TZ_TY;
     const int b = blockIdx.x;
@@ -362,141 +382,246 @@ __global__ void __launch_bounds__(TZ_THREADS, 2) k_pnet_conv_tcz(ConvArgs a, int
                      "r"(TZ_TMEM_COLS) : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
-    if (tid == 0) {   // one commit per output row: lane 0 of warps 0-3 issues one row's MMAs
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(mbar)), "r"(TZ_TY) : "memory");
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(mbar + 1)), "r"(TZ_TY) : "memory");
+    if (tid == 0) {
+        abort_ = 0;
+        for (int i = 0; i < TW_NBAR; ++i) {
+            const int cnt = i < TW_R ? TW_PROD : (i < SETE ? 1 : 4);
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar + i)), "r"(cnt) : "memory");
+        }
     }
     {
+        // 16-byte chunk (tap, K half kh, output channel oc) of [27][2][16][8] goes to block
+        // i = 1 - dy of the 48-row operand of (dz, dx): [9 (dz, dx)][2 kh][3 i][16 oc] chunks
         const uint4* wsrc = reinterpret_cast<const uint4*>(a.wtc);
-        for (int c = tid; c < 27 * 32; c += TZ_THREADS) reinterpret_cast<uint4*>(sw)[c] = __ldg(wsrc + c);
+        for (int c = tid; c < 27 * 32; c += TZ_THREADS) {
+            const int tap = c >> 5, kh = (c >> 4) & 1, oc = c & 15;
+            const int q = (tap / 9) * 3 + tap % 3, i = 2 - (tap / 3) % 3;
+            reinterpret_cast<uint4*>(sw)[q * (TZ_WQ / 16) + kh * 48 + i * 16 + oc] = __ldg(wsrc + c);
+        }
     }
-    for (int lp = 0; lp < 3; ++lp) tz_load_plane(src, ring + lp * TZ_PLANE, x0, y0, wrapc(z0 - 1 + lp, a.nz), a.nx, a.ny);
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tslot;
-    const uint32_t rb = smem_u32(ring), wb = smem_u32(sw);
-    const int wq = warp & 3;                  // tensor-memory lane quadrant of this warp
-    const int x = x0 + 32 * wq + lane;
-    float bias[16];
-    if (EPI == 0) {
+    const uint32_t rb = smem_u32(sm), wb = smem_u32(sw);
+    if (warp >= 4) {   // clear every accumulator set (each epilogue warp its lane quadrant)
+        const uint32_t tl = tmem + ((uint32_t)(32 * (warp - 4)) << 16);
 #pragma unroll
-        for (int n = 0; n < 16; ++n) bias[n] = __ldg(a.bias + n);
+        for (int c = 0; c < TZ_TMEM_COLS; c += 16) tc_st16_zero(tl + c);
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
     }
-    uint32_t ph0 = 0u, ph1 = 0u;
-    bool fail = false;
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+
+    // bounded wait on barrier i for the phase of parity par, by one thread; false on a timeout
+    // or once another role gave up
+    auto wait_one = [&](int i, uint32_t par) -> bool {
+        const uint32_t m = smem_u32(bar + i);
+        for (int it = 0; it < (1 << 22); ++it) {
+            if (tc_mbar_try(m, par)) return true;
+            if (*(volatile int*)&abort_) return false;
+        }
+        atomicExch(&abort_, 1);
+        return false;
+    };
+    // the same for a whole warp (lane 0 waits; the outcome is the warp's)
+    auto wait_warp = [&](int i, uint32_t par) -> bool {
+        int ok = 0;
+        if (lane == 0) ok = wait_one(i, par);
+        return __shfl_sync(0xffffffffu, ok, 0) != 0;
+    };
     double sq = 0.0;
-    // epilogue of output plane o (accumulator set o & 1); warps 0-3 take rows 0, 2, warps 4-7 rows 1, 3
-    auto epilogue = [&](int o) {
-        const uint32_t tl = tmem + ((uint32_t)(32 * wq) << 16) + (uint32_t)((o & 1) * 64);
-        const int z = z0 + o;
-        for (int r = warp >> 2; r < TZ_TY; r += 2) {
-            const long long pt = ((long long)z * a.ny + (y0 + r)) * a.nx + x;
-            if (EPI == 0 || EPI == 3) {
-                float v[16];
-                tc_ld16(tl + 16 * r, v);
-                if (EPI == 0) {
+    if (warp == 0) {
+        // ---------------------------------------------------------------- MMA issuer
+        if (lane == 0) {
+            const unsigned long long adesc0 = tc_desc(rb, TZ_PHALF, 128), bdesc0 = tc_desc(wb, TZ_WQ / 2, 128);
+            int issued = -1;
+            for (int o = 0; o < zc; ++o) {
+                bool ok = true;
+                for (int i = o == 0 ? 0 : o + 2; i <= o + 2 && ok; ++i) ok = wait_one(FULL + i % TW_R, (i / TW_R) & 1);
+                if (ok && o >= TW_S) ok = wait_one(SETE + o % TW_S, ((o / TW_S) - 1) & 1);
+                if (!ok) break;
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t dset = tmem + (uint32_t)((o % TW_S) * 64);
 #pragma unroll
-                    for (int n = 0; n < 16; ++n) v[n] = fmaxf(v[n] + bias[n], 0.0f);
-                } else {
-                    const uint4* mk4 = reinterpret_cast<const uint4*>(a.mask + pt * 16);
-                    const uint4 m0 = __ldg(mk4), m1 = __ldg(mk4 + 1);
-                    const uint32_t mw[8] = {m0.x, m0.y, m0.z, m0.w, m1.x, m1.y, m1.z, m1.w};
+                for (int dz = -1; dz <= 1; ++dz) {
+                    const unsigned long long abase =
+                        adesc0 + (unsigned long long)((((o + 1 + dz) % TW_R) * TZ_PLANE) / 16);
 #pragma unroll
-                    for (int q = 0; q < 8; ++q) {
-                        if (!(mw[q] & 0x7fffu)) v[2 * q] = 0.0f;
-                        if (!(mw[q] & 0x7fff0000u)) v[2 * q + 1] = 0.0f;
+                    for (int ri = 0; ri < TZ_TY + 2; ++ri) {
+                        const int b0 = ri - 2 > 0 ? ri - 2 : 0, b1 = ri < TZ_TY - 1 ? ri : TZ_TY - 1;
+                        const int i0 = b0 - (ri - 2);          // first dy block fed (block i: dy = 1 - i)
+                        const uint32_t idesc = tc_idesc((uint32_t)(16 * (b1 - b0 + 1)));
+#pragma unroll
+                        for (int dx = -1; dx <= 1; ++dx) {
+                            const int q = (dz + 1) * 3 + dx + 1;
+                            const unsigned long long ad = abase + (unsigned long long)(ri * TZ_HX + dx + 1);
+                            const unsigned long long bd =
+                                bdesc0 + (unsigned long long)((q * TZ_WQ + i0 * 256) / 16);
+                            asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, 1, 0;\n"
+                                         " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+                                         ::"r"(dset + 16 * b0), "l"(ad), "l"(bd), "r"(idesc) : "memory");
+                        }
                     }
                 }
-                uint32_t o2[8];
-#pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    __nv_bfloat162 h2 = __floats2bfloat162_rn(v[2 * q], v[2 * q + 1]);
-                    o2[q] = *reinterpret_cast<uint32_t*>(&h2);
-                }
-                uint4* dst = reinterpret_cast<uint4*>(a.out + pt * 16);
-                dst[0] = make_uint4(o2[0], o2[1], o2[2], o2[3]);
-                dst[1] = make_uint4(o2[4], o2[5], o2[6], o2[7]);
-            } else {
-                const double y = (double)(tc_ld1(tl + 16 * r) + __ldg(a.bias));
-                const double pn = a.pn[pt], pm = a.pnm1[pt];
-                if (EPI == 1) {
-                    a.phat[pt] = 2.0 * pn - pm + a.sc[0] * y;
-                } else {
-                    const double e = y - (a.pnext[pt] - (2.0 * pn - pm)) * a.sc[1];
-                    sq += e * e;
-                    a.out[pt * 16] = __double2bfloat16(a.gscale * e);
-                }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                             ::"r"(smem_u32(bar + SETF + o % TW_S)) : "memory");
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                             ::"r"(smem_u32(bar + EMPTY + o % TW_R)) : "memory");
+                issued = o;
             }
-        }
-    };
-    auto wait_set = [&](int o) -> bool {      // MMAs of output plane o are complete (bounded)
-        const uint32_t m = smem_u32(mbar + (o & 1));
-        const uint32_t par = (o & 1) ? ph1 : ph0;
-        bool done = false;
-        for (int i = 0; i < (1 << 22) && !done; ++i) done = tc_mbar_try(m, par);
-        if (o & 1) ph1 ^= 1u; else ph0 ^= 1u;
-        const bool ok = __syncthreads_and(done);
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        return ok;
-    };
-    // descriptors: one per ring slot (row 0, tap offset 0) and per weight tap; the tap and row
-    // offsets are added to the 16-byte address field (no carry: shared addresses < 2^18)
-    const unsigned long long adesc0 = tc_desc(rb, TZ_PHALF, 128), bdesc0 = tc_desc(wb, 256, 128);
-    const bool issuer = lane == 0 && warp < TZ_TY;     // issues the MMAs of output row r = warp
-    for (int o = 0; o < zc; ++o) {
-        if (issuer) {
-            const int r = warp;
-            const uint32_t dcol = tmem + (uint32_t)((o & 1) * 64 + 16 * r);
-#pragma unroll
-            for (int tap = 0; tap < 27; ++tap) {
-                const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
-                const int slot = (o + 1 + dz) & 3;
-                const unsigned long long ad =
-                    adesc0 + (unsigned long long)((slot * TZ_PLANE) / 16 + (r + dy + 1) * TZ_HX + dx + 1);
-                const unsigned long long bd = bdesc0 + (unsigned long long)(tap * 32);
-                asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                             " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
-                             ::"r"(dcol), "l"(ad), "l"(bd), "r"(TC_IDESC), "r"(tap) : "memory");
+            if (issued >= 0 && issued < zc - 1) {
+                // stopped early: the MMAs in flight finish before tensor memory is released
+                const uint32_t m = smem_u32(bar + SETF + issued % TW_S);
+                for (int it = 0; it < (1 << 22) && !tc_mbar_try(m, (issued / TW_S) & 1); ++it) {}
             }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                         ::"r"(smem_u32(mbar + (o & 1))) : "memory");
         }
         __syncwarp();
-        // plane o-1's MMAs done: its first input plane's slot takes input plane o+3, copied
-        // asynchronously while plane o-1 is stored
+    } else if (warp < 4) {
+        // ---------------------------------------------------------------- producers
+        const int pt = tid - 32;
+        uint32_t soff[TW_CPT], doff[TW_CPT];   // per copy: source (16-byte units, plane-relative), destination
+#pragma unroll
+        for (int k = 0; k < TW_CPT; ++k) {
+            const int c = pt + TW_PROD * k;
+            const int pp = c >> 1, h = c & 1;
+            const int yy = pp / TZ_HX, xx = pp - yy * TZ_HX;
+            const int gx = wrapc(x0 + xx - 1, a.nx), gy = wrapc(y0 + yy - 1, a.ny);
+            soff[k] = (uint32_t)(((size_t)gy * a.nx + gx) * 2 + h);
+            doff[k] = (uint32_t)(h * TZ_PHALF + pp * 16);
+        }
+        const size_t plane16 = (size_t)a.ny * a.nx * 2;
         bool ok = true;
-        if (o > 0) ok = wait_set(o - 1);
-        if (o + 3 <= zc + 1)
-            tz_load_plane_async(src, rb + (uint32_t)(((o + 3) & 3) * TZ_PLANE), x0, y0, wrapc(z0 + o + 2, a.nz), a.nx,
-                                a.ny);
-        if (o > 0) {
-            if (ok) epilogue(o - 1);
-            else fail = true;
+        int i = 0;
+        for (; i < zc + 2; ++i) {
+            if (i >= TW_R && !wait_warp(EMPTY + i % TW_R, ((i / TW_R) - 1) & 1)) { ok = false; break; }
+            const uint4* base = src + (size_t)wrapc(z0 - 1 + i, a.nz) * plane16;
+            const uint32_t dst = rb + (uint32_t)((i % TW_R) * TZ_PLANE);
+#pragma unroll
+            for (int k = 0; k < TW_CPT; ++k)
+                if (pt + TW_PROD * k < TZ_HY * TZ_HX * 2)
+                    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst + doff[k]), "l"(base + soff[k])
+                                 : "memory");
+            asm volatile("cp.async.commit_group;" ::: "memory");
+            if (i >= TW_LAG) {   // input i - TW_LAG has landed: publish it to the MMA issuer
+                asm volatile("cp.async.wait_group %0;" ::"n"(TW_LAG) : "memory");
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];"
+                             ::"r"(smem_u32(bar + FULL + (i - TW_LAG) % TW_R)) : "memory");
+            }
         }
         asm volatile("cp.async.wait_all;" ::: "memory");
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        __syncthreads();
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    }
-    if (wait_set(zc - 1)) epilogue(zc - 1);
-    else fail = true;
-    if (fail && tid == 0) atomicExch(a.err, 1);
-    if (EPI == 2) {
-        __shared__ double ws[TZ_THREADS / 32];
-        for (int s2 = 16; s2 > 0; s2 >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, s2);
-        if (lane == 0) ws[warp] = sq;
-        __syncthreads();
-        if (tid == 0) {
-            double t = 0.0;
-            for (int w = 0; w < TZ_THREADS / 32; ++w) t += ws[w];
-            a.red[blockIdx.x] = t;
+        if (ok) {   // the last TW_LAG inputs
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            for (int j = zc + 2 - TW_LAG; j <= zc + 1; ++j)
+                asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar + FULL + j % TW_R))
+                             : "memory");
+        }
+    } else {
+        // ---------------------------------------------------------------- epilogue
+        const int wq = warp - 4;
+        const int x = x0 + 32 * wq + lane;
+        float bias[16];
+        if (EPI == 0) {
+#pragma unroll
+            for (int n = 0; n < 16; ++n) bias[n] = __ldg(a.bias + n);
+        }
+        for (int o = 0; o < zc; ++o) {
+            if (!wait_warp(SETF + o % TW_S, (o / TW_S) & 1)) break;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t tl = tmem + ((uint32_t)(32 * wq) << 16) + (uint32_t)((o % TW_S) * 64);
+            const long long pt0 = ((long long)(z0 + o) * a.ny + y0) * a.nx + x, rs = a.nx;   // row r: pt0 + r rs
+            if (EPI == 0 || EPI == 3) {
+                uint4 mk[TZ_TY][2];
+                if (EPI == 3) {   // the rows' masks first, so that their loads overlap
+#pragma unroll
+                    for (int r = 0; r < TZ_TY; ++r) {
+                        const uint4* mk4 = reinterpret_cast<const uint4*>(a.mask + (pt0 + r * rs) * 16);
+                        mk[r][0] = __ldg(mk4);
+                        mk[r][1] = __ldg(mk4 + 1);
+                    }
+                }
+                uint32_t raw[TZ_TY][16];   // the set's 4 rows, loaded together, one wait
+#pragma unroll
+                for (int r = 0; r < TZ_TY; ++r) tc_ld16_async(tl + 16 * r, raw[r]);
+#pragma unroll
+                for (int r = 0; r < TZ_TY; ++r) tc_wait16(raw[r]);
+#pragma unroll
+                for (int r = 0; r < TZ_TY; ++r) tc_st16_zero(tl + 16 * r);    // the set starts its next plane cleared
+#pragma unroll
+                for (int r = 0; r < TZ_TY; ++r) {
+                    float v[16];
+#pragma unroll
+                    for (int n = 0; n < 16; ++n) v[n] = __uint_as_float(raw[r][n]);
+                    if (EPI == 0) {
+#pragma unroll
+                        for (int n = 0; n < 16; ++n) v[n] = fmaxf(v[n] + bias[n], 0.0f);
+                    } else {
+                        const uint32_t mw[8] = {mk[r][0].x, mk[r][0].y, mk[r][0].z, mk[r][0].w,
+                                                mk[r][1].x, mk[r][1].y, mk[r][1].z, mk[r][1].w};
+#pragma unroll
+                        for (int q = 0; q < 8; ++q) {
+                            if (!(mw[q] & 0x7fffu)) v[2 * q] = 0.0f;
+                            if (!(mw[q] & 0x7fff0000u)) v[2 * q + 1] = 0.0f;
+                        }
+                    }
+                    uint32_t o2[8];
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        __nv_bfloat162 h2 = __floats2bfloat162_rn(v[2 * q], v[2 * q + 1]);
+                        o2[q] = *reinterpret_cast<uint32_t*>(&h2);
+                    }
+                    uint4* dst = reinterpret_cast<uint4*>(a.out + (pt0 + r * rs) * 16);
+                    dst[0] = make_uint4(o2[0], o2[1], o2[2], o2[3]);
+                    dst[1] = make_uint4(o2[4], o2[5], o2[6], o2[7]);
+                }
+            } else {
+                double pn[TZ_TY], pm[TZ_TY], px[TZ_TY];   // the rows' pressures first (overlapped loads)
+#pragma unroll
+                for (int r = 0; r < TZ_TY; ++r) {
+                    pn[r] = a.pn[pt0 + r * rs];
+                    pm[r] = a.pnm1[pt0 + r * rs];
+                    px[r] = EPI == 2 ? a.pnext[pt0 + r * rs] : 0.0;
+                }
+                const float b0 = __ldg(a.bias);
+                uint32_t raw[TZ_TY];
+#pragma unroll
+                for (int r = 0; r < TZ_TY; ++r) raw[r] = tc_ld1_async(tl + 16 * r);
+                tc_wait4(raw);
+#pragma unroll
+                for (int r = 0; r < TZ_TY; ++r) tc_st16_zero(tl + 16 * r);    // the set starts its next plane cleared
+#pragma unroll
+                for (int r = 0; r < TZ_TY; ++r) {
+                    const double y = (double)(__uint_as_float(raw[r]) + b0);
+                    if (EPI == 1) {
+                        a.phat[pt0 + r * rs] = 2.0 * pn[r] - pm[r] + a.sc[0] * y;
+                    } else {
+                        const double e = y - (px[r] - (2.0 * pn[r] - pm[r])) * a.sc[1];
+                        sq += e * e;
+                        a.out[(pt0 + r * rs) * 16] = __double2bfloat16(a.gscale * e);
+                    }
+                }
+            }
+            asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar + SETE + o % TW_S))
+                                        : "memory");
+        }
+        if (EPI == 2) {
+            for (int s2 = 16; s2 > 0; s2 >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, s2);
+            if (lane == 0) ws[wq] = sq;
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (tid == 0) {
+        if (abort_) atomicExch(a.err, 1);
+        if (EPI == 2) a.red[blockIdx.x] = ws[0] + ws[1] + ws[2] + ws[3];
+    }
     if (warp == 0)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TZ_TMEM_COLS) : "memory");
 }
@@ -977,7 +1102,7 @@ template <int NT, int EPI>
 void conv(flups_pnet N, const ConvArgs& a) {
     pk_begin(N, EPI == 0 ? PK_CONV_HIDDEN : (EPI == 3 ? PK_CONV_BWD : PK_CONV_OUT));
     if (N->use_tc == 2) {
-        const int zc = N->nz % 8 == 0 ? 8 : 4;
+        const int zc = N->nz % 16 == 0 ? 16 : (N->nz % 8 == 0 ? 8 : 4);
         const int nb = (N->nx / 128) * (N->ny / TZ_TY) * (N->nz / zc);
         k_pnet_conv_tcz<EPI><<<nb, TZ_THREADS, TZ_SMEM, N->stream>>>(a, zc);
         if (EPI == 2) N->last_red = nb;
