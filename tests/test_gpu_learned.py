@@ -133,8 +133,10 @@ def check_close(y_gpu, y_ref, what):
 
 
 # nx = 32: mma.sync kernels; nx = 64: mma.sync for the 16-channel layers, the row-pair tcgen05
-# kernel for the output layer; nx = 128, 256: tcgen05 kernels (tensor-memory accumulators)
-@pytest.mark.parametrize("shape", [(8, 16, 32), (12, 8, 64), (4, 8, 128), (8, 8, 256)])
+# kernel for the output layer; nx = 128, 256: tcgen05 kernels (tensor-memory accumulators; z
+# chunks of 4, 8 and 16 planes; at nz = 32 two chunks of 16 whose 18 input planes wrap the
+# 8-slot ring twice)
+@pytest.mark.parametrize("shape", [(8, 16, 32), (12, 8, 64), (4, 8, 128), (8, 8, 256), (32, 8, 128)])
 def test_forward_matches_oracle(shape):
     rho, pn, pnm1, _ = net_inputs(shape, 5)
     params = rand_params(50)
@@ -161,7 +163,7 @@ def test_zero_pressure_uses_unit_scale():
     check_close(ph.cpu().numpy(), y_o[0], "y")
 
 
-@pytest.mark.parametrize("shape", [(8, 16, 32), (12, 8, 64), (4, 8, 128)])
+@pytest.mark.parametrize("shape", [(8, 16, 32), (12, 8, 64), (4, 8, 128), (32, 8, 128)])
 def test_gradients_match_oracle(shape):
     rho, pn, pnm1, pnext = net_inputs(shape, 7)
     params = rand_params(52)
