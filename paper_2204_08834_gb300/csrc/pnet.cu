@@ -347,6 +347,9 @@ __device__ __forceinline__ float tc_ld1(uint32_t taddr) {
 // half the A-operand reads.  Every MMA accumulates; the epilogue clears a set after reading it.
 // Every wait is bounded: on a timeout the CTA stops its roles, lets its copies and MMAs finish,
 // and sets a.err.
+// PACKX (the first layer, 3 input channels): the input holds at channel 3 (dx + 1) + c the
+// feature c of the point x + dx (k_pnet_features_x), so the three x taps are one K = 16 operand (9
+// channels used) and a plane takes 18 MMAs (6 rows x 3 dz), against the x-halo-free window.
 constexpr int TZ_TY = 4, TZ_HX = 130, TZ_HY = TZ_TY + 2;
 constexpr int TZ_PHALF = TZ_HY * TZ_HX * 16;          // one 8-channel half of an input plane (12480 B)
 constexpr int TZ_PLANE = 2 * TZ_PHALF;                // 24960 B
@@ -355,7 +358,7 @@ constexpr int TZ_THREADS = 256;
 constexpr int TW_R = 8;                               // input ring slots
 constexpr int TW_S = 4;                               // accumulator sets (4 rows x 16 columns)
 constexpr int TW_PROD = 96;                           // producer threads (warps 1-3)
-constexpr int TW_LAG = 2;                             // planes between a copy's issue and its publication
+constexpr int TW_LAG = 3;                             // planes between a copy's issue and its publication
 static_assert(TW_LAG >= 1 && TW_R - 2 - TW_LAG >= 1, "the producer must publish an input before it waits on "
                                                      "the MMAs that read it");
 constexpr int TW_NBAR = 2 * TW_R + 2 * TW_S;          // full, empty, set full, set empty
@@ -363,7 +366,7 @@ constexpr int TZ_SMEM = TW_R * TZ_PLANE + 27 * 512 + TW_NBAR * 8 + 16;
 constexpr int TZ_TMEM_COLS = TW_S * 64;
 constexpr int TW_CPT = (TZ_HY * TZ_HX * 2 + TW_PROD - 1) / TW_PROD;   // copies per producer thread
 
-template <int EPI>
+template <int EPI, bool PACKX>
 __global__ void __launch_bounds__(TZ_THREADS, 1) k_pnet_conv_tcz(ConvArgs a, int zc) {
     extern __shared__ __align__(128) unsigned char sm[];
     unsigned char* sw = sm + TW_R * TZ_PLANE;
@@ -389,7 +392,7 @@ __global__ void __launch_bounds__(TZ_THREADS, 1) k_pnet_conv_tcz(ConvArgs a, int
             asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar + i)), "r"(cnt) : "memory");
         }
     }
-    {
+    if (!PACKX) {
         // 16-byte chunk (tap, K half kh, output channel oc) of [27][2][16][8] goes to block
         // i = 1 - dy of the 48-row operand of (dz, dx): [9 (dz, dx)][2 kh][3 i][16 oc] chunks
         const uint4* wsrc = reinterpret_cast<const uint4*>(a.wtc);
@@ -397,6 +400,29 @@ __global__ void __launch_bounds__(TZ_THREADS, 1) k_pnet_conv_tcz(ConvArgs a, int
             const int tap = c >> 5, kh = (c >> 4) & 1, oc = c & 15;
             const int q = (tap / 9) * 3 + tap % 3, i = 2 - (tap / 3) % 3;
             reinterpret_cast<uint4*>(sw)[q * (TZ_WQ / 16) + kh * 48 + i * 16 + oc] = __ldg(wsrc + c);
+        }
+    } else {
+        // operand of dz (block i = 1 - dy, K half kh, output channel oc): element k = 8 kh + j is
+        // W(dz, dy, dx = k / 3 - 1; oc, c = k % 3) for k < 9, else 0; [3 dz][2 kh][3 i][16 oc] chunks
+        const unsigned short* wsrc = reinterpret_cast<const unsigned short*>(a.wtc);
+        for (int c = tid; c < 3 * 96; c += TZ_THREADS) {
+            const int q = c / 96, kh = (c / 48) & 1, i = (c / 16) % 3, oc = c & 15;
+            const int dy = 1 - i;
+            uint32_t h[4];
+#pragma unroll
+            for (int jj = 0; jj < 4; ++jj) {
+                uint32_t v2 = 0;
+#pragma unroll
+                for (int hh = 0; hh < 2; ++hh) {
+                    const int k = 8 * kh + 2 * jj + hh;
+                    if (k < 9) {
+                        const int tap = q * 9 + (dy + 1) * 3 + k / 3;
+                        v2 |= (uint32_t)__ldg(wsrc + tap * 256 + oc * 8 + k % 3) << (16 * hh);
+                    }
+                }
+                h[jj] = v2;
+            }
+            reinterpret_cast<uint4*>(sw)[q * (TZ_WQ / 16) + kh * 48 + i * 16 + oc] = make_uint4(h[0], h[1], h[2], h[3]);
         }
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -445,19 +471,22 @@ __global__ void __launch_bounds__(TZ_THREADS, 1) k_pnet_conv_tcz(ConvArgs a, int
                 if (!ok) break;
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 const uint32_t dset = tmem + (uint32_t)((o % TW_S) * 64);
+                unsigned long long abase[3];          // the plane's three input slots
 #pragma unroll
-                for (int dz = -1; dz <= 1; ++dz) {
-                    const unsigned long long abase =
-                        adesc0 + (unsigned long long)((((o + 1 + dz) % TW_R) * TZ_PLANE) / 16);
+                for (int dz = -1; dz <= 1; ++dz)
+                    abase[dz + 1] = adesc0 + (unsigned long long)((((o + 1 + dz) % TW_R) * TZ_PLANE) / 16);
+                // input rows outermost: the 9 MMAs of one row (dz, dx) share one accumulator range
 #pragma unroll
-                    for (int ri = 0; ri < TZ_TY + 2; ++ri) {
-                        const int b0 = ri - 2 > 0 ? ri - 2 : 0, b1 = ri < TZ_TY - 1 ? ri : TZ_TY - 1;
-                        const int i0 = b0 - (ri - 2);          // first dy block fed (block i: dy = 1 - i)
-                        const uint32_t idesc = tc_idesc((uint32_t)(16 * (b1 - b0 + 1)));
+                for (int ri = 0; ri < TZ_TY + 2; ++ri) {
+                    const int b0 = ri - 2 > 0 ? ri - 2 : 0, b1 = ri < TZ_TY - 1 ? ri : TZ_TY - 1;
+                    const int i0 = b0 - (ri - 2);          // first dy block fed (block i: dy = 1 - i)
+                    const uint32_t idesc = tc_idesc((uint32_t)(16 * (b1 - b0 + 1)));
 #pragma unroll
-                        for (int dx = -1; dx <= 1; ++dx) {
-                            const int q = (dz + 1) * 3 + dx + 1;
-                            const unsigned long long ad = abase + (unsigned long long)(ri * TZ_HX + dx + 1);
+                    for (int dz = -1; dz <= 1; ++dz) {
+#pragma unroll
+                        for (int dx = PACKX ? 0 : -1; dx <= (PACKX ? 0 : 1); ++dx) {
+                            const int q = PACKX ? dz + 1 : (dz + 1) * 3 + dx + 1;
+                            const unsigned long long ad = abase[dz + 1] + (unsigned long long)(ri * TZ_HX + dx + 1);
                             const unsigned long long bd =
                                 bdesc0 + (unsigned long long)((q * TZ_WQ + i0 * 256) / 16);
                             asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, 1, 0;\n"
@@ -985,21 +1014,49 @@ __global__ void k_pnet_fin(const double* __restrict__ red, int nblk, double* __r
     }
 }
 
+// Features of point c as bfloat16 bits (the rounding of the 3-channel input layout).
+__device__ __forceinline__ void pn_feat_bits(const double* __restrict__ rho, double rho0, const double* __restrict__ pn,
+                                             const double* __restrict__ pnm1, double is, long long c, uint32_t (&b)[3]) {
+    const __nv_bfloat16 h0 = __double2bfloat16(1.0 - rho0 / rho[c]);
+    const __nv_bfloat16 h1 = __double2bfloat16(pn[c] * is);
+    const __nv_bfloat16 h2 = __double2bfloat16(pnm1[c] * is);
+    b[0] = *reinterpret_cast<const unsigned short*>(&h0);
+    b[1] = *reinterpret_cast<const unsigned short*>(&h1);
+    b[2] = *reinterpret_cast<const unsigned short*>(&h2);
+}
+
+// feat: the 3 features of each point in channels 0-2 of its 16 (the others stay zero).
 __global__ void k_pnet_features(const double* __restrict__ rho, double rho0, const double* __restrict__ pn,
-                                 const double* __restrict__ pnm1, const double* __restrict__ sc, long long n,
-                                 __nv_bfloat16* __restrict__ feat) {
+                                const double* __restrict__ pnm1, const double* __restrict__ sc, long long n,
+                                __nv_bfloat16* __restrict__ feat) {
     const double is = sc[1];
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
-        __nv_bfloat162 lo, hi;
-        lo.x = __double2bfloat16(1.0 - rho0 / rho[c]);
-        lo.y = __double2bfloat16(pn[c] * is);
-        hi.x = __double2bfloat16(pnm1[c] * is);
-        hi.y = __float2bfloat16_rn(0.0f);
-        uint2 u;
-        u.x = *reinterpret_cast<unsigned int*>(&lo);
-        u.y = *reinterpret_cast<unsigned int*>(&hi);
-        *reinterpret_cast<uint2*>(feat + c * 16) = u;
+        uint32_t m[3];
+        pn_feat_bits(rho, rho0, pn, pnm1, is, c, m);
+        *reinterpret_cast<uint2*>(feat + c * 16) = make_uint2(m[0] | (m[1] << 16), m[2]);
     }
+}
+
+// The same with the tcgen05 first layer's input: one CTA of nx threads per x row (nx <= 1024),
+// each point's features computed once and shared through shared memory; featx holds at channel
+// 3 (dx + 1) + c the feature c of the point x + dx (periodic in x), channels 9-15 zero.
+__global__ void k_pnet_features_x(const double* __restrict__ rho, double rho0, const double* __restrict__ pn,
+                                  const double* __restrict__ pnm1, const double* __restrict__ sc,
+                                  __nv_bfloat16* __restrict__ feat, __nv_bfloat16* __restrict__ featx) {
+    __shared__ uint2 row[1024];
+    const int nx = blockDim.x, ix = threadIdx.x;
+    const long long c = (long long)blockIdx.x * nx + ix;
+    uint32_t m[3];
+    pn_feat_bits(rho, rho0, pn, pnm1, sc[1], c, m);
+    const uint2 u = make_uint2(m[0] | (m[1] << 16), m[2]);
+    *reinterpret_cast<uint2*>(feat + c * 16) = u;
+    row[ix] = u;
+    __syncthreads();
+    const uint2 w = row[ix == 0 ? nx - 1 : ix - 1], e = row[ix == nx - 1 ? 0 : ix + 1];
+    // bf16 lanes: u.x = (f0, f1), u.y = (f2, 0), likewise w and e
+    uint4* dst = reinterpret_cast<uint4*>(featx + c * 16);
+    dst[0] = make_uint4(w.x, (w.y & 0xffffu) | (u.x << 16), (u.x >> 16) | (u.y << 16), e.x);
+    dst[1] = make_uint4(e.y & 0xffffu, 0u, 0u, 0u);
 }
 
 }  // namespace
@@ -1012,7 +1069,7 @@ struct flups_pnet_s {
     __nv_bfloat16* wf; __nv_bfloat16* wb;         // packed bfloat16 weights (4 layers each)
     __nv_bfloat16* wtf; __nv_bfloat16* wtb;       // the same in the tcgen05 layout
     int* err;                                     // device error word (bounded waits)
-    int use_tc;                                   // tcgen05 convolutions: 2 nx % 128 == 0 (all), 1 nx == 64 (output layer)
+    int use_tc;                                   // tcgen05 convolutions: 2 nx % 128 == 0, nx <= 1024 (all), 1 nx == 64 (output layer)
     int last_red;                                 // CTAs of the last loss partials
     __nv_bfloat16* feat; __nv_bfloat16* act[3]; __nv_bfloat16* dy; __nv_bfloat16* g[2];
     float* part;                                  // weight-gradient partials [4][ncta][PN_PART]
@@ -1078,10 +1135,11 @@ cudaError_t set_smem_attrs() {
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_pnet_conv<1, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, CONV_SMEM);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_pnet_conv<1, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, CONV_SMEM);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_pnet_wgrad, cudaFuncAttributeMaxDynamicSharedMemorySize, WGRAD_SMEM);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_pnet_conv_tcz<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, TZ_SMEM);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_pnet_conv_tcz<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, TZ_SMEM);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_pnet_conv_tcz<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, TZ_SMEM);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_pnet_conv_tcz<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, TZ_SMEM);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_pnet_conv_tcz<0, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, TZ_SMEM);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_pnet_conv_tcz<0, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, TZ_SMEM);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_pnet_conv_tcz<1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, TZ_SMEM);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_pnet_conv_tcz<2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, TZ_SMEM);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_pnet_conv_tcz<3, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, TZ_SMEM);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_pnet_conv_tcz64<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, T64_SMEM);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_pnet_conv_tcz64<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, T64_SMEM);
     if (e == cudaSuccess) done = dev;
@@ -1098,13 +1156,21 @@ ConvArgs conv_args(flups_pnet N) {
     return a;
 }
 
+// first: the layer reads the 3-channel features; on the tcgen05 path it reads them with their x
+// neighbours packed (N->g[0], written by k_pnet_features) and takes the three x taps in K
 template <int NT, int EPI>
-void conv(flups_pnet N, const ConvArgs& a) {
+void conv(flups_pnet N, const ConvArgs& a, bool first = false) {
     pk_begin(N, EPI == 0 ? PK_CONV_HIDDEN : (EPI == 3 ? PK_CONV_BWD : PK_CONV_OUT));
     if (N->use_tc == 2) {
         const int zc = N->nz % 16 == 0 ? 16 : (N->nz % 8 == 0 ? 8 : 4);
         const int nb = (N->nx / 128) * (N->ny / TZ_TY) * (N->nz / zc);
-        k_pnet_conv_tcz<EPI><<<nb, TZ_THREADS, TZ_SMEM, N->stream>>>(a, zc);
+        if (EPI == 0 && first) {
+            ConvArgs b = a;
+            b.in = N->g[0];
+            k_pnet_conv_tcz<0, true><<<nb, TZ_THREADS, TZ_SMEM, N->stream>>>(b, zc);
+        } else {
+            k_pnet_conv_tcz<EPI, false><<<nb, TZ_THREADS, TZ_SMEM, N->stream>>>(a, zc);
+        }
         if (EPI == 2) N->last_red = nb;
     } else if (N->use_tc == 1 && (EPI == 1 || EPI == 2)) {
         // nx = 64: the row-pair tcgen05 kernel for the 16 -> 1 output layer (measured 20 % faster
@@ -1142,7 +1208,11 @@ void forward_hidden(flups_pnet N, const double* rho, double rho0, const double* 
     pk_begin(N, PK_FEATURES);
     k_pnet_sumsq<<<N->nred, THREADS, 0, s>>>(pn, N->n, N->red);
     k_pnet_fin<<<1, 1024, 0, s>>>(N->red, N->nred, N->sc, 0, 1.0 / (double)N->n);
-    k_pnet_features<<<N->nred, THREADS, 0, s>>>(rho, rho0, pn, pnm1, N->sc, N->n, N->feat);
+    // the tcgen05 first layer reads its x-tap-packed input from N->g[0] (free in the forward pass)
+    if (N->use_tc == 2)
+        k_pnet_features_x<<<(unsigned)(N->n / N->nx), N->nx, 0, s>>>(rho, rho0, pn, pnm1, N->sc, N->feat, N->g[0]);
+    else
+        k_pnet_features<<<N->nred, THREADS, 0, s>>>(rho, rho0, pn, pnm1, N->sc, N->n, N->feat);
     pk_end(N);
     N->launches += 3;
     const __nv_bfloat16* in = N->feat;
@@ -1153,7 +1223,7 @@ void forward_hidden(flups_pnet N, const double* rho, double rho0, const double* 
         a.wtc = N->wtf + (size_t)l * PN_TCW;
         a.bias = N->w + lay_b(l);
         a.out = N->act[l];
-        conv<2, 0>(N, a);
+        conv<2, 0>(N, a, l == 0);
         in = N->act[l];
     }
 }
@@ -1232,7 +1302,7 @@ flups_status flups_pnet_create(flups_pnet* out, int nx, int ny, int nz, const fl
     N->wtf = (__nv_bfloat16*)(b + off_wtf);
     N->wtb = (__nv_bfloat16*)(b + off_wtb);
     N->err = (int*)(b + off_err);
-    N->use_tc = nx % 128 == 0 ? 2 : (nx == 64 ? 1 : 0);
+    N->use_tc = nx % 128 == 0 && nx <= 1024 ? 2 : (nx == 64 ? 1 : 0);
     N->last_red = N->ncta;
     __nv_bfloat16* f = (__nv_bfloat16*)(b + off_feat);
     const size_t fe = (size_t)N->n * 16;
