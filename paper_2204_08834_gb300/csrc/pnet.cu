@@ -313,11 +313,6 @@ __device__ __forceinline__ void tc_wait4(uint32_t (&r)[4]) {
     asm volatile("tcgen05.wait::ld.sync.aligned;" : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]) :: "memory");
 }
 
-__device__ __forceinline__ void tc_st16_zero(uint32_t taddr) {
-    asm volatile("tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1};"
-                 ::"r"(taddr), "r"(0u) : "memory");
-}
-
 __device__ __forceinline__ float tc_ld1(uint32_t taddr) {
     uint32_t r;
     asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];" : "=r"(r) : "r"(taddr));
@@ -344,7 +339,8 @@ __device__ __forceinline__ float tc_ld1(uint32_t taddr) {
 // inside the tile) through the taps dy = +1, 0, -1, whose accumulators are adjacent 16-column
 // blocks, so one MMA of N = 16, 32 or 48 covers them (B: the three dy blocks of one (dz, dx)
 // stacked as 48 rows): 54 MMAs per plane (6 rows x 3 dx x 3 dz) instead of 108 of N = 16, and
-// half the A-operand reads.  Every MMA accumulates; the epilogue clears a set after reading it.
+// half the A-operand reads.  A plane's first MMA clears its accumulator set (a zero A tile, not
+// accumulated); every other MMA accumulates.
 // Every wait is bounded: on a timeout the CTA stops its roles, lets its copies and MMAs finish,
 // and sets a.err.
 // PACKX (the first layer, 3 input channels): the input holds at channel 3 (dx + 1) + c the
@@ -362,7 +358,8 @@ constexpr int TW_LAG = 3;                             // planes between a copy's
 static_assert(TW_LAG >= 1 && TW_R - 2 - TW_LAG >= 1, "the producer must publish an input before it waits on "
                                                      "the MMAs that read it");
 constexpr int TW_NBAR = 2 * TW_R + 2 * TW_S;          // full, empty, set full, set empty
-constexpr int TZ_SMEM = TW_R * TZ_PLANE + 27 * 512 + TW_NBAR * 8 + 16;
+constexpr int TW_ZERO = 4096;                         // a zero A operand (128 points x 16 channels)
+constexpr int TZ_SMEM = TW_R * TZ_PLANE + 27 * 512 + TW_ZERO + TW_NBAR * 8 + 16;
 constexpr int TZ_TMEM_COLS = TW_S * 64;
 constexpr int TW_CPT = (TZ_HY * TZ_HX * 2 + TW_PROD - 1) / TW_PROD;   // copies per producer thread
 
@@ -370,7 +367,8 @@ template <int EPI, bool PACKX>
 __global__ void __launch_bounds__(TZ_THREADS, 1) k_pnet_conv_tcz(ConvArgs a, int zc) {
     extern __shared__ __align__(128) unsigned char sm[];
     unsigned char* sw = sm + TW_R * TZ_PLANE;
-    unsigned long long* bar = reinterpret_cast<unsigned long long*>(sw + 27 * 512);
+    unsigned char* zt = sw + 27 * 512;                         // zero tile
+    unsigned long long* bar = reinterpret_cast<unsigned long long*>(zt + TW_ZERO);
     uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + TW_NBAR);
     __shared__ int abort_;
     __shared__ double ws[4];
@@ -425,21 +423,13 @@ __global__ void __launch_bounds__(TZ_THREADS, 1) k_pnet_conv_tcz(ConvArgs a, int
             reinterpret_cast<uint4*>(sw)[q * (TZ_WQ / 16) + kh * 48 + i * 16 + oc] = make_uint4(h[0], h[1], h[2], h[3]);
         }
     }
+    for (int c = tid; c < TW_ZERO / 16; c += TZ_THREADS) reinterpret_cast<uint4*>(zt)[c] = make_uint4(0u, 0u, 0u, 0u);
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tslot;
     const uint32_t rb = smem_u32(sm), wb = smem_u32(sw);
-    if (warp >= 4) {   // clear every accumulator set (each epilogue warp its lane quadrant)
-        const uint32_t tl = tmem + ((uint32_t)(32 * (warp - 4)) << 16);
-#pragma unroll
-        for (int c = 0; c < TZ_TMEM_COLS; c += 16) tc_st16_zero(tl + c);
-        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
-    }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 
     // bounded wait on barrier i for the phase of parity par, by one thread; false on a timeout
     // or once another role gave up
@@ -463,6 +453,7 @@ __global__ void __launch_bounds__(TZ_THREADS, 1) k_pnet_conv_tcz(ConvArgs a, int
         // ---------------------------------------------------------------- MMA issuer
         if (lane == 0) {
             const unsigned long long adesc0 = tc_desc(rb, TZ_PHALF, 128), bdesc0 = tc_desc(wb, TZ_WQ / 2, 128);
+            const unsigned long long zdesc = tc_desc(smem_u32(zt), TW_ZERO / 2, 128);
             int issued = -1;
             for (int o = 0; o < zc; ++o) {
                 bool ok = true;
@@ -471,6 +462,10 @@ __global__ void __launch_bounds__(TZ_THREADS, 1) k_pnet_conv_tcz(ConvArgs a, int
                 if (!ok) break;
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 const uint32_t dset = tmem + (uint32_t)((o % TW_S) * 64);
+                // the set's 4 rows cleared: zero A times any 64 rows of weights, not accumulated
+                asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, 0, 0;\n"
+                             " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+                             ::"r"(dset), "l"(zdesc), "l"(bdesc0), "r"(tc_idesc(64)) : "memory");
                 unsigned long long abase[3];          // the plane's three input slots
 #pragma unroll
                 for (int dz = -1; dz <= 1; ++dz)
@@ -578,8 +573,6 @@ __global__ void __launch_bounds__(TZ_THREADS, 1) k_pnet_conv_tcz(ConvArgs a, int
 #pragma unroll
                 for (int r = 0; r < TZ_TY; ++r) tc_wait16(raw[r]);
 #pragma unroll
-                for (int r = 0; r < TZ_TY; ++r) tc_st16_zero(tl + 16 * r);    // the set starts its next plane cleared
-#pragma unroll
                 for (int r = 0; r < TZ_TY; ++r) {
                     float v[16];
 #pragma unroll
@@ -620,8 +613,6 @@ __global__ void __launch_bounds__(TZ_THREADS, 1) k_pnet_conv_tcz(ConvArgs a, int
                 for (int r = 0; r < TZ_TY; ++r) raw[r] = tc_ld1_async(tl + 16 * r);
                 tc_wait4(raw);
 #pragma unroll
-                for (int r = 0; r < TZ_TY; ++r) tc_st16_zero(tl + 16 * r);    // the set starts its next plane cleared
-#pragma unroll
                 for (int r = 0; r < TZ_TY; ++r) {
                     const double y = (double)(__uint_as_float(raw[r]) + b0);
                     if (EPI == 1) {
@@ -633,7 +624,6 @@ __global__ void __launch_bounds__(TZ_THREADS, 1) k_pnet_conv_tcz(ConvArgs a, int
                     }
                 }
             }
-            asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             __syncwarp();
             if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar + SETE + o % TW_S))
