@@ -254,31 +254,46 @@ __device__ __forceinline__ void xrow4_inv_body(int bx, const float2* __restrict_
     float msub = 0.f;
     if (SUBM) msub = (float)sc->mean_p;
     int emax = 0;
+    unsigned int fmax_bits = 0u;            // F32 && !ACC: the largest binary32 exponent field (in place)
     float sh = 0.f, sl = 0.f;               // the binary32 pair sum of MEAN
 #pragma unroll
     for (int n1 = 0; n1 < N1; ++n1) {
         float2 z = v[n1];
         if (SUBM) { z.x -= msub; z.y -= msub; }
-        double2 o;
-        if (ACC) {
-            if (PRE) o = pold[PRE ? n1 : 0];
-            else o = old_p(n1);
-            o.x += f2d_bits(z.x);
-            o.y += f2d_bits(z.y);
-        } else {
-            o = make_double2(f2d_bits(z.x), f2d_bits(z.y));
+        if constexpr (F32 && !ACC) {
+            // binary32 store; the exponent is read from the binary32 bits (mapped to the binary64
+            // field after the loop), with no conversion of the value
             if (MEAN) {
                 two_sum_acc(sh, sl, z.x);
                 two_sum_acc(sh, sl, z.y);
             }
+            if (live) d32[N2 * n1] = z;
+            fmax_bits = max(fmax_bits, max(__float_as_uint(z.x) & 0x7F800000u, __float_as_uint(z.y) & 0x7F800000u));
+        } else {
+            double2 o;
+            if (ACC) {
+                if (PRE) o = pold[PRE ? n1 : 0];
+                else o = old_p(n1);
+                o.x += f2d_bits(z.x);
+                o.y += f2d_bits(z.y);
+            } else {
+                o = make_double2(f2d_bits(z.x), f2d_bits(z.y));
+                if (MEAN) {
+                    two_sum_acc(sh, sl, z.x);
+                    two_sum_acc(sh, sl, z.y);
+                }
+            }
+            if (live) dst[N2 * n1] = o;
+            const int ex_ = (int)((__double_as_longlong(o.x) >> 52) & 0x7FF);
+            const int ey_ = (int)((__double_as_longlong(o.y) >> 52) & 0x7FF);
+            emax = max(emax, max(ex_, ey_));
         }
-        if (live) {
-            if (F32 && !ACC) d32[N2 * n1] = z;
-            else dst[N2 * n1] = o;
-        }
-        const int ex_ = (int)((__double_as_longlong(o.x) >> 52) & 0x7FF);
-        const int ey_ = (int)((__double_as_longlong(o.y) >> 52) & 0x7FF);
-        emax = max(emax, max(ex_, ey_));
+    }
+    if constexpr (F32 && !ACC) {
+        // the binary64 field of (double)x: 0 for zero and binary32 subnormals (f2d_bits flushes
+        // them), e + 896 for normal numbers, 2047 for infinities and NaNs
+        const int e32 = (int)(fmax_bits >> 23);
+        emax = e32 == 0 ? 0 : (e32 == 255 ? 2047 : e32 + 896);
     }
     emax = __reduce_max_sync(0xffffffffu, emax);
     if ((tid & 31) == 0) atomicMax(&sc->pexp, emax);

@@ -28,6 +28,16 @@ __global__ void __launch_bounds__(XROW_THREADS) k_xrow4_inv(const float2* __rest
     xrow4_inv_body<N1, N2, ACC, MEAN, SUBM, F32>(blockIdx.x, S, p, p32, g, tw, twr, nrows, sc, part);
 }
 
+// The first inverse into the binary32 iterate (p = x with the mean's sums, stored in p32): four
+// CTAs per SM where the rows are short enough (M <= 256).
+template <int N1, int N2>
+__global__ void __launch_bounds__(XROW_THREADS, N1 <= 16 ? 4 : 2) k_xrow4_inv_first32(
+        const float2* __restrict__ S, double* __restrict__ p, float* __restrict__ p32, Geo g,
+        const float2* __restrict__ tw, const float2* __restrict__ twr, int nrows, DevScalars* __restrict__ sc,
+        double* __restrict__ part) {
+    xrow4_inv_body<N1, N2, 0, true, false, true>(blockIdx.x, S, p, p32, g, tw, twr, nrows, sc, part);
+}
+
 template <typename K, typename... A>
 bool launch_rows(K kern, size_t smem, int nrows, int B, cudaStream_t st, A... args) {
     if (smem > 48 * 1024 &&
@@ -63,7 +73,7 @@ bool inv_n(flups_plan P, double* p, const Geo& g, int mode) {
                                    p, p32, g, tw, twr, nrows, P->sc, P->part);
         case 2: return launch_rows(k_xrow4_inv<N1, N2, 1, false, false, false>, X::SMEM, nrows, X::B, P->stream, S,
                                    p, p32, g, tw, twr, nrows, P->sc, P->part);
-        case 4: return p32 && launch_rows(k_xrow4_inv<N1, N2, 0, true, false, true>, X::SMEM, nrows, X::B,
+        case 4: return p32 && launch_rows(k_xrow4_inv_first32<N1, N2>, X::SMEM, nrows, X::B,
                                           P->stream, S, p, p32, g, tw, twr, nrows, P->sc, P->part);
         case 5: return p32 && launch_rows(k_xrow4_inv<N1, N2, 1, false, true, true>, X::SMEM, nrows, X::B,
                                           P->stream, S, p, p32, g, tw, twr, nrows, P->sc, P->part);
