@@ -96,8 +96,10 @@ KERNEL_WORK = {
 
 # On one-spacing grids where the z-marching defect and the register x rows apply, the first FP32
 # iterate is held in binary32 until the first update: the first inverse writes 4 B a point
-# instead of 8, the first defect and the first update read 4 B of p instead of 8.
-P32_FIRST = {"k_xinv32": 4 + 4, "k_xfwd_residual32": 8 + 4 + 4, "k_xinv_acc32": 4 + 4 + 8}
+# instead of 8, the first defect and the first update read 4 B of p instead of 8. The first
+# defect also writes f's fixed point F - MF (8 B a point), which the norm-only passes read in
+# place of f (the same 8 B).
+P32_FIRST = {"k_xinv32": 4 + 4, "k_xfwd_residual32": 8 + 4 + 4 + 8, "k_xinv_acc32": 4 + 4 + 8}
 
 
 def p32_first(c):

@@ -505,6 +505,9 @@ __device__ __forceinline__ long long fixf(float x, float ka, float kb) {
 // PT = float: p is the first FP32 iterate held in binary32 (rows of nx values, as p), read at
 // 4 bytes a point and taken to fixed point by fixf, the same integers as fixq of its binary64
 // value.
+// fq (one-spacing power-of-two grids, may be null): MODE 2 writes F - MF of every point it owns
+// (fqs[0] = the scale pexp it used, fqs[1] set where some point had no integer form); MODE 3
+// reads it instead of f, skipping f's conversion, when fqs shows the same scale and no gap.
 // As a body: G groups of M threads (the CTA's G row blocks j0 = (bx G + grp) 8 .. +7, consecutive,
 // of the planes by kz .. by kz + kz - 1), each group with its own shared rows; the Stockham tail
 // transforms the 8 G rows together (the four-step tail, N1 > 0, takes G = 1).  part[pidx]
@@ -515,7 +518,7 @@ __device__ __forceinline__ void xres_zm_body(int bx, int by, int G, const double
                                              const FftLen& L, const float2* __restrict__ tw,
                                              const float2* __restrict__ twr, int kz,
                                              const DevScalars* __restrict__ sc, double* __restrict__ part,
-                                             int pidx) {
+                                             int pidx, long long* __restrict__ fq, int* __restrict__ fqs) {
     static_assert(E == 8, "one pair position per thread over 8 rows");
     if (g.skip && *g.skip) return;   // graph-capturable solve: this member already converged
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -554,7 +557,12 @@ __device__ __forceinline__ void xres_zm_body(int bx, int by, int G, const double
         else return make_longlong2(fixq(v.x, sh), fixq(v.y, sh));
     };
     const P2T* P2 = reinterpret_cast<const P2T*>(p);
-    const double2* F2 = reinterpret_cast<const double2*>(f);
+    const bool fq_write = MODE == 2 && PF && fq != nullptr;   // the first defect only
+    const bool fq_read = MODE == 3 && fq != nullptr && ipath && fqs[1] == 0 && fqs[0] == pe_;
+    if (fq_write && pidx == 0 && threadIdx.x == 0) fqs[0] = ipath ? pe_ : -1;
+    bool fq_gap = false;
+    // the raw 64-bit values of f (binary64) or of F - MF (fq_read), [row][M] pairs either way
+    const longlong2* FR = fq_read ? reinterpret_cast<const longlong2*>(fq) : reinterpret_cast<const longlong2*>(f);
     const int nw_ = n == 0 ? M - 1 : n - 1, ne_ = n + 1 == M ? 0 : n + 1;
     auto prow = [&](int k, int j) { return P2 + ((size_t)k * g.ny + j) * M + n; };
     // LO[c M + n]: the centre of the plane below (thread n alone reads and writes column n)
@@ -584,9 +592,9 @@ __device__ __forceinline__ void xres_zm_body(int bx, int by, int G, const double
         // every global load of the plane first (p of plane k+1 with its y halo, f of plane k),
         // so that one memory latency per plane is exposed
         P2T pu[E + 2];
-        double2 fv[E];
+        longlong2 fr[E];
 #pragma unroll
-        for (int c = 0; c < E; ++c) fv[c] = __ldg(F2 + (row0 + c) * M + n);
+        for (int c = 0; c < E; ++c) fr[c] = __ldg(FR + (row0 + c) * M + n);
         const bool more = k + 1 < k1;
 #pragma unroll
         for (int r = 0; r < E + 2; ++r) {
@@ -605,16 +613,24 @@ __device__ __forceinline__ void xres_zm_body(int bx, int by, int G, const double
             long long s1 = qc.x + qe + qs.y + qn.y - nd * qc.y + ql.y + uq[c].y;
             LO[c * M + n] = qc;                // the lower neighbour of plane k+1
             bool ok0 = false, ok1 = false;
-            long long F0 = 0, F1 = 0;
-            if (ipath) {
-                F0 = fixw(fv[c].x, shf, ok0);
-                F1 = fixw(fv[c].y, shf, ok1);
+            long long F0 = 0, F1 = 0;            // F - MF
+            if (fq_read) {
+                ok0 = ok1 = true;
+                F0 = fr[c].x;
+                F1 = fr[c].y;
+            } else if (ipath) {
+                F0 = fixw(__longlong_as_double(fr[c].x), shf, ok0) - mfq;
+                F1 = fixw(__longlong_as_double(fr[c].y), shf, ok1) - mfq;
             }
             if (ok0 && ok1) {
-                zr[c] = make_float2(rscale * i64_to_f32(F0 - mfq - s0), rscale * i64_to_f32(F1 - mfq - s1));
+                zr[c] = make_float2(rscale * i64_to_f32(F0 - s0), rscale * i64_to_f32(F1 - s1));
             } else {
-                zr[c] = make_float2(d2f_bits(fma(-cfix, __ll2double_rn(s0), fv[c].x - mf)),
-                                    d2f_bits(fma(-cfix, __ll2double_rn(s1), fv[c].y - mf)));
+                zr[c] = make_float2(d2f_bits(fma(-cfix, __ll2double_rn(s0), __longlong_as_double(fr[c].x) - mf)),
+                                    d2f_bits(fma(-cfix, __ll2double_rn(s1), __longlong_as_double(fr[c].y) - mf)));
+            }
+            if (fq_write) {
+                fq_gap |= !(ok0 && ok1);
+                reinterpret_cast<longlong2*>(fq)[(row0 + c) * M + n] = make_longlong2(F0, F1);
             }
             acc2 = fmaf(zr[c].x, zr[c].x, fmaf(zr[c].y, zr[c].y, acc2));
         }
@@ -661,6 +677,7 @@ __device__ __forceinline__ void xres_zm_body(int bx, int by, int G, const double
             __syncthreads();
         }
     }
+    if (fq_write && __any_sync(0xffffffffu, fq_gap) && (threadIdx.x & 31) == 0) atomicExch(fqs + 1, 1);
     block_sum_abc<false, true, false>(0.0, acc2, 0.f, part, pidx);
 }
 
@@ -669,9 +686,10 @@ __global__ void __launch_bounds__(512, 1) k_xres_zm(const double* __restrict__ f
                                                    float2* __restrict__ S, Geo g, FftLen L,
                                                    const float2* __restrict__ tw, const float2* __restrict__ twr,
                                                    int kz, const DevScalars* __restrict__ sc,
-                                                   double* __restrict__ part) {
+                                                   double* __restrict__ part, long long* __restrict__ fq,
+                                                   int* __restrict__ fqs) {
     xres_zm_body<E, MODE, N1, N2, PT>(blockIdx.x, blockIdx.y, 1, f, p, S, g, L, tw, twr, kz, sc, part,
-                                      blockIdx.y * gridDim.x + blockIdx.x);
+                                      blockIdx.y * gridDim.x + blockIdx.x, fq, fqs);
 }
 
 // ------------------------------------------------------------- inverse along x (C2R)
@@ -1833,9 +1851,19 @@ void run_xfwd_e(flups_plan P, const double* f, const double* p, const Geo& g) {
                 allow_smem(kern, smem);
                 const int kz = xres_kz(g.ny, g.nz);
                 flups_prof_begin(P, MODE == 3 ? FK_XRES_NORM32 : FK_XFWD_RES32);
+                // f's fixed point: written by the first defect (on the binary32 iterate), read by
+                // the norm-only passes of the same solve
+                long long* fq = nullptr;
+                if (P->fq && MODE == 2 && sizeof(*pp) == 4) {
+                    cudaMemsetAsync(&P->sc->fq_bad, 0, sizeof(int), P->stream);
+                    fq = P->fq;
+                    P->fq_live = 1;
+                } else if (P->fq && MODE == 3 && P->fq_live) {
+                    fq = P->fq;
+                }
                 kern<<<dim3(g.ny / E, (g.nz + kz - 1) / kz), N, smem, P->stream>>>(
                     f, pp, (float2*)P->spec, g, packed(P->lx), (const float2*)P->twx, (const float2*)P->twxr, kz,
-                    P->sc, P->part);
+                    P->sc, P->part, fq, &P->sc->fq_pexp);
                 flups_prof_end(P);
                 FLUPS_COUNT(P, 1);
             };
@@ -2205,7 +2233,7 @@ __global__ void __launch_bounds__(FLUPS_BATCH_THREADS, KIND == 1 ? 2 : 3) k_b_xf
                                          D.sc, D.part);
     } else if (D.zm) {
         xres_zm_body<8, 2, 0, 0, double>(tile % D.zbx, tile / D.zbx, D.zg, D.f, D.p, D.spec, D.g, D.lx, D.twx, D.twxr,
-                                 D.zkz, D.sc, D.part, tile);
+                                 D.zkz, D.sc, D.part, tile, nullptr, nullptr);
     } else if (D.dmode == 2) {
         if (D.ex == 12)
             xfwd_body<float, 12, 2, false>(tile, D.f, D.p, D.spec, D.g, D.lx, D.twx, D.twxr, D.dd, D.lgx, nrows,
@@ -2392,6 +2420,7 @@ cudaError_t launch_add_const(flups_plan P, double* a, double c) {
 cudaError_t launch_xfwd32_from_f(flups_plan P, const double* f) {
     const Geo g = plan_geo(P);
     P->p32_live = 0;                       // a new solve: no binary32 iterate yet
+    P->fq_live = 0;                        // nor a fixed-point copy of f
     run_xfwd<float, 0, true>(P, f, nullptr, g);
     return cudaGetLastError();
 }

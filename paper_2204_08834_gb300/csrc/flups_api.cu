@@ -401,8 +401,10 @@ flups_status flups_plan_create_bc(flups_plan* out, int nx, int ny, int nz, doubl
     P->fin = (double*)A.get(3 * 256 * sizeof(double));
     P->tabs64 = (double*)A.get(6 * (size_t)nz * sizeof(double));
     if (ends && prec == FLUPS_FP32_REFINE) P->rbuf = (double*)A.get(P->npts * sizeof(double));
-    if (!ends && prec == FLUPS_FP32_REFINE && P->uniform_h && p32_path(P->M, ny))
+    if (!ends && prec == FLUPS_FP32_REFINE && P->uniform_h && p32_path(P->M, ny)) {
         P->p32 = (float*)A.get(P->npts * sizeof(float));
+        P->fq = (long long*)A.get(P->npts * sizeof(long long));
+    }
     bool ok = A.ok;
     if (ok) {
         std::vector<double> t(6 * (size_t)nz);

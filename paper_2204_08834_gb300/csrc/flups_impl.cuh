@@ -64,6 +64,8 @@ struct DevScalars {
     unsigned int fin_count;   // blocks of the running final reduction that have finished
     unsigned int mom_hmax;    // momentum predictor: high word of max(|u|, |v|, |w|)
     int    vof_bad;     // VoF step: a face had |u| dt / h above 1 (or not finite)
+    int    fq_pexp;     // scale (pexp) of the fixed-point F - MF written by the first defect (-1: none)
+    int    fq_bad;      // nonzero: some point of that F - MF could not be formed
 };
 
 // Geometry and tables handed to kernels by value.
@@ -135,6 +137,8 @@ struct flups_plan_s {
     void* twy2;                  // W_{ny/2} twiddles (mixed ends along y)
     double* rbuf;                // FP64 defect of the FP32+refine solve with ends (npts)
     float* p32;                  // the first FP32 iterate in binary32 (npts), where p32_path holds
+    long long* fq;               // F - MF of f at the first defect's scale (npts), where p32_path holds
+    int fq_live;                 // fq written in the current solve; host-side state
     int p32_live;                // p32 holds the current iterate (p not yet written); host-side state
     void* tri;                   // walls: a_k/norm, b_k/norm, c_k/norm, compute type (3*nz)
     double sum_dzf;
